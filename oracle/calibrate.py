@@ -1,0 +1,63 @@
+"""Calibrate the graph radius and the edge-score cut of a workload with the
+oracle (test infrastructure; run by hand, results recorded in the presets).
+
+The paper's networks are trained; here the weights are random, so the
+literal radii of the workload descriptions (0.05, 0.1) give almost no edges.
+This script picks, on the calibration events (seed 12345), the radius whose
+mean edge count per hit is ``EDGES_PER_HIT`` (about 20k edges for a
+1,740-hit event, the density the workloads ask for and close to the paper's
+30k edges for 2,200 hits, Sec. 5), and the logit cut whose kept fraction
+equals the genuine-edge fraction of that graph (the trained classifier keeps
+roughly the genuine edges, Sec. 5.2).
+
+    python -m oracle.calibrate batch500 plain
+"""
+from __future__ import annotations
+
+import json
+import sys
+
+import numpy as np
+
+from velo_synth import WORKLOADS, global_particle_ids, make_batch, truth_edge_labels
+from velo_synth.presets import CALIB_SEED
+
+from . import etx_oracle as O
+
+EDGES_PER_HIT = 11.5
+
+
+def calibrate(name: str, n_graph_events: int = 50, n_gnn_events: int = 3) -> dict:
+    wl = WORKLOADS[name]
+    cfg = wl.model
+    W = wl.weights()
+    depth = len(cfg.emb_widths) - 1
+    b = make_batch(wl.recipe, n_graph_events, CALIB_SEED)
+    emb = O.embed(W, depth, b.x, b.y, b.z)
+    lo, hi = 0.05, 8.0
+    for _ in range(30):
+        r = 0.5 * (lo + hi)
+        _, _, eo = O.build_graph(emb, b.plane, b.hit_offsets, r, cfg.k_max)
+        if eo[-1] / b.n_hits < EDGES_PER_HIT:
+            lo = r
+        else:
+            hi = r
+    radius = float(f"{0.5 * (lo + hi):.3g}")
+    _, _, eo = O.build_graph(emb, b.plane, b.hit_offsets, radius, cfg.k_max)
+    gb = make_batch(wl.recipe, n_gnn_events, CALIB_SEED)
+    gemb = O.embed(W, depth, gb.x, gb.y, gb.z)
+    s, d, _ = O.build_graph(gemb, gb.plane, gb.hit_offsets, radius, cfg.k_max)
+    z = O.gnn_forward(W, cfg.n_iters, gb.x, gb.y, gb.z, s, d)
+    y = truth_edge_labels(global_particle_ids(gb), gb.plane, s, d)
+    frac = float(y.mean()) if y.size else 0.0
+    thr = float(f"{np.quantile(z, 1.0 - frac):.6g}") if z.size else 0.0
+    return {"radius": radius, "edges_per_hit": float(eo[-1] / b.n_hits),
+            "edges_per_event": float(eo[-1] / b.n_events), "genuine_fraction": frac,
+            "threshold_logit": thr, "kept_fraction": float((z > thr).mean()) if z.size else 0.0,
+            "logit_mean": float(z.mean()) if z.size else 0.0,
+            "logit_std": float(z.std()) if z.size else 0.0}
+
+
+if __name__ == "__main__":
+    names = sys.argv[1:] or ["plain", "batch500"]
+    print(json.dumps({n: calibrate(n) for n in names}, indent=1))

@@ -1,0 +1,322 @@
+"""FP64 CPU oracle of the ETX4VELO hot path -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg may
+import this module.  The product path (the CUDA library and its Python
+binding) never imports, links or runs it, and this module shares no code
+with that path: it depends on numpy and on the seeded input generator
+(``velo_synth``) alone.
+
+Every function writes out the definition the paper gives, in FP64, with no
+blocking, fusion or reordering beyond what the definition states:
+
+  normalise / embed     Sec. 5.1 (normalised cylindrical inputs, footnote) and
+                        the embedding MLP of Sec. 5.1
+  d2                    Eq. 1
+  build_graph           Sec. 5.1: hits on plane p connect to hits on p+1 and
+                        p+2 with d2 below the cut, at most k_max per node
+                        (Sec. 7.2 keeps the nearest ones)
+  gnn_forward           Sec. 5.2: node and edge encoders, Eq. 4 messages,
+                        residual node then edge updates with distinct weights
+                        per step, edge classifier
+  weighted_bce          the training loss used here for the edge term of Eq. 5
+  gnn_backward          reverse-mode derivative of gnn_forward + loss, by hand
+  connected_components  weakly connected components of the purified hit graph
+                        (Sec. 5 overview, Sec. 7.3), by breadth-first search
+
+Readings where the paper is silent (also listed in the design notes):
+  * radius r is Euclidean: keep d2 < r*r (strict); the k_max cap is joint over
+    planes p+1 and p+2 and keeps the smallest (d2, j) pairs;
+  * edges point from the lower to the higher plane and are listed by (i, j);
+  * every MLP layer of the interaction network is Linear -> LayerNorm(eps
+    1e-5, biased variance, affine) -> ReLU, except the classifier's last
+    Linear; the embedding MLP is Linear -> ReLU with a bare last Linear;
+  * node network input [h, m_out, m_in], edge network input [e, h_i, h_j]
+    with the updated h, edge encoder input [h_i, h_j];
+  * an edge is kept iff its logit > 0 (score > 0.5);
+  * a track label is the smallest event-local hit index of the component.
+
+Parity of every function is pinned by the non-GPU tests (brute force,
+closed forms, invariants, torch float64 cross-checks and finite differences).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+LN_EPS = 1e-5
+
+
+# ----------------------------------------------------------------------------
+# input features and embedding (Sec. 5.1)
+# ----------------------------------------------------------------------------
+def cylindrical(x, y, z):
+    x = np.asarray(x, np.float64)
+    y = np.asarray(y, np.float64)
+    z = np.asarray(z, np.float64)
+    return np.stack([np.sqrt(x * x + y * y), np.arctan2(y, x), z], axis=1)
+
+
+def normalise(feat, mu, sigma):
+    return (feat - np.asarray(mu, np.float64)) / np.asarray(sigma, np.float64)
+
+
+def embed(weights, n_layers, x, y, z):
+    """Embedding MLP on normalised (r, phi, z): ReLU between layers, bare
+    output.  Returns [N, D] float64."""
+    a = normalise(cylindrical(x, y, z), weights["emb_mu"], weights["emb_sigma"])
+    for i in range(n_layers):
+        W = weights[f"emb{i}.W"].astype(np.float64)
+        b = weights[f"emb{i}.b"].astype(np.float64)
+        a = a @ W.T + b
+        if i < n_layers - 1:
+            a = np.maximum(a, 0.0)
+    return a
+
+
+# ----------------------------------------------------------------------------
+# rough graph (Eq. 1, Sec. 5.1, Sec. 7.2)
+# ----------------------------------------------------------------------------
+def d2_fp64(ea, eb):
+    """Eq. 1 for all pairs: ea [n, D], eb [m, D] -> [n, m]."""
+    diff = ea[:, None, :].astype(np.float64) - eb[None, :, :].astype(np.float64)
+    return (diff * diff).sum(-1)
+
+
+def d2_fp32(ea, eb):
+    """Eq. 1 evaluated in FP32, one IEEE rounding per operation, summed over
+    the embedding dimensions in index order (no fused multiply-add).  This is
+    the precision in which the cut and the nearest-k choice are decided when
+    both sides start from the same FP32 embedding."""
+    ea = np.asarray(ea, np.float32)
+    eb = np.asarray(eb, np.float32)
+    s = np.zeros((ea.shape[0], eb.shape[0]), np.float32)
+    for i in range(ea.shape[1]):
+        d = ea[:, None, i] - eb[None, :, i]
+        s = s + d * d
+    return s
+
+
+def build_graph(emb, plane, hit_offsets, radius, k_max, precision="fp64"):
+    """Per event: for hit i on plane p, candidates j on planes p+1, p+2 with
+    d2(i, j) < r^2; keep the k_max smallest by (d2, j); emit edges (i, j)
+    sorted by (i, j).  Indices are batch-global.
+
+    precision "fp64": d2 and r^2 in float64 (the definition);
+    precision "fp32": d2 by ``d2_fp32`` and r^2 = fl32(fl32(r) * fl32(r)).
+    Returns (src int64 [E], dst int64 [E], edge_offsets int64 [B+1])."""
+    plane = np.asarray(plane, np.int64)
+    hit_offsets = np.asarray(hit_offsets, np.int64)
+    if precision == "fp64":
+        r2 = float(radius) * float(radius)
+        dist = d2_fp64
+    elif precision == "fp32":
+        rf = np.float32(radius)
+        r2 = rf * rf
+        dist = d2_fp32
+    else:
+        raise ValueError(precision)
+    src_all, dst_all, counts = [], [], []
+    for b in range(hit_offsets.shape[0] - 1):
+        lo, hi = int(hit_offsets[b]), int(hit_offsets[b + 1])
+        ne = 0
+        pl = plane[lo:hi]
+        for p in np.unique(pl):
+            src_idx = lo + np.nonzero(pl == p)[0]
+            cand = lo + np.nonzero((pl == p + 1) | (pl == p + 2))[0]
+            if cand.size == 0:
+                continue
+            d2 = dist(emb[src_idx], emb[cand])
+            for row, i in enumerate(src_idx):
+                ok = d2[row] < r2
+                js, ds = cand[ok], d2[row][ok]
+                order = np.lexsort((js, ds))          # by d2, then j
+                keep = np.sort(js[order[:k_max]])
+                src_all.append(np.full(keep.size, i, np.int64))
+                dst_all.append(keep.astype(np.int64))
+                ne += keep.size
+        counts.append(ne)
+    src = np.concatenate(src_all) if src_all else np.zeros(0, np.int64)
+    dst = np.concatenate(dst_all) if dst_all else np.zeros(0, np.int64)
+    order = np.lexsort((dst, src))
+    eo = np.zeros(len(counts) + 1, np.int64)
+    np.cumsum(counts, out=eo[1:])
+    return src[order], dst[order], eo
+
+
+# ----------------------------------------------------------------------------
+# interaction network (Sec. 5.2, Eq. 4)
+# ----------------------------------------------------------------------------
+def layer_norm(a, g, be):
+    mu = a.mean(-1, keepdims=True)
+    var = ((a - mu) ** 2).mean(-1, keepdims=True)
+    rstd = 1.0 / np.sqrt(var + LN_EPS)
+    n = (a - mu) * rstd
+    return n * g + be, n, rstd
+
+
+def mlp_block(X, w, prefix, cache=None):
+    """Lin -> LN -> ReLU -> Lin -> LN -> ReLU on rows of X."""
+    f = lambda k: w[f"{prefix}.{k}"].astype(np.float64)
+    a1 = X @ f("W1").T + f("b1")
+    y1, n1, s1 = layer_norm(a1, f("g1"), f("be1"))
+    r1 = np.maximum(y1, 0.0)
+    a2 = r1 @ f("W2").T + f("b2")
+    y2, n2, s2 = layer_norm(a2, f("g2"), f("be2"))
+    out = np.maximum(y2, 0.0)
+    if cache is not None:
+        cache[prefix] = dict(X=X, y1=y1, n1=n1, s1=s1, r1=r1, y2=y2, n2=n2, s2=s2)
+    return out
+
+
+def messages(e, src, dst, n_nodes):
+    """Eq. 4: m_l = [sum over edges l->j of e_lj, sum over edges i->l of e_il]."""
+    H = e.shape[1]
+    m_out = np.zeros((n_nodes, H))
+    m_in = np.zeros((n_nodes, H))
+    np.add.at(m_out, src, e)
+    np.add.at(m_in, dst, e)
+    return np.concatenate([m_out, m_in], axis=1)
+
+
+def gnn_forward(weights, n_iters, x, y, z, src, dst, cache=None):
+    """Edge logits [E] (float64) of the interaction network."""
+    src = np.asarray(src, np.int64)
+    dst = np.asarray(dst, np.int64)
+    N = np.asarray(x).shape[0]
+    xin = normalise(np.stack([np.asarray(x, np.float64), np.asarray(y, np.float64),
+                              np.asarray(z, np.float64)], axis=1),
+                    weights["gnn_mu"], weights["gnn_sigma"])
+    h = mlp_block(xin, weights, "node_enc", cache)
+    e = mlp_block(np.concatenate([h[src], h[dst]], axis=1), weights, "edge_enc", cache)
+    for k in range(n_iters):
+        m = messages(e, src, dst, N)
+        h = h + mlp_block(np.concatenate([h, m], axis=1), weights, f"node{k}", cache)
+        e = e + mlp_block(np.concatenate([e, h[src], h[dst]], axis=1), weights, f"edge{k}", cache)
+    W1 = weights["cls.W1"].astype(np.float64)
+    a1 = e @ W1.T + weights["cls.b1"].astype(np.float64)
+    y1, n1, s1 = layer_norm(a1, weights["cls.g1"].astype(np.float64),
+                            weights["cls.be1"].astype(np.float64))
+    r1 = np.maximum(y1, 0.0)
+    logits = r1 @ weights["cls.W2"].astype(np.float64)[0] + float(weights["cls.b2"][0])
+    if cache is not None:
+        cache["cls"] = dict(X=e, y1=y1, n1=n1, s1=s1, r1=r1)
+        cache["meta"] = dict(N=N, src=src, dst=dst, n_iters=n_iters)
+    return logits
+
+
+# ----------------------------------------------------------------------------
+# loss and reverse pass
+# ----------------------------------------------------------------------------
+def softplus(t):
+    return np.logaddexp(0.0, t)
+
+
+def sigmoid(t):
+    return 0.5 * (1.0 + np.tanh(0.5 * t))
+
+
+def weighted_bce(logits, target, pos_weight=10.0):
+    """mean_e [ w y softplus(-z) + (1 - y) softplus(z) ] and d loss / d z."""
+    z = np.asarray(logits, np.float64)
+    yv = np.asarray(target, np.float64)
+    E = max(z.shape[0], 1)
+    loss = float(np.sum(pos_weight * yv * softplus(-z) + (1.0 - yv) * softplus(z)) / E)
+    dz = (-pos_weight * yv * sigmoid(-z) + (1.0 - yv) * sigmoid(z)) / E
+    return loss, dz
+
+
+def _ln_backward(dy, n, rstd, g):
+    """LayerNorm backward: returns (d input, d gamma, d beta)."""
+    dn = dy * g
+    H = n.shape[-1]
+    da = rstd * (dn - dn.sum(-1, keepdims=True) / H - n * (dn * n).sum(-1, keepdims=True) / H)
+    return da, (dy * n).sum(0), dy.sum(0)
+
+
+def _mlp_block_backward(dout, w, prefix, c, grads):
+    f = lambda k: w[f"{prefix}.{k}"].astype(np.float64)
+    dy2 = dout * (c["y2"] > 0)
+    da2, grads[f"{prefix}.g2"], grads[f"{prefix}.be2"] = _ln_backward(dy2, c["n2"], c["s2"], f("g2"))
+    grads[f"{prefix}.W2"] = da2.T @ c["r1"]
+    grads[f"{prefix}.b2"] = da2.sum(0)
+    dr1 = da2 @ f("W2")
+    dy1 = dr1 * (c["y1"] > 0)
+    da1, grads[f"{prefix}.g1"], grads[f"{prefix}.be1"] = _ln_backward(dy1, c["n1"], c["s1"], f("g1"))
+    grads[f"{prefix}.W1"] = da1.T @ c["X"]
+    grads[f"{prefix}.b1"] = da1.sum(0)
+    return da1 @ f("W1")
+
+
+def gnn_backward(weights, cache, dlogits):
+    """Gradients (float64) of sum_e dlogits[e] * logit[e] w.r.t. every
+    interaction-network parameter, by the chain rule through gnn_forward."""
+    meta = cache["meta"]
+    src, dst, N, L = meta["src"], meta["dst"], meta["N"], meta["n_iters"]
+    grads = {}
+    c = cache["cls"]
+    dz = np.asarray(dlogits, np.float64)
+    W2c = weights["cls.W2"].astype(np.float64)
+    grads["cls.W2"] = (dz @ c["r1"])[None, :]
+    grads["cls.b2"] = np.array([dz.sum()])
+    dr1 = dz[:, None] * W2c
+    dy1 = dr1 * (c["y1"] > 0)
+    da1, grads["cls.g1"], grads["cls.be1"] = _ln_backward(dy1, c["n1"], c["s1"],
+                                                          weights["cls.g1"].astype(np.float64))
+    grads["cls.W1"] = da1.T @ c["X"]
+    grads["cls.b1"] = da1.sum(0)
+    de = da1 @ weights["cls.W1"].astype(np.float64)
+    H = de.shape[1]
+    dh = np.zeros((N, H))
+    for k in reversed(range(L)):
+        # e_{k+1} = e_k + f_edge([e_k, h_{k+1}[src], h_{k+1}[dst]])
+        dX = _mlp_block_backward(de, weights, f"edge{k}", cache[f"edge{k}"], grads)
+        de = de + dX[:, :H]
+        np.add.at(dh, src, dX[:, H:2 * H])
+        np.add.at(dh, dst, dX[:, 2 * H:])
+        # h_{k+1} = h_k + f_node([h_k, m_out(e_k), m_in(e_k)])
+        dX = _mlp_block_backward(dh, weights, f"node{k}", cache[f"node{k}"], grads)
+        dh = dh + dX[:, :H]
+        de = de + dX[:, H:2 * H][src] + dX[:, 2 * H:][dst]
+    dX = _mlp_block_backward(de, weights, "edge_enc", cache["edge_enc"], grads)
+    np.add.at(dh, src, dX[:, :H])
+    np.add.at(dh, dst, dX[:, H:])
+    _mlp_block_backward(dh, weights, "node_enc", cache["node_enc"], grads)
+    return grads
+
+
+# ----------------------------------------------------------------------------
+# purified graph and tracks (Sec. 5 overview, Sec. 7.3)
+# ----------------------------------------------------------------------------
+def edge_mask(logits):
+    """Keep an edge iff its score exceeds 0.5, i.e. its logit is > 0."""
+    return np.asarray(logits) > 0
+
+
+def connected_components(src, dst, mask, hit_offsets):
+    """Weakly connected components of the kept edges, by breadth-first
+    search per event.  Returns int32 labels: for each hit, the smallest
+    event-local index in its component."""
+    hit_offsets = np.asarray(hit_offsets, np.int64)
+    N = int(hit_offsets[-1])
+    src = np.asarray(src, np.int64)[np.asarray(mask, bool)]
+    dst = np.asarray(dst, np.int64)[np.asarray(mask, bool)]
+    adj = [[] for _ in range(N)]
+    for a, b in zip(src.tolist(), dst.tolist()):
+        adj[a].append(b)
+        adj[b].append(a)
+    labels = np.full(N, -1, np.int64)
+    event_of = np.searchsorted(hit_offsets, np.arange(N), side="right") - 1
+    for s in range(N):  # ascending: the first node reached is the component minimum
+        if labels[s] >= 0:
+            continue
+        lab = s - hit_offsets[event_of[s]]
+        labels[s] = lab
+        frontier = [s]
+        while frontier:
+            nxt = []
+            for u in frontier:
+                for v in adj[u]:
+                    if labels[v] < 0:
+                        labels[v] = lab
+                        nxt.append(v)
+            frontier = nxt
+    return labels.astype(np.int32)

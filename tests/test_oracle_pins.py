@@ -1,0 +1,470 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle:
+closed forms, brute force, library routines (scipy, torch float64),
+invariants and finite differences.  CPU only."""
+import json
+import math
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+from oracle import etx_oracle as O
+from velo_synth import (WORKLOADS, ModelConfig, Z_PLANES, concat_events, global_particle_ids,
+                        make_batch, make_weights, truth_edge_labels)
+
+GOLDEN = Path(__file__).parent / "golden"
+TINY = ModelConfig(emb_widths=(3, 16, 16, 4), hidden=16, n_iters=2, radius=1.0, k_max=4)
+
+
+def tiny_batch(n_events=3, seed=0):
+    return make_batch(WORKLOADS["plain"].recipe, n_events, 100 + seed)
+
+
+def random_event_arrays(rng, n, n_planes=5, D=3):
+    plane = np.sort(rng.integers(0, n_planes, size=n)).astype(np.int8)
+    emb = rng.normal(size=(n, D))
+    return emb, plane
+
+
+# ---------------------------------------------------------------------------
+# embedding (Sec. 5.1)
+# ---------------------------------------------------------------------------
+def test_embed_closed_form_golden():
+    g = json.loads((GOLDEN / "embed_closed_form.json").read_text())
+    w = {"emb_mu": np.zeros(3), "emb_sigma": np.ones(3),
+         "emb0.W": np.eye(3), "emb0.b": np.zeros(3),
+         "emb1.W": np.array(g["W1"], float), "emb1.b": np.array(g["b1"], float)}
+    for case in g["cases"]:
+        out = O.embed(w, 2, [case["x"]], [case["y"]], [case["z"]])[0]
+        np.testing.assert_allclose(out, case["expected"], rtol=0, atol=1e-12)
+
+
+def test_embed_normalisation_is_affine():
+    # doubling sigma and shifting mu must equal transforming the raw features
+    rng = np.random.default_rng(3)
+    x, y, z = rng.normal(size=(3, 7)) * 10
+    W = {"emb_mu": np.array([1.0, -0.5, 2.0]), "emb_sigma": np.array([2.0, 0.5, 4.0]),
+         "emb0.W": np.eye(3), "emb0.b": np.full(3, 100.0),   # +100 keeps ReLU linear
+         "emb1.W": np.eye(3), "emb1.b": np.full(3, -100.0)}
+    out = O.embed(W, 2, x, y, z)
+    r = np.hypot(x, y)
+    phi = np.arctan2(y, x)
+    ref = np.stack([(r - 1.0) / 2.0, (phi + 0.5) / 0.5, (z - 2.0) / 4.0], 1)
+    np.testing.assert_allclose(out, ref, atol=1e-12)
+
+
+def test_embed_matches_torch_float64():
+    torch = pytest.importorskip("torch")
+    wl = WORKLOADS["plain"]
+    b = tiny_batch(1)
+    W = make_weights(wl.model, b, perturb=0.2)
+    depth = len(wl.model.emb_widths) - 1
+    feats = np.stack([np.hypot(b.x.astype(float), b.y.astype(float)),
+                      np.arctan2(b.y.astype(float), b.x.astype(float)), b.z.astype(float)], 1)
+    t = (torch.tensor(feats) - torch.tensor(W["emb_mu"], dtype=torch.float64)) / \
+        torch.tensor(W["emb_sigma"], dtype=torch.float64)
+    layers = []
+    for i in range(depth):
+        lin = torch.nn.Linear(wl.model.emb_widths[i], wl.model.emb_widths[i + 1]).double()
+        with torch.no_grad():
+            lin.weight.copy_(torch.tensor(W[f"emb{i}.W"], dtype=torch.float64))
+            lin.bias.copy_(torch.tensor(W[f"emb{i}.b"], dtype=torch.float64))
+        layers.append(lin)
+        if i < depth - 1:
+            layers.append(torch.nn.ReLU())
+    with torch.no_grad():
+        ref = torch.nn.Sequential(*layers)(t).numpy()
+    np.testing.assert_allclose(O.embed(W, depth, b.x, b.y, b.z), ref, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Eq. 1 and the rough graph (Sec. 5.1, Sec. 7.2)
+# ---------------------------------------------------------------------------
+def test_d2_matches_scipy_cdist():
+    from scipy.spatial.distance import cdist
+    rng = np.random.default_rng(1)
+    a, b = rng.normal(size=(9, 8)), rng.normal(size=(11, 8))
+    np.testing.assert_allclose(O.d2_fp64(a, b), cdist(a, b, "sqeuclidean"), rtol=1e-12)
+
+
+def test_d2_fp32_properties():
+    rng = np.random.default_rng(2)
+    a = rng.normal(size=(20, 8)).astype(np.float32)
+    b = rng.normal(size=(30, 8)).astype(np.float32)
+    s = O.d2_fp32(a, b)
+    assert s.dtype == np.float32
+    # exact symmetry: (a-b)^2 == (b-a)^2 in IEEE arithmetic
+    np.testing.assert_array_equal(s, O.d2_fp32(b, a).T)
+    np.testing.assert_array_equal(np.diag(O.d2_fp32(a, a)), np.zeros(20, np.float32))
+    # within the FP32 rounding bound of the exact value (2D+1 roundings)
+    ref = O.d2_fp64(a.astype(np.float64), b.astype(np.float64))
+    assert np.all(np.abs(s - ref) <= (2 * 8 + 1) * 2.0 ** -24 * ref + 1e-30)
+
+
+def brute_force_graph(emb, plane, hit_offsets, radius, k_max, fp32=False):
+    """All-pairs reference written with plain Python loops."""
+    edges = []
+    for b in range(len(hit_offsets) - 1):
+        lo, hi = int(hit_offsets[b]), int(hit_offsets[b + 1])
+        for i in range(lo, hi):
+            cands = []
+            for j in range(lo, hi):
+                if int(plane[j]) - int(plane[i]) not in (1, 2):
+                    continue
+                if fp32:
+                    s = np.float32(0)
+                    for d in range(emb.shape[1]):
+                        t = np.float32(emb[i, d]) - np.float32(emb[j, d])
+                        s = np.float32(s + np.float32(t * t))
+                    r2 = np.float32(radius) * np.float32(radius)
+                    d2 = float(s)
+                    ok = s < r2
+                else:
+                    d2 = sum((float(emb[i, d]) - float(emb[j, d])) ** 2 for d in range(emb.shape[1]))
+                    ok = d2 < radius * radius
+                if ok:
+                    cands.append((d2, j))
+            cands.sort()
+            for _, j in sorted(cands[:k_max], key=lambda t: t[1]):
+                edges.append((i, j))
+    return edges
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("fp32", [False, True])
+def test_graph_brute_force(seed, fp32):
+    rng = np.random.default_rng(seed)
+    parts_emb, parts_plane, offs = [], [], [0]
+    for n in (0, 37, 1, 52, 20):  # includes an empty and a single-hit event
+        e, p = random_event_arrays(rng, n, n_planes=6, D=3)
+        parts_emb.append(e)
+        parts_plane.append(p)
+        offs.append(offs[-1] + n)
+    emb = np.concatenate(parts_emb) if offs[-1] else np.zeros((0, 3))
+    plane = np.concatenate(parts_plane)
+    if fp32:
+        emb = emb.astype(np.float32)
+    radius, k = 1.3, 3
+    s, d, eo = O.build_graph(emb, plane, np.array(offs), radius, k,
+                             precision="fp32" if fp32 else "fp64")
+    ref = brute_force_graph(emb, plane, offs, radius, k, fp32=fp32)
+    assert list(zip(s.tolist(), d.tolist())) == ref
+    for b in range(len(offs) - 1):
+        es = slice(int(eo[b]), int(eo[b + 1]))
+        assert np.all((s[es] >= offs[b]) & (s[es] < offs[b + 1]))
+        assert np.all((d[es] >= offs[b]) & (d[es] < offs[b + 1]))
+
+
+def test_graph_special_cases():
+    rng = np.random.default_rng(5)
+    emb, _ = random_event_arrays(rng, 30, D=4)
+    one_plane = np.full(30, 3, np.int8)
+    s, d, eo = O.build_graph(emb, one_plane, np.array([0, 30]), 1e9, 10 ** 6)
+    assert s.size == 0 and eo.tolist() == [0, 0]
+    # r = inf, k = inf: complete p -> p+1, p+2 bipartite graph
+    plane = np.sort(rng.integers(0, 6, size=30)).astype(np.int8)
+    s, d, eo = O.build_graph(emb, plane, np.array([0, 30]), np.inf, 10 ** 6)
+    n_p = np.bincount(plane, minlength=8)
+    expected = sum(int(n_p[p]) * (int(n_p[p + 1]) + int(n_p[p + 2])) for p in range(6))
+    assert s.size == expected
+    assert np.all(np.isin(plane[d] - plane[s], [1, 2]))
+    # k = 1 keeps the nearest candidate of every hit
+    s1, d1, _ = O.build_graph(emb, plane, np.array([0, 30]), np.inf, 1)
+    for i, j in zip(s1, d1):
+        cand = np.nonzero(np.isin(plane - plane[i], [1, 2]))[0]
+        dist = ((emb[cand] - emb[i]) ** 2).sum(1)
+        assert j == cand[np.lexsort((cand, dist))[0]]
+    # empty batch
+    s, d, eo = O.build_graph(np.zeros((0, 4)), np.zeros(0, np.int8), np.array([0, 0, 0]), 1.0, 5)
+    assert s.size == 0 and eo.tolist() == [0, 0, 0]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_graph_cut_is_strict(precision):
+    # d2 exactly equal to r^2 (0.25 = 0.5^2, exact in binary) is outside the cut
+    emb = np.array([[0.0, 0.0], [0.5, 0.0], [0.0, -0.25], [0.0, -0.5]])
+    plane = np.array([0, 1, 1, 2], np.int8)
+    s, d, _ = O.build_graph(emb, plane, np.array([0, 4]), 0.5, 8, precision=precision)
+    assert list(zip(s.tolist(), d.tolist())) == [(0, 2), (2, 3)]
+
+
+def test_graph_ties_broken_by_index():
+    # three candidates at exactly the same distance: the lowest indices win
+    emb = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0], [-1.0, 0.0]])
+    plane = np.array([0, 1, 1, 2], np.int8)
+    s, d, _ = O.build_graph(emb, plane, np.array([0, 4]), 2.0, 2)
+    assert list(zip(s.tolist(), d.tolist()))[:2] == [(0, 1), (0, 2)]
+
+
+# ---------------------------------------------------------------------------
+# messages (Eq. 4)
+# ---------------------------------------------------------------------------
+def test_messages_are_incidence_products():
+    import scipy.sparse as sp
+    rng = np.random.default_rng(7)
+    N, E, H = 13, 40, 5
+    src, dst = rng.integers(0, N, E), rng.integers(0, N, E)
+    e = rng.normal(size=(E, H))
+    m = O.messages(e, src, dst, N)
+    S_out = sp.csr_matrix((np.ones(E), (src, np.arange(E))), shape=(N, E))
+    S_in = sp.csr_matrix((np.ones(E), (dst, np.arange(E))), shape=(N, E))
+    np.testing.assert_allclose(m[:, :H], S_out @ e, atol=1e-12)
+    np.testing.assert_allclose(m[:, H:], S_in @ e, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# interaction network (Sec. 5.2)
+# ---------------------------------------------------------------------------
+def small_problem(H=16, L=2, n_events=2, seed=0, perturb=0.3):
+    cfg = ModelConfig(emb_widths=(3, 16, 16, 4), hidden=H, n_iters=L, radius=1.5, k_max=6)
+    b = tiny_batch(n_events, seed)
+    W = make_weights(cfg, b, seed=seed, perturb=perturb)
+    emb = O.embed(W, 3, b.x, b.y, b.z)
+    s, d, eo = O.build_graph(emb, b.plane, b.hit_offsets, cfg.radius, cfg.k_max)
+    return cfg, b, W, s, d, eo
+
+
+def test_gnn_permutation_equivariance():
+    cfg, b, W, s, d, _ = small_problem()
+    z = O.gnn_forward(W, cfg.n_iters, b.x, b.y, b.z, s, d)
+    rng = np.random.default_rng(11)
+    N, E = b.n_hits, s.size
+    hp = rng.permutation(N)            # new index of hit i is inv[i]
+    inv = np.empty(N, np.int64)
+    inv[hp] = np.arange(N)
+    ep = rng.permutation(E)
+    z2 = O.gnn_forward(W, cfg.n_iters, b.x[hp], b.y[hp], b.z[hp], inv[s][ep], inv[d][ep])
+    np.testing.assert_allclose(z2, z[ep], rtol=0, atol=1e-12)
+
+
+def test_gnn_zero_step_networks_are_identity():
+    # blocks whose last Linear and LN shift are zero add exactly 0 (ReLU(LN(0)*g + 0) = 0),
+    # so L such steps must equal L = 0 (residual structure of the node/edge updates)
+    cfg, b, W, s, d, _ = small_problem(L=3)
+    W0 = dict(W)
+    for k in range(3):
+        for net in ("node", "edge"):
+            W0[f"{net}{k}.W2"] = np.zeros_like(W[f"{net}{k}.W2"])
+            W0[f"{net}{k}.b2"] = np.zeros_like(W[f"{net}{k}.b2"])
+            W0[f"{net}{k}.be2"] = np.zeros_like(W[f"{net}{k}.be2"])
+    z3 = O.gnn_forward(W0, 3, b.x, b.y, b.z, s, d)
+    z0 = O.gnn_forward(W0, 0, b.x, b.y, b.z, s, d)
+    np.testing.assert_array_equal(z3, z0)
+
+
+def test_gnn_hidden1_closed_form():
+    # H = 1: LayerNorm of one value is 0, so every block outputs ReLU(beta2); the
+    # residual streams just add those constants and logit = W2 * ReLU(be1) + b2
+    cfg = ModelConfig(emb_widths=(3, 16, 16, 4), hidden=1, n_iters=3)
+    b = tiny_batch(1)
+    W = make_weights(cfg, b, perturb=1.0)
+    s = np.array([0, 0, 5]); d = np.array([3, 4, 9])
+    z = O.gnn_forward(W, 3, b.x, b.y, b.z, s, d)
+    e = max(W["edge_enc.be2"][0], 0.0) + sum(max(W[f"edge{k}.be2"][0], 0.0) for k in range(3))
+    assert e >= 0  # e only enters through LN, which discards it for H = 1
+    expected = float(W["cls.W2"][0, 0]) * max(float(W["cls.be1"][0]), 0.0) + float(W["cls.b2"][0])
+    np.testing.assert_allclose(z, expected, atol=1e-12)
+
+
+def test_gnn_event_batching_invariance():
+    cfg, b, W, s, d, eo = small_problem(n_events=3)
+    z = O.gnn_forward(W, cfg.n_iters, b.x, b.y, b.z, s, d)
+    for ev in range(3):
+        lo, hi = int(b.hit_offsets[ev]), int(b.hit_offsets[ev + 1])
+        es = slice(int(eo[ev]), int(eo[ev + 1]))
+        zi = O.gnn_forward(W, cfg.n_iters, b.x[lo:hi], b.y[lo:hi], b.z[lo:hi], s[es] - lo, d[es] - lo)
+        np.testing.assert_allclose(zi, z[es], atol=1e-12)
+
+
+def torch_reference_forward(torch, W, L, x, y, z, src, dst):
+    """Independent float64 restatement with torch.nn modules and index_add_."""
+    t = lambda a: torch.tensor(np.asarray(a, np.float64))
+    H = W["node_enc.W1"].shape[0]
+
+    def block(X, p):
+        seq = torch.nn.Sequential(torch.nn.Linear(X.shape[1], H), torch.nn.LayerNorm(H, eps=1e-5),
+                                  torch.nn.ReLU(), torch.nn.Linear(H, H),
+                                  torch.nn.LayerNorm(H, eps=1e-5), torch.nn.ReLU()).double()
+        seq[0].weight = torch.nn.Parameter(t(W[p + ".W1"]))
+        seq[0].bias = torch.nn.Parameter(t(W[p + ".b1"]))
+        seq[1].weight = torch.nn.Parameter(t(W[p + ".g1"]))
+        seq[1].bias = torch.nn.Parameter(t(W[p + ".be1"]))
+        seq[3].weight = torch.nn.Parameter(t(W[p + ".W2"]))
+        seq[3].bias = torch.nn.Parameter(t(W[p + ".b2"]))
+        seq[4].weight = torch.nn.Parameter(t(W[p + ".g2"]))
+        seq[4].bias = torch.nn.Parameter(t(W[p + ".be2"]))
+        return seq(X), list(seq.parameters())
+
+    params = {}
+    si, di = torch.tensor(src), torch.tensor(dst)
+    xin = (torch.stack([t(x), t(y), t(z)], 1) - t(W["gnn_mu"])) / t(W["gnn_sigma"])
+    h, params["node_enc"] = block(xin, "node_enc")
+    e, params["edge_enc"] = block(torch.cat([h[si], h[di]], 1), "edge_enc")
+    N = h.shape[0]
+    for k in range(L):
+        mo = torch.zeros(N, H, dtype=torch.float64).index_add_(0, si, e)
+        mi = torch.zeros(N, H, dtype=torch.float64).index_add_(0, di, e)
+        dh, params[f"node{k}"] = block(torch.cat([h, mo, mi], 1), f"node{k}")
+        h = h + dh
+        de, params[f"edge{k}"] = block(torch.cat([e, h[si], h[di]], 1), f"edge{k}")
+        e = e + de
+    c1 = torch.nn.Linear(H, H).double()
+    c1.weight = torch.nn.Parameter(t(W["cls.W1"]))
+    c1.bias = torch.nn.Parameter(t(W["cls.b1"]))
+    ln = torch.nn.LayerNorm(H, eps=1e-5).double()
+    ln.weight = torch.nn.Parameter(t(W["cls.g1"]))
+    ln.bias = torch.nn.Parameter(t(W["cls.be1"]))
+    c2 = torch.nn.Linear(H, 1).double()
+    c2.weight = torch.nn.Parameter(t(W["cls.W2"]))
+    c2.bias = torch.nn.Parameter(t(W["cls.b2"]))
+    logits = c2(torch.relu(ln(c1(e))))[:, 0]
+    params["cls"] = [c1.weight, c1.bias, ln.weight, ln.bias, c2.weight, c2.bias]
+    return logits, params
+
+
+def test_gnn_forward_and_backward_match_torch_autograd():
+    torch = pytest.importorskip("torch")
+    cfg, b, W, s, d, _ = small_problem(H=16, L=2, n_events=2)
+    cache = {}
+    z = O.gnn_forward(W, cfg.n_iters, b.x, b.y, b.z, s, d, cache)
+    zt, params = torch_reference_forward(torch, W, cfg.n_iters, b.x, b.y, b.z, s, d)
+    np.testing.assert_allclose(z, zt.detach().numpy(), atol=1e-10)
+    y = truth_edge_labels(global_particle_ids(b), b.plane, s, d)
+    loss, dz = O.weighted_bce(z, y, 10.0)
+    lt = torch.nn.functional.binary_cross_entropy_with_logits(
+        zt, torch.tensor(y, dtype=torch.float64), pos_weight=torch.tensor(10.0, dtype=torch.float64))
+    np.testing.assert_allclose(loss, float(lt), rtol=1e-12)
+    lt.backward()
+    grads = O.gnn_backward(W, cache, dz)
+    names = ["W1", "b1", "g1", "be1", "W2", "b2", "g2", "be2"]
+    for blk, plist in params.items():
+        nm = ["W1", "b1", "g1", "be1", "W2", "b2"] if blk == "cls" else names
+        for n, p in zip(nm, plist):
+            np.testing.assert_allclose(grads[f"{blk}.{n}"], p.grad.numpy(), rtol=1e-8, atol=1e-12,
+                                       err_msg=f"{blk}.{n}")
+
+
+def test_backward_central_finite_differences():
+    cfg, b, W, s, d, _ = small_problem(H=16, L=2, n_events=1, perturb=0.3)
+    y = truth_edge_labels(global_particle_ids(b), b.plane, s, d)
+    Wd = {k: np.asarray(v, np.float64) for k, v in W.items()}
+    cache = {}
+    z = O.gnn_forward(Wd, cfg.n_iters, b.x, b.y, b.z, s, d, cache)
+    _, dz = O.weighted_bce(z, y)
+    grads = O.gnn_backward(Wd, cache, dz)
+    rng = np.random.default_rng(0)
+    h = 1e-6
+    for name in ["node_enc.W1", "edge_enc.g2", "node0.W1", "node1.b1", "edge0.W2", "edge1.be1",
+                 "cls.W1", "cls.W2", "cls.b2"]:
+        flat = Wd[name].reshape(-1)
+        idx = rng.choice(flat.size, size=min(6, flat.size), replace=False)
+        fd, an = [], []
+        for i in idx:
+            old = flat[i]
+            flat[i] = old + h
+            lp, _ = O.weighted_bce(O.gnn_forward(Wd, cfg.n_iters, b.x, b.y, b.z, s, d), y)
+            flat[i] = old - h
+            lm, _ = O.weighted_bce(O.gnn_forward(Wd, cfg.n_iters, b.x, b.y, b.z, s, d), y)
+            flat[i] = old
+            fd.append((lp - lm) / (2 * h))
+            an.append(grads[name].reshape(-1)[i])
+        fd, an = np.array(fd), np.array(an)
+        assert np.linalg.norm(fd - an) <= 1e-6 * max(np.linalg.norm(fd), 1e-8) + 1e-9, name
+
+
+def test_weighted_bce_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(4)
+    z = rng.normal(size=50) * 3
+    y = (rng.uniform(size=50) < 0.3).astype(float)
+    zt = torch.tensor(z, requires_grad=True)
+    lt = torch.nn.functional.binary_cross_entropy_with_logits(
+        zt, torch.tensor(y), pos_weight=torch.tensor(10.0, dtype=torch.float64))
+    lt.backward()
+    loss, dz = O.weighted_bce(z, y, 10.0)
+    np.testing.assert_allclose(loss, float(lt), rtol=1e-13)
+    np.testing.assert_allclose(dz, zt.grad.numpy(), rtol=1e-12, atol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# components (Sec. 5 overview, Sec. 7.3)
+# ---------------------------------------------------------------------------
+def scipy_labels(src, dst, mask, hit_offsets):
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+    N = int(hit_offsets[-1])
+    m = np.asarray(mask, bool)
+    A = sp.coo_matrix((np.ones(int(m.sum())), (np.asarray(src)[m], np.asarray(dst)[m])), shape=(N, N))
+    _, comp = connected_components(A, directed=True, connection="weak")
+    first = {}
+    for i in range(N):
+        first.setdefault(comp[i], i)
+    ev = np.searchsorted(hit_offsets, np.arange(N), side="right") - 1
+    return np.array([first[comp[i]] - hit_offsets[ev[i]] for i in range(N)], np.int64)
+
+
+def test_cc_matches_scipy_random_graphs():
+    rng = np.random.default_rng(9)
+    offs = np.array([0, 0, 40, 41, 90, 150])
+    src, dst = [], []
+    for b in range(5):
+        lo, hi = offs[b], offs[b + 1]
+        if hi - lo < 2:
+            continue
+        ne = rng.integers(0, 2 * (hi - lo))
+        src.append(rng.integers(lo, hi, ne))
+        dst.append(rng.integers(lo, hi, ne))
+    src, dst = np.concatenate(src), np.concatenate(dst)
+    mask = rng.uniform(size=src.size) < 0.4
+    lab = O.connected_components(src, dst, mask, offs)
+    np.testing.assert_array_equal(lab, scipy_labels(src, dst, mask, offs))
+
+
+def test_cc_golden_graphs():
+    for case in json.loads((GOLDEN / "wcc_graphs.json").read_text())["cases"]:
+        lab = O.connected_components(case["src"], case["dst"], case["mask"], case["hit_offsets"])
+        assert lab.tolist() == case["labels"], case["name"]
+
+
+def test_cc_truth_edges_reproduce_particles():
+    b = make_batch(WORKLOADS["batch500"].recipe, 3, 1000)
+    pid = global_particle_ids(b)
+    src, dst = [], []
+    for p in np.unique(pid[pid >= 0]):
+        hits = np.nonzero(pid == p)[0]
+        hits = hits[np.argsort(b.plane[hits], kind="stable")]
+        src.append(hits[:-1])
+        dst.append(hits[1:])
+    src, dst = np.concatenate(src), np.concatenate(dst)
+    y = truth_edge_labels(pid, b.plane, src, dst)
+    assert y.min() == 1.0  # the generator's truth agrees: every such edge is genuine
+    lab = O.connected_components(src, dst, np.ones(src.size, bool), b.hit_offsets)
+    ev = np.searchsorted(b.hit_offsets, np.arange(b.n_hits), side="right") - 1
+    glab = lab + b.hit_offsets[ev]
+    for p in np.unique(pid[pid >= 0]):
+        hits = np.nonzero(pid == p)[0]
+        assert np.all(glab[hits] == hits.min())
+    noise = np.nonzero(pid < 0)[0]
+    assert np.all(glab[noise] == noise)
+
+
+def test_generator_geometry():
+    b = make_batch(WORKLOADS["batch500"].recipe, 4, 1000)
+    r = np.hypot(b.x.astype(float), b.y.astype(float))
+    assert np.all((r > 5.0) & (r < 40.1))
+    np.testing.assert_array_equal(b.z, Z_PLANES[b.plane].astype(np.float32))
+    for e in range(b.n_events):
+        p = b.plane[b.hit_offsets[e]:b.hit_offsets[e + 1]]
+        assert np.all(np.diff(p.astype(int)) >= 0)
+    # an event is identical alone and inside a batch
+    one = make_batch(WORKLOADS["batch500"].recipe, 1, 1002)
+    lo, hi = b.hit_offsets[2], b.hit_offsets[3]
+    np.testing.assert_array_equal(one.x, b.x[lo:hi])
+    # straight tracks from the vertex: hits of one particle share phi
+    pid = b.particle_id[b.hit_offsets[0]:b.hit_offsets[1]]
+    x, y = b.x[:b.hit_offsets[1]], b.y[:b.hit_offsets[1]]
+    for p in np.unique(pid[pid >= 0])[:10]:
+        ph = np.arctan2(y[pid == p], x[pid == p])
+        assert np.ptp(np.unwrap(ph)) < 0.01
+    assert concat_events([]).n_hits == 0
+    assert math.isclose(float(np.diff(b.hit_offsets).mean()), 1700, rel_tol=0.5)
