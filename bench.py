@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Throughput of the ETX4VELO hot path on GB300: events/s from hits to track
+labels for a 500-event batch of synthetic VELO-like events.
+
+One step = embedding -> graph -> interaction network -> components over the
+whole batch, inputs resident in HBM (``value``); ``e2e`` is the same step
+through the public API from pinned host buffers, copies included.
+
+    python bench.py [--gpus N --steps K --warmup W --dtype f32 --impl ours|reference]
+
+Multi-GPU (torchrun, one rank per GPU): every rank runs its own replica of
+the workload (events are independent, so there is no collective on the data
+path); ``value`` = events of all ranks / max over ranks of the timed span.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "events/s (hits->tracks, 500-event batch)"
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="batch500")
+    p.add_argument("--dtype", default="f32", choices=["f32", "bf16", "fp8"])
+    p.add_argument("--cpu-seconds", type=float, default=15.0,
+                   help="budget of the oracle CPU baseline sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ---------------------------------------------------------------------------
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", self.gpu_id], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(self.NAMES, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_query_id(local_rank: int) -> str:
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(0).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(local_rank)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per launch of the kernels that can dominate
+# ---------------------------------------------------------------------------
+def kernel_work(name: str, H: int, E: int, N: int, D: int, emb_widths) -> tuple:
+    """(bound, amount, unit) for one launch; FLOPs counted as 2 per FMA."""
+    gnn_block = 2 * (3 * H * H + H * H)
+    if name.startswith("gnn_edge_update"):
+        return "flop", E * gnn_block
+    if name.startswith("gnn_node_update"):
+        return "flop", N * gnn_block
+    if name.startswith("gnn_edge_encoder"):
+        return "flop", E * 2 * (2 * H * H + H * H)
+    if name.startswith("gnn_classifier"):
+        return "flop", E * 2 * (H * H + H)
+    if name.startswith("embed"):
+        w = list(emb_widths)
+        return "flop", N * sum(2 * w[i] * w[i + 1] for i in range(len(w) - 1))
+    if name == "gnn_messages":
+        return "byte", 2 * E * H * 4 + 4 * E + 2 * N * H * 4 + 8 * N
+    return "byte", 0
+
+
+# ---------------------------------------------------------------------------
+# oracle baseline (CPU)
+# ---------------------------------------------------------------------------
+def oracle_events_per_s(wl, W, batch, seconds: float, max_events: int | None = None):
+    from oracle import etx_oracle as O
+    m = wl.model
+    depth = len(m.emb_widths) - 1
+    done, t0 = 0, time.perf_counter()
+    order = list(range(batch.n_events))
+    while True:
+        b = batch.event(order[done % len(order)])
+        emb = O.embed(W, depth, b.x, b.y, b.z)
+        s, d, _ = O.build_graph(emb, b.plane, b.hit_offsets, m.radius, m.k_max)
+        z = O.gnn_forward(W, m.n_iters, b.x, b.y, b.z, s, d)
+        O.connected_components(s, d, z > m.threshold_logit, b.hit_offsets)
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or (max_events and done >= max_events):
+            return done / el, done, el
+
+
+def cpu_threads() -> int:
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from velo_synth import WORKLOADS
+    wl = WORKLOADS[args.workload]
+    batch = wl.batch()
+    W = wl.weights()
+    for _ in range(args.warmup):
+        oracle_events_per_s(wl, W, batch, 0.0, max_events=1)
+    per = []
+    n_total, t_total = 0, 0.0
+    for _ in range(args.steps):
+        _, n, el = oracle_events_per_s(wl, W, batch, 0.0, max_events=1)
+        n_total += n
+        t_total += el
+        per.append(el)
+    v = n_total / t_total
+    out = {"metric": METRIC, "value": v, "unit": "events/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": f"{wl.name}: {wl.n_events} events, hidden {wl.model.hidden}, "
+                                  f"{wl.model.n_iters} steps; each step is one event of it",
+                      "global_batch": wl.n_events},
+           "cpu_baseline": {"value": v, "unit": "events/s", "cores": cpu_threads(),
+                            "kind": "oracle", "sample": f"{args.steps} events of {wl.name}, one per step"},
+           "e2e": {"value": v, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2407_12119_gb300 import build as build_mod
+    from paper_2407_12119_gb300.pipeline import TrackFinder
+    from velo_synth import WORKLOADS, pack_blob
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build_mod.build()
+    barrier(world)
+
+    wl = WORKLOADS[args.workload]
+    m = wl.model
+    batch = wl.batch()
+    W = wl.weights()
+    N, B = batch.n_hits, batch.n_events
+    tf = TrackFinder(m, pack_blob(m, W), B, N, N * m.k_max, device=local, dtype=args.dtype)
+    dev = tf.dev
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    hx, hy, hz, hp, ho = (pin(batch.x), pin(batch.y), pin(batch.z), pin(batch.plane),
+                          pin(batch.hit_offsets))
+    dx, dy, dz, dp, do = (t.to(dev) for t in (hx, hy, hz, hp, ho))
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return tf.run_device(dx, dy, dz, dp, do, N, B)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    tf.ctx.sync()
+    E = int(tf.eoff[B].item())
+
+    # ---- timed region: device-resident inputs ------------------------------
+    tf.ctx.profile(True)
+    n_launch0 = tf.ctx.launch_count
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_query_id(local)) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    launches = tf.ctx.launch_count - n_launch0
+    prof = tf.ctx.profile_read()
+    tf.ctx.profile(False)
+    tf.ctx.sync()
+    ms_total = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
+    ms_step = ms_total / args.steps
+    value = world * B * args.steps / (ms_total / 1e3)
+
+    # ---- end to end through the public API from pinned host buffers -------
+    lab_h = torch.empty(N, dtype=torch.int32, pin_memory=True)
+    nt_h = torch.empty(B, dtype=torch.int32, pin_memory=True)
+    for _ in range(2):
+        tf.find_tracks(hx, hy, hz, hp, ho, lab_h, nt_h)
+    torch.cuda.synchronize()
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        tf.find_tracks(hx, hy, hz, hp, ho, lab_h, nt_h)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    tf.ctx.sync()
+    h2d = N * (3 * 4 + 1) + (B + 1) * 4
+    d2h = N * 4 + B * 4
+
+    if rank != 0:
+        return
+    # ---- roofline of the dominant kernel -----------------------------------
+    peaks, peak_kind = measured_peaks()
+    top = max(prof.items(), key=lambda kv: kv[1][0])
+    name, (tot_ms, cnt) = top
+    avg_s = tot_ms / cnt / 1e3
+    kind, amount = kernel_work(name, m.hidden, E, N, m.emb_dim, m.emb_widths)
+    if kind == "flop":
+        achieved = amount / avg_s / 1e12
+        if args.dtype == "f32":
+            roof = {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+        else:
+            pk = peaks.get("bf16_tflops_sustained", 1700.0)
+            if args.dtype == "fp8":
+                pk *= 2.0
+            roof = {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+                    "peak_source": f"{peak_kind} bf16 sustained" + (" x2 (fp8 nominal ratio)" if args.dtype == "fp8" else "")}
+    else:
+        achieved = amount / avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs", 6800.0),
+                "unit": "GB/s", "peak_source": f"{peak_kind} hbm copy"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = name
+    roof["launch_ms"] = tot_ms / cnt
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        v, n, el = oracle_events_per_s(wl, W, batch, args.cpu_seconds)
+        cpu = {"value": v, "unit": "events/s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"{n} events of {wl.name} through the FP64 oracle in {el:.1f} s"}
+
+    kernels = {k: {"ms_per_step": t / args.steps, "launches_per_step": c / args.steps}
+               for k, (t, c) in sorted(prof.items(), key=lambda kv: -kv[1][0])}
+    out = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
+           "data": "synthetic",
+           "config": {"workload": f"{wl.name}: {B} events, {N} hits, {E} edges, embedding "
+                                  f"{'-'.join(map(str, m.emb_widths))}, k {m.k_max}, r {m.radius}, "
+                                  f"hidden {m.hidden}, {m.n_iters} steps",
+                      "global_batch": B * world, "hits": N, "edges": E,
+                      "edges_per_s": world * E * args.steps / (ms_total / 1e3),
+                      "l2": "working set (edge features %.1f GB) larger than L2" % (E * m.hidden * 4 / 1e9),
+                      "parallelism": f"replicas x{world}"},
+           "roofline": roof,
+           "cpu_baseline": cpu,
+           "e2e": {"value": world * B * args.steps / (e2e_ms / 1e3), "unit": "events/s",
+                   "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+           "gpu_launches": int(launches),
+           "clocks": clk.summary(),
+           "kernels": kernels}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+    rank, world, _ = dist_env()
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

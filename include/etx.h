@@ -1,0 +1,203 @@
+/*
+ * etx.h -- C ABI of the GB300 (sm_103a) ETX4VELO track-finding hot path.
+ *
+ * One batch = B events of uneven size, concatenated.  Hits are given as
+ * structure-of-arrays float32 x, y, z plus an int8 plane index, and
+ * hit_offsets[B+1] (event b owns hits [hit_offsets[b], hit_offsets[b+1])).
+ * Inside an event, hits must be sorted by plane (non-decreasing).
+ *
+ * Pipeline (paper Sec. 5 and Sec. 7, triplet stage excluded as in the
+ * paper's own C++/CUDA port):
+ *   etx_embed            hit embedding MLP                     (Sec. 5.1)
+ *   etx_build_graph      radius-capped k-NN graph p -> p+1, p+2 (Eq. 1, Sec. 5.1, Sec. 7.2)
+ *   etx_gnn_forward      interaction network edge logits       (Sec. 5.2, Eq. 4)
+ *   etx_gnn_backward     gradient of the network parameters    (Sec. 5.2, Eq. 5)
+ *   etx_edges_to_tracks  threshold + connected components      (Sec. 5, Sec. 7.3)
+ *
+ * Conventions shared by every entry point
+ *  - All array arguments are DEVICE pointers owned by the caller unless a
+ *    comment says "host".  The library never frees caller memory.
+ *  - Every call is asynchronous on the given stream (NULL = legacy default
+ *    stream) and performs no host synchronisation, except etx_ctx_sync.
+ *  - Host-detectable argument errors return a non-zero etx_status before
+ *    anything is launched; the message is in etx_last_error().
+ *  - Data-dependent errors found on the device (unsorted planes, edges out of
+ *    order, capacity overflow, an iteration cap hit) are recorded in a device
+ *    error word owned by the context; the kernels that detect them skip the
+ *    offending work (never trap), and etx_ctx_sync() returns the status.
+ *  - Indices (src, dst) are batch-global int32 hit indices.  Track labels
+ *    are event-local.
+ *  - A context is bound to one device and is not thread-safe; calls that
+ *    share a context must be issued on one stream (they share scratch).
+ */
+#ifndef ETX_H
+#define ETX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum etx_status {
+  ETX_OK = 0,
+  ETX_ERR_ARG = 1,          /* bad pointer, size, shape or configuration          */
+  ETX_ERR_UNSORTED = 2,     /* hits not plane-sorted, plane out of range, or edges
+                               not sorted by source / out of range                */
+  ETX_ERR_CAPACITY = 3,     /* an output or context buffer is too small           */
+  ETX_ERR_CUDA = 4,         /* a CUDA runtime call failed                          */
+  ETX_ERR_TIMEOUT = 5,      /* a bounded device loop reached its iteration cap     */
+  ETX_ERR_UNSUPPORTED = 6,  /* shape or dtype not supported by this build          */
+  ETX_ERR_STATE = 7         /* weights not loaded, or saved activations missing    */
+} etx_status;
+
+/* Arithmetic type of the interaction-network GEMMs.  Accumulation, LayerNorm,
+ * residual streams, message sums and logits are FP32 in every mode. */
+typedef enum etx_dtype { ETX_F32 = 0, ETX_BF16 = 1, ETX_FP8E4M3 = 2 } etx_dtype;
+
+#define ETX_MAX_EMB_LAYERS 8
+
+/* Model shapes and context capacities. */
+typedef struct etx_config {
+  int32_t emb_depth;                           /* Linear layers of the embedding MLP      */
+  int32_t emb_widths[ETX_MAX_EMB_LAYERS + 1];  /* widths[0] = 3 ... widths[depth] = D     */
+  int32_t hidden;                              /* n_h = n_e = H: 16, 32, 64 or 128         */
+  int32_t n_iters;                             /* message-passing steps L >= 0             */
+  int32_t n_planes;                            /* detector planes (26)                    */
+  int32_t max_events;                          /* capacity: events per call               */
+  int64_t max_hits;                            /* capacity: hits per call (< 2^31)        */
+  int64_t max_edges;                           /* capacity: edges per call (< 2^31)       */
+  int32_t train;                               /* nonzero: keep per-step activations for
+                                                  etx_gnn_backward                        */
+} etx_config;
+
+typedef struct etx_ctx etx_ctx;
+
+/* Create a context on `device`: validates `cfg`, allocates every scratch
+ * buffer for the given capacities (cudaMalloc; nothing is allocated later),
+ * and records the SM count for persistent-grid sizing.  On failure *out is
+ * NULL and the status says why. */
+etx_status etx_ctx_create(const etx_config* cfg, int32_t device, etx_ctx** out);
+
+/* Free the context and its device memory.  NULL is accepted. */
+etx_status etx_ctx_destroy(etx_ctx* ctx);
+
+/* Last error message of this context (static string when ctx is NULL). */
+const char* etx_last_error(const etx_ctx* ctx);
+
+/* Number of float32 values of the weight blob for `cfg` (or -1 if invalid).
+ * Blob order: normalisation (emb mu[3], sigma[3], gnn mu[3], sigma[3]),
+ * embedding layers (W[out][in], b[out]) ..., then the interaction network:
+ * node encoder, edge encoder, L x (node net, edge net), each block as
+ * W1[H][K] b1 g1 be1 W2[H][H] b2 g2 be2, and the classifier W1[H][H] b1 g1
+ * be1 W2[1][H] b2[1]. */
+int64_t etx_weights_size(const etx_config* cfg);
+
+/* Copy a HOST weight blob of `n_floats` values into the context (device
+ * repacking for every arithmetic type).  Synchronous. */
+etx_status etx_load_weights(etx_ctx* ctx, const float* host_blob, int64_t n_floats);
+
+/* Wait for `stream`, then return and clear the context's device error word
+ * (ETX_OK if no kernel recorded an error). */
+etx_status etx_ctx_sync(etx_ctx* ctx, void* stream);
+
+/*
+ * Hit embedding (Sec. 5.1): e_h = MLP((r, phi, z) normalised), r = sqrt(x^2 +
+ * y^2), phi = atan2(y, x); hidden layers Linear -> ReLU, bare last Linear.
+ *   x, y, z   float32 [n_hits]
+ *   emb       float32 [n_hits][D] row-major, written
+ * FP32 throughout.
+ */
+etx_status etx_embed(etx_ctx* ctx, const float* x, const float* y, const float* z,
+                     int64_t n_hits, float* emb, void* stream);
+
+/*
+ * Rough graph (Eq. 1, Sec. 5.1, Sec. 7.2): for each hit i on plane p, the
+ * hits j of the same event on planes p+1 and p+2 with
+ *     d2(i, j) = sum_d (e_i,d - e_j,d)^2 < radius^2
+ * (evaluated in FP32, one rounding per operation, dimensions in index order,
+ * r^2 = radius * radius rounded to FP32); if more than k_max qualify, the
+ * k_max smallest by (d2, j) are kept.  Edges i -> j are written sorted by
+ * (i, j), so events are contiguous.
+ *   emb          float32 [n_hits][D]
+ *   plane        int8 [n_hits], 0 <= plane < n_planes, sorted within each event
+ *   hit_offsets  int32 [n_events + 1] (device)
+ *   src, dst     int32 [edge_capacity], written ([0, n_edges) valid)
+ *   edge_offsets int32 [n_events + 1], written: edges of event b are
+ *                [edge_offsets[b], edge_offsets[b+1]); n_edges = edge_offsets[n_events]
+ * If the edges do not fit, ETX_ERR_CAPACITY is recorded on the device, src/dst
+ * are left unwritten and edge_offsets still holds the required counts.
+ * edge_capacity >= n_hits * k_max can never overflow.
+ */
+etx_status etx_build_graph(etx_ctx* ctx, const float* emb, const int8_t* plane,
+                           const int32_t* hit_offsets, int32_t n_events, int64_t n_hits,
+                           float radius, int32_t k_max, int32_t* src, int32_t* dst,
+                           int64_t edge_capacity, int32_t* edge_offsets, void* stream);
+
+/*
+ * Interaction network (Sec. 5.2, Eq. 4): node encoder on (x, y, z)
+ * normalised, edge encoder on [h_i, h_j], then L steps of
+ *     m_l = [sum_{l->j} e_lj, sum_{i->l} e_il]
+ *     h  <- h + node_net_k([h, m])          (distinct weights per step)
+ *     e  <- e + edge_net_k([e, h_i, h_j])   (with the updated h)
+ * and the edge classifier; writes one FP32 logit per edge.
+ *   src, dst     int32 [>= n_edges]: src non-decreasing (as etx_build_graph writes)
+ *   edge_offsets int32 [n_events + 1]: only edge_offsets[n_events] (= n_edges)
+ *                is read, on the device, so the call needs no host sync
+ *   logits       float32 [>= n_edges], written
+ * With cfg.train set, the per-step encodings are kept in the context for
+ * etx_gnn_backward.
+ */
+etx_status etx_gnn_forward(etx_ctx* ctx, const float* x, const float* y, const float* z,
+                           int64_t n_hits, const int32_t* src, const int32_t* dst,
+                           const int32_t* edge_offsets, int32_t n_events, etx_dtype dtype,
+                           float* logits, void* stream);
+
+/*
+ * Reverse pass of the last etx_gnn_forward of this context (train contexts
+ * only): given dlogits = dLoss/dlogit [n_edges], writes dparams, float32 in
+ * the blob's interaction-network order, starting at the node encoder (the
+ * normalisation and embedding entries are not part of it); its length is
+ * etx_gnn_param_count(cfg).  Message-passing steps are recomputed from the
+ * kept per-step encodings (checkpointing).
+ */
+int64_t etx_gnn_param_count(const etx_config* cfg);
+etx_status etx_gnn_backward(etx_ctx* ctx, const float* dlogits, float* dparams, void* stream);
+
+/*
+ * Purified hit graph and tracks (Sec. 5, Sec. 7.3): keep edge e iff
+ * logits[e] > threshold_logit (score > sigmoid(threshold_logit); 0.0f is the
+ * paper's 0.5), then weakly connected components by lock-free union-find.
+ *   labels      int32 [n_hits], written: smallest event-local hit index of the
+ *               hit's component (a hit with no kept edge labels itself)
+ *   n_tracks    int32 [n_events] or NULL: number of components per event with
+ *               at least `min_hits` hits
+ */
+etx_status etx_edges_to_tracks(etx_ctx* ctx, const int32_t* src, const int32_t* dst,
+                               const float* logits, float threshold_logit,
+                               const int32_t* edge_offsets, const int32_t* hit_offsets,
+                               int32_t n_events, int64_t n_hits, int32_t min_hits,
+                               int32_t* labels, int32_t* n_tracks, void* stream);
+
+/*
+ * Instrumentation (no counterpart in the paper; used by the benchmark).
+ *   etx_launch_count    number of kernels this context has launched so far.
+ *   etx_profile_enable  when on, every kernel launch is bracketed by a CUDA
+ *                       event pair recorded on its own stream.
+ *   etx_profile_read    synchronises on the recorded events and aggregates
+ *                       them by kernel name: names[i] (static strings owned
+ *                       by the library), total_ms[i], counts[i]; returns the
+ *                       number of entries written (<= max_entries) or -1,
+ *                       and clears the record.
+ */
+int64_t etx_launch_count(const etx_ctx* ctx);
+etx_status etx_profile_enable(etx_ctx* ctx, int32_t on);
+int32_t etx_profile_read(etx_ctx* ctx, const char** names, double* total_ms, int64_t* counts,
+                         int32_t max_entries);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ETX_H */

@@ -1,0 +1,133 @@
+// Purified hit graph -> track labels (paper Sec. 5 overview and Sec. 7.3).
+//
+// Weakly connected components by a lock-free union-find over the kept edges:
+// every hit starts as its own root; an edge hooks the larger of its two roots
+// under the smaller with atomicCAS (retrying if another thread hooked it
+// first), and finds use path halving.  Because a parent always has a smaller
+// index than its child, the root of a component is its smallest hit index,
+// so the label is exact and independent of scheduling; it is written
+// event-local.  Every loop carries an iteration cap: hitting it records
+// ETX_ERR_TIMEOUT in the context's error word instead of spinning.
+//
+// The paper's own kernel instead sweeps the planes forward and backward
+// taking minimum neighbour labels; that is not an exact connected-components
+// algorithm in general, so it is not used here.
+#include "etx_internal.cuh"
+
+namespace etx {
+namespace {
+
+constexpr int kFindCap = 1 << 22;
+constexpr int kUnionCap = 1 << 20;
+
+__device__ __forceinline__ int find_root(int* parent, int x, int* err) {
+  volatile int* par = parent;
+  for (int it = 0; it < kFindCap; ++it) {
+    const int p = par[x];
+    if (p == x) return x;
+    const int gp = par[p];
+    if (gp != p) par[x] = gp;  // halving: gp is an ancestor of x
+    x = gp;
+  }
+  set_err(err, DERR_TIMEOUT);
+  return x;
+}
+
+__global__ void k_init(int32_t* __restrict__ parent, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    parent[i] = (int)i;
+}
+
+__global__ void k_union(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                        const float* __restrict__ logits, float thr,
+                        const int32_t* __restrict__ n_edges_dev, int n_hits,
+                        int32_t* parent, int* err) {
+  const int E = *n_edges_dev;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    if (!(logits[e] > thr)) continue;
+    int a = src[e], b = dst[e];
+    if (a < 0 || a >= n_hits || b < 0 || b >= n_hits) {
+      set_err(err, DERR_RANGE);
+      continue;
+    }
+    int it = 0;
+    for (; it < kUnionCap; ++it) {
+      a = find_root(parent, a, err);
+      b = find_root(parent, b, err);
+      if (a == b) break;
+      if (a < b) { const int t = a; a = b; b = t; }  // hook larger root a under b
+      const int old = atomicCAS(parent + a, a, b);
+      if (old == a) break;
+      a = old;  // a was hooked meanwhile: continue from its new parent
+    }
+    if (it == kUnionCap) set_err(err, DERR_TIMEOUT);
+  }
+}
+
+__global__ void k_labels(int32_t* parent, const int32_t* __restrict__ hoff, int32_t n_events,
+                         int64_t n_hits, int32_t* __restrict__ labels, int* err) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_hits;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int r = find_root(parent, (int)i, err);
+    int lo = 0, hi = n_events;  // event b with hoff[b] <= i < hoff[b+1]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (hoff[mid] <= i) lo = mid; else hi = mid;
+    }
+    labels[i] = r - hoff[lo];
+  }
+}
+
+__global__ void k_count_tracks(const int32_t* __restrict__ labels, const int32_t* __restrict__ hoff,
+                               int32_t n_events, int64_t n_hits, int32_t min_hits,
+                               int32_t* __restrict__ size_tmp, int32_t* __restrict__ n_tracks) {
+  // size_tmp[i] = size of the component whose root is hit i (filled by atomics)
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_hits;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = n_events;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (hoff[mid] <= i) lo = mid; else hi = mid;
+    }
+    const int root = hoff[lo] + labels[i];
+    const int sz = atomicAdd(size_tmp + root, 1) + 1;
+    if (sz == min_hits) atomicAdd(n_tracks + lo, 1);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_edges_to_tracks(etx_ctx* ctx, const int32_t* src, const int32_t* dst,
+                                   const float* logits, float thr, const int32_t* n_edges_dev,
+                                   const int32_t* hit_offsets, int32_t n_events, int64_t n_hits,
+                                   int32_t min_hits, int32_t* labels, int32_t* n_tracks,
+                                   cudaStream_t s) {
+  if (n_hits == 0) {
+    if (n_tracks && n_events > 0)
+      return cudaMemsetAsync(n_tracks, 0, (size_t)n_events * sizeof(int32_t), s);
+    return cudaSuccess;
+  }
+  const int gn = grid_for(ctx, (const void*)k_init, 256, 0, (n_hits + 255) / 256);
+  launch(ctx, "cc_init", k_init, gn, 256, 0, s, ctx->parent, n_hits);
+  const int ge = grid_for(ctx, (const void*)k_union, 256, 0, (ctx->cfg.max_edges + 255) / 256);
+  launch(ctx, "cc_union", k_union, ge, 256, 0, s, src, dst, logits, thr, n_edges_dev, (int)n_hits,
+         ctx->parent, ctx->d_err);
+  const int gl = grid_for(ctx, (const void*)k_labels, 256, 0, (n_hits + 255) / 256);
+  launch(ctx, "cc_labels", k_labels, gl, 256, 0, s, ctx->parent, hit_offsets, n_events, n_hits,
+         labels, ctx->d_err);
+  if (n_tracks) {
+    cudaError_t e = cudaMemsetAsync(n_tracks, 0, (size_t)n_events * sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    // reuse the parent array as the per-root size counter
+    e = cudaMemsetAsync(ctx->parent, 0, (size_t)n_hits * sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    const int mh = min_hits < 1 ? 1 : min_hits;
+    launch(ctx, "cc_count_tracks", k_count_tracks, gl, 256, 0, s, labels, hit_offsets, n_events,
+           n_hits, mh, ctx->parent, n_tracks);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace etx

@@ -1,0 +1,443 @@
+// C ABI of libetx: context lifetime, weight repacking, argument checks and
+// the launch sequence of each pipeline step.  See include/etx.h.
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "etx_internal.cuh"
+
+namespace etx {
+cudaError_t knn_set_smem_attr();
+
+int grid_for(const etx_ctx* ctx, const void* kernel, int threads, size_t smem, int64_t max_blocks) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess)
+    per_sm = 1;
+  if (per_sm < 1) per_sm = 1;
+  int64_t g = (int64_t)per_sm * ctx->n_sms;
+  if (g > max_blocks) g = max_blocks;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+void prof_begin(etx_ctx* ctx, const char* name, cudaStream_t s) {
+  if (!ctx->prof_on) return;
+  if (ctx->prof_used == ctx->prof.size()) {
+    ProfRec r{name, nullptr, nullptr};
+    if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return;
+    ctx->prof.push_back(r);
+  }
+  ProfRec& r = ctx->prof[ctx->prof_used];
+  r.name = name;
+  cudaEventRecord(r.a, s);
+}
+
+void prof_end(etx_ctx* ctx, cudaStream_t s) {
+  if (!ctx->prof_on || ctx->prof_used == ctx->prof.size()) return;
+  cudaEventRecord(ctx->prof[ctx->prof_used].b, s);
+  ++ctx->prof_used;
+}
+
+namespace {
+
+__global__ void k_clamp_edges(const int32_t* __restrict__ edge_offsets, int32_t n_events,
+                              int64_t cap, int32_t* __restrict__ n_edges, int* err) {
+  int E = edge_offsets[n_events];
+  if (E < 0) {
+    set_err(err, DERR_RANGE);
+    E = 0;
+  }
+  if (E > cap) {
+    set_err(err, DERR_CAPACITY);
+    E = (int)cap;
+  }
+  *n_edges = E;
+}
+
+bool valid_width(int w) { return w == 16 || w == 32 || w == 64 || w == 128; }
+
+etx_status fail(etx_ctx* ctx, etx_status st, const char* msg) {
+  if (ctx) ctx->err = msg;
+  return st;
+}
+
+etx_status cuda_fail(etx_ctx* ctx, cudaError_t e, const char* where) {
+  if (ctx) {
+    ctx->err = std::string(where) + ": " + cudaGetErrorString(e);
+  }
+  return ETX_ERR_CUDA;
+}
+
+const char* config_problem(const etx_config* c) {
+  if (!c) return "config is NULL";
+  if (c->emb_depth < 2 || c->emb_depth > ETX_MAX_EMB_LAYERS)
+    return "emb_depth must be in [2, 8]";
+  if (c->emb_widths[0] != 3) return "emb_widths[0] must be 3 (r, phi, z)";
+  for (int l = 1; l < c->emb_depth; ++l)
+    if (c->emb_widths[l] != c->emb_widths[1]) return "embedding hidden widths must be equal";
+  if (!valid_width(c->emb_widths[1])) return "embedding hidden width must be 16, 32, 64 or 128";
+  const int D = c->emb_widths[c->emb_depth];
+  if (D < 1 || D > 32) return "embedding dimension D must be in [1, 32]";
+  if (!valid_width(c->hidden)) return "hidden must be 16, 32, 64 or 128";
+  if (c->n_iters < 0 || c->n_iters > 64) return "n_iters must be in [0, 64]";
+  if (c->n_planes < 2 || c->n_planes > kMaxPlanes) return "n_planes must be in [2, 64]";
+  if (c->max_events < 1) return "max_events must be >= 1";
+  if (c->max_hits < 1 || c->max_hits >= (int64_t)1 << 31) return "max_hits must be in [1, 2^31)";
+  if (c->max_edges < 1 || c->max_edges >= (int64_t)1 << 31) return "max_edges must be in [1, 2^31)";
+  return nullptr;
+}
+
+int64_t block_floats(int H, int K) { return (int64_t)H * K + 3 * H + (int64_t)H * H + 3 * H; }
+
+template <class T>
+etx_status dmalloc(etx_ctx* ctx, T** p, size_t count, const char* what) {
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+  return ETX_OK;
+}
+
+}  // namespace
+}  // namespace etx
+
+using namespace etx;
+
+extern "C" {
+
+int64_t etx_gnn_param_count(const etx_config* c) {
+  if (config_problem(c)) return -1;
+  const int64_t H = c->hidden;
+  int64_t n = block_floats(H, 3) + block_floats(H, 2 * H);
+  n += (int64_t)c->n_iters * 2 * block_floats(H, 3 * H);
+  n += H * H + 3 * H + H + 1;
+  return n;
+}
+
+int64_t etx_weights_size(const etx_config* c) {
+  if (config_problem(c)) return -1;
+  int64_t n = 12;
+  for (int l = 0; l < c->emb_depth; ++l)
+    n += (int64_t)c->emb_widths[l + 1] * c->emb_widths[l] + c->emb_widths[l + 1];
+  return n + etx_gnn_param_count(c);
+}
+
+const char* etx_last_error(const etx_ctx* ctx) {
+  if (!ctx) return "no context";
+  return ctx->err.c_str();
+}
+
+etx_status etx_ctx_create(const etx_config* cfg, int32_t device, etx_ctx** out) {
+  if (!out) return ETX_ERR_ARG;
+  *out = nullptr;
+  if (config_problem(cfg)) return ETX_ERR_ARG;
+  etx_ctx* ctx = new (std::nothrow) etx_ctx();
+  if (!ctx) return ETX_ERR_ARG;
+  ctx->cfg = *cfg;
+  ctx->device = device;
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return ETX_ERR_CUDA;
+  }
+  cudaDeviceGetAttribute(&ctx->n_sms, cudaDevAttrMultiProcessorCount, device);
+  if (ctx->n_sms < 1) ctx->n_sms = 1;
+  const int64_t N = cfg->max_hits, E = cfg->max_edges, B = cfg->max_events;
+  const int64_t H = cfg->hidden;
+  etx_status st = ETX_OK;
+  auto chk = [&](etx_status s) { if (st == ETX_OK) st = s; };
+  chk(dmalloc(ctx, &ctx->d_err, 1, "error word"));
+  chk(dmalloc(ctx, &ctx->n_edges, 1, "edge count"));
+  chk(dmalloc(ctx, &ctx->plane_off, (size_t)B * (cfg->n_planes + 1), "plane offsets"));
+  chk(dmalloc(ctx, &ctx->hit_cnt, (size_t)N + 1, "hit counts"));
+  ctx->scan_tmp_ints = scan_tmp_ints(N + 1) + 8;
+  chk(dmalloc(ctx, &ctx->scan_tmp, ctx->scan_tmp_ints, "scan scratch"));
+  chk(dmalloc(ctx, &ctx->out_off, (size_t)N + 1, "out offsets"));
+  chk(dmalloc(ctx, &ctx->in_off, (size_t)N + 1, "in offsets"));
+  chk(dmalloc(ctx, &ctx->in_cnt, (size_t)N + 1, "in counts"));
+  chk(dmalloc(ctx, &ctx->perm_in, (size_t)E, "in permutation"));
+  chk(dmalloc(ctx, &ctx->h, (size_t)N * H, "node features"));
+  chk(dmalloc(ctx, &ctx->m, (size_t)N * 2 * H, "messages"));
+  chk(dmalloc(ctx, &ctx->e, (size_t)E * H, "edge features"));
+  chk(dmalloc(ctx, &ctx->parent, (size_t)N, "union-find parents"));
+  if (st == ETX_OK) {
+    e = cudaMemset(ctx->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) st = cuda_fail(ctx, e, "cudaMemset");
+  }
+  if (st == ETX_OK) {
+    e = knn_set_smem_attr();
+    if (e != cudaSuccess) st = cuda_fail(ctx, e, "kNN shared-memory attribute");
+  }
+  if (st != ETX_OK) {
+    etx_ctx_destroy(ctx);
+    return st;
+  }
+  *out = ctx;
+  return ETX_OK;
+}
+
+etx_status etx_ctx_destroy(etx_ctx* ctx) {
+  if (!ctx) return ETX_OK;
+  cudaSetDevice(ctx->device);
+  void* bufs[] = {ctx->d_err, ctx->n_edges, ctx->w_dev, ctx->blob_dev, ctx->plane_off,
+                  ctx->hit_cnt, ctx->scan_tmp, ctx->out_off, ctx->in_off, ctx->in_cnt,
+                  ctx->perm_in, ctx->h, ctx->m, ctx->e, ctx->parent};
+  for (void* p : bufs)
+    if (p) cudaFree(p);
+  for (auto& r : ctx->prof) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  delete ctx;
+  return ETX_OK;
+}
+
+int64_t etx_launch_count(const etx_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+etx_status etx_profile_enable(etx_ctx* ctx, int32_t on) {
+  if (!ctx) return ETX_ERR_ARG;
+  ctx->prof_on = on != 0;
+  ctx->prof_used = 0;
+  return ETX_OK;
+}
+
+int32_t etx_profile_read(etx_ctx* ctx, const char** names, double* total_ms, int64_t* counts,
+                         int32_t max_entries) {
+  if (!ctx) return -1;
+  cudaSetDevice(ctx->device);
+  int32_t n = 0;
+  for (size_t i = 0; i < ctx->prof_used; ++i) {
+    const ProfRec& r = ctx->prof[i];
+    if (cudaEventSynchronize(r.b) != cudaSuccess) return -1;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) return -1;
+    int32_t k = 0;
+    while (k < n && std::strcmp(names[k], r.name) != 0) ++k;
+    if (k == n) {
+      if (n == max_entries) continue;
+      names[n] = r.name;
+      total_ms[n] = 0.0;
+      counts[n] = 0;
+      ++n;
+    }
+    total_ms[k] += ms;
+    counts[k] += 1;
+  }
+  ctx->prof_used = 0;
+  return n;
+}
+
+etx_status etx_load_weights(etx_ctx* ctx, const float* blob, int64_t n_floats) {
+  if (!ctx) return ETX_ERR_ARG;
+  if (!blob) return fail(ctx, ETX_ERR_ARG, "weight blob is NULL");
+  const etx_config& c = ctx->cfg;
+  if (n_floats != etx_weights_size(&c)) return fail(ctx, ETX_ERR_ARG, "weight blob size does not match the config");
+  cudaSetDevice(ctx->device);
+  const int H = c.hidden;
+  // --- host-side repack: every Linear to W^T [k_pad][n] ---------------------
+  std::vector<float> dev;
+  dev.reserve((size_t)n_floats * 2);
+  const float* p = blob;
+  struct Pending { size_t wt, b; int k_in, k_pad, n; };
+  // every array starts on a 16-byte boundary (float4 loads of W^T chunks)
+  auto align4 = [&]() { while (dev.size() % 4) dev.push_back(0.f); };
+  auto push_lin = [&](int n_out, int k_in) {
+    align4();
+    Pending q;
+    q.k_in = k_in;
+    q.k_pad = k_in <= 4 ? 4 : k_in;
+    q.n = n_out;
+    q.wt = dev.size();
+    dev.resize(dev.size() + (size_t)q.k_pad * n_out, 0.f);
+    for (int o = 0; o < n_out; ++o)
+      for (int k = 0; k < k_in; ++k) dev[q.wt + (size_t)k * n_out + o] = p[(size_t)o * k_in + k];
+    p += (size_t)n_out * k_in;
+    align4();
+    q.b = dev.size();
+    dev.insert(dev.end(), p, p + n_out);
+    p += n_out;
+    return q;
+  };
+  auto push_vec = [&](int n) {
+    align4();
+    size_t at = dev.size();
+    dev.insert(dev.end(), p, p + n);
+    p += n;
+    return at;
+  };
+  const size_t norm_at = push_vec(12);
+  std::vector<Pending> emb;
+  for (int l = 0; l < c.emb_depth; ++l) emb.push_back(push_lin(c.emb_widths[l + 1], c.emb_widths[l]));
+  struct PB { Pending l1, l2; size_t g1, be1, g2, be2; };
+  auto push_block = [&](int k_in) {
+    PB b;
+    b.l1 = push_lin(H, k_in);
+    b.g1 = push_vec(H);
+    b.be1 = push_vec(H);
+    b.l2 = push_lin(H, H);
+    b.g2 = push_vec(H);
+    b.be2 = push_vec(H);
+    return b;
+  };
+  PB node_enc = push_block(3), edge_enc = push_block(2 * H);
+  std::vector<PB> node, edge;
+  for (int k = 0; k < c.n_iters; ++k) {
+    node.push_back(push_block(3 * H));
+    edge.push_back(push_block(3 * H));
+  }
+  Pending cl1 = push_lin(H, H);
+  size_t cg1 = push_vec(H), cbe1 = push_vec(H), cw2 = push_vec(H), cb2 = push_vec(1);
+  if (p != blob + n_floats) return fail(ctx, ETX_ERR_ARG, "internal: blob walk mismatch");
+  if (ctx->w_dev) cudaFree(ctx->w_dev);
+  if (ctx->blob_dev) cudaFree(ctx->blob_dev);
+  ctx->w_dev = nullptr;
+  ctx->blob_dev = nullptr;
+  if (dmalloc(ctx, &ctx->w_dev, dev.size(), "weights") != ETX_OK) return ETX_ERR_CUDA;
+  if (dmalloc(ctx, &ctx->blob_dev, (size_t)n_floats, "weight blob") != ETX_OK) return ETX_ERR_CUDA;
+  cudaError_t e = cudaMemcpy(ctx->w_dev, dev.data(), dev.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(ctx->blob_dev, blob, (size_t)n_floats * sizeof(float), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "weight upload");
+  ctx->w_dev_floats = dev.size();
+  float* base = ctx->w_dev;
+  auto lin = [&](const Pending& q) {
+    LinF32 l;
+    l.wt = base + q.wt;
+    l.b = base + q.b;
+    l.k_in = q.k_in;
+    l.k_pad = q.k_pad;
+    l.n = q.n;
+    return l;
+  };
+  auto blk = [&](const PB& b) {
+    BlockF32 o;
+    o.l1 = lin(b.l1);
+    o.l2 = lin(b.l2);
+    o.g1 = base + b.g1;
+    o.be1 = base + b.be1;
+    o.g2 = base + b.g2;
+    o.be2 = base + b.be2;
+    return o;
+  };
+  ctx->w = Weights();
+  ctx->w.norm = base + norm_at;
+  for (auto& q : emb) ctx->w.emb.push_back(lin(q));
+  ctx->w.node_enc = blk(node_enc);
+  ctx->w.edge_enc = blk(edge_enc);
+  for (auto& b : node) ctx->w.node.push_back(blk(b));
+  for (auto& b : edge) ctx->w.edge.push_back(blk(b));
+  ctx->w.cls.l1 = lin(cl1);
+  ctx->w.cls.g1 = base + cg1;
+  ctx->w.cls.be1 = base + cbe1;
+  ctx->w.cls.w2 = base + cw2;
+  ctx->w.cls.b2 = base + cb2;
+  ctx->weights_loaded = true;
+  return ETX_OK;
+}
+
+etx_status etx_ctx_sync(etx_ctx* ctx, void* stream) {
+  if (!ctx) return ETX_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+  int word = 0;
+  e = cudaMemcpy(&word, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "error word read");
+  if (word) {
+    e = cudaMemset(ctx->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "error word reset");
+  }
+  if (word & DERR_TIMEOUT) return fail(ctx, ETX_ERR_TIMEOUT, "a device loop reached its iteration cap");
+  if (word & DERR_CAPACITY) return fail(ctx, ETX_ERR_CAPACITY, "an edge buffer was too small");
+  if (word & DERR_UNSORTED) return fail(ctx, ETX_ERR_UNSORTED, "hits not plane-sorted / edges not sorted by source / bad offsets");
+  if (word & DERR_RANGE) return fail(ctx, ETX_ERR_UNSORTED, "an index was out of range");
+  return ETX_OK;
+}
+
+etx_status etx_embed(etx_ctx* ctx, const float* x, const float* y, const float* z, int64_t n_hits,
+                     float* emb, void* stream) {
+  if (!ctx) return ETX_ERR_ARG;
+  if (!ctx->weights_loaded) return fail(ctx, ETX_ERR_STATE, "weights not loaded");
+  if (n_hits < 0 || n_hits >= ((int64_t)1 << 31)) return fail(ctx, ETX_ERR_ARG, "n_hits out of range");
+  if (n_hits > 0 && (!x || !y || !z || !emb)) return fail(ctx, ETX_ERR_ARG, "NULL array");
+  cudaSetDevice(ctx->device);
+  cudaError_t e = launch_embed(ctx, x, y, z, n_hits, emb, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "etx_embed launch");
+  return ETX_OK;
+}
+
+etx_status etx_build_graph(etx_ctx* ctx, const float* emb, const int8_t* plane,
+                           const int32_t* hit_offsets, int32_t n_events, int64_t n_hits,
+                           float radius, int32_t k_max, int32_t* src, int32_t* dst,
+                           int64_t edge_capacity, int32_t* edge_offsets, void* stream) {
+  if (!ctx) return ETX_ERR_ARG;
+  if (n_events < 0 || n_events > ctx->cfg.max_events) return fail(ctx, ETX_ERR_CAPACITY, "n_events exceeds the context capacity");
+  if (n_hits < 0 || n_hits > ctx->cfg.max_hits) return fail(ctx, ETX_ERR_CAPACITY, "n_hits exceeds the context capacity");
+  if (!(radius >= 0.f) || radius > 1e18f) return fail(ctx, ETX_ERR_ARG, "radius must be finite and >= 0");
+  if (k_max < 1) return fail(ctx, ETX_ERR_ARG, "k_max must be >= 1");
+  if (edge_capacity < 0 || edge_capacity >= ((int64_t)1 << 31)) return fail(ctx, ETX_ERR_ARG, "edge_capacity out of range");
+  if (!hit_offsets || !edge_offsets) return fail(ctx, ETX_ERR_ARG, "NULL offsets");
+  if (n_hits > 0 && (!emb || !plane)) return fail(ctx, ETX_ERR_ARG, "NULL array");
+  if (edge_capacity > 0 && (!src || !dst)) return fail(ctx, ETX_ERR_ARG, "NULL edge arrays");
+  if (n_hits * (int64_t)k_max >= ((int64_t)1 << 31)) return fail(ctx, ETX_ERR_ARG, "n_hits * k_max must stay below 2^31");
+  cudaSetDevice(ctx->device);
+  cudaError_t e = launch_build_graph(ctx, emb, plane, hit_offsets, n_events, n_hits, radius, k_max,
+                                     src, dst, edge_capacity, edge_offsets, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "etx_build_graph launch");
+  return ETX_OK;
+}
+
+etx_status etx_gnn_forward(etx_ctx* ctx, const float* x, const float* y, const float* z,
+                           int64_t n_hits, const int32_t* src, const int32_t* dst,
+                           const int32_t* edge_offsets, int32_t n_events, etx_dtype dtype,
+                           float* logits, void* stream) {
+  if (!ctx) return ETX_ERR_ARG;
+  if (!ctx->weights_loaded) return fail(ctx, ETX_ERR_STATE, "weights not loaded");
+  if (n_events < 0 || n_events > ctx->cfg.max_events) return fail(ctx, ETX_ERR_CAPACITY, "n_events exceeds the context capacity");
+  if (n_hits < 0 || n_hits > ctx->cfg.max_hits) return fail(ctx, ETX_ERR_CAPACITY, "n_hits exceeds the context capacity");
+  if (!edge_offsets || !src || !dst || !logits) return fail(ctx, ETX_ERR_ARG, "NULL edge array");
+  if (n_hits > 0 && (!x || !y || !z)) return fail(ctx, ETX_ERR_ARG, "NULL hit array");
+  if (dtype != ETX_F32) return fail(ctx, ETX_ERR_UNSUPPORTED, "dtype not built yet");
+  if (n_hits == 0) return ETX_OK;  // no hits, hence no edges: nothing to compute
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  launch(ctx, "clamp_edges", k_clamp_edges, 1, 1, 0, s, edge_offsets, n_events, ctx->cfg.max_edges,
+         ctx->n_edges, ctx->d_err);
+  cudaError_t e = launch_edge_index(ctx, n_hits, src, dst, ctx->n_edges, s);
+  if (e == cudaSuccess)
+    e = launch_gnn_forward_f32(ctx, x, y, z, n_hits, src, dst, ctx->n_edges, logits, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "etx_gnn_forward launch");
+  return ETX_OK;
+}
+
+etx_status etx_gnn_backward(etx_ctx* ctx, const float* dlogits, float* dparams, void* stream) {
+  (void)dlogits;
+  (void)dparams;
+  (void)stream;
+  if (!ctx) return ETX_ERR_ARG;
+  return fail(ctx, ETX_ERR_UNSUPPORTED, "backward not built yet");
+}
+
+etx_status etx_edges_to_tracks(etx_ctx* ctx, const int32_t* src, const int32_t* dst,
+                               const float* logits, float threshold_logit,
+                               const int32_t* edge_offsets, const int32_t* hit_offsets,
+                               int32_t n_events, int64_t n_hits, int32_t min_hits,
+                               int32_t* labels, int32_t* n_tracks, void* stream) {
+  if (!ctx) return ETX_ERR_ARG;
+  if (n_events < 0 || n_events > ctx->cfg.max_events) return fail(ctx, ETX_ERR_CAPACITY, "n_events exceeds the context capacity");
+  if (n_hits < 0 || n_hits > ctx->cfg.max_hits) return fail(ctx, ETX_ERR_CAPACITY, "n_hits exceeds the context capacity");
+  if (!edge_offsets || !hit_offsets || !src || !dst || !logits) return fail(ctx, ETX_ERR_ARG, "NULL array");
+  if (n_hits > 0 && !labels) return fail(ctx, ETX_ERR_ARG, "NULL labels");
+  if (threshold_logit != threshold_logit) return fail(ctx, ETX_ERR_ARG, "threshold is NaN");
+  if (n_events == 0 && n_hits > 0) return fail(ctx, ETX_ERR_ARG, "hits without events");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  launch(ctx, "clamp_edges", k_clamp_edges, 1, 1, 0, s, edge_offsets, n_events, (int64_t)INT32_MAX,
+         ctx->n_edges, ctx->d_err);
+  cudaError_t e = launch_edges_to_tracks(ctx, src, dst, logits, threshold_logit, ctx->n_edges,
+                                         hit_offsets, n_events, n_hits, min_hits, labels, n_tracks, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "etx_edges_to_tracks launch");
+  return ETX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,161 @@
+// Internal declarations shared by the CUDA translation units of libetx.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/etx.h"
+
+namespace etx {
+
+// Device error word bits (the context's d_err).
+enum : int {
+  DERR_UNSORTED = 1,
+  DERR_CAPACITY = 2,
+  DERR_TIMEOUT = 4,
+  DERR_RANGE = 8,
+};
+
+__device__ __forceinline__ void set_err(int* err, int bit) { atomicOr(err, bit); }
+
+constexpr int kMaxPlanes = 64;
+constexpr float kLnEps = 1e-5f;
+
+// One Linear layer of the FP32 path: W^T stored [k_pad][n] row-major (k-major),
+// zero rows for k >= k_in; bias[n].
+struct LinF32 {
+  const float* wt = nullptr;
+  const float* b = nullptr;
+  int k_in = 0, k_pad = 0, n = 0;
+};
+
+// Lin -> LN -> ReLU -> Lin -> LN -> ReLU block.
+struct BlockF32 {
+  LinF32 l1, l2;
+  const float *g1 = nullptr, *be1 = nullptr, *g2 = nullptr, *be2 = nullptr;
+};
+
+struct ClassifierF32 {
+  LinF32 l1;
+  const float *g1 = nullptr, *be1 = nullptr;
+  const float* w2 = nullptr;  // [H]
+  const float* b2 = nullptr;  // [1]
+};
+
+// BF16 copy of one Linear, PyTorch layout W[n][k] (k contiguous), for the
+// tensor-core path.
+struct LinBF16 {
+  const uint16_t* w = nullptr;
+  int k = 0, n = 0;
+};
+
+struct Weights {
+  const float* norm = nullptr;  // emb mu[3], sigma[3], gnn mu[3], sigma[3] (device)
+  std::vector<LinF32> emb;
+  BlockF32 node_enc, edge_enc;
+  std::vector<BlockF32> node, edge;
+  ClassifierF32 cls;
+};
+
+}  // namespace etx
+
+namespace etx {
+struct ProfRec {
+  const char* name;
+  cudaEvent_t a, b;
+};
+}  // namespace etx
+
+struct etx_ctx {
+  etx_config cfg{};
+  int device = 0;
+  int n_sms = 0;
+  std::string err;
+  bool weights_loaded = false;
+
+  int* d_err = nullptr;
+  int32_t* n_edges = nullptr;    // device: edge count of the current call, clamped
+
+  // weights
+  float* w_dev = nullptr;   // repacked FP32 weights
+  size_t w_dev_floats = 0;
+  float* blob_dev = nullptr;  // raw blob copy (float32) for the backward pass
+  etx::Weights w;
+
+  // graph scratch
+  int32_t* plane_off = nullptr;  // [max_events * (n_planes + 1)]
+  int32_t* hit_cnt = nullptr;    // [max_hits + 1]
+  int32_t* scan_tmp = nullptr;   // block partials
+  size_t scan_tmp_ints = 0;
+
+  // interaction-network scratch
+  int32_t* out_off = nullptr;    // [max_hits + 1]
+  int32_t* in_off = nullptr;     // [max_hits + 1]
+  int32_t* in_cnt = nullptr;     // [max_hits + 1]
+  int32_t* perm_in = nullptr;    // [max_edges]
+  float* h = nullptr;            // [max_hits * H]
+  float* m = nullptr;            // [max_hits * 2H]
+  float* e = nullptr;            // [max_edges * H]
+
+  // components
+  int32_t* parent = nullptr;     // [max_hits]
+
+  // launch accounting and optional per-launch CUDA-event timing
+  int64_t launches = 0;
+  bool prof_on = false;
+  std::vector<etx::ProfRec> prof;
+  size_t prof_used = 0;
+};
+
+namespace etx {
+
+// ---- launch helpers implemented in the .cu files --------------------------
+// scan.cu: exclusive scan of n int32 (n host-known); out[n] receives the total.
+cudaError_t exclusive_scan(etx_ctx* ctx, const int32_t* in, int32_t* out, int64_t n,
+                           cudaStream_t s);
+size_t scan_tmp_ints(int64_t n);
+
+// embed.cu
+cudaError_t launch_embed(etx_ctx* ctx, const float* x, const float* y, const float* z,
+                         int64_t n, float* emb, cudaStream_t s);
+
+// graph.cu
+cudaError_t launch_build_graph(etx_ctx* ctx, const float* emb, const int8_t* plane,
+                               const int32_t* hit_offsets, int32_t n_events, int64_t n_hits,
+                               float radius, int32_t k_max, int32_t* src, int32_t* dst,
+                               int64_t edge_capacity, int32_t* edge_offsets, cudaStream_t s);
+
+// gnn_f32.cu
+cudaError_t launch_gnn_forward_f32(etx_ctx* ctx, const float* x, const float* y, const float* z,
+                                   int64_t n_hits, const int32_t* src, const int32_t* dst,
+                                   const int32_t* n_edges_dev, float* logits, cudaStream_t s);
+cudaError_t launch_edge_index(etx_ctx* ctx, int64_t n_hits, const int32_t* src,
+                              const int32_t* dst, const int32_t* n_edges_dev, cudaStream_t s);
+
+// cc.cu
+cudaError_t launch_edges_to_tracks(etx_ctx* ctx, const int32_t* src, const int32_t* dst,
+                                   const float* logits, float thr, const int32_t* n_edges_dev,
+                                   const int32_t* hit_offsets, int32_t n_events, int64_t n_hits,
+                                   int32_t min_hits, int32_t* labels, int32_t* n_tracks,
+                                   cudaStream_t s);
+
+int grid_for(const etx_ctx* ctx, const void* kernel, int threads, size_t smem, int64_t max_blocks);
+
+void prof_begin(etx_ctx* ctx, const char* name, cudaStream_t s);
+void prof_end(etx_ctx* ctx, cudaStream_t s);
+
+// Launch one of this library's kernels: counted, and timed with a CUDA event
+// pair on the launching stream when profiling is on.
+template <typename... KArgs, typename... Args>
+inline void launch(etx_ctx* ctx, const char* name, void (*kernel)(KArgs...), dim3 grid,
+                   dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+  prof_begin(ctx, name, s);
+  kernel<<<grid, block, smem, s>>>(static_cast<KArgs>(args)...);
+  prof_end(ctx, s);
+  ++ctx->launches;
+}
+
+}  // namespace etx

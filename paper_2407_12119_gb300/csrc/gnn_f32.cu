@@ -1,0 +1,338 @@
+// Interaction network forward (paper Sec. 5.2, Eq. 4), FP32 SIMT path.
+//
+// Edge index structures (the src-CSR comes from the sorted edge list, the
+// dst-CSC from a counting sort whose segments are then sorted by edge id so
+// every sum has a fixed order), then one fused kernel per MLP block: gather
+// the block's input rows into shared memory chunk by chunk ([h_i, h_j],
+// [h, m_out, m_in] or [e, h_i, h_j]), Lin -> LN -> ReLU -> Lin -> LN -> ReLU in
+// registers, residual add and store.  Messages are segment sums over the CSR
+// and CSC ranges, one warp (or a lane group) per hit, no atomics.
+// All edge-row kernels read the edge count from device memory and walk their
+// tiles with a persistent grid-stride loop, so no host synchronisation is
+// needed between the graph build and the network.
+#include "simt_tile.cuh"
+
+namespace etx {
+namespace {
+
+constexpr int kKC = 16;
+constexpr int kLdaChunk = kKC + 4;
+
+enum Mode { NODE_ENC = 0, EDGE_ENC = 1, NODE_UPD = 2, EDGE_UPD = 3, CLS = 4 };
+
+struct MlpArgs {
+  int64_t n_rows;               // hits (rows of the node modes)
+  const int32_t* n_rows_dev;    // edge modes
+  const float *x, *y, *z;
+  const float* norm;            // gnn mu[3], sigma[3]
+  const int32_t *src, *dst;
+  const float* h;               // [N][H]
+  const float* m;               // [N][2H]
+  float* e;                     // [E][H]
+  float* h_out;                 // [N][H]
+  float* logits;                // [E]
+  BlockF32 blk;
+  ClassifierF32 cls;
+};
+
+// ---------------------------------------------------------------------------
+// index structures
+// ---------------------------------------------------------------------------
+__global__ void k_out_offsets(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                              const int32_t* __restrict__ n_edges_dev, int n_hits,
+                              int32_t* __restrict__ out_off, int* err) {
+  const int E = *n_edges_dev;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e <= E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int lo = e == 0 ? 0 : src[e - 1] + 1;
+    int hi = e == E ? n_hits : src[e];
+    if (e < E) {
+      const int s = src[e], d = dst[e];
+      if (s < 0 || s >= n_hits || d < 0 || d >= n_hits) {
+        set_err(err, DERR_RANGE);
+        continue;
+      }
+      if (e > 0 && s < src[e - 1]) {
+        set_err(err, DERR_UNSORTED);
+        continue;
+      }
+    }
+    lo = max(lo, 0);
+    hi = min(hi, n_hits);
+    for (int i = lo; i <= hi; ++i) out_off[i] = (int)e;
+  }
+}
+
+__global__ void k_in_count(const int32_t* __restrict__ dst, const int32_t* __restrict__ n_edges_dev,
+                           int n_hits, int32_t* __restrict__ cnt) {
+  const int E = *n_edges_dev;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int d = dst[e];
+    if (d >= 0 && d < n_hits) atomicAdd(cnt + d, 1);
+  }
+}
+
+__global__ void k_in_fill(const int32_t* __restrict__ dst, const int32_t* __restrict__ n_edges_dev,
+                          int n_hits, const int32_t* __restrict__ in_off, int32_t* __restrict__ cursor,
+                          int32_t* __restrict__ perm) {
+  const int E = *n_edges_dev;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int d = dst[e];
+    if (d >= 0 && d < n_hits) perm[in_off[d] + atomicAdd(cursor + d, 1)] = (int)e;
+  }
+}
+
+// Sort each dst segment by edge id (insertion sort; segments are short).
+__global__ void k_in_sort(const int32_t* __restrict__ in_off, int n_hits, int32_t* __restrict__ perm) {
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < n_hits;
+       l += (int64_t)gridDim.x * blockDim.x) {
+    const int a = in_off[l], b = in_off[l + 1];
+    for (int i = a + 1; i < b; ++i) {
+      const int v = perm[i];
+      int j = i - 1;
+      while (j >= a && perm[j] > v) {
+        perm[j + 1] = perm[j];
+        --j;
+      }
+      perm[j + 1] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// messages (Eq. 4): m_l = [sum_{l->j} e_lj, sum_{i->l} e_il]
+// ---------------------------------------------------------------------------
+template <int H>
+__global__ void k_messages(const float* __restrict__ e, const int32_t* __restrict__ out_off,
+                           const int32_t* __restrict__ in_off, const int32_t* __restrict__ perm,
+                           const int32_t* __restrict__ n_edges_dev, int n_hits,
+                           float* __restrict__ m) {
+  constexpr int G = H / 4;          // lanes per hit
+  constexpr int PER_WARP = 32 / G;  // hits per warp
+  const int E = *n_edges_dev;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane / G, c = (lane % G) * 4;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t l0 = warp0 * PER_WARP; l0 < n_hits; l0 += nwarps * PER_WARP) {
+    const int64_t l = l0 + sub;
+    if (l >= n_hits) continue;
+    const int o0 = min(max(out_off[l], 0), E), o1 = min(max(out_off[l + 1], 0), E);
+    const int i0 = min(max(in_off[l], 0), E), i1 = min(max(in_off[l + 1], 0), E);
+    float4 so = make_float4(0.f, 0.f, 0.f, 0.f), si = so;
+    for (int q = o0; q < o1; ++q) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(e + (int64_t)q * H + c));
+      so.x += v.x; so.y += v.y; so.z += v.z; so.w += v.w;
+    }
+    for (int q = i0; q < i1; ++q) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(e + (int64_t)perm[q] * H + c));
+      si.x += v.x; si.y += v.y; si.z += v.z; si.w += v.w;
+    }
+    *reinterpret_cast<float4*>(m + l * 2 * H + c) = so;
+    *reinterpret_cast<float4*>(m + l * 2 * H + H + c) = si;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// fused MLP blocks
+// ---------------------------------------------------------------------------
+template <int H, int MODE>
+__device__ __forceinline__ float4 gather4(const MlpArgs& a, int64_t row, bool valid, int k,
+                                          int srow, int drow) {
+  if (!valid) return make_float4(0.f, 0.f, 0.f, 0.f);
+  const float* p;
+  if constexpr (MODE == EDGE_ENC) {
+    p = k < H ? a.h + (int64_t)srow * H + k : a.h + (int64_t)drow * H + (k - H);
+  } else if constexpr (MODE == NODE_UPD) {
+    p = k < H ? a.h + row * H + k : a.m + row * 2 * H + (k - H);
+  } else if constexpr (MODE == EDGE_UPD) {
+    p = k < H ? a.e + row * H + k
+              : (k < 2 * H ? a.h + (int64_t)srow * H + (k - H) : a.h + (int64_t)drow * H + (k - 2 * H));
+  } else {  // CLS
+    p = a.e + row * H + k;
+  }
+  return *reinterpret_cast<const float4*>(p);
+}
+
+template <int H, int MODE>
+__global__ void __launch_bounds__(kTileThreads) k_mlp(MlpArgs a) {
+  constexpr int LDA2 = H + 4;
+  __shared__ __align__(16) float As[kTileM * kLdaChunk];
+  __shared__ __align__(16) float A2[kTileM * LDA2];
+  __shared__ __align__(16) float Ws[kKC * H];
+  __shared__ int s_src[kTileM], s_dst[kTileM];
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int64_t n_rows = (MODE == NODE_ENC || MODE == NODE_UPD) ? a.n_rows : (int64_t)*a.n_rows_dev;
+  const int64_t n_tiles = (n_rows + kTileM - 1) / kTileM;
+  const LinF32& l1 = MODE == CLS ? a.cls.l1 : a.blk.l1;
+
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int64_t row0 = tile * kTileM;
+    __syncthreads();
+    if constexpr (MODE == EDGE_ENC || MODE == EDGE_UPD) {
+      if (tid < kTileM) {
+        const int64_t r = row0 + tid;
+        // out-of-range ids are flagged by the index pass; clamp so reads stay in bounds
+        const int nn = (int)a.n_rows;
+        s_src[tid] = r < n_rows ? min(max(a.src[r], 0), nn - 1) : 0;
+        s_dst[tid] = r < n_rows ? min(max(a.dst[r], 0), nn - 1) : 0;
+      }
+    }
+    TileAcc<H> acc;
+    acc.zero();
+    if constexpr (MODE == NODE_ENC) {
+      if (tid < kTileM) {
+        const int64_t r = row0 + tid;
+        float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < n_rows) {
+          f.x = (a.x[r] - __ldg(a.norm + 0)) / __ldg(a.norm + 3);
+          f.y = (a.y[r] - __ldg(a.norm + 1)) / __ldg(a.norm + 4);
+          f.z = (a.z[r] - __ldg(a.norm + 2)) / __ldg(a.norm + 5);
+        }
+        *reinterpret_cast<float4*>(As + tid * 4) = f;
+      }
+      if (tid < H) reinterpret_cast<float4*>(Ws)[tid] = __ldg(reinterpret_cast<const float4*>(l1.wt) + tid);
+      __syncthreads();
+      acc.template mma<4>(As, 4, 0, Ws, ty, tx);
+    } else {
+      const int K1 = l1.k_pad;
+      const int qrow = tid >> 2, qk = (tid & 3) * 4;  // one float4 of the A chunk per thread
+      const int64_t grow = row0 + qrow;
+      const bool valid = grow < n_rows;
+      for (int k0 = 0; k0 < K1; k0 += kKC) {
+        __syncthreads();
+        if constexpr (MODE == EDGE_ENC || MODE == EDGE_UPD) {
+          *reinterpret_cast<float4*>(As + qrow * kLdaChunk + qk) =
+              gather4<H, MODE>(a, grow, valid, k0 + qk, s_src[qrow], s_dst[qrow]);
+        } else {
+          *reinterpret_cast<float4*>(As + qrow * kLdaChunk + qk) =
+              gather4<H, MODE>(a, grow, valid, k0 + qk, 0, 0);
+        }
+        load_w_chunk<kKC, H>(Ws, l1.wt + (size_t)k0 * H, tid);
+        __syncthreads();
+        acc.template mma<kKC>(As, kLdaChunk, 0, Ws, ty, tx);
+      }
+    }
+    if constexpr (MODE == CLS) {
+      bias_ln_relu<H>(acc, a.cls.l1.b, a.cls.g1, a.cls.be1, tx);
+      const float b2 = __ldg(a.cls.b2);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        float s = 0.f;
+#pragma unroll
+        for (int j = 0; j < H / 16; ++j) s = fmaf(acc.v[r][j], __ldg(a.cls.w2 + ColMap<H>::col(tx, j)), s);
+        s = halfwarp_sum(s);
+        const int64_t row = row0 + ty * 4 + r;
+        if (tx == 0 && row < n_rows) a.logits[row] = s + b2;
+      }
+    } else {
+      bias_ln_relu<H>(acc, a.blk.l1.b, a.blk.g1, a.blk.be1, tx);
+      store_tile_smem<H>(acc, A2, LDA2, ty, tx);
+      acc.zero();
+      for (int k0 = 0; k0 < H; k0 += kKC) {
+        __syncthreads();
+        load_w_chunk<kKC, H>(Ws, a.blk.l2.wt + (size_t)k0 * H, tid);
+        __syncthreads();
+        acc.template mma<kKC>(A2, LDA2, k0, Ws, ty, tx);
+      }
+      bias_ln_relu<H>(acc, a.blk.l2.b, a.blk.g2, a.blk.be2, tx);
+      // residual + store (each thread owns whole float4 groups or strided columns)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int64_t row = row0 + ty * 4 + r;
+        if (row >= n_rows) continue;
+        float* out = (MODE == NODE_ENC || MODE == NODE_UPD) ? a.h_out + row * H : a.e + row * H;
+        const float* res = MODE == NODE_UPD ? a.h + row * H : (MODE == EDGE_UPD ? a.e + row * H : nullptr);
+#pragma unroll
+        for (int j = 0; j < H / 16; ++j) {
+          const int c = ColMap<H>::col(tx, j);
+          float v = acc.v[r][j];
+          if (res) v += res[c];
+          out[c] = v;
+        }
+      }
+    }
+  }
+}
+
+constexpr const char* kMlpName[] = {"gnn_node_encoder_f32", "gnn_edge_encoder_f32",
+                                    "gnn_node_update_f32", "gnn_edge_update_f32",
+                                    "gnn_classifier_f32"};
+
+template <int H, int MODE>
+void launch_mlp(etx_ctx* ctx, const MlpArgs& a, int64_t max_rows, cudaStream_t s) {
+  const int64_t tiles = (max_rows + kTileM - 1) / kTileM;
+  if (tiles == 0) return;
+  const int grid = grid_for(ctx, (const void*)k_mlp<H, MODE>, kTileThreads, 0, tiles);
+  launch(ctx, kMlpName[MODE], k_mlp<H, MODE>, grid, kTileThreads, 0, s, a);
+}
+
+template <int H>
+cudaError_t forward(etx_ctx* ctx, const float* x, const float* y, const float* z, int64_t N,
+                    const int32_t* src, const int32_t* dst, const int32_t* n_edges_dev,
+                    float* logits, cudaStream_t s) {
+  const int64_t Ecap = ctx->cfg.max_edges;
+  MlpArgs a{};
+  a.n_rows = N;
+  a.n_rows_dev = n_edges_dev;
+  a.x = x; a.y = y; a.z = z;
+  a.norm = ctx->w.norm + 6;
+  a.src = src; a.dst = dst;
+  a.h = ctx->h; a.m = ctx->m; a.e = ctx->e; a.h_out = ctx->h; a.logits = logits;
+
+  a.blk = ctx->w.node_enc;
+  launch_mlp<H, NODE_ENC>(ctx, a, N, s);
+  a.blk = ctx->w.edge_enc;
+  launch_mlp<H, EDGE_ENC>(ctx, a, Ecap, s);
+  const int msg_grid = grid_for(ctx, (const void*)k_messages<H>, 256, 0,
+                                (N + (256 / 32) * (32 / (H / 4)) - 1) / ((256 / 32) * (32 / (H / 4))));
+  for (int k = 0; k < ctx->cfg.n_iters; ++k) {
+    if (N > 0)
+      launch(ctx, "gnn_messages", k_messages<H>, msg_grid, 256, 0, s, ctx->e, ctx->out_off,
+             ctx->in_off, ctx->perm_in, n_edges_dev, (int)N, ctx->m);
+    a.blk = ctx->w.node[k];
+    launch_mlp<H, NODE_UPD>(ctx, a, N, s);
+    a.blk = ctx->w.edge[k];
+    launch_mlp<H, EDGE_UPD>(ctx, a, Ecap, s);
+  }
+  a.cls = ctx->w.cls;
+  launch_mlp<H, CLS>(ctx, a, Ecap, s);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_edge_index(etx_ctx* ctx, int64_t N, const int32_t* src, const int32_t* dst,
+                              const int32_t* n_edges_dev, cudaStream_t s) {
+  const int64_t Ecap = ctx->cfg.max_edges;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(ctx->out_off, 0, (N + 1) * sizeof(int32_t), s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(ctx->in_cnt, 0, (N + 1) * sizeof(int32_t), s)) != cudaSuccess) return e;
+  const int ge = grid_for(ctx, (const void*)k_out_offsets, 256, 0, (Ecap + 256) / 256);
+  launch(ctx, "index_out_offsets", k_out_offsets, ge, 256, 0, s, src, dst, n_edges_dev, (int)N,
+         ctx->out_off, ctx->d_err);
+  launch(ctx, "index_in_count", k_in_count, ge, 256, 0, s, dst, n_edges_dev, (int)N, ctx->in_cnt);
+  if ((e = exclusive_scan(ctx, ctx->in_cnt, ctx->in_off, N, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(ctx->in_cnt, 0, (N + 1) * sizeof(int32_t), s)) != cudaSuccess) return e;
+  launch(ctx, "index_in_fill", k_in_fill, ge, 256, 0, s, dst, n_edges_dev, (int)N, ctx->in_off,
+         ctx->in_cnt, ctx->perm_in);
+  const int gn = grid_for(ctx, (const void*)k_in_sort, 256, 0, (N + 255) / 256);
+  if (N > 0) launch(ctx, "index_in_sort", k_in_sort, gn, 256, 0, s, ctx->in_off, (int)N, ctx->perm_in);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gnn_forward_f32(etx_ctx* ctx, const float* x, const float* y, const float* z,
+                                   int64_t n_hits, const int32_t* src, const int32_t* dst,
+                                   const int32_t* n_edges_dev, float* logits, cudaStream_t s) {
+  switch (ctx->cfg.hidden) {
+    case 16: return forward<16>(ctx, x, y, z, n_hits, src, dst, n_edges_dev, logits, s);
+    case 32: return forward<32>(ctx, x, y, z, n_hits, src, dst, n_edges_dev, logits, s);
+    case 64: return forward<64>(ctx, x, y, z, n_hits, src, dst, n_edges_dev, logits, s);
+    case 128: return forward<128>(ctx, x, y, z, n_hits, src, dst, n_edges_dev, logits, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace etx

@@ -1,0 +1,241 @@
+// Rough-graph construction (paper Eq. 1, Sec. 5.1, Sec. 7.2).
+//
+// Hits arrive plane-sorted per event, so the candidates of every source hit
+// on plane p (the hits of planes p+1 and p+2) form one contiguous index range.
+// One block per (event, plane): the candidate embeddings are staged in shared
+// memory (structure of arrays, so lane j reads candidate j bank-conflict free),
+// one warp per source hit, lanes over candidates, ballot + popc to count and
+// compact the hits inside the radius.  When more than k_max hits qualify, the
+// k_max-th smallest squared distance is found by a 32-step radix select on
+// the FP32 bit patterns (non-negative floats order like their bits); ties at
+// that value are taken in ascending candidate index, which realises the
+// (d2, j) order.
+//
+// Two launches of the same kernel: pass 0 writes per-hit counts, an
+// exclusive scan turns them into CSR offsets (which is also the src-CSR of the
+// edge list), pass 1 writes the edges at those offsets in (i, j) order.
+#include "etx_internal.cuh"
+
+namespace etx {
+namespace {
+
+constexpr int kKnnThreads = 128;
+constexpr int kStageFloats = 16384;  // 64 KB of staged candidate coordinates per block
+constexpr int kMaxDim = 32;
+
+// Squared distance, FP32, one rounding per operation, dimensions in order.
+__device__ __forceinline__ float d2_ordered(const float* __restrict__ ei, const float* cand,
+                                            int stride, int D) {
+  float s = 0.f;
+  for (int d = 0; d < D; ++d) {
+    const float t = __fsub_rn(ei[d], cand[d * stride]);
+    s = __fadd_rn(s, __fmul_rn(t, t));
+  }
+  return s;
+}
+
+__global__ void k_check_hits(const int8_t* __restrict__ plane, const int32_t* __restrict__ hoff,
+                             int32_t n_events, int64_t n_hits, int n_planes, int* err) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i <= n_events) {
+    const int v = hoff[i];
+    if ((i == 0 && v != 0) || (i == n_events && v != n_hits) || (i > 0 && v < hoff[i - 1]))
+      set_err(err, DERR_UNSORTED);
+  }
+  if (i >= n_hits) return;
+  const int p = plane[i];
+  if (p < 0 || p >= n_planes) {
+    set_err(err, DERR_UNSORTED);
+    return;
+  }
+  if (i > 0 && plane[i - 1] > p) {
+    // allowed only at an event boundary
+    int lo = 0, hi = n_events;  // find b with hoff[b] <= i < hoff[b+1]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (hoff[mid] <= i) lo = mid; else hi = mid;
+    }
+    if (hoff[lo] != i) set_err(err, DERR_UNSORTED);
+  }
+}
+
+// plane_off[b*(P+1) + p] = first hit of event b with plane >= p (p = 0..P).
+__global__ void k_plane_bins(const int8_t* __restrict__ plane, const int32_t* __restrict__ hoff,
+                             int32_t n_events, int n_hits, int n_planes,
+                             int32_t* __restrict__ plane_off) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t total = (int64_t)n_events * (n_planes + 1);
+  if (t >= total) return;
+  const int b = (int)(t / (n_planes + 1)), p = (int)(t % (n_planes + 1));
+  // clamp so malformed offsets (flagged by k_check_hits) cannot index out of range
+  int lo = min(max(hoff[b], 0), n_hits), hi = min(max(hoff[b + 1], 0), n_hits);
+  if (hi < lo) hi = lo;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (plane[mid] < p) lo = mid + 1; else hi = mid;
+  }
+  plane_off[t] = lo;
+}
+
+template <bool EMIT>
+__global__ void __launch_bounds__(kKnnThreads)
+k_knn(const float* __restrict__ emb, int D, const int32_t* __restrict__ plane_off, int n_planes,
+      float radius, int k_max, int32_t* __restrict__ cnt_or_off, int64_t n_hits,
+      int32_t* __restrict__ src, int32_t* __restrict__ dst, int64_t capacity, int* err) {
+  extern __shared__ float cand_s[];  // [D][n_stage]
+  const int b = blockIdx.x / (n_planes - 1);
+  const int p = blockIdx.x % (n_planes - 1);
+  const int32_t* po = plane_off + (int64_t)b * (n_planes + 1);
+  const int s_lo = po[p], s_hi = po[p + 1];
+  const int c_lo = po[p + 1], c_hi = po[min(p + 3, n_planes)];
+  const int n_cand = c_hi - c_lo;
+  if (EMIT && cnt_or_off[n_hits] > capacity) {
+    if (threadIdx.x == 0) set_err(err, DERR_CAPACITY);
+    return;
+  }
+  if (s_hi <= s_lo) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  if (n_cand <= 0) {
+    if (!EMIT)
+      for (int i = s_lo + threadIdx.x; i < s_hi; i += blockDim.x) cnt_or_off[i] = 0;
+    return;
+  }
+  // candidate storage: shared (SoA, stride n_cand) or global (AoS, stride 1)
+  const bool staged = n_cand * D <= kStageFloats;
+  if (staged) {
+    for (int t = threadIdx.x; t < n_cand * D; t += blockDim.x) {
+      const int j = t / D, d = t - j * D;
+      cand_s[d * n_cand + j] = emb[(int64_t)(c_lo + j) * D + d];
+    }
+    __syncthreads();
+  }
+  const float* cbase = staged ? cand_s : emb + (int64_t)c_lo * D;
+  const int cstride = staged ? n_cand : 1;       // stride between dimensions
+  const int cstep = staged ? 1 : D;              // stride between candidates
+  const float r2 = __fmul_rn(radius, radius);
+
+  for (int i = s_lo + warp; i < s_hi; i += kKnnThreads / 32) {
+    float ei[kMaxDim];
+    for (int d = 0; d < D; ++d) ei[d] = emb[(int64_t)i * D + d];
+    // pass A: count the hits inside the radius
+    int cnt = 0;
+    for (int j0 = 0; j0 < n_cand; j0 += 32) {
+      const int j = j0 + lane;
+      bool ok = false;
+      if (j < n_cand) ok = d2_ordered(ei, cbase + (int64_t)j * cstep, cstride, D) < r2;
+      cnt += __popc(__ballot_sync(0xffffffffu, ok));
+    }
+    if (!EMIT) {
+      if (lane == 0) cnt_or_off[i] = min(cnt, k_max);
+      continue;
+    }
+    const int base = cnt_or_off[i];
+    uint32_t kth = 0xffffffffu;  // keep keys < kth, plus `take_eq` keys == kth
+    int take_eq = 0;
+    if (cnt > k_max) {
+      // radix select: largest v with #{key < v} < k_max is the k_max-th smallest key
+      uint32_t prefix = 0;
+      for (int bit = 31; bit >= 0; --bit) {
+        const uint32_t trial = prefix | (1u << bit);
+        int c = 0;
+        for (int j0 = 0; j0 < n_cand; j0 += 32) {
+          const int j = j0 + lane;
+          bool lt = false;
+          if (j < n_cand) {
+            const float d2 = d2_ordered(ei, cbase + (int64_t)j * cstep, cstride, D);
+            lt = d2 < r2 && __float_as_uint(d2) < trial;
+          }
+          c += __popc(__ballot_sync(0xffffffffu, lt));
+        }
+        if (c < k_max) prefix = trial;
+      }
+      kth = prefix;
+      int less = 0;
+      for (int j0 = 0; j0 < n_cand; j0 += 32) {
+        const int j = j0 + lane;
+        bool lt = false;
+        if (j < n_cand) {
+          const float d2 = d2_ordered(ei, cbase + (int64_t)j * cstep, cstride, D);
+          lt = d2 < r2 && __float_as_uint(d2) < kth;
+        }
+        less += __popc(__ballot_sync(0xffffffffu, lt));
+      }
+      take_eq = k_max - less;
+    }
+    // pass B: write the kept edges in ascending j
+    int written = 0, eq_seen = 0;
+    for (int j0 = 0; j0 < n_cand; j0 += 32) {
+      const int j = j0 + lane;
+      bool in = false, eq = false;
+      if (j < n_cand) {
+        const float d2 = d2_ordered(ei, cbase + (int64_t)j * cstep, cstride, D);
+        if (d2 < r2) {
+          const uint32_t key = __float_as_uint(d2);
+          in = key < kth;
+          eq = key == kth;
+        }
+      }
+      const unsigned eqm = __ballot_sync(0xffffffffu, eq);
+      if (eq) in = eq_seen + __popc(eqm & lt_mask) < take_eq;
+      eq_seen += __popc(eqm);
+      const unsigned inm = __ballot_sync(0xffffffffu, in);
+      if (in) {
+        const int pos = base + written + __popc(inm & lt_mask);
+        src[pos] = i;
+        dst[pos] = c_lo + j;
+      }
+      written += __popc(inm);
+    }
+  }
+}
+
+__global__ void k_edge_offsets(const int32_t* __restrict__ off, const int32_t* __restrict__ hoff,
+                               int32_t n_events, int n_hits, int32_t* __restrict__ edge_offsets) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b <= n_events) edge_offsets[b] = off[min(max(hoff[b], 0), n_hits)];
+}
+
+}  // namespace
+
+cudaError_t launch_build_graph(etx_ctx* ctx, const float* emb, const int8_t* plane,
+                               const int32_t* hit_offsets, int32_t n_events, int64_t n_hits,
+                               float radius, int32_t k_max, int32_t* src, int32_t* dst,
+                               int64_t edge_capacity, int32_t* edge_offsets, cudaStream_t s) {
+  const int P = ctx->cfg.n_planes;
+  const int D = ctx->cfg.emb_widths[ctx->cfg.emb_depth];
+  const int64_t nchk = (n_hits > n_events ? n_hits : n_events + 1);
+  launch(ctx, "graph_check_hits", k_check_hits, (unsigned)((nchk + 255) / 256), 256, 0, s, plane,
+         hit_offsets, n_events, n_hits, P, ctx->d_err);
+  const int64_t nb = (int64_t)n_events * (P + 1);
+  if (nb > 0)
+    launch(ctx, "graph_plane_bins", k_plane_bins, (unsigned)((nb + 255) / 256), 256, 0, s, plane,
+           hit_offsets, n_events, (int)n_hits, P, ctx->plane_off);
+  int32_t* cnt = ctx->hit_cnt;  // counts, then (in place) offsets; [n_hits + 1]
+  const unsigned blocks = (unsigned)n_events * (unsigned)(P - 1);
+  const size_t smem = (size_t)kStageFloats * sizeof(float);
+  // hits of the last plane get no block: start from zero counts
+  cudaError_t e0 = cudaMemsetAsync(cnt, 0, (size_t)(n_hits + 1) * sizeof(int32_t), s);
+  if (e0 != cudaSuccess) return e0;
+  if (n_hits > 0 && blocks > 0)
+    launch(ctx, "graph_knn_count", k_knn<false>, blocks, kKnnThreads, smem, s, emb, D,
+           ctx->plane_off, P, radius, k_max, cnt, n_hits, nullptr, nullptr, 0, ctx->d_err);
+  cudaError_t e = exclusive_scan(ctx, cnt, cnt, n_hits, s);
+  if (e != cudaSuccess) return e;
+  if (n_hits > 0 && blocks > 0)
+    launch(ctx, "graph_knn_emit", k_knn<true>, blocks, kKnnThreads, smem, s, emb, D,
+           ctx->plane_off, P, radius, k_max, cnt, n_hits, src, dst, edge_capacity, ctx->d_err);
+  launch(ctx, "graph_edge_offsets", k_edge_offsets, (unsigned)((n_events + 1 + 255) / 256), 256, 0,
+         s, cnt, hit_offsets, n_events, (int)n_hits, edge_offsets);
+  return cudaGetLastError();
+}
+
+cudaError_t knn_set_smem_attr() {
+  const size_t smem = (size_t)kStageFloats * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(k_knn<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_knn<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+}  // namespace etx

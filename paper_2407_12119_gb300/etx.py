@@ -1,0 +1,265 @@
+"""Thin ctypes binding of libetx (include/etx.h).
+
+Argument marshalling only: every step of the pipeline runs in the CUDA
+library.  PyTorch provides device memory and the current stream.  If the
+library has not been built the import of this module still works, but the
+first call raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import numpy as np
+import torch
+
+_LIB_PATH = Path(__file__).resolve().parent / "libetx.so"
+_lib = None
+
+ETX_OK, ETX_ERR_ARG, ETX_ERR_UNSORTED, ETX_ERR_CAPACITY = 0, 1, 2, 3
+ETX_ERR_CUDA, ETX_ERR_TIMEOUT, ETX_ERR_UNSUPPORTED, ETX_ERR_STATE = 4, 5, 6, 7
+_STATUS_NAMES = {0: "ETX_OK", 1: "ETX_ERR_ARG", 2: "ETX_ERR_UNSORTED", 3: "ETX_ERR_CAPACITY",
+                 4: "ETX_ERR_CUDA", 5: "ETX_ERR_TIMEOUT", 6: "ETX_ERR_UNSUPPORTED",
+                 7: "ETX_ERR_STATE"}
+DTYPES = {"f32": 0, "bf16": 1, "fp8": 2}
+MAX_EMB_LAYERS = 8
+
+EXPORTED = ["etx_ctx_create", "etx_ctx_destroy", "etx_last_error", "etx_weights_size",
+            "etx_load_weights", "etx_ctx_sync", "etx_embed", "etx_build_graph",
+            "etx_gnn_forward", "etx_gnn_param_count", "etx_gnn_backward",
+            "etx_edges_to_tracks", "etx_launch_count", "etx_profile_enable", "etx_profile_read"]
+
+
+class EtxConfig(ctypes.Structure):
+    _fields_ = [("emb_depth", ctypes.c_int32),
+                ("emb_widths", ctypes.c_int32 * (MAX_EMB_LAYERS + 1)),
+                ("hidden", ctypes.c_int32),
+                ("n_iters", ctypes.c_int32),
+                ("n_planes", ctypes.c_int32),
+                ("max_events", ctypes.c_int32),
+                ("max_hits", ctypes.c_int64),
+                ("max_edges", ctypes.c_int64),
+                ("train", ctypes.c_int32)]
+
+
+class EtxError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def library_path() -> Path:
+    return _LIB_PATH
+
+
+def lib() -> ctypes.CDLL:
+    """Load libetx.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not _LIB_PATH.exists():
+        raise RuntimeError(f"{_LIB_PATH.name} is not built: run "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(str(_LIB_PATH))
+    vp, i32, i64, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+    cfgp = ctypes.POINTER(EtxConfig)
+    sig = {
+        "etx_ctx_create": (i32, [cfgp, i32, ctypes.POINTER(vp)]),
+        "etx_ctx_destroy": (i32, [vp]),
+        "etx_last_error": (ctypes.c_char_p, [vp]),
+        "etx_weights_size": (i64, [cfgp]),
+        "etx_gnn_param_count": (i64, [cfgp]),
+        "etx_load_weights": (i32, [vp, vp, i64]),
+        "etx_ctx_sync": (i32, [vp, vp]),
+        "etx_embed": (i32, [vp, vp, vp, vp, i64, vp, vp]),
+        "etx_build_graph": (i32, [vp, vp, vp, vp, i32, i64, f32, i32, vp, vp, i64, vp, vp]),
+        "etx_gnn_forward": (i32, [vp, vp, vp, vp, i64, vp, vp, vp, i32, i32, vp, vp]),
+        "etx_gnn_backward": (i32, [vp, vp, vp, vp]),
+        "etx_edges_to_tracks": (i32, [vp, vp, vp, vp, f32, vp, vp, i32, i64, i32, vp, vp, vp]),
+        "etx_launch_count": (i64, [vp]),
+        "etx_profile_enable": (i32, [vp, i32]),
+        "etx_profile_read": (i32, [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_int64), i32]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def make_config(model, max_events: int, max_hits: int, max_edges: int, train: bool = False) -> EtxConfig:
+    """``model`` needs emb_widths, hidden, n_iters and n_planes attributes."""
+    c = EtxConfig()
+    w = list(model.emb_widths)
+    if len(w) - 1 > MAX_EMB_LAYERS:
+        raise ValueError("too many embedding layers")
+    c.emb_depth = len(w) - 1
+    for i, v in enumerate(w):
+        c.emb_widths[i] = int(v)
+    c.hidden = int(model.hidden)
+    c.n_iters = int(model.n_iters)
+    c.n_planes = int(getattr(model, "n_planes", 26))
+    c.max_events = int(max_events)
+    c.max_hits = int(max_hits)
+    c.max_edges = int(max_edges)
+    c.train = int(bool(train))
+    return c
+
+
+def weights_size(model) -> int:
+    return int(lib().etx_weights_size(ctypes.byref(make_config(model, 1, 1, 1))))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _need(t, dtype, name, device):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.device != device:
+        raise ValueError(f"{name} must be on {device}, got {t.device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+class Context:
+    """An etx_ctx: model shapes, capacities, loaded weights and scratch."""
+
+    def __init__(self, model, max_events: int, max_hits: int, max_edges: int, device: int = 0,
+                 train: bool = False):
+        L = lib()
+        self.model = model
+        self.cfg = make_config(model, max_events, max_hits, max_edges, train)
+        self.device = torch.device("cuda", device)
+        h = ctypes.c_void_p()
+        st = L.etx_ctx_create(ctypes.byref(self.cfg), int(device), ctypes.byref(h))
+        if st != ETX_OK:
+            raise EtxError(st, "etx_ctx_create failed (bad config or out of device memory)")
+        self._h = h
+        self.emb_dim = int(model.emb_widths[-1])
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().etx_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != ETX_OK:
+            msg = lib().etx_last_error(self._h)
+            raise EtxError(st, msg.decode() if msg else "")
+
+    # ---- entry points ------------------------------------------------------
+    def load_weights(self, blob: np.ndarray):
+        b = np.ascontiguousarray(blob, dtype=np.float32)
+        self._check(lib().etx_load_weights(self._h, b.ctypes.data_as(ctypes.c_void_p), b.size))
+
+    @property
+    def launch_count(self) -> int:
+        """Kernels launched by this context so far."""
+        return int(lib().etx_launch_count(self._h))
+
+    def profile(self, on: bool = True):
+        self._check(lib().etx_profile_enable(self._h, int(bool(on))))
+
+    def profile_read(self, max_entries: int = 64) -> dict:
+        """{kernel name: (total ms, launches)} since the last read."""
+        names = (ctypes.c_char_p * max_entries)()
+        ms = (ctypes.c_double * max_entries)()
+        cnt = (ctypes.c_int64 * max_entries)()
+        n = lib().etx_profile_read(self._h, names, ms, cnt, max_entries)
+        if n < 0:
+            raise EtxError(ETX_ERR_CUDA, "etx_profile_read failed")
+        return {names[i].decode(): (float(ms[i]), int(cnt[i])) for i in range(n)}
+
+    def sync(self, stream=None):
+        self._check(lib().etx_ctx_sync(self._h, _stream(stream)))
+
+    def embed(self, x, y, z, out=None, stream=None):
+        dev = self.device
+        for t, n in ((x, "x"), (y, "y"), (z, "z")):
+            _need(t, torch.float32, n, dev)
+        n = x.shape[0]
+        if out is None:
+            out = torch.empty((n, self.emb_dim), dtype=torch.float32, device=dev)
+        _need(out, torch.float32, "emb", dev)
+        self._check(lib().etx_embed(self._h, _ptr(x), _ptr(y), _ptr(z), n, _ptr(out), _stream(stream)))
+        return out
+
+    def build_graph(self, emb, plane, hit_offsets, radius: float, k_max: int,
+                    edge_capacity: int | None = None, out=None, stream=None):
+        dev = self.device
+        _need(emb, torch.float32, "emb", dev)
+        _need(plane, torch.int8, "plane", dev)
+        _need(hit_offsets, torch.int32, "hit_offsets", dev)
+        n_hits = emb.shape[0]
+        n_events = hit_offsets.shape[0] - 1
+        if edge_capacity is None:
+            edge_capacity = max(1, n_hits * int(k_max))
+        if out is None:
+            src = torch.empty(edge_capacity, dtype=torch.int32, device=dev)
+            dst = torch.empty(edge_capacity, dtype=torch.int32, device=dev)
+            eoff = torch.empty(n_events + 1, dtype=torch.int32, device=dev)
+        else:
+            src, dst, eoff = out
+        self._check(lib().etx_build_graph(self._h, _ptr(emb), _ptr(plane), _ptr(hit_offsets),
+                                          n_events, n_hits, float(radius), int(k_max), _ptr(src),
+                                          _ptr(dst), int(src.shape[0]), _ptr(eoff), _stream(stream)))
+        return src, dst, eoff
+
+    def gnn_forward(self, x, y, z, src, dst, edge_offsets, dtype: str = "f32", logits=None,
+                    stream=None):
+        dev = self.device
+        for t, n in ((x, "x"), (y, "y"), (z, "z")):
+            _need(t, torch.float32, n, dev)
+        _need(src, torch.int32, "src", dev)
+        _need(dst, torch.int32, "dst", dev)
+        _need(edge_offsets, torch.int32, "edge_offsets", dev)
+        if logits is None:
+            logits = torch.empty(src.shape[0], dtype=torch.float32, device=dev)
+        _need(logits, torch.float32, "logits", dev)
+        n_events = edge_offsets.shape[0] - 1
+        self._check(lib().etx_gnn_forward(self._h, _ptr(x), _ptr(y), _ptr(z), x.shape[0], _ptr(src),
+                                          _ptr(dst), _ptr(edge_offsets), n_events, DTYPES[dtype],
+                                          _ptr(logits), _stream(stream)))
+        return logits
+
+    def edges_to_tracks(self, src, dst, logits, threshold_logit: float, edge_offsets, hit_offsets,
+                        min_hits: int = 3, labels=None, n_tracks=None, stream=None):
+        dev = self.device
+        _need(src, torch.int32, "src", dev)
+        _need(dst, torch.int32, "dst", dev)
+        _need(logits, torch.float32, "logits", dev)
+        _need(edge_offsets, torch.int32, "edge_offsets", dev)
+        _need(hit_offsets, torch.int32, "hit_offsets", dev)
+        n_events = hit_offsets.shape[0] - 1
+        n_hits = None
+        if labels is None:
+            n_hits = int(hit_offsets[-1].item())
+            labels = torch.empty(n_hits, dtype=torch.int32, device=dev)
+        n_hits = labels.shape[0]
+        if n_tracks is None:
+            n_tracks = torch.empty(max(n_events, 1), dtype=torch.int32, device=dev)
+        self._check(lib().etx_edges_to_tracks(self._h, _ptr(src), _ptr(dst), _ptr(logits),
+                                              float(threshold_logit), _ptr(edge_offsets),
+                                              _ptr(hit_offsets), n_events, n_hits, int(min_hits),
+                                              _ptr(labels), _ptr(n_tracks), _stream(stream)))
+        return labels, n_tracks

@@ -1,0 +1,358 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Integer outputs (edge lists, offsets, labels) must match exactly when both
+sides start from the same inputs; FP32 logits within max-abs 1e-4; the only
+allowed graph differences end to end are pairs within 1e-5 of the radius (or
+of the k-th kept distance), which are counted and reported.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import etx_oracle as O
+from velo_synth import (WORKLOADS, ModelConfig, concat_events, make_batch, make_event,
+                        make_weights, pack_blob)
+
+pytestmark = pytest.mark.gpu
+
+LOGIT_TOL = 1e-4      # FP32 logits vs FP64 oracle (max-abs)
+NEAR_CUT = 1e-5       # distance band around the radius / k-th distance
+
+
+@pytest.fixture(scope="module")
+def etx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2407_12119_gb300 import build as b
+    b.build()
+    from paper_2407_12119_gb300 import etx as m
+    return m
+
+
+def cuda(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def events(recipe, seeds, extra=()):
+    parts = [make_event(recipe, s) for s in seeds]
+    for pos, part in extra:
+        parts.insert(pos, part)
+    return concat_events(parts)
+
+
+def empty_event():
+    z = np.zeros(0, np.float32)
+    return (z, z, z, np.zeros(0, np.int8), np.zeros(0, np.int32))
+
+
+class Setup:
+    def __init__(self, etx, model, batch, weights, max_edges=None):
+        self.model, self.b, self.W = model, batch, weights
+        N = max(batch.n_hits, 1)
+        self.ctx = etx.Context(model, max(batch.n_events, 1), N,
+                               max_edges or max(N * model.k_max, 1))
+        self.ctx.load_weights(pack_blob(model, weights))
+        self.x, self.y, self.z = (cuda(batch.x), cuda(batch.y), cuda(batch.z))
+        self.plane = cuda(batch.plane)
+        self.hoff = cuda(batch.hit_offsets)
+        self.depth = len(model.emb_widths) - 1
+
+    def oracle_emb(self):
+        return O.embed(self.W, self.depth, self.b.x, self.b.y, self.b.z)
+
+
+def setup_for(etx, name, n_events=None, perturb=0.2, extra=(), model=None, seeds=None):
+    wl = WORKLOADS[name]
+    model = model or wl.model
+    if seeds is None:
+        seeds = [wl.base_seed + i for i in range(n_events or wl.n_events)]
+    b = events(wl.recipe, seeds, extra)
+    W = make_weights(model, wl.calibration(), perturb=perturb)
+    return Setup(etx, model, b, W)
+
+
+def oracle_graph32(st, emb64, radius=None, k=None):
+    emb32 = emb64.astype(np.float32)
+    s, d, eo = O.build_graph(emb32, st.b.plane, st.b.hit_offsets,
+                             st.model.radius if radius is None else radius,
+                             st.model.k_max if k is None else k, precision="fp32")
+    return emb32, s, d, eo
+
+
+def gpu_graph(st, emb32, radius=None, k=None, cap=None):
+    src, dst, eo = st.ctx.build_graph(cuda(emb32), st.plane, st.hoff,
+                                      st.model.radius if radius is None else radius,
+                                      st.model.k_max if k is None else k, edge_capacity=cap)
+    st.ctx.sync()
+    eo = eo.cpu().numpy()
+    E = int(eo[-1])
+    return src[:E].cpu().numpy(), dst[:E].cpu().numpy(), eo
+
+
+# ---------------------------------------------------------------------------
+# embedding
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name,n", [("plain", 1), ("batch500", 4)])
+def test_embed_parity(etx, name, n):
+    st = setup_for(etx, name, n)
+    ref = st.oracle_emb()
+    out = st.ctx.embed(st.x, st.y, st.z)
+    st.ctx.sync()
+    got = out.cpu().numpy().astype(np.float64)
+    err = np.abs(got - ref)
+    # FP32 MLP: the error scales with the magnitude of the outputs
+    bound = 2e-6 * (1.0 + np.abs(ref).max())
+    print(f"embed {name}: max |err| {err.max():.3e}, bound {bound:.3e}")
+    assert err.max() <= bound
+
+
+# ---------------------------------------------------------------------------
+# graph, stage-isolated: both sides start from the same FP32 embedding
+# ---------------------------------------------------------------------------
+def _check_graph_exact(st, emb64, radius=None, k=None):
+    emb32, s, d, eo = oracle_graph32(st, emb64, radius, k)
+    gs, gd, geo = gpu_graph(st, emb32, radius, k)
+    np.testing.assert_array_equal(geo, eo)
+    np.testing.assert_array_equal(gs, s)
+    np.testing.assert_array_equal(gd, d)
+    return s.size
+
+
+def test_graph_exact_plain(etx):
+    st = setup_for(etx, "plain", 1)
+    assert _check_graph_exact(st, st.oracle_emb()) > 0
+
+
+def test_graph_exact_ragged_batch_with_empty_events(etx):
+    wl = WORKLOADS["batch500"]
+    st = setup_for(etx, "batch500", seeds=[1000, 1001, 1002, 1003, 1004],
+                   extra=[(0, empty_event()), (3, empty_event())])
+    assert st.b.n_events == 7
+    assert _check_graph_exact(st, st.oracle_emb()) > 0
+
+
+def test_graph_exact_k_cap_binding(etx):
+    st = setup_for(etx, "batch500", 3)
+    emb = st.oracle_emb()
+    n = _check_graph_exact(st, emb, radius=3.0, k=4)
+    assert n > 0
+    # the cap binds for most sources here
+    _, s, _, _ = oracle_graph32(st, emb, radius=3.0, k=4)
+    assert np.bincount(s).max() == 4
+
+
+def test_graph_exact_ties_between_duplicate_hits(etx):
+    wl = WORKLOADS["plain"]
+    x, y, z, p, pid = make_event(wl.recipe, 7)
+    # every hit twice: identical embeddings, so distances tie exactly
+    order = np.argsort(np.concatenate([p, p]), kind="stable")
+    dup = tuple(np.concatenate([a, a])[order] for a in (x, y, z, p, pid))
+    b = concat_events([dup])
+    W = make_weights(wl.model, wl.calibration(), perturb=0.2)
+    st = Setup(etx, wl.model, b, W)
+    assert _check_graph_exact(st, st.oracle_emb(), k=3) > 0
+
+
+def test_graph_exact_unstaged_candidates(etx):
+    # planes 1 and 2 hold more candidates than the shared-memory stage fits
+    rng = np.random.default_rng(3)
+    counts = [12, 1100, 1100, 5]
+    plane = np.concatenate([np.full(c, i, np.int8) for i, c in enumerate(counts)])
+    r = np.sqrt(rng.uniform(5.1 ** 2, 40 ** 2, plane.size))
+    ph = rng.uniform(0, 2 * np.pi, plane.size)
+    ev = ((r * np.cos(ph)).astype(np.float32), (r * np.sin(ph)).astype(np.float32),
+          np.linspace(-287, 750, 26)[plane].astype(np.float32), plane, np.full(plane.size, -1, np.int32))
+    b = concat_events([ev])
+    model = WORKLOADS["batch500"].model
+    W = make_weights(model, WORKLOADS["batch500"].calibration(), perturb=0.2)
+    st = Setup(etx, model, b, W)
+    assert _check_graph_exact(st, st.oracle_emb(), radius=2.0, k=8) > 0
+
+
+def test_graph_literal_radius_gives_no_edges(etx):
+    st = setup_for(etx, "batch500", 2)
+    emb = st.oracle_emb()
+    assert _check_graph_exact(st, emb, radius=1e-3) == 0
+
+
+def test_graph_capacity_overflow_is_reported(etx):
+    st = setup_for(etx, "plain", 1)
+    emb32, s, d, eo = oracle_graph32(st, st.oracle_emb())
+    src, dst, geo = st.ctx.build_graph(cuda(emb32), st.plane, st.hoff, st.model.radius,
+                                       st.model.k_max, edge_capacity=max(1, s.size // 2))
+    with pytest.raises(etx.EtxError) as ei:
+        st.ctx.sync()
+    assert ei.value.status == etx.ETX_ERR_CAPACITY
+    np.testing.assert_array_equal(geo.cpu().numpy(), eo)  # counts are still reported
+
+
+# ---------------------------------------------------------------------------
+# graph, end to end: GPU embedding + GPU graph vs FP64 oracle
+# ---------------------------------------------------------------------------
+def test_graph_end_to_end_only_near_cut_pairs_differ(etx):
+    st = setup_for(etx, "batch500", 4)
+    emb64 = st.oracle_emb()
+    s, d, _ = O.build_graph(emb64, st.b.plane, st.b.hit_offsets, st.model.radius, st.model.k_max)
+    emb = st.ctx.embed(st.x, st.y, st.z)
+    src, dst, eo = st.ctx.build_graph(emb, st.plane, st.hoff, st.model.radius, st.model.k_max)
+    st.ctx.sync()
+    E = int(eo[-1].item())
+    gset = set(zip(src[:E].cpu().tolist(), dst[:E].cpu().tolist()))
+    oset = set(zip(s.tolist(), d.tolist()))
+    diff = gset ^ oset
+    r, k = st.model.radius, st.model.k_max
+    unexplained = 0
+    for i, j in diff:
+        dist = np.sqrt(((emb64[i] - emb64[j]) ** 2).sum())
+        if abs(dist - r) <= NEAR_CUT:
+            continue
+        # rank near-tie: the cap binds and j sits at the k-th kept distance
+        cand = np.nonzero(np.isin(st.b.plane.astype(int) - int(st.b.plane[i]), [1, 2]))[0]
+        ev = np.searchsorted(st.b.hit_offsets, i, side="right") - 1
+        cand = cand[(cand >= st.b.hit_offsets[ev]) & (cand < st.b.hit_offsets[ev + 1])]
+        dd = np.sort(np.sqrt(((emb64[cand] - emb64[i]) ** 2).sum(1)))
+        dd = dd[dd < r]
+        if dd.size > k and abs(dist - dd[k - 1]) <= NEAR_CUT:
+            continue
+        unexplained += 1
+    print(f"end-to-end graph: {len(oset)} oracle edges, {len(diff)} differ, all near the cut")
+    assert unexplained == 0
+    assert len(diff) <= 1e-3 * max(len(oset), 1)
+
+
+# ---------------------------------------------------------------------------
+# interaction network
+# ---------------------------------------------------------------------------
+GNN_CASES = [
+    ("plain", 1, None),
+    ("batch500", 2, None),
+    ("batch500", 2, ModelConfig(emb_widths=(3, 128, 128, 128, 8), hidden=64, n_iters=3,
+                                radius=1.14, k_max=32)),
+    ("plain", 2, ModelConfig(emb_widths=(3, 32, 32, 4), hidden=16, n_iters=4, radius=1.5,
+                             k_max=16)),
+]
+
+
+@pytest.mark.parametrize("name,n,model", GNN_CASES)
+def test_gnn_forward_parity(etx, name, n, model):
+    st = setup_for(etx, name, n, model=model)
+    emb64 = st.oracle_emb()
+    s, d, eo = O.build_graph(emb64, st.b.plane, st.b.hit_offsets, st.model.radius, st.model.k_max)
+    ref = O.gnn_forward(st.W, st.model.n_iters, st.b.x, st.b.y, st.b.z, s, d)
+    logits = st.ctx.gnn_forward(st.x, st.y, st.z, cuda(s, torch.int32), cuda(d, torch.int32),
+                                cuda(eo, torch.int32))
+    st.ctx.sync()
+    err = np.abs(logits.cpu().numpy().astype(np.float64) - ref)
+    print(f"gnn {name} H={st.model.hidden} L={st.model.n_iters}: E={s.size} max |err| {err.max():.3e}")
+    assert err.max() <= LOGIT_TOL
+
+
+def test_gnn_forward_without_edges(etx):
+    st = setup_for(etx, "plain", 1)
+    z = torch.zeros(1, dtype=torch.int32, device="cuda")
+    eo = torch.zeros(2, dtype=torch.int32, device="cuda")
+    logits = st.ctx.gnn_forward(st.x, st.y, st.z, z, z, eo)
+    st.ctx.sync()
+    assert logits.shape[0] == 1
+
+
+def test_gnn_rejects_unsorted_edges(etx):
+    st = setup_for(etx, "plain", 1)
+    s = cuda(np.array([5, 2], np.int32))
+    d = cuda(np.array([40, 41], np.int32))
+    eo = cuda(np.array([0, 2], np.int32))
+    st.ctx.gnn_forward(st.x, st.y, st.z, s, d, eo)
+    with pytest.raises(etx.EtxError) as ei:
+        st.ctx.sync()
+    assert ei.value.status == etx.ETX_ERR_UNSORTED
+
+
+# ---------------------------------------------------------------------------
+# components: same mask on both sides -> identical labels
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("quantile", [0.0, 0.5, 0.9, 0.99, 1.0])
+def test_cc_labels_exact(etx, quantile):
+    st = setup_for(etx, "batch500", 3)
+    emb64 = st.oracle_emb()
+    s, d, eo = O.build_graph(emb64, st.b.plane, st.b.hit_offsets, st.model.radius, st.model.k_max)
+    rng = np.random.default_rng(int(quantile * 100))
+    logits = rng.normal(size=s.size).astype(np.float32)
+    thr = np.float32(np.quantile(logits, quantile)) if quantile < 1.0 else np.float32(10.0)
+    ref = O.connected_components(s, d, logits > thr, st.b.hit_offsets)
+    labels, nt = st.ctx.edges_to_tracks(cuda(s, torch.int32), cuda(d, torch.int32), cuda(logits),
+                                        float(thr), cuda(eo, torch.int32), st.hoff, min_hits=3)
+    st.ctx.sync()
+    np.testing.assert_array_equal(labels.cpu().numpy(), ref)
+    # tracks with >= 3 hits per event
+    for b in range(st.b.n_events):
+        lo, hi = st.b.hit_offsets[b], st.b.hit_offsets[b + 1]
+        sizes = np.bincount(ref[lo:hi], minlength=hi - lo)
+        assert int(nt[b].item()) == int((sizes >= 3).sum())
+
+
+def test_cc_golden_graphs_on_gpu(etx):
+    import json
+    from pathlib import Path
+    cases = json.loads((Path(__file__).parent / "golden" / "wcc_graphs.json").read_text())["cases"]
+    model = WORKLOADS["plain"].model
+    ctx = etx.Context(model, 8, 64, 64)
+    for c in cases:
+        logits = np.where(np.array(c["mask"]) > 0, 1.0, -1.0).astype(np.float32)
+        hoff = np.array(c["hit_offsets"], np.int32)
+        eo = np.array([0] * (len(hoff) - 1) + [len(c["src"])], np.int32)
+        labels, _ = ctx.edges_to_tracks(cuda(np.array(c["src"], np.int32)),
+                                        cuda(np.array(c["dst"], np.int32)), cuda(logits), 0.0,
+                                        cuda(eo), cuda(hoff))
+        ctx.sync()
+        assert labels.cpu().tolist() == c["labels"], c["name"]
+
+
+# ---------------------------------------------------------------------------
+# whole pipeline and host-side errors
+# ---------------------------------------------------------------------------
+def test_pipeline_end_to_end_labels(etx):
+    st = setup_for(etx, "batch500", 3, perturb=0.0)
+    thr = st.model.threshold_logit
+    emb64 = st.oracle_emb()
+    s, d, _ = O.build_graph(emb64, st.b.plane, st.b.hit_offsets, st.model.radius, st.model.k_max)
+    z = O.gnn_forward(st.W, st.model.n_iters, st.b.x, st.b.y, st.b.z, s, d)
+    ref = O.connected_components(s, d, z > thr, st.b.hit_offsets)
+    emb = st.ctx.embed(st.x, st.y, st.z)
+    src, dst, eo = st.ctx.build_graph(emb, st.plane, st.hoff, st.model.radius, st.model.k_max)
+    logits = st.ctx.gnn_forward(st.x, st.y, st.z, src, dst, eo)
+    labels, _ = st.ctx.edges_to_tracks(src, dst, logits, thr, eo, st.hoff)
+    st.ctx.sync()
+    agree = float((labels.cpu().numpy() == ref).mean())
+    print(f"pipeline label agreement {agree:.6f}")
+    assert agree >= 0.99
+
+
+def test_host_argument_errors(etx):
+    st = setup_for(etx, "plain", 1)
+    emb = st.ctx.embed(st.x, st.y, st.z)
+    with pytest.raises(etx.EtxError) as ei:
+        st.ctx.build_graph(emb, st.plane, st.hoff, 1.0, 0)
+    assert ei.value.status == etx.ETX_ERR_ARG
+    big = cuda(np.array([0, 0, 0, st.b.n_hits], np.int32))
+    with pytest.raises(etx.EtxError) as ei:
+        st.ctx.build_graph(emb, st.plane, big, 1.0, 4)
+    assert ei.value.status == etx.ETX_ERR_CAPACITY
+    ctx2 = etx.Context(st.model, 1, 1000, 1000)
+    with pytest.raises(etx.EtxError) as ei:
+        ctx2.embed(st.x, st.y, st.z)
+    assert ei.value.status == etx.ETX_ERR_STATE
+    st.ctx.sync()
+
+
+def test_unsorted_planes_are_reported(etx):
+    st = setup_for(etx, "plain", 1)
+    emb = st.ctx.embed(st.x, st.y, st.z)
+    bad = st.b.plane.copy()[::-1].copy()
+    st.ctx.build_graph(emb, cuda(bad), st.hoff, st.model.radius, st.model.k_max)
+    with pytest.raises(etx.EtxError) as ei:
+        st.ctx.sync()
+    assert ei.value.status == etx.ETX_ERR_UNSORTED
+    st.ctx.sync()  # the error word was cleared
