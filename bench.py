@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0,
                    help="budget of the oracle CPU baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--events", type=int, default=None,
+                   help="use only the first N events of the workload (profiling captures)")
     return p.parse_args()
 
 
@@ -245,7 +247,7 @@ def run_ours(args):
 
     wl = WORKLOADS[args.workload]
     m = wl.model
-    batch = wl.batch()
+    batch = wl.batch(args.events)
     W = wl.weights()
     N, B = batch.n_hits, batch.n_events
     tf = TrackFinder(m, pack_blob(m, W), B, N, N * m.k_max, device=local, dtype=args.dtype)

@@ -153,13 +153,28 @@ def layer_norm(a, g, be):
     return n * g + be, n, rstd
 
 
-def mlp_block(X, w, prefix, cache=None):
-    """Lin -> LN -> ReLU -> Lin -> LN -> ReLU on rows of X."""
+def round_bf16(a):
+    """Round to BF16 as a tensor core operand is formed from an FP32 value:
+    first to FP32, then to the nearest BF16 (8 significand bits), ties to
+    even.  Returned as float64."""
+    u = np.asarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _identity(a):
+    return a
+
+
+def mlp_block(X, w, prefix, cache=None, op=_identity):
+    """Lin -> LN -> ReLU -> Lin -> LN -> ReLU on rows of X.  ``op`` is applied
+    to both operands of each matrix product (identity: exact FP64;
+    ``round_bf16``: the BF16-operand, wide-accumulator reading)."""
     f = lambda k: w[f"{prefix}.{k}"].astype(np.float64)
-    a1 = X @ f("W1").T + f("b1")
+    a1 = op(X) @ op(f("W1")).T + f("b1")
     y1, n1, s1 = layer_norm(a1, f("g1"), f("be1"))
     r1 = np.maximum(y1, 0.0)
-    a2 = r1 @ f("W2").T + f("b2")
+    a2 = op(r1) @ op(f("W2")).T + f("b2")
     y2, n2, s2 = layer_norm(a2, f("g2"), f("be2"))
     out = np.maximum(y2, 0.0)
     if cache is not None:
@@ -177,8 +192,15 @@ def messages(e, src, dst, n_nodes):
     return np.concatenate([m_out, m_in], axis=1)
 
 
-def gnn_forward(weights, n_iters, x, y, z, src, dst, cache=None):
-    """Edge logits [E] (float64) of the interaction network."""
+def gnn_forward(weights, n_iters, x, y, z, src, dst, cache=None, gemm="fp64"):
+    """Edge logits [E] (float64) of the interaction network.
+
+    gemm="bf16" reads the mixed-precision configuration: the operands of every
+    matrix product with a hidden-width input (edge encoder, node and edge
+    networks, first classifier layer) are rounded to BF16 and the products
+    accumulate exactly; the node encoder (3 inputs), LayerNorm, residual adds,
+    message sums and the last classifier dot product stay exact."""
+    op = {"fp64": _identity, "bf16": round_bf16}[gemm]
     src = np.asarray(src, np.int64)
     dst = np.asarray(dst, np.int64)
     N = np.asarray(x).shape[0]
@@ -186,13 +208,14 @@ def gnn_forward(weights, n_iters, x, y, z, src, dst, cache=None):
                               np.asarray(z, np.float64)], axis=1),
                     weights["gnn_mu"], weights["gnn_sigma"])
     h = mlp_block(xin, weights, "node_enc", cache)
-    e = mlp_block(np.concatenate([h[src], h[dst]], axis=1), weights, "edge_enc", cache)
+    e = mlp_block(np.concatenate([h[src], h[dst]], axis=1), weights, "edge_enc", cache, op)
     for k in range(n_iters):
         m = messages(e, src, dst, N)
-        h = h + mlp_block(np.concatenate([h, m], axis=1), weights, f"node{k}", cache)
-        e = e + mlp_block(np.concatenate([e, h[src], h[dst]], axis=1), weights, f"edge{k}", cache)
+        h = h + mlp_block(np.concatenate([h, m], axis=1), weights, f"node{k}", cache, op)
+        e = e + mlp_block(np.concatenate([e, h[src], h[dst]], axis=1), weights, f"edge{k}", cache,
+                          op)
     W1 = weights["cls.W1"].astype(np.float64)
-    a1 = e @ W1.T + weights["cls.b1"].astype(np.float64)
+    a1 = op(e) @ op(W1).T + weights["cls.b1"].astype(np.float64)
     y1, n1, s1 = layer_norm(a1, weights["cls.g1"].astype(np.float64),
                             weights["cls.be1"].astype(np.float64))
     r1 = np.maximum(y1, 0.0)

@@ -87,6 +87,32 @@ const char* config_problem(const etx_config* c) {
   return nullptr;
 }
 
+// Round to the nearest BF16, ties to even (NaN stays NaN).
+uint16_t f32_to_bf16(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7fffffffu) > 0x7f800000u) return static_cast<uint16_t>((u >> 16) | 0x40u);
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return static_cast<uint16_t>(u >> 16);
+}
+
+// Append the tensor-core image of W[n_out][k] (n_out == 128, k % 64 == 0): for
+// each 64-column chunk, 128 rows of 128 bytes with the 16-byte unit u of row n
+// stored at unit position u ^ (n % 8) -- the K-major 128-byte-swizzle layout.
+void append_bf16_image(const float* W, int n_out, int k, std::vector<uint8_t>& img) {
+  const size_t at = img.size();
+  img.resize(at + (size_t)n_out * k * 2);
+  for (int c = 0; c < k / 64; ++c)
+    for (int n = 0; n < n_out; ++n)
+      for (int u = 0; u < 8; ++u)
+        for (int j = 0; j < 8; ++j) {
+          const uint16_t b = f32_to_bf16(W[(size_t)n * k + 64 * c + 8 * u + j]);
+          const size_t off = at + (size_t)c * n_out * 128 + (size_t)n * 128 + ((u ^ (n & 7)) * 16) + 2 * j;
+          img[off] = static_cast<uint8_t>(b & 0xff);
+          img[off + 1] = static_cast<uint8_t>(b >> 8);
+        }
+}
+
 int64_t block_floats(int H, int K) { return (int64_t)H * K + 3 * H + (int64_t)H * H + 3 * H; }
 
 template <class T>
@@ -178,7 +204,7 @@ etx_status etx_ctx_create(const etx_config* cfg, int32_t device, etx_ctx** out) 
 etx_status etx_ctx_destroy(etx_ctx* ctx) {
   if (!ctx) return ETX_OK;
   cudaSetDevice(ctx->device);
-  void* bufs[] = {ctx->d_err, ctx->n_edges, ctx->w_dev, ctx->blob_dev, ctx->plane_off,
+  void* bufs[] = {ctx->d_err, ctx->n_edges, ctx->w_dev, ctx->blob_dev, ctx->w_tc, ctx->plane_off,
                   ctx->hit_cnt, ctx->scan_tmp, ctx->out_off, ctx->in_off, ctx->in_cnt,
                   ctx->perm_in, ctx->h, ctx->m, ctx->e, ctx->parent};
   for (void* p : bufs)
@@ -237,7 +263,7 @@ etx_status etx_load_weights(etx_ctx* ctx, const float* blob, int64_t n_floats) {
   std::vector<float> dev;
   dev.reserve((size_t)n_floats * 2);
   const float* p = blob;
-  struct Pending { size_t wt, b; int k_in, k_pad, n; };
+  struct Pending { size_t wt, b; int k_in, k_pad, n; const float* w; };
   // every array starts on a 16-byte boundary (float4 loads of W^T chunks)
   auto align4 = [&]() { while (dev.size() % 4) dev.push_back(0.f); };
   auto push_lin = [&](int n_out, int k_in) {
@@ -246,6 +272,7 @@ etx_status etx_load_weights(etx_ctx* ctx, const float* blob, int64_t n_floats) {
     q.k_in = k_in;
     q.k_pad = k_in <= 4 ? 4 : k_in;
     q.n = n_out;
+    q.w = p;
     q.wt = dev.size();
     dev.resize(dev.size() + (size_t)q.k_pad * n_out, 0.f);
     for (int o = 0; o < n_out; ++o)
@@ -298,6 +325,29 @@ etx_status etx_load_weights(etx_ctx* ctx, const float* blob, int64_t n_floats) {
     e = cudaMemcpy(ctx->blob_dev, blob, (size_t)n_floats * sizeof(float), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "weight upload");
   ctx->w_dev_floats = dev.size();
+  // --- BF16 tensor-core operand images (hidden == 128) ------------------------
+  if (ctx->w_tc) cudaFree(ctx->w_tc);
+  ctx->w_tc = nullptr;
+  std::vector<size_t> tc_off;
+  if (H == 128) {
+    std::vector<uint8_t> img;
+    auto push_img = [&](const Pending& q) {
+      tc_off.push_back(img.size());
+      append_bf16_image(q.w, q.n, q.k_in, img);
+    };
+    push_img(edge_enc.l1);
+    push_img(edge_enc.l2);
+    for (int k = 0; k < c.n_iters; ++k) {
+      push_img(node[k].l1);
+      push_img(node[k].l2);
+      push_img(edge[k].l1);
+      push_img(edge[k].l2);
+    }
+    push_img(cl1);
+    if (dmalloc(ctx, &ctx->w_tc, img.size(), "tensor-core weights") != ETX_OK) return ETX_ERR_CUDA;
+    e = cudaMemcpy(ctx->w_tc, img.data(), img.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-core weight upload");
+  }
   float* base = ctx->w_dev;
   auto lin = [&](const Pending& q) {
     LinF32 l;
@@ -330,6 +380,23 @@ etx_status etx_load_weights(etx_ctx* ctx, const float* blob, int64_t n_floats) {
   ctx->w.cls.be1 = base + cbe1;
   ctx->w.cls.w2 = base + cw2;
   ctx->w.cls.b2 = base + cb2;
+  if (H == 128) {
+    size_t i = 0;
+    auto next = [&]() { return ctx->w_tc + tc_off[i++]; };
+    ctx->w.edge_enc_tc.w1 = next();
+    ctx->w.edge_enc_tc.w2 = next();
+    for (int k = 0; k < c.n_iters; ++k) {
+      BlockTC nb, eb;
+      nb.w1 = next();
+      nb.w2 = next();
+      eb.w1 = next();
+      eb.w2 = next();
+      ctx->w.node_tc.push_back(nb);
+      ctx->w.edge_tc.push_back(eb);
+    }
+    ctx->w.cls_tc.w1 = next();
+    ctx->w.has_tc = true;
+  }
   ctx->weights_loaded = true;
   return ETX_OK;
 }
@@ -397,7 +464,9 @@ etx_status etx_gnn_forward(etx_ctx* ctx, const float* x, const float* y, const f
   if (n_hits < 0 || n_hits > ctx->cfg.max_hits) return fail(ctx, ETX_ERR_CAPACITY, "n_hits exceeds the context capacity");
   if (!edge_offsets || !src || !dst || !logits) return fail(ctx, ETX_ERR_ARG, "NULL edge array");
   if (n_hits > 0 && (!x || !y || !z)) return fail(ctx, ETX_ERR_ARG, "NULL hit array");
-  if (dtype != ETX_F32) return fail(ctx, ETX_ERR_UNSUPPORTED, "dtype not built yet");
+  if (dtype != ETX_F32 && dtype != ETX_BF16) return fail(ctx, ETX_ERR_UNSUPPORTED, "dtype not built yet");
+  if (dtype == ETX_BF16 && !ctx->w.has_tc)
+    return fail(ctx, ETX_ERR_UNSUPPORTED, "the tensor-core path needs hidden == 128");
   if (n_hits == 0) return ETX_OK;  // no hits, hence no edges: nothing to compute
   cudaSetDevice(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
@@ -405,7 +474,7 @@ etx_status etx_gnn_forward(etx_ctx* ctx, const float* x, const float* y, const f
          ctx->n_edges, ctx->d_err);
   cudaError_t e = launch_edge_index(ctx, n_hits, src, dst, ctx->n_edges, s);
   if (e == cudaSuccess)
-    e = launch_gnn_forward_f32(ctx, x, y, z, n_hits, src, dst, ctx->n_edges, logits, s);
+    e = launch_gnn_forward(ctx, x, y, z, n_hits, src, dst, ctx->n_edges, logits, dtype == ETX_BF16, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "etx_gnn_forward launch");
   return ETX_OK;
 }

@@ -45,11 +45,12 @@ struct ClassifierF32 {
   const float* b2 = nullptr;  // [1]
 };
 
-// BF16 copy of one Linear, PyTorch layout W[n][k] (k contiguous), for the
-// tensor-core path.
-struct LinBF16 {
-  const uint16_t* w = nullptr;
-  int k = 0, n = 0;
+// Tensor-core copies of a block's two Linear weights: BF16, W[n][k] split in
+// 64-column chunks of 128 rows x 128 bytes, each laid out exactly as the
+// K-major 128-byte-swizzle shared-memory operand (16 KB per chunk).
+struct BlockTC {
+  const uint8_t* w1 = nullptr;
+  const uint8_t* w2 = nullptr;
 };
 
 struct Weights {
@@ -58,6 +59,9 @@ struct Weights {
   BlockF32 node_enc, edge_enc;
   std::vector<BlockF32> node, edge;
   ClassifierF32 cls;
+  bool has_tc = false;          // BF16 images exist (hidden == 128)
+  BlockTC edge_enc_tc, cls_tc;
+  std::vector<BlockTC> node_tc, edge_tc;
 };
 
 }  // namespace etx
@@ -83,6 +87,7 @@ struct etx_ctx {
   float* w_dev = nullptr;   // repacked FP32 weights
   size_t w_dev_floats = 0;
   float* blob_dev = nullptr;  // raw blob copy (float32) for the backward pass
+  uint8_t* w_tc = nullptr;    // BF16 operand images of the interaction network
   etx::Weights w;
 
   // graph scratch
@@ -129,11 +134,21 @@ cudaError_t launch_build_graph(etx_ctx* ctx, const float* emb, const int8_t* pla
                                int64_t edge_capacity, int32_t* edge_offsets, cudaStream_t s);
 
 // gnn_f32.cu
-cudaError_t launch_gnn_forward_f32(etx_ctx* ctx, const float* x, const float* y, const float* z,
-                                   int64_t n_hits, const int32_t* src, const int32_t* dst,
-                                   const int32_t* n_edges_dev, float* logits, cudaStream_t s);
+// tc: BF16 tensor-core MLP blocks (hidden == 128), else FP32 SIMT
+cudaError_t launch_gnn_forward(etx_ctx* ctx, const float* x, const float* y, const float* z,
+                               int64_t n_hits, const int32_t* src, const int32_t* dst,
+                               const int32_t* n_edges_dev, float* logits, bool tc, cudaStream_t s);
 cudaError_t launch_edge_index(etx_ctx* ctx, int64_t n_hits, const int32_t* src,
                               const int32_t* dst, const int32_t* n_edges_dev, cudaStream_t s);
+
+// gnn_tc.cu (hidden == 128 only)
+cudaError_t launch_edge_encoder_tc(etx_ctx* ctx, int64_t N, const int32_t* src, const int32_t* dst,
+                                   const int32_t* n_edges_dev, cudaStream_t s);
+cudaError_t launch_node_update_tc(etx_ctx* ctx, int k, int64_t N, cudaStream_t s);
+cudaError_t launch_edge_update_tc(etx_ctx* ctx, int k, int64_t N, const int32_t* src,
+                                  const int32_t* dst, const int32_t* n_edges_dev, cudaStream_t s);
+cudaError_t launch_classifier_tc(etx_ctx* ctx, int64_t N, const int32_t* n_edges_dev, float* logits,
+                                 cudaStream_t s);
 
 // cc.cu
 cudaError_t launch_edges_to_tracks(etx_ctx* ctx, const int32_t* src, const int32_t* dst,

@@ -272,7 +272,7 @@ void launch_mlp(etx_ctx* ctx, const MlpArgs& a, int64_t max_rows, cudaStream_t s
 template <int H>
 cudaError_t forward(etx_ctx* ctx, const float* x, const float* y, const float* z, int64_t N,
                     const int32_t* src, const int32_t* dst, const int32_t* n_edges_dev,
-                    float* logits, cudaStream_t s) {
+                    float* logits, bool tc, cudaStream_t s) {
   const int64_t Ecap = ctx->cfg.max_edges;
   MlpArgs a{};
   a.n_rows = N;
@@ -281,25 +281,42 @@ cudaError_t forward(etx_ctx* ctx, const float* x, const float* y, const float* z
   a.norm = ctx->w.norm + 6;
   a.src = src; a.dst = dst;
   a.h = ctx->h; a.m = ctx->m; a.e = ctx->e; a.h_out = ctx->h; a.logits = logits;
+  cudaError_t e = cudaSuccess;
+  auto chain = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
 
+  // the node encoder (K = 3) always runs on the FP32 SIMT path
   a.blk = ctx->w.node_enc;
   launch_mlp<H, NODE_ENC>(ctx, a, N, s);
-  a.blk = ctx->w.edge_enc;
-  launch_mlp<H, EDGE_ENC>(ctx, a, Ecap, s);
+  if (tc) {
+    chain(launch_edge_encoder_tc(ctx, N, src, dst, n_edges_dev, s));
+  } else {
+    a.blk = ctx->w.edge_enc;
+    launch_mlp<H, EDGE_ENC>(ctx, a, Ecap, s);
+  }
   const int msg_grid = grid_for(ctx, (const void*)k_messages<H>, 256, 0,
                                 (N + (256 / 32) * (32 / (H / 4)) - 1) / ((256 / 32) * (32 / (H / 4))));
   for (int k = 0; k < ctx->cfg.n_iters; ++k) {
     if (N > 0)
       launch(ctx, "gnn_messages", k_messages<H>, msg_grid, 256, 0, s, ctx->e, ctx->out_off,
              ctx->in_off, ctx->perm_in, n_edges_dev, (int)N, ctx->m);
-    a.blk = ctx->w.node[k];
-    launch_mlp<H, NODE_UPD>(ctx, a, N, s);
-    a.blk = ctx->w.edge[k];
-    launch_mlp<H, EDGE_UPD>(ctx, a, Ecap, s);
+    if (tc) {
+      chain(launch_node_update_tc(ctx, k, N, s));
+      chain(launch_edge_update_tc(ctx, k, N, src, dst, n_edges_dev, s));
+    } else {
+      a.blk = ctx->w.node[k];
+      launch_mlp<H, NODE_UPD>(ctx, a, N, s);
+      a.blk = ctx->w.edge[k];
+      launch_mlp<H, EDGE_UPD>(ctx, a, Ecap, s);
+    }
   }
-  a.cls = ctx->w.cls;
-  launch_mlp<H, CLS>(ctx, a, Ecap, s);
-  return cudaGetLastError();
+  if (tc) {
+    chain(launch_classifier_tc(ctx, N, n_edges_dev, logits, s));
+  } else {
+    a.cls = ctx->w.cls;
+    launch_mlp<H, CLS>(ctx, a, Ecap, s);
+  }
+  chain(cudaGetLastError());
+  return e;
 }
 
 }  // namespace
@@ -323,14 +340,14 @@ cudaError_t launch_edge_index(etx_ctx* ctx, int64_t N, const int32_t* src, const
   return cudaGetLastError();
 }
 
-cudaError_t launch_gnn_forward_f32(etx_ctx* ctx, const float* x, const float* y, const float* z,
-                                   int64_t n_hits, const int32_t* src, const int32_t* dst,
-                                   const int32_t* n_edges_dev, float* logits, cudaStream_t s) {
+cudaError_t launch_gnn_forward(etx_ctx* ctx, const float* x, const float* y, const float* z,
+                               int64_t n_hits, const int32_t* src, const int32_t* dst,
+                               const int32_t* n_edges_dev, float* logits, bool tc, cudaStream_t s) {
   switch (ctx->cfg.hidden) {
-    case 16: return forward<16>(ctx, x, y, z, n_hits, src, dst, n_edges_dev, logits, s);
-    case 32: return forward<32>(ctx, x, y, z, n_hits, src, dst, n_edges_dev, logits, s);
-    case 64: return forward<64>(ctx, x, y, z, n_hits, src, dst, n_edges_dev, logits, s);
-    case 128: return forward<128>(ctx, x, y, z, n_hits, src, dst, n_edges_dev, logits, s);
+    case 16: return forward<16>(ctx, x, y, z, n_hits, src, dst, n_edges_dev, logits, false, s);
+    case 32: return forward<32>(ctx, x, y, z, n_hits, src, dst, n_edges_dev, logits, false, s);
+    case 64: return forward<64>(ctx, x, y, z, n_hits, src, dst, n_edges_dev, logits, false, s);
+    case 128: return forward<128>(ctx, x, y, z, n_hits, src, dst, n_edges_dev, logits, tc, s);
     default: return cudaErrorInvalidValue;
   }
 }

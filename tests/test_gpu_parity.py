@@ -356,3 +356,28 @@ def test_unsorted_planes_are_reported(etx):
         st.ctx.sync()
     assert ei.value.status == etx.ETX_ERR_UNSORTED
     st.ctx.sync()  # the error word was cleared
+
+
+# ---------------------------------------------------------------------------
+# tensor-core (BF16 operand) interaction network
+# ---------------------------------------------------------------------------
+BF16_TOL = 2e-2   # vs the oracle's BF16-operand reading (max-abs)
+
+
+@pytest.mark.parametrize("n_events", [1, 3])
+def test_gnn_forward_bf16_tensor_cores(etx, n_events):
+    st = setup_for(etx, "batch500", n_events)
+    emb64 = st.oracle_emb()
+    s, d, eo = O.build_graph(emb64, st.b.plane, st.b.hit_offsets, st.model.radius, st.model.k_max)
+    args = (st.W, st.model.n_iters, st.b.x, st.b.y, st.b.z, s, d)
+    ref64 = O.gnn_forward(*args)
+    ref16 = O.gnn_forward(*args, gemm="bf16")
+    logits = st.ctx.gnn_forward(st.x, st.y, st.z, cuda(s, torch.int32), cuda(d, torch.int32),
+                                cuda(eo, torch.int32), dtype="bf16")
+    st.ctx.sync()
+    got = logits.cpu().numpy().astype(np.float64)
+    e16, e64 = np.abs(got - ref16), np.abs(got - ref64)
+    print(f"bf16 E={s.size}: max|err| vs bf16 reading {e16.max():.3e} (mean {e16.mean():.2e}), "
+          f"vs fp64 {e64.max():.3e} (mean {e64.mean():.2e}), oracle bf16-vs-fp64 "
+          f"{np.abs(ref16 - ref64).max():.3e}")
+    assert e16.max() <= BF16_TOL

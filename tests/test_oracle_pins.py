@@ -468,3 +468,32 @@ def test_generator_geometry():
         assert np.ptp(np.unwrap(ph)) < 0.01
     assert concat_events([]).n_hits == 0
     assert math.isclose(float(np.diff(b.hit_offsets).mean()), 1700, rel_tol=0.5)
+
+
+# ---------------------------------------------------------------------------
+# BF16 operand reading of the mixed-precision configuration
+# ---------------------------------------------------------------------------
+def test_round_bf16_closed_forms():
+    one = 1.0
+    cases = [(one, one), (one + 2 ** -8, one),                 # tie -> even (down)
+             (one + 3 * 2 ** -8, one + 2 ** -6),               # tie -> even (up)
+             (one + 2 ** -8 + 2 ** -20, one + 2 ** -7),        # above the tie
+             (-(one + 2 ** -9), -one), (0.0, 0.0), (2.0 ** -130, 2.0 ** -130)]
+    for x, want in cases:
+        assert O.round_bf16(np.array([x]))[0] == want, x
+
+
+def test_round_bf16_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(8)
+    a = (rng.normal(size=4000) * np.exp(rng.uniform(-20, 20, 4000))).astype(np.float32)
+    ref = torch.from_numpy(a).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(O.round_bf16(a), ref)
+
+
+def test_gnn_bf16_reading_is_close_to_exact():
+    cfg, b, W, s, d, _ = small_problem(H=16, L=2, n_events=1)
+    z64 = O.gnn_forward(W, cfg.n_iters, b.x, b.y, b.z, s, d)
+    z16 = O.gnn_forward(W, cfg.n_iters, b.x, b.y, b.z, s, d, gemm="bf16")
+    err = np.abs(z16 - z64).max()
+    assert 0 < err < 0.1   # rounding operands to 8 significand bits moves the logits a little
