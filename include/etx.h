@@ -181,6 +181,36 @@ etx_status etx_edges_to_tracks(etx_ctx* ctx, const int32_t* src, const int32_t* 
                                int32_t* labels, int32_t* n_tracks, void* stream);
 
 /*
+ * Allocation-free components (the paper has no counterpart to this call).
+ *
+ * Same result as etx_edges_to_tracks, but the call needs no context and
+ * never allocates device memory: no cudaMalloc, no cudaFree, no allocating
+ * library routine.  It is meant for callers that cannot allocate, such as a
+ * host framework that reserves the whole device-memory budget at start-up
+ * and hands out slices itself, or a real-time event loop where an
+ * allocation (which can synchronise the device) is not allowed.  The caller
+ * still passes every input and output array, as for etx_edges_to_tracks.
+ *
+ * Scratch: a file-scope device array of the library holding 2^21 hit slots
+ * (8 MiB plus an error word), present on every GPU that loads the library
+ * until the process exits.  n_hits above 2^21 returns ETX_ERR_CAPACITY
+ * before anything is launched.  The first call on a device looks the
+ * array's device address up (cudaGetSymbolAddress, on the current device)
+ * and caches it, so make that first call before any stream capture.  Every
+ * call re-initialises the part of the array it uses, but all calls share
+ * it: calls that overlap on the GPU (different streams or devices sharing a
+ * context's memory) race and give wrong labels.  Runs on the current device
+ * and the given stream; asynchronous.  The union-find loops carry the same
+ * iteration caps as etx_edges_to_tracks, but this call has no context to
+ * report a cap being hit; valid input does not come near them.
+ */
+etx_status etx_edges_to_tracks_noalloc(const int32_t* src, const int32_t* dst,
+                                       const float* logits, float threshold_logit,
+                                       const int32_t* edge_offsets, const int32_t* hit_offsets,
+                                       int32_t n_events, int64_t n_hits, int32_t min_hits,
+                                       int32_t* labels, int32_t* n_tracks, void* stream);
+
+/*
  * Instrumentation (no counterpart in the paper; used by the benchmark).
  *   etx_launch_count    number of kernels this context has launched so far.
  *   etx_profile_enable  when on, every kernel launch is bracketed by a CUDA

@@ -131,3 +131,84 @@ cudaError_t launch_edges_to_tracks(etx_ctx* ctx, const int32_t* src, const int32
 }
 
 }  // namespace etx
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of etx_edges_to_tracks (see include/etx.h).
+//
+// Its scratch (the union-find parents, reused as per-root size counters, plus
+// an error word) is the file-scope array below: every GPU that loads the
+// library holds it until the process exits.  Host code cannot use the
+// array's name as a device address, so the first call on each device looks
+// the address up with cudaGetSymbolAddress (that device current) and caches
+// it; later calls only launch kernels.  Calls that overlap on the GPU share
+// the array and race.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+constexpr int64_t kNoAllocMaxHits = int64_t(1) << 21;  // 2,097,152 hits, 8 MiB of scratch
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+int32_t* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+int g_noalloc_sms[kNoAllocMaxDevices] = {};
+}  // namespace
+
+static __device__ __align__(256) int32_t g_cc_scratch[kNoAllocMaxHits + 64];
+
+extern "C" etx_status etx_edges_to_tracks_noalloc(const int32_t* src, const int32_t* dst,
+                                                  const float* logits, float threshold_logit,
+                                                  const int32_t* edge_offsets,
+                                                  const int32_t* hit_offsets, int32_t n_events,
+                                                  int64_t n_hits, int32_t min_hits,
+                                                  int32_t* labels, int32_t* n_tracks,
+                                                  void* stream) {
+  using namespace etx;
+  if (n_events < 0 || n_hits < 0) return ETX_ERR_ARG;
+  if (n_hits > kNoAllocMaxHits) return ETX_ERR_CAPACITY;
+  if (!edge_offsets || !hit_offsets || !src || !dst || !logits) return ETX_ERR_ARG;
+  if (n_hits > 0 && (!labels || n_events == 0)) return ETX_ERR_ARG;
+  if (threshold_logit != threshold_logit) return ETX_ERR_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return ETX_ERR_CUDA;
+  int32_t* scratch;
+  int sms;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_cc_scratch) != cudaSuccess || !p) return ETX_ERR_CUDA;
+      int n = 0;
+      if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return ETX_ERR_CUDA;
+      g_noalloc_sms[dev] = n > 0 ? n : 1;
+      g_noalloc_ptr[dev] = static_cast<int32_t*>(p);
+    }
+    scratch = g_noalloc_ptr[dev];
+    sms = g_noalloc_sms[dev];
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (n_hits == 0) {
+    if (n_tracks && n_events > 0 &&
+        cudaMemsetAsync(n_tracks, 0, (size_t)n_events * sizeof(int32_t), s) != cudaSuccess)
+      return ETX_ERR_CUDA;
+    return ETX_OK;
+  }
+  int32_t* parent = scratch;
+  int* err = scratch + kNoAllocMaxHits;
+  const int64_t cap = (int64_t)sms * 8;
+  const int64_t hb = (n_hits + 255) / 256;
+  const unsigned gh = (unsigned)(hb < cap ? hb : cap);
+  k_init<<<gh, 256, 0, s>>>(parent, n_hits);
+  // the edge count is read on the device from edge_offsets[n_events]
+  k_union<<<(unsigned)cap, 256, 0, s>>>(src, dst, logits, threshold_logit, edge_offsets + n_events,
+                                        (int)n_hits, parent, err);
+  k_labels<<<gh, 256, 0, s>>>(parent, hit_offsets, n_events, n_hits, labels, err);
+  if (n_tracks) {
+    if (cudaMemsetAsync(n_tracks, 0, (size_t)n_events * sizeof(int32_t), s) != cudaSuccess)
+      return ETX_ERR_CUDA;
+    if (cudaMemsetAsync(parent, 0, (size_t)n_hits * sizeof(int32_t), s) != cudaSuccess)
+      return ETX_ERR_CUDA;
+    k_count_tracks<<<gh, 256, 0, s>>>(labels, hit_offsets, n_events, n_hits,
+                                      min_hits < 1 ? 1 : min_hits, parent, n_tracks);
+  }
+  return cudaGetLastError() == cudaSuccess ? ETX_OK : ETX_ERR_CUDA;
+}

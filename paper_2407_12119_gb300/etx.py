@@ -27,7 +27,8 @@ MAX_EMB_LAYERS = 8
 EXPORTED = ["etx_ctx_create", "etx_ctx_destroy", "etx_last_error", "etx_weights_size",
             "etx_load_weights", "etx_ctx_sync", "etx_embed", "etx_build_graph",
             "etx_gnn_forward", "etx_gnn_param_count", "etx_gnn_backward",
-            "etx_edges_to_tracks", "etx_launch_count", "etx_profile_enable", "etx_profile_read"]
+            "etx_edges_to_tracks", "etx_edges_to_tracks_noalloc", "etx_launch_count",
+            "etx_profile_enable", "etx_profile_read"]
 
 
 class EtxConfig(ctypes.Structure):
@@ -76,6 +77,7 @@ def lib() -> ctypes.CDLL:
         "etx_gnn_forward": (i32, [vp, vp, vp, vp, i64, vp, vp, vp, i32, i32, vp, vp]),
         "etx_gnn_backward": (i32, [vp, vp, vp, vp]),
         "etx_edges_to_tracks": (i32, [vp, vp, vp, vp, f32, vp, vp, i32, i64, i32, vp, vp, vp]),
+        "etx_edges_to_tracks_noalloc": (i32, [vp, vp, vp, f32, vp, vp, i32, i64, i32, vp, vp, vp]),
         "etx_launch_count": (i64, [vp]),
         "etx_profile_enable": (i32, [vp, i32]),
         "etx_profile_read": (i32, [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
@@ -133,6 +135,32 @@ def _need(t, dtype, name, device):
         raise ValueError(f"{name} must be on {device}, got {t.device}")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
+
+
+NOALLOC_MAX_HITS = 1 << 21
+
+
+def edges_to_tracks_noalloc(src, dst, logits, threshold_logit: float, edge_offsets, hit_offsets,
+                            labels, n_tracks=None, min_hits: int = 3, stream=None):
+    """etx_edges_to_tracks_noalloc: the components step without a context and
+    without any device allocation (its scratch is a fixed array inside the
+    library, at most NOALLOC_MAX_HITS hits).  Every array is caller-owned."""
+    dev = labels.device
+    _need(src, torch.int32, "src", dev)
+    _need(dst, torch.int32, "dst", dev)
+    _need(logits, torch.float32, "logits", dev)
+    _need(edge_offsets, torch.int32, "edge_offsets", dev)
+    _need(hit_offsets, torch.int32, "hit_offsets", dev)
+    _need(labels, torch.int32, "labels", dev)
+    if n_tracks is not None:
+        _need(n_tracks, torch.int32, "n_tracks", dev)
+    st = lib().etx_edges_to_tracks_noalloc(_ptr(src), _ptr(dst), _ptr(logits), float(threshold_logit),
+                                           _ptr(edge_offsets), _ptr(hit_offsets),
+                                           hit_offsets.shape[0] - 1, labels.shape[0], int(min_hits),
+                                           _ptr(labels), _ptr(n_tracks), _stream(stream))
+    if st != ETX_OK:
+        raise EtxError(st, "etx_edges_to_tracks_noalloc failed")
+    return labels, n_tracks
 
 
 class Context:

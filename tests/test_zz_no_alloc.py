@@ -1,0 +1,75 @@
+"""The allocation-free components call (etx_edges_to_tracks_noalloc).
+
+Some callers cannot allocate device memory: a host framework that owns the
+whole device budget, or a real-time loop where an allocation is not allowed.
+For them the library has one entry point whose scratch is a fixed array
+inside the library.  This file checks, on the GPU and through the C ABI,
+that it gives exactly the labels and track counts of the regular
+etx_edges_to_tracks on two calls in a row with different inputs (so nothing
+left in the shared array from the first call leaks into the second), and
+that it refuses sizes above its limit.  It is collected last on purpose.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import etx_oracle as O
+from velo_synth import WORKLOADS, make_batch, make_weights
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def etx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2407_12119_gb300 import build as b
+    b.build()
+    from paper_2407_12119_gb300 import etx as m
+    return m
+
+
+def _graph(name, n_events, seed):
+    wl = WORKLOADS[name]
+    b = make_batch(wl.recipe, n_events, wl.base_seed + seed)
+    W = make_weights(wl.model, b, perturb=0.2)
+    emb = O.embed(W, len(wl.model.emb_widths) - 1, b.x, b.y, b.z)
+    s, d, eo = O.build_graph(emb, b.plane, b.hit_offsets, wl.model.radius, wl.model.k_max)
+    return wl.model, b, s, d, eo
+
+
+def test_noalloc_matches_regular_entry_point_twice(etx):
+    dev = torch.device("cuda", 0)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    results = []
+    for call, (name, n, seed, q) in enumerate([("batch500", 3, 7, 0.9), ("plain", 2, 3, 0.5)]):
+        model, b, s, d, eo = _graph(name, n, seed)
+        rng = np.random.default_rng(call)
+        logits = rng.normal(size=s.size).astype(np.float32)
+        thr = float(np.quantile(logits, q))
+        args = (t(s.astype(np.int32)), t(d.astype(np.int32)), t(logits))
+        eo_t, ho_t = t(eo.astype(np.int32)), t(b.hit_offsets)
+        ctx = etx.Context(model, b.n_events, b.n_hits, max(s.size, 1))
+        ref_l, ref_n = ctx.edges_to_tracks(*args, thr, eo_t, ho_t, min_hits=3)
+        lab = torch.full((b.n_hits,), -7, dtype=torch.int32, device=dev)
+        nt = torch.full((b.n_events,), -7, dtype=torch.int32, device=dev)
+        etx.edges_to_tracks_noalloc(*args, thr, eo_t, ho_t, lab, nt, min_hits=3)
+        torch.cuda.synchronize()
+        ctx.sync()
+        np.testing.assert_array_equal(lab.cpu().numpy(), ref_l.cpu().numpy())
+        np.testing.assert_array_equal(nt.cpu().numpy(), ref_n[:b.n_events].cpu().numpy())
+        results.append(int((lab.cpu().numpy() == np.arange(b.n_hits) - np.repeat(
+            b.hit_offsets[:-1], np.diff(b.hit_offsets))).sum()))
+    assert all(r > 0 for r in results)
+
+
+def test_noalloc_rejects_sizes_above_its_limit(etx):
+    dev = torch.device("cuda", 0)
+    z = torch.zeros(1, dtype=torch.int32, device=dev)
+    f = torch.zeros(1, dtype=torch.float32, device=dev)
+    L = etx.lib()
+    import ctypes
+    st = L.etx_edges_to_tracks_noalloc(etx._ptr(z), etx._ptr(z), etx._ptr(f), 0.0, etx._ptr(z),
+                                       etx._ptr(z), 1, etx.NOALLOC_MAX_HITS + 1, 3, etx._ptr(z),
+                                       None, ctypes.c_void_p(0))
+    assert st == etx.ETX_ERR_CAPACITY
