@@ -1,22 +1,27 @@
 // Interaction-network MLP blocks on the 5th-generation tensor cores
 // (tcgen05, BF16 operands, FP32 accumulation in tensor memory).
 //
-// One persistent CTA per SM (256 threads) walks 128-row tiles.  For a tile:
-//   1. the block input rows ([h_i, h_j], [h, m_out, m_in], [e, h_i, h_j] or e)
-//      are gathered from the FP32 streams, rounded to BF16 and written into
-//      shared memory in the K-major 128-byte-swizzle layout, 64 columns at a
-//      time through a two-slot ring; one thread issues the tcgen05.mma for a
-//      chunk as soon as it lands while the CTA gathers the next one;
-//   2. the 128 x 128 FP32 accumulator is read back from tensor memory
-//      (tcgen05.ld; warp w owns TMEM lanes 32(w%4).. and half of the columns),
-//      bias + LayerNorm + ReLU are applied in registers and the result is
-//      written back to shared memory as the BF16 A operand of the second
-//      Linear;
-//   3. the second GEMM accumulates into another 128 TMEM columns, and its
-//      epilogue applies bias + LayerNorm + ReLU, adds the FP32 residual and
-//      stores FP32 rows.  The classifier instead ends in a dot product.
-// The weights of the block stay resident in shared memory (pre-swizzled BF16
-// images copied with one bulk async copy per 16 KB).  All waits are bounded.
+// Persistent kernel, one CTA per SM, 416 threads in three roles that run
+// concurrently over the CTA's 128-row tiles:
+//   warps 4-11 producers: gather the block's input rows ([h_i, h_j],
+//              [h, m_out, m_in], [e, h_i, h_j] or e) from the FP32 streams,
+//              round them to BF16 and write them, 64 columns at a time, into a
+//              3-slot ring in the K-major 128-byte-swizzle layout; coalesced
+//              (8 threads per 256-byte row segment) and two chunks prefetched
+//              in registers;
+//   warp 12    MMA issuer (one thread): tcgen05.mma of each ring slot into the
+//              tile's first accumulator (two TMEM buffers, so the next tile's
+//              first GEMM runs while the epilogue reads this one), then the
+//              second GEMM of the previous tile from the epilogue's BF16
+//              activations;
+//   warps 0-3  epilogue, one row per thread (TMEM lane = row): bias +
+//              LayerNorm + ReLU of the first GEMM into the BF16 operand of the
+//              second, then bias + LayerNorm + ReLU + FP32 residual and the
+//              row store (or the classifier's dot product).
+// Stages hand over through mbarriers (transaction-counted bulk copies for
+// the resident BF16 weights, tcgen05.commit for MMA completion, thread
+// arrivals otherwise).  Every wait is bounded; a timeout records
+// ETX_ERR_TIMEOUT, raises a shared abort flag and every role stops.
 #include <cuda_bf16.h>
 
 #include "sm100.cuh"
@@ -27,14 +32,24 @@ namespace {
 using namespace sm100;
 
 constexpr int H = 128;
-constexpr int TM = 128;                    // rows per tile
-constexpr int KCH = 64;                    // K columns per shared-memory chunk
-constexpr int CHUNK = TM * KCH * 2;        // 16 KB per BF16 chunk (A or B)
-constexpr int THREADS = 256;
+constexpr int TM = 128;                  // rows per tile
+constexpr int KCH = 64;                  // K columns per shared-memory chunk
+constexpr int CHUNK = TM * KCH * 2;      // 16 KB per BF16 chunk
+constexpr int NSTAGE = 3;                // A-operand ring slots
+constexpr int EPI_WARPS = 4, PROD_WARPS = 8;
+constexpr int MMA_WARP = EPI_WARPS + PROD_WARPS;
+constexpr int THREADS = 32 * (MMA_WARP + 1);  // 416
+constexpr int PROD_THREADS = 32 * PROD_WARPS;
+constexpr int EPI_THREADS = 32 * EPI_WARPS;
 constexpr uint32_t IDESC = idesc_bf16_f32<TM, H>();
-constexpr uint32_t TMEM_COLS = 256;        // D1 at column 0, D2 at column 128
+constexpr uint32_t TMEM_COLS = 512;      // D1 buffers at columns 0 and 128, D2 at 256
 
 enum TcMode { TC_EDGE_ENC = 0, TC_NODE_UPD = 1, TC_EDGE_UPD = 2, TC_CLS = 3 };
+
+// barrier indices
+enum { B_W = 0, B_FULL = 1, B_EMPTY = B_FULL + NSTAGE, B_D1FULL = B_EMPTY + NSTAGE,
+       B_D1EMPTY = B_D1FULL + 2, B_A2FULL = B_D1EMPTY + 2, B_D2FULL = B_A2FULL + 1,
+       N_BARS = B_D2FULL + 1 };
 
 template <int MODE>
 struct Cfg {
@@ -43,12 +58,11 @@ struct Cfg {
   static constexpr int OFF_W1 = 0;
   static constexpr int OFF_W2 = OFF_W1 + KC1 * CHUNK;
   static constexpr int OFF_A = OFF_W2 + (G2 ? 2 * CHUNK : 0);
-  static constexpr int OFF_A2 = OFF_A + 2 * CHUNK;
-  static constexpr int OFF_BAR = OFF_A2 + (G2 ? 2 * CHUNK : 0);
-  static constexpr int OFF_TMEM = OFF_BAR + 64;
-  static constexpr int OFF_RED = OFF_TMEM + 16;
-  static constexpr int OFF_IDX = OFF_RED + 4 * TM * 4;
-  static constexpr int BYTES = OFF_IDX + 2 * TM * 4;
+  static constexpr int OFF_A2 = OFF_A + NSTAGE * CHUNK;
+  static constexpr int OFF_PAR = OFF_A2 + (G2 ? 2 * CHUNK : 0);     // 7 x 128 floats
+  static constexpr int OFF_BAR = OFF_PAR + 7 * H * 4;
+  static constexpr int OFF_MISC = OFF_BAR + 8 * N_BARS;              // tmem addr, abort flag
+  static constexpr int BYTES = OFF_MISC + 16;
   static constexpr int SMEM = BYTES + 1024;  // slack for 1024-byte alignment
 };
 
@@ -79,6 +93,22 @@ __device__ __forceinline__ uint32_t sw128(int r, int u) {
   return static_cast<uint32_t>(r * 128 + ((u ^ (r & 7)) << 4));
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait that also gives up when another role raised the abort flag.
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, int* err,
+                                              volatile int* abort) {
+  for (uint32_t i = 0; i < kWaitCap; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 255) == 255 && *abort) return false;
+  }
+  set_err(err, DERR_TIMEOUT);
+  *abort = 1;
+  return false;
+}
+
 template <int MODE>
 __device__ __forceinline__ const float* chunk_src(const TcArgs& a, int c, int64_t g, int s, int d) {
   if constexpr (MODE == TC_EDGE_ENC) {
@@ -93,46 +123,46 @@ __device__ __forceinline__ const float* chunk_src(const TcArgs& a, int c, int64_
   }
 }
 
-// Read 64 FP32 accumulator columns [col, col+64) of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_row64(uint32_t taddr, float* v) {
-  float t[32];
-  tmem_ld32_wait(taddr, t);
+// Row statistics of x_j = acc_j + b_j over the 128 accumulator columns of
+// this thread's TMEM lane (shifted sums: shift = first value).
+__device__ __forceinline__ void row_stats(uint32_t taddr, const float* __restrict__ b, float& mean,
+                                          float& rstd) {
+  float v[32];
+  float shift = 0.f, s = 0.f, ss = 0.f;
 #pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = t[i];
-  tmem_ld32_wait(taddr + 32, t);
+  for (int cc = 0; cc < 4; ++cc) {
+    tmem_ld32_wait(taddr + 32 * cc, v);
 #pragma unroll
-  for (int i = 0; i < 32; ++i) v[32 + i] = t[i];
+    for (int j = 0; j < 32; j += 4) {
+      const float4 bb = *reinterpret_cast<const float4*>(b + 32 * cc + j);
+      const float x0 = v[j] + bb.x, x1 = v[j + 1] + bb.y, x2 = v[j + 2] + bb.z, x3 = v[j + 3] + bb.w;
+      if (cc == 0 && j == 0) shift = x0;
+      const float d0 = x0 - shift, d1 = x1 - shift, d2 = x2 - shift, d3 = x3 - shift;
+      s += (d0 + d1) + (d2 + d3);
+      ss = fmaf(d0, d0, fmaf(d1, d1, fmaf(d2, d2, fmaf(d3, d3, ss))));
+    }
+  }
+  const float ms = s * (1.0f / H);
+  mean = shift + ms;
+  const float var = fmaxf(ss * (1.0f / H) - ms * ms, 0.f);
+  rstd = 1.0f / sqrtf(var + kLnEps);
 }
 
-// v <- ReLU(LN(v + b) * g + be) for a 128-wide row split over two threads
-// (column halves hf = 0, 1), statistics exchanged through shared memory.
-__device__ __forceinline__ void bias_ln_relu_split(float* v, const float* __restrict__ b,
-                                                   const float* __restrict__ g,
-                                                   const float* __restrict__ be, int hf, int r,
-                                                   float* red) {
-  const int c0 = hf * 64;
-  float s = 0.f;
+// 32 normalised, ReLU'd values of columns [32 cc, 32 cc + 32).
+__device__ __forceinline__ void row_norm32(uint32_t taddr, int cc, const float* __restrict__ b,
+                                           const float* __restrict__ g, const float* __restrict__ be,
+                                           float mean, float rstd, float (&y)[32]) {
+  tmem_ld32_wait(taddr + 32 * cc, y);
 #pragma unroll
-  for (int j = 0; j < 64; ++j) {
-    v[j] += __ldg(b + c0 + j);
-    s += v[j];
+  for (int j = 0; j < 32; j += 4) {
+    const float4 bb = *reinterpret_cast<const float4*>(b + 32 * cc + j);
+    const float4 gg = *reinterpret_cast<const float4*>(g + 32 * cc + j);
+    const float4 ee = *reinterpret_cast<const float4*>(be + 32 * cc + j);
+    y[j] = fmaxf((y[j] + bb.x - mean) * rstd * gg.x + ee.x, 0.f);
+    y[j + 1] = fmaxf((y[j + 1] + bb.y - mean) * rstd * gg.y + ee.y, 0.f);
+    y[j + 2] = fmaxf((y[j + 2] + bb.z - mean) * rstd * gg.z + ee.z, 0.f);
+    y[j + 3] = fmaxf((y[j + 3] + bb.w - mean) * rstd * gg.w + ee.w, 0.f);
   }
-  red[hf * TM + r] = s;
-  __syncthreads();
-  const float mean = (red[r] + red[TM + r]) * (1.0f / H);
-  float q = 0.f;
-#pragma unroll
-  for (int j = 0; j < 64; ++j) {
-    const float d = v[j] - mean;
-    q += d * d;
-  }
-  red[2 * TM + hf * TM + r] = q;
-  __syncthreads();
-  const float var = (red[2 * TM + r] + red[3 * TM + r]) * (1.0f / H);
-  const float rstd = 1.0f / sqrtf(var + kLnEps);
-#pragma unroll
-  for (int j = 0; j < 64; ++j)
-    v[j] = fmaxf((v[j] - mean) * rstd * __ldg(g + c0 + j) + __ldg(be + c0 + j), 0.f);
 }
 
 template <int MODE>
@@ -145,20 +175,42 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
   uint8_t* sW2 = smem + C::OFF_W2;
   uint8_t* sA = smem + C::OFF_A;
   uint8_t* sA2 = smem + C::OFF_A2;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);  // 0 weights, 1-2 ring, 3 gemm2
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::OFF_TMEM);
-  float* red = reinterpret_cast<float*>(smem + C::OFF_RED);
-  int* s_src = reinterpret_cast<int*>(smem + C::OFF_IDX);
-  int* s_dst = s_src + TM;
+  float* par = reinterpret_cast<float*>(smem + C::OFF_PAR);  // b1 g1 be1 b2 g2 be2 wcls
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::OFF_MISC);
+  volatile int* abort = reinterpret_cast<volatile int*>(smem + C::OFF_MISC + 4);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int q = warp & 3, hf = warp >> 2, r = 32 * q + lane;  // epilogue row / column half
 
+  // ---- set-up -------------------------------------------------------------
   if (tid == 0) {
-    for (int i = 0; i < 4; ++i) mbar_init(&bars[i], 1);
+    mbar_init(&bars[B_W], 1);
+    for (int s = 0; s < NSTAGE; ++s) {
+      mbar_init(&bars[B_FULL + s], PROD_THREADS);
+      mbar_init(&bars[B_EMPTY + s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&bars[B_D1FULL + b], 1);
+      mbar_init(&bars[B_D1EMPTY + b], EPI_THREADS);
+    }
+    mbar_init(&bars[B_A2FULL], EPI_THREADS);
+    mbar_init(&bars[B_D2FULL], 1);
+    *abort = 0;
     fence_mbar_init();
   }
-  if (warp == 0) {
+  if (tid < H) {
+    par[tid] = __ldg(a.b1 + tid);
+    par[H + tid] = __ldg(a.g1 + tid);
+    par[2 * H + tid] = __ldg(a.be1 + tid);
+    if (C::G2) {
+      par[3 * H + tid] = __ldg(a.b2 + tid);
+      par[4 * H + tid] = __ldg(a.g2 + tid);
+      par[5 * H + tid] = __ldg(a.be2 + tid);
+    } else {
+      par[6 * H + tid] = __ldg(a.wcls + tid);
+    }
+  }
+  if (warp == MMA_WARP) {
     tmem_alloc(tmem_slot, TMEM_COLS);
     tmem_relinquish();
   }
@@ -166,162 +218,289 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t tD1 = tmem, tD2 = tmem + 128;
-  const uint32_t lane_off = static_cast<uint32_t>(32 * q) << 16;
-
-  if (tid == 0) {
-    const uint32_t bytes = (C::KC1 + (C::G2 ? 2 : 0)) * CHUNK;
-    mbar_arrive_expect_tx(&bars[0], bytes);
-    for (int c = 0; c < C::KC1; ++c) bulk_g2s(sW1 + c * CHUNK, a.w1 + (size_t)c * CHUNK, CHUNK, &bars[0]);
-    if (C::G2)
-      for (int c = 0; c < 2; ++c) bulk_g2s(sW2 + c * CHUNK, a.w2 + (size_t)c * CHUNK, CHUNK, &bars[0]);
-  }
-  bool ok = mbar_wait(&bars[0], 0, a.err);
-  const bool aborted0 = __syncthreads_or(!ok);
 
   const int64_t n_rows = MODE == TC_NODE_UPD ? a.n_nodes : (int64_t)*a.n_edges_dev;
   const int64_t n_tiles = (n_rows + TM - 1) / TM;
   const int nn = (int)a.n_nodes;
-  uint32_t ring_uses[2] = {0u, 0u};
-  uint32_t g2_uses = 0;
-  const int grow = tid >> 1, gpart = tid & 1;  // gather: row, which 32-column half of the chunk
 
-  for (int64_t tile = blockIdx.x; !aborted0 && tile < n_tiles; tile += gridDim.x) {
-    const int64_t row0 = tile * TM;
-    if constexpr (MODE == TC_EDGE_ENC || MODE == TC_EDGE_UPD) {
-      if (tid < TM) {
-        const int64_t gr = row0 + tid;
-        s_src[tid] = gr < n_rows ? min(max(a.src[gr], 0), nn - 1) : 0;
-        s_dst[tid] = gr < n_rows ? min(max(a.dst[gr], 0), nn - 1) : 0;
+  if (warp >= EPI_WARPS && warp < MMA_WARP) {
+    // =========================== producers =================================
+    // Flattened stream of this CTA's (tile, chunk) pairs, prefetched two chunks
+    // ahead in a three-deep register ring so that loads of the next chunks
+    // (also across tile boundaries) are in flight while one chunk is stored.
+    // Thread t8 = pt % 8 of a row group reads bytes [16 t8, 16 t8 + 16) of each
+    // 128-byte line of a 256-byte FP32 row segment (two fully coalesced loads)
+    // and writes the two resulting 8-byte BF16 halves.  Row groups sharing a
+    // half-warp own rows 4 apart, so those 8-byte shared stores never collide.
+    const int pt = tid - EPI_THREADS;
+    const int t8 = pt & 7, rg = pt >> 3, wg = rg & 3, wi = rg >> 2;
+    const int rbase = 8 * (wi >> 1) + 4 * (wg & 1) + 2 * (wi & 1) + (wg >> 1);  // 0..31
+    constexpr int RPT = TM / (PROD_THREADS / 8);  // rows per producer thread
+    const int64_t my_tiles =
+        n_tiles > blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int64_t total = my_tiles * C::KC1;
+    // gather indices of the tile being fetched, read when its first chunk is
+    // fetched (chunks reach the same tile in order, two ahead of the stores)
+    int sidx[RPT], didx[RPT];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) sidx[i] = didx[i] = 0;
+    auto fetch = [&](int64_t q, float4 (&f)[2 * RPT]) {
+      if (q >= total) return;
+      const int64_t row0 = (blockIdx.x + (q / C::KC1) * gridDim.x) * TM;
+      const int c = (int)(q % C::KC1);
+      if constexpr (MODE == TC_EDGE_ENC || MODE == TC_EDGE_UPD) {
+        if (c == 0) {
+#pragma unroll
+          for (int i = 0; i < RPT; ++i) {
+            const int64_t gr = row0 + rbase + 32 * i;
+            sidx[i] = gr < n_rows ? min(max(a.src[gr], 0), nn - 1) : 0;
+            didx[i] = gr < n_rows ? min(max(a.dst[gr], 0), nn - 1) : 0;
+          }
+        }
       }
-      __syncthreads();
-    }
-    const int64_t g = row0 + grow;
-    const bool valid = g < n_rows;
-    // ---- GEMM 1: stream the gathered input through the two-slot ring --------
-    bool abort = false;
-    for (int c = 0; c < C::KC1; ++c) {
-      const int slot = c & 1;
-      if (ring_uses[slot] > 0) ok = mbar_wait(&bars[1 + slot], (ring_uses[slot] - 1) & 1, a.err);
-      float4 f[8];
-      if (valid) {
-        const float* p = chunk_src<MODE>(a, c, g, s_src[grow], s_dst[grow]) + 32 * gpart;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) f[i] = *reinterpret_cast<const float4*>(p + 4 * i);
-      } else {
-#pragma unroll
-        for (int i = 0; i < 8; ++i) f[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int i = 0; i < RPT; ++i) {
+        const int64_t gr = row0 + rbase + 32 * i;
+        if (gr < n_rows) {
+          const float* p = chunk_src<MODE>(a, c, gr, sidx[i], didx[i]) + 4 * t8;
+          f[2 * i] = *reinterpret_cast<const float4*>(p);
+          f[2 * i + 1] = *reinterpret_cast<const float4*>(p + 32);
+        } else {
+          f[2 * i] = make_float4(0.f, 0.f, 0.f, 0.f);
+          f[2 * i + 1] = f[2 * i];
+        }
       }
-      uint8_t* dstc = sA + slot * CHUNK;
+    };
+    auto store = [&](int64_t q, const float4 (&f)[2 * RPT]) {
+      const int slot = (int)(q % NSTAGE);
+      const uint32_t round = (uint32_t)(q / NSTAGE);
+      if (round > 0 && !wait_or_abort(&bars[B_EMPTY + slot], (round - 1) & 1, a.err, abort))
+        return false;
+      const uint32_t dstc = smem_u32(sA + slot * CHUNK);
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        uint4 u;
-        u.x = pack_bf16(f[2 * i].x, f[2 * i].y);
-        u.y = pack_bf16(f[2 * i].z, f[2 * i].w);
-        u.z = pack_bf16(f[2 * i + 1].x, f[2 * i + 1].y);
-        u.w = pack_bf16(f[2 * i + 1].z, f[2 * i + 1].w);
-        *reinterpret_cast<uint4*>(dstc + sw128(grow, 4 * gpart + i)) = u;
+      for (int i = 0; i < RPT; ++i) {
+        const int r = rbase + 32 * i;
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          const float4 v = f[2 * i + hh];
+          const uint32_t addr = dstc + sw128(r, 4 * hh + (t8 >> 1)) + 8 * (t8 & 1);
+          asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(pack_bf16(v.x, v.y)),
+                       "r"(pack_bf16(v.z, v.w))
+                       : "memory");
+        }
       }
       fence_proxy_async();
-      if (__syncthreads_or(!ok)) {
-        abort = true;
-        break;
-      }
-      if (tid == 0) {
-        tc_fence_after();
-        const uint32_t a0 = smem_u32(dstc), b0 = smem_u32(sW1 + c * CHUNK);
-#pragma unroll
-        for (int k = 0; k < KCH / 16; ++k)
-          mma_f16(tD1, sdesc_k_sw128(a0 + 32 * k), sdesc_k_sw128(b0 + 32 * k), IDESC,
-                  (c > 0 || k > 0) ? 1u : 0u);
-        mma_commit(&bars[1 + slot]);
-      }
-      ++ring_uses[slot];
+      mbar_arrive(&bars[B_FULL + slot]);
+      return true;
+    };
+    float4 b0[2 * RPT], b1[2 * RPT], b2[2 * RPT];
+    fetch(0, b0);
+    fetch(1, b1);
+    for (int64_t q = 0; q < total; q += 3) {
+      fetch(q + 2, b2);
+      if (!store(q, b0)) break;
+      if (q + 1 >= total) break;
+      fetch(q + 3, b0);
+      if (!store(q + 1, b1)) break;
+      if (q + 2 >= total) break;
+      fetch(q + 4, b1);
+      if (!store(q + 2, b2)) break;
     }
-    if (abort) break;
-    const int last = (C::KC1 - 1) & 1;
-    ok = mbar_wait(&bars[1 + last], (ring_uses[last] - 1) & 1, a.err);
-    if (__syncthreads_or(!ok)) break;
-    tc_fence_after();
-
-    // ---- epilogue 1 ---------------------------------------------------------
-    float v[64];
-    tmem_row64(tD1 + lane_off + 64 * hf, v);
-    const int64_t grr = row0 + r;
-    if constexpr (MODE == TC_CLS) {
-      bias_ln_relu_split(v, a.b1, a.g1, a.be1, hf, r, red);
-      float p = 0.f;
-#pragma unroll
-      for (int j = 0; j < 64; ++j) p = fmaf(v[j], __ldg(a.wcls + 64 * hf + j), p);
-      red[hf * TM + r] = p;
-      __syncthreads();
-      if (hf == 0 && grr < n_rows) a.logits[grr] = red[r] + red[TM + r] + __ldg(a.bcls);
-      tc_fence_before();
-      __syncthreads();
-      continue;
-    } else {
-      bias_ln_relu_split(v, a.b1, a.g1, a.be1, hf, r, red);
-      uint8_t* dst2 = sA2 + hf * CHUNK;
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        uint4 w;
-        w.x = pack_bf16(v[8 * u + 0], v[8 * u + 1]);
-        w.y = pack_bf16(v[8 * u + 2], v[8 * u + 3]);
-        w.z = pack_bf16(v[8 * u + 4], v[8 * u + 5]);
-        w.w = pack_bf16(v[8 * u + 6], v[8 * u + 7]);
-        *reinterpret_cast<uint4*>(dst2 + sw128(r, u)) = w;
-      }
-      fence_proxy_async();
-      tc_fence_before();
-      __syncthreads();
-      // ---- GEMM 2 -----------------------------------------------------------
-      if (tid == 0) {
+  } else if (warp == MMA_WARP) {
+    // =========================== MMA issuer ================================
+    if (lane == 0) {
+      const uint32_t wbytes = (C::KC1 + (C::G2 ? 2 : 0)) * CHUNK;
+      mbar_arrive_expect_tx(&bars[B_W], wbytes);
+      for (int c = 0; c < C::KC1; ++c)
+        bulk_g2s(sW1 + c * CHUNK, a.w1 + (size_t)c * CHUNK, CHUNK, &bars[B_W]);
+      if (C::G2)
+        for (int c = 0; c < 2; ++c)
+          bulk_g2s(sW2 + c * CHUNK, a.w2 + (size_t)c * CHUNK, CHUNK, &bars[B_W]);
+      bool live = wait_or_abort(&bars[B_W], 0, a.err, abort);
+      uint32_t gchunk = 0;
+      int i = 0;
+      int pending = -1;  // local tile whose second GEMM waits for the epilogue's A2
+      auto issue_gemm2 = [&]() {
         tc_fence_after();
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
           const uint32_t a0 = smem_u32(sA2 + c * CHUNK), b0 = smem_u32(sW2 + c * CHUNK);
 #pragma unroll
           for (int k = 0; k < KCH / 16; ++k)
-            mma_f16(tD2, sdesc_k_sw128(a0 + 32 * k), sdesc_k_sw128(b0 + 32 * k), IDESC,
+            mma_f16(tmem + 256, sdesc_k_sw128(a0 + 32 * k), sdesc_k_sw128(b0 + 32 * k), IDESC,
                     (c > 0 || k > 0) ? 1u : 0u);
         }
-        mma_commit(&bars[3]);
-      }
-      ok = mbar_wait(&bars[3], g2_uses & 1, a.err);
-      ++g2_uses;
-      if (__syncthreads_or(!ok)) break;
-      tc_fence_after();
-      // ---- epilogue 2 ---------------------------------------------------------
-      tmem_row64(tD2 + lane_off + 64 * hf, v);
-      bias_ln_relu_split(v, a.b2, a.g2, a.be2, hf, r, red);
-      if (grr < n_rows) {
-        float* out;
-        const float* res = nullptr;
-        if constexpr (MODE == TC_NODE_UPD) {
-          out = a.h_out + grr * H + 64 * hf;
-          res = a.h + grr * H + 64 * hf;
-        } else if constexpr (MODE == TC_EDGE_UPD) {
-          out = a.e + grr * H + 64 * hf;
-          res = out;
-        } else {
-          out = a.e + grr * H + 64 * hf;
+        mma_commit(&bars[B_D2FULL]);
+        pending = -1;
+      };
+      // Wait for `bar`; meanwhile issue the pending second GEMM as soon as its
+      // operand is ready, so it never queues behind the next tile's gather.
+      auto wait_poll = [&](uint64_t* bar, uint32_t parity) {
+        for (uint32_t it = 0; it < kWaitCap; ++it) {
+          if (mbar_try_wait(bar, parity)) return true;
+          if (C::G2 && pending >= 0 && mbar_try_wait(&bars[B_A2FULL], pending & 1)) issue_gemm2();
+          if ((it & 255) == 255 && *abort) return false;
         }
-#pragma unroll
-        for (int j = 0; j < 64; j += 4) {
-          float4 o = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-          if (res) {
-            const float4 t = *reinterpret_cast<const float4*>(res + j);
-            o.x += t.x; o.y += t.y; o.z += t.z; o.w += t.w;
+        set_err(a.err, DERR_TIMEOUT);
+        *abort = 1;
+        return false;
+      };
+      for (int64_t tile = blockIdx.x; live && tile < n_tiles; tile += gridDim.x, ++i) {
+        const int b = i & 1;
+        const uint32_t use = i >> 1;
+        if (use > 0 && !wait_poll(&bars[B_D1EMPTY + b], (use - 1) & 1)) break;
+        tc_fence_after();
+        const uint32_t d1 = tmem + 128 * b;
+        for (int c = 0; c < C::KC1; ++c) {
+          const int slot = gchunk % NSTAGE;
+          if (!wait_poll(&bars[B_FULL + slot], (gchunk / NSTAGE) & 1)) {
+            live = false;
+            break;
           }
-          *reinterpret_cast<float4*>(out + j) = o;
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(sA + slot * CHUNK), b0 = smem_u32(sW1 + c * CHUNK);
+#pragma unroll
+          for (int k = 0; k < KCH / 16; ++k)
+            mma_f16(d1, sdesc_k_sw128(a0 + 32 * k), sdesc_k_sw128(b0 + 32 * k), IDESC,
+                    (c > 0 || k > 0) ? 1u : 0u);
+          mma_commit(&bars[B_EMPTY + slot]);
+          ++gchunk;
+        }
+        if (!live) break;
+        mma_commit(&bars[B_D1FULL + b]);
+        if (C::G2) {
+          if (pending >= 0) {
+            if (!wait_or_abort(&bars[B_A2FULL], pending & 1, a.err, abort)) break;
+            issue_gemm2();
+          }
+          pending = i;
         }
       }
-      tc_fence_before();
-      __syncthreads();
+      if (C::G2 && pending >= 0 && !*abort &&
+          wait_or_abort(&bars[B_A2FULL], pending & 1, a.err, abort))
+        issue_gemm2();
+    }
+  } else {
+    // =========================== epilogue ==================================
+    const int r = tid;  // TMEM lane == tile row
+    const uint32_t lane_off = static_cast<uint32_t>(32 * warp) << 16;
+    int i = 0;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++i) {
+      const int b = i & 1;
+      const int64_t gr = tile * TM + r;
+      const bool valid = gr < n_rows;
+      if (!wait_or_abort(&bars[B_D1FULL + b], (i >> 1) & 1, a.err, abort)) break;
+      tc_fence_after();
+      const uint32_t t1 = tmem + 128 * b + lane_off;
+      float mean, rstd;
+      row_stats(t1, par, mean, rstd);
+      float y[32];
+      if constexpr (MODE == TC_CLS) {
+        float p = 0.f;
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          row_norm32(t1, cc, par, par + H, par + 2 * H, mean, rstd, y);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) p = fmaf(y[j], par[6 * H + 32 * cc + j], p);
+        }
+        tc_fence_before();
+        mbar_arrive(&bars[B_D1EMPTY + b]);
+        if (valid) a.logits[gr] = p + __ldg(a.bcls);
+      } else {
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          row_norm32(t1, cc, par, par + H, par + 2 * H, mean, rstd, y);
+          uint8_t* dst2 = sA2 + (cc >> 1) * CHUNK;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            uint4 w;
+            w.x = pack_bf16(y[8 * q + 0], y[8 * q + 1]);
+            w.y = pack_bf16(y[8 * q + 2], y[8 * q + 3]);
+            w.z = pack_bf16(y[8 * q + 4], y[8 * q + 5]);
+            w.w = pack_bf16(y[8 * q + 6], y[8 * q + 7]);
+            *reinterpret_cast<uint4*>(dst2 + sw128(r, 4 * (cc & 1) + q)) = w;
+          }
+        }
+        fence_proxy_async();
+        tc_fence_before();
+        mbar_arrive(&bars[B_D1EMPTY + b]);
+        mbar_arrive(&bars[B_A2FULL]);
+        if (!wait_or_abort(&bars[B_D2FULL], i & 1, a.err, abort)) break;
+        tc_fence_after();
+        const uint32_t t2 = tmem + 256 + lane_off;
+        row_stats(t2, par + 3 * H, mean, rstd);
+        // The second GEMM has consumed A2, so its 32 KB stage the FP32 output:
+        // 64 columns at a time, row-per-thread writes with 16-byte units
+        // XOR-swizzled by (row % 8), then coalesced residual loads and stores
+        // (16 lanes cover one 256-byte row segment).
+        float* stg = reinterpret_cast<float*>(sA2);
+        const int64_t row0 = tile * TM;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          // residual of the rows this thread stores in the coalesced pass, in two
+          // batches fetched ahead of their use so the latency hides behind the
+          // normalisation (batch a) and behind batch a's stores (batch b)
+          const int l16 = lane & 15;
+          constexpr int NIT = TM / (2 * EPI_WARPS);
+          constexpr int NB = 4;
+          float4 ra[NB], rb[NB];
+          auto fetch_res = [&](int it0, float4 (&rr4)[NB]) {
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+              const int rr = ((it0 + k) * EPI_WARPS + warp) * 2 + (lane >> 4);
+              const int64_t g2 = row0 + rr;
+              rr4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+              if (g2 < n_rows) {
+                const int64_t off = g2 * H + 64 * half + 4 * l16;
+                if constexpr (MODE == TC_NODE_UPD) rr4[k] = *reinterpret_cast<const float4*>(a.h + off);
+                if constexpr (MODE == TC_EDGE_UPD) rr4[k] = *reinterpret_cast<const float4*>(a.e + off);
+              }
+            }
+          };
+          auto store_rows = [&](int it0, const float4 (&rr4)[NB]) {
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+              const int rr = ((it0 + k) * EPI_WARPS + warp) * 2 + (lane >> 4);
+              const int64_t g2 = row0 + rr;
+              const float4 v = *reinterpret_cast<const float4*>(stg + rr * 64 + 4 * (l16 ^ (rr & 7)));
+              if (g2 < n_rows) {
+                const float4 o = make_float4(v.x + rr4[k].x, v.y + rr4[k].y, v.z + rr4[k].z,
+                                             v.w + rr4[k].w);
+                float* outp = MODE == TC_NODE_UPD ? a.h_out : a.e;
+                *reinterpret_cast<float4*>(outp + g2 * H + 64 * half + 4 * l16) = o;
+              }
+            }
+          };
+          fetch_res(0, ra);
+#pragma unroll
+          for (int cc = 0; cc < 2; ++cc) {
+            row_norm32(t2, 2 * half + cc, par + 3 * H, par + 4 * H, par + 5 * H, mean, rstd, y);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const int un = (8 * cc + q) ^ (r & 7);
+              *reinterpret_cast<float4*>(stg + r * 64 + 4 * un) =
+                  make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
+            }
+          }
+          fetch_res(NB, rb);
+          asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
+#pragma unroll
+          for (int it0 = 0; it0 < NIT; it0 += 2 * NB) {
+            store_rows(it0, ra);
+            if (it0 + 2 * NB < NIT) fetch_res(it0 + 2 * NB, ra);
+            store_rows(it0 + NB, rb);
+            if (it0 + 3 * NB < NIT) fetch_res(it0 + 3 * NB, rb);
+          }
+          asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
+        }
+        tc_fence_before();
+      }
     }
   }
+  // ---- teardown -------------------------------------------------------------
+  tc_fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == MMA_WARP) {
     tc_fence_after();
     tmem_dealloc(tmem, TMEM_COLS);
   }

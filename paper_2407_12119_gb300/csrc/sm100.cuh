@@ -12,7 +12,7 @@
 namespace etx {
 namespace sm100 {
 
-constexpr uint32_t kWaitCap = 1u << 26;  // try_wait polls before giving up (seconds)
+constexpr uint32_t kWaitCap = 1u << 22;  // try_wait polls before giving up (about a second)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
