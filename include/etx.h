@@ -166,6 +166,29 @@ int64_t etx_gnn_param_count(const etx_config* cfg);
 etx_status etx_gnn_backward(etx_ctx* ctx, const float* dlogits, float* dparams, void* stream);
 
 /*
+ * Training loss: the edge term of Eq. 5 read as class-weighted binary cross
+ * entropy on the logits (the paper uses a sigmoid focal loss; this build's
+ * training workload asks for BCE with a positive-class weight):
+ *     loss = mean_e [ w y_e softplus(-z_e) + (1 - y_e) softplus(z_e) ]
+ * over the n_edges = edge_offsets[n_events] edges (read on the device).
+ *   targets  float32 [n_edges], 1 for genuine edges, 0 otherwise
+ *   loss     float32 [1], written
+ *   dlogits  float32 [n_edges], written: d loss / d z_e
+ */
+etx_status etx_weighted_bce(etx_ctx* ctx, const float* logits, const float* targets,
+                            const int32_t* edge_offsets, int32_t n_events, float pos_weight,
+                            float* loss, float* dlogits, void* stream);
+
+/*
+ * One Adam update (Kingma & Ba) of n float32 parameters in place, with
+ * bias-corrected moments; m and v are caller-owned state (zero before step 1),
+ * step counts from 1.  No counterpart in the paper's text beyond "trained".
+ */
+etx_status etx_adam_step(etx_ctx* ctx, float* params, const float* grads, float* m, float* v,
+                         int64_t n, float lr, float beta1, float beta2, float eps, int64_t step,
+                         void* stream);
+
+/*
  * Purified hit graph and tracks (Sec. 5, Sec. 7.3): keep edge e iff
  * logits[e] > threshold_logit (score > sigmoid(threshold_logit); 0.0f is the
  * paper's 0.5), then weakly connected components by lock-free union-find.

@@ -185,6 +185,18 @@ etx_status etx_ctx_create(const etx_config* cfg, int32_t device, etx_ctx** out) 
   chk(dmalloc(ctx, &ctx->m, (size_t)N * 2 * H, "messages"));
   chk(dmalloc(ctx, &ctx->e, (size_t)E * H, "edge features"));
   chk(dmalloc(ctx, &ctx->parent, (size_t)N, "union-find parents"));
+  if (cfg->train) {
+    const size_t L1 = (size_t)cfg->n_iters + 1, R = (size_t)(N > E ? N : E);
+    chk(dmalloc(ctx, &ctx->h_ck, L1 * N * H, "node checkpoints"));
+    chk(dmalloc(ctx, &ctx->e_ck, L1 * E * H, "edge checkpoints"));
+    chk(dmalloc(ctx, &ctx->de, (size_t)E * H, "edge gradients"));
+    chk(dmalloc(ctx, &ctx->dh, (size_t)N * H, "node gradients"));
+    chk(dmalloc(ctx, &ctx->bw_X, R * 3 * H, "backward inputs"));
+    chk(dmalloc(ctx, &ctx->bw_DX, R * 3 * H, "backward input gradients"));
+    float** rows[] = {&ctx->bw_R1, &ctx->bw_DA1, &ctx->bw_DY1, &ctx->bw_DY1N1,
+                      &ctx->bw_DA2, &ctx->bw_DY2, &ctx->bw_DY2N2};
+    for (float** q : rows) chk(dmalloc(ctx, q, R * H, "backward row factors"));
+  }
   if (st == ETX_OK) {
     e = cudaMemset(ctx->d_err, 0, sizeof(int));
     if (e != cudaSuccess) st = cuda_fail(ctx, e, "cudaMemset");
@@ -206,7 +218,9 @@ etx_status etx_ctx_destroy(etx_ctx* ctx) {
   cudaSetDevice(ctx->device);
   void* bufs[] = {ctx->d_err, ctx->n_edges, ctx->w_dev, ctx->blob_dev, ctx->w_tc, ctx->plane_off,
                   ctx->hit_cnt, ctx->scan_tmp, ctx->out_off, ctx->in_off, ctx->in_cnt,
-                  ctx->perm_in, ctx->h, ctx->m, ctx->e, ctx->parent};
+                  ctx->perm_in, ctx->h, ctx->m, ctx->e, ctx->parent, ctx->h_ck, ctx->e_ck,
+                  ctx->de, ctx->dh, ctx->bw_X, ctx->bw_DX, ctx->bw_R1, ctx->bw_DA1, ctx->bw_DY1,
+                  ctx->bw_DY1N1, ctx->bw_DA2, ctx->bw_DY2, ctx->bw_DY2N2};
   for (void* p : bufs)
     if (p) cudaFree(p);
   for (auto& r : ctx->prof) {
@@ -294,6 +308,7 @@ etx_status etx_load_weights(etx_ctx* ctx, const float* blob, int64_t n_floats) {
   const size_t norm_at = push_vec(12);
   std::vector<Pending> emb;
   for (int l = 0; l < c.emb_depth; ++l) emb.push_back(push_lin(c.emb_widths[l + 1], c.emb_widths[l]));
+  const int64_t gnn_offset = p - blob;
   struct PB { Pending l1, l2; size_t g1, be1, g2, be2; };
   auto push_block = [&](int k_in) {
     PB b;
@@ -397,6 +412,8 @@ etx_status etx_load_weights(etx_ctx* ctx, const float* blob, int64_t n_floats) {
     ctx->w.cls_tc.w1 = next();
     ctx->w.has_tc = true;
   }
+  ctx->gnn_blob_offset = gnn_offset;
+  ctx->fwd_saved = false;
   ctx->weights_loaded = true;
   return ETX_OK;
 }
@@ -476,15 +493,57 @@ etx_status etx_gnn_forward(etx_ctx* ctx, const float* x, const float* y, const f
   if (e == cudaSuccess)
     e = launch_gnn_forward(ctx, x, y, z, n_hits, src, dst, ctx->n_edges, logits, dtype == ETX_BF16, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "etx_gnn_forward launch");
+  if (ctx->cfg.train) {
+    ctx->fwd_x = x;
+    ctx->fwd_y = y;
+    ctx->fwd_z = z;
+    ctx->fwd_src = src;
+    ctx->fwd_dst = dst;
+    ctx->fwd_n_hits = n_hits;
+    ctx->fwd_saved = true;
+  }
   return ETX_OK;
 }
 
 etx_status etx_gnn_backward(etx_ctx* ctx, const float* dlogits, float* dparams, void* stream) {
-  (void)dlogits;
-  (void)dparams;
-  (void)stream;
   if (!ctx) return ETX_ERR_ARG;
-  return fail(ctx, ETX_ERR_UNSUPPORTED, "backward not built yet");
+  if (!ctx->cfg.train) return fail(ctx, ETX_ERR_STATE, "context was not created for training");
+  if (!ctx->fwd_saved) return fail(ctx, ETX_ERR_STATE, "no training forward since the weights were loaded");
+  if (!dlogits || !dparams) return fail(ctx, ETX_ERR_ARG, "NULL array");
+  cudaSetDevice(ctx->device);
+  cudaError_t e = launch_gnn_backward(ctx, dlogits, dparams, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "etx_gnn_backward launch");
+  return ETX_OK;
+}
+
+etx_status etx_weighted_bce(etx_ctx* ctx, const float* logits, const float* targets,
+                            const int32_t* edge_offsets, int32_t n_events, float pos_weight,
+                            float* loss, float* dlogits, void* stream) {
+  if (!ctx) return ETX_ERR_ARG;
+  if (!logits || !targets || !edge_offsets || !loss || !dlogits) return fail(ctx, ETX_ERR_ARG, "NULL array");
+  if (n_events < 0 || n_events > ctx->cfg.max_events) return fail(ctx, ETX_ERR_CAPACITY, "n_events exceeds the context capacity");
+  if (!(pos_weight >= 0.f)) return fail(ctx, ETX_ERR_ARG, "pos_weight must be >= 0");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  launch(ctx, "clamp_edges", k_clamp_edges, 1, 1, 0, s, edge_offsets, n_events, ctx->cfg.max_edges,
+         ctx->n_edges, ctx->d_err);
+  cudaError_t e = launch_weighted_bce(ctx, logits, targets, ctx->n_edges, pos_weight, loss, dlogits, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "etx_weighted_bce launch");
+  return ETX_OK;
+}
+
+etx_status etx_adam_step(etx_ctx* ctx, float* params, const float* grads, float* m, float* v,
+                         int64_t n, float lr, float beta1, float beta2, float eps, int64_t step,
+                         void* stream) {
+  if (!ctx) return ETX_ERR_ARG;
+  if (n < 0 || (n > 0 && (!params || !grads || !m || !v))) return fail(ctx, ETX_ERR_ARG, "NULL array");
+  if (step < 1) return fail(ctx, ETX_ERR_ARG, "step counts from 1");
+  if (n == 0) return ETX_OK;
+  cudaSetDevice(ctx->device);
+  cudaError_t e = launch_adam(ctx, params, grads, m, v, n, lr, beta1, beta2, eps, step,
+                              (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "etx_adam_step launch");
+  return ETX_OK;
 }
 
 etx_status etx_edges_to_tracks(etx_ctx* ctx, const int32_t* src, const int32_t* dst,

@@ -108,6 +108,20 @@ struct etx_ctx {
   // components
   int32_t* parent = nullptr;     // [max_hits]
 
+  // training (cfg.train): checkpoints of the last forward and backward scratch
+  float* h_ck = nullptr;         // [(L+1) * max_hits * H]: h^k
+  float* e_ck = nullptr;         // [(L+1) * max_edges * H]: e^k
+  float* de = nullptr;           // [max_edges * H]
+  float* dh = nullptr;           // [max_hits * H]
+  float *bw_X = nullptr, *bw_DX = nullptr;          // [rows * 3H]
+  float *bw_R1 = nullptr, *bw_DA1 = nullptr, *bw_DY1 = nullptr, *bw_DY1N1 = nullptr;  // [rows * H]
+  float *bw_DA2 = nullptr, *bw_DY2 = nullptr, *bw_DY2N2 = nullptr;
+  bool fwd_saved = false;        // a training forward ran since the weights were loaded
+  const float *fwd_x = nullptr, *fwd_y = nullptr, *fwd_z = nullptr;
+  const int32_t *fwd_src = nullptr, *fwd_dst = nullptr;
+  int64_t fwd_n_hits = 0;
+  int64_t gnn_blob_offset = 0;   // first interaction-network value in the weight blob
+
   // launch accounting and optional per-launch CUDA-event timing
   int64_t launches = 0;
   bool prof_on = false;
@@ -140,6 +154,18 @@ cudaError_t launch_gnn_forward(etx_ctx* ctx, const float* x, const float* y, con
                                const int32_t* n_edges_dev, float* logits, bool tc, cudaStream_t s);
 cudaError_t launch_edge_index(etx_ctx* ctx, int64_t n_hits, const int32_t* src,
                               const int32_t* dst, const int32_t* n_edges_dev, cudaStream_t s);
+// messages of edge features e (uses the context's edge index structures)
+cudaError_t launch_messages(etx_ctx* ctx, const float* e, float* m, int64_t n_hits, cudaStream_t s);
+
+// gnn_bwd.cu
+cudaError_t launch_checkpoint(etx_ctx* ctx, float* dst, const float* src, int64_t rows_host,
+                              const int32_t* rows_dev, int64_t rows_cap, cudaStream_t s);
+cudaError_t launch_gnn_backward(etx_ctx* ctx, const float* dlogits, float* dparams, cudaStream_t s);
+cudaError_t launch_weighted_bce(etx_ctx* ctx, const float* logits, const float* targets,
+                                const int32_t* n_edges_dev, float pos_weight, float* loss,
+                                float* dlogits, cudaStream_t s);
+cudaError_t launch_adam(etx_ctx* ctx, float* p, const float* g, float* m, float* v, int64_t n,
+                        float lr, float b1, float b2, float eps, int64_t step, cudaStream_t s);
 
 // gnn_tc.cu (hidden == 128 only)
 cudaError_t launch_edge_encoder_tc(etx_ctx* ctx, int64_t N, const int32_t* src, const int32_t* dst,

@@ -283,6 +283,13 @@ cudaError_t forward(etx_ctx* ctx, const float* x, const float* y, const float* z
   a.h = ctx->h; a.m = ctx->m; a.e = ctx->e; a.h_out = ctx->h; a.logits = logits;
   cudaError_t e = cudaSuccess;
   auto chain = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+  // training: keep h^k and e^k for the reverse pass
+  const bool keep = ctx->cfg.train != 0;
+  auto save = [&](int k) {
+    if (!keep) return;
+    chain(launch_checkpoint(ctx, ctx->h_ck + (size_t)k * N * H, ctx->h, N, nullptr, N, s));
+    chain(launch_checkpoint(ctx, ctx->e_ck + (size_t)k * Ecap * H, ctx->e, 0, n_edges_dev, Ecap, s));
+  };
 
   // the node encoder (K = 3) always runs on the FP32 SIMT path
   a.blk = ctx->w.node_enc;
@@ -293,6 +300,7 @@ cudaError_t forward(etx_ctx* ctx, const float* x, const float* y, const float* z
     a.blk = ctx->w.edge_enc;
     launch_mlp<H, EDGE_ENC>(ctx, a, Ecap, s);
   }
+  save(0);
   const int msg_grid = grid_for(ctx, (const void*)k_messages<H>, 256, 0,
                                 (N + (256 / 32) * (32 / (H / 4)) - 1) / ((256 / 32) * (32 / (H / 4))));
   for (int k = 0; k < ctx->cfg.n_iters; ++k) {
@@ -308,6 +316,7 @@ cudaError_t forward(etx_ctx* ctx, const float* x, const float* y, const float* z
       a.blk = ctx->w.edge[k];
       launch_mlp<H, EDGE_UPD>(ctx, a, Ecap, s);
     }
+    save(k + 1);
   }
   if (tc) {
     chain(launch_classifier_tc(ctx, N, n_edges_dev, logits, s));
@@ -320,6 +329,24 @@ cudaError_t forward(etx_ctx* ctx, const float* x, const float* y, const float* z
 }
 
 }  // namespace
+
+cudaError_t launch_messages(etx_ctx* ctx, const float* e, float* m, int64_t N, cudaStream_t s) {
+  if (N == 0) return cudaSuccess;
+  auto go = [&](auto kernel, int per_block) {
+    const int grid = grid_for(ctx, (const void*)kernel, 256, 0, (N + per_block - 1) / per_block);
+    launch(ctx, "gnn_messages", kernel, grid, 256, 0, s, e, (const int32_t*)ctx->out_off,
+           (const int32_t*)ctx->in_off, (const int32_t*)ctx->perm_in,
+           (const int32_t*)ctx->n_edges, (int)N, m);
+  };
+  switch (ctx->cfg.hidden) {
+    case 16: go(k_messages<16>, 8 * 8); break;
+    case 32: go(k_messages<32>, 8 * 4); break;
+    case 64: go(k_messages<64>, 8 * 2); break;
+    case 128: go(k_messages<128>, 8); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_edge_index(etx_ctx* ctx, int64_t N, const int32_t* src, const int32_t* dst,
                               const int32_t* n_edges_dev, cudaStream_t s) {

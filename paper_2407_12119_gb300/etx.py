@@ -28,7 +28,7 @@ EXPORTED = ["etx_ctx_create", "etx_ctx_destroy", "etx_last_error", "etx_weights_
             "etx_load_weights", "etx_ctx_sync", "etx_embed", "etx_build_graph",
             "etx_gnn_forward", "etx_gnn_param_count", "etx_gnn_backward",
             "etx_edges_to_tracks", "etx_edges_to_tracks_noalloc", "etx_launch_count",
-            "etx_profile_enable", "etx_profile_read"]
+            "etx_profile_enable", "etx_profile_read", "etx_weighted_bce", "etx_adam_step"]
 
 
 class EtxConfig(ctypes.Structure):
@@ -78,6 +78,8 @@ def lib() -> ctypes.CDLL:
         "etx_gnn_backward": (i32, [vp, vp, vp, vp]),
         "etx_edges_to_tracks": (i32, [vp, vp, vp, vp, f32, vp, vp, i32, i64, i32, vp, vp, vp]),
         "etx_edges_to_tracks_noalloc": (i32, [vp, vp, vp, f32, vp, vp, i32, i64, i32, vp, vp, vp]),
+        "etx_weighted_bce": (i32, [vp, vp, vp, vp, i32, f32, vp, vp, vp]),
+        "etx_adam_step": (i32, [vp, vp, vp, vp, vp, i64, f32, f32, f32, f32, i64, vp]),
         "etx_launch_count": (i64, [vp]),
         "etx_profile_enable": (i32, [vp, i32]),
         "etx_profile_read": (i32, [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
@@ -269,6 +271,42 @@ class Context:
                                           _ptr(dst), _ptr(edge_offsets), n_events, DTYPES[dtype],
                                           _ptr(logits), _stream(stream)))
         return logits
+
+    @property
+    def gnn_param_count(self) -> int:
+        return int(lib().etx_gnn_param_count(ctypes.byref(self.cfg)))
+
+    def gnn_backward(self, dlogits, dparams=None, stream=None):
+        """Gradient of sum(dlogits * logits) w.r.t. the interaction-network
+        parameters (blob order from the node encoder on) for the last training
+        forward of this context."""
+        _need(dlogits, torch.float32, "dlogits", self.device)
+        if dparams is None:
+            dparams = torch.empty(self.gnn_param_count, dtype=torch.float32, device=self.device)
+        _need(dparams, torch.float32, "dparams", self.device)
+        self._check(lib().etx_gnn_backward(self._h, _ptr(dlogits), _ptr(dparams), _stream(stream)))
+        return dparams
+
+    def weighted_bce(self, logits, targets, edge_offsets, pos_weight: float = 10.0, stream=None):
+        """(loss [1], dlogits [len(logits)]) of the class-weighted BCE."""
+        dev = self.device
+        _need(logits, torch.float32, "logits", dev)
+        _need(targets, torch.float32, "targets", dev)
+        _need(edge_offsets, torch.int32, "edge_offsets", dev)
+        loss = torch.empty(1, dtype=torch.float32, device=dev)
+        dlogits = torch.zeros_like(logits)
+        self._check(lib().etx_weighted_bce(self._h, _ptr(logits), _ptr(targets), _ptr(edge_offsets),
+                                           edge_offsets.shape[0] - 1, float(pos_weight), _ptr(loss),
+                                           _ptr(dlogits), _stream(stream)))
+        return loss, dlogits
+
+    def adam_step(self, params, grads, m, v, step: int, lr: float = 1e-3, beta1: float = 0.9,
+                  beta2: float = 0.999, eps: float = 1e-8, stream=None):
+        for t, n in ((params, "params"), (grads, "grads"), (m, "m"), (v, "v")):
+            _need(t, torch.float32, n, self.device)
+        self._check(lib().etx_adam_step(self._h, _ptr(params), _ptr(grads), _ptr(m), _ptr(v),
+                                        params.numel(), float(lr), float(beta1), float(beta2),
+                                        float(eps), int(step), _stream(stream)))
 
     def edges_to_tracks(self, src, dst, logits, threshold_logit: float, edge_offsets, hit_offsets,
                         min_hits: int = 3, labels=None, n_tracks=None, stream=None):

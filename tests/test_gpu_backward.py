@@ -1,0 +1,161 @@
+"""Training path on the GPU: weighted BCE, hand-written backward and Adam,
+checked against the FP64 oracle (its gradient and central finite
+differences) and torch's Adam."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import etx_oracle as O
+from velo_synth import (WORKLOADS, ModelConfig, global_particle_ids, make_batch, make_weights,
+                        pack_blob, truth_edge_labels, unpack_blob, blob_layout)
+
+pytestmark = pytest.mark.gpu
+GRAD_RTOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def etx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2407_12119_gb300 import build as b
+    b.build()
+    from paper_2407_12119_gb300 import etx as m
+    return m
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def problem(H, L, n_events, seed=0, perturb=0.3):
+    cfg = ModelConfig(emb_widths=(3, 32, 32, 4), hidden=H, n_iters=L, radius=1.5, k_max=16)
+    wl = WORKLOADS["plain"]
+    b = make_batch(wl.recipe, n_events, 5000 + seed)
+    W = make_weights(cfg, wl.calibration(), seed=seed, perturb=perturb)
+    emb = O.embed(W, 3, b.x, b.y, b.z)
+    s, d, eo = O.build_graph(emb, b.plane, b.hit_offsets, cfg.radius, cfg.k_max)
+    y = truth_edge_labels(global_particle_ids(b), b.plane, s, d)
+    return cfg, b, W, s, d, eo, y
+
+
+def gnn_names(cfg):
+    names = [n for n, _ in blob_layout(cfg)]
+    return names[names.index("node_enc.W1"):]
+
+
+def gpu_grads(etx, cfg, b, W, s, d, eo, y, dtype="f32"):
+    ctx = etx.Context(cfg, b.n_events, b.n_hits, max(s.size, 1), train=True)
+    ctx.load_weights(pack_blob(cfg, W))
+    x, yy, z = cuda(b.x), cuda(b.y), cuda(b.z)
+    st, dt, eot = cuda(s.astype(np.int32)), cuda(d.astype(np.int32)), cuda(eo.astype(np.int32))
+    logits = ctx.gnn_forward(x, yy, z, st, dt, eot, dtype=dtype)
+    loss, dl = ctx.weighted_bce(logits, cuda(y.astype(np.float32)), eot, 10.0)
+    g = ctx.gnn_backward(dl)
+    ctx.sync()
+    flat = g.cpu().numpy().astype(np.float64)
+    out, o = {}, 0
+    shapes = dict(blob_layout(cfg))
+    for n in gnn_names(cfg):
+        k = int(np.prod(shapes[n]))
+        out[n] = flat[o:o + k].reshape(shapes[n])
+        o += k
+    return float(loss.item()), out, logits.cpu().numpy()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-12)
+
+
+@pytest.mark.parametrize("H,L,n_events", [(16, 2, 1), (32, 3, 2), (128, 2, 2)])
+def test_backward_matches_oracle_gradient(etx, H, L, n_events):
+    cfg, b, W, s, d, eo, y = problem(H, L, n_events)
+    cache = {}
+    z = O.gnn_forward(W, L, b.x, b.y, b.z, s, d, cache)
+    loss_ref, dz = O.weighted_bce(z, y, 10.0)
+    ref = O.gnn_backward(W, cache, dz)
+    loss, g, _ = gpu_grads(etx, cfg, b, W, s, d, eo, y)
+    assert abs(loss - loss_ref) <= 1e-5 * max(1.0, abs(loss_ref))
+    worst = max((rel(g[n], ref[n]), n) for n in ref)
+    print(f"H={H} L={L}: E={s.size}, worst per-tensor relative L2 {worst[0]:.2e} ({worst[1]})")
+    assert worst[0] <= GRAD_RTOL, worst
+
+
+def test_backward_matches_finite_differences(etx):
+    # FP64 central differences (h = 1e-6) of the oracle loss on a 1-event,
+    # hidden-16 copy, against the GPU gradient
+    cfg, b, W, s, d, eo, y = problem(16, 2, 1, seed=3)
+    _, g, _ = gpu_grads(etx, cfg, b, W, s, d, eo, y)
+    Wd = {k: np.asarray(v, np.float64) for k, v in W.items()}
+    rng = np.random.default_rng(1)
+    h = 1e-6
+    for name in ["node_enc.W1", "node_enc.b2", "edge_enc.W1", "node0.W1", "node1.g1", "edge0.W2",
+                 "edge1.be2", "cls.W1", "cls.W2", "cls.b2"]:
+        flat = Wd[name].reshape(-1)
+        idx = rng.choice(flat.size, size=min(5, flat.size), replace=False)
+        fd = []
+        for i in idx:
+            old = flat[i]
+            flat[i] = old + h
+            lp, _ = O.weighted_bce(O.gnn_forward(Wd, 2, b.x, b.y, b.z, s, d), y)
+            flat[i] = old - h
+            lm, _ = O.weighted_bce(O.gnn_forward(Wd, 2, b.x, b.y, b.z, s, d), y)
+            flat[i] = old
+            fd.append((lp - lm) / (2 * h))
+        fd = np.array(fd)
+        got = g[name].reshape(-1)[idx]
+        assert rel(got, fd) <= GRAD_RTOL or np.abs(got - fd).max() <= 1e-7, (name, got, fd)
+
+
+def test_adam_matches_torch(etx):
+    cfg = WORKLOADS["plain"].model
+    ctx = etx.Context(cfg, 1, 16, 16)
+    rng = np.random.default_rng(2)
+    p0 = rng.normal(size=1000).astype(np.float32)
+    p = cuda(p0.copy())
+    m, v = torch.zeros_like(p), torch.zeros_like(p)
+    ref = torch.nn.Parameter(torch.from_numpy(p0.copy()))
+    opt = torch.optim.Adam([ref], lr=1e-3, betas=(0.9, 0.999), eps=1e-8)
+    for t in range(1, 4):
+        gr = rng.normal(size=1000).astype(np.float32)
+        ctx.adam_step(p, cuda(gr), m, v, t)
+        ref.grad = torch.from_numpy(gr)
+        opt.step()
+    ctx.sync()
+    np.testing.assert_allclose(p.cpu().numpy(), ref.detach().numpy(), rtol=1e-5, atol=1e-6)
+
+
+def test_training_steps_reduce_the_loss(etx):
+    from paper_2407_12119_gb300.train import Trainer
+    wl = WORKLOADS["train64"]
+    cfg = wl.model
+    b = wl.batch(8)
+    W = wl.weights()
+    emb = O.embed(W, 3, b.x, b.y, b.z)
+    s, d, eo = O.build_graph(emb, b.plane, b.hit_offsets, cfg.radius, cfg.k_max)
+    y = truth_edge_labels(global_particle_ids(b), b.plane, s, d).astype(np.float32)
+    tr = Trainer(cfg, pack_blob(cfg, W), b.n_events, b.n_hits, s.size, dtype="bf16")
+    args = [cuda(a) for a in (b.x, b.y, b.z, s.astype(np.int32), d.astype(np.int32),
+                              eo.astype(np.int32), y)]
+    losses = [float(tr.step(*args).item()) for _ in range(8)]
+    tr.ctx.sync()
+    print("losses", [round(l, 4) for l in losses])
+    assert losses[-1] < losses[0]
+
+
+def test_autograd_function_matches_backward(etx):
+    from paper_2407_12119_gb300.train import InteractionNetworkFn
+    cfg, b, W, s, d, eo, y = problem(32, 2, 1)
+    ctx = etx.Context(cfg, b.n_events, b.n_hits, s.size, train=True)
+    blob = pack_blob(cfg, W)
+    ctx.load_weights(blob)
+    theta = cuda(blob[blob.size - ctx.gnn_param_count:]).requires_grad_(True)
+    args = (cuda(b.x), cuda(b.y), cuda(b.z), cuda(s.astype(np.int32)), cuda(d.astype(np.int32)),
+            cuda(eo.astype(np.int32)))
+    logits = InteractionNetworkFn.apply(theta, ctx, *args, "f32")
+    w = torch.linspace(-1, 1, logits.numel(), device="cuda")
+    (logits * w).sum().backward()
+    cache = {}
+    O.gnn_forward(W, 2, b.x, b.y, b.z, s, d, cache)
+    ref = O.gnn_backward(W, cache, w.cpu().numpy().astype(np.float64))
+    flat = np.concatenate([ref[n].reshape(-1) for n in gnn_names(cfg)])
+    assert rel(theta.grad.cpu().numpy().astype(np.float64), flat) <= GRAD_RTOL
