@@ -162,19 +162,48 @@ def round_bf16(a):
     return r.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
+def round_e4m3(a):
+    """Round to the FP8 e4m3 format (1 sign, 4 exponent bits with bias 7, 3
+    mantissa bits, no infinities, largest finite 448): first to FP32, then to
+    the nearest e4m3 value, ties to even; magnitudes above 448 saturate."""
+    x = np.asarray(a, np.float32).astype(np.float64)
+    ax = np.abs(x)
+    _, e = np.frexp(ax)                        # ax in [2^(e-1), 2^e)
+    ex = np.maximum(e - 1, -6)                 # subnormal spacing 2^-9 below 2^-6
+    step = np.ldexp(1.0, ex - 3)
+    r = np.minimum(np.round(ax / step) * step, 448.0)   # np.round: half to even
+    return np.copysign(r, x)
+
+
+def quant_weight_e4m3(W):
+    """Per-tensor scaled e4m3 weights: s = amax|W| / 448 (FP32), W ~ e4m3(W / s) * s."""
+    W32 = np.asarray(W, np.float32)
+    amax = np.float32(np.abs(W32).max()) if W32.size else np.float32(0)
+    s = np.float32(amax / np.float32(448.0)) if amax > 0 else np.float32(1.0)
+    return round_e4m3(W32 / s) * float(s)
+
+
 def _identity(a):
     return a
 
 
-def mlp_block(X, w, prefix, cache=None, op=_identity):
+GEMM_READINGS = {
+    "fp64": (_identity, _identity),
+    "bf16": (round_bf16, round_bf16),
+    "fp8": (round_e4m3, quant_weight_e4m3),
+}
+
+
+def mlp_block(X, w, prefix, cache=None, op=_identity, op_w=None):
     """Lin -> LN -> ReLU -> Lin -> LN -> ReLU on rows of X.  ``op`` is applied
-    to both operands of each matrix product (identity: exact FP64;
-    ``round_bf16``: the BF16-operand, wide-accumulator reading)."""
+    to the activation operand and ``op_w`` (default ``op``) to the weight
+    operand of each matrix product (identity: exact FP64)."""
+    op_w = op if op_w is None else op_w
     f = lambda k: w[f"{prefix}.{k}"].astype(np.float64)
-    a1 = op(X) @ op(f("W1")).T + f("b1")
+    a1 = op(X) @ op_w(w[f"{prefix}.W1"]).T + f("b1")
     y1, n1, s1 = layer_norm(a1, f("g1"), f("be1"))
     r1 = np.maximum(y1, 0.0)
-    a2 = op(r1) @ op(f("W2")).T + f("b2")
+    a2 = op(r1) @ op_w(w[f"{prefix}.W2"]).T + f("b2")
     y2, n2, s2 = layer_norm(a2, f("g2"), f("be2"))
     out = np.maximum(y2, 0.0)
     if cache is not None:
@@ -199,8 +228,10 @@ def gnn_forward(weights, n_iters, x, y, z, src, dst, cache=None, gemm="fp64"):
     matrix product with a hidden-width input (edge encoder, node and edge
     networks, first classifier layer) are rounded to BF16 and the products
     accumulate exactly; the node encoder (3 inputs), LayerNorm, residual adds,
-    message sums and the last classifier dot product stay exact."""
-    op = {"fp64": _identity, "bf16": round_bf16}[gemm]
+    message sums and the last classifier dot product stay exact.
+    gemm="fp8" rounds those activation operands to e4m3 (scale 1) and the
+    weights to per-tensor scaled e4m3 (``quant_weight_e4m3``)."""
+    op, op_w = GEMM_READINGS[gemm]
     src = np.asarray(src, np.int64)
     dst = np.asarray(dst, np.int64)
     N = np.asarray(x).shape[0]
@@ -208,14 +239,14 @@ def gnn_forward(weights, n_iters, x, y, z, src, dst, cache=None, gemm="fp64"):
                               np.asarray(z, np.float64)], axis=1),
                     weights["gnn_mu"], weights["gnn_sigma"])
     h = mlp_block(xin, weights, "node_enc", cache)
-    e = mlp_block(np.concatenate([h[src], h[dst]], axis=1), weights, "edge_enc", cache, op)
+    e = mlp_block(np.concatenate([h[src], h[dst]], axis=1), weights, "edge_enc", cache, op, op_w)
     for k in range(n_iters):
         m = messages(e, src, dst, N)
-        h = h + mlp_block(np.concatenate([h, m], axis=1), weights, f"node{k}", cache, op)
+        h = h + mlp_block(np.concatenate([h, m], axis=1), weights, f"node{k}", cache, op, op_w)
         e = e + mlp_block(np.concatenate([e, h[src], h[dst]], axis=1), weights, f"edge{k}", cache,
-                          op)
+                          op, op_w)
     W1 = weights["cls.W1"].astype(np.float64)
-    a1 = op(e) @ op(W1).T + weights["cls.b1"].astype(np.float64)
+    a1 = op(e) @ op_w(weights["cls.W1"]).T + weights["cls.b1"].astype(np.float64)
     y1, n1, s1 = layer_norm(a1, weights["cls.g1"].astype(np.float64),
                             weights["cls.be1"].astype(np.float64))
     r1 = np.maximum(y1, 0.0)

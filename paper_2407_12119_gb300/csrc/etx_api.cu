@@ -1,5 +1,7 @@
 // C ABI of libetx: context lifetime, weight repacking, argument checks and
 // the launch sequence of each pipeline step.  See include/etx.h.
+#include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -110,6 +112,50 @@ void append_bf16_image(const float* W, int n_out, int k, std::vector<uint8_t>& i
           const size_t off = at + (size_t)c * n_out * 128 + (size_t)n * 128 + ((u ^ (n & 7)) * 16) + 2 * j;
           img[off] = static_cast<uint8_t>(b & 0xff);
           img[off + 1] = static_cast<uint8_t>(b >> 8);
+        }
+}
+
+// e4m3: 1 sign bit, 4 exponent bits (bias 7), 3 mantissa bits, no infinities,
+// largest finite value 448.  Round to nearest, ties to even; magnitudes that
+// round above 448 saturate to 448.
+uint8_t f32_to_e4m3(float f) {
+  const uint8_t sign = std::signbit(f) ? 0x80 : 0x00;
+  if (std::isnan(f)) return 0x7F;
+  const float a = std::fabs(f);
+  if (a == 0.f) return sign;
+  int e = 0;
+  (void)std::frexp(a, &e);                 // a in [2^(e-1), 2^e)
+  const int ex = std::max(e - 1, -6);      // below 2^-6 the spacing stays 2^-9
+  const float step = std::ldexp(1.0f, ex - 3);
+  const float r = std::nearbyint(a / step) * step;
+  if (r >= 448.f) return sign | 0x7E;
+  if (r < std::ldexp(1.0f, -6)) return sign | static_cast<uint8_t>(r / std::ldexp(1.0f, -9));
+  int e2 = 0;
+  const float m2 = std::frexp(r, &e2);     // r = m2 2^e2, m2 in [0.5, 1)
+  const int E = e2 - 1 + 7;
+  const int M = static_cast<int>((m2 * 2.f - 1.f) * 8.f);
+  return sign | static_cast<uint8_t>((E << 3) | M);
+}
+
+// Per-tensor scale amax / 448 (1 for an all-zero tensor).
+float e4m3_scale(const float* W, size_t n) {
+  float m = 0.f;
+  for (size_t i = 0; i < n; ++i) m = std::max(m, std::fabs(W[i]));
+  return m > 0.f ? m / 448.0f : 1.0f;
+}
+
+// e4m3 image of W[n_out][k] / s: 128-column chunks, 16-byte unit u of row n at
+// unit position u ^ (n % 8) (the 128-byte-swizzle K-major operand layout).
+void append_e4m3_image(const float* W, int n_out, int k, float s, std::vector<uint8_t>& img) {
+  const size_t at = img.size();
+  img.resize(at + (size_t)n_out * k);
+  for (int c = 0; c < k / 128; ++c)
+    for (int n = 0; n < n_out; ++n)
+      for (int u = 0; u < 8; ++u)
+        for (int j = 0; j < 16; ++j) {
+          const float q = W[(size_t)n * k + 128 * c + 16 * u + j] / s;
+          img[at + (size_t)c * n_out * 128 + (size_t)n * 128 + ((u ^ (n & 7)) * 16) + j] =
+              f32_to_e4m3(q);
         }
 }
 
@@ -343,12 +389,17 @@ etx_status etx_load_weights(etx_ctx* ctx, const float* blob, int64_t n_floats) {
   // --- BF16 tensor-core operand images (hidden == 128) ------------------------
   if (ctx->w_tc) cudaFree(ctx->w_tc);
   ctx->w_tc = nullptr;
-  std::vector<size_t> tc_off;
+  std::vector<size_t> tc_off, f8_off;
+  std::vector<float> f8_scale;
   if (H == 128) {
-    std::vector<uint8_t> img;
+    std::vector<uint8_t> img, img8;
     auto push_img = [&](const Pending& q) {
       tc_off.push_back(img.size());
       append_bf16_image(q.w, q.n, q.k_in, img);
+      const float sc = e4m3_scale(q.w, (size_t)q.n * q.k_in);
+      f8_off.push_back(img8.size());
+      f8_scale.push_back(sc);
+      append_e4m3_image(q.w, q.n, q.k_in, sc, img8);
     };
     push_img(edge_enc.l1);
     push_img(edge_enc.l2);
@@ -359,6 +410,9 @@ etx_status etx_load_weights(etx_ctx* ctx, const float* blob, int64_t n_floats) {
       push_img(edge[k].l2);
     }
     push_img(cl1);
+    const size_t b16 = img.size();
+    img.insert(img.end(), img8.begin(), img8.end());  // FP8 images after the BF16 ones
+    for (auto& o : f8_off) o += b16;
     if (dmalloc(ctx, &ctx->w_tc, img.size(), "tensor-core weights") != ETX_OK) return ETX_ERR_CUDA;
     e = cudaMemcpy(ctx->w_tc, img.data(), img.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor-core weight upload");
@@ -397,19 +451,26 @@ etx_status etx_load_weights(etx_ctx* ctx, const float* blob, int64_t n_floats) {
   ctx->w.cls.b2 = base + cb2;
   if (H == 128) {
     size_t i = 0;
-    auto next = [&]() { return ctx->w_tc + tc_off[i++]; };
-    ctx->w.edge_enc_tc.w1 = next();
-    ctx->w.edge_enc_tc.w2 = next();
+    // fills (w, w8, scale) of the next Linear in image order
+    auto next = [&](const uint8_t** w, const uint8_t** w8, float* sc) {
+      *w = ctx->w_tc + tc_off[i];
+      *w8 = ctx->w_tc + f8_off[i];
+      *sc = f8_scale[i];
+      ++i;
+    };
+    auto block = [&](BlockTC& t) {
+      next(&t.w1, &t.w1f8, &t.s1);
+      next(&t.w2, &t.w2f8, &t.s2);
+    };
+    block(ctx->w.edge_enc_tc);
     for (int k = 0; k < c.n_iters; ++k) {
       BlockTC nb, eb;
-      nb.w1 = next();
-      nb.w2 = next();
-      eb.w1 = next();
-      eb.w2 = next();
+      block(nb);
+      block(eb);
       ctx->w.node_tc.push_back(nb);
       ctx->w.edge_tc.push_back(eb);
     }
-    ctx->w.cls_tc.w1 = next();
+    next(&ctx->w.cls_tc.w1, &ctx->w.cls_tc.w1f8, &ctx->w.cls_tc.s1);
     ctx->w.has_tc = true;
   }
   ctx->gnn_blob_offset = gnn_offset;
@@ -481,8 +542,9 @@ etx_status etx_gnn_forward(etx_ctx* ctx, const float* x, const float* y, const f
   if (n_hits < 0 || n_hits > ctx->cfg.max_hits) return fail(ctx, ETX_ERR_CAPACITY, "n_hits exceeds the context capacity");
   if (!edge_offsets || !src || !dst || !logits) return fail(ctx, ETX_ERR_ARG, "NULL edge array");
   if (n_hits > 0 && (!x || !y || !z)) return fail(ctx, ETX_ERR_ARG, "NULL hit array");
-  if (dtype != ETX_F32 && dtype != ETX_BF16) return fail(ctx, ETX_ERR_UNSUPPORTED, "dtype not built yet");
-  if (dtype == ETX_BF16 && !ctx->w.has_tc)
+  if (dtype != ETX_F32 && dtype != ETX_BF16 && dtype != ETX_FP8E4M3)
+    return fail(ctx, ETX_ERR_ARG, "unknown dtype");
+  if (dtype != ETX_F32 && !ctx->w.has_tc)
     return fail(ctx, ETX_ERR_UNSUPPORTED, "the tensor-core path needs hidden == 128");
   if (n_hits == 0) return ETX_OK;  // no hits, hence no edges: nothing to compute
   cudaSetDevice(ctx->device);
@@ -491,7 +553,7 @@ etx_status etx_gnn_forward(etx_ctx* ctx, const float* x, const float* y, const f
          ctx->n_edges, ctx->d_err);
   cudaError_t e = launch_edge_index(ctx, n_hits, src, dst, ctx->n_edges, s);
   if (e == cudaSuccess)
-    e = launch_gnn_forward(ctx, x, y, z, n_hits, src, dst, ctx->n_edges, logits, dtype == ETX_BF16, s);
+    e = launch_gnn_forward(ctx, x, y, z, n_hits, src, dst, ctx->n_edges, logits, dtype, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "etx_gnn_forward launch");
   if (ctx->cfg.train) {
     ctx->fwd_x = x;

@@ -48,9 +48,14 @@ struct ClassifierF32 {
 // Tensor-core copies of a block's two Linear weights: BF16, W[n][k] split in
 // 64-column chunks of 128 rows x 128 bytes, each laid out exactly as the
 // K-major 128-byte-swizzle shared-memory operand (16 KB per chunk).
+// FP8 (e4m3) images use the same layout with 128 K columns per chunk and hold
+// W / s rounded to e4m3, s = amax(W) / 448 per tensor (the epilogue rescales).
 struct BlockTC {
   const uint8_t* w1 = nullptr;
   const uint8_t* w2 = nullptr;
+  const uint8_t* w1f8 = nullptr;
+  const uint8_t* w2f8 = nullptr;
+  float s1 = 1.f, s2 = 1.f;
 };
 
 struct Weights {
@@ -148,10 +153,11 @@ cudaError_t launch_build_graph(etx_ctx* ctx, const float* emb, const int8_t* pla
                                int64_t edge_capacity, int32_t* edge_offsets, cudaStream_t s);
 
 // gnn_f32.cu
-// tc: BF16 tensor-core MLP blocks (hidden == 128), else FP32 SIMT
+// dtype ETX_BF16 / ETX_FP8E4M3: tensor-core MLP blocks (hidden == 128), ETX_F32: SIMT
 cudaError_t launch_gnn_forward(etx_ctx* ctx, const float* x, const float* y, const float* z,
                                int64_t n_hits, const int32_t* src, const int32_t* dst,
-                               const int32_t* n_edges_dev, float* logits, bool tc, cudaStream_t s);
+                               const int32_t* n_edges_dev, float* logits, etx_dtype dtype,
+                               cudaStream_t s);
 cudaError_t launch_edge_index(etx_ctx* ctx, int64_t n_hits, const int32_t* src,
                               const int32_t* dst, const int32_t* n_edges_dev, cudaStream_t s);
 // messages of edge features e (uses the context's edge index structures)
@@ -168,13 +174,15 @@ cudaError_t launch_adam(etx_ctx* ctx, float* p, const float* g, float* m, float*
                         float lr, float b1, float b2, float eps, int64_t step, cudaStream_t s);
 
 // gnn_tc.cu (hidden == 128 only)
+// f8: e4m3 operands (kind::f8f6f4), else BF16 (kind::f16)
 cudaError_t launch_edge_encoder_tc(etx_ctx* ctx, int64_t N, const int32_t* src, const int32_t* dst,
-                                   const int32_t* n_edges_dev, cudaStream_t s);
-cudaError_t launch_node_update_tc(etx_ctx* ctx, int k, int64_t N, cudaStream_t s);
+                                   const int32_t* n_edges_dev, bool f8, cudaStream_t s);
+cudaError_t launch_node_update_tc(etx_ctx* ctx, int k, int64_t N, bool f8, cudaStream_t s);
 cudaError_t launch_edge_update_tc(etx_ctx* ctx, int k, int64_t N, const int32_t* src,
-                                  const int32_t* dst, const int32_t* n_edges_dev, cudaStream_t s);
+                                  const int32_t* dst, const int32_t* n_edges_dev, bool f8,
+                                  cudaStream_t s);
 cudaError_t launch_classifier_tc(etx_ctx* ctx, int64_t N, const int32_t* n_edges_dev, float* logits,
-                                 cudaStream_t s);
+                                 bool f8, cudaStream_t s);
 
 // cc.cu
 cudaError_t launch_edges_to_tracks(etx_ctx* ctx, const int32_t* src, const int32_t* dst,

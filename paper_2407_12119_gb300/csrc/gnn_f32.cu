@@ -272,7 +272,9 @@ void launch_mlp(etx_ctx* ctx, const MlpArgs& a, int64_t max_rows, cudaStream_t s
 template <int H>
 cudaError_t forward(etx_ctx* ctx, const float* x, const float* y, const float* z, int64_t N,
                     const int32_t* src, const int32_t* dst, const int32_t* n_edges_dev,
-                    float* logits, bool tc, cudaStream_t s) {
+                    float* logits, etx_dtype dtype, cudaStream_t s) {
+  const bool tc = dtype != ETX_F32;
+  const bool f8 = dtype == ETX_FP8E4M3;
   const int64_t Ecap = ctx->cfg.max_edges;
   MlpArgs a{};
   a.n_rows = N;
@@ -295,7 +297,7 @@ cudaError_t forward(etx_ctx* ctx, const float* x, const float* y, const float* z
   a.blk = ctx->w.node_enc;
   launch_mlp<H, NODE_ENC>(ctx, a, N, s);
   if (tc) {
-    chain(launch_edge_encoder_tc(ctx, N, src, dst, n_edges_dev, s));
+    chain(launch_edge_encoder_tc(ctx, N, src, dst, n_edges_dev, f8, s));
   } else {
     a.blk = ctx->w.edge_enc;
     launch_mlp<H, EDGE_ENC>(ctx, a, Ecap, s);
@@ -308,8 +310,8 @@ cudaError_t forward(etx_ctx* ctx, const float* x, const float* y, const float* z
       launch(ctx, "gnn_messages", k_messages<H>, msg_grid, 256, 0, s, ctx->e, ctx->out_off,
              ctx->in_off, ctx->perm_in, n_edges_dev, (int)N, ctx->m);
     if (tc) {
-      chain(launch_node_update_tc(ctx, k, N, s));
-      chain(launch_edge_update_tc(ctx, k, N, src, dst, n_edges_dev, s));
+      chain(launch_node_update_tc(ctx, k, N, f8, s));
+      chain(launch_edge_update_tc(ctx, k, N, src, dst, n_edges_dev, f8, s));
     } else {
       a.blk = ctx->w.node[k];
       launch_mlp<H, NODE_UPD>(ctx, a, N, s);
@@ -319,7 +321,7 @@ cudaError_t forward(etx_ctx* ctx, const float* x, const float* y, const float* z
     save(k + 1);
   }
   if (tc) {
-    chain(launch_classifier_tc(ctx, N, n_edges_dev, logits, s));
+    chain(launch_classifier_tc(ctx, N, n_edges_dev, logits, f8, s));
   } else {
     a.cls = ctx->w.cls;
     launch_mlp<H, CLS>(ctx, a, Ecap, s);
@@ -369,12 +371,13 @@ cudaError_t launch_edge_index(etx_ctx* ctx, int64_t N, const int32_t* src, const
 
 cudaError_t launch_gnn_forward(etx_ctx* ctx, const float* x, const float* y, const float* z,
                                int64_t n_hits, const int32_t* src, const int32_t* dst,
-                               const int32_t* n_edges_dev, float* logits, bool tc, cudaStream_t s) {
+                               const int32_t* n_edges_dev, float* logits, etx_dtype dtype,
+                               cudaStream_t s) {
   switch (ctx->cfg.hidden) {
-    case 16: return forward<16>(ctx, x, y, z, n_hits, src, dst, n_edges_dev, logits, false, s);
-    case 32: return forward<32>(ctx, x, y, z, n_hits, src, dst, n_edges_dev, logits, false, s);
-    case 64: return forward<64>(ctx, x, y, z, n_hits, src, dst, n_edges_dev, logits, false, s);
-    case 128: return forward<128>(ctx, x, y, z, n_hits, src, dst, n_edges_dev, logits, tc, s);
+    case 16: return forward<16>(ctx, x, y, z, n_hits, src, dst, n_edges_dev, logits, ETX_F32, s);
+    case 32: return forward<32>(ctx, x, y, z, n_hits, src, dst, n_edges_dev, logits, ETX_F32, s);
+    case 64: return forward<64>(ctx, x, y, z, n_hits, src, dst, n_edges_dev, logits, ETX_F32, s);
+    case 128: return forward<128>(ctx, x, y, z, n_hits, src, dst, n_edges_dev, logits, dtype, s);
     default: return cudaErrorInvalidValue;
   }
 }

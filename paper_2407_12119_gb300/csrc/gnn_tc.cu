@@ -23,6 +23,7 @@
 // arrivals otherwise).  Every wait is bounded; a timeout records
 // ETX_ERR_TIMEOUT, raises a shared abort flag and every role stops.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "sm100.cuh"
 
@@ -33,15 +34,15 @@ using namespace sm100;
 
 constexpr int H = 128;
 constexpr int TM = 128;                  // rows per tile
-constexpr int KCH = 64;                  // K columns per shared-memory chunk
-constexpr int CHUNK = TM * KCH * 2;      // 16 KB per BF16 chunk
+constexpr int CHUNK = TM * 128;          // 16 KB operand chunk: 128 rows x 128 bytes
+constexpr int SUB = 64;                  // K columns a producer fetches per step (256 B FP32)
+constexpr int KSTEPS = 4;                // MMAs per chunk (32 bytes of K each)
 constexpr int NSTAGE = 3;                // A-operand ring slots
 constexpr int EPI_WARPS = 4, PROD_WARPS = 8;
 constexpr int MMA_WARP = EPI_WARPS + PROD_WARPS;
 constexpr int THREADS = 32 * (MMA_WARP + 1);  // 416
 constexpr int PROD_THREADS = 32 * PROD_WARPS;
 constexpr int EPI_THREADS = 32 * EPI_WARPS;
-constexpr uint32_t IDESC = idesc_bf16_f32<TM, H>();
 constexpr uint32_t TMEM_COLS = 512;      // D1 buffers at columns 0 and 128, D2 at 256
 
 enum TcMode { TC_EDGE_ENC = 0, TC_NODE_UPD = 1, TC_EDGE_UPD = 2, TC_CLS = 3 };
@@ -51,14 +52,27 @@ enum { B_W = 0, B_FULL = 1, B_EMPTY = B_FULL + NSTAGE, B_D1FULL = B_EMPTY + NSTA
        B_D1EMPTY = B_D1FULL + 2, B_A2FULL = B_D1EMPTY + 2, B_D2FULL = B_A2FULL + 1,
        N_BARS = B_D2FULL + 1 };
 
-template <int MODE>
+// Operand type: BF16 (2 bytes, 64 K columns per 128-byte row) or FP8 e4m3
+// (1 byte, 128 K columns per row).
+template <bool F8>
+struct Elt {
+  static constexpr int KCH = F8 ? 128 : 64;   // K columns per chunk
+  static constexpr int SUBS = KCH / SUB;       // producer steps per chunk
+  static constexpr uint32_t IDESC = F8 ? idesc_e4m3_f32<TM, H>() : idesc_bf16_f32<TM, H>();
+};
+
+template <int MODE, bool F8>
 struct Cfg {
-  static constexpr int KC1 = MODE == TC_EDGE_ENC ? 4 : (MODE == TC_CLS ? 2 : 6);
+  static constexpr int KIN = MODE == TC_EDGE_ENC ? 2 * H : (MODE == TC_CLS ? H : 3 * H);
+  static constexpr int KC1 = KIN / Elt<F8>::KCH;     // chunks of the first GEMM
+  static constexpr int KS = KIN / SUB;               // producer steps per tile
+  static constexpr int C2 = H / Elt<F8>::KCH;        // chunks of the second GEMM
   static constexpr bool G2 = MODE != TC_CLS;
   static constexpr int OFF_W1 = 0;
   static constexpr int OFF_W2 = OFF_W1 + KC1 * CHUNK;
-  static constexpr int OFF_A = OFF_W2 + (G2 ? 2 * CHUNK : 0);
+  static constexpr int OFF_A = OFF_W2 + (G2 ? C2 * CHUNK : 0);
   static constexpr int OFF_A2 = OFF_A + NSTAGE * CHUNK;
+  // A2 holds the second GEMM's operand, then stages 128 x 64 FP32 outputs (32 KB)
   static constexpr int OFF_PAR = OFF_A2 + (G2 ? 2 * CHUNK : 0);     // 7 x 128 floats
   static constexpr int OFF_BAR = OFF_PAR + 7 * H * 4;
   static constexpr int OFF_MISC = OFF_BAR + 8 * N_BARS;              // tmem addr, abort flag
@@ -75,13 +89,21 @@ struct TcArgs {
   float* e;
   float* h_out;
   float* logits;
-  const uint8_t* w1;  // BF16 swizzled image, KC1 chunks
-  const uint8_t* w2;  // BF16 swizzled image, 2 chunks
+  const uint8_t* w1;  // swizzled operand image of W1 (KC1 chunks)
+  const uint8_t* w2;  // swizzled operand image of W2 (C2 chunks)
+  float ws1, ws2;     // per-tensor weight scales (1 for BF16)
   const float *b1, *g1, *be1, *b2, *g2, *be2;
   const float* wcls;  // classifier last Linear [H]
   const float* bcls;  // [1]
   int* err;
 };
+
+// Four values to e4m3 (saturating), first value in the lowest byte.
+__device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d) {
+  const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+  const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+  return lo | (hi << 16);
+}
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   __nv_bfloat162 t = __floats2bfloat162_rn(a, b);
@@ -109,24 +131,26 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, in
   return false;
 }
 
+// Source of columns [col0, col0 + 64) of block-input row g.
 template <int MODE>
-__device__ __forceinline__ const float* chunk_src(const TcArgs& a, int c, int64_t g, int s, int d) {
+__device__ __forceinline__ const float* chunk_src(const TcArgs& a, int col0, int64_t g, int s, int d) {
   if constexpr (MODE == TC_EDGE_ENC) {
-    return c < 2 ? a.h + (int64_t)s * H + KCH * c : a.h + (int64_t)d * H + KCH * (c - 2);
+    return col0 < H ? a.h + (int64_t)s * H + col0 : a.h + (int64_t)d * H + (col0 - H);
   } else if constexpr (MODE == TC_NODE_UPD) {
-    return c < 2 ? a.h + g * H + KCH * c : a.m + g * 2 * H + KCH * (c - 2);
+    return col0 < H ? a.h + g * H + col0 : a.m + g * 2 * H + (col0 - H);
   } else if constexpr (MODE == TC_EDGE_UPD) {
-    return c < 2 ? a.e + g * H + KCH * c
-                 : (c < 4 ? a.h + (int64_t)s * H + KCH * (c - 2) : a.h + (int64_t)d * H + KCH * (c - 4));
+    return col0 < H ? a.e + g * H + col0
+                    : (col0 < 2 * H ? a.h + (int64_t)s * H + (col0 - H)
+                                    : a.h + (int64_t)d * H + (col0 - 2 * H));
   } else {
-    return a.e + g * H + KCH * c;
+    return a.e + g * H + col0;
   }
 }
 
-// Row statistics of x_j = acc_j + b_j over the 128 accumulator columns of
-// this thread's TMEM lane (shifted sums: shift = first value).
-__device__ __forceinline__ void row_stats(uint32_t taddr, const float* __restrict__ b, float& mean,
-                                          float& rstd) {
+// Row statistics of x_j = sc * acc_j + b_j over the 128 accumulator columns
+// of this thread's TMEM lane (shifted sums: shift = first value).
+__device__ __forceinline__ void row_stats(uint32_t taddr, const float* __restrict__ b, float sc,
+                                          float& mean, float& rstd) {
   float v[32];
   float shift = 0.f, s = 0.f, ss = 0.f;
 #pragma unroll
@@ -135,7 +159,8 @@ __device__ __forceinline__ void row_stats(uint32_t taddr, const float* __restric
 #pragma unroll
     for (int j = 0; j < 32; j += 4) {
       const float4 bb = *reinterpret_cast<const float4*>(b + 32 * cc + j);
-      const float x0 = v[j] + bb.x, x1 = v[j + 1] + bb.y, x2 = v[j + 2] + bb.z, x3 = v[j + 3] + bb.w;
+      const float x0 = fmaf(v[j], sc, bb.x), x1 = fmaf(v[j + 1], sc, bb.y),
+                  x2 = fmaf(v[j + 2], sc, bb.z), x3 = fmaf(v[j + 3], sc, bb.w);
       if (cc == 0 && j == 0) shift = x0;
       const float d0 = x0 - shift, d1 = x1 - shift, d2 = x2 - shift, d3 = x3 - shift;
       s += (d0 + d1) + (d2 + d3);
@@ -151,23 +176,24 @@ __device__ __forceinline__ void row_stats(uint32_t taddr, const float* __restric
 // 32 normalised, ReLU'd values of columns [32 cc, 32 cc + 32).
 __device__ __forceinline__ void row_norm32(uint32_t taddr, int cc, const float* __restrict__ b,
                                            const float* __restrict__ g, const float* __restrict__ be,
-                                           float mean, float rstd, float (&y)[32]) {
+                                           float sc, float mean, float rstd, float (&y)[32]) {
   tmem_ld32_wait(taddr + 32 * cc, y);
 #pragma unroll
   for (int j = 0; j < 32; j += 4) {
     const float4 bb = *reinterpret_cast<const float4*>(b + 32 * cc + j);
     const float4 gg = *reinterpret_cast<const float4*>(g + 32 * cc + j);
     const float4 ee = *reinterpret_cast<const float4*>(be + 32 * cc + j);
-    y[j] = fmaxf((y[j] + bb.x - mean) * rstd * gg.x + ee.x, 0.f);
-    y[j + 1] = fmaxf((y[j + 1] + bb.y - mean) * rstd * gg.y + ee.y, 0.f);
-    y[j + 2] = fmaxf((y[j + 2] + bb.z - mean) * rstd * gg.z + ee.z, 0.f);
-    y[j + 3] = fmaxf((y[j + 3] + bb.w - mean) * rstd * gg.w + ee.w, 0.f);
+    y[j] = fmaxf((fmaf(y[j], sc, bb.x) - mean) * rstd * gg.x + ee.x, 0.f);
+    y[j + 1] = fmaxf((fmaf(y[j + 1], sc, bb.y) - mean) * rstd * gg.y + ee.y, 0.f);
+    y[j + 2] = fmaxf((fmaf(y[j + 2], sc, bb.z) - mean) * rstd * gg.z + ee.z, 0.f);
+    y[j + 3] = fmaxf((fmaf(y[j + 3], sc, bb.w) - mean) * rstd * gg.w + ee.w, 0.f);
   }
 }
 
-template <int MODE>
+template <int MODE, bool F8>
 __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
-  using C = Cfg<MODE>;
+  using C = Cfg<MODE, F8>;
+  using EL = Elt<F8>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -238,7 +264,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
     constexpr int RPT = TM / (PROD_THREADS / 8);  // rows per producer thread
     const int64_t my_tiles =
         n_tiles > blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    const int64_t total = my_tiles * C::KC1;
+    const int64_t total = my_tiles * C::KS;  // 64-column steps
     // gather indices of the tile being fetched, read when its first chunk is
     // fetched (chunks reach the same tile in order, two ahead of the stores)
     int sidx[RPT], didx[RPT];
@@ -246,8 +272,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
     for (int i = 0; i < RPT; ++i) sidx[i] = didx[i] = 0;
     auto fetch = [&](int64_t q, float4 (&f)[2 * RPT]) {
       if (q >= total) return;
-      const int64_t row0 = (blockIdx.x + (q / C::KC1) * gridDim.x) * TM;
-      const int c = (int)(q % C::KC1);
+      const int64_t row0 = (blockIdx.x + (q / C::KS) * gridDim.x) * TM;
+      const int c = (int)(q % C::KS);
       if constexpr (MODE == TC_EDGE_ENC || MODE == TC_EDGE_UPD) {
         if (c == 0) {
 #pragma unroll
@@ -262,7 +288,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
       for (int i = 0; i < RPT; ++i) {
         const int64_t gr = row0 + rbase + 32 * i;
         if (gr < n_rows) {
-          const float* p = chunk_src<MODE>(a, c, gr, sidx[i], didx[i]) + 4 * t8;
+          const float* p = chunk_src<MODE>(a, SUB * c, gr, sidx[i], didx[i]) + 4 * t8;
           f[2 * i] = *reinterpret_cast<const float4*>(p);
           f[2 * i + 1] = *reinterpret_cast<const float4*>(p + 32);
         } else {
@@ -272,9 +298,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
       }
     };
     auto store = [&](int64_t q, const float4 (&f)[2 * RPT]) {
-      const int slot = (int)(q % NSTAGE);
-      const uint32_t round = (uint32_t)(q / NSTAGE);
-      if (round > 0 && !wait_or_abort(&bars[B_EMPTY + slot], (round - 1) & 1, a.err, abort))
+      const int64_t j = q / EL::SUBS;            // ring chunk
+      const int hpart = (int)(q % EL::SUBS);     // which 64 columns of it
+      const int slot = (int)(j % NSTAGE);
+      const uint32_t round = (uint32_t)(j / NSTAGE);
+      if (hpart == 0 && round > 0 &&
+          !wait_or_abort(&bars[B_EMPTY + slot], (round - 1) & 1, a.err, abort))
         return false;
       const uint32_t dstc = smem_u32(sA + slot * CHUNK);
 #pragma unroll
@@ -283,14 +312,23 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
           const float4 v = f[2 * i + hh];
-          const uint32_t addr = dstc + sw128(r, 4 * hh + (t8 >> 1)) + 8 * (t8 & 1);
-          asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(pack_bf16(v.x, v.y)),
-                       "r"(pack_bf16(v.z, v.w))
-                       : "memory");
+          if constexpr (F8) {
+            // columns 64 hpart + 32 hh + 4 t8 .. +3: 16 values per 16-byte unit
+            const uint32_t addr = dstc + sw128(r, 4 * hpart + 2 * hh + (t8 >> 2)) + 4 * (t8 & 3);
+            asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr), "r"(pack_e4m3x4(v.x, v.y, v.z, v.w))
+                         : "memory");
+          } else {
+            const uint32_t addr = dstc + sw128(r, 4 * hh + (t8 >> 1)) + 8 * (t8 & 1);
+            asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(pack_bf16(v.x, v.y)),
+                         "r"(pack_bf16(v.z, v.w))
+                         : "memory");
+          }
         }
       }
-      fence_proxy_async();
-      mbar_arrive(&bars[B_FULL + slot]);
+      if (hpart == EL::SUBS - 1) {
+        fence_proxy_async();
+        mbar_arrive(&bars[B_FULL + slot]);
+      }
       return true;
     };
     float4 b0[2 * RPT], b1[2 * RPT], b2[2 * RPT];
@@ -309,12 +347,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
   } else if (warp == MMA_WARP) {
     // =========================== MMA issuer ================================
     if (lane == 0) {
-      const uint32_t wbytes = (C::KC1 + (C::G2 ? 2 : 0)) * CHUNK;
+      const uint32_t wbytes = (C::KC1 + (C::G2 ? C::C2 : 0)) * CHUNK;
       mbar_arrive_expect_tx(&bars[B_W], wbytes);
       for (int c = 0; c < C::KC1; ++c)
         bulk_g2s(sW1 + c * CHUNK, a.w1 + (size_t)c * CHUNK, CHUNK, &bars[B_W]);
       if (C::G2)
-        for (int c = 0; c < 2; ++c)
+        for (int c = 0; c < C::C2; ++c)
           bulk_g2s(sW2 + c * CHUNK, a.w2 + (size_t)c * CHUNK, CHUNK, &bars[B_W]);
       bool live = wait_or_abort(&bars[B_W], 0, a.err, abort);
       uint32_t gchunk = 0;
@@ -323,12 +361,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
       auto issue_gemm2 = [&]() {
         tc_fence_after();
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
+        for (int c = 0; c < C::C2; ++c) {
           const uint32_t a0 = smem_u32(sA2 + c * CHUNK), b0 = smem_u32(sW2 + c * CHUNK);
 #pragma unroll
-          for (int k = 0; k < KCH / 16; ++k)
-            mma_f16(tmem + 256, sdesc_k_sw128(a0 + 32 * k), sdesc_k_sw128(b0 + 32 * k), IDESC,
-                    (c > 0 || k > 0) ? 1u : 0u);
+          for (int k = 0; k < KSTEPS; ++k)
+            mma_tc<F8>(tmem + 256, sdesc_k_sw128(a0 + 32 * k), sdesc_k_sw128(b0 + 32 * k),
+                       EL::IDESC, (c > 0 || k > 0) ? 1u : 0u);
         }
         mma_commit(&bars[B_D2FULL]);
         pending = -1;
@@ -360,9 +398,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
           tc_fence_after();
           const uint32_t a0 = smem_u32(sA + slot * CHUNK), b0 = smem_u32(sW1 + c * CHUNK);
 #pragma unroll
-          for (int k = 0; k < KCH / 16; ++k)
-            mma_f16(d1, sdesc_k_sw128(a0 + 32 * k), sdesc_k_sw128(b0 + 32 * k), IDESC,
-                    (c > 0 || k > 0) ? 1u : 0u);
+          for (int k = 0; k < KSTEPS; ++k)
+            mma_tc<F8>(d1, sdesc_k_sw128(a0 + 32 * k), sdesc_k_sw128(b0 + 32 * k), EL::IDESC,
+                       (c > 0 || k > 0) ? 1u : 0u);
           mma_commit(&bars[B_EMPTY + slot]);
           ++gchunk;
         }
@@ -393,13 +431,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
       tc_fence_after();
       const uint32_t t1 = tmem + 128 * b + lane_off;
       float mean, rstd;
-      row_stats(t1, par, mean, rstd);
+      row_stats(t1, par, a.ws1, mean, rstd);
       float y[32];
       if constexpr (MODE == TC_CLS) {
         float p = 0.f;
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {
-          row_norm32(t1, cc, par, par + H, par + 2 * H, mean, rstd, y);
+          row_norm32(t1, cc, par, par + H, par + 2 * H, a.ws1, mean, rstd, y);
 #pragma unroll
           for (int j = 0; j < 32; ++j) p = fmaf(y[j], par[6 * H + 32 * cc + j], p);
         }
@@ -409,16 +447,28 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
       } else {
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {
-          row_norm32(t1, cc, par, par + H, par + 2 * H, mean, rstd, y);
-          uint8_t* dst2 = sA2 + (cc >> 1) * CHUNK;
+          row_norm32(t1, cc, par, par + H, par + 2 * H, a.ws1, mean, rstd, y);
+          if constexpr (F8) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            uint4 w;
-            w.x = pack_bf16(y[8 * q + 0], y[8 * q + 1]);
-            w.y = pack_bf16(y[8 * q + 2], y[8 * q + 3]);
-            w.z = pack_bf16(y[8 * q + 4], y[8 * q + 5]);
-            w.w = pack_bf16(y[8 * q + 6], y[8 * q + 7]);
-            *reinterpret_cast<uint4*>(dst2 + sw128(r, 4 * (cc & 1) + q)) = w;
+            for (int q = 0; q < 2; ++q) {
+              uint4 w;
+              w.x = pack_e4m3x4(y[16 * q + 0], y[16 * q + 1], y[16 * q + 2], y[16 * q + 3]);
+              w.y = pack_e4m3x4(y[16 * q + 4], y[16 * q + 5], y[16 * q + 6], y[16 * q + 7]);
+              w.z = pack_e4m3x4(y[16 * q + 8], y[16 * q + 9], y[16 * q + 10], y[16 * q + 11]);
+              w.w = pack_e4m3x4(y[16 * q + 12], y[16 * q + 13], y[16 * q + 14], y[16 * q + 15]);
+              *reinterpret_cast<uint4*>(sA2 + sw128(r, 2 * cc + q)) = w;
+            }
+          } else {
+            uint8_t* dst2 = sA2 + (cc >> 1) * CHUNK;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              uint4 w;
+              w.x = pack_bf16(y[8 * q + 0], y[8 * q + 1]);
+              w.y = pack_bf16(y[8 * q + 2], y[8 * q + 3]);
+              w.z = pack_bf16(y[8 * q + 4], y[8 * q + 5]);
+              w.w = pack_bf16(y[8 * q + 6], y[8 * q + 7]);
+              *reinterpret_cast<uint4*>(dst2 + sw128(r, 4 * (cc & 1) + q)) = w;
+            }
           }
         }
         fence_proxy_async();
@@ -428,7 +478,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
         if (!wait_or_abort(&bars[B_D2FULL], i & 1, a.err, abort)) break;
         tc_fence_after();
         const uint32_t t2 = tmem + 256 + lane_off;
-        row_stats(t2, par + 3 * H, mean, rstd);
+        row_stats(t2, par + 3 * H, a.ws2, mean, rstd);
         // The second GEMM has consumed A2, so its 32 KB stage the FP32 output:
         // 64 columns at a time, row-per-thread writes with 16-byte units
         // XOR-swizzled by (row % 8), then coalesced residual loads and stores
@@ -474,7 +524,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
           fetch_res(0, ra);
 #pragma unroll
           for (int cc = 0; cc < 2; ++cc) {
-            row_norm32(t2, 2 * half + cc, par + 3 * H, par + 4 * H, par + 5 * H, mean, rstd, y);
+            row_norm32(t2, 2 * half + cc, par + 3 * H, par + 4 * H, par + 5 * H, a.ws2, mean, rstd, y);
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
               const int un = (8 * cc + q) ^ (r & 7);
@@ -506,13 +556,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
   }
 }
 
-template <int MODE>
+template <int MODE, bool F8>
 cudaError_t launch_tc(etx_ctx* ctx, const char* name, const TcArgs& a, int64_t max_rows,
                       cudaStream_t s) {
-  using C = Cfg<MODE>;
+  using C = Cfg<MODE, F8>;
   static bool attr_set[8] = {false};
   if (!attr_set[ctx->device & 7]) {
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_tc<MODE, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          C::SMEM);
     if (e != cudaSuccess) return e;
     attr_set[ctx->device & 7] = true;
@@ -520,7 +570,7 @@ cudaError_t launch_tc(etx_ctx* ctx, const char* name, const TcArgs& a, int64_t m
   const int64_t tiles = (max_rows + TM - 1) / TM;
   if (tiles == 0) return cudaSuccess;
   const int grid = (int)(tiles < ctx->n_sms ? tiles : ctx->n_sms);
-  launch(ctx, name, k_mlp_tc<MODE>, grid, THREADS, C::SMEM, s, a);
+  launch(ctx, name, k_mlp_tc<MODE, F8>, grid, THREADS, C::SMEM, s, a);
   return cudaGetLastError();
 }
 
@@ -540,9 +590,11 @@ TcArgs base_args(etx_ctx* ctx, int64_t N, const int32_t* src, const int32_t* dst
   return a;
 }
 
-void set_block(TcArgs& a, const BlockF32& f, const BlockTC& t) {
-  a.w1 = t.w1;
-  a.w2 = t.w2;
+void set_block(TcArgs& a, const BlockF32& f, const BlockTC& t, bool f8) {
+  a.w1 = f8 ? t.w1f8 : t.w1;
+  a.w2 = f8 ? t.w2f8 : t.w2;
+  a.ws1 = f8 ? t.s1 : 1.f;
+  a.ws2 = f8 ? t.s2 : 1.f;
   a.b1 = f.l1.b;
   a.g1 = f.g1;
   a.be1 = f.be1;
@@ -551,38 +603,52 @@ void set_block(TcArgs& a, const BlockF32& f, const BlockTC& t) {
   a.be2 = f.be2;
 }
 
+template <int MODE>
+cudaError_t launch_any(etx_ctx* ctx, bool f8, const char* n16, const char* n8, const TcArgs& a,
+                       int64_t max_rows, cudaStream_t s) {
+  return f8 ? launch_tc<MODE, true>(ctx, n8, a, max_rows, s)
+            : launch_tc<MODE, false>(ctx, n16, a, max_rows, s);
+}
+
 }  // namespace
 
 cudaError_t launch_edge_encoder_tc(etx_ctx* ctx, int64_t N, const int32_t* src, const int32_t* dst,
-                                   const int32_t* n_edges_dev, cudaStream_t s) {
+                                   const int32_t* n_edges_dev, bool f8, cudaStream_t s) {
   TcArgs a = base_args(ctx, N, src, dst, n_edges_dev, nullptr);
-  set_block(a, ctx->w.edge_enc, ctx->w.edge_enc_tc);
-  return launch_tc<TC_EDGE_ENC>(ctx, "gnn_edge_encoder_bf16", a, ctx->cfg.max_edges, s);
+  set_block(a, ctx->w.edge_enc, ctx->w.edge_enc_tc, f8);
+  return launch_any<TC_EDGE_ENC>(ctx, f8, "gnn_edge_encoder_bf16", "gnn_edge_encoder_fp8", a,
+                                 ctx->cfg.max_edges, s);
 }
 
-cudaError_t launch_node_update_tc(etx_ctx* ctx, int k, int64_t N, cudaStream_t s) {
+cudaError_t launch_node_update_tc(etx_ctx* ctx, int k, int64_t N, bool f8, cudaStream_t s) {
   TcArgs a = base_args(ctx, N, nullptr, nullptr, nullptr, nullptr);
-  set_block(a, ctx->w.node[k], ctx->w.node_tc[k]);
-  return launch_tc<TC_NODE_UPD>(ctx, "gnn_node_update_bf16", a, N, s);
+  set_block(a, ctx->w.node[k], ctx->w.node_tc[k], f8);
+  return launch_any<TC_NODE_UPD>(ctx, f8, "gnn_node_update_bf16", "gnn_node_update_fp8", a, N, s);
 }
 
 cudaError_t launch_edge_update_tc(etx_ctx* ctx, int k, int64_t N, const int32_t* src,
-                                  const int32_t* dst, const int32_t* n_edges_dev, cudaStream_t s) {
+                                  const int32_t* dst, const int32_t* n_edges_dev, bool f8,
+                                  cudaStream_t s) {
   TcArgs a = base_args(ctx, N, src, dst, n_edges_dev, nullptr);
-  set_block(a, ctx->w.edge[k], ctx->w.edge_tc[k]);
-  return launch_tc<TC_EDGE_UPD>(ctx, "gnn_edge_update_bf16", a, ctx->cfg.max_edges, s);
+  set_block(a, ctx->w.edge[k], ctx->w.edge_tc[k], f8);
+  return launch_any<TC_EDGE_UPD>(ctx, f8, "gnn_edge_update_bf16", "gnn_edge_update_fp8", a,
+                                 ctx->cfg.max_edges, s);
 }
 
 cudaError_t launch_classifier_tc(etx_ctx* ctx, int64_t N, const int32_t* n_edges_dev, float* logits,
-                                 cudaStream_t s) {
+                                 bool f8, cudaStream_t s) {
   TcArgs a = base_args(ctx, N, nullptr, nullptr, n_edges_dev, logits);
-  a.w1 = ctx->w.cls_tc.w1;
+  const BlockTC& t = ctx->w.cls_tc;
+  a.w1 = f8 ? t.w1f8 : t.w1;
+  a.ws1 = f8 ? t.s1 : 1.f;
+  a.ws2 = 1.f;
   a.b1 = ctx->w.cls.l1.b;
   a.g1 = ctx->w.cls.g1;
   a.be1 = ctx->w.cls.be1;
   a.wcls = ctx->w.cls.w2;
   a.bcls = ctx->w.cls.b2;
-  return launch_tc<TC_CLS>(ctx, "gnn_classifier_bf16", a, ctx->cfg.max_edges, s);
+  return launch_any<TC_CLS>(ctx, f8, "gnn_classifier_bf16", "gnn_classifier_fp8", a,
+                            ctx->cfg.max_edges, s);
 }
 
 }  // namespace etx

@@ -118,6 +118,13 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32() {
          (static_cast<uint32_t>(M >> 4) << 24);
 }
 
+// Same for kind::f8f6f4 with both operands e4m3 (type code 0 in bits 7-9
+// and 10-12), FP32 accumulation.
+template <int M, int N>
+__host__ __device__ constexpr uint32_t idesc_e4m3_f32() {
+  return (1u << 4) | (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
+}
+
 // D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread.
 __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
                                         uint32_t idesc, uint32_t accumulate) {
@@ -127,6 +134,23 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
       "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
       : "memory");
+}
+
+__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                       uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+template <bool F8>
+__device__ __forceinline__ void mma_tc(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                       uint32_t idesc, uint32_t accumulate) {
+  if constexpr (F8) mma_f8(d_tmem, a_desc, b_desc, idesc, accumulate);
+  else mma_f16(d_tmem, a_desc, b_desc, idesc, accumulate);
 }
 
 // Arrive once on `bar` when every tcgen05 operation this thread issued so far

@@ -381,3 +381,27 @@ def test_gnn_forward_bf16_tensor_cores(etx, n_events):
           f"vs fp64 {e64.max():.3e} (mean {e64.mean():.2e}), oracle bf16-vs-fp64 "
           f"{np.abs(ref16 - ref64).max():.3e}")
     assert e16.max() <= BF16_TOL
+
+
+FP8_TOL = 0.15    # vs the oracle's e4m3 reading (max-abs); e4m3 keeps 3 mantissa bits
+
+
+@pytest.mark.parametrize("n_events", [1, 3])
+def test_gnn_forward_fp8_tensor_cores(etx, n_events):
+    st = setup_for(etx, "batch500", n_events)
+    emb64 = st.oracle_emb()
+    s, d, eo = O.build_graph(emb64, st.b.plane, st.b.hit_offsets, st.model.radius, st.model.k_max)
+    args = (st.W, st.model.n_iters, st.b.x, st.b.y, st.b.z, s, d)
+    ref64 = O.gnn_forward(*args)
+    ref8 = O.gnn_forward(*args, gemm="fp8")
+    logits = st.ctx.gnn_forward(st.x, st.y, st.z, cuda(s, torch.int32), cuda(d, torch.int32),
+                                cuda(eo, torch.int32), dtype="fp8")
+    st.ctx.sync()
+    got = logits.cpu().numpy().astype(np.float64)
+    e8, e64 = np.abs(got - ref8), np.abs(got - ref64)
+    print(f"fp8 E={s.size}: max|err| vs e4m3 reading {e8.max():.3e} (mean {e8.mean():.2e}), "
+          f"vs fp64 {e64.max():.3e} (mean {e64.mean():.2e}), oracle fp8-vs-fp64 "
+          f"{np.abs(ref8 - ref64).max():.3e}")
+    assert e8.max() <= FP8_TOL
+    # a layout or scale error would be far larger than the e4m3 rounding itself
+    assert e8.mean() <= 0.5 * max(np.abs(ref8 - ref64).mean(), 1e-6) + 1e-2

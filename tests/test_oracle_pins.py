@@ -497,3 +497,33 @@ def test_gnn_bf16_reading_is_close_to_exact():
     z16 = O.gnn_forward(W, cfg.n_iters, b.x, b.y, b.z, s, d, gemm="bf16")
     err = np.abs(z16 - z64).max()
     assert 0 < err < 0.1   # rounding operands to 8 significand bits moves the logits a little
+
+
+def test_round_e4m3_closed_forms():
+    cases = [(1.0, 1.0), (1.0625, 1.0),                 # tie between 1 and 1.125 -> even (1)
+             (1.1875, 1.25),                            # tie between 1.125 and 1.25 -> even (1.25)
+             (448.0, 448.0), (500.0, 448.0), (-1e9, -448.0),   # saturation
+             (2.0 ** -9, 2.0 ** -9), (2.0 ** -10, 0.0),        # smallest subnormal / tie to zero
+             (3 * 2.0 ** -10, 2.0 ** -8),               # tie between 1 and 2 subnormal steps -> 2
+             (0.0, 0.0), (240.0, 240.0), (232.0, 224.0)]      # 232: tie between 224 and 240 -> 224
+    for x, want in cases:
+        assert O.round_e4m3(np.array([x]))[0] == want, x
+
+
+def test_round_e4m3_matches_torch():
+    torch = pytest.importorskip("torch")
+    if not hasattr(torch, "float8_e4m3fn"):
+        pytest.skip("no float8 in this torch")
+    rng = np.random.default_rng(6)
+    a = (rng.normal(size=4000) * np.exp(rng.uniform(-12, 5, 4000))).astype(np.float32)
+    a = np.clip(a, -448, 448)
+    ref = torch.from_numpy(a).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    np.testing.assert_array_equal(O.round_e4m3(a), ref)
+
+
+def test_quant_weight_e4m3_scale():
+    W = np.array([[0.5, -2.0], [0.25, 0.0]], np.float32)
+    q = O.quant_weight_e4m3(W)
+    # the largest magnitude maps to 448 s, i.e. back to itself up to the rounding of s
+    np.testing.assert_allclose(q[0, 1], -2.0, rtol=1e-6)
+    assert np.all(np.abs(q - W) <= 2.0 ** -4 * np.abs(W) + 1e-12)
