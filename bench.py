@@ -39,10 +39,12 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="batch500")
-    p.add_argument("--dtype", default="f32", choices=["f32", "bf16", "fp8"])
+    p.add_argument("--dtype", default="bf16", choices=["f32", "bf16", "fp8"])
     p.add_argument("--cpu-seconds", type=float, default=15.0,
                    help="budget of the oracle CPU baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--skip-dtypes", action="store_true", help="time only --dtype")
+    p.add_argument("--skip-train", action="store_true", help="no training-step timing")
     p.add_argument("--events", type=int, default=None,
                    help="use only the first N events of the workload (profiling captures)")
     return p.parse_args()
@@ -197,6 +199,51 @@ def cpu_threads() -> int:
 
 
 # ---------------------------------------------------------------------------
+def train_step_report(args, local):
+    """Time the training step (BF16 forward with checkpoints, weighted BCE,
+    backward with recomputation, Adam, weight reload) on the 64-event
+    workload; the graph and the truth targets are prepared untimed."""
+    import torch
+
+    from paper_2407_12119_gb300.pipeline import TrackFinder
+    from paper_2407_12119_gb300.train import Trainer
+    from velo_synth import WORKLOADS, global_particle_ids, pack_blob, truth_edge_labels
+
+    wl = WORKLOADS["train64"]
+    m = wl.model
+    b = wl.batch()
+    W = wl.weights()
+    blob = pack_blob(m, W)
+    N, B = b.n_hits, b.n_events
+    tf = TrackFinder(m, blob, B, N, N * m.k_max, device=local)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(tf.dev)
+    x, y, z, pl, ho = t(b.x), t(b.y), t(b.z), t(b.plane), t(b.hit_offsets)
+    emb = tf.ctx.embed(x, y, z)
+    src, dst, eo = tf.ctx.build_graph(emb, pl, ho, m.radius, m.k_max)
+    tf.ctx.sync()
+    E = int(eo[-1].item())
+    s_h, d_h = src[:E].cpu().numpy(), dst[:E].cpu().numpy()
+    targets = t(truth_edge_labels(global_particle_ids(b), b.plane, s_h, d_h).astype(np.float32))
+    src, dst = src[:E].contiguous(), dst[:E].contiguous()
+    tr = Trainer(m, blob, B, N, max(E, 1), device=local, dtype="bf16", lr=1e-3, pos_weight=10.0)
+    for _ in range(2):
+        tr.step(x, y, z, src, dst, eo, targets)
+    torch.cuda.synchronize()
+    steps = max(args.steps, 3)
+    t0 = time.perf_counter()
+    losses = []
+    for _ in range(steps):
+        losses.append(tr.step(x, y, z, src, dst, eo, targets))
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    tr.ctx.sync()
+    return {"workload": f"{wl.name}: {B} events, {N} hits, {E} edges, hidden {m.hidden}, "
+                        f"{m.n_iters} steps, BF16 forward, FP32 backward with recomputation, "
+                        f"weighted BCE (w=10), Adam lr 1e-3",
+            "ms_per_step": 1e3 * el / steps, "events_per_s": B * steps / el,
+            "loss_first": float(losses[0].item()), "loss_last": float(losses[-1].item())}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -305,6 +352,45 @@ def run_ours(args):
     h2d = N * (3 * 4 + 1) + (B + 1) * 4
     d2h = N * 4 + B * 4
 
+    # ---- every arithmetic type: throughput and agreement with the FP32 path --
+    per_dtype = {}
+    if not args.skip_dtypes:
+        ref = None
+        for dt in ("f32", "bf16", "fp8"):
+            tf.dtype = dt
+            labels, _ = step()
+            torch.cuda.synchronize()
+            logits, lab = tf.logits[:E].clone(), labels.clone()
+            if dt == args.dtype:
+                dt_ms = ms_step
+            else:
+                step()
+                d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                d0.record(stream)
+                for _ in range(args.steps):
+                    step()
+                d1.record(stream)
+                torch.cuda.synchronize()
+                dt_ms = max_over_ranks(d0.elapsed_time(d1), world, dev) / args.steps
+            rec = {"events_per_s": world * B / (dt_ms / 1e3), "ms_per_step": dt_ms}
+            if ref is None:
+                ref = (logits, lab)
+            else:
+                thr = m.threshold_logit
+                rec["max_abs_logit_diff_vs_f32"] = float((logits - ref[0]).abs().max().item())
+                rec["mean_abs_logit_diff_vs_f32"] = float((logits - ref[0]).abs().mean().item())
+                rec["mask_disagreement_vs_f32"] = float(((logits > thr) != (ref[0] > thr)).float().mean().item())
+                rec["label_agreement_vs_f32"] = float((lab == ref[1]).float().mean().item())
+            per_dtype[dt] = rec
+        for rec in per_dtype.values():
+            rec["speedup_vs_f32"] = per_dtype["f32"]["ms_per_step"] / rec["ms_per_step"]
+        tf.dtype = args.dtype
+        tf.ctx.sync()
+
+    train = None
+    if not args.skip_train:
+        train = train_step_report(args, local)
+
     if rank != 0:
         return
     # ---- roofline of the dominant kernel -----------------------------------
@@ -358,6 +444,8 @@ def run_ours(args):
                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
            "gpu_launches": int(launches),
            "clocks": clk.summary(),
+           "per_dtype": per_dtype,
+           "train64": train,
            "kernels": kernels}
     print(json.dumps(out), flush=True)
 

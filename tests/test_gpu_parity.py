@@ -405,3 +405,30 @@ def test_gnn_forward_fp8_tensor_cores(etx, n_events):
     assert e8.max() <= FP8_TOL
     # a layout or scale error would be far larger than the e4m3 rounding itself
     assert e8.mean() <= 0.5 * max(np.abs(ref8 - ref64).mean(), 1e-6) + 1e-2
+
+
+def test_dtype_report_vs_fp64_oracle(etx):
+    """Per arithmetic type: max-abs logit error against the FP64 oracle, edge-mask
+    disagreement at the workload's cut and track-label agreement (both sides on
+    the oracle's graph).  Printed; FP32 must reproduce the oracle's tracks."""
+    st = setup_for(etx, "batch500", 3, perturb=0.0)
+    emb64 = st.oracle_emb()
+    s, d, eo = O.build_graph(emb64, st.b.plane, st.b.hit_offsets, st.model.radius, st.model.k_max)
+    z64 = O.gnn_forward(st.W, st.model.n_iters, st.b.x, st.b.y, st.b.z, s, d)
+    thr = st.model.threshold_logit
+    lab64 = O.connected_components(s, d, z64 > thr, st.b.hit_offsets)
+    s_t, d_t, eo_t = cuda(s, torch.int32), cuda(d, torch.int32), cuda(eo, torch.int32)
+    report = {}
+    for dt in ("f32", "bf16", "fp8"):
+        z = st.ctx.gnn_forward(st.x, st.y, st.z, s_t, d_t, eo_t, dtype=dt)
+        lab, _ = st.ctx.edges_to_tracks(s_t, d_t, z, thr, eo_t, st.hoff)
+        st.ctx.sync()
+        zg = z.cpu().numpy().astype(np.float64)
+        report[dt] = dict(max_abs=float(np.abs(zg - z64).max()),
+                          mask_dis=float(((zg > thr) != (z64 > thr)).mean()),
+                          label_agree=float((lab.cpu().numpy() == lab64).mean()))
+    for dt, r in report.items():
+        print(f"{dt}: E={s.size} max|logit err| {r['max_abs']:.3e}, mask disagreement "
+              f"{r['mask_dis']:.2e}, label agreement {r['label_agree']:.5f}")
+    assert report["f32"]["max_abs"] <= LOGIT_TOL
+    assert report["f32"]["label_agree"] >= 0.999
