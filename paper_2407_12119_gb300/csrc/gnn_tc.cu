@@ -152,7 +152,8 @@ __device__ __forceinline__ const float* chunk_src(const TcArgs& a, int col0, int
 __device__ __forceinline__ void row_stats(uint32_t taddr, const float* __restrict__ b, float sc,
                                           float& mean, float& rstd) {
   float v[32];
-  float shift = 0.f, s = 0.f, ss = 0.f;
+  float shift = 0.f;
+  float s4[4] = {0.f, 0.f, 0.f, 0.f}, q4[4] = {0.f, 0.f, 0.f, 0.f};  // independent chains
 #pragma unroll
   for (int cc = 0; cc < 4; ++cc) {
     tmem_ld32_wait(taddr + 32 * cc, v);
@@ -163,10 +164,12 @@ __device__ __forceinline__ void row_stats(uint32_t taddr, const float* __restric
                   x2 = fmaf(v[j + 2], sc, bb.z), x3 = fmaf(v[j + 3], sc, bb.w);
       if (cc == 0 && j == 0) shift = x0;
       const float d0 = x0 - shift, d1 = x1 - shift, d2 = x2 - shift, d3 = x3 - shift;
-      s += (d0 + d1) + (d2 + d3);
-      ss = fmaf(d0, d0, fmaf(d1, d1, fmaf(d2, d2, fmaf(d3, d3, ss))));
+      s4[0] += d0; s4[1] += d1; s4[2] += d2; s4[3] += d3;
+      q4[0] = fmaf(d0, d0, q4[0]); q4[1] = fmaf(d1, d1, q4[1]);
+      q4[2] = fmaf(d2, d2, q4[2]); q4[3] = fmaf(d3, d3, q4[3]);
     }
   }
+  const float s = (s4[0] + s4[1]) + (s4[2] + s4[3]), ss = (q4[0] + q4[1]) + (q4[2] + q4[3]);
   const float ms = s * (1.0f / H);
   mean = shift + ms;
   const float var = fmaxf(ss * (1.0f / H) - ms * ms, 0.f);
@@ -212,14 +215,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
   if (tid == 0) {
     mbar_init(&bars[B_W], 1);
     for (int s = 0; s < NSTAGE; ++s) {
-      mbar_init(&bars[B_FULL + s], PROD_THREADS);
+      mbar_init(&bars[B_FULL + s], PROD_WARPS);  // one arrival per producer warp
       mbar_init(&bars[B_EMPTY + s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&bars[B_D1FULL + b], 1);
-      mbar_init(&bars[B_D1EMPTY + b], EPI_THREADS);
+      mbar_init(&bars[B_D1EMPTY + b], EPI_WARPS);
     }
-    mbar_init(&bars[B_A2FULL], EPI_THREADS);
+    mbar_init(&bars[B_A2FULL], EPI_WARPS);
     mbar_init(&bars[B_D2FULL], 1);
     *abort = 0;
     fence_mbar_init();
@@ -327,7 +330,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
       }
       if (hpart == EL::SUBS - 1) {
         fence_proxy_async();
-        mbar_arrive(&bars[B_FULL + slot]);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars[B_FULL + slot]);
       }
       return true;
     };
@@ -442,7 +446,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
           for (int j = 0; j < 32; ++j) p = fmaf(y[j], par[6 * H + 32 * cc + j], p);
         }
         tc_fence_before();
-        mbar_arrive(&bars[B_D1EMPTY + b]);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bars[B_D1EMPTY + b]);
         if (valid) a.logits[gr] = p + __ldg(a.bcls);
       } else {
 #pragma unroll
@@ -473,8 +478,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
         }
         fence_proxy_async();
         tc_fence_before();
-        mbar_arrive(&bars[B_D1EMPTY + b]);
-        mbar_arrive(&bars[B_A2FULL]);
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&bars[B_D1EMPTY + b]);
+          mbar_arrive(&bars[B_A2FULL]);
+        }
         if (!wait_or_abort(&bars[B_D2FULL], i & 1, a.err, abort)) break;
         tc_fence_after();
         const uint32_t t2 = tmem + 256 + lane_off;

@@ -23,6 +23,21 @@ constexpr int kKnnThreads = 128;
 constexpr int kStageFloats = 16384;  // 64 KB of staged candidate coordinates per block
 constexpr int kMaxDim = 32;
 
+// register-resident candidate keys per lane: 16 (512 candidates per block) or
+// 64 (2048, the shared-memory stage limit for D = 8)
+
+// Squared distance for a compile-time dimension (same operation order).
+template <int D>
+__device__ __forceinline__ float d2_fixed(const float (&ei)[D], const float* cand, int stride) {
+  float s = 0.f;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const float t = __fsub_rn(ei[d], cand[d * stride]);
+    s = __fadd_rn(s, __fmul_rn(t, t));
+  }
+  return s;
+}
+
 // Squared distance, FP32, one rounding per operation, dimensions in order.
 __device__ __forceinline__ float d2_ordered(const float* __restrict__ ei, const float* cand,
                                             int stride, int D) {
@@ -77,12 +92,122 @@ __global__ void k_plane_bins(const int8_t* __restrict__ plane, const int32_t* __
   plane_off[t] = lo;
 }
 
-template <bool EMIT>
+// Fast path for one source hit (compile-time D, candidates staged, at most
+// 32 * kMaxI of them): every lane keeps the sortable keys (FP32 bit
+// patterns; non-qualifying candidates get the all-ones sentinel) of its
+// candidates in registers, so the count, the radix select and the write all
+// run over registers without recomputing distances.
+template <bool EMIT, int D, int kMaxI>
+__device__ __forceinline__ void knn_source_fast(const float* __restrict__ emb, int i,
+                                                const float* cand_s, int n_cand, int c_lo,
+                                                float r2, int k_max, int32_t* cnt_or_off,
+                                                int32_t* __restrict__ src, int32_t* __restrict__ dst,
+                                                int lane, int* hist) {
+  const unsigned full = 0xffffffffu, lt_mask = (1u << lane) - 1u;
+  float ei[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) ei[d] = emb[(int64_t)i * D + d];
+  const int nt = (n_cand + 31) >> 5;
+  uint32_t key[kMaxI];
+  int cnt = 0;
+#pragma unroll
+  for (int t = 0; t < kMaxI; ++t) {
+    key[t] = 0xffffffffu;
+    if (t < nt) {
+      const int j = 32 * t + lane;
+      if (j < n_cand) {
+        const float d2 = d2_fixed<D>(ei, cand_s + j, n_cand);
+        if (d2 < r2) key[t] = __float_as_uint(d2);
+      }
+      cnt += __popc(__ballot_sync(full, key[t] != 0xffffffffu));
+    }
+  }
+  if (!EMIT) {
+    if (lane == 0) cnt_or_off[i] = min(cnt, k_max);
+    return;
+  }
+  uint32_t kth = 0xffffffffu;
+  int take_eq = 0;
+  const bool capped = cnt > k_max;
+  if (capped) {
+    // radix select in four 8-bit digits with a per-warp 256-bin histogram:
+    // find the rank-th smallest key among those sharing the digits chosen so far
+    uint32_t prefix = 0, pmask = 0;
+    int rank = k_max;  // 1-based rank still to locate
+    for (int shift = 24; shift >= 0; shift -= 8) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) hist[8 * lane + q] = 0;
+      __syncwarp();
+#pragma unroll
+      for (int t = 0; t < kMaxI; ++t)
+        if (t < nt && key[t] != 0xffffffffu && (key[t] & pmask) == prefix)
+          atomicAdd(hist + ((key[t] >> shift) & 255u), 1);
+      __syncwarp();
+      int c8[8], sum = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        c8[q] = hist[8 * lane + q];
+        sum += c8[q];
+      }
+      int incl = sum;  // inclusive scan of the lanes' 8-bin sums
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(full, incl, o);
+        if (lane >= o) incl += v;
+      }
+      const int excl = incl - sum;
+      const unsigned hit = __ballot_sync(full, excl < rank && rank <= incl);
+      const int owner = __ffs(hit) - 1;
+      int digit = 0, below = 0;
+      if (lane == owner) {
+        int acc = excl;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (acc + c8[q] >= rank) {
+            digit = 8 * lane + q;
+            below = acc;
+            break;
+          }
+          acc += c8[q];
+        }
+      }
+      digit = __shfl_sync(full, digit, owner);
+      below = __shfl_sync(full, below, owner);
+      prefix |= static_cast<uint32_t>(digit) << shift;
+      pmask |= 255u << shift;
+      rank -= below;
+      __syncwarp();
+    }
+    kth = prefix;          // the k_max-th smallest key
+    take_eq = rank;        // how many keys equal to kth are kept (in index order)
+  }
+  const int base = cnt_or_off[i];
+  int written = 0, eq_seen = 0;
+#pragma unroll
+  for (int t = 0; t < kMaxI; ++t) {
+    if (t >= nt) break;
+    bool in = key[t] < kth;
+    const bool eq = capped && key[t] == kth;
+    const unsigned eqm = __ballot_sync(full, eq);
+    if (eq) in = eq_seen + __popc(eqm & lt_mask) < take_eq;
+    eq_seen += __popc(eqm);
+    const unsigned inm = __ballot_sync(full, in);
+    if (in) {
+      const int pos = base + written + __popc(inm & lt_mask);
+      src[pos] = i;
+      dst[pos] = c_lo + 32 * t + lane;
+    }
+    written += __popc(inm);
+  }
+}
+
+template <bool EMIT, int DT>
 __global__ void __launch_bounds__(kKnnThreads)
 k_knn(const float* __restrict__ emb, int D, const int32_t* __restrict__ plane_off, int n_planes,
       float radius, int k_max, int32_t* __restrict__ cnt_or_off, int64_t n_hits,
       int32_t* __restrict__ src, int32_t* __restrict__ dst, int64_t capacity, int* err) {
-  extern __shared__ float cand_s[];  // [D][n_stage]
+  extern __shared__ float cand_s[];  // [D][n_stage], then 256 ints per warp (select histograms)
+  int* hist_s = reinterpret_cast<int*>(cand_s + kStageFloats);
   const int b = blockIdx.x / (n_planes - 1);
   const int p = blockIdx.x % (n_planes - 1);
   const int32_t* po = plane_off + (int64_t)b * (n_planes + 1);
@@ -115,7 +240,19 @@ k_knn(const float* __restrict__ emb, int D, const int32_t* __restrict__ plane_of
   const int cstep = staged ? 1 : D;              // stride between candidates
   const float r2 = __fmul_rn(radius, radius);
 
+  const bool fast = DT > 0 && staged && n_cand <= 32 * 64;
   for (int i = s_lo + warp; i < s_hi; i += kKnnThreads / 32) {
+    if constexpr (DT > 0) {
+      if (fast) {
+        if (n_cand <= 32 * 16)
+          knn_source_fast<EMIT, DT, 16>(emb, i, cand_s, n_cand, c_lo, r2, k_max, cnt_or_off, src,
+                                        dst, lane, hist_s + 256 * warp);
+        else
+          knn_source_fast<EMIT, DT, 64>(emb, i, cand_s, n_cand, c_lo, r2, k_max, cnt_or_off, src,
+                                        dst, lane, hist_s + 256 * warp);
+        continue;
+      }
+    }
     float ei[kMaxDim];
     for (int d = 0; d < D; ++d) ei[d] = emb[(int64_t)i * D + d];
     // pass A: count the hits inside the radius
@@ -213,29 +350,41 @@ cudaError_t launch_build_graph(etx_ctx* ctx, const float* emb, const int8_t* pla
            hit_offsets, n_events, (int)n_hits, P, ctx->plane_off);
   int32_t* cnt = ctx->hit_cnt;  // counts, then (in place) offsets; [n_hits + 1]
   const unsigned blocks = (unsigned)n_events * (unsigned)(P - 1);
-  const size_t smem = (size_t)kStageFloats * sizeof(float);
+  const size_t smem = (size_t)kStageFloats * sizeof(float) + kKnnThreads / 32 * 256 * sizeof(int);
   // hits of the last plane get no block: start from zero counts
   cudaError_t e0 = cudaMemsetAsync(cnt, 0, (size_t)(n_hits + 1) * sizeof(int32_t), s);
   if (e0 != cudaSuccess) return e0;
-  if (n_hits > 0 && blocks > 0)
-    launch(ctx, "graph_knn_count", k_knn<false>, blocks, kKnnThreads, smem, s, emb, D,
-           ctx->plane_off, P, radius, k_max, cnt, n_hits, nullptr, nullptr, 0, ctx->d_err);
+  auto knn = [&](auto kernel, const char* name, int32_t* sp, int32_t* dp, int64_t cap) {
+    launch(ctx, name, kernel, blocks, kKnnThreads, smem, s, emb, D, (const int32_t*)ctx->plane_off,
+           P, radius, k_max, cnt, n_hits, sp, dp, cap, ctx->d_err);
+  };
+  if (n_hits > 0 && blocks > 0) {
+    if (D == 8) knn(k_knn<false, 8>, "graph_knn_count", nullptr, nullptr, 0);
+    else if (D == 4) knn(k_knn<false, 4>, "graph_knn_count", nullptr, nullptr, 0);
+    else knn(k_knn<false, 0>, "graph_knn_count", nullptr, nullptr, 0);
+  }
   cudaError_t e = exclusive_scan(ctx, cnt, cnt, n_hits, s);
   if (e != cudaSuccess) return e;
-  if (n_hits > 0 && blocks > 0)
-    launch(ctx, "graph_knn_emit", k_knn<true>, blocks, kKnnThreads, smem, s, emb, D,
-           ctx->plane_off, P, radius, k_max, cnt, n_hits, src, dst, edge_capacity, ctx->d_err);
+  if (n_hits > 0 && blocks > 0) {
+    if (D == 8) knn(k_knn<true, 8>, "graph_knn_emit", src, dst, edge_capacity);
+    else if (D == 4) knn(k_knn<true, 4>, "graph_knn_emit", src, dst, edge_capacity);
+    else knn(k_knn<true, 0>, "graph_knn_emit", src, dst, edge_capacity);
+  }
   launch(ctx, "graph_edge_offsets", k_edge_offsets, (unsigned)((n_events + 1 + 255) / 256), 256, 0,
          s, cnt, hit_offsets, n_events, (int)n_hits, edge_offsets);
   return cudaGetLastError();
 }
 
 cudaError_t knn_set_smem_attr() {
-  const size_t smem = (size_t)kStageFloats * sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(k_knn<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_knn<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int smem = (int)(kStageFloats * sizeof(float) + kKnnThreads / 32 * 256 * sizeof(int));
+  const void* ks[] = {(const void*)k_knn<false, 0>, (const void*)k_knn<true, 0>,
+                      (const void*)k_knn<false, 4>, (const void*)k_knn<true, 4>,
+                      (const void*)k_knn<false, 8>, (const void*)k_knn<true, 8>};
+  for (const void* k : ks) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace etx

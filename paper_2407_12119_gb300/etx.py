@@ -8,12 +8,14 @@ first call raises: there is no CPU fallback.
 from __future__ import annotations
 
 import ctypes
+import os
 from pathlib import Path
 
 import numpy as np
 import torch
 
-_LIB_PATH = Path(__file__).resolve().parent / "libetx.so"
+# ETX_LIBRARY may name another build of the same library (same ABI)
+_LIB_PATH = Path(os.environ.get("ETX_LIBRARY") or Path(__file__).resolve().parent / "libetx.so")
 _lib = None
 
 ETX_OK, ETX_ERR_ARG, ETX_ERR_UNSORTED, ETX_ERR_CAPACITY = 0, 1, 2, 3

@@ -156,10 +156,11 @@ def test_graph_exact_ties_between_duplicate_hits(etx):
     assert _check_graph_exact(st, st.oracle_emb(), k=3) > 0
 
 
-def test_graph_exact_unstaged_candidates(etx):
-    # planes 1 and 2 hold more candidates than the shared-memory stage fits
+@pytest.mark.parametrize("counts", [[12, 500, 500, 5], [12, 1100, 1100, 5]])
+def test_graph_exact_large_candidate_sets(etx, counts):
+    # 1,000 candidates: the 64-key register path; 2,200: more than the
+    # shared-memory stage holds, so the generic path reads global memory
     rng = np.random.default_rng(3)
-    counts = [12, 1100, 1100, 5]
     plane = np.concatenate([np.full(c, i, np.int8) for i, c in enumerate(counts)])
     r = np.sqrt(rng.uniform(5.1 ** 2, 40 ** 2, plane.size))
     ph = rng.uniform(0, 2 * np.pi, plane.size)
