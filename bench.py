@@ -30,6 +30,10 @@ if ROOT not in sys.path:
 
 METRIC = "events/s (hits->tracks, 500-event batch)"
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
+# dram__bytes_read.sum + dram__bytes_write.sum per edge of one launch, from ncu
+# captures on the 50-event case (profiles/edge_update_bf16_batch500.md); to be
+# re-taken whenever the kernel changes
+MEASURED_DRAM_BYTES_PER_EDGE = {"gnn_edge_update_bf16": (633.189376e6 + 520.522496e6) / 1113945}
 
 
 def parse():
@@ -319,12 +323,16 @@ def run_ours(args):
     barrier(world)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     with ClockSampler(gpu_query_id(local)) as clk:
         ev0.record(stream)
-        for _ in range(args.steps):
+        for k in range(args.steps):
             step()
+            marks[k].record(stream)
         ev1.record(stream)
         torch.cuda.synchronize()
+    per_step = [ev0.elapsed_time(marks[0])] + [marks[k - 1].elapsed_time(marks[k])
+                                               for k in range(1, args.steps)]
     barrier(world)
     launches = tf.ctx.launch_count - n_launch0
     prof = tf.ctx.profile_read()
@@ -415,7 +423,10 @@ def run_ours(args):
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs", 6800.0),
                 "unit": "GB/s", "peak_source": f"{peak_kind} hbm copy"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    # DRAM bytes per launch from the ncu capture of the same kernel on a 50-event
+    # case (committed summary under profiles/), scaled by the edges of a launch
+    per_edge = MEASURED_DRAM_BYTES_PER_EDGE.get(name)
+    roof["traffic"] = per_edge * E if per_edge else None
     roof["kernel"] = name
     roof["launch_ms"] = tot_ms / cnt
 
@@ -444,6 +455,8 @@ def run_ours(args):
                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
            "gpu_launches": int(launches),
            "clocks": clk.summary(),
+           "latency_ms": {"p50": float(np.percentile(per_step, 50)),
+                          "p99": float(np.percentile(per_step, 99)), "per_step": per_step},
            "per_dtype": per_dtype,
            "train64": train,
            "kernels": kernels}
