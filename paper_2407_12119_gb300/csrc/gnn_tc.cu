@@ -1,27 +1,32 @@
 // Interaction-network MLP blocks on the 5th-generation tensor cores
-// (tcgen05, BF16 operands, FP32 accumulation in tensor memory).
+// (tcgen05, BF16 or e4m3 operands, FP32 accumulation in tensor memory).
 //
-// Persistent kernel, one CTA per SM, 416 threads in three roles that run
+// Persistent kernel, one CTA per SM, 544 threads in three roles that run
 // concurrently over the CTA's 128-row tiles:
-//   warps 4-11 producers: gather the block's input rows ([h_i, h_j],
+//   warps 8-15 producers: gather the block's input rows ([h_i, h_j],
 //              [h, m_out, m_in], [e, h_i, h_j] or e) from the FP32 streams,
-//              round them to BF16 and write them, 64 columns at a time, into a
-//              3-slot ring in the K-major 128-byte-swizzle layout; coalesced
-//              (8 threads per 256-byte row segment) and two chunks prefetched
-//              in registers;
-//   warp 12    MMA issuer (one thread): tcgen05.mma of each ring slot into the
-//              tile's first accumulator (two TMEM buffers, so the next tile's
-//              first GEMM runs while the epilogue reads this one), then the
-//              second GEMM of the previous tile from the epilogue's BF16
-//              activations;
-//   warps 0-3  epilogue, one row per thread (TMEM lane = row): bias +
-//              LayerNorm + ReLU of the first GEMM into the BF16 operand of the
-//              second, then bias + LayerNorm + ReLU + FP32 residual and the
-//              row store (or the classifier's dot product).
+//              round them to the operand type and write them, 64 columns at a
+//              time, into a 3-slot ring in the K-major 128-byte-swizzle layout;
+//              coalesced (8 threads per 256-byte row segment), one chunk
+//              prefetched in registers;
+//   warp 16    MMA issuer (one thread), an event loop over two queues: the
+//              first GEMM of the next tile, one ring slot at a time, and the
+//              second GEMM of the oldest tile whose activations are ready;
+//   warps 0-7  epilogue, two groups of four warps that take alternate tiles, so
+//              that one group's second epilogue overlaps the other's first.
+//              Warp w reads TMEM lanes 32 (w % 4) .. +31, one row per thread.
+//              Bias + LayerNorm + ReLU of the first GEMM are written back to
+//              tensor memory, over the accumulator columns already consumed, as
+//              the A operand of the second GEMM; bias + LayerNorm + ReLU + FP32
+//              residual of the second are staged per warp in shared memory and
+//              stored coalesced (or, for the classifier, reduced to the logit).
+//              Elementwise math uses the packed FP32x2 instructions.
+// Tensor memory (512 columns): group g owns D1 at column 128 g (first GEMM,
+// then its activations in the first 64 columns) and D2 at 256 + 128 g.
 // Stages hand over through mbarriers (transaction-counted bulk copies for
-// the resident BF16 weights, tcgen05.commit for MMA completion, thread
-// arrivals otherwise).  Every wait is bounded; a timeout records
-// ETX_ERR_TIMEOUT, raises a shared abort flag and every role stops.
+// the resident weights, tcgen05.commit for MMA completion, warp arrivals
+// otherwise).  Every wait is bounded; a timeout records ETX_ERR_TIMEOUT,
+// raises a shared abort flag and every role stops.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
@@ -38,22 +43,23 @@ constexpr int CHUNK = TM * 128;          // 16 KB operand chunk: 128 rows x 128 
 constexpr int SUB = 64;                  // K columns a producer fetches per step (256 B FP32)
 constexpr int KSTEPS = 4;                // MMAs per chunk (32 bytes of K each)
 constexpr int NSTAGE = 3;                // A-operand ring slots
-constexpr int EPI_WARPS = 4, PROD_WARPS = 8;
+constexpr int EPI_WARPS = 8, PROD_WARPS = 8;  // two epilogue groups of four warps
 constexpr int MMA_WARP = EPI_WARPS + PROD_WARPS;
-constexpr int THREADS = 32 * (MMA_WARP + 1);  // 416
+constexpr int THREADS = 32 * (MMA_WARP + 1);  // 544: 96 registers per thread
+constexpr int NCH = H / 32;              // 32-column chunks of a row
 constexpr int PROD_THREADS = 32 * PROD_WARPS;
-constexpr int EPI_THREADS = 32 * EPI_WARPS;
-constexpr uint32_t TMEM_COLS = 512;      // D1 buffers at columns 0 and 128, D2 at 256
+constexpr uint32_t TMEM_COLS = 512;
 
 enum TcMode { TC_EDGE_ENC = 0, TC_NODE_UPD = 1, TC_EDGE_UPD = 2, TC_CLS = 3 };
 
-// barrier indices
+// barrier indices (the per-group ones come in pairs, index + group)
 enum { B_W = 0, B_FULL = 1, B_EMPTY = B_FULL + NSTAGE, B_D1FULL = B_EMPTY + NSTAGE,
-       B_D1EMPTY = B_D1FULL + 2, B_A2FULL = B_D1EMPTY + 2, B_D2FULL = B_A2FULL + 1,
-       N_BARS = B_D2FULL + 1 };
+       B_D1EMPTY = B_D1FULL + 2, B_A2FULL = B_D1EMPTY + 2, B_D2FULL = B_A2FULL + 2,
+       B_D2EMPTY = B_D2FULL + 2, N_BARS = B_D2EMPTY + 2 };
 
 // Operand type: BF16 (2 bytes, 64 K columns per 128-byte row) or FP8 e4m3
-// (1 byte, 128 K columns per row).
+// (1 byte, 128 K columns per row).  Either way one MMA consumes 32 bytes of K,
+// which is 8 columns of an A operand held in tensor memory.
 template <bool F8>
 struct Elt {
   static constexpr int KCH = F8 ? 128 : 64;   // K columns per chunk
@@ -71,9 +77,8 @@ struct Cfg {
   static constexpr int OFF_W1 = 0;
   static constexpr int OFF_W2 = OFF_W1 + KC1 * CHUNK;
   static constexpr int OFF_A = OFF_W2 + (G2 ? C2 * CHUNK : 0);
-  static constexpr int OFF_A2 = OFF_A + NSTAGE * CHUNK;
-  // A2 holds the second GEMM's operand, then stages 128 x 64 FP32 outputs (32 KB)
-  static constexpr int OFF_PAR = OFF_A2 + (G2 ? 2 * CHUNK : 0);     // 7 x 128 floats
+  static constexpr int OFF_STG = OFF_A + NSTAGE * CHUNK;            // 8 per-warp 4 KB output stages
+  static constexpr int OFF_PAR = OFF_STG + (G2 ? EPI_WARPS * 4096 : 0);  // 7 x 128 floats
   static constexpr int OFF_BAR = OFF_PAR + 7 * H * 4;
   static constexpr int OFF_MISC = OFF_BAR + 8 * N_BARS;              // tmem addr, abort flag
   static constexpr int BYTES = OFF_MISC + 16;
@@ -119,12 +124,20 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Bounded wait that also gives up when another role raised the abort flag.
+// Bounded wait (2 s of device time, or an iteration cap) that also gives up
+// when another role raised the abort flag.  A waiting thread sleeps in
+// try_wait for up to 256 ns per poll.
 __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, int* err,
                                               volatile int* abort) {
-  for (uint32_t i = 0; i < kWaitCap; ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 255) == 255 && *abort) return false;
+  uint64_t t0 = 0;
+  for (uint32_t i = 0; i < (kWaitCap << 4); ++i) {
+    if (mbar_try_wait_sleep(bar, parity, 256)) return true;
+    if ((i & 15) == 15) {
+      if (*abort) return false;
+      const uint64_t now = globaltimer_ns();
+      if (t0 == 0) t0 = now;
+      else if (now - t0 > kWaitNs) break;
+    }
   }
   set_err(err, DERR_TIMEOUT);
   *abort = 1;
@@ -147,49 +160,73 @@ __device__ __forceinline__ const float* chunk_src(const TcArgs& a, int col0, int
   }
 }
 
-// Row statistics of x_j = sc * acc_j + b_j over the 128 accumulator columns
-// of this thread's TMEM lane (shifted sums: shift = first value).
-__device__ __forceinline__ void row_stats(uint32_t taddr, const float* __restrict__ b, float sc,
-                                          float& mean, float& rstd) {
-  float v[32];
-  float shift = 0.f;
-  float s4[4] = {0.f, 0.f, 0.f, 0.f}, q4[4] = {0.f, 0.f, 0.f, 0.f};  // independent chains
-#pragma unroll
-  for (int cc = 0; cc < 4; ++cc) {
-    tmem_ld32_wait(taddr + 32 * cc, v);
-#pragma unroll
-    for (int j = 0; j < 32; j += 4) {
-      const float4 bb = *reinterpret_cast<const float4*>(b + 32 * cc + j);
-      const float x0 = fmaf(v[j], sc, bb.x), x1 = fmaf(v[j + 1], sc, bb.y),
-                  x2 = fmaf(v[j + 2], sc, bb.z), x3 = fmaf(v[j + 3], sc, bb.w);
-      if (cc == 0 && j == 0) shift = x0;
-      const float d0 = x0 - shift, d1 = x1 - shift, d2 = x2 - shift, d3 = x3 - shift;
-      s4[0] += d0; s4[1] += d1; s4[2] += d2; s4[3] += d3;
-      q4[0] = fmaf(d0, d0, q4[0]); q4[1] = fmaf(d1, d1, q4[1]);
-      q4[2] = fmaf(d2, d2, q4[2]); q4[3] = fmaf(d3, d3, q4[3]);
-    }
-  }
-  const float s = (s4[0] + s4[1]) + (s4[2] + s4[3]), ss = (q4[0] + q4[1]) + (q4[2] + q4[3]);
-  const float ms = s * (1.0f / H);
-  mean = shift + ms;
-  const float var = fmaxf(ss * (1.0f / H) - ms * ms, 0.f);
-  rstd = 1.0f / sqrtf(var + kLnEps);
+// Two values to BF16 with ReLU, first value in the low half.
+__device__ __forceinline__ uint32_t pack_bf16_relu(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
 }
 
-// 32 normalised, ReLU'd values of columns [32 cc, 32 cc + 32).
-__device__ __forceinline__ void row_norm32(uint32_t taddr, int cc, const float* __restrict__ b,
-                                           const float* __restrict__ g, const float* __restrict__ be,
-                                           float sc, float mean, float rstd, float (&y)[32]) {
-  tmem_ld32_wait(taddr + 32 * cc, y);
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// Shared-memory float4 load kept in program order (limits how many parameter
+// loads the compiler hoists ahead of their use, and so the registers they hold).
+__device__ __forceinline__ float4 lds4(const float* p) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(smem_u32(p)));
+  return v;
+}
+
+// t = sc * acc + b over N columns, in place; returns the sum of t (fixed
+// summation order: four interleaved pair chains).
+template <int N>
+__device__ __forceinline__ float bias_sum(float* __restrict__ t, const float* __restrict__ b, float sc) {
+  float2 acc[4] = {f2(0.f, 0.f), f2(0.f, 0.f), f2(0.f, 0.f), f2(0.f, 0.f)};
+  const float2 sc2 = f2(sc, sc);
 #pragma unroll
-  for (int j = 0; j < 32; j += 4) {
-    const float4 bb = *reinterpret_cast<const float4*>(b + 32 * cc + j);
-    const float4 gg = *reinterpret_cast<const float4*>(g + 32 * cc + j);
-    const float4 ee = *reinterpret_cast<const float4*>(be + 32 * cc + j);
-    y[j] = fmaxf((fmaf(y[j], sc, bb.x) - mean) * rstd * gg.x + ee.x, 0.f);
-    y[j + 1] = fmaxf((fmaf(y[j + 1], sc, bb.y) - mean) * rstd * gg.y + ee.y, 0.f);
-    y[j + 2] = fmaxf((fmaf(y[j + 2], sc, bb.z) - mean) * rstd * gg.z + ee.z, 0.f);
-    y[j + 3] = fmaxf((fmaf(y[j + 3], sc, bb.w) - mean) * rstd * gg.w + ee.w, 0.f);
+  for (int j = 0; j < N; j += 4) {
+    const float4 bb = lds4(b + j);
+    const float2 x0 = __ffma2_rn(f2(t[j], t[j + 1]), sc2, f2(bb.x, bb.y));
+    const float2 x1 = __ffma2_rn(f2(t[j + 2], t[j + 3]), sc2, f2(bb.z, bb.w));
+    t[j] = x0.x; t[j + 1] = x0.y; t[j + 2] = x1.x; t[j + 3] = x1.y;
+    acc[(j >> 1) & 3] = __fadd2_rn(acc[(j >> 1) & 3], x0);
+    acc[((j >> 1) + 1) & 3] = __fadd2_rn(acc[((j >> 1) + 1) & 3], x1);
+  }
+  const float2 s01 = __fadd2_rn(acc[0], acc[1]), s23 = __fadd2_rn(acc[2], acc[3]);
+  const float2 s = __fadd2_rn(s01, s23);
+  return s.x + s.y;
+}
+
+// t -= mean in place over N values; returns the sum of squares of the centred values.
+template <int N>
+__device__ __forceinline__ float centre_sq(float* __restrict__ t, float mean) {
+  float2 acc[4] = {f2(0.f, 0.f), f2(0.f, 0.f), f2(0.f, 0.f), f2(0.f, 0.f)};
+  const float2 nm = f2(-mean, -mean);
+#pragma unroll
+  for (int j = 0; j < N; j += 2) {
+    const float2 d = __fadd2_rn(f2(t[j], t[j + 1]), nm);
+    t[j] = d.x; t[j + 1] = d.y;
+    acc[(j >> 1) & 3] = __ffma2_rn(d, d, acc[(j >> 1) & 3]);
+  }
+  const float2 s01 = __fadd2_rn(acc[0], acc[1]), s23 = __fadd2_rn(acc[2], acc[3]);
+  const float2 s = __fadd2_rn(s01, s23);
+  return s.x + s.y;
+}
+
+// y = (d * rstd) * g + be for N centred values d (ReLU left to the caller).
+template <int N>
+__device__ __forceinline__ void affine(float* __restrict__ d, const float* __restrict__ g,
+                                       const float* __restrict__ be, float rstd) {
+  const float2 rs = f2(rstd, rstd);
+#pragma unroll
+  for (int j = 0; j < N; j += 4) {
+    const float4 gg = lds4(g + j);
+    const float4 ee = lds4(be + j);
+    const float2 y0 = __ffma2_rn(__fmul2_rn(f2(d[j], d[j + 1]), rs), f2(gg.x, gg.y), f2(ee.x, ee.y));
+    const float2 y1 =
+        __ffma2_rn(__fmul2_rn(f2(d[j + 2], d[j + 3]), rs), f2(gg.z, gg.w), f2(ee.z, ee.w));
+    d[j] = y0.x; d[j + 1] = y0.y; d[j + 2] = y1.x; d[j + 3] = y1.y;
   }
 }
 
@@ -203,7 +240,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
   uint8_t* sW1 = smem + C::OFF_W1;
   uint8_t* sW2 = smem + C::OFF_W2;
   uint8_t* sA = smem + C::OFF_A;
-  uint8_t* sA2 = smem + C::OFF_A2;
   float* par = reinterpret_cast<float*>(smem + C::OFF_PAR);  // b1 g1 be1 b2 g2 be2 wcls
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::OFF_MISC);
@@ -218,12 +254,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
       mbar_init(&bars[B_FULL + s], PROD_WARPS);  // one arrival per producer warp
       mbar_init(&bars[B_EMPTY + s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(&bars[B_D1FULL + b], 1);
-      mbar_init(&bars[B_D1EMPTY + b], EPI_WARPS);
+    for (int g = 0; g < 2; ++g) {
+      mbar_init(&bars[B_D1FULL + g], 1);
+      // D1 is free again once the second GEMM has read the activations in it
+      // (or, for the classifier, once the epilogue group has read it)
+      mbar_init(&bars[B_D1EMPTY + g], C::G2 ? 1 : 4);
+      mbar_init(&bars[B_A2FULL + g], 4);
+      mbar_init(&bars[B_D2FULL + g], 1);
+      mbar_init(&bars[B_D2EMPTY + g], 4);
     }
-    mbar_init(&bars[B_A2FULL], EPI_WARPS);
-    mbar_init(&bars[B_D2FULL], 1);
     *abort = 0;
     fence_mbar_init();
   }
@@ -250,26 +289,24 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
 
   const int64_t n_rows = MODE == TC_NODE_UPD ? a.n_nodes : (int64_t)*a.n_edges_dev;
   const int64_t n_tiles = (n_rows + TM - 1) / TM;
+  const int64_t my_tiles = n_tiles > blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int nn = (int)a.n_nodes;
 
   if (warp >= EPI_WARPS && warp < MMA_WARP) {
     // =========================== producers =================================
-    // Flattened stream of this CTA's (tile, chunk) pairs, prefetched two chunks
-    // ahead in a three-deep register ring so that loads of the next chunks
-    // (also across tile boundaries) are in flight while one chunk is stored.
+    // Flattened stream of this CTA's (tile, chunk) pairs with the next chunk's
+    // loads in flight (also across tile boundaries) while one chunk is stored.
     // Thread t8 = pt % 8 of a row group reads bytes [16 t8, 16 t8 + 16) of each
     // 128-byte line of a 256-byte FP32 row segment (two fully coalesced loads)
     // and writes the two resulting 8-byte BF16 halves.  Row groups sharing a
     // half-warp own rows 4 apart, so those 8-byte shared stores never collide.
-    const int pt = tid - EPI_THREADS;
+    const int pt = tid - 32 * EPI_WARPS;
     const int t8 = pt & 7, rg = pt >> 3, wg = rg & 3, wi = rg >> 2;
     const int rbase = 8 * (wi >> 1) + 4 * (wg & 1) + 2 * (wi & 1) + (wg >> 1);  // 0..31
     constexpr int RPT = TM / (PROD_THREADS / 8);  // rows per producer thread
-    const int64_t my_tiles =
-        n_tiles > blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const int64_t total = my_tiles * C::KS;  // 64-column steps
     // gather indices of the tile being fetched, read when its first chunk is
-    // fetched (chunks reach the same tile in order, two ahead of the stores)
+    // fetched (chunks reach the same tile in order, one ahead of the stores)
     int sidx[RPT], didx[RPT];
 #pragma unroll
     for (int i = 0; i < RPT; ++i) sidx[i] = didx[i] = 0;
@@ -335,18 +372,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
       }
       return true;
     };
-    float4 b0[2 * RPT], b1[2 * RPT], b2[2 * RPT];
+    float4 b0[2 * RPT], b1[2 * RPT];
     fetch(0, b0);
-    fetch(1, b1);
-    for (int64_t q = 0; q < total; q += 3) {
-      fetch(q + 2, b2);
+    for (int64_t q = 0; q < total; q += 2) {
+      fetch(q + 1, b1);
       if (!store(q, b0)) break;
       if (q + 1 >= total) break;
-      fetch(q + 3, b0);
+      fetch(q + 2, b0);
       if (!store(q + 1, b1)) break;
-      if (q + 2 >= total) break;
-      fetch(q + 4, b1);
-      if (!store(q + 2, b2)) break;
     }
   } else if (warp == MMA_WARP) {
     // =========================== MMA issuer ================================
@@ -358,200 +391,218 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
       if (C::G2)
         for (int c = 0; c < C::C2; ++c)
           bulk_g2s(sW2 + c * CHUNK, a.w2 + (size_t)c * CHUNK, CHUNK, &bars[B_W]);
-      bool live = wait_or_abort(&bars[B_W], 0, a.err, abort);
-      uint32_t gchunk = 0;
-      int i = 0;
-      int pending = -1;  // local tile whose second GEMM waits for the epilogue's A2
-      auto issue_gemm2 = [&]() {
-        tc_fence_after();
+      if (wait_or_abort(&bars[B_W], 0, a.err, abort)) {
+        int64_t g1 = 0, g2 = 0;  // next local tile of the first / second GEMM
+        int c1 = 0;              // next chunk of tile g1
+        bool d1_free = false;    // D1 of tile g1 may be written
+        uint32_t gchunk = 0, idle = 0;
+        uint64_t t0 = 0;
+        while (C::G2 ? g2 < my_tiles : g1 < my_tiles) {
+          bool progress = false;
+          // second GEMM of tile g2, A = its activations in D1, into D2
+          if (C::G2 && g2 < g1) {
+            const int b = (int)(g2 & 1);
+            const uint32_t u = (uint32_t)(g2 >> 1);
+            if (mbar_try_wait(&bars[B_A2FULL + b], u & 1) &&
+                (u == 0 || mbar_try_wait(&bars[B_D2EMPTY + b], (u - 1) & 1))) {
+              tc_fence_after();
+              const uint32_t a2 = tmem + 128 * b, d2 = tmem + 256 + 128 * b;
 #pragma unroll
-        for (int c = 0; c < C::C2; ++c) {
-          const uint32_t a0 = smem_u32(sA2 + c * CHUNK), b0 = smem_u32(sW2 + c * CHUNK);
+              for (int c = 0; c < C::C2; ++c)
 #pragma unroll
-          for (int k = 0; k < KSTEPS; ++k)
-            mma_tc<F8>(tmem + 256, sdesc_k_sw128(a0 + 32 * k), sdesc_k_sw128(b0 + 32 * k),
-                       EL::IDESC, (c > 0 || k > 0) ? 1u : 0u);
-        }
-        mma_commit(&bars[B_D2FULL]);
-        pending = -1;
-      };
-      // Wait for `bar`; meanwhile issue the pending second GEMM as soon as its
-      // operand is ready, so it never queues behind the next tile's gather.
-      auto wait_poll = [&](uint64_t* bar, uint32_t parity) {
-        for (uint32_t it = 0; it < kWaitCap; ++it) {
-          if (mbar_try_wait(bar, parity)) return true;
-          if (C::G2 && pending >= 0 && mbar_try_wait(&bars[B_A2FULL], pending & 1)) issue_gemm2();
-          if ((it & 255) == 255 && *abort) return false;
-        }
-        set_err(a.err, DERR_TIMEOUT);
-        *abort = 1;
-        return false;
-      };
-      for (int64_t tile = blockIdx.x; live && tile < n_tiles; tile += gridDim.x, ++i) {
-        const int b = i & 1;
-        const uint32_t use = i >> 1;
-        if (use > 0 && !wait_poll(&bars[B_D1EMPTY + b], (use - 1) & 1)) break;
-        tc_fence_after();
-        const uint32_t d1 = tmem + 128 * b;
-        for (int c = 0; c < C::KC1; ++c) {
-          const int slot = gchunk % NSTAGE;
-          if (!wait_poll(&bars[B_FULL + slot], (gchunk / NSTAGE) & 1)) {
-            live = false;
-            break;
+                for (int k = 0; k < KSTEPS; ++k)
+                  mma_tc_ts<F8>(d2, a2 + 8 * (c * KSTEPS + k),
+                                sdesc_k_sw128(smem_u32(sW2 + c * CHUNK) + 32 * k), EL::IDESC,
+                                (c > 0 || k > 0) ? 1u : 0u);
+              mma_commit(&bars[B_D2FULL + b]);
+              mma_commit(&bars[B_D1EMPTY + b]);
+              ++g2;
+              progress = true;
+            }
           }
-          tc_fence_after();
-          const uint32_t a0 = smem_u32(sA + slot * CHUNK), b0 = smem_u32(sW1 + c * CHUNK);
+          // next ring slot of the first GEMM of tile g1, into D1
+          if (g1 < my_tiles) {
+            const int b = (int)(g1 & 1);
+            const uint32_t u = (uint32_t)(g1 >> 1);
+            if (!d1_free) d1_free = u == 0 || mbar_try_wait(&bars[B_D1EMPTY + b], (u - 1) & 1);
+            const int slot = (int)(gchunk % NSTAGE);
+            if (d1_free && mbar_try_wait(&bars[B_FULL + slot], (gchunk / NSTAGE) & 1)) {
+              tc_fence_after();
+              const uint32_t a0 = smem_u32(sA + slot * CHUNK), w0 = smem_u32(sW1 + c1 * CHUNK);
 #pragma unroll
-          for (int k = 0; k < KSTEPS; ++k)
-            mma_tc<F8>(d1, sdesc_k_sw128(a0 + 32 * k), sdesc_k_sw128(b0 + 32 * k), EL::IDESC,
-                       (c > 0 || k > 0) ? 1u : 0u);
-          mma_commit(&bars[B_EMPTY + slot]);
-          ++gchunk;
-        }
-        if (!live) break;
-        mma_commit(&bars[B_D1FULL + b]);
-        if (C::G2) {
-          if (pending >= 0) {
-            if (!wait_or_abort(&bars[B_A2FULL], pending & 1, a.err, abort)) break;
-            issue_gemm2();
+              for (int k = 0; k < KSTEPS; ++k)
+                mma_tc<F8>(tmem + 128 * b, sdesc_k_sw128(a0 + 32 * k), sdesc_k_sw128(w0 + 32 * k),
+                           EL::IDESC, (c1 > 0 || k > 0) ? 1u : 0u);
+              mma_commit(&bars[B_EMPTY + slot]);
+              ++gchunk;
+              if (++c1 == C::KC1) {
+                mma_commit(&bars[B_D1FULL + b]);
+                c1 = 0;
+                ++g1;
+                d1_free = false;
+              }
+              progress = true;
+            }
           }
-          pending = i;
+          if (progress) {
+            idle = 0;
+            t0 = 0;
+          } else if ((++idle & 63) == 0) {
+            if (*abort) break;
+            const uint64_t now = globaltimer_ns();
+            if (t0 == 0) {
+              t0 = now;
+            } else if (now - t0 > kWaitNs || idle > (kWaitCap << 4)) {
+              set_err(a.err, DERR_TIMEOUT);
+              *abort = 1;
+              break;
+            }
+          }
         }
       }
-      if (C::G2 && pending >= 0 && !*abort &&
-          wait_or_abort(&bars[B_A2FULL], pending & 1, a.err, abort))
-        issue_gemm2();
     }
   } else {
     // =========================== epilogue ==================================
-    const int r = tid;  // TMEM lane == tile row
-    const uint32_t lane_off = static_cast<uint32_t>(32 * warp) << 16;
-    int i = 0;
-    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++i) {
-      const int b = i & 1;
-      const int64_t gr = tile * TM + r;
-      const bool valid = gr < n_rows;
-      if (!wait_or_abort(&bars[B_D1FULL + b], (i >> 1) & 1, a.err, abort)) break;
+    const int grp = warp >> 2, qr = warp & 3;  // group, TMEM lane quarter
+    const int r = 32 * qr + lane;              // TMEM lane == tile row
+    const uint32_t lane_off = static_cast<uint32_t>(32 * qr) << 16;
+    const uint32_t t1 = tmem + 128 * grp + lane_off;        // D1, then the activations
+    const uint32_t t2 = tmem + 256 + 128 * grp + lane_off;  // D2
+    float* stg = reinterpret_cast<float*>(smem + C::OFF_STG + 4096 * warp);  // 32 rows x 32 FP32
+    // LayerNorm statistics of t = sc * acc + b over the row's 128 columns (the
+    // mean, then the centred second moment), from 32-column chunks read from TMEM.
+    auto layer_stats = [&](uint32_t tb, float (&t)[32], const float* b, float sc, float& mean,
+                           float& rstd) {
+      float s = 0.f;
+#pragma unroll 1
+      for (int ch = 0; ch < NCH; ++ch) {
+        tmem_ld32_wait(tb + 32 * ch, t);
+        s += bias_sum<32>(t, b + 32 * ch, sc);
+      }
+      mean = s * (1.0f / H);
+      float q = 0.f;
+#pragma unroll 1
+      for (int ch = 0; ch < NCH; ++ch) {
+        tmem_ld32_wait(tb + 32 * ch, t);
+        bias_sum<32>(t, b + 32 * ch, sc);
+        q += centre_sq<32>(t, mean);
+      }
+      rstd = 1.0f / sqrtf(q * (1.0f / H) + kLnEps);
+    };
+    // Chunk ch of the row, normalised (ReLU left to the caller).
+    auto norm_chunk = [&](uint32_t tb, float (&t)[32], int ch, const float* p3, float sc,
+                          float mean, float rstd) {
+      tmem_ld32_wait(tb + 32 * ch, t);
+      bias_sum<32>(t, p3 + 32 * ch, sc);
+      centre_sq<32>(t, mean);
+      affine<32>(t, p3 + H + 32 * ch, p3 + 2 * H + 32 * ch, rstd);
+    };
+    const float* resid = MODE == TC_NODE_UPD ? a.h : a.e;
+    float* outp = MODE == TC_NODE_UPD ? a.h_out : a.e;
+    for (int64_t i = grp; i < my_tiles; i += 2) {
+      const uint32_t ph = (uint32_t)(i >> 1) & 1;
+      const int64_t row0 = (blockIdx.x + i * gridDim.x) * TM;
+      const int64_t gr = row0 + r;
+      if (!wait_or_abort(&bars[B_D1FULL + grp], ph, a.err, abort)) break;
       tc_fence_after();
-      const uint32_t t1 = tmem + 128 * b + lane_off;
+      float t[32];
       float mean, rstd;
-      row_stats(t1, par, a.ws1, mean, rstd);
-      float y[32];
+      layer_stats(t1, t, par, a.ws1, mean, rstd);
       if constexpr (MODE == TC_CLS) {
-        float p = 0.f;
+        float2 acc[2] = {f2(0.f, 0.f), f2(0.f, 0.f)};
+#pragma unroll 1
+        for (int ch = 0; ch < NCH; ++ch) {
+          norm_chunk(t1, t, ch, par, a.ws1, mean, rstd);
+          const float* wc = par + 6 * H + 32 * ch;
 #pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
-          row_norm32(t1, cc, par, par + H, par + 2 * H, a.ws1, mean, rstd, y);
-#pragma unroll
-          for (int j = 0; j < 32; ++j) p = fmaf(y[j], par[6 * H + 32 * cc + j], p);
+          for (int j = 0; j < 32; j += 4) {
+            const float4 ww = lds4(wc + j);
+            acc[0] = __ffma2_rn(f2(fmaxf(t[j], 0.f), fmaxf(t[j + 1], 0.f)), f2(ww.x, ww.y), acc[0]);
+            acc[1] = __ffma2_rn(f2(fmaxf(t[j + 2], 0.f), fmaxf(t[j + 3], 0.f)), f2(ww.z, ww.w), acc[1]);
+          }
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&bars[B_D1EMPTY + b]);
-        if (valid) a.logits[gr] = p + __ldg(a.bcls);
+        if (lane == 0) mbar_arrive(&bars[B_D1EMPTY + grp]);
+        const float2 pp = __fadd2_rn(acc[0], acc[1]);
+        if (gr < n_rows) a.logits[gr] = (pp.x + pp.y) + __ldg(a.bcls);
       } else {
-#pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
-          row_norm32(t1, cc, par, par + H, par + 2 * H, a.ws1, mean, rstd, y);
+        // Activations of chunk ch (32 columns) go to TMEM columns [16 ch, 16 ch + 16)
+        // as BF16 pairs (or [8 ch, 8 ch + 8) as e4m3 quads): accumulator columns
+        // this warp has already read in this pass, as chunks run in order.
+#pragma unroll 1
+        for (int ch = 0; ch < NCH; ++ch) {
+          norm_chunk(t1, t, ch, par, a.ws1, mean, rstd);
           if constexpr (F8) {
+            uint32_t v[8];
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
-              uint4 w;
-              w.x = pack_e4m3x4(y[16 * q + 0], y[16 * q + 1], y[16 * q + 2], y[16 * q + 3]);
-              w.y = pack_e4m3x4(y[16 * q + 4], y[16 * q + 5], y[16 * q + 6], y[16 * q + 7]);
-              w.z = pack_e4m3x4(y[16 * q + 8], y[16 * q + 9], y[16 * q + 10], y[16 * q + 11]);
-              w.w = pack_e4m3x4(y[16 * q + 12], y[16 * q + 13], y[16 * q + 14], y[16 * q + 15]);
-              *reinterpret_cast<uint4*>(sA2 + sw128(r, 2 * cc + q)) = w;
-            }
+            for (int q = 0; q < 8; ++q)
+              v[q] = pack_e4m3x4(fmaxf(t[4 * q], 0.f), fmaxf(t[4 * q + 1], 0.f),
+                                 fmaxf(t[4 * q + 2], 0.f), fmaxf(t[4 * q + 3], 0.f));
+            tmem_st8(t1 + 8 * ch, v);
           } else {
-            uint8_t* dst2 = sA2 + (cc >> 1) * CHUNK;
+            uint32_t v[16];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              uint4 w;
-              w.x = pack_bf16(y[8 * q + 0], y[8 * q + 1]);
-              w.y = pack_bf16(y[8 * q + 2], y[8 * q + 3]);
-              w.z = pack_bf16(y[8 * q + 4], y[8 * q + 5]);
-              w.w = pack_bf16(y[8 * q + 6], y[8 * q + 7]);
-              *reinterpret_cast<uint4*>(dst2 + sw128(r, 4 * (cc & 1) + q)) = w;
-            }
+            for (int q = 0; q < 16; ++q) v[q] = pack_bf16_relu(t[2 * q], t[2 * q + 1]);
+            tmem_st16(t1 + 16 * ch, v);
           }
         }
-        fence_proxy_async();
+        tmem_wait_st();
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(&bars[B_D1EMPTY + b]);
-          mbar_arrive(&bars[B_A2FULL]);
-        }
-        if (!wait_or_abort(&bars[B_D2FULL], i & 1, a.err, abort)) break;
+        if (lane == 0) mbar_arrive(&bars[B_A2FULL + grp]);
+        // This lane's rows in the coalesced layout are crow + 4 it (it < 8); row
+        // crow + 4 it exists iff 4 it < nval.
+        const int u8 = lane & 7;
+        const int64_t crow = row0 + 32 * qr + (lane >> 3);
+        const int nval = (int)(n_rows - crow < 32 ? (n_rows - crow > 0 ? n_rows - crow : 0) : 32);
+        const int64_t coff = crow * H + 4 * u8;
+        if (!wait_or_abort(&bars[B_D2FULL + grp], ph, a.err, abort)) break;
         tc_fence_after();
-        const uint32_t t2 = tmem + 256 + lane_off;
-        row_stats(t2, par + 3 * H, a.ws2, mean, rstd);
-        // The second GEMM has consumed A2, so its 32 KB stage the FP32 output:
-        // 64 columns at a time, row-per-thread writes with 16-byte units
-        // XOR-swizzled by (row % 8), then coalesced residual loads and stores
-        // (16 lanes cover one 256-byte row segment).
-        float* stg = reinterpret_cast<float*>(sA2);
-        const int64_t row0 = tile * TM;
+        layer_stats(t2, t, par + 3 * H, a.ws2, mean, rstd);
+        // Pass p: normalise 32 columns (re-read from TMEM) and stage them row per
+        // thread with 16-byte units XOR-swizzled by (row % 8); read them back in
+        // the coalesced layout of the stores (8 lanes per 128-byte row segment,
+        // 4 rows per instruction), add the residual (requested before the
+        // staging) and store.  No warp barrier follows the global stores.
+#pragma unroll 1
+        for (int p = 0; p < NCH; ++p) {
+          norm_chunk(t2, t, p, par + 3 * H, a.ws2, mean, rstd);
+          if (p == NCH - 1) {  // D2 fully read: the group's next second GEMM may overwrite it
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars[B_D2EMPTY + grp]);
+          }
+          float4 res[8];
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          // residual of the rows this thread stores in the coalesced pass, in two
-          // batches fetched ahead of their use so the latency hides behind the
-          // normalisation (batch a) and behind batch a's stores (batch b)
-          const int l16 = lane & 15;
-          constexpr int NIT = TM / (2 * EPI_WARPS);
-          constexpr int NB = 4;
-          float4 ra[NB], rb[NB];
-          auto fetch_res = [&](int it0, float4 (&rr4)[NB]) {
+          for (int it = 0; it < 8; ++it) {
+            res[it] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (MODE != TC_EDGE_ENC && 4 * it < nval)
+              res[it] = *reinterpret_cast<const float4*>(resid + coff + 4 * it * H + 32 * p);
+          }
 #pragma unroll
-            for (int k = 0; k < NB; ++k) {
-              const int rr = ((it0 + k) * EPI_WARPS + warp) * 2 + (lane >> 4);
-              const int64_t g2 = row0 + rr;
-              rr4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-              if (g2 < n_rows) {
-                const int64_t off = g2 * H + 64 * half + 4 * l16;
-                if constexpr (MODE == TC_NODE_UPD) rr4[k] = *reinterpret_cast<const float4*>(a.h + off);
-                if constexpr (MODE == TC_EDGE_UPD) rr4[k] = *reinterpret_cast<const float4*>(a.e + off);
-              }
-            }
-          };
-          auto store_rows = [&](int it0, const float4 (&rr4)[NB]) {
+          for (int u = 0; u < 8; ++u)
+            *reinterpret_cast<float4*>(stg + 32 * lane + 4 * (u ^ (lane & 7))) =
+                make_float4(fmaxf(t[4 * u], 0.f), fmaxf(t[4 * u + 1], 0.f),
+                            fmaxf(t[4 * u + 2], 0.f), fmaxf(t[4 * u + 3], 0.f));
+          __syncwarp();
+          float4 v[8];
 #pragma unroll
-            for (int k = 0; k < NB; ++k) {
-              const int rr = ((it0 + k) * EPI_WARPS + warp) * 2 + (lane >> 4);
-              const int64_t g2 = row0 + rr;
-              const float4 v = *reinterpret_cast<const float4*>(stg + rr * 64 + 4 * (l16 ^ (rr & 7)));
-              if (g2 < n_rows) {
-                const float4 o = make_float4(v.x + rr4[k].x, v.y + rr4[k].y, v.z + rr4[k].z,
-                                             v.w + rr4[k].w);
-                float* outp = MODE == TC_NODE_UPD ? a.h_out : a.e;
-                *reinterpret_cast<float4*>(outp + g2 * H + 64 * half + 4 * l16) = o;
-              }
-            }
-          };
-          fetch_res(0, ra);
+          for (int it = 0; it < 8; ++it) {
+            const int lr = 4 * it + (lane >> 3);
+            v[it] = *reinterpret_cast<const float4*>(stg + 32 * lr + 4 * (u8 ^ (lr & 7)));
+          }
+          __syncwarp();  // the stage is free for the next pass
 #pragma unroll
-          for (int cc = 0; cc < 2; ++cc) {
-            row_norm32(t2, 2 * half + cc, par + 3 * H, par + 4 * H, par + 5 * H, a.ws2, mean, rstd, y);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const int un = (8 * cc + q) ^ (r & 7);
-              *reinterpret_cast<float4*>(stg + r * 64 + 4 * un) =
-                  make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
+          for (int it = 0; it < 8; ++it) {
+            if (4 * it < nval) {
+              const float2 o0 = __fadd2_rn(f2(v[it].x, v[it].y), f2(res[it].x, res[it].y));
+              const float2 o1 = __fadd2_rn(f2(v[it].z, v[it].w), f2(res[it].z, res[it].w));
+              *reinterpret_cast<float4*>(outp + coff + 4 * it * H + 32 * p) =
+                  make_float4(o0.x, o0.y, o1.x, o1.y);
             }
           }
-          fetch_res(NB, rb);
-          asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
-#pragma unroll
-          for (int it0 = 0; it0 < NIT; it0 += 2 * NB) {
-            store_rows(it0, ra);
-            if (it0 + 2 * NB < NIT) fetch_res(it0 + 2 * NB, ra);
-            store_rows(it0 + NB, rb);
-            if (it0 + 3 * NB < NIT) fetch_res(it0 + 3 * NB, rb);
-          }
-          asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
         }
-        tc_fence_before();
       }
     }
   }
