@@ -231,6 +231,7 @@ etx_status etx_ctx_create(const etx_config* cfg, int32_t device, etx_ctx** out) 
   chk(dmalloc(ctx, &ctx->m, (size_t)N * 2 * H, "messages"));
   chk(dmalloc(ctx, &ctx->e, (size_t)E * H, "edge features"));
   chk(dmalloc(ctx, &ctx->parent, (size_t)N, "union-find parents"));
+  if (H == 128) chk(dmalloc(ctx, &ctx->h_lp, (size_t)N * 2 * H, "low-precision node features"));
   if (cfg->train) {
     const size_t L1 = (size_t)cfg->n_iters + 1, R = (size_t)(N > E ? N : E);
     chk(dmalloc(ctx, &ctx->h_ck, L1 * N * H, "node checkpoints"));
@@ -266,7 +267,7 @@ etx_status etx_ctx_destroy(etx_ctx* ctx) {
                   ctx->hit_cnt, ctx->scan_tmp, ctx->out_off, ctx->in_off, ctx->in_cnt,
                   ctx->perm_in, ctx->h, ctx->m, ctx->e, ctx->parent, ctx->h_ck, ctx->e_ck,
                   ctx->de, ctx->dh, ctx->bw_X, ctx->bw_DX, ctx->bw_R1, ctx->bw_DA1, ctx->bw_DY1,
-                  ctx->bw_DY1N1, ctx->bw_DA2, ctx->bw_DY2, ctx->bw_DY2N2};
+                  ctx->bw_DY1N1, ctx->bw_DA2, ctx->bw_DY2, ctx->bw_DY2N2, ctx->h_lp};
   for (void* p : bufs)
     if (p) cudaFree(p);
   for (auto& r : ctx->prof) {

@@ -110,6 +110,10 @@ struct etx_ctx {
   float* m = nullptr;            // [max_hits * 2H]
   float* e = nullptr;            // [max_edges * H]
 
+  // tensor-core paths: h rounded to the operand type (BF16 rows of 256 bytes,
+  // or e4m3 rows of 128 bytes) for the edge blocks' gathers
+  uint8_t* h_lp = nullptr;       // [max_hits * 256 bytes]
+
   // components
   int32_t* parent = nullptr;     // [max_hits]
 
@@ -174,6 +178,8 @@ cudaError_t launch_adam(etx_ctx* ctx, float* p, const float* g, float* m, float*
                         float lr, float b1, float b2, float eps, int64_t step, cudaStream_t s);
 
 // gnn_tc.cu (hidden == 128 only)
+// ctx->h_lp = h rounded to BF16 (or e4m3) for rows [0, N)
+cudaError_t launch_h_lowp(etx_ctx* ctx, int64_t N, bool f8, cudaStream_t s);
 // f8: e4m3 operands (kind::f8f6f4), else BF16 (kind::f16)
 cudaError_t launch_edge_encoder_tc(etx_ctx* ctx, int64_t N, const int32_t* src, const int32_t* dst,
                                    const int32_t* n_edges_dev, bool f8, cudaStream_t s);

@@ -127,8 +127,8 @@ __global__ void __launch_bounds__(kTileThreads) k_block_bwd(BwdArgs a) {
     if constexpr (MODE == B_EDGE_ENC || MODE == B_EDGE_UPD) {
       if (tid < kTileM) {
         const int64_t r = row0 + tid;
-        s_src[tid] = r < n_rows ? min(max(a.src[r], 0), nn - 1) : 0;
-        s_dst[tid] = r < n_rows ? min(max(a.dst[r], 0), nn - 1) : 0;
+        s_src[tid] = r < n_rows ? min(max(a.src[r], 0), max(nn - 1, 0)) : 0;
+        s_dst[tid] = r < n_rows ? min(max(a.dst[r], 0), max(nn - 1, 0)) : 0;
       }
     }
     // ---- forward recompute: GEMM 1 -------------------------------------------

@@ -176,8 +176,8 @@ __global__ void __launch_bounds__(kTileThreads) k_mlp(MlpArgs a) {
         const int64_t r = row0 + tid;
         // out-of-range ids are flagged by the index pass; clamp so reads stay in bounds
         const int nn = (int)a.n_rows;
-        s_src[tid] = r < n_rows ? min(max(a.src[r], 0), nn - 1) : 0;
-        s_dst[tid] = r < n_rows ? min(max(a.dst[r], 0), nn - 1) : 0;
+        s_src[tid] = r < n_rows ? min(max(a.src[r], 0), max(nn - 1, 0)) : 0;
+        s_dst[tid] = r < n_rows ? min(max(a.dst[r], 0), max(nn - 1, 0)) : 0;
       }
     }
     TileAcc<H> acc;
@@ -297,6 +297,7 @@ cudaError_t forward(etx_ctx* ctx, const float* x, const float* y, const float* z
   a.blk = ctx->w.node_enc;
   launch_mlp<H, NODE_ENC>(ctx, a, N, s);
   if (tc) {
+    chain(launch_h_lowp(ctx, N, f8, s));
     chain(launch_edge_encoder_tc(ctx, N, src, dst, n_edges_dev, f8, s));
   } else {
     a.blk = ctx->w.edge_enc;

@@ -1,25 +1,29 @@
 // Interaction-network MLP blocks on the 5th-generation tensor cores
 // (tcgen05, BF16 or e4m3 operands, FP32 accumulation in tensor memory).
 //
-// Persistent kernel, one CTA per SM, 544 threads in three roles that run
-// concurrently over the CTA's 128-row tiles:
-//   warps 8-15 producers: gather the block's input rows ([h_i, h_j],
-//              [h, m_out, m_in], [e, h_i, h_j] or e) from the FP32 streams,
-//              round them to the operand type and write them, 64 columns at a
-//              time, into a 3-slot ring in the K-major 128-byte-swizzle layout;
-//              coalesced (8 threads per 256-byte row segment), one chunk
-//              prefetched in registers;
-//   warp 16    MMA issuer (one thread), an event loop over two queues: the
+// Persistent kernel, one CTA per SM, 512 threads (16 warps, so 128 registers
+// a thread) in three roles that run concurrently over the CTA's 128-row tiles:
+//   warps 8-14 producers: fill a 3-slot ring of A-operand chunks (128 rows x
+//              128 bytes, K-major 128-byte swizzle).  Columns that come from
+//              the FP32 streams (e, [h, m_out, m_in]) are loaded coalesced,
+//              rounded to the operand type and stored, one step of loads in
+//              flight in registers; gathered node rows ([h_i, h_j] of the edge
+//              blocks) are copied without conversion from a low-precision copy
+//              of h by asynchronous 16-byte copies that the ring's mbarrier
+//              counts;
+//   warp 15    MMA issuer (one thread), an event loop over two queues: the
 //              first GEMM of the next tile, one ring slot at a time, and the
 //              second GEMM of the oldest tile whose activations are ready;
 //   warps 0-7  epilogue, two groups of four warps that take alternate tiles, so
 //              that one group's second epilogue overlaps the other's first.
-//              Warp w reads TMEM lanes 32 (w % 4) .. +31, one row per thread.
-//              Bias + LayerNorm + ReLU of the first GEMM are written back to
-//              tensor memory, over the accumulator columns already consumed, as
-//              the A operand of the second GEMM; bias + LayerNorm + ReLU + FP32
-//              residual of the second are staged per warp in shared memory and
-//              stored coalesced (or, for the classifier, reduced to the logit).
+//              Warp w reads TMEM lanes 32 (w % 4) .. +31, one row per thread,
+//              64 columns per wait.  Bias + LayerNorm (one pass of shifted
+//              sums) + ReLU of the first GEMM are written back to tensor memory,
+//              over the accumulator columns already consumed, as the A operand
+//              of the second GEMM; bias + LayerNorm + ReLU + FP32 residual of
+//              the second are staged per warp in shared memory and stored
+//              coalesced (or, for the classifier, reduced to the logit); the
+//              node update also writes the low-precision copy of h.
 //              Elementwise math uses the packed FP32x2 instructions.
 // Tensor memory (512 columns): group g owns D1 at column 128 g (first GEMM,
 // then its activations in the first 64 columns) and D2 at 256 + 128 g.
@@ -43,10 +47,11 @@ constexpr int CHUNK = TM * 128;          // 16 KB operand chunk: 128 rows x 128 
 constexpr int SUB = 64;                  // K columns a producer fetches per step (256 B FP32)
 constexpr int KSTEPS = 4;                // MMAs per chunk (32 bytes of K each)
 constexpr int NSTAGE = 3;                // A-operand ring slots
-constexpr int EPI_WARPS = 8, PROD_WARPS = 8;  // two epilogue groups of four warps
+// 16 warps: an SM sub-partition then holds four, and each thread 128 registers
+constexpr int EPI_WARPS = 8, PROD_WARPS = 7;  // two epilogue groups of four warps
 constexpr int MMA_WARP = EPI_WARPS + PROD_WARPS;
-constexpr int THREADS = 32 * (MMA_WARP + 1);  // 544: 96 registers per thread
-constexpr int NCH = H / 32;              // 32-column chunks of a row
+constexpr int THREADS = 32 * (MMA_WARP + 1);  // 512
+constexpr int NCH = H / 64;              // 64-column chunks of a row (two TMEM loads, one wait)
 constexpr int PROD_THREADS = 32 * PROD_WARPS;
 constexpr uint32_t TMEM_COLS = 512;
 
@@ -100,6 +105,7 @@ struct TcArgs {
   const float *b1, *g1, *be1, *b2, *g2, *be2;
   const float* wcls;  // classifier last Linear [H]
   const float* bcls;  // [1]
+  uint8_t* h_lp;      // h rounded to the operand type (node update writes it)
   int* err;
 };
 
@@ -214,6 +220,41 @@ __device__ __forceinline__ float centre_sq(float* __restrict__ t, float mean) {
   return s.x + s.y;
 }
 
+// t = sc * acc + b over N columns, in place; adds the sums of d = t - shift and
+// of d^2 to s and q (four interleaved pair chains, fixed order).
+template <int N>
+__device__ __forceinline__ void shifted_sums(float* __restrict__ t, const float* __restrict__ b,
+                                             float sc, float shift, float& s, float& q) {
+  float2 as[2] = {f2(0.f, 0.f), f2(0.f, 0.f)}, aq[2] = {f2(0.f, 0.f), f2(0.f, 0.f)};
+  const float2 sc2 = f2(sc, sc), ns = f2(-shift, -shift);
+#pragma unroll
+  for (int j = 0; j < N; j += 4) {
+    const float4 bb = lds4(b + j);
+    const float2 x0 = __ffma2_rn(f2(t[j], t[j + 1]), sc2, f2(bb.x, bb.y));
+    const float2 x1 = __ffma2_rn(f2(t[j + 2], t[j + 3]), sc2, f2(bb.z, bb.w));
+    t[j] = x0.x; t[j + 1] = x0.y; t[j + 2] = x1.x; t[j + 3] = x1.y;
+    const float2 d0 = __fadd2_rn(x0, ns), d1 = __fadd2_rn(x1, ns);
+    as[0] = __fadd2_rn(as[0], d0);
+    as[1] = __fadd2_rn(as[1], d1);
+    aq[0] = __ffma2_rn(d0, d0, aq[0]);
+    aq[1] = __ffma2_rn(d1, d1, aq[1]);
+  }
+  const float2 ss = __fadd2_rn(as[0], as[1]), qq = __fadd2_rn(aq[0], aq[1]);
+  s += ss.x + ss.y;
+  q += qq.x + qq.y;
+}
+
+// t -= mean over N values.
+template <int N>
+__device__ __forceinline__ void centre(float* __restrict__ t, float mean) {
+  const float2 nm = f2(-mean, -mean);
+#pragma unroll
+  for (int j = 0; j < N; j += 2) {
+    const float2 d = __fadd2_rn(f2(t[j], t[j + 1]), nm);
+    t[j] = d.x; t[j + 1] = d.y;
+  }
+}
+
 // y = (d * rstd) * g + be for N centred values d (ReLU left to the caller).
 template <int N>
 __device__ __forceinline__ void affine(float* __restrict__ d, const float* __restrict__ g,
@@ -294,75 +335,58 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
 
   if (warp >= EPI_WARPS && warp < MMA_WARP) {
     // =========================== producers =================================
-    // Flattened stream of this CTA's (tile, chunk) pairs with the next chunk's
-    // loads in flight (also across tile boundaries) while one chunk is stored.
-    // Thread t8 = pt % 8 of a row group reads bytes [16 t8, 16 t8 + 16) of each
-    // 128-byte line of a 256-byte FP32 row segment (two fully coalesced loads)
-    // and writes the two resulting 8-byte BF16 halves.  Row groups sharing a
-    // half-warp own rows 4 apart, so those 8-byte shared stores never collide.
+    // Ring chunks are filled in order.  Chunks of FP32 stream columns are
+    // converted by the producer threads: a 64-column step of the tile is 2048
+    // float4 pieces, piece f = pt + PROD_THREADS k is row f / 16, columns
+    // 4 (f % 16) .. +3, so consecutive threads read consecutive 16 bytes of a
+    // row (coalesced) and write 8 (BF16) or 4 (e4m3) bytes of its swizzled
+    // operand row.  Chunks of gathered node rows ([h_i, h_j] of the edge
+    // blocks) are copied from the low-precision copy of h with asynchronous
+    // 16-byte copies: piece f is row f / 8, 16-byte unit f % 8, no conversion.
     const int pt = tid - 32 * EPI_WARPS;
-    const int t8 = pt & 7, rg = pt >> 3, wg = rg & 3, wi = rg >> 2;
-    const int rbase = 8 * (wi >> 1) + 4 * (wg & 1) + 2 * (wi & 1) + (wg >> 1);  // 0..31
-    constexpr int RPT = TM / (PROD_THREADS / 8);  // rows per producer thread
-    const int64_t total = my_tiles * C::KS;  // 64-column steps
-    // gather indices of the tile being fetched, read when its first chunk is
-    // fetched (chunks reach the same tile in order, one ahead of the stores)
-    int sidx[RPT], didx[RPT];
+    constexpr int NF = (TM * SUB / 4 + PROD_THREADS - 1) / PROD_THREADS;  // float4 pieces per thread
+    constexpr int NG = (TM * 8 + PROD_THREADS - 1) / PROD_THREADS;        // 16-byte copies per thread
+    constexpr bool GATHER = MODE == TC_EDGE_ENC || MODE == TC_EDGE_UPD;
+    // 64-column FP32 steps per tile done by the threads (the copies do the rest)
+    constexpr int SE = GATHER ? (MODE == TC_EDGE_UPD ? H / SUB : 0) : C::KS;
+    // Loads of step c (64 columns of the FP32 block input) of local tile t.
+    auto fetch = [&](int64_t t, int c, float4 (&f)[NF]) {
+      if (t >= my_tiles) return;
+      const int64_t row0 = (blockIdx.x + t * gridDim.x) * TM;
 #pragma unroll
-    for (int i = 0; i < RPT; ++i) sidx[i] = didx[i] = 0;
-    auto fetch = [&](int64_t q, float4 (&f)[2 * RPT]) {
-      if (q >= total) return;
-      const int64_t row0 = (blockIdx.x + (q / C::KS) * gridDim.x) * TM;
-      const int c = (int)(q % C::KS);
-      if constexpr (MODE == TC_EDGE_ENC || MODE == TC_EDGE_UPD) {
-        if (c == 0) {
-#pragma unroll
-          for (int i = 0; i < RPT; ++i) {
-            const int64_t gr = row0 + rbase + 32 * i;
-            sidx[i] = gr < n_rows ? min(max(a.src[gr], 0), nn - 1) : 0;
-            didx[i] = gr < n_rows ? min(max(a.dst[gr], 0), nn - 1) : 0;
-          }
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < RPT; ++i) {
-        const int64_t gr = row0 + rbase + 32 * i;
-        if (gr < n_rows) {
-          const float* p = chunk_src<MODE>(a, SUB * c, gr, sidx[i], didx[i]) + 4 * t8;
-          f[2 * i] = *reinterpret_cast<const float4*>(p);
-          f[2 * i + 1] = *reinterpret_cast<const float4*>(p + 32);
-        } else {
-          f[2 * i] = make_float4(0.f, 0.f, 0.f, 0.f);
-          f[2 * i + 1] = f[2 * i];
-        }
+      for (int k = 0; k < NF; ++k) {
+        const int fi = pt + PROD_THREADS * k;
+        const int64_t gr = row0 + (fi >> 4);
+        f[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (fi < TM * SUB / 4 && gr < n_rows)
+          f[k] = *reinterpret_cast<const float4*>(chunk_src<MODE>(a, SUB * c, gr, 0, 0) + 4 * (fi & 15));
       }
     };
-    auto store = [&](int64_t q, const float4 (&f)[2 * RPT]) {
-      const int64_t j = q / EL::SUBS;            // ring chunk
-      const int hpart = (int)(q % EL::SUBS);     // which 64 columns of it
-      const int slot = (int)(j % NSTAGE);
+    // Wait until ring chunk j's slot is free again (its previous round consumed).
+    auto slot_free = [&](int64_t j) {
       const uint32_t round = (uint32_t)(j / NSTAGE);
-      if (hpart == 0 && round > 0 &&
-          !wait_or_abort(&bars[B_EMPTY + slot], (round - 1) & 1, a.err, abort))
-        return false;
-      const uint32_t dstc = smem_u32(sA + slot * CHUNK);
+      return round == 0 ||
+             wait_or_abort(&bars[B_EMPTY + (int)(j % NSTAGE)], (round - 1) & 1, a.err, abort);
+    };
+    // Convert and store step c of local tile t.
+    auto store = [&](int64_t t, int c, const float4 (&f)[NF]) {
+      const int64_t j = t * C::KC1 + c / EL::SUBS;  // ring chunk
+      const int hpart = c % EL::SUBS;              // which 64 columns of it
+      const int slot = (int)(j % NSTAGE);
+      if (hpart == 0 && !slot_free(j)) return false;
+      uint8_t* dstc = sA + slot * CHUNK;
 #pragma unroll
-      for (int i = 0; i < RPT; ++i) {
-        const int r = rbase + 32 * i;
-#pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-          const float4 v = f[2 * i + hh];
-          if constexpr (F8) {
-            // columns 64 hpart + 32 hh + 4 t8 .. +3: 16 values per 16-byte unit
-            const uint32_t addr = dstc + sw128(r, 4 * hpart + 2 * hh + (t8 >> 2)) + 4 * (t8 & 3);
-            asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr), "r"(pack_e4m3x4(v.x, v.y, v.z, v.w))
-                         : "memory");
-          } else {
-            const uint32_t addr = dstc + sw128(r, 4 * hh + (t8 >> 1)) + 8 * (t8 & 1);
-            asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(pack_bf16(v.x, v.y)),
-                         "r"(pack_bf16(v.z, v.w))
-                         : "memory");
-          }
+      for (int k = 0; k < NF; ++k) {
+        const int fi = pt + PROD_THREADS * k;
+        if (fi < TM * SUB / 4) {
+          const int r = fi >> 4, u = fi & 15;
+          const float4 v = f[k];
+          if constexpr (F8)
+            *reinterpret_cast<uint32_t*>(dstc + sw128(r, 4 * hpart + (u >> 2)) + 4 * (u & 3)) =
+                pack_e4m3x4(v.x, v.y, v.z, v.w);
+          else
+            *reinterpret_cast<uint2*>(dstc + sw128(r, u >> 1) + 8 * (u & 1)) =
+                make_uint2(pack_bf16(v.x, v.y), pack_bf16(v.z, v.w));
         }
       }
       if (hpart == EL::SUBS - 1) {
@@ -372,14 +396,77 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
       }
       return true;
     };
-    float4 b0[2 * RPT], b1[2 * RPT];
-    fetch(0, b0);
-    for (int64_t q = 0; q < total; q += 2) {
-      fetch(q + 1, b1);
-      if (!store(q, b0)) break;
-      if (q + 1 >= total) break;
-      fetch(q + 2, b0);
-      if (!store(q + 1, b1)) break;
+    float4 b0[NF], b1[NF];
+    if constexpr (GATHER) {
+      constexpr int KE = (SE * SUB) / EL::KCH;  // chunks of FP32 stream columns
+      constexpr int KH = H / EL::KCH;           // chunks per gathered node row
+      // node indices of this thread's copy rows, loaded one tile ahead of use
+      int gs[NG], gd[NG], ns[NG], nd[NG];
+      auto load_idx = [&](int64_t t, int (&xs)[NG], int (&xd)[NG]) {
+        const int64_t r0 = (blockIdx.x + t * gridDim.x) * TM;
+#pragma unroll
+        for (int k = 0; k < NG; ++k) {
+          const int fi = pt + PROD_THREADS * k;
+          const int64_t gr = r0 + (fi >> 3);
+          const bool ok = t < my_tiles && fi < TM * 8 && gr < n_rows;
+          xs[k] = ok ? min(max(a.src[gr], 0), max(nn - 1, 0)) : 0;
+          xd[k] = ok ? min(max(a.dst[gr], 0), max(nn - 1, 0)) : 0;
+        }
+      };
+      load_idx(0, gs, gd);
+      if constexpr (SE > 0) {
+        fetch(0, 0, b0);
+        fetch(0, 1, b1);
+      }
+      for (int64_t t = 0; t < my_tiles; ++t) {
+        load_idx(t + 1, ns, nd);
+        if constexpr (SE > 0) {
+          if (!store(t, 0, b0)) break;
+          if (!store(t, 1, b1)) break;
+          fetch(t + 1, 0, b0);  // in flight while this tile's gathers are issued
+          fetch(t + 1, 1, b1);
+        }
+        bool ok = true;
+        for (int c = KE; c < C::KC1; ++c) {
+          const int64_t j = t * C::KC1 + c;
+          const int slot = (int)(j % NSTAGE);
+          if (!slot_free(j)) {
+            ok = false;
+            break;
+          }
+          const int hc = c - KE;
+          const int rowbytes = F8 ? H : 2 * H;
+          const int cbase = (hc % KH) * 128;  // byte offset of the chunk in the node row
+#pragma unroll
+          for (int k = 0; k < NG; ++k) {
+            const int fi = pt + PROD_THREADS * k;
+            if (fi < TM * 8)
+              cp_async16(sA + slot * CHUNK + sw128(fi >> 3, fi & 7),
+                         a.h_lp + (int64_t)(hc < KH ? gs[k] : gd[k]) * rowbytes + cbase + 16 * (fi & 7));
+          }
+          cp_async_arrive(&bars[B_FULL + slot]);
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&bars[B_FULL + slot]);
+        }
+        if (!ok) break;
+#pragma unroll
+        for (int k = 0; k < NG; ++k) {
+          gs[k] = ns[k];
+          gd[k] = nd[k];
+        }
+      }
+    } else {
+      // every chunk from the FP32 streams: a flattened stream of steps with the
+      // next step's loads in flight while one is stored
+      const int64_t total = my_tiles * C::KS;
+      fetch(0, 0, b0);
+      for (int64_t q = 0; q < total; q += 2) {
+        fetch((q + 1) / C::KS, (int)((q + 1) % C::KS), b1);
+        if (!store(q / C::KS, (int)(q % C::KS), b0)) break;
+        if (q + 1 >= total) break;
+        fetch((q + 2) / C::KS, (int)((q + 2) % C::KS), b0);
+        if (!store((q + 1) / C::KS, (int)((q + 1) % C::KS), b1)) break;
+      }
     }
   } else if (warp == MMA_WARP) {
     // =========================== MMA issuer ================================
@@ -428,6 +515,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
             const int slot = (int)(gchunk % NSTAGE);
             if (d1_free && mbar_try_wait(&bars[B_FULL + slot], (gchunk / NSTAGE) & 1)) {
               tc_fence_after();
+              fence_proxy_async();  // ring data written by asynchronous copies
               const uint32_t a0 = smem_u32(sA + slot * CHUNK), w0 = smem_u32(sW1 + c1 * CHUNK);
 #pragma unroll
               for (int k = 0; k < KSTEPS; ++k)
@@ -469,33 +557,30 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
     const uint32_t t1 = tmem + 128 * grp + lane_off;        // D1, then the activations
     const uint32_t t2 = tmem + 256 + 128 * grp + lane_off;  // D2
     float* stg = reinterpret_cast<float*>(smem + C::OFF_STG + 4096 * warp);  // 32 rows x 32 FP32
-    // LayerNorm statistics of t = sc * acc + b over the row's 128 columns (the
-    // mean, then the centred second moment), from 32-column chunks read from TMEM.
-    auto layer_stats = [&](uint32_t tb, float (&t)[32], const float* b, float sc, float& mean,
+    // LayerNorm statistics of t = sc * acc + b over the row's 128 columns, in one
+    // pass over two 64-column chunks read from TMEM: sums of d = t - t_0 and of
+    // d^2 (shifted by the row's first value, so the variance does not cancel).
+    auto layer_stats = [&](uint32_t tb, float (&t)[64], const float* b, float sc, float& mean,
                            float& rstd) {
-      float s = 0.f;
+      float s = 0.f, q = 0.f, shift = 0.f;
 #pragma unroll 1
       for (int ch = 0; ch < NCH; ++ch) {
-        tmem_ld32_wait(tb + 32 * ch, t);
-        s += bias_sum<32>(t, b + 32 * ch, sc);
+        tmem_ld64_wait(tb + 64 * ch, t);
+        if (ch == 0) shift = fmaf(t[0], sc, b[0]);
+        shifted_sums<64>(t, b + 64 * ch, sc, shift, s, q);
       }
-      mean = s * (1.0f / H);
-      float q = 0.f;
-#pragma unroll 1
-      for (int ch = 0; ch < NCH; ++ch) {
-        tmem_ld32_wait(tb + 32 * ch, t);
-        bias_sum<32>(t, b + 32 * ch, sc);
-        q += centre_sq<32>(t, mean);
-      }
-      rstd = 1.0f / sqrtf(q * (1.0f / H) + kLnEps);
+      const float ms = s * (1.0f / H);
+      mean = shift + ms;
+      rstd = 1.0f / sqrtf(fmaxf(q * (1.0f / H) - ms * ms, 0.f) + kLnEps);
     };
-    // Chunk ch of the row, normalised (ReLU left to the caller).
-    auto norm_chunk = [&](uint32_t tb, float (&t)[32], int ch, const float* p3, float sc,
+    // Chunk ch (64 columns) of the row, normalised (ReLU left to the caller).
+    auto norm_chunk = [&](uint32_t tb, float (&t)[64], int ch, const float* p3, float sc,
                           float mean, float rstd) {
-      tmem_ld32_wait(tb + 32 * ch, t);
-      bias_sum<32>(t, p3 + 32 * ch, sc);
-      centre_sq<32>(t, mean);
-      affine<32>(t, p3 + H + 32 * ch, p3 + 2 * H + 32 * ch, rstd);
+      tmem_ld64_wait(tb + 64 * ch, t);
+      float s_unused = 0.f, q_unused = 0.f;
+      shifted_sums<64>(t, p3 + 64 * ch, sc, 0.f, s_unused, q_unused);
+      centre<64>(t, mean);
+      affine<64>(t, p3 + H + 64 * ch, p3 + 2 * H + 64 * ch, rstd);
     };
     const float* resid = MODE == TC_NODE_UPD ? a.h : a.e;
     float* outp = MODE == TC_NODE_UPD ? a.h_out : a.e;
@@ -505,7 +590,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
       const int64_t gr = row0 + r;
       if (!wait_or_abort(&bars[B_D1FULL + grp], ph, a.err, abort)) break;
       tc_fence_after();
-      float t[32];
+      float t[64];
       float mean, rstd;
       layer_stats(t1, t, par, a.ws1, mean, rstd);
       if constexpr (MODE == TC_CLS) {
@@ -513,9 +598,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
 #pragma unroll 1
         for (int ch = 0; ch < NCH; ++ch) {
           norm_chunk(t1, t, ch, par, a.ws1, mean, rstd);
-          const float* wc = par + 6 * H + 32 * ch;
+          const float* wc = par + 6 * H + 64 * ch;
 #pragma unroll
-          for (int j = 0; j < 32; j += 4) {
+          for (int j = 0; j < 64; j += 4) {
             const float4 ww = lds4(wc + j);
             acc[0] = __ffma2_rn(f2(fmaxf(t[j], 0.f), fmaxf(t[j + 1], 0.f)), f2(ww.x, ww.y), acc[0]);
             acc[1] = __ffma2_rn(f2(fmaxf(t[j + 2], 0.f), fmaxf(t[j + 3], 0.f)), f2(ww.z, ww.w), acc[1]);
@@ -527,79 +612,89 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
         const float2 pp = __fadd2_rn(acc[0], acc[1]);
         if (gr < n_rows) a.logits[gr] = (pp.x + pp.y) + __ldg(a.bcls);
       } else {
-        // Activations of chunk ch (32 columns) go to TMEM columns [16 ch, 16 ch + 16)
-        // as BF16 pairs (or [8 ch, 8 ch + 8) as e4m3 quads): accumulator columns
-        // this warp has already read in this pass, as chunks run in order.
+        // Activations of chunk ch (64 columns) go to TMEM columns [32 ch, 32 ch + 32)
+        // as BF16 pairs (or [16 ch, 16 ch + 16) as e4m3 quads): accumulator
+        // columns this warp has already read, as chunks run in order.
 #pragma unroll 1
         for (int ch = 0; ch < NCH; ++ch) {
           norm_chunk(t1, t, ch, par, a.ws1, mean, rstd);
           if constexpr (F8) {
-            uint32_t v[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-              v[q] = pack_e4m3x4(fmaxf(t[4 * q], 0.f), fmaxf(t[4 * q + 1], 0.f),
-                                 fmaxf(t[4 * q + 2], 0.f), fmaxf(t[4 * q + 3], 0.f));
-            tmem_st8(t1 + 8 * ch, v);
-          } else {
             uint32_t v[16];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) v[q] = pack_bf16_relu(t[2 * q], t[2 * q + 1]);
+            for (int q = 0; q < 16; ++q)
+              v[q] = pack_e4m3x4(fmaxf(t[4 * q], 0.f), fmaxf(t[4 * q + 1], 0.f),
+                                 fmaxf(t[4 * q + 2], 0.f), fmaxf(t[4 * q + 3], 0.f));
             tmem_st16(t1 + 16 * ch, v);
+          } else {
+#pragma unroll
+            for (int h2 = 0; h2 < 2; ++h2) {
+              uint32_t v[16];
+#pragma unroll
+              for (int q = 0; q < 16; ++q) v[q] = pack_bf16_relu(t[32 * h2 + 2 * q], t[32 * h2 + 2 * q + 1]);
+              tmem_st16(t1 + 32 * ch + 16 * h2, v);
+            }
           }
         }
         tmem_wait_st();
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&bars[B_A2FULL + grp]);
-        // This lane's rows in the coalesced layout are crow + 4 it (it < 8); row
-        // crow + 4 it exists iff 4 it < nval.
-        const int u8 = lane & 7;
-        const int64_t crow = row0 + 32 * qr + (lane >> 3);
+        // Output: each 64-column chunk goes out as four 16-column quarters.  A
+        // quarter is staged row per thread (64 bytes a row, 16-byte units
+        // XOR-swizzled by (row / 2) % 4) in one of two 2 KB buffers, read back in
+        // the coalesced layout (4 lanes per 64-byte row segment, 8 rows per
+        // instruction), added to the residual and stored.  The two buffers
+        // alternate, so one warp barrier per quarter orders the staging; no
+        // barrier waits on the global stores.
+        const int u4 = lane & 3;
+        const int64_t crow = row0 + 32 * qr + (lane >> 2);  // rows crow + 8 it, it < 4
         const int nval = (int)(n_rows - crow < 32 ? (n_rows - crow > 0 ? n_rows - crow : 0) : 32);
-        const int64_t coff = crow * H + 4 * u8;
+        const int64_t coff = crow * H + 4 * u4;
         if (!wait_or_abort(&bars[B_D2FULL + grp], ph, a.err, abort)) break;
         tc_fence_after();
         layer_stats(t2, t, par + 3 * H, a.ws2, mean, rstd);
-        // Pass p: normalise 32 columns (re-read from TMEM) and stage them row per
-        // thread with 16-byte units XOR-swizzled by (row % 8); read them back in
-        // the coalesced layout of the stores (8 lanes per 128-byte row segment,
-        // 4 rows per instruction), add the residual (requested before the
-        // staging) and store.  No warp barrier follows the global stores.
 #pragma unroll 1
-        for (int p = 0; p < NCH; ++p) {
-          norm_chunk(t2, t, p, par + 3 * H, a.ws2, mean, rstd);
-          if (p == NCH - 1) {  // D2 fully read: the group's next second GEMM may overwrite it
+        for (int ch = 0; ch < NCH; ++ch) {
+          norm_chunk(t2, t, ch, par + 3 * H, a.ws2, mean, rstd);
+          if (ch == NCH - 1) {  // D2 fully read: the group's next second GEMM may overwrite it
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&bars[B_D2EMPTY + grp]);
           }
-          float4 res[8];
 #pragma unroll
-          for (int it = 0; it < 8; ++it) {
-            res[it] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (MODE != TC_EDGE_ENC && 4 * it < nval)
-              res[it] = *reinterpret_cast<const float4*>(resid + coff + 4 * it * H + 32 * p);
-          }
+          for (int hh = 0; hh < 4; ++hh) {
+            const int col = 64 * ch + 16 * hh;  // first column of the quarter
+            float* buf = stg + 512 * (hh & 1);  // 2 KB: 32 rows x 16 FP32
+            float4 res[4];
 #pragma unroll
-          for (int u = 0; u < 8; ++u)
-            *reinterpret_cast<float4*>(stg + 32 * lane + 4 * (u ^ (lane & 7))) =
-                make_float4(fmaxf(t[4 * u], 0.f), fmaxf(t[4 * u + 1], 0.f),
-                            fmaxf(t[4 * u + 2], 0.f), fmaxf(t[4 * u + 3], 0.f));
-          __syncwarp();
-          float4 v[8];
+            for (int it = 0; it < 4; ++it) {
+              res[it] = make_float4(0.f, 0.f, 0.f, 0.f);
+              if (MODE != TC_EDGE_ENC && 8 * it < nval)
+                res[it] = *reinterpret_cast<const float4*>(resid + coff + 8 * it * H + col);
+            }
 #pragma unroll
-          for (int it = 0; it < 8; ++it) {
-            const int lr = 4 * it + (lane >> 3);
-            v[it] = *reinterpret_cast<const float4*>(stg + 32 * lr + 4 * (u8 ^ (lr & 7)));
-          }
-          __syncwarp();  // the stage is free for the next pass
+            for (int u = 0; u < 4; ++u)
+              *reinterpret_cast<float4*>(buf + 16 * lane + 4 * (u ^ ((lane >> 1) & 3))) =
+                  make_float4(fmaxf(t[16 * hh + 4 * u], 0.f), fmaxf(t[16 * hh + 4 * u + 1], 0.f),
+                              fmaxf(t[16 * hh + 4 * u + 2], 0.f), fmaxf(t[16 * hh + 4 * u + 3], 0.f));
+            __syncwarp();
 #pragma unroll
-          for (int it = 0; it < 8; ++it) {
-            if (4 * it < nval) {
-              const float2 o0 = __fadd2_rn(f2(v[it].x, v[it].y), f2(res[it].x, res[it].y));
-              const float2 o1 = __fadd2_rn(f2(v[it].z, v[it].w), f2(res[it].z, res[it].w));
-              *reinterpret_cast<float4*>(outp + coff + 4 * it * H + 32 * p) =
-                  make_float4(o0.x, o0.y, o1.x, o1.y);
+            for (int it = 0; it < 4; ++it) {
+              const int lr = 8 * it + (lane >> 2);
+              const float4 v = *reinterpret_cast<const float4*>(buf + 16 * lr + 4 * (u4 ^ ((lr >> 1) & 3)));
+              if (8 * it < nval) {
+                const float2 o0 = __fadd2_rn(f2(v.x, v.y), f2(res[it].x, res[it].y));
+                const float2 o1 = __fadd2_rn(f2(v.z, v.w), f2(res[it].z, res[it].w));
+                const int64_t el = coff + 8 * it * H + col;  // element index in the stream
+                *reinterpret_cast<float4*>(outp + el) = make_float4(o0.x, o0.y, o1.x, o1.y);
+                if constexpr (MODE == TC_NODE_UPD) {  // the copy the edge blocks gather
+                  if constexpr (F8)
+                    *reinterpret_cast<uint32_t*>(a.h_lp + el) = pack_e4m3x4(o0.x, o0.y, o1.x, o1.y);
+                  else
+                    *reinterpret_cast<uint2*>(a.h_lp + 2 * el) =
+                        make_uint2(pack_bf16(o0.x, o0.y), pack_bf16(o1.x, o1.y));
+                }
+              }
             }
           }
         }
@@ -633,6 +728,19 @@ cudaError_t launch_tc(etx_ctx* ctx, const char* name, const TcArgs& a, int64_t m
   return cudaGetLastError();
 }
 
+// h (FP32, [n][128]) rounded to BF16 rows of 256 bytes or e4m3 rows of 128 bytes.
+template <bool F8>
+__global__ void k_h_lowp(const float* __restrict__ h, uint8_t* __restrict__ out, int64_t n4) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const float4 v = reinterpret_cast<const float4*>(h)[q];
+    if constexpr (F8)
+      reinterpret_cast<uint32_t*>(out)[q] = pack_e4m3x4(v.x, v.y, v.z, v.w);
+    else
+      reinterpret_cast<uint2*>(out)[q] = make_uint2(pack_bf16(v.x, v.y), pack_bf16(v.z, v.w));
+  }
+}
+
 TcArgs base_args(etx_ctx* ctx, int64_t N, const int32_t* src, const int32_t* dst,
                  const int32_t* n_edges_dev, float* logits) {
   TcArgs a{};
@@ -645,6 +753,7 @@ TcArgs base_args(etx_ctx* ctx, int64_t N, const int32_t* src, const int32_t* dst
   a.e = ctx->e;
   a.h_out = ctx->h;
   a.logits = logits;
+  a.h_lp = ctx->h_lp;
   a.err = ctx->d_err;
   return a;
 }
@@ -692,6 +801,18 @@ cudaError_t launch_edge_update_tc(etx_ctx* ctx, int k, int64_t N, const int32_t*
   set_block(a, ctx->w.edge[k], ctx->w.edge_tc[k], f8);
   return launch_any<TC_EDGE_UPD>(ctx, f8, "gnn_edge_update_bf16", "gnn_edge_update_fp8", a,
                                  ctx->cfg.max_edges, s);
+}
+
+cudaError_t launch_h_lowp(etx_ctx* ctx, int64_t N, bool f8, cudaStream_t s) {
+  const int64_t n4 = N * H / 4;
+  if (n4 == 0) return cudaSuccess;
+  const int grid = grid_for(ctx, f8 ? (const void*)k_h_lowp<true> : (const void*)k_h_lowp<false>,
+                            256, 0, (n4 + 255) / 256);
+  if (f8)
+    launch(ctx, "gnn_h_lowp", k_h_lowp<true>, grid, 256, 0, s, (const float*)ctx->h, ctx->h_lp, n4);
+  else
+    launch(ctx, "gnn_h_lowp", k_h_lowp<false>, grid, 256, 0, s, (const float*)ctx->h, ctx->h_lp, n4);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_classifier_tc(etx_ctx* ctx, int64_t N, const int32_t* n_edges_dev, float* logits,
