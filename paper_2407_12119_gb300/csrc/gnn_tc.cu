@@ -46,7 +46,6 @@ constexpr int TM = 128;                  // rows per tile
 constexpr int CHUNK = TM * 128;          // 16 KB operand chunk: 128 rows x 128 bytes
 constexpr int SUB = 64;                  // K columns a producer fetches per step (256 B FP32)
 constexpr int KSTEPS = 4;                // MMAs per chunk (32 bytes of K each)
-constexpr int NSTAGE = 3;                // A-operand ring slots
 // 16 warps: an SM sub-partition then holds four, and each thread 128 registers
 constexpr int EPI_WARPS = 8, PROD_WARPS = 7;  // two epilogue groups of four warps
 constexpr int MMA_WARP = EPI_WARPS + PROD_WARPS;
@@ -57,10 +56,6 @@ constexpr uint32_t TMEM_COLS = 512;
 
 enum TcMode { TC_EDGE_ENC = 0, TC_NODE_UPD = 1, TC_EDGE_UPD = 2, TC_CLS = 3 };
 
-// barrier indices (the per-group ones come in pairs, index + group)
-enum { B_W = 0, B_FULL = 1, B_EMPTY = B_FULL + NSTAGE, B_D1FULL = B_EMPTY + NSTAGE,
-       B_D1EMPTY = B_D1FULL + 2, B_A2FULL = B_D1EMPTY + 2, B_D2FULL = B_A2FULL + 2,
-       B_D2EMPTY = B_D2FULL + 2, N_BARS = B_D2EMPTY + 2 };
 
 // Operand type: BF16 (2 bytes, 64 K columns per 128-byte row) or FP8 e4m3
 // (1 byte, 128 K columns per row).  Either way one MMA consumes 32 bytes of K,
@@ -72,6 +67,8 @@ struct Elt {
   static constexpr uint32_t IDESC = F8 ? idesc_e4m3_f32<TM, H>() : idesc_bf16_f32<TM, H>();
 };
 
+constexpr int SMEM_MAX = 232448;         // opt-in shared memory per CTA
+
 template <int MODE, bool F8>
 struct Cfg {
   static constexpr int KIN = MODE == TC_EDGE_ENC ? 2 * H : (MODE == TC_CLS ? H : 3 * H);
@@ -82,12 +79,25 @@ struct Cfg {
   static constexpr int OFF_W1 = 0;
   static constexpr int OFF_W2 = OFF_W1 + KC1 * CHUNK;
   static constexpr int OFF_A = OFF_W2 + (G2 ? C2 * CHUNK : 0);
-  static constexpr int OFF_STG = OFF_A + NSTAGE * CHUNK;            // 8 per-warp 4 KB output stages
+  static constexpr int FIXED = OFF_A + (G2 ? EPI_WARPS * 4096 : 0) + 7 * H * 4 + 8 * 64 + 16 + 1024;
+  // A-operand ring slots.  A deeper ring lets the first GEMM of later tiles
+  // queue in the (in-order) tensor pipe ahead of the second GEMM the epilogue
+  // waits for; measured best: 3 slots of BF16 chunks, 2 of e4m3 chunks.
+  static constexpr int NST_WANT = F8 ? 2 : 3;
+  static constexpr int NST = (SMEM_MAX - FIXED) / CHUNK > NST_WANT ? NST_WANT : (SMEM_MAX - FIXED) / CHUNK;
+  static_assert(NST >= 2, "shared memory too small for the ring");
+  // barrier indices (the per-group ones come in pairs, index + group)
+  static constexpr int B_W = 0, B_FULL = 1, B_EMPTY = B_FULL + NST, B_D1FULL = B_EMPTY + NST,
+                       B_D1EMPTY = B_D1FULL + 2, B_A2FULL = B_D1EMPTY + 2, B_D2FULL = B_A2FULL + 2,
+                       B_D2EMPTY = B_D2FULL + 2, N_BARS = B_D2EMPTY + 2;
+  static_assert(N_BARS <= 64, "barrier area");
+  static constexpr int OFF_STG = OFF_A + NST * CHUNK;               // 8 per-warp 4 KB output stages
   static constexpr int OFF_PAR = OFF_STG + (G2 ? EPI_WARPS * 4096 : 0);  // 7 x 128 floats
   static constexpr int OFF_BAR = OFF_PAR + 7 * H * 4;
-  static constexpr int OFF_MISC = OFF_BAR + 8 * N_BARS;              // tmem addr, abort flag
+  static constexpr int OFF_MISC = OFF_BAR + 8 * 64;                  // tmem addr, abort flag
   static constexpr int BYTES = OFF_MISC + 16;
   static constexpr int SMEM = BYTES + 1024;  // slack for 1024-byte alignment
+  static_assert(SMEM <= SMEM_MAX, "shared memory");
 };
 
 struct TcArgs {
@@ -275,6 +285,10 @@ template <int MODE, bool F8>
 __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
   using C = Cfg<MODE, F8>;
   using EL = Elt<F8>;
+  constexpr int NSTAGE = C::NST;
+  constexpr int B_W = C::B_W, B_FULL = C::B_FULL, B_EMPTY = C::B_EMPTY, B_D1FULL = C::B_D1FULL,
+                B_D1EMPTY = C::B_D1EMPTY, B_A2FULL = C::B_A2FULL, B_D2FULL = C::B_D2FULL,
+                B_D2EMPTY = C::B_D2EMPTY;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
