@@ -3,8 +3,10 @@
 labels for a 500-event batch of synthetic VELO-like events.
 
 One step = embedding -> graph -> interaction network -> components over the
-whole batch, inputs resident in HBM (``value``); ``e2e`` is the same step
-through the public API from pinned host buffers, copies included.
+whole batch, inputs resident in HBM, the step's launches captured once in a
+CUDA graph and replayed (``value``); the per-kernel profile comes from the
+same step launched eagerly; ``e2e`` is the step through the public API from
+pinned host buffers, copies included.
 
     python bench.py [--gpus N --steps K --warmup W --dtype f32 --impl ours|reference]
 
@@ -32,8 +34,8 @@ METRIC = "events/s (hits->tracks, 500-event batch)"
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
 # dram__bytes_read.sum + dram__bytes_write.sum per edge of one launch, from ncu
 # captures on the 50-event case (profiles/edge_update_bf16_batch500.md); to be
-# re-taken whenever the kernel changes
-MEASURED_DRAM_BYTES_PER_EDGE = {"gnn_edge_update_bf16": (633.189376e6 + 520.522496e6) / 1113945}
+# re-taken whenever the kernel changes (absent: traffic reported as null)
+MEASURED_DRAM_BYTES_PER_EDGE = {"gnn_edge_update_bf16": (604.385024e6 + 514.457856e6) / 1113945}
 
 
 def parse():
@@ -317,9 +319,28 @@ def run_ours(args):
     tf.ctx.sync()
     E = int(tf.eoff[B].item())
 
-    # ---- timed region: device-resident inputs ------------------------------
+    # ---- eager launches with per-kernel CUDA events (the kernel profile) ----
     tf.ctx.profile(True)
     n_launch0 = tf.ctx.launch_count
+    barrier(world)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(args.steps):
+        step()
+    p1.record(stream)
+    torch.cuda.synchronize()
+    launches_per_step = (tf.ctx.launch_count - n_launch0) / args.steps
+    prof = tf.ctx.profile_read()
+    tf.ctx.profile(False)
+    tf.ctx.sync()
+    eager_ms_step = max_over_ranks(p0.elapsed_time(p1), world, dev) / args.steps
+
+    # ---- timed region: the step captured in one CUDA graph, replayed ---------
+    tf.capture(dx, dy, dz, dp, do, N, B)
+    for _ in range(max(args.warmup, 3)):
+        tf.replay()
+    tf.ctx.sync()
     barrier(world)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -327,16 +348,14 @@ def run_ours(args):
     with ClockSampler(gpu_query_id(local)) as clk:
         ev0.record(stream)
         for k in range(args.steps):
-            step()
+            tf.replay()
             marks[k].record(stream)
         ev1.record(stream)
         torch.cuda.synchronize()
     per_step = [ev0.elapsed_time(marks[0])] + [marks[k - 1].elapsed_time(marks[k])
                                                for k in range(1, args.steps)]
     barrier(world)
-    launches = tf.ctx.launch_count - n_launch0
-    prof = tf.ctx.profile_read()
-    tf.ctx.profile(False)
+    launches = launches_per_step * args.steps  # kernel nodes of the replayed graphs
     tf.ctx.sync()
     ms_total = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     ms_step = ms_total / args.steps
@@ -370,7 +389,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             logits, lab = tf.logits[:E].clone(), labels.clone()
             if dt == args.dtype:
-                dt_ms = ms_step
+                dt_ms = eager_ms_step
             else:
                 step()
                 d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -448,7 +467,9 @@ def run_ours(args):
                       "global_batch": B * world, "hits": N, "edges": E,
                       "edges_per_s": world * E * args.steps / (ms_total / 1e3),
                       "l2": "working set (edge features %.1f GB) larger than L2" % (E * m.hidden * 4 / 1e9),
-                      "parallelism": f"replicas x{world}"},
+                      "parallelism": f"replicas x{world}",
+                      "execution": f"one CUDA graph per step ({int(launches_per_step)} kernel "
+                                   f"launches); eager launches {eager_ms_step:.2f} ms per step"},
            "roofline": roof,
            "cpu_baseline": cpu,
            "e2e": {"value": world * B * args.steps / (e2e_ms / 1e3), "unit": "events/s",

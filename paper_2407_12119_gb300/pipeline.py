@@ -3,8 +3,9 @@ out (paper Sec. 5 without the triplet stage, as in its Sec. 7 port).
 
 ``TrackFinder.run_device`` works on device-resident tensors; ``find_tracks``
 takes host arrays, copies them to the GPU, runs the four library calls and
-copies the labels back.  Both only marshal arguments: every step runs in
-libetx.
+copies the labels back; ``capture`` records one ``run_device`` call (every
+launch of the four steps) into a CUDA graph that ``replay`` re-issues with a
+single launch.  All of them only marshal arguments: every step runs in libetx.
 """
 from __future__ import annotations
 
@@ -54,6 +55,32 @@ class TrackFinder:
                                        labels=self.labels[:n_hits],
                                        n_tracks=self.n_tracks[:max(n_events, 1)])
         return labels, nt
+
+    def capture(self, x, y, z, plane, hit_offsets, n_hits: int, n_events: int,
+                min_hits: int = 3):
+        """Record ``run_device`` on these device tensors into one CUDA graph.
+
+        The graph is specialised to the tensors' addresses and to ``n_hits`` and
+        ``n_events``: to process another batch of the same sizes, copy its hits
+        into the same tensors and call ``replay``.  One eager call runs first, so
+        one-time set-up (kernel attributes) happens outside the capture.
+        Returns the (labels, n_tracks) views that each replay rewrites.
+        """
+        self.run_device(x, y, z, plane, hit_offsets, n_hits, n_events, min_hits)
+        torch.cuda.synchronize(self.dev)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.graph_out = self.run_device(x, y, z, plane, hit_offsets, n_hits, n_events,
+                                             min_hits)
+        torch.cuda.synchronize(self.dev)
+        return self.graph_out
+
+    def replay(self):
+        """Re-issue the captured step on the current stream; returns its outputs."""
+        if getattr(self, "graph", None) is None:
+            raise RuntimeError("TrackFinder.replay: nothing captured (call capture first)")
+        self.graph.replay()
+        return self.graph_out
 
     def find_tracks(self, x, y, z, plane, hit_offsets, labels_out=None, n_tracks_out=None,
                     min_hits: int = 3):
