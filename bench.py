@@ -318,6 +318,9 @@ def run_ours(args):
         step()
     tf.ctx.sync()
     E = int(tf.eoff[B].item())
+    # launch configurations timed on this batch by the library's autotuner
+    tuned = {k: v for k, v in tf.autotune(dx, dy, dz, dp, do, N, B).items()
+             if k == "knn_split" or k.endswith("/" + args.dtype)}
 
     # ---- eager launches with per-kernel CUDA events (the kernel profile) ----
     tf.ctx.profile(True)
@@ -469,7 +472,8 @@ def run_ours(args):
                       "l2": "working set (edge features %.1f GB) larger than L2" % (E * m.hidden * 4 / 1e9),
                       "parallelism": f"replicas x{world}",
                       "execution": f"one CUDA graph per step ({int(launches_per_step)} kernel "
-                                   f"launches); eager launches {eager_ms_step:.2f} ms per step"},
+                                   f"launches); eager launches {eager_ms_step:.2f} ms per step",
+                      "tuned": tuned},
            "roofline": roof,
            "cpu_baseline": cpu,
            "e2e": {"value": world * B * args.steps / (e2e_ms / 1e3), "unit": "events/s",

@@ -234,6 +234,36 @@ etx_status etx_edges_to_tracks_noalloc(const int32_t* src, const int32_t* dst,
                                        int32_t* labels, int32_t* n_tracks, void* stream);
 
 /*
+ * Autotuner (no counterpart in the paper: it picks launch configurations, not
+ * results).  Runs the embedding, the graph and (for ETX_BF16 / ETX_FP8E4M3)
+ * the interaction network on the given batch, timing with CUDA events each
+ * candidate of
+ *   "knn_split"                 blocks that share the sources of one
+ *                               (event, plane) in the k-NN: 1, 2 or 4
+ *                               (per-event work partitioning);
+ *   "tc_stages/<block>/<dtype>" A-operand ring slots of the tensor-core MLP
+ *                               kernel, 2 or 3, for block edge_encoder,
+ *                               node_update, edge_update or classifier and
+ *                               dtype bf16 or fp8,
+ * and keeps the fastest in the context for all later calls.  Outputs do not
+ * depend on these choices.  On return emb, src, dst, edge_offsets (and logits
+ * for the tensor-core dtypes) hold the results of the chosen configuration,
+ * as the regular calls would write them; arguments, layouts and errors are
+ * those of etx_embed, etx_build_graph and etx_gnn_forward.  Synchronises the
+ * stream (the host waits) and clears any pending profile record.
+ * etx_tuned returns the current value of a knob by the names above, or -1;
+ * etx_set_tuned sets one (a value outside the candidates above, or an unknown
+ * knob, is ETX_ERR_ARG), e.g. to restore a configuration tuned earlier.
+ */
+etx_status etx_autotune(etx_ctx* ctx, const float* x, const float* y, const float* z,
+                        const int8_t* plane, const int32_t* hit_offsets, int32_t n_events,
+                        int64_t n_hits, float radius, int32_t k_max, etx_dtype dtype, float* emb,
+                        int32_t* src, int32_t* dst, int64_t edge_capacity, int32_t* edge_offsets,
+                        float* logits, void* stream);
+int32_t etx_tuned(const etx_ctx* ctx, const char* knob);
+etx_status etx_set_tuned(etx_ctx* ctx, const char* knob, int32_t value);
+
+/*
  * Instrumentation (no counterpart in the paper; used by the benchmark).
  *   etx_launch_count    number of kernels this context has launched so far.
  *   etx_profile_enable  when on, every kernel launch is bracketed by a CUDA

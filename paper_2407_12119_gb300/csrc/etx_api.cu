@@ -632,3 +632,139 @@ etx_status etx_edges_to_tracks(etx_ctx* ctx, const int32_t* src, const int32_t* 
 }
 
 }  // extern "C"
+
+// ---- autotuner ---------------------------------------------------------------
+
+namespace {
+
+const char* const kTcBlock[4] = {"edge_encoder", "node_update", "edge_update", "classifier"};
+
+// Milliseconds of the recorded launches whose name starts with `prefix`
+// (waits for them); clears the record.
+double prof_take(etx_ctx* ctx, const char* prefix) {
+  double ms = 0.0;
+  const size_t n = std::strlen(prefix);
+  for (size_t i = 0; i < ctx->prof_used; ++i) {
+    const ProfRec& r = ctx->prof[i];
+    float t = 0.f;
+    if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess)
+      return -1.0;
+    if (std::strncmp(r.name, prefix, n) == 0) ms += t;
+  }
+  ctx->prof_used = 0;
+  return ms;
+}
+
+}  // namespace
+
+extern "C" {
+
+etx_status etx_autotune(etx_ctx* ctx, const float* x, const float* y, const float* z,
+                        const int8_t* plane, const int32_t* hit_offsets, int32_t n_events,
+                        int64_t n_hits, float radius, int32_t k_max, etx_dtype dtype, float* emb,
+                        int32_t* src, int32_t* dst, int64_t edge_capacity, int32_t* edge_offsets,
+                        float* logits, void* stream) {
+  if (!ctx) return ETX_ERR_ARG;
+  etx_status st = etx_embed(ctx, x, y, z, n_hits, emb, stream);
+  if (st != ETX_OK) return st;
+  const bool prof_was = ctx->prof_on;
+  ctx->prof_on = true;
+  ctx->prof_used = 0;
+  constexpr int kReps = 2;
+  // k-NN: blocks per (event, plane)
+  const int splits[3] = {1, 2, 4};
+  double best = 1e300;
+  int best_split = ctx->knn_split;
+  for (int split : splits) {
+    ctx->knn_split = split;
+    double ms = 0.0;
+    for (int r = 0; r <= kReps && st == ETX_OK; ++r) {
+      st = etx_build_graph(ctx, emb, plane, hit_offsets, n_events, n_hits, radius, k_max, src, dst,
+                           edge_capacity, edge_offsets, stream);
+      const double t = prof_take(ctx, "graph_knn");
+      if (t < 0) st = fail(ctx, ETX_ERR_CUDA, "autotune timing");
+      if (r > 0) ms += t;  // the first run warms up
+    }
+    if (st != ETX_OK) break;
+    if (ms < best) {
+      best = ms;
+      best_split = split;
+    }
+  }
+  ctx->knn_split = best_split;
+  if (st == ETX_OK)
+    st = etx_build_graph(ctx, emb, plane, hit_offsets, n_events, n_hits, radius, k_max, src, dst,
+                         edge_capacity, edge_offsets, stream);
+  // tensor-core MLP kernels: ring slots per block
+  if (st == ETX_OK && dtype != ETX_F32) {
+    const int f8 = dtype == ETX_FP8E4M3 ? 1 : 0;
+    const char* suffix = f8 ? "_fp8" : "_bf16";
+    double ms[2][4] = {};
+    for (int v = 0; v < 2 && st == ETX_OK; ++v) {
+      for (int m = 0; m < 4; ++m) ctx->tc_stages[m][f8] = 2 + v;
+      for (int r = 0; r <= kReps && st == ETX_OK; ++r) {
+        st = etx_gnn_forward(ctx, x, y, z, n_hits, src, dst, edge_offsets, n_events, dtype, logits,
+                             stream);
+        for (int m = 0; m < 4 && st == ETX_OK; ++m) {
+          const std::string name = std::string("gnn_") + kTcBlock[m] + suffix;
+          double t = 0.0;
+          for (size_t i = 0; i < ctx->prof_used; ++i) {
+            const ProfRec& rec = ctx->prof[i];
+            float e = 0.f;
+            if (cudaEventSynchronize(rec.b) != cudaSuccess ||
+                cudaEventElapsedTime(&e, rec.a, rec.b) != cudaSuccess) {
+              st = fail(ctx, ETX_ERR_CUDA, "autotune timing");
+              break;
+            }
+            if (name == rec.name) t += e;
+          }
+          if (r > 0) ms[v][m] += t;
+        }
+        ctx->prof_used = 0;
+      }
+    }
+    for (int m = 0; m < 4; ++m) ctx->tc_stages[m][f8] = ms[0][m] < ms[1][m] ? 2 : 3;
+    if (st == ETX_OK)
+      st = etx_gnn_forward(ctx, x, y, z, n_hits, src, dst, edge_offsets, n_events, dtype, logits,
+                           stream);
+  }
+  ctx->prof_on = prof_was;
+  ctx->prof_used = 0;
+  if (st == ETX_OK) {
+    const cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) st = cuda_fail(ctx, e, "autotune");
+  }
+  return st;
+}
+
+int32_t etx_tuned(const etx_ctx* ctx, const char* knob) {
+  if (!ctx || !knob) return -1;
+  const std::string k(knob);
+  if (k == "knn_split") return ctx->knn_split;
+  for (int m = 0; m < 4; ++m)
+    for (int f8 = 0; f8 < 2; ++f8)
+      if (k == std::string("tc_stages/") + kTcBlock[m] + (f8 ? "/fp8" : "/bf16"))
+        return ctx->tc_stages[m][f8];
+  return -1;
+}
+
+etx_status etx_set_tuned(etx_ctx* ctx, const char* knob, int32_t value) {
+  if (!ctx) return ETX_ERR_ARG;
+  if (!knob) return fail(ctx, ETX_ERR_ARG, "knob name is NULL");
+  const std::string k(knob);
+  if (k == "knn_split") {
+    if (value != 1 && value != 2 && value != 4) return fail(ctx, ETX_ERR_ARG, "knn_split must be 1, 2 or 4");
+    ctx->knn_split = value;
+    return ETX_OK;
+  }
+  for (int m = 0; m < 4; ++m)
+    for (int f8 = 0; f8 < 2; ++f8)
+      if (k == std::string("tc_stages/") + kTcBlock[m] + (f8 ? "/fp8" : "/bf16")) {
+        if (value != 2 && value != 3) return fail(ctx, ETX_ERR_ARG, "tc_stages must be 2 or 3");
+        ctx->tc_stages[m][f8] = value;
+        return ETX_OK;
+      }
+  return fail(ctx, ETX_ERR_ARG, "unknown knob");
+}
+
+}  // extern "C"

@@ -131,6 +131,11 @@ struct etx_ctx {
   int64_t fwd_n_hits = 0;
   int64_t gnn_blob_offset = 0;   // first interaction-network value in the weight blob
 
+  // launch configurations picked by etx_autotune (defaults: measured on the
+  // 500-event workload)
+  int knn_split = 1;                         // blocks per (event, plane) in the k-NN
+  int tc_stages[4][2] = {{3, 2}, {3, 2}, {3, 2}, {3, 2}};  // ring slots [mode][e4m3]
+
   // launch accounting and optional per-launch CUDA-event timing
   int64_t launches = 0;
   bool prof_on = false;

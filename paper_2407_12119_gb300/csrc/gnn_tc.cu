@@ -69,7 +69,7 @@ struct Elt {
 
 constexpr int SMEM_MAX = 232448;         // opt-in shared memory per CTA
 
-template <int MODE, bool F8>
+template <int MODE, bool F8, int NS>
 struct Cfg {
   static constexpr int KIN = MODE == TC_EDGE_ENC ? 2 * H : (MODE == TC_CLS ? H : 3 * H);
   static constexpr int KC1 = KIN / Elt<F8>::KCH;     // chunks of the first GEMM
@@ -80,11 +80,10 @@ struct Cfg {
   static constexpr int OFF_W2 = OFF_W1 + KC1 * CHUNK;
   static constexpr int OFF_A = OFF_W2 + (G2 ? C2 * CHUNK : 0);
   static constexpr int FIXED = OFF_A + (G2 ? EPI_WARPS * 4096 : 0) + 7 * H * 4 + 8 * 64 + 16 + 1024;
-  // A-operand ring slots.  A deeper ring lets the first GEMM of later tiles
-  // queue in the (in-order) tensor pipe ahead of the second GEMM the epilogue
-  // waits for; measured best: 3 slots of BF16 chunks, 2 of e4m3 chunks.
-  static constexpr int NST_WANT = F8 ? 2 : 3;
-  static constexpr int NST = (SMEM_MAX - FIXED) / CHUNK > NST_WANT ? NST_WANT : (SMEM_MAX - FIXED) / CHUNK;
+  // NS A-operand ring slots (as far as shared memory holds them).  A deeper ring
+  // lets the first GEMM of later tiles queue in the (in-order) tensor pipe
+  // ahead of the second GEMM the epilogue waits for; the autotuner picks NS.
+  static constexpr int NST = (SMEM_MAX - FIXED) / CHUNK > NS ? NS : (SMEM_MAX - FIXED) / CHUNK;
   static_assert(NST >= 2, "shared memory too small for the ring");
   // barrier indices (the per-group ones come in pairs, index + group)
   static constexpr int B_W = 0, B_FULL = 1, B_EMPTY = B_FULL + NST, B_D1FULL = B_EMPTY + NST,
@@ -281,9 +280,9 @@ __device__ __forceinline__ void affine(float* __restrict__ d, const float* __res
   }
 }
 
-template <int MODE, bool F8>
+template <int MODE, bool F8, int NS>
 __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
-  using C = Cfg<MODE, F8>;
+  using C = Cfg<MODE, F8, NS>;
   using EL = Elt<F8>;
   constexpr int NSTAGE = C::NST;
   constexpr int B_W = C::B_W, B_FULL = C::B_FULL, B_EMPTY = C::B_EMPTY, B_D1FULL = C::B_D1FULL,
@@ -724,22 +723,30 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
   }
 }
 
-template <int MODE, bool F8>
-cudaError_t launch_tc(etx_ctx* ctx, const char* name, const TcArgs& a, int64_t max_rows,
-                      cudaStream_t s) {
-  using C = Cfg<MODE, F8>;
+template <int MODE, bool F8, int NS>
+cudaError_t launch_tc_ns(etx_ctx* ctx, const char* name, const TcArgs& a, int64_t max_rows,
+                         cudaStream_t s) {
+  using C = Cfg<MODE, F8, NS>;
   static bool attr_set[8] = {false};
   if (!attr_set[ctx->device & 7]) {
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_tc<MODE, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         C::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_tc<MODE, F8, NS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     attr_set[ctx->device & 7] = true;
   }
   const int64_t tiles = (max_rows + TM - 1) / TM;
   if (tiles == 0) return cudaSuccess;
   const int grid = (int)(tiles < ctx->n_sms ? tiles : ctx->n_sms);
-  launch(ctx, name, k_mlp_tc<MODE, F8>, grid, THREADS, C::SMEM, s, a);
+  launch(ctx, name, k_mlp_tc<MODE, F8, NS>, grid, THREADS, C::SMEM, s, a);
   return cudaGetLastError();
+}
+
+// ring depth from the context's tuning (2 or 3 slots)
+template <int MODE, bool F8>
+cudaError_t launch_tc(etx_ctx* ctx, const char* name, const TcArgs& a, int64_t max_rows,
+                      cudaStream_t s) {
+  return ctx->tc_stages[MODE][F8 ? 1 : 0] == 2 ? launch_tc_ns<MODE, F8, 2>(ctx, name, a, max_rows, s)
+                                                : launch_tc_ns<MODE, F8, 3>(ctx, name, a, max_rows, s);
 }
 
 // h (FP32, [n][128]) rounded to BF16 rows of 256 bytes or e4m3 rows of 128 bytes.

@@ -205,11 +205,15 @@ template <bool EMIT, int DT>
 __global__ void __launch_bounds__(kKnnThreads)
 k_knn(const float* __restrict__ emb, int D, const int32_t* __restrict__ plane_off, int n_planes,
       float radius, int k_max, int32_t* __restrict__ cnt_or_off, int64_t n_hits,
-      int32_t* __restrict__ src, int32_t* __restrict__ dst, int64_t capacity, int* err) {
+      int32_t* __restrict__ src, int32_t* __restrict__ dst, int64_t capacity, int* err,
+      int split) {
   extern __shared__ float cand_s[];  // [D][n_stage], then 256 ints per warp (select histograms)
   int* hist_s = reinterpret_cast<int*>(cand_s + kStageFloats);
-  const int b = blockIdx.x / (n_planes - 1);
-  const int p = blockIdx.x % (n_planes - 1);
+  // `split` blocks share the sources of one (event, plane): block `part` takes
+  // every split-th group of warps' sources (each stages the candidates itself)
+  const int bp = blockIdx.x / split, part = blockIdx.x % split;
+  const int b = bp / (n_planes - 1);
+  const int p = bp % (n_planes - 1);
   const int32_t* po = plane_off + (int64_t)b * (n_planes + 1);
   const int s_lo = po[p], s_hi = po[p + 1];
   const int c_lo = po[p + 1], c_hi = po[min(p + 3, n_planes)];
@@ -223,9 +227,12 @@ k_knn(const float* __restrict__ emb, int D, const int32_t* __restrict__ plane_of
   const unsigned lt_mask = (1u << lane) - 1u;
   if (n_cand <= 0) {
     if (!EMIT)
-      for (int i = s_lo + threadIdx.x; i < s_hi; i += blockDim.x) cnt_or_off[i] = 0;
+      for (int i = s_lo + part * blockDim.x + threadIdx.x; i < s_hi; i += blockDim.x * split)
+        cnt_or_off[i] = 0;
     return;
   }
+  constexpr int WPB = kKnnThreads / 32;  // warps per block
+  if (s_lo + part * WPB >= s_hi) return;  // no source for this part
   // candidate storage: shared (SoA, stride n_cand) or global (AoS, stride 1)
   const bool staged = n_cand * D <= kStageFloats;
   if (staged) {
@@ -241,7 +248,7 @@ k_knn(const float* __restrict__ emb, int D, const int32_t* __restrict__ plane_of
   const float r2 = __fmul_rn(radius, radius);
 
   const bool fast = DT > 0 && staged && n_cand <= 32 * 64;
-  for (int i = s_lo + warp; i < s_hi; i += kKnnThreads / 32) {
+  for (int i = s_lo + part * WPB + warp; i < s_hi; i += WPB * split) {
     if constexpr (DT > 0) {
       if (fast) {
         if (n_cand <= 32 * 16)
@@ -349,14 +356,15 @@ cudaError_t launch_build_graph(etx_ctx* ctx, const float* emb, const int8_t* pla
     launch(ctx, "graph_plane_bins", k_plane_bins, (unsigned)((nb + 255) / 256), 256, 0, s, plane,
            hit_offsets, n_events, (int)n_hits, P, ctx->plane_off);
   int32_t* cnt = ctx->hit_cnt;  // counts, then (in place) offsets; [n_hits + 1]
-  const unsigned blocks = (unsigned)n_events * (unsigned)(P - 1);
+  const int split = ctx->knn_split;
+  const unsigned blocks = (unsigned)n_events * (unsigned)(P - 1) * (unsigned)split;
   const size_t smem = (size_t)kStageFloats * sizeof(float) + kKnnThreads / 32 * 256 * sizeof(int);
   // hits of the last plane get no block: start from zero counts
   cudaError_t e0 = cudaMemsetAsync(cnt, 0, (size_t)(n_hits + 1) * sizeof(int32_t), s);
   if (e0 != cudaSuccess) return e0;
   auto knn = [&](auto kernel, const char* name, int32_t* sp, int32_t* dp, int64_t cap) {
     launch(ctx, name, kernel, blocks, kKnnThreads, smem, s, emb, D, (const int32_t*)ctx->plane_off,
-           P, radius, k_max, cnt, n_hits, sp, dp, cap, ctx->d_err);
+           P, radius, k_max, cnt, n_hits, sp, dp, cap, ctx->d_err, split);
   };
   if (n_hits > 0 && blocks > 0) {
     if (D == 8) knn(k_knn<false, 8>, "graph_knn_count", nullptr, nullptr, 0);

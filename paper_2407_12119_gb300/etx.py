@@ -30,7 +30,12 @@ EXPORTED = ["etx_ctx_create", "etx_ctx_destroy", "etx_last_error", "etx_weights_
             "etx_load_weights", "etx_ctx_sync", "etx_embed", "etx_build_graph",
             "etx_gnn_forward", "etx_gnn_param_count", "etx_gnn_backward",
             "etx_edges_to_tracks", "etx_edges_to_tracks_noalloc", "etx_launch_count",
-            "etx_profile_enable", "etx_profile_read", "etx_weighted_bce", "etx_adam_step"]
+            "etx_profile_enable", "etx_profile_read", "etx_weighted_bce", "etx_adam_step",
+            "etx_autotune", "etx_tuned", "etx_set_tuned"]
+# knob names of the autotuner (etx_tuned)
+TUNE_KNOBS = ["knn_split"] + [f"tc_stages/{b}/{d}" for b in
+                              ("edge_encoder", "node_update", "edge_update", "classifier")
+                              for d in ("bf16", "fp8")]
 
 
 class EtxConfig(ctypes.Structure):
@@ -82,6 +87,10 @@ def lib() -> ctypes.CDLL:
         "etx_edges_to_tracks_noalloc": (i32, [vp, vp, vp, f32, vp, vp, i32, i64, i32, vp, vp, vp]),
         "etx_weighted_bce": (i32, [vp, vp, vp, vp, i32, f32, vp, vp, vp]),
         "etx_adam_step": (i32, [vp, vp, vp, vp, vp, i64, f32, f32, f32, f32, i64, vp]),
+        "etx_autotune": (i32, [vp, vp, vp, vp, vp, vp, i32, i64, f32, i32, i32, vp, vp, vp, i64,
+                               vp, vp, vp]),
+        "etx_tuned": (i32, [vp, ctypes.c_char_p]),
+        "etx_set_tuned": (i32, [vp, ctypes.c_char_p, i32]),
         "etx_launch_count": (i64, [vp]),
         "etx_profile_enable": (i32, [vp, i32]),
         "etx_profile_read": (i32, [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
@@ -273,6 +282,36 @@ class Context:
                                           _ptr(dst), _ptr(edge_offsets), n_events, DTYPES[dtype],
                                           _ptr(logits), _stream(stream)))
         return logits
+
+    def autotune(self, x, y, z, plane, hit_offsets, radius: float, k_max: int, emb, src, dst,
+                 edge_offsets, logits, dtype: str = "bf16", stream=None):
+        """Time the candidate launch configurations on this batch and keep the
+        fastest (see etx_autotune); returns {knob: value}.  The output tensors
+        receive the results of the chosen configuration."""
+        dev = self.device
+        for t, n in ((x, "x"), (y, "y"), (z, "z"), (emb, "emb"), (logits, "logits")):
+            _need(t, torch.float32, n, dev)
+        _need(plane, torch.int8, "plane", dev)
+        for t, n in ((hit_offsets, "hit_offsets"), (src, "src"), (dst, "dst"),
+                     (edge_offsets, "edge_offsets")):
+            _need(t, torch.int32, n, dev)
+        n_hits, n_events = x.shape[0], hit_offsets.shape[0] - 1
+        self._check(lib().etx_autotune(self._h, _ptr(x), _ptr(y), _ptr(z), _ptr(plane),
+                                       _ptr(hit_offsets), n_events, n_hits, float(radius),
+                                       int(k_max), DTYPES[dtype], _ptr(emb), _ptr(src), _ptr(dst),
+                                       int(src.shape[0]), _ptr(edge_offsets), _ptr(logits),
+                                       _stream(stream)))
+        return self.tuned()
+
+    def tuned(self) -> dict:
+        """Current launch configuration chosen by the autotuner, by knob name."""
+        return {k: int(lib().etx_tuned(self._h, k.encode())) for k in TUNE_KNOBS}
+
+    def set_tuned(self, **knobs):
+        """Set launch-configuration knobs (names as in ``tuned()``, with '/'
+        written as '__'), e.g. ``set_tuned(knn_split=2)``."""
+        for k, v in knobs.items():
+            self._check(lib().etx_set_tuned(self._h, k.replace("__", "/").encode(), int(v)))
 
     @property
     def gnn_param_count(self) -> int:

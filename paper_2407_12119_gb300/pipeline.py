@@ -56,6 +56,18 @@ class TrackFinder:
                                        n_tracks=self.n_tracks[:max(n_events, 1)])
         return labels, nt
 
+    def autotune(self, x, y, z, plane, hit_offsets, n_hits: int, n_events: int):
+        """Let the library time its candidate launch configurations on this batch
+        (k-NN work partitioning, tensor-core ring depth) and keep the fastest;
+        returns the choices.  Capture after tuning: a graph keeps the
+        configuration it was recorded with."""
+        m = self.model
+        eoff = self.eoff[:n_events + 1]
+        return self.ctx.autotune(x[:n_hits], y[:n_hits], z[:n_hits], plane[:n_hits],
+                                 hit_offsets[:n_events + 1], m.radius, m.k_max,
+                                 self.emb[:n_hits], self.src, self.dst, eoff, self.logits,
+                                 dtype=self.dtype)
+
     def capture(self, x, y, z, plane, hit_offsets, n_hits: int, n_events: int,
                 min_hits: int = 3):
         """Record ``run_device`` on these device tensors into one CUDA graph.
