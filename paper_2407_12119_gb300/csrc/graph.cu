@@ -92,113 +92,91 @@ __global__ void k_plane_bins(const int8_t* __restrict__ plane, const int32_t* __
   plane_off[t] = lo;
 }
 
-// Fast path for one source hit (compile-time D, candidates staged, at most
-// 32 * kMaxI of them): every lane keeps the sortable keys (FP32 bit
-// patterns; non-qualifying candidates get the all-ones sentinel) of its
-// candidates in registers, so the count, the radix select and the write all
-// run over registers without recomputing distances.
-template <bool EMIT, int D, int kMaxI>
-__device__ __forceinline__ void knn_source_fast(const float* __restrict__ emb, int i,
+// Fast path for one source hit (compile-time D, candidates staged): one pass
+// over the candidates lists the qualifying ones (d2 < r2) in the warp's
+// scratch as (key, j) pairs, key = the FP32 bit pattern of d2 (order-preserving
+// for d2 >= 0), in ascending j (ballot compaction).  If more than k_max
+// qualify, a pair is kept iff fewer than k_max listed pairs are smaller than it
+// ((key, j) pairs are distinct, so this keeps exactly the k_max smallest by
+// (d2, j)); kept pairs are written in list order, i.e. ascending j.  Returns
+// false (nothing written) when more than kListCap qualify: the caller then
+// takes the general path.  The loops run over runtime trip counts so that the
+// code stays small (instruction-cache misses dominated the unrolled version).
+constexpr int kListCap = 256;  // (key, j) pairs per warp: 2 KB of shared memory
+
+template <bool EMIT, int D>
+__device__ __forceinline__ bool knn_source_list(const float* __restrict__ emb, int i,
                                                 const float* cand_s, int n_cand, int c_lo,
                                                 float r2, int k_max, int32_t* cnt_or_off,
-                                                int32_t* __restrict__ src, int32_t* __restrict__ dst,
-                                                int lane, int* hist) {
+                                                int32_t* __restrict__ src,
+                                                int32_t* __restrict__ dst, int lane,
+                                                uint64_t* list) {
   const unsigned full = 0xffffffffu, lt_mask = (1u << lane) - 1u;
   float ei[D];
 #pragma unroll
   for (int d = 0; d < D; ++d) ei[d] = emb[(int64_t)i * D + d];
-  const int nt = (n_cand + 31) >> 5;
-  uint32_t key[kMaxI];
-  int cnt = 0;
-#pragma unroll
-  for (int t = 0; t < kMaxI; ++t) {
-    key[t] = 0xffffffffu;
-    if (t < nt) {
-      const int j = 32 * t + lane;
-      if (j < n_cand) {
-        const float d2 = d2_fixed<D>(ei, cand_s + j, n_cand);
-        if (d2 < r2) key[t] = __float_as_uint(d2);
-      }
-      cnt += __popc(__ballot_sync(full, key[t] != 0xffffffffu));
+  int n = 0;
+#pragma unroll 1
+  for (int j0 = 0; j0 < n_cand; j0 += 32) {
+    const int j = j0 + lane;
+    bool in = false;
+    uint32_t key = 0;
+    if (j < n_cand) {
+      const float d2 = d2_fixed<D>(ei, cand_s + j, n_cand);
+      in = d2 < r2;
+      key = __float_as_uint(d2);
     }
+    const unsigned m = __ballot_sync(full, in);
+    if (EMIT && in) {
+      const int pos = n + __popc(m & lt_mask);
+      if (pos < kListCap) list[pos] = (static_cast<uint64_t>(key) << 32) | static_cast<uint32_t>(j);
+    }
+    n += __popc(m);
   }
   if (!EMIT) {
-    if (lane == 0) cnt_or_off[i] = min(cnt, k_max);
-    return;
+    if (lane == 0) cnt_or_off[i] = min(n, k_max);
+    return true;
   }
-  uint32_t kth = 0xffffffffu;
-  int take_eq = 0;
-  const bool capped = cnt > k_max;
-  if (capped) {
-    // radix select in four 8-bit digits with a per-warp 256-bin histogram:
-    // find the rank-th smallest key among those sharing the digits chosen so far
-    uint32_t prefix = 0, pmask = 0;
-    int rank = k_max;  // 1-based rank still to locate
-    for (int shift = 24; shift >= 0; shift -= 8) {
-#pragma unroll
-      for (int q = 0; q < 8; ++q) hist[8 * lane + q] = 0;
-      __syncwarp();
-#pragma unroll
-      for (int t = 0; t < kMaxI; ++t)
-        if (t < nt && key[t] != 0xffffffffu && (key[t] & pmask) == prefix)
-          atomicAdd(hist + ((key[t] >> shift) & 255u), 1);
-      __syncwarp();
-      int c8[8], sum = 0;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        c8[q] = hist[8 * lane + q];
-        sum += c8[q];
-      }
-      int incl = sum;  // inclusive scan of the lanes' 8-bin sums
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(full, incl, o);
-        if (lane >= o) incl += v;
-      }
-      const int excl = incl - sum;
-      const unsigned hit = __ballot_sync(full, excl < rank && rank <= incl);
-      const int owner = __ffs(hit) - 1;
-      int digit = 0, below = 0;
-      if (lane == owner) {
-        int acc = excl;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          if (acc + c8[q] >= rank) {
-            digit = 8 * lane + q;
-            below = acc;
-            break;
-          }
-          acc += c8[q];
-        }
-      }
-      digit = __shfl_sync(full, digit, owner);
-      below = __shfl_sync(full, below, owner);
-      prefix |= static_cast<uint32_t>(digit) << shift;
-      pmask |= 255u << shift;
-      rank -= below;
-      __syncwarp();
-    }
-    kth = prefix;          // the k_max-th smallest key
-    take_eq = rank;        // how many keys equal to kth are kept (in index order)
-  }
+  if (n > kListCap) return false;
+  __syncwarp();
   const int base = cnt_or_off[i];
-  int written = 0, eq_seen = 0;
+  constexpr int R = kListCap / 32;  // list entries per lane: q = 32 r + lane
+  bool keep[R];
 #pragma unroll
-  for (int t = 0; t < kMaxI; ++t) {
-    if (t >= nt) break;
-    bool in = key[t] < kth;
-    const bool eq = capped && key[t] == kth;
-    const unsigned eqm = __ballot_sync(full, eq);
-    if (eq) in = eq_seen + __popc(eqm & lt_mask) < take_eq;
-    eq_seen += __popc(eqm);
-    const unsigned inm = __ballot_sync(full, in);
-    if (in) {
-      const int pos = base + written + __popc(inm & lt_mask);
-      src[pos] = i;
-      dst[pos] = c_lo + 32 * t + lane;
+  for (int r = 0; r < R; ++r) keep[r] = 32 * r + lane < n;
+  if (n > k_max) {
+    uint64_t mine[R];
+    int rank[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      mine[r] = keep[r] ? list[32 * r + lane] : ~0ull;
+      rank[r] = 0;
     }
-    written += __popc(inm);
+    const int nr = (n + 31) >> 5;  // lanes' entries in use
+#pragma unroll 1
+    for (int q = 0; q < n; ++q) {
+      const uint64_t x = list[q];
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (r < nr) rank[r] += x < mine[r];
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) keep[r] = keep[r] && rank[r] < k_max;
   }
+  int written = 0;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    if (32 * r >= n) break;
+    const unsigned m = __ballot_sync(full, keep[r]);
+    if (keep[r]) {
+      const int pos = base + written + __popc(m & lt_mask);
+      src[pos] = i;
+      dst[pos] = c_lo + static_cast<int>(static_cast<uint32_t>(list[32 * r + lane]));
+    }
+    written += __popc(m);
+  }
+  __syncwarp();
+  return true;
 }
 
 template <bool EMIT, int DT>
@@ -207,8 +185,8 @@ k_knn(const float* __restrict__ emb, int D, const int32_t* __restrict__ plane_of
       float radius, int k_max, int32_t* __restrict__ cnt_or_off, int64_t n_hits,
       int32_t* __restrict__ src, int32_t* __restrict__ dst, int64_t capacity, int* err,
       int split) {
-  extern __shared__ float cand_s[];  // [D][n_stage], then 256 ints per warp (select histograms)
-  int* hist_s = reinterpret_cast<int*>(cand_s + kStageFloats);
+  extern __shared__ float cand_s[];  // [D][n_stage], then kListCap (key, j) pairs per warp
+  uint64_t* list_s = reinterpret_cast<uint64_t*>(cand_s + kStageFloats);  // per-warp pair lists
   // `split` blocks share the sources of one (event, plane): block `part` takes
   // every split-th group of warps' sources (each stages the candidates itself)
   const int bp = blockIdx.x / split, part = blockIdx.x % split;
@@ -247,18 +225,12 @@ k_knn(const float* __restrict__ emb, int D, const int32_t* __restrict__ plane_of
   const int cstep = staged ? 1 : D;              // stride between candidates
   const float r2 = __fmul_rn(radius, radius);
 
-  const bool fast = DT > 0 && staged && n_cand <= 32 * 64;
+  const bool fast = DT > 0 && staged;
   for (int i = s_lo + part * WPB + warp; i < s_hi; i += WPB * split) {
     if constexpr (DT > 0) {
-      if (fast) {
-        if (n_cand <= 32 * 16)
-          knn_source_fast<EMIT, DT, 16>(emb, i, cand_s, n_cand, c_lo, r2, k_max, cnt_or_off, src,
-                                        dst, lane, hist_s + 256 * warp);
-        else
-          knn_source_fast<EMIT, DT, 64>(emb, i, cand_s, n_cand, c_lo, r2, k_max, cnt_or_off, src,
-                                        dst, lane, hist_s + 256 * warp);
+      if (fast && knn_source_list<EMIT, DT>(emb, i, cand_s, n_cand, c_lo, r2, k_max, cnt_or_off,
+                                            src, dst, lane, list_s + kListCap * warp))
         continue;
-      }
     }
     float ei[kMaxDim];
     for (int d = 0; d < D; ++d) ei[d] = emb[(int64_t)i * D + d];
@@ -358,7 +330,7 @@ cudaError_t launch_build_graph(etx_ctx* ctx, const float* emb, const int8_t* pla
   int32_t* cnt = ctx->hit_cnt;  // counts, then (in place) offsets; [n_hits + 1]
   const int split = ctx->knn_split;
   const unsigned blocks = (unsigned)n_events * (unsigned)(P - 1) * (unsigned)split;
-  const size_t smem = (size_t)kStageFloats * sizeof(float) + kKnnThreads / 32 * 256 * sizeof(int);
+  const size_t smem = (size_t)kStageFloats * sizeof(float) + kKnnThreads / 32 * kListCap * sizeof(uint64_t);
   // hits of the last plane get no block: start from zero counts
   cudaError_t e0 = cudaMemsetAsync(cnt, 0, (size_t)(n_hits + 1) * sizeof(int32_t), s);
   if (e0 != cudaSuccess) return e0;
@@ -384,7 +356,7 @@ cudaError_t launch_build_graph(etx_ctx* ctx, const float* emb, const int8_t* pla
 }
 
 cudaError_t knn_set_smem_attr() {
-  const int smem = (int)(kStageFloats * sizeof(float) + kKnnThreads / 32 * 256 * sizeof(int));
+  const int smem = (int)(kStageFloats * sizeof(float) + kKnnThreads / 32 * kListCap * sizeof(uint64_t));
   const void* ks[] = {(const void*)k_knn<false, 0>, (const void*)k_knn<true, 0>,
                       (const void*)k_knn<false, 4>, (const void*)k_knn<true, 4>,
                       (const void*)k_knn<false, 8>, (const void*)k_knn<true, 8>};
