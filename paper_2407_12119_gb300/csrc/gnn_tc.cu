@@ -32,7 +32,6 @@
 // otherwise).  Every wait is bounded; a timeout records ETX_ERR_TIMEOUT,
 // raises a shared abort flag and every role stops.
 #include <cuda_bf16.h>
-#include <cuda_fp8.h>
 
 #include "sm100.cuh"
 
@@ -118,11 +117,17 @@ struct TcArgs {
   int* err;
 };
 
-// Four values to e4m3 (saturating), first value in the lowest byte.
+// Four values to e4m3 (round to nearest even, saturating to +-448), first value
+// in the lowest byte.
 __device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d) {
-  const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
-  const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
-  return lo | (hi << 16);
+  uint32_t r;
+  asm("{\n\t.reg .b16 lo, hi;\n\t"
+      "cvt.rn.satfinite.e4m3x2.f32 lo, %2, %1;\n\t"
+      "cvt.rn.satfinite.e4m3x2.f32 hi, %4, %3;\n\t"
+      "mov.b32 %0, {lo, hi};\n\t}"
+      : "=r"(r)
+      : "f"(a), "f"(b), "f"(c), "f"(d));
+  return r;
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
