@@ -67,7 +67,6 @@ struct Elt {
 };
 
 constexpr int SMEM_MAX = 232448;         // opt-in shared memory per CTA
-
 template <int MODE, bool F8, int NS>
 struct Cfg {
   static constexpr int KIN = MODE == TC_EDGE_ENC ? 2 * H : (MODE == TC_CLS ? H : 3 * H);
@@ -377,7 +376,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
         const int64_t gr = row0 + (fi >> 4);
         f[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (fi < TM * SUB / 4 && gr < n_rows)
-          f[k] = *reinterpret_cast<const float4*>(chunk_src<MODE>(a, SUB * c, gr, 0, 0) + 4 * (fi & 15));
+          // L2 only: the epilogue re-reads these rows (the residual) from L2
+          f[k] = __ldcg(reinterpret_cast<const float4*>(chunk_src<MODE>(a, SUB * c, gr, 0, 0) + 4 * (fi & 15)));
       }
     };
     // Wait until ring chunk j's slot is free again (its previous round consumed).
@@ -704,7 +704,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
                 const float2 o0 = __fadd2_rn(f2(v.x, v.y), f2(res[it].x, res[it].y));
                 const float2 o1 = __fadd2_rn(f2(v.z, v.w), f2(res[it].z, res[it].w));
                 const int64_t el = coff + 8 * it * H + col;  // element index in the stream
-                *reinterpret_cast<float4*>(outp + el) = make_float4(o0.x, o0.y, o1.x, o1.y);
+                // streaming store: the row is not read again in this launch
+                __stcs(reinterpret_cast<float4*>(outp + el), make_float4(o0.x, o0.y, o1.x, o1.y));
                 if constexpr (MODE == TC_NODE_UPD) {  // the copy the edge blocks gather
                   if constexpr (F8)
                     *reinterpret_cast<uint32_t*>(a.h_lp + el) = pack_e4m3x4(o0.x, o0.y, o1.x, o1.y);
