@@ -76,6 +76,12 @@ def max_over_ranks(value: float, world: int, device=None) -> float:
     return float(t.item())
 
 
+def replica_throughput(world: int, events_per_rank: int, steps: int, ms_total_max: float) -> float:
+    """Whole-job events/s of `world` replicas, each processing `events_per_rank`
+    events per step, timed as the maximum over ranks of the span of `steps` steps."""
+    return world * events_per_rank * steps / (ms_total_max / 1e3)
+
+
 def barrier(world: int):
     if world > 1:
         import torch.distributed as dist
@@ -366,7 +372,7 @@ def run_ours(args):
     tf.ctx.sync()
     ms_total = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     ms_step = ms_total / args.steps
-    value = world * B * args.steps / (ms_total / 1e3)
+    value = replica_throughput(world, B, args.steps, ms_total)
 
     # ---- end to end through the public API from pinned host buffers -------
     lab_h = torch.empty(N, dtype=torch.int32, pin_memory=True)
