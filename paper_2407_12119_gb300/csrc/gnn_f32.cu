@@ -104,8 +104,30 @@ __global__ void k_in_sort(const int32_t* __restrict__ in_off, int n_hits, int32_
 // ---------------------------------------------------------------------------
 // messages (Eq. 4): m_l = [sum_{l->j} e_lj, sum_{i->l} e_il]
 // ---------------------------------------------------------------------------
-template <int H>
-__global__ void k_messages(const float* __restrict__ e, const int32_t* __restrict__ out_off,
+// Two values to BF16 (round to nearest even), first value in the low half.
+__device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+
+// Four values to e4m3 (round to nearest even, saturating), first in the lowest byte.
+__device__ __forceinline__ uint32_t e4m3x4(float a, float b, float c, float d) {
+  uint32_t r;
+  asm("{\n\t.reg .b16 lo, hi;\n\t"
+      "cvt.rn.satfinite.e4m3x2.f32 lo, %2, %1;\n\t"
+      "cvt.rn.satfinite.e4m3x2.f32 hi, %4, %3;\n\t"
+      "mov.b32 %0, {lo, hi};\n\t}"
+      : "=r"(r)
+      : "f"(a), "f"(b), "f"(c), "f"(d));
+  return r;
+}
+
+// OUTT 0: FP32 messages; 1: rounded to BF16, 2: to e4m3 (the tensor-core node
+// update's operand type; sums are FP32 either way), rows of 2H values at m.
+template <int H, int OUTT = 0>
+__global__ void __launch_bounds__(256, 8)  // 32 registers: eight 256-thread blocks per SM
+k_messages(const float* __restrict__ e, const int32_t* __restrict__ out_off,
                            const int32_t* __restrict__ in_off, const int32_t* __restrict__ perm,
                            const int32_t* __restrict__ n_edges_dev, int n_hits,
                            float* __restrict__ m) {
@@ -130,8 +152,18 @@ __global__ void k_messages(const float* __restrict__ e, const int32_t* __restric
       const float4 v = __ldg(reinterpret_cast<const float4*>(e + (int64_t)perm[q] * H + c));
       si.x += v.x; si.y += v.y; si.z += v.z; si.w += v.w;
     }
-    *reinterpret_cast<float4*>(m + l * 2 * H + c) = so;
-    *reinterpret_cast<float4*>(m + l * 2 * H + H + c) = si;
+    if constexpr (OUTT == 0) {
+      *reinterpret_cast<float4*>(m + l * 2 * H + c) = so;
+      *reinterpret_cast<float4*>(m + l * 2 * H + H + c) = si;
+    } else if constexpr (OUTT == 1) {
+      uint16_t* mb = reinterpret_cast<uint16_t*>(m) + l * 2 * H;
+      *reinterpret_cast<uint2*>(mb + c) = make_uint2(bf16x2(so.x, so.y), bf16x2(so.z, so.w));
+      *reinterpret_cast<uint2*>(mb + H + c) = make_uint2(bf16x2(si.x, si.y), bf16x2(si.z, si.w));
+    } else {
+      uint8_t* m8 = reinterpret_cast<uint8_t*>(m) + l * 2 * H;
+      *reinterpret_cast<uint32_t*>(m8 + c) = e4m3x4(so.x, so.y, so.z, so.w);
+      *reinterpret_cast<uint32_t*>(m8 + H + c) = e4m3x4(si.x, si.y, si.z, si.w);
+    }
   }
 }
 
@@ -307,9 +339,12 @@ cudaError_t forward(etx_ctx* ctx, const float* x, const float* y, const float* z
   const int msg_grid = grid_for(ctx, (const void*)k_messages<H>, 256, 0,
                                 (N + (256 / 32) * (32 / (H / 4)) - 1) / ((256 / 32) * (32 / (H / 4))));
   for (int k = 0; k < ctx->cfg.n_iters; ++k) {
-    if (N > 0)
-      launch(ctx, "gnn_messages", k_messages<H>, msg_grid, 256, 0, s, ctx->e, ctx->out_off,
-             ctx->in_off, ctx->perm_in, n_edges_dev, (int)N, ctx->m);
+    if (N > 0) {
+      // the tensor-core node update takes the messages in its operand type
+      auto kern = !tc ? k_messages<H, 0> : (f8 ? k_messages<H, 2> : k_messages<H, 1>);
+      launch(ctx, "gnn_messages", kern, msg_grid, 256, 0, s, ctx->e, ctx->out_off, ctx->in_off,
+             ctx->perm_in, n_edges_dev, (int)N, ctx->m);
+    }
     if (tc) {
       chain(launch_node_update_tc(ctx, k, N, f8, s));
       chain(launch_edge_update_tc(ctx, k, N, src, dst, n_edges_dev, f8, s));

@@ -113,6 +113,7 @@ struct TcArgs {
   const float* wcls;  // classifier last Linear [H]
   const float* bcls;  // [1]
   uint8_t* h_lp;      // h rounded to the operand type (node update writes it)
+  const uint8_t* m_lp;  // node update: [m_out, m_in] rounded to the operand type, rows of 2H
   int* err;
 };
 
@@ -363,9 +364,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
     const int pt = tid - 32 * EPI_WARPS;
     constexpr int NF = (TM * SUB / 4 + PROD_THREADS - 1) / PROD_THREADS;  // float4 pieces per thread
     constexpr int NG = (TM * 8 + PROD_THREADS - 1) / PROD_THREADS;        // 16-byte copies per thread
-    constexpr bool GATHER = MODE == TC_EDGE_ENC || MODE == TC_EDGE_UPD;
+    // edge blocks copy [h_i, h_j] from the low-precision h; the node update
+    // copies [m_out, m_in] from the low-precision messages (its own row)
+    constexpr bool GATHER = MODE != TC_CLS;
     // 64-column FP32 steps per tile done by the threads (the copies do the rest)
-    constexpr int SE = GATHER ? (MODE == TC_EDGE_UPD ? H / SUB : 0) : C::KS;
+    constexpr int SE = GATHER ? (MODE == TC_EDGE_ENC ? 0 : H / SUB) : C::KS;
     // Loads of step c (64 columns of the FP32 block input) of local tile t.
     auto fetch = [&](int64_t t, int c, float4 (&f)[NF]) {
       if (t >= my_tiles) return;
@@ -427,8 +430,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
           const int fi = pt + PROD_THREADS * k;
           const int64_t gr = r0 + (fi >> 3);
           const bool ok = t < my_tiles && fi < TM * 8 && gr < n_rows;
-          xs[k] = ok ? min(max(a.src[gr], 0), max(nn - 1, 0)) : 0;
-          xd[k] = ok ? min(max(a.dst[gr], 0), max(nn - 1, 0)) : 0;
+          if constexpr (MODE == TC_NODE_UPD) {
+            xs[k] = xd[k] = ok ? (int)gr : 0;
+          } else {
+            xs[k] = ok ? min(max(a.src[gr], 0), max(nn - 1, 0)) : 0;
+            xd[k] = ok ? min(max(a.dst[gr], 0), max(nn - 1, 0)) : 0;
+          }
         }
       };
       load_idx(0, gs, gd);
@@ -458,14 +465,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
             break;
           }
           const int hc = c - KE;
-          const int rowbytes = F8 ? H : 2 * H;
-          const int cbase = (hc % KH) * 128;  // byte offset of the chunk in the node row
+          // source rows: node rows of h (H values) or message rows (2H values)
+          const int rowbytes = (MODE == TC_NODE_UPD ? 2 : 1) * (F8 ? H : 2 * H);
+          const int cbase = (MODE == TC_NODE_UPD ? hc : hc % KH) * 128;  // byte offset in the row
+          const uint8_t* srcb = MODE == TC_NODE_UPD ? a.m_lp : a.h_lp;
 #pragma unroll
           for (int k = 0; k < NG; ++k) {
             const int fi = pt + PROD_THREADS * k;
             if (fi < TM * 8)
               cp_async16(sA + slot * CHUNK + sw128(fi >> 3, fi & 7),
-                         a.h_lp + (int64_t)(hc < KH ? gs[k] : gd[k]) * rowbytes + cbase + 16 * (fi & 7));
+                         srcb + (int64_t)(hc < KH ? gs[k] : gd[k]) * rowbytes + cbase + 16 * (fi & 7));
           }
           cp_async_arrive(&bars[B_FULL + slot]);
           __syncwarp();
@@ -822,6 +831,7 @@ cudaError_t launch_edge_encoder_tc(etx_ctx* ctx, int64_t N, const int32_t* src, 
 
 cudaError_t launch_node_update_tc(etx_ctx* ctx, int k, int64_t N, bool f8, cudaStream_t s) {
   TcArgs a = base_args(ctx, N, nullptr, nullptr, nullptr, nullptr);
+  a.m_lp = reinterpret_cast<const uint8_t*>(ctx->m);  // written by the messages kernel
   set_block(a, ctx->w.node[k], ctx->w.node_tc[k], f8);
   return launch_any<TC_NODE_UPD>(ctx, f8, "gnn_node_update_bf16", "gnn_node_update_fp8", a, N, s);
 }
