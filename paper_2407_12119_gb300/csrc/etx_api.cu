@@ -699,8 +699,9 @@ etx_status etx_autotune(etx_ctx* ctx, const float* x, const float* y, const floa
   if (st == ETX_OK && dtype != ETX_F32) {
     const int f8 = dtype == ETX_FP8E4M3 ? 1 : 0;
     const char* suffix = f8 ? "_fp8" : "_bf16";
-    double ms[2][4] = {};
-    for (int v = 0; v < 2 && st == ETX_OK; ++v) {
+    constexpr int NV = 4;  // ring slots 2 .. 5
+    double ms[NV][4] = {};
+    for (int v = 0; v < NV && st == ETX_OK; ++v) {
       for (int m = 0; m < 4; ++m) ctx->tc_stages[m][f8] = 2 + v;
       for (int r = 0; r <= kReps && st == ETX_OK; ++r) {
         st = etx_gnn_forward(ctx, x, y, z, n_hits, src, dst, edge_offsets, n_events, dtype, logits,
@@ -723,7 +724,12 @@ etx_status etx_autotune(etx_ctx* ctx, const float* x, const float* y, const floa
         ctx->prof_used = 0;
       }
     }
-    for (int m = 0; m < 4; ++m) ctx->tc_stages[m][f8] = ms[0][m] < ms[1][m] ? 2 : 3;
+    for (int m = 0; m < 4; ++m) {
+      int best_v = 0;
+      for (int v = 1; v < NV; ++v)
+        if (ms[v][m] < ms[best_v][m]) best_v = v;
+      ctx->tc_stages[m][f8] = 2 + best_v;
+    }
     if (st == ETX_OK)
       st = etx_gnn_forward(ctx, x, y, z, n_hits, src, dst, edge_offsets, n_events, dtype, logits,
                            stream);
@@ -760,7 +766,7 @@ etx_status etx_set_tuned(etx_ctx* ctx, const char* knob, int32_t value) {
   for (int m = 0; m < 4; ++m)
     for (int f8 = 0; f8 < 2; ++f8)
       if (k == std::string("tc_stages/") + kTcBlock[m] + (f8 ? "/fp8" : "/bf16")) {
-        if (value != 2 && value != 3) return fail(ctx, ETX_ERR_ARG, "tc_stages must be 2 or 3");
+        if (value < 2 || value > 5) return fail(ctx, ETX_ERR_ARG, "tc_stages must be 2 to 5");
         ctx->tc_stages[m][f8] = value;
         return ETX_OK;
       }

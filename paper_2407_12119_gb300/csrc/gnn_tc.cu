@@ -761,12 +761,16 @@ cudaError_t launch_tc_ns(etx_ctx* ctx, const char* name, const TcArgs& a, int64_
   return cudaGetLastError();
 }
 
-// ring depth from the context's tuning (2 or 3 slots)
+// ring depth from the context's tuning (2 to 5 slots; capped by shared memory)
 template <int MODE, bool F8>
 cudaError_t launch_tc(etx_ctx* ctx, const char* name, const TcArgs& a, int64_t max_rows,
                       cudaStream_t s) {
-  return ctx->tc_stages[MODE][F8 ? 1 : 0] == 2 ? launch_tc_ns<MODE, F8, 2>(ctx, name, a, max_rows, s)
-                                                : launch_tc_ns<MODE, F8, 3>(ctx, name, a, max_rows, s);
+  switch (ctx->tc_stages[MODE][F8 ? 1 : 0]) {
+    case 2: return launch_tc_ns<MODE, F8, 2>(ctx, name, a, max_rows, s);
+    case 4: return launch_tc_ns<MODE, F8, 4>(ctx, name, a, max_rows, s);
+    case 5: return launch_tc_ns<MODE, F8, 5>(ctx, name, a, max_rows, s);
+    default: return launch_tc_ns<MODE, F8, 3>(ctx, name, a, max_rows, s);
+  }
 }
 
 // h (FP32, [n][128]) rounded to BF16 rows of 256 bytes or e4m3 rows of 128 bytes.

@@ -42,7 +42,7 @@ def test_every_configuration_gives_the_same_results(finder, dtype):
     for blk in ("edge_encoder", "node_update", "edge_update", "classifier"):
         tf.ctx.set_tuned(**{f"tc_stages__{blk}__{dtype}": 3})
     ref = outputs(tf, args)
-    for split, stages in ((2, 2), (4, 3), (4, 2)):
+    for split, stages in ((2, 2), (4, 3), (4, 2), (1, 4), (2, 5)):
         tf.ctx.set_tuned(knn_split=split)
         for blk in ("edge_encoder", "node_update", "edge_update", "classifier"):
             tf.ctx.set_tuned(**{f"tc_stages__{blk}__{dtype}": stages})
@@ -58,7 +58,7 @@ def test_autotune_picks_candidates_and_keeps_results(finder):
     choice = tf.autotune(*args)
     assert choice["knn_split"] in (1, 2, 4)
     for blk in ("edge_encoder", "node_update", "edge_update", "classifier"):
-        assert choice[f"tc_stages/{blk}/bf16"] in (2, 3)
+        assert choice[f"tc_stages/{blk}/bf16"] in (2, 3, 4, 5)
     E = int(tf.eoff[args[-1]].item())
     assert torch.equal(tf.logits[:E], ref[3])  # the tuner's own last forward
     got = outputs(tf, args)
@@ -72,6 +72,6 @@ def test_set_tuned_rejects_bad_values(finder):
     with pytest.raises(EtxError):
         tf.ctx.set_tuned(knn_split=3)
     with pytest.raises(EtxError):
-        tf.ctx.set_tuned(tc_stages__edge_update__bf16=5)
+        tf.ctx.set_tuned(tc_stages__edge_update__bf16=6)
     with pytest.raises(EtxError):
         tf.ctx.set_tuned(no_such_knob=1)
