@@ -70,8 +70,20 @@ struct TileAcc {
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
           const float av = c == 0 ? a[r].x : c == 1 ? a[r].y : c == 2 ? a[r].z : a[r].w;
+          if constexpr (CPT % 2 == 0) {
+            // packed FP32x2 FMAs (each lane the same IEEE fma as fmaf)
+            const float2 a2 = make_float2(av, av);
 #pragma unroll
-          for (int j = 0; j < CPT; ++j) v[r][j] = fmaf(av, w[j], v[r][j]);
+            for (int j = 0; j < CPT; j += 2) {
+              const float2 p = __ffma2_rn(a2, make_float2(w[j], w[j + 1]),
+                                          make_float2(v[r][j], v[r][j + 1]));
+              v[r][j] = p.x;
+              v[r][j + 1] = p.y;
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) v[r][j] = fmaf(av, w[j], v[r][j]);
+          }
         }
       }
     }
