@@ -374,3 +374,33 @@ def connected_components(src, dst, mask, hit_offsets):
                         nxt.append(v)
             frontier = nxt
     return labels.astype(np.int32)
+
+
+def plane_sweep_components(src, dst, mask, plane, hit_offsets, n_planes=26):
+    """The paper's plane-ordered label propagation (Sec. 7.3), a variant of the
+    components step that is not exact.  Every hit starts with its own index.
+    Forward: for planes 1 .. n_planes-1 in turn, every hit of the plane takes,
+    all at once, the smallest label among itself and the hits its kept
+    incoming edges come from (lower planes, final by then).  Backward: for
+    planes n_planes-2 .. 0 in turn, every hit of the plane takes the smallest
+    label among itself and the hits its kept outgoing edges go to.  Returns
+    event-local labels (int32)."""
+    hit_offsets = np.asarray(hit_offsets, np.int64)
+    N = int(hit_offsets[-1])
+    keep = np.asarray(mask, bool)
+    s = np.asarray(src, np.int64)[keep]
+    d = np.asarray(dst, np.int64)[keep]
+    plane = np.asarray(plane, np.int64)
+    lab = np.arange(N, dtype=np.int64)
+    for p in range(1, n_planes):
+        sel = plane[d] == p
+        new = lab.copy()
+        np.minimum.at(new, d[sel], lab[s[sel]])
+        lab = new
+    for p in range(n_planes - 2, -1, -1):
+        sel = plane[s] == p
+        new = lab.copy()
+        np.minimum.at(new, s[sel], lab[d[sel]])
+        lab = new
+    event_of = np.searchsorted(hit_offsets, np.arange(N), side="right") - 1
+    return (lab - hit_offsets[event_of]).astype(np.int32)

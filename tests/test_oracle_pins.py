@@ -448,6 +448,77 @@ def test_cc_truth_edges_reproduce_particles():
     assert np.all(glab[noise] == noise)
 
 
+def test_plane_sweep_counterexample_worked_by_hand():
+    # Sec. 7.3 sweep on the golden counter-example (hits e=0, a=1, c=2 on plane 0,
+    # b=3, d=4 on plane 1): forward b <- min(3, a, c) = 1, d <- min(4, c, e) = 0;
+    # backward a <- min(1, b) = 1, c <- min(2, b, d) = 0, e <- min(0, d) = 0.
+    case = next(c for c in json.loads((GOLDEN / "wcc_graphs.json").read_text())["cases"]
+                if c["name"] == "plane_sweep_counterexample")
+    plane = np.array([0, 0, 0, 1, 1])
+    lab = O.plane_sweep_components(case["src"], case["dst"], case["mask"], plane,
+                                   case["hit_offsets"])
+    assert lab.tolist() == [0, 1, 0, 1, 0]
+    assert case["labels"] == [0, 0, 0, 0, 0]  # the exact components differ
+
+
+def random_plane_graph(rng, sizes, n_planes=26, p_edge=0.15):
+    """Plane-sorted events of random sizes with random edges p -> p+1, p+2."""
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    plane = np.concatenate([np.sort(rng.integers(0, n_planes, n)) for n in sizes]).astype(np.int8)
+    src, dst = [], []
+    for b in range(len(sizes)):
+        lo, hi = offs[b], offs[b + 1]
+        for i in range(lo, hi):
+            for j in range(lo, hi):
+                if 1 <= plane[j] - plane[i] <= 2 and rng.uniform() < p_edge:
+                    src.append(i)
+                    dst.append(j)
+    return np.array(src, np.int64), np.array(dst, np.int64), plane, offs
+
+
+def test_plane_sweep_refines_exact_components():
+    inexact = 0
+    for seed in range(12):
+        rng = np.random.default_rng(seed)
+        src, dst, plane, offs = random_plane_graph(rng, [0, 60, 1, 45, 80], p_edge=0.25)
+        mask = rng.uniform(size=src.size) < 0.5
+        sweep = O.plane_sweep_components(src, dst, mask, plane, offs)
+        exact = O.connected_components(src, dst, mask, offs)
+        ev = np.searchsorted(offs, np.arange(offs[-1]), side="right") - 1
+        g_sweep = sweep + offs[ev]
+        g_exact = exact + offs[ev]
+        # every sweep label names a hit of the same exact component (so of the same
+        # event), no lower than the component minimum; equal sweep labels imply
+        # equal exact labels
+        assert np.all(g_exact[g_sweep] == g_exact)
+        assert np.all(sweep >= exact)
+        for lab in np.unique(g_sweep):
+            assert len(np.unique(g_exact[g_sweep == lab])) == 1
+        inexact += int(np.any(sweep != exact))
+    assert inexact > 0  # the random graphs exercise the inexactness
+
+
+def test_plane_sweep_special_cases():
+    rng = np.random.default_rng(5)
+    src, dst, plane, offs = random_plane_graph(rng, [30, 30])
+    none = O.plane_sweep_components(src, dst, np.zeros(src.size, bool), plane, offs)
+    ev = np.searchsorted(offs, np.arange(offs[-1]), side="right") - 1
+    np.testing.assert_array_equal(none, np.arange(offs[-1]) - offs[ev])
+    # tracks (one hit per plane, consecutive): the sweep is exact
+    b = make_batch(WORKLOADS["batch500"].recipe, 2, 1000)
+    pid = global_particle_ids(b)
+    s, d = [], []
+    for p in np.unique(pid[pid >= 0]):
+        hits = np.nonzero(pid == p)[0]
+        hits = hits[np.argsort(b.plane[hits], kind="stable")]
+        s.append(hits[:-1])
+        d.append(hits[1:])
+    s, d = np.concatenate(s), np.concatenate(d)
+    keep = np.ones(s.size, bool)
+    np.testing.assert_array_equal(O.plane_sweep_components(s, d, keep, b.plane, b.hit_offsets),
+                                  O.connected_components(s, d, keep, b.hit_offsets))
+
+
 def test_generator_geometry():
     b = make_batch(WORKLOADS["batch500"].recipe, 4, 1000)
     r = np.hypot(b.x.astype(float), b.y.astype(float))
