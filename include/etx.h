@@ -234,6 +234,27 @@ etx_status etx_edges_to_tracks_noalloc(const int32_t* src, const int32_t* dst,
                                        int32_t* labels, int32_t* n_tracks, void* stream);
 
 /*
+ * The paper's own track-building kernel (Sec. 7.3), for comparison with
+ * etx_edges_to_tracks: a plane-ordered propagation of minimum labels.  Every
+ * hit starts with its own index; forward, for planes 1 .. n_planes-1 in turn,
+ * each hit of the plane takes the smallest label among itself and the hits
+ * that its kept incoming edges (logit > threshold_logit) come from; backward,
+ * for planes n_planes-2 .. 0 in turn, each hit takes the smallest label among
+ * itself and the hits its kept outgoing edges go to.  This is not an exact
+ * connected-components algorithm (one component can end with several
+ * labels); labels[i] is the event-local index of a hit of the same component.
+ * Needs plane (int8 [n_hits], ascending within each event) and edges sorted by
+ * (src, dst) as etx_build_graph writes them; edge_offsets[n_events] is the
+ * edge count.  Errors as etx_edges_to_tracks; unsorted planes or edges are
+ * reported by etx_ctx_sync.  Asynchronous on `stream`.
+ */
+etx_status etx_edges_to_tracks_sweep(etx_ctx* ctx, const int32_t* src, const int32_t* dst,
+                                     const float* logits, float threshold_logit,
+                                     const int32_t* edge_offsets, const int8_t* plane,
+                                     const int32_t* hit_offsets, int32_t n_events, int64_t n_hits,
+                                     int32_t* labels, void* stream);
+
+/*
  * Autotuner (no counterpart in the paper: it picks launch configurations, not
  * results).  Runs the embedding, the graph and (for ETX_BF16 / ETX_FP8E4M3)
  * the interaction network on the given batch, timing with CUDA events each

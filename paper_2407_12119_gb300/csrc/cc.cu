@@ -11,7 +11,8 @@
 //
 // The paper's own kernel instead sweeps the planes forward and backward
 // taking minimum neighbour labels; that is not an exact connected-components
-// algorithm in general, so it is not used here.
+// algorithm in general, so it is not the track builder here.  It is provided
+// as a variant (k_plane_sweep) for comparison.
 #include "etx_internal.cuh"
 
 namespace etx {
@@ -31,6 +32,46 @@ __device__ __forceinline__ int find_root(int* parent, int x, int* err) {
   }
   set_err(err, DERR_TIMEOUT);
   return x;
+}
+
+// The paper's plane-ordered propagation (Sec. 7.3), one block per event.  Every
+// hit starts with its own index; forward, for planes 1 .. P-1 in turn, every
+// kept edge i -> j with j on the plane lowers lab[j] to lab[i] (i lies on one of
+// the two previous planes, whose labels are final); backward, for planes
+// P-2 .. 0, every kept edge i -> j with i on the plane lowers lab[i] to lab[j].
+// Edges are sorted by src and hits by plane, so the edges leaving planes
+// [a, b) are the contiguous range out_off[first hit of a] .. out_off[first hit
+// of b].  The result is independent of thread order (minimum of fixed values).
+__global__ void k_plane_sweep(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                              const float* __restrict__ logits, float thr,
+                              const int32_t* __restrict__ plane_off, int n_planes,
+                              const int32_t* __restrict__ out_off,
+                              const int32_t* __restrict__ hit_offsets, int32_t* lab,
+                              int32_t* __restrict__ labels) {
+  const int b = blockIdx.x;
+  const int32_t* po = plane_off + (int64_t)b * (n_planes + 1);
+  const int h0 = po[0], h1 = po[n_planes];
+  for (int i = h0 + threadIdx.x; i < h1; i += blockDim.x) lab[i] = i;
+  __syncthreads();
+  for (int p = 1; p < n_planes; ++p) {
+    const int j0 = po[p], j1 = po[p + 1];  // hits of plane p
+    const int e0 = out_off[po[p >= 2 ? p - 2 : 0]], e1 = out_off[po[p]];
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const int i = src[e], j = dst[e];
+      if (j >= j0 && j < j1 && i >= h0 && i < h1 && logits[e] > thr) atomicMin(&lab[j], lab[i]);
+    }
+    __syncthreads();
+  }
+  for (int p = n_planes - 2; p >= 0; --p) {
+    const int e0 = out_off[po[p]], e1 = out_off[po[p + 1]];
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const int i = src[e], j = dst[e];
+      if (i >= h0 && i < h1 && j >= h0 && j < h1 && logits[e] > thr) atomicMin(&lab[i], lab[j]);
+    }
+    __syncthreads();
+  }
+  const int base = hit_offsets[b];
+  for (int i = h0 + threadIdx.x; i < h1; i += blockDim.x) labels[i] = lab[i] - base;
 }
 
 __global__ void k_init(int32_t* __restrict__ parent, int64_t n) {
@@ -98,6 +139,16 @@ __global__ void k_count_tracks(const int32_t* __restrict__ labels, const int32_t
 }
 
 }  // namespace
+
+cudaError_t launch_plane_sweep(etx_ctx* ctx, const int32_t* src, const int32_t* dst,
+                               const float* logits, float thr, const int32_t* hit_offsets,
+                               int32_t n_events, int64_t n_hits, int32_t* labels, cudaStream_t s) {
+  if (n_events == 0 || n_hits == 0) return cudaSuccess;
+  launch(ctx, "cc_plane_sweep", k_plane_sweep, (unsigned)n_events, 256, 0, s, src, dst, logits, thr,
+         (const int32_t*)ctx->plane_off, ctx->cfg.n_planes, (const int32_t*)ctx->out_off,
+         hit_offsets, ctx->parent, labels);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_edges_to_tracks(etx_ctx* ctx, const int32_t* src, const int32_t* dst,
                                    const float* logits, float thr, const int32_t* n_edges_dev,

@@ -631,6 +631,31 @@ etx_status etx_edges_to_tracks(etx_ctx* ctx, const int32_t* src, const int32_t* 
   return ETX_OK;
 }
 
+etx_status etx_edges_to_tracks_sweep(etx_ctx* ctx, const int32_t* src, const int32_t* dst,
+                                     const float* logits, float threshold_logit,
+                                     const int32_t* edge_offsets, const int8_t* plane,
+                                     const int32_t* hit_offsets, int32_t n_events, int64_t n_hits,
+                                     int32_t* labels, void* stream) {
+  if (!ctx) return ETX_ERR_ARG;
+  if (n_events < 0 || n_events > ctx->cfg.max_events) return fail(ctx, ETX_ERR_CAPACITY, "n_events exceeds the context capacity");
+  if (n_hits < 0 || n_hits > ctx->cfg.max_hits) return fail(ctx, ETX_ERR_CAPACITY, "n_hits exceeds the context capacity");
+  if (!edge_offsets || !hit_offsets || !src || !dst || !logits) return fail(ctx, ETX_ERR_ARG, "NULL array");
+  if (n_hits > 0 && (!labels || !plane)) return fail(ctx, ETX_ERR_ARG, "NULL labels or plane");
+  if (threshold_logit != threshold_logit) return fail(ctx, ETX_ERR_ARG, "threshold is NaN");
+  if (n_events == 0 && n_hits > 0) return fail(ctx, ETX_ERR_ARG, "hits without events");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  launch(ctx, "clamp_edges", k_clamp_edges, 1, 1, 0, s, edge_offsets, n_events, ctx->cfg.max_edges,
+         ctx->n_edges, ctx->d_err);
+  cudaError_t e = launch_plane_bins(ctx, plane, hit_offsets, n_events, n_hits, s);
+  if (e == cudaSuccess) e = launch_out_offsets(ctx, n_hits, src, dst, ctx->n_edges, s);
+  if (e == cudaSuccess)
+    e = launch_plane_sweep(ctx, src, dst, logits, threshold_logit, hit_offsets, n_events, n_hits,
+                           labels, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "etx_edges_to_tracks_sweep launch");
+  return ETX_OK;
+}
+
 }  // extern "C"
 
 // ---- autotuner ---------------------------------------------------------------

@@ -195,7 +195,18 @@ cudaError_t launch_edge_update_tc(etx_ctx* ctx, int k, int64_t N, const int32_t*
 cudaError_t launch_classifier_tc(etx_ctx* ctx, int64_t N, const int32_t* n_edges_dev, float* logits,
                                  bool f8, cudaStream_t s);
 
+// graph.cu: hit checks and ctx->plane_off (first hit of each plane, per event)
+cudaError_t launch_plane_bins(etx_ctx* ctx, const int8_t* plane, const int32_t* hit_offsets,
+                              int32_t n_events, int64_t n_hits, cudaStream_t s);
+// gnn_f32.cu: ctx->out_off, the src-CSR of edges sorted by src (checks order and range)
+cudaError_t launch_out_offsets(etx_ctx* ctx, int64_t N, const int32_t* src, const int32_t* dst,
+                               const int32_t* n_edges_dev, cudaStream_t s);
+
 // cc.cu
+// the paper's plane-sweep labels (needs ctx->plane_off and ctx->out_off)
+cudaError_t launch_plane_sweep(etx_ctx* ctx, const int32_t* src, const int32_t* dst,
+                               const float* logits, float thr, const int32_t* hit_offsets,
+                               int32_t n_events, int64_t n_hits, int32_t* labels, cudaStream_t s);
 cudaError_t launch_edges_to_tracks(etx_ctx* ctx, const int32_t* src, const int32_t* dst,
                                    const float* logits, float thr, const int32_t* n_edges_dev,
                                    const int32_t* hit_offsets, int32_t n_events, int64_t n_hits,

@@ -386,6 +386,16 @@ cudaError_t launch_messages(etx_ctx* ctx, const float* e, float* m, int64_t N, c
   return cudaGetLastError();
 }
 
+cudaError_t launch_out_offsets(etx_ctx* ctx, int64_t N, const int32_t* src, const int32_t* dst,
+                               const int32_t* n_edges_dev, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(ctx->out_off, 0, (N + 1) * sizeof(int32_t), s);
+  if (e != cudaSuccess) return e;
+  const int ge = grid_for(ctx, (const void*)k_out_offsets, 256, 0, (ctx->cfg.max_edges + 256) / 256);
+  launch(ctx, "index_out_offsets", k_out_offsets, ge, 256, 0, s, src, dst, n_edges_dev, (int)N,
+         ctx->out_off, ctx->d_err);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_edge_index(etx_ctx* ctx, int64_t N, const int32_t* src, const int32_t* dst,
                               const int32_t* n_edges_dev, cudaStream_t s) {
   const int64_t Ecap = ctx->cfg.max_edges;

@@ -355,6 +355,19 @@ cudaError_t launch_build_graph(etx_ctx* ctx, const float* emb, const int8_t* pla
   return cudaGetLastError();
 }
 
+cudaError_t launch_plane_bins(etx_ctx* ctx, const int8_t* plane, const int32_t* hit_offsets,
+                              int32_t n_events, int64_t n_hits, cudaStream_t s) {
+  const int P = ctx->cfg.n_planes;
+  const int64_t nchk = (n_hits > n_events ? n_hits : n_events + 1);
+  launch(ctx, "graph_check_hits", k_check_hits, (unsigned)((nchk + 255) / 256), 256, 0, s, plane,
+         hit_offsets, n_events, n_hits, P, ctx->d_err);
+  const int64_t nb = (int64_t)n_events * (P + 1);
+  if (nb > 0)
+    launch(ctx, "graph_plane_bins", k_plane_bins, (unsigned)((nb + 255) / 256), 256, 0, s, plane,
+           hit_offsets, n_events, (int)n_hits, P, ctx->plane_off);
+  return cudaGetLastError();
+}
+
 cudaError_t knn_set_smem_attr() {
   const int smem = (int)(kStageFloats * sizeof(float) + kKnnThreads / 32 * kListCap * sizeof(uint64_t));
   const void* ks[] = {(const void*)k_knn<false, 0>, (const void*)k_knn<true, 0>,

@@ -31,7 +31,7 @@ EXPORTED = ["etx_ctx_create", "etx_ctx_destroy", "etx_last_error", "etx_weights_
             "etx_gnn_forward", "etx_gnn_param_count", "etx_gnn_backward",
             "etx_edges_to_tracks", "etx_edges_to_tracks_noalloc", "etx_launch_count",
             "etx_profile_enable", "etx_profile_read", "etx_weighted_bce", "etx_adam_step",
-            "etx_autotune", "etx_tuned", "etx_set_tuned"]
+            "etx_autotune", "etx_tuned", "etx_set_tuned", "etx_edges_to_tracks_sweep"]
 # knob names of the autotuner (etx_tuned)
 TUNE_KNOBS = ["knn_split"] + [f"tc_stages/{b}/{d}" for b in
                               ("edge_encoder", "node_update", "edge_update", "classifier")
@@ -90,6 +90,7 @@ def lib() -> ctypes.CDLL:
         "etx_autotune": (i32, [vp, vp, vp, vp, vp, vp, i32, i64, f32, i32, i32, vp, vp, vp, i64,
                                vp, vp, vp]),
         "etx_tuned": (i32, [vp, ctypes.c_char_p]),
+        "etx_edges_to_tracks_sweep": (i32, [vp, vp, vp, vp, f32, vp, vp, vp, i32, i64, vp, vp]),
         "etx_set_tuned": (i32, [vp, ctypes.c_char_p, i32]),
         "etx_launch_count": (i64, [vp]),
         "etx_profile_enable": (i32, [vp, i32]),
@@ -282,6 +283,26 @@ class Context:
                                           _ptr(dst), _ptr(edge_offsets), n_events, DTYPES[dtype],
                                           _ptr(logits), _stream(stream)))
         return logits
+
+    def edges_to_tracks_sweep(self, src, dst, logits, threshold_logit: float, edge_offsets,
+                              plane, hit_offsets, labels=None, stream=None):
+        """The paper's plane-sweep labels (Sec. 7.3; not exact components)."""
+        dev = self.device
+        _need(src, torch.int32, "src", dev)
+        _need(dst, torch.int32, "dst", dev)
+        _need(logits, torch.float32, "logits", dev)
+        _need(edge_offsets, torch.int32, "edge_offsets", dev)
+        _need(plane, torch.int8, "plane", dev)
+        _need(hit_offsets, torch.int32, "hit_offsets", dev)
+        n_hits, n_events = plane.shape[0], hit_offsets.shape[0] - 1
+        if labels is None:
+            labels = torch.empty(n_hits, dtype=torch.int32, device=dev)
+        _need(labels, torch.int32, "labels", dev)
+        self._check(lib().etx_edges_to_tracks_sweep(self._h, _ptr(src), _ptr(dst), _ptr(logits),
+                                                    float(threshold_logit), _ptr(edge_offsets),
+                                                    _ptr(plane), _ptr(hit_offsets), n_events,
+                                                    n_hits, _ptr(labels), _stream(stream)))
+        return labels
 
     def autotune(self, x, y, z, plane, hit_offsets, radius: float, k_max: int, emb, src, dst,
                  edge_offsets, logits, dtype: str = "bf16", stream=None):
