@@ -427,6 +427,26 @@ def run_ours(args):
         tf.dtype = args.dtype
         tf.ctx.sync()
 
+    # ---- the plane-ordered two-sweep labelling (Sec. 7.3) beside the exact
+    # components, on the edges and logits of the same step --------------------
+    labels, _ = step()
+    sweep_lab = torch.empty(N, dtype=torch.int32, device=dev)
+    sweep = lambda: tf.ctx.edges_to_tracks_sweep(tf.src, tf.dst, tf.logits, m.threshold_logit,
+                                                 tf.eoff, dp, do, labels=sweep_lab)
+    sweep()
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(args.steps):
+        sweep()
+    s1.record(stream)
+    torch.cuda.synchronize()
+    tf.ctx.sync()
+    exact_ms = sum(t for k, (t, _) in prof.items() if k.startswith("cc_")) / args.steps
+    plane_sweep = {"ms_per_step": max_over_ranks(s0.elapsed_time(s1), world, dev) / args.steps,
+                   "exact_components_ms_per_step": exact_ms,
+                   "hits_labelled_differently": float((sweep_lab != labels).float().mean().item())}
+
     train = None
     if not args.skip_train:
         train = train_step_report(args, local)
@@ -492,6 +512,7 @@ def run_ours(args):
            "latency_ms": {"p50": float(np.percentile(per_step, 50)),
                           "p99": float(np.percentile(per_step, 99)), "per_step": per_step},
            "per_dtype": per_dtype,
+           "plane_sweep": plane_sweep,
            "train64": train,
            "kernels": kernels}
     print(json.dumps(out), flush=True)
