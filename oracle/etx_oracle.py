@@ -22,6 +22,11 @@ blocking, fusion or reordering beyond what the definition states:
   gnn_backward          reverse-mode derivative of gnn_forward + loss, by hand
   connected_components  weakly connected components of the purified hit graph
                         (Sec. 5 overview, Sec. 7.3), by breadth-first search
+  plane_sweep_components  the paper's plane-ordered two-sweep labelling
+                        (Sec. 7.3), which is not exact
+  track_metrics         the counts behind the Table 1 metrics (Sec. 6):
+                        70% matching, efficiency, clone and fake rates, hit
+                        efficiency and purity
 
 Readings where the paper is silent (also listed in the design notes):
   * radius r is Euclidean: keep d2 < r*r (strict); the k_max cap is joint over
@@ -33,7 +38,9 @@ Readings where the paper is silent (also listed in the design notes):
   * node network input [h, m_out, m_in], edge network input [e, h_i, h_j]
     with the updated h, edge encoder input [h_i, h_j];
   * an edge is kept iff its logit > 0 (score > 0.5);
-  * a track label is the smallest event-local hit index of the component.
+  * a track label is the smallest event-local hit index of the component;
+  * a reconstructed track needs at least three hits, like a reconstructible
+    particle (Sec. 3).
 
 Parity of every function is pinned by the non-GPU tests (brute force,
 closed forms, invariants, torch float64 cross-checks and finite differences).
@@ -404,3 +411,77 @@ def plane_sweep_components(src, dst, mask, plane, hit_offsets, n_planes=26):
         lab = new
     event_of = np.searchsorted(hit_offsets, np.arange(N), side="right") - 1
     return (lab - hit_offsets[event_of]).astype(np.int32)
+
+
+# ----------------------------------------------------------------------------
+# track-finding performance on truth (Sec. 6, Table 1)
+# ----------------------------------------------------------------------------
+TRACK_METRIC_COUNTS = ("particles", "matched_particles", "candidates", "candidate_particles",
+                       "tracks", "unmatched_tracks")
+
+
+def track_metrics(labels, particle_id, hit_offsets, min_hits=3, match_num=7, match_den=10):
+    """Counts and sums behind the Table 1 metrics, event by event.
+
+    A track is a set of hits of one event sharing a label, kept if it has at
+    least ``min_hits`` hits; a particle counts (is reconstructible, Sec. 3) if
+    it has at least ``min_hits`` hits; noise hits have particle id -1.  A track
+    and a particle form a matching candidate when at least match_num/match_den
+    (70%) of the track's hits belong to the particle (Sec. 6), so a track has
+    at most one candidate particle.  Returns a dict of integer counts
+    (TRACK_METRIC_COUNTS: reconstructible particles, those with a candidate,
+    candidates, distinct particles among the candidates, tracks, tracks with
+    no candidate) and the FP64 sums over candidates of matched/particle hits
+    ("hit_eff_sum") and matched/track hits ("hit_purity_sum").  With the
+    paper's 3 hits and 70%, a matched track has at least 3 hits of its
+    particle, so every candidate particle is reconstructible."""
+    hit_offsets = np.asarray(hit_offsets, np.int64)
+    labels = np.asarray(labels, np.int64)
+    particle_id = np.asarray(particle_id, np.int64)
+    out = dict.fromkeys(TRACK_METRIC_COUNTS, 0)
+    out["hit_eff_sum"] = 0.0
+    out["hit_purity_sum"] = 0.0
+    for b in range(hit_offsets.shape[0] - 1):
+        lab = labels[hit_offsets[b]:hit_offsets[b + 1]].tolist()
+        pid = particle_id[hit_offsets[b]:hit_offsets[b + 1]].tolist()
+        particle_hits = {}
+        for p in pid:
+            if p >= 0:
+                particle_hits[p] = particle_hits.get(p, 0) + 1
+        reconstructible = {p for p, n in particle_hits.items() if n >= min_hits}
+        tracks = {}
+        for lb, p in zip(lab, pid):
+            tracks.setdefault(lb, []).append(p)
+        matched = set()
+        for members in tracks.values():
+            size = len(members)
+            if size < min_hits:
+                continue
+            out["tracks"] += 1
+            owner = None
+            for p in set(members):
+                n = members.count(p)
+                if p >= 0 and n * match_den >= match_num * size:
+                    owner, n_owned = p, n
+            if owner is None:
+                out["unmatched_tracks"] += 1
+                continue
+            out["candidates"] += 1
+            matched.add(owner)
+            out["hit_eff_sum"] += n_owned / particle_hits[owner]
+            out["hit_purity_sum"] += n_owned / size
+        out["particles"] += len(reconstructible)
+        out["matched_particles"] += len(matched & reconstructible)
+        out["candidate_particles"] += len(matched)
+    return out
+
+
+def track_metric_rates(m):
+    """The Table 1 ratios from ``track_metrics`` totals (NaN where a
+    denominator is zero)."""
+    div = lambda a, b: a / b if b else float("nan")
+    return {"efficiency": div(m["matched_particles"], m["particles"]),
+            "clone_rate": div(m["candidates"] - m["candidate_particles"], m["candidates"]),
+            "fake_rate": div(m["unmatched_tracks"], m["tracks"]),
+            "hit_efficiency": div(m["hit_eff_sum"], m["candidates"]),
+            "hit_purity": div(m["hit_purity_sum"], m["candidates"])}

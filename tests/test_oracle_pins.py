@@ -598,3 +598,138 @@ def test_quant_weight_e4m3_scale():
     # the largest magnitude maps to 448 s, i.e. back to itself up to the rounding of s
     np.testing.assert_allclose(q[0, 1], -2.0, rtol=1e-6)
     assert np.all(np.abs(q - W) <= 2.0 ** -4 * np.abs(W) + 1e-12)
+
+
+# ---------------------------------------------------------------------------
+# track-finding metrics (Sec. 6, Table 1)
+# ---------------------------------------------------------------------------
+def test_track_metrics_worked_by_hand():
+    case = json.loads((GOLDEN / "track_metrics.json").read_text())["cases"][0]
+    m = O.track_metrics(case["labels"], case["particle_id"], case["hit_offsets"])
+    exp = case["expected"]
+    for k in O.TRACK_METRIC_COUNTS:
+        assert m[k] == exp[k], k
+    assert m["hit_eff_sum"] == pytest.approx(exp["hit_eff_sum"], abs=1e-15)
+    assert m["hit_purity_sum"] == pytest.approx(exp["hit_purity_sum"], abs=1e-15)
+    r = O.track_metric_rates(m)
+    assert r["efficiency"] == exp["efficiency"]
+    assert r["clone_rate"] == exp["clone_rate"]
+    assert r["fake_rate"] == exp["fake_rate"][0] / exp["fake_rate"][1]
+    assert r["hit_efficiency"] == exp["hit_efficiency"]
+    assert r["hit_purity"] == exp["hit_purity"]
+
+
+def truth_labels(batch):
+    """Every particle's hits form one track (label = its first hit), noise alone."""
+    lab = np.empty(batch.n_hits, np.int64)
+    for b in range(batch.n_events):
+        lo, hi = int(batch.hit_offsets[b]), int(batch.hit_offsets[b + 1])
+        first = {}
+        for i in range(lo, hi):
+            p = int(batch.particle_id[i])
+            lab[i] = i - lo if p < 0 else first.setdefault(p, i - lo)
+    return lab
+
+
+def test_track_metrics_of_the_truth_partition_are_perfect():
+    batch = tiny_batch(4)
+    m = O.track_metrics(truth_labels(batch), batch.particle_id, batch.hit_offsets)
+    n_rec = sum(int((np.bincount(batch.event(b).particle_id[batch.event(b).particle_id >= 0]) >= 3).sum())
+                for b in range(batch.n_events))
+    assert n_rec > 50
+    assert m["particles"] == m["matched_particles"] == m["candidates"] == m["tracks"] == n_rec
+    assert m["candidate_particles"] == n_rec and m["unmatched_tracks"] == 0
+    assert m["hit_eff_sum"] == m["hit_purity_sum"] == n_rec
+    r = O.track_metric_rates(m)
+    assert (r["efficiency"], r["clone_rate"], r["fake_rate"]) == (1.0, 0.0, 0.0)
+
+
+def test_track_metrics_special_cases():
+    # one event, every hit one label: one track, matched only if a particle holds 70%
+    pid = np.array([0] * 7 + [1] * 3)
+    m = O.track_metrics(np.zeros(10), pid, [0, 10])
+    assert (m["tracks"], m["candidates"], m["particles"], m["matched_particles"]) == (1, 1, 2, 1)
+    assert m["hit_eff_sum"] == 1.0 and m["hit_purity_sum"] == 0.7
+    m = O.track_metrics(np.zeros(10), np.array([0] * 6 + [1] * 4), [0, 10])
+    assert (m["tracks"], m["unmatched_tracks"], m["candidates"]) == (1, 1, 0)
+    # every hit alone: no track, nothing matched
+    m = O.track_metrics(np.arange(10), pid, [0, 10])
+    assert (m["tracks"], m["candidates"], m["particles"], m["matched_particles"]) == (0, 0, 2, 0)
+    # all noise: no particle; empty batch
+    m = O.track_metrics(np.zeros(5), -np.ones(5), [0, 5])
+    assert (m["particles"], m["tracks"], m["unmatched_tracks"]) == (0, 1, 1)
+    m = O.track_metrics(np.zeros(0), np.zeros(0), [0, 0, 0])
+    assert all(m[k] == 0 for k in O.TRACK_METRIC_COUNTS)
+    assert math.isnan(O.track_metric_rates(m)["efficiency"])
+
+
+def test_track_metrics_invariant_under_relabelling():
+    rng = np.random.default_rng(11)
+    batch = tiny_batch(3, seed=5)
+    lab = truth_labels(batch)
+    # split some particles in two and move hits between tracks, so that
+    # clones and unmatched tracks occur
+    for b in range(batch.n_events):
+        lo, hi = int(batch.hit_offsets[b]), int(batch.hit_offsets[b + 1])
+        n, seg, pid = hi - lo, lab[lo:hi], batch.particle_id[lo:hi]
+        for p in np.unique(pid[pid >= 0])[::3]:
+            hits = np.nonzero(pid == p)[0]
+            seg[hits[len(hits) // 2:]] = hits[len(hits) // 2]
+        pick = np.nonzero(rng.uniform(size=n) < 0.2)[0]
+        seg[pick] = seg[rng.integers(0, n, size=pick.size)]
+    m = O.track_metrics(lab, batch.particle_id, batch.hit_offsets)
+    assert m["unmatched_tracks"] > 0 and m["candidates"] > m["candidate_particles"] > 0
+    lab2, pid2 = lab.copy(), batch.particle_id.astype(np.int64).copy()
+    for b in range(batch.n_events):
+        lo, hi = int(batch.hit_offsets[b]), int(batch.hit_offsets[b + 1])
+        perm = rng.permutation(hi - lo)
+        lab2[lo:hi] = perm[lab[lo:hi]]                     # bijection of label values
+        sig = pid2[lo:hi] >= 0
+        pperm = rng.permutation(int(pid2[lo:hi][sig].max()) + 1)
+        pid2[lo:hi][sig] = pperm[pid2[lo:hi][sig]]         # bijection of particle ids
+        order = rng.permutation(hi - lo) + lo              # hit order inside the event
+        lab2[lo:hi], pid2[lo:hi] = lab2[order].copy(), pid2[order].copy()
+    m2 = O.track_metrics(lab2, pid2, batch.hit_offsets)
+    for k in O.TRACK_METRIC_COUNTS:
+        assert m2[k] == m[k], k
+    assert m2["hit_eff_sum"] == pytest.approx(m["hit_eff_sum"], rel=1e-14)
+    assert m2["hit_purity_sum"] == pytest.approx(m["hit_purity_sum"], rel=1e-14)
+
+
+def test_track_metrics_against_a_contingency_table():
+    """The same quantities from a (track, particle) count matrix built with
+    scipy.sparse, on random labellings of a synthetic batch."""
+    sp = pytest.importorskip("scipy.sparse")
+    rng = np.random.default_rng(2)
+    batch = tiny_batch(3, seed=9)
+    for trial in range(4):
+        lab = truth_labels(batch)
+        pick = rng.uniform(size=lab.size) < 0.1 * (trial + 1)
+        for b in range(batch.n_events):
+            lo, hi = int(batch.hit_offsets[b]), int(batch.hit_offsets[b + 1])
+            sel = pick[lo:hi]
+            lab[lo:hi][sel] = rng.integers(0, max(hi - lo, 1), size=int(sel.sum()))
+        tot = dict.fromkeys(O.TRACK_METRIC_COUNTS, 0)
+        tot["hit_eff_sum"] = tot["hit_purity_sum"] = 0.0
+        for b in range(batch.n_events):
+            lo, hi = int(batch.hit_offsets[b]), int(batch.hit_offsets[b + 1])
+            n, l, p = hi - lo, lab[lo:hi], batch.particle_id[lo:hi].astype(np.int64)
+            C = sp.coo_matrix((np.ones(n), (l, p + 1)), shape=(n, n + 1)).toarray()  # col 0 = noise
+            size, phits = C.sum(1), C.sum(0)
+            is_track = size >= 3
+            cand = is_track[:, None] & (10 * C >= 7 * size[:, None])
+            cand[:, 0] = False
+            tr, pa = np.nonzero(cand)
+            tot["particles"] += int((phits[1:] >= 3).sum())
+            tot["matched_particles"] += int(np.unique(pa[phits[pa] >= 3]).size)
+            tot["candidates"] += tr.size
+            tot["candidate_particles"] += int(np.unique(pa).size)
+            tot["tracks"] += int(is_track.sum())
+            tot["unmatched_tracks"] += int(is_track.sum()) - tr.size
+            tot["hit_eff_sum"] += float((C[tr, pa] / phits[pa]).sum())
+            tot["hit_purity_sum"] += float((C[tr, pa] / size[tr]).sum())
+        m = O.track_metrics(lab, batch.particle_id, batch.hit_offsets)
+        for k in O.TRACK_METRIC_COUNTS:
+            assert m[k] == tot[k], (trial, k)
+        assert m["hit_eff_sum"] == pytest.approx(tot["hit_eff_sum"], rel=1e-13)
+        assert m["hit_purity_sum"] == pytest.approx(tot["hit_purity_sum"], rel=1e-13)
