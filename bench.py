@@ -296,7 +296,8 @@ def run_ours(args):
 
     from paper_2407_12119_gb300 import build as build_mod
     from paper_2407_12119_gb300.pipeline import TrackFinder
-    from velo_synth import WORKLOADS, pack_blob
+    from velo_synth import (WORKLOADS, compact_particle_ids, global_particle_ids, pack_blob,
+                            truth_edge_labels)
 
     rank, world, local = dist_env()
     if world > 1:
@@ -393,6 +394,17 @@ def run_ours(args):
     d2h = N * 4 + B * 4
 
     # ---- every arithmetic type: throughput and agreement with the FP32 path --
+    # Table 1 metrics (Sec. 6) of a labelling against the synthetic truth, on the device
+    pid_d = torch.from_numpy(compact_particle_ids(batch)).to(dev)
+    metric_ws = torch.empty(max(tf.ctx.track_metrics_workspace(B, N), 8), dtype=torch.uint8,
+                            device=dev)
+
+    def physics(labels):
+        _, vals = tf.ctx.track_metrics(labels, pid_d, do, workspace=metric_ws)
+        v = vals.cpu().numpy()
+        return {k: float(x) for k, x in zip(("efficiency", "clone_rate", "fake_rate",
+                                              "hit_efficiency", "hit_purity"), v[2:])}
+
     per_dtype = {}
     if not args.skip_dtypes:
         ref = None
@@ -401,6 +413,7 @@ def run_ours(args):
             labels, _ = step()
             torch.cuda.synchronize()
             logits, lab = tf.logits[:E].clone(), labels.clone()
+            phys = physics(lab)
             if dt == args.dtype:
                 dt_ms = eager_ms_step
             else:
@@ -412,7 +425,8 @@ def run_ours(args):
                 d1.record(stream)
                 torch.cuda.synchronize()
                 dt_ms = max_over_ranks(d0.elapsed_time(d1), world, dev) / args.steps
-            rec = {"events_per_s": world * B / (dt_ms / 1e3), "ms_per_step": dt_ms}
+            rec = {"events_per_s": world * B / (dt_ms / 1e3), "ms_per_step": dt_ms,
+                   "track_metrics": phys}
             if ref is None:
                 ref = (logits, lab)
             else:
@@ -445,7 +459,26 @@ def run_ours(args):
     exact_ms = sum(t for k, (t, _) in prof.items() if k.startswith("cc_")) / args.steps
     plane_sweep = {"ms_per_step": max_over_ranks(s0.elapsed_time(s1), world, dev) / args.steps,
                    "exact_components_ms_per_step": exact_ms,
-                   "hits_labelled_differently": float((sweep_lab != labels).float().mean().item())}
+                   "hits_labelled_differently": float((sweep_lab != labels).float().mean().item()),
+                   "track_metrics": physics(sweep_lab),
+                   "track_metrics_exact": physics(labels)}
+    # graph-stage ceiling: exact components of the built graph's genuine edges
+    src_h, dst_h = tf.src[:E].cpu().numpy(), tf.dst[:E].cpu().numpy()
+    genuine = truth_edge_labels(global_particle_ids(batch), batch.plane, src_h, dst_h)
+    truth_logits = torch.from_numpy(np.where(genuine > 0, 1.0, -1.0).astype(np.float32)).to(dev)
+    truth_lab, _ = tf.ctx.edges_to_tracks(tf.src, tf.dst, truth_logits, 0.0, tf.eoff, do)
+    m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    m0.record(stream)
+    for _ in range(args.steps):
+        tf.ctx.track_metrics(truth_lab, pid_d, do, workspace=metric_ws)
+    m1.record(stream)
+    torch.cuda.synchronize()
+    track_metrics = {"ms": m0.elapsed_time(m1) / args.steps,
+                     "graph_ceiling": physics(truth_lab),
+                     "genuine_edges_in_graph": float(genuine.mean()),
+                     "note": "random-init weights: the classifier's metrics are not physics "
+                             "numbers; the graph ceiling keeps only the built graph's genuine edges"}
+    tf.ctx.sync()
 
     train = None
     if not args.skip_train:
@@ -513,6 +546,7 @@ def run_ours(args):
                           "p99": float(np.percentile(per_step, 99)), "per_step": per_step},
            "per_dtype": per_dtype,
            "plane_sweep": plane_sweep,
+           "track_metrics": track_metrics,
            "train64": train,
            "kernels": kernels}
     print(json.dumps(out), flush=True)

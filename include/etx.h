@@ -255,6 +255,45 @@ etx_status etx_edges_to_tracks_sweep(etx_ctx* ctx, const int32_t* src, const int
                                      int32_t* labels, void* stream);
 
 /*
+ * Track-finding performance against truth (Sec. 6, Table 1), for evaluating
+ * labels on synthetic or simulated events.  A track is a set of hits of one
+ * event that share a label; it counts when it has at least min_hits hits.  A
+ * particle counts (is reconstructible, Sec. 3) when it has at least min_hits
+ * hits.  A track and a particle form a matching candidate when at least
+ * match_num / match_den of the track's hits belong to the particle (the
+ * paper: 3 hits, 7/10).
+ *
+ * labels       int32 [n_hits], event-local, each in [0, hits of its event)
+ *              (the output of etx_edges_to_tracks or _sweep)
+ * particle_id  int32 [n_hits], event-local particle index in [0, hits of its
+ *              event), -1 for noise
+ * hit_offsets  int32 [n_events + 1], as everywhere
+ * workspace    device scratch of at least etx_track_metrics_workspace()
+ *              bytes, 8-byte aligned, owned by the caller
+ * counts       int64 [6] (device) receives: reconstructible particles,
+ *              those with a candidate, candidates, distinct particles among
+ *              the candidates, tracks, tracks without a candidate
+ * values       double [7] (device) receives: sum over candidates of matched /
+ *              particle hits, sum over candidates of matched / track hits,
+ *              efficiency, clone rate, fake rate, hit efficiency, hit purity
+ *              (the last five are NaN where their denominator is zero)
+ *
+ * Counts are exact; the FP64 sums are formed in a fixed order (the same
+ * inputs give the same bits).  ETX_ERR_ARG for NULL arrays, min_hits < 1, a
+ * match fraction outside (1/2, 1] (at most one particle per track) or an
+ * unaligned workspace; ETX_ERR_CAPACITY for a small workspace.  Labels or
+ * particle ids out of range are skipped and reported by etx_ctx_sync
+ * (ETX_ERR_UNSORTED, "an index was out of range").  Asynchronous on `stream`; writes nothing but the workspace
+ * and the two outputs.
+ */
+size_t etx_track_metrics_workspace(int32_t n_events, int64_t n_hits);
+etx_status etx_track_metrics(etx_ctx* ctx, const int32_t* labels, const int32_t* particle_id,
+                             const int32_t* hit_offsets, int32_t n_events, int64_t n_hits,
+                             int32_t min_hits, int32_t match_num, int32_t match_den,
+                             void* workspace, size_t workspace_bytes, int64_t* counts,
+                             double* values, void* stream);
+
+/*
  * Autotuner (no counterpart in the paper: it picks launch configurations, not
  * results).  Runs the embedding, the graph and (for ETX_BF16 / ETX_FP8E4M3)
  * the interaction network on the given batch, timing with CUDA events each

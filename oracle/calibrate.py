@@ -27,7 +27,10 @@ from . import etx_oracle as O
 EDGES_PER_HIT = 11.5
 
 
-def calibrate(name: str, n_graph_events: int = 50, n_gnn_events: int = 3) -> dict:
+def calibrate(name: str, n_graph_events: int = 50, n_gnn_events: int = 3,
+              keep_radius: bool = False) -> dict:
+    """``keep_radius``: keep the workload's radius (a workload sharing another
+    one's embedding) and calibrate the logit cut only."""
     wl = WORKLOADS[name]
     cfg = wl.model
     W = wl.weights()
@@ -35,14 +38,14 @@ def calibrate(name: str, n_graph_events: int = 50, n_gnn_events: int = 3) -> dic
     b = make_batch(wl.recipe, n_graph_events, CALIB_SEED)
     emb = O.embed(W, depth, b.x, b.y, b.z)
     lo, hi = 0.05, 8.0
-    for _ in range(30):
+    for _ in range(0 if keep_radius else 30):
         r = 0.5 * (lo + hi)
         _, _, eo = O.build_graph(emb, b.plane, b.hit_offsets, r, cfg.k_max)
         if eo[-1] / b.n_hits < EDGES_PER_HIT:
             lo = r
         else:
             hi = r
-    radius = float(f"{0.5 * (lo + hi):.3g}")
+    radius = cfg.radius if keep_radius else float(f"{0.5 * (lo + hi):.3g}")
     _, _, eo = O.build_graph(emb, b.plane, b.hit_offsets, radius, cfg.k_max)
     gb = make_batch(wl.recipe, n_gnn_events, CALIB_SEED)
     gemb = O.embed(W, depth, gb.x, gb.y, gb.z)
@@ -59,5 +62,8 @@ def calibrate(name: str, n_graph_events: int = 50, n_gnn_events: int = 3) -> dic
 
 
 if __name__ == "__main__":
-    names = sys.argv[1:] or ["plain", "batch500"]
-    print(json.dumps({n: calibrate(n) for n in names}, indent=1))
+    args = sys.argv[1:]
+    keep = "--keep-radius" in args
+    names = [a for a in args if not a.startswith("--")] or ["plain", "batch500"]
+    print(json.dumps({n: calibrate(n, n_graph_events=5 if keep else 50, keep_radius=keep)
+                      for n in names}, indent=1))

@@ -656,6 +656,36 @@ etx_status etx_edges_to_tracks_sweep(etx_ctx* ctx, const int32_t* src, const int
   return ETX_OK;
 }
 
+size_t etx_track_metrics_workspace(int32_t n_events, int64_t n_hits) {
+  if (n_events < 0 || n_hits < 0) return 0;
+  return track_metrics_workspace(n_events, n_hits);
+}
+
+etx_status etx_track_metrics(etx_ctx* ctx, const int32_t* labels, const int32_t* particle_id,
+                             const int32_t* hit_offsets, int32_t n_events, int64_t n_hits,
+                             int32_t min_hits, int32_t match_num, int32_t match_den,
+                             void* workspace, size_t workspace_bytes, int64_t* counts,
+                             double* values, void* stream) {
+  if (!ctx) return ETX_ERR_ARG;
+  if (n_events < 0 || n_hits < 0 || n_hits > INT32_MAX) return fail(ctx, ETX_ERR_ARG, "bad n_events or n_hits");
+  if (n_events == 0 && n_hits > 0) return fail(ctx, ETX_ERR_ARG, "hits without events");
+  if (!counts || !values || (n_events > 0 && !hit_offsets)) return fail(ctx, ETX_ERR_ARG, "NULL array");
+  if (n_hits > 0 && (!labels || !particle_id)) return fail(ctx, ETX_ERR_ARG, "NULL labels or particle_id");
+  if (min_hits < 1) return fail(ctx, ETX_ERR_ARG, "min_hits must be at least 1");
+  if (match_num <= 0 || match_num > match_den || 2 * (int64_t)match_num <= match_den)
+    return fail(ctx, ETX_ERR_ARG, "match fraction must lie in (1/2, 1]");
+  if (workspace_bytes < track_metrics_workspace(n_events, n_hits))
+    return fail(ctx, ETX_ERR_CAPACITY, "workspace smaller than etx_track_metrics_workspace()");
+  if (n_events > 0 && (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 7)))
+    return fail(ctx, ETX_ERR_ARG, "workspace NULL or not 8-byte aligned");
+  cudaSetDevice(ctx->device);
+  cudaError_t e = launch_track_metrics(ctx, labels, particle_id, hit_offsets, n_events, n_hits,
+                                       min_hits, match_num, match_den, workspace, counts, values,
+                                       (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "etx_track_metrics launch");
+  return ETX_OK;
+}
+
 }  // extern "C"
 
 // ---- autotuner ---------------------------------------------------------------

@@ -202,6 +202,13 @@ cudaError_t launch_plane_bins(etx_ctx* ctx, const int8_t* plane, const int32_t* 
 cudaError_t launch_out_offsets(etx_ctx* ctx, int64_t N, const int32_t* src, const int32_t* dst,
                                const int32_t* n_edges_dev, cudaStream_t s);
 
+// metrics.cu: Table 1 counts; workspace = per-event tallies then six int32 arrays of n_hits
+size_t track_metrics_workspace(int32_t n_events, int64_t n_hits);
+cudaError_t launch_track_metrics(etx_ctx* ctx, const int32_t* labels, const int32_t* particle_id,
+                                 const int32_t* hit_offsets, int32_t n_events, int64_t n_hits,
+                                 int32_t min_hits, int32_t num, int32_t den, void* workspace,
+                                 int64_t* counts, double* values, cudaStream_t s);
+
 // cc.cu
 // the paper's plane-sweep labels (needs ctx->plane_off and ctx->out_off)
 cudaError_t launch_plane_sweep(etx_ctx* ctx, const int32_t* src, const int32_t* dst,

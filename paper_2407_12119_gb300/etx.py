@@ -31,7 +31,13 @@ EXPORTED = ["etx_ctx_create", "etx_ctx_destroy", "etx_last_error", "etx_weights_
             "etx_gnn_forward", "etx_gnn_param_count", "etx_gnn_backward",
             "etx_edges_to_tracks", "etx_edges_to_tracks_noalloc", "etx_launch_count",
             "etx_profile_enable", "etx_profile_read", "etx_weighted_bce", "etx_adam_step",
-            "etx_autotune", "etx_tuned", "etx_set_tuned", "etx_edges_to_tracks_sweep"]
+            "etx_autotune", "etx_tuned", "etx_set_tuned", "etx_edges_to_tracks_sweep",
+            "etx_track_metrics_workspace", "etx_track_metrics"]
+# etx_track_metrics outputs
+TRACK_COUNTS = ["particles", "matched_particles", "candidates", "candidate_particles", "tracks",
+                "unmatched_tracks"]
+TRACK_VALUES = ["hit_eff_sum", "hit_purity_sum", "efficiency", "clone_rate", "fake_rate",
+                "hit_efficiency", "hit_purity"]
 # knob names of the autotuner (etx_tuned)
 TUNE_KNOBS = ["knn_split"] + [f"tc_stages/{b}/{d}" for b in
                               ("edge_encoder", "node_update", "edge_update", "classifier")
@@ -92,6 +98,9 @@ def lib() -> ctypes.CDLL:
         "etx_tuned": (i32, [vp, ctypes.c_char_p]),
         "etx_edges_to_tracks_sweep": (i32, [vp, vp, vp, vp, f32, vp, vp, vp, i32, i64, vp, vp]),
         "etx_set_tuned": (i32, [vp, ctypes.c_char_p, i32]),
+        "etx_track_metrics_workspace": (ctypes.c_size_t, [i32, i64]),
+        "etx_track_metrics": (i32, [vp, vp, vp, vp, i32, i64, i32, i32, i32, vp, ctypes.c_size_t,
+                                    vp, vp, vp]),
         "etx_launch_count": (i64, [vp]),
         "etx_profile_enable": (i32, [vp, i32]),
         "etx_profile_read": (i32, [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
@@ -303,6 +312,36 @@ class Context:
                                                     _ptr(plane), _ptr(hit_offsets), n_events,
                                                     n_hits, _ptr(labels), _stream(stream)))
         return labels
+
+    @staticmethod
+    def track_metrics_workspace(n_events: int, n_hits: int) -> int:
+        """Bytes of device scratch that track_metrics needs."""
+        return int(lib().etx_track_metrics_workspace(int(n_events), int(n_hits)))
+
+    def track_metrics(self, labels, particle_id, hit_offsets, min_hits: int = 3,
+                      match=(7, 10), workspace=None, stream=None):
+        """Table 1 counts and ratios (Sec. 6) computed on the device; returns
+        (counts int64[6], values float64[7]) device tensors ordered as
+        TRACK_COUNTS and TRACK_VALUES."""
+        dev = self.device
+        _need(labels, torch.int32, "labels", dev)
+        _need(particle_id, torch.int32, "particle_id", dev)
+        _need(hit_offsets, torch.int32, "hit_offsets", dev)
+        n_hits, n_events = labels.shape[0], hit_offsets.shape[0] - 1
+        if particle_id.shape[0] != n_hits:
+            raise ValueError("labels and particle_id differ in length")
+        need = lib().etx_track_metrics_workspace(n_events, n_hits)
+        if workspace is None:
+            workspace = torch.empty(max(need, 8), dtype=torch.uint8, device=dev)
+        _need(workspace, torch.uint8, "workspace", dev)
+        counts = torch.empty(6, dtype=torch.int64, device=dev)
+        values = torch.empty(7, dtype=torch.float64, device=dev)
+        self._check(lib().etx_track_metrics(self._h, _ptr(labels), _ptr(particle_id),
+                                            _ptr(hit_offsets), n_events, n_hits, int(min_hits),
+                                            int(match[0]), int(match[1]), _ptr(workspace),
+                                            workspace.numel(), _ptr(counts), _ptr(values),
+                                            _stream(stream)))
+        return counts, values
 
     def autotune(self, x, y, z, plane, hit_offsets, radius: float, k_max: int, emb, src, dst,
                  edge_offsets, logits, dtype: str = "bf16", stream=None):

@@ -175,3 +175,16 @@ def global_particle_ids(batch: Batch) -> np.ndarray:
             seg[m] += base
             base += mx
     return out
+
+
+def compact_particle_ids(batch: Batch) -> np.ndarray:
+    """Event-local particle ids renumbered 0..P-1 in ascending order of the
+    original id (noise stays -1), so every id is below the event's hit count."""
+    out = np.full(batch.n_hits, -1, np.int32)
+    for b in range(batch.n_events):
+        lo, hi = int(batch.hit_offsets[b]), int(batch.hit_offsets[b + 1])
+        seg = batch.particle_id[lo:hi]
+        m = seg >= 0
+        if m.any():
+            out[lo:hi][m] = np.unique(seg[m], return_inverse=True)[1]
+    return out

@@ -12,7 +12,8 @@ Radii and logit cuts: the workload descriptions give radii 0.05 and 0.1,
 meant for trained embeddings; with random weights they yield no edges.  The
 values used here were produced by ``python -m oracle.calibrate`` (11.5
 edges per hit on the calibration events; logit cut keeping the genuine-edge
-fraction) and are recorded in oracle/calibration.json.  ``LITERAL_RADIUS``
+fraction) and are recorded in oracle/calibration.json; pileup4x keeps the
+batch500 radius (same embedding) with its own cut (its network has 8 steps).  ``LITERAL_RADIUS``
 keeps the described values for the degenerate-case tests.
 """
 from __future__ import annotations
@@ -63,5 +64,6 @@ WORKLOADS = {
     "train64": Workload("train64", PLAIN_RECIPE, 64, 5000,
                         ModelConfig(emb_widths=(3, 32, 32, 4), hidden=128, n_iters=6,
                                     radius=1.5, k_max=16, threshold_logit=-0.717108)),
-    "pileup4x": Workload("pileup4x", PILEUP_RECIPE, 1000, 9000, replace(BIG_MODEL, n_iters=8)),
+    "pileup4x": Workload("pileup4x", PILEUP_RECIPE, 1000, 9000,
+                         replace(BIG_MODEL, n_iters=8, threshold_logit=0.422708)),
 }
