@@ -27,6 +27,11 @@ blocking, fusion or reordering beyond what the definition states:
   track_metrics         the counts behind the Table 1 metrics (Sec. 6):
                         70% matching, efficiency, clone and fake rates, hit
                         efficiency and purity
+  embedding_pairs       the embedding's training set (Sec. 5.1): hard
+                        negatives from the graph rule, one random pair per
+                        query, the genuine edges
+  hinge_embedding_loss  Eq. 2-3 and its gradient with respect to the embedding
+  embed_backward        reverse pass of the embedding MLP
 
 Readings where the paper is silent (also listed in the design notes):
   * radius r is Euclidean: keep d2 < r*r (strict); the k_max cap is joint over
@@ -485,3 +490,128 @@ def track_metric_rates(m):
             "fake_rate": div(m["unmatched_tracks"], m["tracks"]),
             "hit_efficiency": div(m["hit_eff_sum"], m["candidates"]),
             "hit_purity": div(m["hit_purity_sum"], m["candidates"])}
+
+
+# ----------------------------------------------------------------------------
+# embedding training (Sec. 5.1, Eq. 2-3)
+# ----------------------------------------------------------------------------
+def embedding_queries(particle_id, hit_offsets, min_hits=3):
+    """Query nodes (Sec. 5.1): hits of particles with at least ``min_hits``
+    hits in their event (reconstructible, Sec. 3).  Noise (-1) never."""
+    particle_id = np.asarray(particle_id, np.int64)
+    hit_offsets = np.asarray(hit_offsets, np.int64)
+    q = np.zeros(particle_id.shape[0], bool)
+    for b in range(hit_offsets.shape[0] - 1):
+        lo, hi = int(hit_offsets[b]), int(hit_offsets[b + 1])
+        pid = particle_id[lo:hi]
+        for p in set(pid.tolist()) - {-1}:
+            members = np.nonzero(pid == p)[0]
+            if members.size >= min_hits:
+                q[lo + members] = True
+    return q
+
+
+def next_hit_of_particle(particle_id, hit_offsets):
+    """For every hit, the hit of the same particle that follows it in plane
+    order (hits are plane-sorted within an event, at most one hit per
+    particle and plane), or -1."""
+    particle_id = np.asarray(particle_id, np.int64)
+    hit_offsets = np.asarray(hit_offsets, np.int64)
+    nxt = np.full(particle_id.shape[0], -1, np.int64)
+    for b in range(hit_offsets.shape[0] - 1):
+        lo, hi = int(hit_offsets[b]), int(hit_offsets[b + 1])
+        last = {}
+        for i in range(hi - 1, lo - 1, -1):
+            p = int(particle_id[i])
+            if p >= 0:
+                nxt[i] = last.get(p, -1)
+                last[p] = i
+    return nxt
+
+
+def embedding_pairs(emb, plane, particle_id, hit_offsets, radius, k_max, rand, min_hits=3,
+                    precision="fp32"):
+    """Training set T of Sec. 5.1 for a batch whose noise hits were removed.
+
+    From every query q (``embedding_queries``) on plane p, to hits a on planes
+    p+1 and p+2 of its event:
+      * hard negatives: the pairs the graph rule itself produces
+        (``build_graph`` with the training radius and k_max);
+      * one random pair: the (rand[q] mod c)-th hit, in index order, of the c
+        hits on planes p+1 and p+2 (none when c = 0); the random numbers are
+        inputs;
+      * the genuine edge: q -> the next hit of q's particle, when it lies on
+        p+1 or p+2.
+    T is the union as a set.  A pair is genuine iff a is the next hit of q's
+    particle (a genuine edge: successive hits of one particle).  Returns
+    (q int64 [T], a int64 [T], genuine bool [T]) sorted by (q, a)."""
+    plane = np.asarray(plane, np.int64)
+    rand = np.asarray(rand, np.uint64)
+    hit_offsets = np.asarray(hit_offsets, np.int64)
+    is_q = embedding_queries(particle_id, hit_offsets, min_hits)
+    nxt = next_hit_of_particle(particle_id, hit_offsets)
+    s, d, _ = build_graph(emb, plane, hit_offsets, radius, k_max, precision=precision)
+    pairs = {(int(i), int(j)) for i, j in zip(s.tolist(), d.tolist()) if is_q[i]}
+    for b in range(hit_offsets.shape[0] - 1):
+        lo, hi = int(hit_offsets[b]), int(hit_offsets[b + 1])
+        for q in range(lo, hi):
+            if not is_q[q]:
+                continue
+            p = plane[q]
+            cand = [j for j in range(lo, hi) if plane[j] in (p + 1, p + 2)]
+            if cand:
+                pairs.add((q, cand[int(rand[q] % np.uint64(len(cand)))]))
+            if nxt[q] >= 0 and plane[nxt[q]] - p <= 2:
+                pairs.add((q, int(nxt[q])))
+    out = sorted(pairs)
+    q = np.array([x for x, _ in out], np.int64)
+    a = np.array([y for _, y in out], np.int64)
+    return q, a, (nxt[q] == a) if out else np.zeros(0, bool)
+
+
+def hinge_embedding_loss(emb, q, a, genuine, margin=1.0, w_genuine=2.0):
+    """Eq. 2-3: L = L_fake + w_genuine * L_genuine with L_genuine the mean of
+    d2(q, a) over genuine pairs and L_fake the mean of max(0, margin - d2)
+    over fake pairs (an empty set contributes 0; at d2 = margin the hinge
+    is inactive).  Returns (L, L_genuine, L_fake, dL/d emb [N, D])."""
+    emb = np.asarray(emb, np.float64)
+    q = np.asarray(q, np.int64)
+    a = np.asarray(a, np.int64)
+    g = np.asarray(genuine, bool)
+    diff = emb[q] - emb[a]
+    d2 = (diff * diff).sum(1)
+    n_g, n_f = int(g.sum()), int((~g).sum())
+    L_g = d2[g].mean() if n_g else 0.0
+    hinge = np.maximum(0.0, margin - d2[~g])
+    L_f = hinge.mean() if n_f else 0.0
+    # dL/d d2 per pair
+    coef = np.zeros(q.shape[0])
+    if n_g:
+        coef[g] = w_genuine / n_g
+    if n_f:
+        coef[~g] = np.where(d2[~g] < margin, -1.0 / n_f, 0.0)
+    grad = np.zeros_like(emb)
+    contrib = 2.0 * coef[:, None] * diff
+    np.add.at(grad, q, contrib)
+    np.add.at(grad, a, -contrib)
+    return L_f + w_genuine * L_g, L_g, L_f, grad
+
+
+def embed_backward(weights, n_layers, x, y, z, d_emb):
+    """Reverse pass of ``embed`` for dL/d emb = d_emb: returns
+    {"emb{i}.W": [out, in], "emb{i}.b": [out]} in float64."""
+    acts = [normalise(cylindrical(x, y, z), weights["emb_mu"], weights["emb_sigma"])]
+    for i in range(n_layers):
+        W = weights[f"emb{i}.W"].astype(np.float64)
+        b = weights[f"emb{i}.b"].astype(np.float64)
+        out = acts[-1] @ W.T + b
+        acts.append(np.maximum(out, 0.0) if i < n_layers - 1 else out)
+    grads = {}
+    dz = np.asarray(d_emb, np.float64)               # d L / d (pre-activation of the last layer)
+    for i in range(n_layers - 1, -1, -1):
+        grads[f"emb{i}.W"] = dz.T @ acts[i]
+        grads[f"emb{i}.b"] = dz.sum(0)
+        if i > 0:
+            W = weights[f"emb{i}.W"].astype(np.float64)
+            dz = (dz @ W) * (acts[i] > 0)               # through Linear, then ReLU of layer i-1
+    return grads

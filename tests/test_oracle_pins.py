@@ -733,3 +733,166 @@ def test_track_metrics_against_a_contingency_table():
             assert m[k] == tot[k], (trial, k)
         assert m["hit_eff_sum"] == pytest.approx(tot["hit_eff_sum"], rel=1e-13)
         assert m["hit_purity_sum"] == pytest.approx(tot["hit_purity_sum"], rel=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# embedding training (Sec. 5.1, Eq. 2-3)
+# ---------------------------------------------------------------------------
+def training_batch(n_events=2, seed=3):
+    from velo_synth import drop_noise
+    return drop_noise(tiny_batch(n_events, seed))
+
+
+def test_embedding_pairs_against_brute_force():
+    b = training_batch()
+    rng = np.random.default_rng(4)
+    emb = rng.normal(size=(b.n_hits, 3)).astype(np.float32)
+    rand = rng.integers(0, 2 ** 32, size=b.n_hits, dtype=np.uint64)
+    radius, k_max = 1.2, 5
+    q, a, g = O.embedding_pairs(emb, b.plane, b.particle_id, b.hit_offsets, radius, k_max, rand)
+    r2 = np.float32(radius) * np.float32(radius)
+    want = {}
+    for ev in range(b.n_events):
+        lo, hi = int(b.hit_offsets[ev]), int(b.hit_offsets[ev + 1])
+        pid, pl = b.particle_id[lo:hi], b.plane[lo:hi].astype(int)
+        sizes = {p: int((pid == p).sum()) for p in set(pid.tolist())}
+        for i in range(hi - lo):
+            if sizes[int(pid[i])] < 3:
+                continue
+            cand = [j for j in range(hi - lo) if pl[j] - pl[i] in (1, 2)]
+            scored = sorted((float(O.d2_fp32(emb[lo + i][None], emb[lo + j][None])[0, 0]), j)
+                            for j in cand)
+            chosen = {j for _, j in [(d, j) for d, j in scored if d < r2][:k_max]}
+            if cand:
+                chosen.add(cand[int(rand[lo + i]) % len(cand)])
+            later = [j for j in range(i + 1, hi - lo) if pid[j] == pid[i]]
+            if later and pl[later[0]] - pl[i] <= 2:
+                chosen.add(later[0])
+            for j in chosen:
+                want[(lo + i, lo + j)] = bool(later and later[0] == j)
+    got = {(int(x), int(y)): bool(f) for x, y, f in zip(q, a, g)}
+    assert got == want
+    assert list(zip(q.tolist(), a.tolist())) == sorted(got)
+    assert 0 < g.sum() < g.size
+
+
+def test_embedding_pairs_truth_and_structure():
+    b = training_batch(3, seed=8)
+    rng = np.random.default_rng(1)
+    emb = rng.normal(size=(b.n_hits, 4)).astype(np.float32)
+    rand = rng.integers(0, 2 ** 32, size=b.n_hits, dtype=np.uint64)
+    q, a, g = O.embedding_pairs(emb, b.plane, b.particle_id, b.hit_offsets, 1.5, 8, rand)
+    # the genuine flag is the generator's own genuine-edge definition
+    y = truth_edge_labels(global_particle_ids(b), b.plane, q, a)
+    assert np.array_equal(g, y > 0)
+    gap = b.plane[a].astype(int) - b.plane[q].astype(int)
+    assert set(gap.tolist()) <= {1, 2}
+    is_q = O.embedding_queries(b.particle_id, b.hit_offsets)
+    assert is_q[q].all()
+    # every query with a successor within two planes has its genuine pair
+    nxt = O.next_hit_of_particle(b.particle_id, b.hit_offsets)
+    need = {(i, int(nxt[i])) for i in np.nonzero(is_q)[0]
+            if nxt[i] >= 0 and b.plane[nxt[i]] - b.plane[i] <= 2}
+    assert need <= set(zip(q.tolist(), a.tolist()))
+    # radius 0: only the random and the genuine pair of each query remain
+    q0, a0, g0 = O.embedding_pairs(emb, b.plane, b.particle_id, b.hit_offsets, 0.0, 8, rand)
+    per_q = np.bincount(q0, minlength=b.n_hits)
+    assert per_q.max() <= 2 and set(zip(q0[g0].tolist(), a0[g0].tolist())) == need
+    # query definition: particles with at least three hits
+    counts = {}
+    for ev in range(b.n_events):
+        lo, hi = int(b.hit_offsets[ev]), int(b.hit_offsets[ev + 1])
+        for i in range(lo, hi):
+            counts[(ev, int(b.particle_id[i]))] = counts.get((ev, int(b.particle_id[i])), 0) + 1
+    ev_of = np.searchsorted(b.hit_offsets, np.arange(b.n_hits), side="right") - 1
+    assert all(is_q[i] == (counts[(int(ev_of[i]), int(b.particle_id[i]))] >= 3)
+               for i in range(b.n_hits))
+
+
+def test_hinge_loss_closed_forms():
+    emb = np.array([[0.0, 0.0], [0.3, 0.4], [3.0, 4.0]])
+    L, Lg, Lf, d = O.hinge_embedding_loss(emb, [0], [1], [True], w_genuine=2.0)
+    assert (L, Lg, Lf) == pytest.approx((0.5, 0.25, 0.0), abs=1e-15)
+    np.testing.assert_allclose(d[0], [-1.2, -1.6], atol=1e-15)
+    np.testing.assert_allclose(d[1], [1.2, 1.6], atol=1e-15)
+    L, Lg, Lf, d = O.hinge_embedding_loss(emb, [0, 0], [1, 2], [False, False])
+    assert (L, Lg, Lf) == pytest.approx((0.375, 0.0, 0.375), abs=1e-15)   # (0.75 + 0) / 2
+    np.testing.assert_allclose(d[0], [0.3, 0.4], atol=1e-15)               # -2 (e0 - e1) / 2
+    assert not d[2].any()                                                   # d2 = 25 > margin
+    L, *_ = O.hinge_embedding_loss(emb, [0], [2], [False], margin=25.0)    # d2 = margin: inactive
+    assert L == 0.0
+    L, Lg, Lf, d = O.hinge_embedding_loss(emb, [], [], [])
+    assert (L, Lg, Lf) == (0.0, 0.0, 0.0) and not d.any()
+
+
+def test_hinge_loss_against_torch_autograd_and_differences():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(6)
+    emb = rng.normal(scale=0.6, size=(12, 3))
+    q = rng.integers(0, 12, 40)
+    a = (q + 1 + rng.integers(0, 11, 40)) % 12
+    g = rng.uniform(size=40) < 0.3
+    L, Lg, Lf, d = O.hinge_embedding_loss(emb, q, a, g, margin=1.0, w_genuine=3.0)
+    t = torch.tensor(emb, dtype=torch.float64, requires_grad=True)
+    d2 = ((t[torch.tensor(q)] - t[torch.tensor(a)]) ** 2).sum(1)
+    gt = torch.tensor(g)
+    lt = torch.relu(1.0 - d2[~gt]).mean() + 3.0 * d2[gt].mean()
+    lt.backward()
+    assert L == pytest.approx(lt.item(), rel=1e-14)
+    np.testing.assert_allclose(d, t.grad.numpy(), rtol=1e-12, atol=1e-14)
+    h = 1e-6
+    for (i, k) in [(0, 0), (5, 2), (11, 1)]:
+        e2 = emb.copy(); e2[i, k] += h
+        e1 = emb.copy(); e1[i, k] -= h
+        fd = (O.hinge_embedding_loss(e2, q, a, g, 1.0, 3.0)[0]
+              - O.hinge_embedding_loss(e1, q, a, g, 1.0, 3.0)[0]) / (2 * h)
+        assert d[i, k] == pytest.approx(fd, rel=1e-6, abs=1e-8)
+
+
+def test_embed_backward_against_torch_autograd_and_differences():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(9)
+    widths = (3, 16, 16, 4)
+    W = {"emb_mu": rng.normal(size=3), "emb_sigma": rng.uniform(0.5, 2.0, 3)}
+    for i in range(3):
+        W[f"emb{i}.W"] = rng.normal(scale=0.5, size=(widths[i + 1], widths[i]))
+        W[f"emb{i}.b"] = rng.normal(scale=0.3, size=widths[i + 1])
+    x, y, z = rng.normal(size=(3, 30)) * np.array([[10.0], [10.0], [100.0]])
+    up = rng.normal(size=(30, 4))
+    grads = O.embed_backward(W, 3, x, y, z, up)
+    feat = torch.tensor(O.normalise(O.cylindrical(x, y, z), W["emb_mu"], W["emb_sigma"]))
+    lins = [torch.nn.Linear(widths[i], widths[i + 1]).double() for i in range(3)]
+    with torch.no_grad():
+        for i, lin in enumerate(lins):
+            lin.weight.copy_(torch.tensor(W[f"emb{i}.W"]))
+            lin.bias.copy_(torch.tensor(W[f"emb{i}.b"]))
+    h = feat
+    for i, lin in enumerate(lins):
+        h = lin(h)
+        if i < 2:
+            h = torch.relu(h)
+    (h * torch.tensor(up)).sum().backward()
+    for i, lin in enumerate(lins):
+        np.testing.assert_allclose(grads[f"emb{i}.W"], lin.weight.grad.numpy(), rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(grads[f"emb{i}.b"], lin.bias.grad.numpy(), rtol=1e-12, atol=1e-12)
+    f = lambda WW: float((O.embed(WW, 3, x, y, z) * up).sum())
+    for name, idx in [("emb0.W", (3, 1)), ("emb1.b", (7,)), ("emb2.W", (2, 9))]:
+        Wp = {k: v.copy() for k, v in W.items()}; Wp[name][idx] += 1e-6
+        Wm = {k: v.copy() for k, v in W.items()}; Wm[name][idx] -= 1e-6
+        assert grads[name][idx] == pytest.approx((f(Wp) - f(Wm)) / 2e-6, rel=1e-5, abs=1e-7)
+
+
+def test_embedding_pairs_worked_by_hand():
+    g = json.loads((GOLDEN / "embedding_pairs.json").read_text())
+    ev = g["event"]
+    emb = np.zeros((8, 2), np.float32)
+    for case in g["cases"]:
+        q, a, gen = O.embedding_pairs(emb, ev["plane"], ev["particle_id"], [0, 8], 0.0, 5,
+                                      np.array(case["rand"], np.uint64))
+        assert [[int(x), int(y), bool(f)] for x, y, f in zip(q, a, gen)] == case["pairs"]
+
+
+def test_hinge_gradient_vanishes_at_the_margin():
+    emb = np.array([[0.0, 0.0], [3.0, 4.0]])
+    L, _, _, d = O.hinge_embedding_loss(emb, [0], [1], [False], margin=25.0)
+    assert L == 0.0 and not d.any()

@@ -4,12 +4,12 @@ Only input generation lives here (events, truth, weights, the blob format);
 none of the track-finding arithmetic does.
 """
 from .events import (N_PLANES, Z_PLANES, Batch, EventRecipe, compact_particle_ids, concat_events,
-                     global_particle_ids,
+                     drop_noise, global_particle_ids,
                      make_batch, make_event, truth_edge_labels)
 from .model import ModelConfig, blob_layout, blob_size, make_weights, pack_blob, unpack_blob
 from .presets import WORKLOADS, Workload
 
 __all__ = ["N_PLANES", "Z_PLANES", "Batch", "EventRecipe", "compact_particle_ids", "concat_events",
-           "global_particle_ids",
+           "drop_noise", "global_particle_ids",
            "make_batch", "make_event", "truth_edge_labels", "ModelConfig", "blob_layout",
            "blob_size", "make_weights", "pack_blob", "unpack_blob", "WORKLOADS", "Workload"]

@@ -188,3 +188,15 @@ def compact_particle_ids(batch: Batch) -> np.ndarray:
         if m.any():
             out[lo:hi][m] = np.unique(seg[m], return_inverse=True)[1]
     return out
+
+
+def drop_noise(batch: Batch) -> Batch:
+    """The batch without its noise hits (particle id -1), order kept: the
+    embedding is trained on events with noise removed (Sec. 5.1)."""
+    keep = batch.particle_id >= 0
+    counts = np.array([int(keep[batch.hit_offsets[b]:batch.hit_offsets[b + 1]].sum())
+                       for b in range(batch.n_events)], np.int64)
+    offs = np.zeros(batch.n_events + 1, np.int64)
+    np.cumsum(counts, out=offs[1:])
+    return Batch(batch.x[keep], batch.y[keep], batch.z[keep], batch.plane[keep],
+                 batch.particle_id[keep], offs.astype(np.int32))
