@@ -255,6 +255,76 @@ etx_status etx_edges_to_tracks_sweep(etx_ctx* ctx, const int32_t* src, const int
                                      int32_t* labels, void* stream);
 
 /*
+ * Training of the hit embedding (Sec. 5.1, Eq. 2-3).  A step is
+ *   etx_embed_forward_train -> etx_embedding_pairs -> etx_hinge_loss ->
+ *   etx_embed_backward -> etx_adam_step on the embedding parameters ->
+ *   etx_load_weights.
+ * The batch has its noise hits removed (Sec. 5.1), hits plane-sorted per
+ * event as everywhere.
+ *
+ * etx_embed_param_count: number of embedding parameters, in blob order
+ * (W[out][in], b[out] per layer; they follow the 12 normalisation values of
+ * the blob), or -1 for an invalid config.
+ *
+ * etx_embed_forward_train: etx_embed that also keeps, in `workspace` (at
+ * least etx_embed_train_workspace() bytes, 16-byte aligned, owned by the
+ * caller), the normalised inputs and every hidden layer's activations for
+ * etx_embed_backward.  emb float32 [n_hits][D] is written.
+ *
+ * etx_embed_backward: d_params float32 [etx_embed_param_count] receives
+ * dL/dtheta for the upstream gradient d_emb float32 [n_hits][D], through the
+ * activations that the last etx_embed_forward_train of the same n_hits and
+ * weights left in `workspace` (the rest of the workspace is scratch).  The
+ * weights are read from the context's copy of the blob.  FP32 SIMT; the
+ * weight gradients accumulate with atomics (order not fixed).
+ *
+ * etx_embedding_pairs: the training set T (Sec. 5.1).  For each query q (a
+ * hit whose particle has at least min_hits hits in its event) on plane p,
+ * partners on planes p+1 and p+2 of the event: the pairs of the graph rule
+ * (etx_build_graph with `radius` and `k_max`: hard negatives), one random
+ * partner (the (rand[q] mod c)-th of the c hits on p+1 and p+2, in index
+ * order; rand uint32 [n_hits] is an input), and the genuine edge q -> next
+ * hit of q's particle when it lies on p+1 or p+2.  The union is written
+ * sorted by (q, a): pair_q, pair_a int32 [capacity] batch-global hit
+ * indices, pair_genuine uint8 [capacity] (1 iff a is the next hit of q's
+ * particle); n_pairs int32 (device) receives the count.
+ *   particle_id  int32 [n_hits], event-local in [0, hits of the event), no
+ *                noise (-1 is reported by etx_ctx_sync as out of range)
+ *   workspace    at least etx_embedding_pairs_workspace() bytes, 4-byte
+ *                aligned, caller-owned scratch
+ * Uses the context's graph scratch (so n_events and n_hits within its
+ * capacity).  More pairs than `capacity`: ETX_ERR_CAPACITY at etx_ctx_sync and
+ * n_pairs = 0.  Asynchronous on `stream`.
+ *
+ * etx_hinge_loss: Eq. 2-3 over the n_pairs (device) pairs: loss float32 [3]
+ * (device) = {L_fake + w_genuine * L_genuine, L_genuine, L_fake}, L_genuine
+ * = mean d2 over genuine pairs, L_fake = mean max(0, margin - d2) over fake
+ * pairs (an empty set contributes 0; the hinge is inactive at d2 = margin);
+ * d_emb float32 [n_hits][D] = dL/d emb (overwritten; atomics, order not
+ * fixed).  pair_capacity bounds n_pairs (sizes the grid).  D <= 16.
+ * Indices outside [0, n_hits) are skipped and reported by etx_ctx_sync.
+ */
+int64_t etx_embed_param_count(const etx_config* cfg);
+size_t etx_embed_train_workspace(const etx_config* cfg, int64_t n_hits);
+etx_status etx_embed_forward_train(etx_ctx* ctx, const float* x, const float* y, const float* z,
+                                   int64_t n_hits, float* emb, void* workspace,
+                                   size_t workspace_bytes, void* stream);
+etx_status etx_embed_backward(etx_ctx* ctx, int64_t n_hits, const float* d_emb, float* d_params,
+                              void* workspace, size_t workspace_bytes, void* stream);
+size_t etx_embedding_pairs_workspace(int32_t n_events, int64_t n_hits, int32_t k_max);
+etx_status etx_embedding_pairs(etx_ctx* ctx, const float* emb, const int8_t* plane,
+                               const int32_t* particle_id, const int32_t* hit_offsets,
+                               int32_t n_events, int64_t n_hits, float radius, int32_t k_max,
+                               const uint32_t* rand, int32_t min_hits, void* workspace,
+                               size_t workspace_bytes, int32_t* pair_q, int32_t* pair_a,
+                               uint8_t* pair_genuine, int64_t capacity, int32_t* n_pairs,
+                               void* stream);
+etx_status etx_hinge_loss(etx_ctx* ctx, const float* emb, int64_t n_hits, const int32_t* pair_q,
+                          const int32_t* pair_a, const uint8_t* pair_genuine,
+                          const int32_t* n_pairs, int64_t pair_capacity, float margin,
+                          float w_genuine, float* loss, float* d_emb, void* stream);
+
+/*
  * Track-finding performance against truth (Sec. 6, Table 1), for evaluating
  * labels on synthetic or simulated events.  A track is a set of hits of one
  * event that share a label; it counts when it has at least min_hits hits.  A

@@ -19,11 +19,27 @@ struct EmbArgs {
   int dim;  // D
 };
 
+// Copy a 64-row activation tile from shared memory to rows [row0, n) of a
+// row-major [n][EW] array (the training forward keeps them for the reverse pass).
 template <int EW>
+__device__ __forceinline__ void save_tile(const float* Act, int lda, float* __restrict__ out,
+                                          int64_t row0, int64_t n, int tid) {
+  for (int idx = tid; idx < kTileM * EW / 4; idx += kTileThreads) {
+    const int r = idx / (EW / 4), c4 = idx - r * (EW / 4);
+    if (row0 + r < n)
+      *reinterpret_cast<float4*>(out + (row0 + r) * EW + c4 * 4) =
+          *reinterpret_cast<const float4*>(Act + r * lda + c4 * 4);
+  }
+}
+
+// SAVE: also write the normalised inputs ([n][4], last column 0) and every
+// hidden layer's activations ([n][EW] each, after ReLU) to `saved`.
+template <int EW, bool SAVE>
 __global__ void __launch_bounds__(kTileThreads) k_embed(const float* __restrict__ x,
                                                         const float* __restrict__ y,
                                                         const float* __restrict__ z, int64_t n,
-                                                        EmbArgs a, float* __restrict__ emb) {
+                                                        EmbArgs a, float* __restrict__ emb,
+                                                        float* __restrict__ saved) {
   constexpr int LDA = EW + 4;
   __shared__ __align__(16) float In[kTileM * 4];
   __shared__ __align__(16) float Act[kTileM * LDA];
@@ -47,6 +63,9 @@ __global__ void __launch_bounds__(kTileThreads) k_embed(const float* __restrict_
         f2 = (zv - mu2) * is2;
       }
       *reinterpret_cast<float4*>(In + tid * 4) = make_float4(f0, f1, f2, 0.f);
+      if constexpr (SAVE) {
+        if (i < n) *reinterpret_cast<float4*>(saved + i * 4) = make_float4(f0, f1, f2, 0.f);
+      }
     }
     if (tid < 4 * EW / 4) {
       // layer 0 weights: W^T [4][EW] (k padded 3 -> 4 with a zero row)
@@ -64,6 +83,10 @@ __global__ void __launch_bounds__(kTileThreads) k_embed(const float* __restrict_
       for (int r = 0; r < 4; ++r) acc.v[r][j] = fmaxf(acc.v[r][j] + bj, 0.f);
     }
     store_tile_smem<EW>(acc, Act, LDA, ty, tx);
+    if constexpr (SAVE) {
+      __syncthreads();
+      save_tile<EW>(Act, LDA, saved + n * 4, row0, n, tid);
+    }
 
     for (int l = 1; l < a.depth - 1; ++l) {
       acc.zero();
@@ -81,6 +104,10 @@ __global__ void __launch_bounds__(kTileThreads) k_embed(const float* __restrict_
       }
       __syncthreads();  // everyone finished reading Act
       store_tile_smem<EW>(acc, Act, LDA, ty, tx);
+      if constexpr (SAVE) {
+        __syncthreads();
+        save_tile<EW>(Act, LDA, saved + n * 4 + (int64_t)l * n * EW, row0, n, tid);
+      }
     }
     __syncthreads();
     // last layer: EW -> D, thread = (row, group of outputs)
@@ -109,17 +136,22 @@ __global__ void __launch_bounds__(kTileThreads) k_embed(const float* __restrict_
 
 template <int EW>
 cudaError_t run(etx_ctx* ctx, const float* x, const float* y, const float* z, int64_t n,
-                const EmbArgs& a, float* emb, cudaStream_t s) {
+                const EmbArgs& a, float* emb, float* saved, cudaStream_t s) {
   const int64_t tiles = (n + kTileM - 1) / kTileM;
-  const int grid = grid_for(ctx, (const void*)k_embed<EW>, kTileThreads, 0, tiles);
-  launch(ctx, "embed_mlp", k_embed<EW>, grid, kTileThreads, 0, s, x, y, z, n, a, emb);
+  if (saved) {
+    const int grid = grid_for(ctx, (const void*)k_embed<EW, true>, kTileThreads, 0, tiles);
+    launch(ctx, "embed_mlp_save", k_embed<EW, true>, grid, kTileThreads, 0, s, x, y, z, n, a, emb,
+           saved);
+  } else {
+    const int grid = grid_for(ctx, (const void*)k_embed<EW, false>, kTileThreads, 0, tiles);
+    launch(ctx, "embed_mlp", k_embed<EW, false>, grid, kTileThreads, 0, s, x, y, z, n, a, emb,
+           (float*)nullptr);
+  }
   return cudaGetLastError();
 }
 
-}  // namespace
-
-cudaError_t launch_embed(etx_ctx* ctx, const float* x, const float* y, const float* z,
-                         int64_t n, float* emb, cudaStream_t s) {
+cudaError_t dispatch(etx_ctx* ctx, const float* x, const float* y, const float* z, int64_t n,
+                     float* emb, float* saved, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   EmbArgs a{};
   a.norm = ctx->w.norm;
@@ -127,12 +159,24 @@ cudaError_t launch_embed(etx_ctx* ctx, const float* x, const float* y, const flo
   a.dim = ctx->cfg.emb_widths[a.depth];
   for (int l = 0; l < a.depth; ++l) a.lin[l] = ctx->w.emb[l];
   switch (ctx->cfg.emb_widths[1]) {
-    case 16: return run<16>(ctx, x, y, z, n, a, emb, s);
-    case 32: return run<32>(ctx, x, y, z, n, a, emb, s);
-    case 64: return run<64>(ctx, x, y, z, n, a, emb, s);
-    case 128: return run<128>(ctx, x, y, z, n, a, emb, s);
+    case 16: return run<16>(ctx, x, y, z, n, a, emb, saved, s);
+    case 32: return run<32>(ctx, x, y, z, n, a, emb, saved, s);
+    case 64: return run<64>(ctx, x, y, z, n, a, emb, saved, s);
+    case 128: return run<128>(ctx, x, y, z, n, a, emb, saved, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+}  // namespace
+
+cudaError_t launch_embed(etx_ctx* ctx, const float* x, const float* y, const float* z,
+                         int64_t n, float* emb, cudaStream_t s) {
+  return dispatch(ctx, x, y, z, n, emb, nullptr, s);
+}
+
+cudaError_t launch_embed_save(etx_ctx* ctx, const float* x, const float* y, const float* z,
+                              int64_t n, float* emb, float* saved, cudaStream_t s) {
+  return dispatch(ctx, x, y, z, n, emb, saved, s);
 }
 
 }  // namespace etx

@@ -219,6 +219,7 @@ etx_status etx_ctx_create(const etx_config* cfg, int32_t device, etx_ctx** out) 
   auto chk = [&](etx_status s) { if (st == ETX_OK) st = s; };
   chk(dmalloc(ctx, &ctx->d_err, 1, "error word"));
   chk(dmalloc(ctx, &ctx->n_edges, 1, "edge count"));
+  chk(dmalloc(ctx, &ctx->small, 8, "reduction scratch"));
   chk(dmalloc(ctx, &ctx->plane_off, (size_t)B * (cfg->n_planes + 1), "plane offsets"));
   chk(dmalloc(ctx, &ctx->hit_cnt, (size_t)N + 1, "hit counts"));
   ctx->scan_tmp_ints = scan_tmp_ints(N + 1) + 8;
@@ -267,7 +268,8 @@ etx_status etx_ctx_destroy(etx_ctx* ctx) {
                   ctx->hit_cnt, ctx->scan_tmp, ctx->out_off, ctx->in_off, ctx->in_cnt,
                   ctx->perm_in, ctx->h, ctx->m, ctx->e, ctx->parent, ctx->h_ck, ctx->e_ck,
                   ctx->de, ctx->dh, ctx->bw_X, ctx->bw_DX, ctx->bw_R1, ctx->bw_DA1, ctx->bw_DY1,
-                  ctx->bw_DY1N1, ctx->bw_DA2, ctx->bw_DY2, ctx->bw_DY2N2, ctx->h_lp};
+                  ctx->bw_DY1N1, ctx->bw_DA2, ctx->bw_DY2, ctx->bw_DY2N2, ctx->h_lp,
+                  ctx->small};
   for (void* p : bufs)
     if (p) cudaFree(p);
   for (auto& r : ctx->prof) {
@@ -653,6 +655,107 @@ etx_status etx_edges_to_tracks_sweep(etx_ctx* ctx, const int32_t* src, const int
     e = launch_plane_sweep(ctx, src, dst, logits, threshold_logit, hit_offsets, n_events, n_hits,
                            labels, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "etx_edges_to_tracks_sweep launch");
+  return ETX_OK;
+}
+
+// ---- embedding training (Sec. 5.1, Eq. 2-3) ----------------------------------
+
+int64_t etx_embed_param_count(const etx_config* cfg) {
+  if (!cfg || cfg->emb_depth < 1 || cfg->emb_depth > ETX_MAX_EMB_LAYERS) return -1;
+  return embed_param_count(*cfg);
+}
+
+size_t etx_embed_train_workspace(const etx_config* cfg, int64_t n_hits) {
+  if (!cfg || n_hits < 0 || cfg->emb_depth < 1 || cfg->emb_depth > ETX_MAX_EMB_LAYERS) return 0;
+  return embed_backward_workspace(*cfg, n_hits);
+}
+
+etx_status etx_embed_forward_train(etx_ctx* ctx, const float* x, const float* y, const float* z,
+                                   int64_t n_hits, float* emb, void* workspace,
+                                   size_t workspace_bytes, void* stream) {
+  if (!ctx) return ETX_ERR_ARG;
+  if (!ctx->weights_loaded) return fail(ctx, ETX_ERR_STATE, "weights not loaded");
+  if (n_hits < 0 || n_hits >= ((int64_t)1 << 31)) return fail(ctx, ETX_ERR_ARG, "n_hits out of range");
+  if (n_hits > 0 && (!x || !y || !z || !emb || !workspace)) return fail(ctx, ETX_ERR_ARG, "NULL array");
+  if (workspace_bytes < embed_backward_workspace(ctx->cfg, n_hits))
+    return fail(ctx, ETX_ERR_CAPACITY, "workspace smaller than etx_embed_train_workspace()");
+  if (reinterpret_cast<uintptr_t>(workspace) & 15) return fail(ctx, ETX_ERR_ARG, "workspace not 16-byte aligned");
+  cudaSetDevice(ctx->device);
+  cudaError_t e = launch_embed_save(ctx, x, y, z, n_hits, emb, static_cast<float*>(workspace),
+                                    (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "etx_embed_forward_train launch");
+  return ETX_OK;
+}
+
+etx_status etx_embed_backward(etx_ctx* ctx, int64_t n_hits, const float* d_emb, float* d_params,
+                              void* workspace, size_t workspace_bytes, void* stream) {
+  if (!ctx) return ETX_ERR_ARG;
+  if (!ctx->weights_loaded || !ctx->blob_dev) return fail(ctx, ETX_ERR_STATE, "weights not loaded");
+  if (n_hits < 0 || n_hits >= ((int64_t)1 << 31)) return fail(ctx, ETX_ERR_ARG, "n_hits out of range");
+  if (!d_params || (n_hits > 0 && (!d_emb || !workspace))) return fail(ctx, ETX_ERR_ARG, "NULL array");
+  if (workspace_bytes < embed_backward_workspace(ctx->cfg, n_hits))
+    return fail(ctx, ETX_ERR_CAPACITY, "workspace smaller than etx_embed_train_workspace()");
+  const int64_t EW = ctx->cfg.emb_widths[1];
+  float* saved = static_cast<float*>(workspace);
+  float* dz_a = saved + n_hits * 4 + (int64_t)(ctx->cfg.emb_depth - 1) * n_hits * EW;
+  float* dz_b = dz_a + n_hits * EW;
+  cudaSetDevice(ctx->device);
+  cudaError_t e = launch_embed_backward(ctx, n_hits, saved, d_emb, dz_a, dz_b, d_params,
+                                        (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "etx_embed_backward launch");
+  return ETX_OK;
+}
+
+size_t etx_embedding_pairs_workspace(int32_t n_events, int64_t n_hits, int32_t k_max) {
+  if (n_events < 0 || n_hits < 0 || k_max < 1) return 0;
+  return embedding_pairs_workspace(n_events, n_hits, k_max);
+}
+
+etx_status etx_embedding_pairs(etx_ctx* ctx, const float* emb, const int8_t* plane,
+                               const int32_t* particle_id, const int32_t* hit_offsets,
+                               int32_t n_events, int64_t n_hits, float radius, int32_t k_max,
+                               const uint32_t* rand, int32_t min_hits, void* workspace,
+                               size_t workspace_bytes, int32_t* pair_q, int32_t* pair_a,
+                               uint8_t* pair_genuine, int64_t capacity, int32_t* n_pairs,
+                               void* stream) {
+  if (!ctx) return ETX_ERR_ARG;
+  if (n_events < 0 || n_events > ctx->cfg.max_events) return fail(ctx, ETX_ERR_CAPACITY, "n_events exceeds the context capacity");
+  if (n_hits < 0 || n_hits > ctx->cfg.max_hits) return fail(ctx, ETX_ERR_CAPACITY, "n_hits exceeds the context capacity");
+  if (n_events == 0 && n_hits > 0) return fail(ctx, ETX_ERR_ARG, "hits without events");
+  if (!(radius >= 0.f) || radius > 1e18f) return fail(ctx, ETX_ERR_ARG, "radius must be finite and >= 0");
+  if (k_max < 1 || n_hits * (int64_t)k_max >= ((int64_t)1 << 31)) return fail(ctx, ETX_ERR_ARG, "k_max out of range");
+  if (min_hits < 1) return fail(ctx, ETX_ERR_ARG, "min_hits must be at least 1");
+  if (capacity < 0 || capacity >= ((int64_t)1 << 31)) return fail(ctx, ETX_ERR_ARG, "capacity out of range");
+  if (!hit_offsets || !n_pairs || !workspace) return fail(ctx, ETX_ERR_ARG, "NULL array");
+  if (n_hits > 0 && (!emb || !plane || !particle_id || !rand)) return fail(ctx, ETX_ERR_ARG, "NULL array");
+  if (capacity > 0 && (!pair_q || !pair_a || !pair_genuine)) return fail(ctx, ETX_ERR_ARG, "NULL pair arrays");
+  if (workspace_bytes < embedding_pairs_workspace(n_events, n_hits, k_max))
+    return fail(ctx, ETX_ERR_CAPACITY, "workspace smaller than etx_embedding_pairs_workspace()");
+  if (reinterpret_cast<uintptr_t>(workspace) & 3) return fail(ctx, ETX_ERR_ARG, "workspace not 4-byte aligned");
+  cudaSetDevice(ctx->device);
+  cudaError_t e = launch_embedding_pairs(ctx, emb, plane, particle_id, hit_offsets, n_events, n_hits,
+                                         radius, k_max, rand, min_hits, workspace, pair_q, pair_a,
+                                         pair_genuine, capacity, n_pairs, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "etx_embedding_pairs launch");
+  return ETX_OK;
+}
+
+etx_status etx_hinge_loss(etx_ctx* ctx, const float* emb, int64_t n_hits, const int32_t* pair_q,
+                          const int32_t* pair_a, const uint8_t* pair_genuine,
+                          const int32_t* n_pairs, int64_t pair_capacity, float margin,
+                          float w_genuine, float* loss, float* d_emb, void* stream) {
+  if (!ctx) return ETX_ERR_ARG;
+  if (n_hits < 0 || n_hits >= ((int64_t)1 << 31)) return fail(ctx, ETX_ERR_ARG, "n_hits out of range");
+  if (pair_capacity < 0 || pair_capacity >= ((int64_t)1 << 31)) return fail(ctx, ETX_ERR_ARG, "pair_capacity out of range");
+  if (!n_pairs || !loss || (n_hits > 0 && (!emb || !d_emb))) return fail(ctx, ETX_ERR_ARG, "NULL array");
+  if (pair_capacity > 0 && (!pair_q || !pair_a || !pair_genuine)) return fail(ctx, ETX_ERR_ARG, "NULL pair arrays");
+  if (!(margin == margin) || !(w_genuine >= 0.f) || w_genuine > 1e30f) return fail(ctx, ETX_ERR_ARG, "bad margin or w_genuine");
+  if (ctx->cfg.emb_widths[ctx->cfg.emb_depth] > 16) return fail(ctx, ETX_ERR_UNSUPPORTED, "embedding dimension above 16");
+  cudaSetDevice(ctx->device);
+  cudaError_t e = launch_hinge_loss(ctx, emb, n_hits, pair_q, pair_a, pair_genuine, n_pairs,
+                                    pair_capacity, margin, w_genuine, loss, d_emb, ctx->small,
+                                    (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "etx_hinge_loss launch");
   return ETX_OK;
 }
 

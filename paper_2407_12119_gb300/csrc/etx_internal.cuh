@@ -87,6 +87,7 @@ struct etx_ctx {
 
   int* d_err = nullptr;
   int32_t* n_edges = nullptr;    // device: edge count of the current call, clamped
+  double* small = nullptr;       // device: 8 doubles of reduction scratch (loss sums, counts)
 
   // weights
   float* w_dev = nullptr;   // repacked FP32 weights
@@ -201,6 +202,27 @@ cudaError_t launch_plane_bins(etx_ctx* ctx, const int8_t* plane, const int32_t* 
 // gnn_f32.cu: ctx->out_off, the src-CSR of edges sorted by src (checks order and range)
 cudaError_t launch_out_offsets(etx_ctx* ctx, int64_t N, const int32_t* src, const int32_t* dst,
                                const int32_t* n_edges_dev, cudaStream_t s);
+
+// embed_train.cu: the embedding's training set and hinge loss (Sec. 5.1, Eq. 2-3)
+size_t embedding_pairs_workspace(int32_t n_events, int64_t n_hits, int32_t k_max);
+cudaError_t launch_embedding_pairs(etx_ctx* ctx, const float* emb, const int8_t* plane,
+                                   const int32_t* particle_id, const int32_t* hit_offsets,
+                                   int32_t n_events, int64_t n_hits, float radius, int32_t k_max,
+                                   const uint32_t* rand, int32_t min_hits, void* workspace,
+                                   int32_t* pq, int32_t* pa, uint8_t* pg, int64_t capacity,
+                                   int32_t* n_pairs, cudaStream_t s);
+// scratch: 3 doubles of device memory
+cudaError_t launch_hinge_loss(etx_ctx* ctx, const float* emb, int64_t n_hits, const int32_t* pq,
+                              const int32_t* pa, const uint8_t* pg, const int32_t* n_pairs,
+                              int64_t pair_capacity, float margin, float w_genuine, float* loss,
+                              float* d_emb, void* scratch, cudaStream_t s);
+// embed.cu / gnn_bwd.cu: embedding forward with saved activations, and its reverse pass
+size_t embed_backward_workspace(const etx_config& cfg, int64_t n_hits);
+int64_t embed_param_count(const etx_config& cfg);
+cudaError_t launch_embed_save(etx_ctx* ctx, const float* x, const float* y, const float* z,
+                              int64_t n, float* emb, float* saved, cudaStream_t s);
+cudaError_t launch_embed_backward(etx_ctx* ctx, int64_t n, const float* saved, const float* d_emb,
+                                  float* dz_a, float* dz_b, float* d_params, cudaStream_t s);
 
 // metrics.cu: Table 1 counts; workspace = per-event tallies then six int32 arrays of n_hits
 size_t track_metrics_workspace(int32_t n_events, int64_t n_hits);

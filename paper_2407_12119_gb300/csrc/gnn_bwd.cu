@@ -805,4 +805,117 @@ cudaError_t launch_adam(etx_ctx* ctx, float* p, const float* g, float* m, float*
   return cudaGetLastError();
 }
 
+// ---- embedding MLP reverse pass (training of Sec. 5.1) -----------------------
+
+namespace {
+
+// Y[r][:] = (X[r][:K] . W[K][NT]) * (mask[r][:] > 0): the gradient through one
+// Linear layer (W in its original [out][in] layout, K = out) and the ReLU of
+// the layer below (mask = its saved activations).
+template <int NT>
+__global__ void __launch_bounds__(kTileThreads)
+k_back_rows(const float* __restrict__ X, int K, const float* __restrict__ W,
+            const float* __restrict__ mask, float* __restrict__ Y, int64_t n) {
+  __shared__ __align__(16) float As[kTileM * kLdaChunk];
+  __shared__ __align__(16) float Ws[kKC * NT];
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int64_t tiles = (n + kTileM - 1) / kTileM;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t row0 = tile * kTileM;
+    TileAcc<NT> acc;
+    acc.zero();
+    for (int k0 = 0; k0 < K; k0 += kKC) {
+      __syncthreads();
+      for (int i = tid; i < kTileM * kKC; i += kTileThreads) {
+        const int mm = i / kKC, kk = i - mm * kKC;
+        const int64_t r = row0 + mm;
+        const int k = k0 + kk;
+        As[mm * kLdaChunk + kk] = (r < n && k < K) ? X[r * K + k] : 0.f;
+      }
+      for (int i = tid; i < kKC * NT; i += kTileThreads) {
+        const int kk = i / NT, c = i - kk * NT;
+        const int k = k0 + kk;
+        Ws[i] = k < K ? W[(int64_t)k * NT + c] : 0.f;
+      }
+      __syncthreads();
+      acc.template mma<kKC>(As, kLdaChunk, 0, Ws, ty, tx);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int64_t row = row0 + ty * 4 + r;
+      if (row >= n) continue;
+#pragma unroll
+      for (int j = 0; j < NT / 16; ++j) {
+        const int64_t o = row * NT + ColMap<NT>::col(tx, j);
+        Y[o] = mask[o] > 0.f ? acc.v[r][j] : 0.f;
+      }
+    }
+  }
+}
+
+template <int NT>
+void back_rows(etx_ctx* ctx, const float* X, int K, const float* W, const float* mask, float* Y,
+               int64_t n, cudaStream_t s) {
+  const int64_t tiles = (n + kTileM - 1) / kTileM;
+  const int grid = grid_for(ctx, (const void*)k_back_rows<NT>, kTileThreads, 0, tiles);
+  launch(ctx, "embtrain_back_rows", k_back_rows<NT>, grid, kTileThreads, 0, s, X, K, W, mask, Y, n);
+}
+
+}  // namespace
+
+int64_t embed_param_count(const etx_config& c) {
+  int64_t p = 0;
+  for (int l = 0; l < c.emb_depth; ++l)
+    p += (int64_t)c.emb_widths[l + 1] * c.emb_widths[l] + c.emb_widths[l + 1];
+  return p;
+}
+
+size_t embed_backward_workspace(const etx_config& c, int64_t n) {
+  const int64_t EW = c.emb_widths[1];
+  // saved inputs [n][4] and hidden activations [depth-1][n][EW], two gradient buffers [n][EW]
+  return (size_t)(n * 4 + (int64_t)(c.emb_depth - 1) * n * EW + 2 * n * EW) * sizeof(float);
+}
+
+cudaError_t launch_embed_backward(etx_ctx* ctx, int64_t n, const float* saved, const float* d_emb,
+                                  float* dz_a, float* dz_b, float* d_params, cudaStream_t s) {
+  const etx_config& c = ctx->cfg;
+  const int depth = c.emb_depth, EW = c.emb_widths[1];
+  int64_t woff[ETX_MAX_EMB_LAYERS], boff[ETX_MAX_EMB_LAYERS], off = 0;
+  for (int l = 0; l < depth; ++l) {
+    woff[l] = off;
+    off += (int64_t)c.emb_widths[l + 1] * c.emb_widths[l];
+    boff[l] = off;
+    off += c.emb_widths[l + 1];
+  }
+  cudaError_t e = cudaMemsetAsync(d_params, 0, (size_t)off * sizeof(float), s);
+  if (e != cudaSuccess || n == 0) return e;
+  const float* Wblob = ctx->blob_dev + 12;  // embedding parameters follow the 12 normalisation values
+  auto act = [&](int l) { return saved + n * 4 + (int64_t)l * n * EW; };
+  const int splits = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->n_sms, (n + 1023) / 1024));
+  const int cb = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->n_sms * 4, n));
+  const float* dz = d_emb;  // gradient at the output of layer l (before its ReLU, if any)
+  for (int l = depth - 1; l >= 0; --l) {
+    const int M = c.emb_widths[l + 1], n_in = c.emb_widths[l];
+    const float* in = l > 0 ? act(l - 1) : saved;
+    const int ld_in = l > 0 ? EW : 4;
+    launch(ctx, "embtrain_weight_grad", k_gemm_tn,
+           dim3((M + kTileM - 1) / kTileM, (n_in + 127) / 128, splits), kTileThreads, 0, s, dz, M,
+           in, ld_in, M, n_in, n, (const int32_t*)nullptr, d_params + woff[l]);
+    launch(ctx, "embtrain_colsum", k_colsum, cb, M, 0, s, dz, M, (const float*)nullptr, n,
+           (const int32_t*)nullptr, d_params + boff[l]);
+    if (l > 0) {
+      float* out = dz == dz_a ? dz_b : dz_a;
+      switch (EW) {
+        case 16: back_rows<16>(ctx, dz, M, Wblob + woff[l], act(l - 1), out, n, s); break;
+        case 32: back_rows<32>(ctx, dz, M, Wblob + woff[l], act(l - 1), out, n, s); break;
+        case 64: back_rows<64>(ctx, dz, M, Wblob + woff[l], act(l - 1), out, n, s); break;
+        case 128: back_rows<128>(ctx, dz, M, Wblob + woff[l], act(l - 1), out, n, s); break;
+        default: return cudaErrorInvalidValue;
+      }
+      dz = out;
+    }
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace etx

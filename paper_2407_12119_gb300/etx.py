@@ -32,7 +32,9 @@ EXPORTED = ["etx_ctx_create", "etx_ctx_destroy", "etx_last_error", "etx_weights_
             "etx_edges_to_tracks", "etx_edges_to_tracks_noalloc", "etx_launch_count",
             "etx_profile_enable", "etx_profile_read", "etx_weighted_bce", "etx_adam_step",
             "etx_autotune", "etx_tuned", "etx_set_tuned", "etx_edges_to_tracks_sweep",
-            "etx_track_metrics_workspace", "etx_track_metrics"]
+            "etx_track_metrics_workspace", "etx_track_metrics", "etx_embed_param_count",
+            "etx_embed_train_workspace", "etx_embed_forward_train", "etx_embed_backward",
+            "etx_embedding_pairs_workspace", "etx_embedding_pairs", "etx_hinge_loss"]
 # etx_track_metrics outputs
 TRACK_COUNTS = ["particles", "matched_particles", "candidates", "candidate_particles", "tracks",
                 "unmatched_tracks"]
@@ -99,6 +101,14 @@ def lib() -> ctypes.CDLL:
         "etx_edges_to_tracks_sweep": (i32, [vp, vp, vp, vp, f32, vp, vp, vp, i32, i64, vp, vp]),
         "etx_set_tuned": (i32, [vp, ctypes.c_char_p, i32]),
         "etx_track_metrics_workspace": (ctypes.c_size_t, [i32, i64]),
+        "etx_embed_param_count": (i64, [cfgp]),
+        "etx_embed_train_workspace": (ctypes.c_size_t, [cfgp, i64]),
+        "etx_embed_forward_train": (i32, [vp, vp, vp, vp, i64, vp, vp, ctypes.c_size_t, vp]),
+        "etx_embed_backward": (i32, [vp, i64, vp, vp, vp, ctypes.c_size_t, vp]),
+        "etx_embedding_pairs_workspace": (ctypes.c_size_t, [i32, i64, i32]),
+        "etx_embedding_pairs": (i32, [vp, vp, vp, vp, vp, i32, i64, f32, i32, vp, i32, vp,
+                                      ctypes.c_size_t, vp, vp, vp, i64, vp, vp]),
+        "etx_hinge_loss": (i32, [vp, vp, i64, vp, vp, vp, vp, i64, f32, f32, vp, vp, vp]),
         "etx_track_metrics": (i32, [vp, vp, vp, vp, i32, i64, i32, i32, i32, vp, ctypes.c_size_t,
                                     vp, vp, vp]),
         "etx_launch_count": (i64, [vp]),
@@ -312,6 +322,93 @@ class Context:
                                                     _ptr(plane), _ptr(hit_offsets), n_events,
                                                     n_hits, _ptr(labels), _stream(stream)))
         return labels
+
+    # ---- embedding training (Sec. 5.1, Eq. 2-3) ----------------------------
+    @property
+    def embed_param_count(self) -> int:
+        return int(lib().etx_embed_param_count(ctypes.byref(self.cfg)))
+
+    def embed_train_workspace(self, n_hits: int):
+        """Device scratch for embed_forward_train / embed_backward."""
+        n = int(lib().etx_embed_train_workspace(ctypes.byref(self.cfg), int(n_hits)))
+        return torch.empty(max(n, 16), dtype=torch.uint8, device=self.device)
+
+    def embed_forward_train(self, x, y, z, workspace, emb=None, stream=None):
+        dev = self.device
+        for t, n in ((x, "x"), (y, "y"), (z, "z")):
+            _need(t, torch.float32, n, dev)
+        _need(workspace, torch.uint8, "workspace", dev)
+        n_hits = x.shape[0]
+        D = int(self.cfg.emb_widths[self.cfg.emb_depth])
+        if emb is None:
+            emb = torch.empty(n_hits, D, dtype=torch.float32, device=dev)
+        _need(emb, torch.float32, "emb", dev)
+        self._check(lib().etx_embed_forward_train(self._h, _ptr(x), _ptr(y), _ptr(z), n_hits,
+                                                  _ptr(emb), _ptr(workspace), workspace.numel(),
+                                                  _stream(stream)))
+        return emb
+
+    def embed_backward(self, d_emb, workspace, d_params=None, stream=None):
+        dev = self.device
+        _need(d_emb, torch.float32, "d_emb", dev)
+        _need(workspace, torch.uint8, "workspace", dev)
+        if d_params is None:
+            d_params = torch.empty(self.embed_param_count, dtype=torch.float32, device=dev)
+        _need(d_params, torch.float32, "d_params", dev)
+        self._check(lib().etx_embed_backward(self._h, d_emb.shape[0], _ptr(d_emb), _ptr(d_params),
+                                             _ptr(workspace), workspace.numel(), _stream(stream)))
+        return d_params
+
+    def embedding_pairs(self, emb, plane, particle_id, hit_offsets, radius: float, k_max: int,
+                        rand, capacity: int, min_hits: int = 3, workspace=None, out=None,
+                        stream=None):
+        """Training set of Sec. 5.1; returns (pair_q, pair_a, pair_genuine, n_pairs) device
+        tensors (the first n_pairs entries are valid)."""
+        dev = self.device
+        _need(emb, torch.float32, "emb", dev)
+        _need(plane, torch.int8, "plane", dev)
+        _need(particle_id, torch.int32, "particle_id", dev)
+        _need(hit_offsets, torch.int32, "hit_offsets", dev)
+        _need(rand, torch.int32, "rand (uint32 bits in an int32 tensor)", dev)
+        n_hits, n_events = plane.shape[0], hit_offsets.shape[0] - 1
+        if workspace is None:
+            need = lib().etx_embedding_pairs_workspace(n_events, n_hits, int(k_max))
+            workspace = torch.empty(max(need, 16), dtype=torch.uint8, device=dev)
+        _need(workspace, torch.uint8, "workspace", dev)
+        if out is None:
+            cap = max(int(capacity), 1)
+            out = (torch.empty(cap, dtype=torch.int32, device=dev),
+                   torch.empty(cap, dtype=torch.int32, device=dev),
+                   torch.empty(cap, dtype=torch.uint8, device=dev),
+                   torch.empty(1, dtype=torch.int32, device=dev))
+        pq, pa, pg, npairs = out
+        self._check(lib().etx_embedding_pairs(self._h, _ptr(emb), _ptr(plane), _ptr(particle_id),
+                                              _ptr(hit_offsets), n_events, n_hits, float(radius),
+                                              int(k_max), _ptr(rand), int(min_hits),
+                                              _ptr(workspace), workspace.numel(), _ptr(pq),
+                                              _ptr(pa), _ptr(pg), int(capacity), _ptr(npairs),
+                                              _stream(stream)))
+        return pq, pa, pg, npairs
+
+    def hinge_loss(self, emb, pair_q, pair_a, pair_genuine, n_pairs, margin: float = 1.0,
+                   w_genuine: float = 2.0, loss=None, d_emb=None, stream=None):
+        """Eq. 2-3; returns (loss float32[3] = {L, L_genuine, L_fake}, d_emb) on the device."""
+        dev = self.device
+        _need(emb, torch.float32, "emb", dev)
+        _need(pair_q, torch.int32, "pair_q", dev)
+        _need(pair_a, torch.int32, "pair_a", dev)
+        _need(pair_genuine, torch.uint8, "pair_genuine", dev)
+        _need(n_pairs, torch.int32, "n_pairs", dev)
+        if loss is None:
+            loss = torch.empty(3, dtype=torch.float32, device=dev)
+        if d_emb is None:
+            d_emb = torch.empty_like(emb)
+        _need(d_emb, torch.float32, "d_emb", dev)
+        self._check(lib().etx_hinge_loss(self._h, _ptr(emb), emb.shape[0], _ptr(pair_q),
+                                         _ptr(pair_a), _ptr(pair_genuine), _ptr(n_pairs),
+                                         pair_q.shape[0], float(margin), float(w_genuine),
+                                         _ptr(loss), _ptr(d_emb), _stream(stream)))
+        return loss, d_emb
 
     @staticmethod
     def track_metrics_workspace(n_events: int, n_hits: int) -> int:

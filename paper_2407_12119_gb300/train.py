@@ -61,3 +61,68 @@ class Trainer:
         self.ctx.adam_step(self.theta, grads, self.m, self.v, self.t, lr=self.lr)
         self.sync()
         return loss
+
+
+class EmbeddingTrainer:
+    """Training of the hit embedding (Sec. 5.1): the training pairs of the
+    current embedding (hard negatives from the graph rule, one random pair
+    per query, the genuine edges), the hinge loss of Eq. 2-3, the reverse pass
+    and Adam -- every step runs in libetx.  Batches have their noise hits
+    removed and event-local particle ids (velo_synth.drop_noise,
+    compact_particle_ids).  Defaults follow the paper: k_max 50 and d2 below
+    1.5 for the hard negatives, margin 1; w_genuine (> 1 in the paper, value
+    not given) is 2."""
+
+    EMB_OFFSET = 12  # the embedding parameters follow the 12 normalisation values
+
+    def __init__(self, model, blob: np.ndarray, max_events: int, max_hits: int, device: int = 0,
+                 lr: float = 1e-3, radius: float = float(np.sqrt(1.5)), k_max: int = 50,
+                 margin: float = 1.0, w_genuine: float = 2.0, seed: int = 0):
+        self.ctx = Context(model, max_events, max_hits, 1, device=device)
+        dev = self.ctx.device
+        self.blob = np.array(blob, dtype=np.float32, copy=True)
+        self.n_theta = self.ctx.embed_param_count
+        o = self.EMB_OFFSET
+        self.theta = torch.from_numpy(self.blob[o:o + self.n_theta].copy()).to(dev)
+        self.m = torch.zeros_like(self.theta)
+        self.v = torch.zeros_like(self.theta)
+        self.lr, self.radius, self.k_max = lr, radius, k_max
+        self.margin, self.w_genuine = margin, w_genuine
+        self.t = 0
+        D = int(model.emb_widths[-1])
+        self.emb = torch.empty(max_hits, D, dtype=torch.float32, device=dev)
+        self.d_emb = torch.empty_like(self.emb)
+        self.ws = self.ctx.embed_train_workspace(max_hits)
+        self.capacity = max_hits * (k_max + 2)
+        self.pairs = (torch.empty(self.capacity, dtype=torch.int32, device=dev),
+                      torch.empty(self.capacity, dtype=torch.int32, device=dev),
+                      torch.empty(self.capacity, dtype=torch.uint8, device=dev),
+                      torch.empty(1, dtype=torch.int32, device=dev))
+        self.gen = torch.Generator(device=dev)
+        self.gen.manual_seed(seed)
+        self.loss = torch.empty(3, dtype=torch.float32, device=dev)
+        self.ctx.load_weights(self.blob)
+
+    def sync(self):
+        """Load the current embedding parameters into the context."""
+        o = self.EMB_OFFSET
+        self.blob[o:o + self.n_theta] = self.theta.detach().cpu().numpy()
+        self.ctx.load_weights(self.blob)
+
+    def step(self, x, y, z, plane, particle_id, hit_offsets):
+        """One step; returns the loss tensor {L, L_genuine, L_fake} of the
+        embedding before the update."""
+        n = x.shape[0]
+        emb = self.ctx.embed_forward_train(x, y, z, self.ws, emb=self.emb[:n])
+        rand = torch.randint(-2 ** 31, 2 ** 31 - 1, (n,), dtype=torch.int32, device=x.device,
+                             generator=self.gen)
+        pq, pa, pg, npairs = self.ctx.embedding_pairs(emb, plane, particle_id, hit_offsets,
+                                                      self.radius, self.k_max, rand,
+                                                      self.capacity, out=self.pairs)
+        self.ctx.hinge_loss(emb, pq, pa, pg, npairs, self.margin, self.w_genuine, loss=self.loss,
+                            d_emb=self.d_emb[:n])
+        grads = self.ctx.embed_backward(self.d_emb[:n], self.ws)
+        self.t += 1
+        self.ctx.adam_step(self.theta, grads, self.m, self.v, self.t, lr=self.lr)
+        self.sync()
+        return self.loss

@@ -1,0 +1,162 @@
+"""Embedding training (Sec. 5.1, Eq. 2-3) on the GPU against the oracle:
+the training pairs bit-exact (integers and flags; the graph rule's cut and
+nearest-k decided in FP32 on both sides), the hinge loss and its embedding
+gradient, and the embedding MLP's reverse pass within FP32 tolerances."""
+import json
+from pathlib import Path
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import etx_oracle as O
+from velo_synth import WORKLOADS, compact_particle_ids, drop_noise, pack_blob
+
+pytestmark = pytest.mark.gpu
+GOLDEN = Path(__file__).parent / "golden"
+
+
+@pytest.fixture(scope="module")
+def etx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2407_12119_gb300 import build as b
+    b.build()
+    from paper_2407_12119_gb300 import etx as m
+    return m
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rand_bits(rng, n):
+    u = rng.integers(0, 2 ** 32, size=n, dtype=np.uint64).astype(np.uint32)
+    return u, cuda(u.view(np.int32))
+
+
+def gpu_pairs(ctx, emb, plane, pid, hoff, radius, k_max, rand_t, capacity=None):
+    n = plane.shape[0]
+    cap = n * (k_max + 2) if capacity is None else capacity
+    pq, pa, pg, npairs = ctx.embedding_pairs(cuda(emb), cuda(plane), cuda(pid), cuda(hoff), radius,
+                                             k_max, rand_t, cap)
+    ctx.sync()
+    k = int(npairs.item())
+    return pq[:k].cpu().numpy(), pa[:k].cpu().numpy(), pg[:k].cpu().numpy().astype(bool)
+
+
+def test_pairs_worked_by_hand(etx):
+    g = json.loads((GOLDEN / "embedding_pairs.json").read_text())
+    ev = g["event"]
+    m = WORKLOADS["plain"].model
+    ctx = etx.Context(m, 4, 64, 64)
+    D = m.emb_widths[-1]
+    for case in g["cases"]:
+        r = np.array(case["rand"], np.uint32)
+        q, a, f = gpu_pairs(ctx, np.zeros((8, D), np.float32), np.array(ev["plane"], np.int8),
+                            np.array(ev["particle_id"], np.int32), np.array([0, 8], np.int32), 0.0, 5,
+                            cuda(r.view(np.int32)))
+        assert [[int(x), int(y), bool(z)] for x, y, z in zip(q, a, f)] == case["pairs"]
+
+
+@pytest.mark.parametrize("k_max,radius,seed", [(50, float(np.sqrt(1.5)), 0), (4, 1.0, 1), (1, 2.0, 2)])
+def test_pairs_match_oracle(etx, k_max, radius, seed):
+    rng = np.random.default_rng(seed)
+    wl = WORKLOADS["plain"]
+    b = drop_noise(wl.batch(6))
+    pid = compact_particle_ids(b)
+    D = wl.model.emb_widths[-1]
+    emb = (rng.normal(size=(b.n_hits, D)) * 0.8).astype(np.float32)
+    r, rt = rand_bits(rng, b.n_hits)
+    ctx = etx.Context(wl.model, b.n_events, b.n_hits, 1)
+    q, a, f = gpu_pairs(ctx, emb, b.plane, pid, b.hit_offsets, radius, k_max, rt)
+    qo, ao, fo = O.embedding_pairs(emb, b.plane, pid, b.hit_offsets, radius, k_max, r,
+                                   precision="fp32")
+    assert np.array_equal(q, qo) and np.array_equal(a, ao) and np.array_equal(f, fo)
+    assert 0 < f.sum() < f.size
+
+
+def test_pairs_capacity_and_noise_are_reported(etx):
+    wl = WORKLOADS["plain"]
+    b = drop_noise(wl.batch(2))
+    pid = compact_particle_ids(b)
+    emb = np.zeros((b.n_hits, wl.model.emb_widths[-1]), np.float32)
+    _, rt = rand_bits(np.random.default_rng(0), b.n_hits)
+    ctx = etx.Context(wl.model, b.n_events, b.n_hits, 1)
+    out = ctx.embedding_pairs(cuda(emb), cuda(b.plane), cuda(pid), cuda(b.hit_offsets), 1.0, 8, rt, 5)
+    with pytest.raises(etx.EtxError) as e:
+        ctx.sync()
+    assert e.value.status == etx.ETX_ERR_CAPACITY
+    assert int(out[3].item()) == 0                        # nothing exposed on overflow
+    bad = pid.copy()
+    bad[3] = -1                                           # a noise hit left in
+    ctx.embedding_pairs(cuda(emb), cuda(b.plane), cuda(bad), cuda(b.hit_offsets), 1.0, 8, rt, 10 ** 5)
+    with pytest.raises(etx.EtxError):
+        ctx.sync()
+
+
+def test_hinge_loss_matches_oracle(etx):
+    rng = np.random.default_rng(5)
+    wl = WORKLOADS["plain"]
+    b = drop_noise(wl.batch(4))
+    pid = compact_particle_ids(b)
+    D = wl.model.emb_widths[-1]
+    emb = (rng.normal(size=(b.n_hits, D)) * 0.4).astype(np.float32)
+    r, _ = rand_bits(rng, b.n_hits)
+    q, a, g = O.embedding_pairs(emb, b.plane, pid, b.hit_offsets, 1.0, 20, r, precision="fp32")
+    ctx = etx.Context(wl.model, b.n_events, b.n_hits, 1)
+    cap = q.size + 7                                     # grid sized by the capacity
+    pad = lambda v, dt: np.concatenate([v.astype(dt), np.zeros(7, dt)])
+    loss, d = ctx.hinge_loss(cuda(emb), cuda(pad(q, np.int32)), cuda(pad(a, np.int32)),
+                             cuda(pad(g, np.uint8)), cuda(np.array([q.size], np.int32)), 1.0, 2.5)
+    ctx.sync()
+    L, Lg, Lf, dref = O.hinge_embedding_loss(emb, q, a, g, 1.0, 2.5)
+    np.testing.assert_allclose(loss.cpu().numpy(), [L, Lg, Lf], rtol=2e-6)
+    # FP32 terms scattered with atomics: error far below 1e-5 of the largest entry
+    dg = d.cpu().numpy()
+    assert np.abs(dg - dref).max() <= 1e-5 * np.abs(dref).max()
+    assert cap > q.size
+
+
+def test_embed_backward_matches_oracle(etx):
+    rng = np.random.default_rng(7)
+    wl = WORKLOADS["batch500"]
+    m = wl.model
+    b = drop_noise(wl.batch(3))
+    W = wl.weights(perturb=0.2)
+    blob = pack_blob(m, W)
+    ctx = etx.Context(m, b.n_events, b.n_hits, 1)
+    ctx.load_weights(blob)
+    ws = ctx.embed_train_workspace(b.n_hits)
+    x, y, z = cuda(b.x), cuda(b.y), cuda(b.z)
+    emb = ctx.embed_forward_train(x, y, z, ws)
+    plain = ctx.embed(x, y, z)
+    assert torch.equal(emb, plain)                       # the saving forward computes the same
+    up = rng.normal(size=(b.n_hits, m.emb_widths[-1])).astype(np.float32)
+    grads = ctx.embed_backward(cuda(up), ws).cpu().numpy()
+    ref = O.embed_backward(W, len(m.emb_widths) - 1, b.x, b.y, b.z, up)
+    off = 0
+    for i in range(len(m.emb_widths) - 1):
+        for name in (f"emb{i}.W", f"emb{i}.b"):
+            r = ref[name].ravel()
+            g = grads[off:off + r.size]
+            off += r.size
+            # FP32 sums over ~5k rows (atomics across blocks): within 1e-4 of the largest entry
+            assert np.abs(g - r).max() <= 1e-4 * np.abs(r).max(), name
+    assert off == grads.size == ctx.embed_param_count
+
+
+def test_embedding_training_reduces_the_loss(etx):
+    from paper_2407_12119_gb300.train import EmbeddingTrainer
+    wl = WORKLOADS["batch500"]
+    m = wl.model
+    b = drop_noise(wl.batch(8))
+    pid = compact_particle_ids(b)
+    tr = EmbeddingTrainer(m, pack_blob(m, wl.weights()), b.n_events, b.n_hits, lr=1e-3)
+    args = [cuda(v) for v in (b.x, b.y, b.z, b.plane, pid, b.hit_offsets)]
+    first = tr.step(*args).cpu().numpy().copy()
+    for _ in range(40):
+        last = tr.step(*args).cpu().numpy().copy()
+    tr.ctx.sync()
+    print("embedding training: loss", first, "->", last)
+    assert last[0] < 0.8 * first[0]
