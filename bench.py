@@ -260,6 +260,42 @@ def train_step_report(args, local):
             "loss_first": float(losses[0].item()), "loss_last": float(losses[-1].item())}
 
 
+def embedding_train_report(args, local):
+    """Time the embedding training step (Sec. 5.1: saving forward, training
+    pairs with k_max 50 and d2 < 1.5, hinge loss, reverse pass, Adam, weight
+    reload) on 64 noise-free events of the 500-event recipe."""
+    import torch
+
+    from paper_2407_12119_gb300.train import EmbeddingTrainer
+    from velo_synth import WORKLOADS, compact_particle_ids, drop_noise, pack_blob
+
+    wl = WORKLOADS["batch500"]
+    m = wl.model
+    b = drop_noise(wl.batch(64))
+    pid = compact_particle_ids(b)
+    tr = EmbeddingTrainer(m, pack_blob(m, wl.weights()), b.n_events, b.n_hits, device=local)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(tr.ctx.device)
+    batch = [t(v) for v in (b.x, b.y, b.z, b.plane, pid, b.hit_offsets)]
+    first = tr.step(*batch).cpu().numpy().copy()
+    tr.step(*batch)
+    torch.cuda.synchronize()
+    steps = max(args.steps, 3)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        last = tr.step(*batch)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    n_pairs = int(tr.pairs[3].item())
+    last = last.cpu().numpy()
+    tr.ctx.sync()
+    return {"workload": f"{b.n_events} events of {wl.name} without noise, {b.n_hits} hits, embedding "
+                        f"{'-'.join(map(str, m.emb_widths))}, k_max 50, d2 < 1.5, margin 1, "
+                        f"w_genuine 2, Adam lr 1e-3",
+            "ms_per_step": 1e3 * el / steps, "events_per_s": b.n_events * steps / el,
+            "pairs_per_step": n_pairs, "loss_first": float(first[0]),
+            "loss_last": float(last[0]), "steps_timed": steps}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -480,9 +516,10 @@ def run_ours(args):
                              "numbers; the graph ceiling keeps only the built graph's genuine edges"}
     tf.ctx.sync()
 
-    train = None
+    train = emb_train = None
     if not args.skip_train:
         train = train_step_report(args, local)
+        emb_train = embedding_train_report(args, local)
 
     if rank != 0:
         return
@@ -548,6 +585,7 @@ def run_ours(args):
            "plane_sweep": plane_sweep,
            "track_metrics": track_metrics,
            "train64": train,
+           "embedding_train": emb_train,
            "kernels": kernels}
     print(json.dumps(out), flush=True)
 
