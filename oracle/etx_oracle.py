@@ -32,6 +32,9 @@ blocking, fusion or reordering beyond what the definition states:
                         query, the genuine edges
   hinge_embedding_loss  Eq. 2-3 and its gradient with respect to the embedding
   embed_backward        reverse pass of the embedding MLP
+  build_triplets        articulations and left / right elbows of the purified
+                        graph (Sec. 5.3)
+  triplet_logits        the articulation and elbow classifiers (Sec. 5.3)
 
 Readings where the paper is silent (also listed in the design notes):
   * radius r is Euclidean: keep d2 < r*r (strict); the k_max cap is joint over
@@ -615,3 +618,61 @@ def embed_backward(weights, n_layers, x, y, z, d_emb):
             W = weights[f"emb{i}.W"].astype(np.float64)
             dz = (dz @ W) * (acts[i] > 0)               # through Linear, then ReLU of layer i-1
     return grads
+
+
+# ----------------------------------------------------------------------------
+# triplets of the purified graph (Sec. 5.3) and their classifiers
+# ----------------------------------------------------------------------------
+TRIPLET_ARTICULATION, TRIPLET_LEFT_ELBOW, TRIPLET_RIGHT_ELBOW = 0, 1, 2
+
+
+def build_triplets(src, dst, mask, n_hits):
+    """Triplets of the kept edges (Sec. 5.3), each a pair of edges sharing a
+    common hit C: articulations A->C, C->B (first = the edge into C), left
+    elbows C->A, C->B and right elbows A->C, B->C (first < second by edge
+    index).  Returned as (first, second, kind) int64 arrays: all
+    articulations, then all left elbows, then all right elbows; within a kind
+    by C, then first, then second."""
+    src = np.asarray(src, np.int64)
+    dst = np.asarray(dst, np.int64)
+    keep = np.nonzero(np.asarray(mask, bool))[0]
+    out_e = [[] for _ in range(n_hits)]
+    in_e = [[] for _ in range(n_hits)]
+    for k in keep.tolist():
+        out_e[src[k]].append(k)
+        in_e[dst[k]].append(k)
+    lists = ([], [], [])
+    for c in range(n_hits):
+        for i in in_e[c]:
+            for o in out_e[c]:
+                lists[TRIPLET_ARTICULATION].append((i, o))
+        for x in range(len(out_e[c])):
+            for y in range(x + 1, len(out_e[c])):
+                lists[TRIPLET_LEFT_ELBOW].append((out_e[c][x], out_e[c][y]))
+        for x in range(len(in_e[c])):
+            for y in range(x + 1, len(in_e[c])):
+                lists[TRIPLET_RIGHT_ELBOW].append((in_e[c][x], in_e[c][y]))
+    first = np.array([p[0] for l in lists for p in l], np.int64)
+    second = np.array([p[1] for l in lists for p in l], np.int64)
+    kind = np.concatenate([np.full(len(l), t, np.int64) for t, l in enumerate(lists)])
+    return first, second, kind
+
+
+def triplet_logits(tw, e, first, second, kind):
+    """The two triplet classifiers (Sec. 5.3; articulations "art", elbows
+    "elb"): Lin(2H, H) -> LN -> ReLU -> Lin(H, 1) on [e_first, e_second],
+    the final edge encodings.  Returns float64 logits."""
+    e = np.asarray(e, np.float64)
+    first = np.asarray(first, np.int64)
+    second = np.asarray(second, np.int64)
+    kind = np.asarray(kind, np.int64)
+    x = np.concatenate([e[first], e[second]], axis=1) if first.size else np.zeros((0, 2 * e.shape[1]))
+    out = np.zeros(first.shape[0])
+    for name, sel in (("art", kind == TRIPLET_ARTICULATION), ("elb", kind != TRIPLET_ARTICULATION)):
+        if not sel.any():
+            continue
+        a = x[sel] @ np.asarray(tw[f"{name}.W1"], np.float64).T + np.asarray(tw[f"{name}.b1"], np.float64)
+        a = np.maximum(layer_norm(a, np.asarray(tw[f"{name}.g1"], np.float64),
+                                  np.asarray(tw[f"{name}.be1"], np.float64))[0], 0.0)
+        out[sel] = a @ np.asarray(tw[f"{name}.W2"], np.float64)[0] + float(np.asarray(tw[f"{name}.b2"])[0])
+    return out

@@ -896,3 +896,80 @@ def test_hinge_gradient_vanishes_at_the_margin():
     emb = np.array([[0.0, 0.0], [3.0, 4.0]])
     L, _, _, d = O.hinge_embedding_loss(emb, [0], [1], [False], margin=25.0)
     assert L == 0.0 and not d.any()
+
+
+# ---------------------------------------------------------------------------
+# triplets (Sec. 5.3)
+# ---------------------------------------------------------------------------
+def random_edges(rng, n_hits=30, n_planes=6, p=0.3):
+    plane = np.sort(rng.integers(0, n_planes, n_hits))
+    e = [(i, j) for i in range(n_hits) for j in range(n_hits)
+         if 1 <= plane[j] - plane[i] <= 2 and rng.uniform() < p]
+    src = np.array([a for a, _ in e], np.int64)
+    dst = np.array([b for _, b in e], np.int64)
+    return src, dst
+
+
+def test_triplets_against_brute_force_pairs():
+    rng = np.random.default_rng(12)
+    for trial in range(5):
+        src, dst = random_edges(rng)
+        mask = rng.uniform(size=src.size) < 0.6
+        f, s, k = O.build_triplets(src, dst, mask, 30)
+        want = []
+        kept = np.nonzero(mask)[0].tolist()
+        for a in kept:
+            for b in kept:
+                if a == b:
+                    continue
+                if dst[a] == src[b]:
+                    want.append((O.TRIPLET_ARTICULATION, int(dst[a]), a, b))
+                if a < b and src[a] == src[b]:
+                    want.append((O.TRIPLET_LEFT_ELBOW, int(src[a]), a, b))
+                if a < b and dst[a] == dst[b]:
+                    want.append((O.TRIPLET_RIGHT_ELBOW, int(dst[a]), a, b))
+        want.sort()
+        assert [(int(t), int(f_), int(s_)) for t, f_, s_ in zip(k, f, s)] == [(t, a, b) for t, _, a, b in want]
+        # closed-form counts from the kept in- and out-degrees
+        indeg = np.bincount(dst[mask], minlength=30)
+        outdeg = np.bincount(src[mask], minlength=30)
+        assert (k == 0).sum() == int((indeg * outdeg).sum())
+        assert (k == 1).sum() == int((outdeg * (outdeg - 1) // 2).sum())
+        assert (k == 2).sum() == int((indeg * (indeg - 1) // 2).sum())
+
+
+def test_triplets_of_a_track_chain_are_articulations():
+    # hits 0..5 on planes 0..5, edges i -> i+1: n-2 articulations, no elbows
+    src, dst = np.arange(5), np.arange(1, 6)
+    f, s, k = O.build_triplets(src, dst, np.ones(5, bool), 6)
+    assert k.tolist() == [0] * 4 and f.tolist() == [0, 1, 2, 3] and s.tolist() == [1, 2, 3, 4]
+    # a fork at hit 1 (1 -> 2 and 1 -> 3) and a merge at hit 4 (2 -> 4, 3 -> 4)
+    src, dst = np.array([0, 1, 1, 2, 3]), np.array([1, 2, 3, 4, 4])
+    f, s, k = O.build_triplets(src, dst, np.ones(5, bool), 5)
+    assert list(zip(k.tolist(), f.tolist(), s.tolist())) == [
+        (0, 0, 1), (0, 0, 2), (0, 1, 3), (0, 2, 4), (1, 1, 2), (2, 3, 4)]
+    f, s, k = O.build_triplets(src, dst, np.zeros(5, bool), 5)
+    assert f.size == 0
+
+
+def test_triplet_classifiers_against_torch():
+    torch = pytest.importorskip("torch")
+    from velo_synth import make_triplet_weights
+    cfg = ModelConfig(emb_widths=(3, 8, 4), hidden=16, n_iters=1, radius=1.0, k_max=4)
+    tw = make_triplet_weights(cfg, perturb=0.3)
+    rng = np.random.default_rng(2)
+    e = rng.normal(size=(20, 16))
+    f, s = rng.integers(0, 20, 30), rng.integers(0, 20, 30)
+    k = rng.integers(0, 3, 30)
+    z = O.triplet_logits(tw, e, f, s, k)
+    for name, sel in (("art", k == 0), ("elb", k != 0)):
+        l1 = torch.nn.Linear(32, 16).double()
+        ln = torch.nn.LayerNorm(16, eps=1e-5).double()
+        l2 = torch.nn.Linear(16, 1).double()
+        with torch.no_grad():
+            l1.weight.copy_(torch.tensor(tw[f"{name}.W1"])); l1.bias.copy_(torch.tensor(tw[f"{name}.b1"]))
+            ln.weight.copy_(torch.tensor(tw[f"{name}.g1"])); ln.bias.copy_(torch.tensor(tw[f"{name}.be1"]))
+            l2.weight.copy_(torch.tensor(tw[f"{name}.W2"])); l2.bias.copy_(torch.tensor(tw[f"{name}.b2"]))
+            x = torch.cat([torch.tensor(e[f[sel]]), torch.tensor(e[s[sel]])], 1)
+            want = l2(torch.relu(ln(l1(x))))[:, 0].numpy()
+        np.testing.assert_allclose(z[sel], want, rtol=1e-12, atol=1e-12)

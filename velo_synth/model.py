@@ -124,3 +124,43 @@ def unpack_blob(cfg: ModelConfig, blob: np.ndarray) -> dict:
         out[name] = blob[o:o + n].reshape(shape)
         o += n
     return out
+
+
+def triplet_layout(cfg: ModelConfig):
+    """Ordered (name, shape) list of the triplet-classifier blob: one MLP for
+    articulations ("art") and one for elbows ("elb"), each Lin(2H, H) -> LN
+    -> ReLU -> Lin(H, 1) on the two edges' final encodings."""
+    H = cfg.hidden
+    out = []
+    for p in ("art", "elb"):
+        out += [(f"{p}.W1", (H, 2 * H)), (f"{p}.b1", (H,)), (f"{p}.g1", (H,)), (f"{p}.be1", (H,)),
+                (f"{p}.W2", (1, H)), (f"{p}.b2", (1,))]
+    return out
+
+
+def make_triplet_weights(cfg: ModelConfig, seed: int = 0, perturb: float = 0.0) -> dict:
+    """Kaiming-normal weights (fan-in, gain sqrt 2); biases 0, LayerNorm (1, 0),
+    optionally perturbed like ``make_weights``."""
+    rng = np.random.default_rng(seed + 104729)
+    prng = np.random.default_rng(seed + 130363)
+    p = {}
+    for name, shape in triplet_layout(cfg):
+        leaf = name.rsplit(".", 1)[1]
+        if leaf.startswith("W"):
+            v = rng.normal(0.0, np.sqrt(2.0 / shape[1]), size=shape)
+        else:
+            v = np.ones(shape) if leaf.startswith("g") else np.zeros(shape)
+            if perturb:
+                v = v + prng.normal(0.0, perturb, size=shape)
+        p[name] = v
+    return {k: np.asarray(v, np.float32) for k, v in p.items()}
+
+
+def pack_triplet_blob(cfg: ModelConfig, weights: dict) -> np.ndarray:
+    parts = []
+    for name, shape in triplet_layout(cfg):
+        a = np.asarray(weights[name], np.float32)
+        if a.shape != tuple(shape):
+            raise ValueError(f"{name}: shape {a.shape} != {shape}")
+        parts.append(a.reshape(-1))
+    return np.concatenate(parts).astype(np.float32)
