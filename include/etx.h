@@ -255,6 +255,48 @@ etx_status etx_edges_to_tracks_sweep(etx_ctx* ctx, const int32_t* src, const int
                                      int32_t* labels, void* stream);
 
 /*
+ * Triplets (Sec. 5.3) of the kept edges (logit > threshold_logit) and their
+ * two classifiers.  The paper's triplet-aware track building (Sec. 5.4) is
+ * not part of this library.
+ *
+ * etx_build_triplets: every pair of kept edges sharing a hit C, as
+ *   articulation  A->C, C->B   (kind 0; first = the edge into C)
+ *   left elbow    C->A, C->B   (kind 1; first < second)
+ *   right elbow   A->C, B->C   (kind 2; first < second)
+ * written type-major (all articulations, then left, then right elbows), by
+ * C, then first, then second: first, second int32 [capacity] edge indices,
+ * kind int8 [capacity]; counts int32 [4] (device) = {total, articulations,
+ * left elbows, right elbows}.  Edges sorted by (src, dst) as etx_build_graph
+ * writes them, edge_offsets[n_events] = edge count.  workspace: at least
+ * etx_triplets_workspace() bytes, 4-byte aligned, caller-owned scratch.
+ * Rebuilds the context's edge index structures for these edges (the final
+ * edge encodings of the last etx_gnn_forward are kept).  More triplets than
+ * `capacity`: ETX_ERR_CAPACITY at etx_ctx_sync and counts all 0.
+ *
+ * etx_load_triplet_weights: HOST blob of etx_triplet_weights_size() floats:
+ * articulation classifier then elbow classifier, each W1[H][2H] b1[H]
+ * g1[H] be1[H] W2[1][H] b2[1] (Lin -> LN -> ReLU -> Lin).  Synchronous.
+ *
+ * etx_classify_triplets: logits float32 [capacity] (rows [0, counts[0])
+ * written) of the triplets from etx_build_triplets, on [e_first, e_second]
+ * of the final edge encodings of the last etx_gnn_forward of this context
+ * (FP32 SIMT, any dtype of that forward).  Articulations use the first
+ * classifier, elbows the second.
+ */
+int64_t etx_triplet_weights_size(const etx_config* cfg);
+etx_status etx_load_triplet_weights(etx_ctx* ctx, const float* host_blob, int64_t n_floats);
+size_t etx_triplets_workspace(int64_t n_hits);
+etx_status etx_build_triplets(etx_ctx* ctx, const int32_t* src, const int32_t* dst,
+                              const float* logits, float threshold_logit,
+                              const int32_t* edge_offsets, int32_t n_events, int64_t n_hits,
+                              void* workspace, size_t workspace_bytes, int32_t* first,
+                              int32_t* second, int8_t* kind, int64_t capacity, int32_t* counts,
+                              void* stream);
+etx_status etx_classify_triplets(etx_ctx* ctx, const int32_t* first, const int32_t* second,
+                                 const int32_t* counts, int64_t capacity, float* logits,
+                                 void* stream);
+
+/*
  * Training of the hit embedding (Sec. 5.1, Eq. 2-3).  A step is
  *   etx_embed_forward_train -> etx_embedding_pairs -> etx_hinge_loss ->
  *   etx_embed_backward -> etx_adam_step on the embedding parameters ->

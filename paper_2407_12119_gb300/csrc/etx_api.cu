@@ -269,7 +269,7 @@ etx_status etx_ctx_destroy(etx_ctx* ctx) {
                   ctx->perm_in, ctx->h, ctx->m, ctx->e, ctx->parent, ctx->h_ck, ctx->e_ck,
                   ctx->de, ctx->dh, ctx->bw_X, ctx->bw_DX, ctx->bw_R1, ctx->bw_DA1, ctx->bw_DY1,
                   ctx->bw_DY1N1, ctx->bw_DA2, ctx->bw_DY2, ctx->bw_DY2N2, ctx->h_lp,
-                  ctx->small};
+                  ctx->small, ctx->w_trip};
   for (void* p : bufs)
     if (p) cudaFree(p);
   for (auto& r : ctx->prof) {
@@ -655,6 +655,72 @@ etx_status etx_edges_to_tracks_sweep(etx_ctx* ctx, const int32_t* src, const int
     e = launch_plane_sweep(ctx, src, dst, logits, threshold_logit, hit_offsets, n_events, n_hits,
                            labels, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "etx_edges_to_tracks_sweep launch");
+  return ETX_OK;
+}
+
+// ---- triplets (Sec. 5.3) -------------------------------------------------------
+
+int64_t etx_triplet_weights_size(const etx_config* cfg) {
+  if (!cfg || cfg->hidden < 1) return -1;
+  return triplet_weights_size(cfg->hidden);
+}
+
+etx_status etx_load_triplet_weights(etx_ctx* ctx, const float* blob, int64_t n_floats) {
+  if (!ctx) return ETX_ERR_ARG;
+  if (!blob) return fail(ctx, ETX_ERR_ARG, "weight blob is NULL");
+  if (n_floats != triplet_weights_size(ctx->cfg.hidden))
+    return fail(ctx, ETX_ERR_ARG, "triplet blob size does not match the config");
+  cudaSetDevice(ctx->device);
+  cudaError_t e = load_triplet_weights(ctx, blob);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "triplet weight upload");
+  return ETX_OK;
+}
+
+size_t etx_triplets_workspace(int64_t n_hits) {
+  return n_hits < 0 ? 0 : triplets_workspace(n_hits);
+}
+
+etx_status etx_build_triplets(etx_ctx* ctx, const int32_t* src, const int32_t* dst,
+                              const float* logits, float threshold_logit,
+                              const int32_t* edge_offsets, int32_t n_events, int64_t n_hits,
+                              void* workspace, size_t workspace_bytes, int32_t* first,
+                              int32_t* second, int8_t* kind, int64_t capacity, int32_t* counts,
+                              void* stream) {
+  if (!ctx) return ETX_ERR_ARG;
+  if (n_events < 0 || n_events > ctx->cfg.max_events) return fail(ctx, ETX_ERR_CAPACITY, "n_events exceeds the context capacity");
+  if (n_hits < 0 || n_hits > ctx->cfg.max_hits) return fail(ctx, ETX_ERR_CAPACITY, "n_hits exceeds the context capacity");
+  if (!edge_offsets || !src || !dst || !logits || !counts || !workspace) return fail(ctx, ETX_ERR_ARG, "NULL array");
+  if (capacity < 0 || capacity >= ((int64_t)1 << 31)) return fail(ctx, ETX_ERR_ARG, "capacity out of range");
+  if (capacity > 0 && (!first || !second || !kind)) return fail(ctx, ETX_ERR_ARG, "NULL triplet arrays");
+  if (threshold_logit != threshold_logit) return fail(ctx, ETX_ERR_ARG, "threshold is NaN");
+  if (workspace_bytes < triplets_workspace(n_hits))
+    return fail(ctx, ETX_ERR_CAPACITY, "workspace smaller than etx_triplets_workspace()");
+  if (reinterpret_cast<uintptr_t>(workspace) & 3) return fail(ctx, ETX_ERR_ARG, "workspace not 4-byte aligned");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  launch(ctx, "clamp_edges", k_clamp_edges, 1, 1, 0, s, edge_offsets, n_events, ctx->cfg.max_edges,
+         ctx->n_edges, ctx->d_err);
+  cudaError_t e = launch_build_triplets(ctx, src, dst, logits, threshold_logit, n_hits, workspace,
+                                        capacity, first, second, kind, counts, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "etx_build_triplets launch");
+  return ETX_OK;
+}
+
+etx_status etx_classify_triplets(etx_ctx* ctx, const int32_t* first, const int32_t* second,
+                                 const int32_t* counts, int64_t capacity, float* logits,
+                                 void* stream) {
+  if (!ctx) return ETX_ERR_ARG;
+  if (!ctx->trip_loaded) return fail(ctx, ETX_ERR_STATE, "triplet weights not loaded");
+  if (!counts || (capacity > 0 && (!first || !second || !logits))) return fail(ctx, ETX_ERR_ARG, "NULL array");
+  if (capacity < 0 || capacity >= ((int64_t)1 << 31)) return fail(ctx, ETX_ERR_ARG, "capacity out of range");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = launch_triplet_classifier(ctx, first, second, nullptr, counts + 1, capacity,
+                                            ctx->trip_art, logits, s);
+  if (e == cudaSuccess)
+    e = launch_triplet_classifier(ctx, first, second, counts + 1, counts, capacity, ctx->trip_elb,
+                                  logits, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "etx_classify_triplets launch");
   return ETX_OK;
 }
 

@@ -118,6 +118,11 @@ struct etx_ctx {
   // components
   int32_t* parent = nullptr;     // [max_hits]
 
+  // triplet classifiers (etx_load_triplet_weights): articulations, elbows
+  float* w_trip = nullptr;
+  etx::ClassifierF32 trip_art, trip_elb;
+  bool trip_loaded = false;
+
   // training (cfg.train): checkpoints of the last forward and backward scratch
   float* h_ck = nullptr;         // [(L+1) * max_hits * H]: h^k
   float* e_ck = nullptr;         // [(L+1) * max_edges * H]: e^k
@@ -202,6 +207,20 @@ cudaError_t launch_plane_bins(etx_ctx* ctx, const int8_t* plane, const int32_t* 
 // gnn_f32.cu: ctx->out_off, the src-CSR of edges sorted by src (checks order and range)
 cudaError_t launch_out_offsets(etx_ctx* ctx, int64_t N, const int32_t* src, const int32_t* dst,
                                const int32_t* n_edges_dev, cudaStream_t s);
+
+// triplets.cu: triplets of the kept edges (Sec. 5.3) and the classifier weights
+size_t triplets_workspace(int64_t n_hits);
+cudaError_t launch_build_triplets(etx_ctx* ctx, const int32_t* src, const int32_t* dst,
+                                  const float* logits, float thr, int64_t n_hits, void* workspace,
+                                  int64_t capacity, int32_t* first, int32_t* second, int8_t* kind,
+                                  int32_t* counts, cudaStream_t s);
+cudaError_t load_triplet_weights(etx_ctx* ctx, const float* blob);
+int64_t triplet_weights_size(int H);
+// gnn_f32.cu: a triplet classifier over rows [*row_lo_dev (or 0), *row_hi_dev) of first/second
+cudaError_t launch_triplet_classifier(etx_ctx* ctx, const int32_t* first, const int32_t* second,
+                                      const int32_t* row_lo_dev, const int32_t* row_hi_dev,
+                                      int64_t capacity, const ClassifierF32& cls, float* logits,
+                                      cudaStream_t s);
 
 // embed_train.cu: the embedding's training set and hinge loss (Sec. 5.1, Eq. 2-3)
 size_t embedding_pairs_workspace(int32_t n_events, int64_t n_hits, int32_t k_max);

@@ -18,7 +18,8 @@ namespace {
 constexpr int kKC = 16;
 constexpr int kLdaChunk = kKC + 4;
 
-enum Mode { NODE_ENC = 0, EDGE_ENC = 1, NODE_UPD = 2, EDGE_UPD = 3, CLS = 4 };
+// TRI: a triplet classifier (Sec. 5.3) on [e_first, e_second], rows [*row_lo_dev, *n_rows_dev)
+enum Mode { NODE_ENC = 0, EDGE_ENC = 1, NODE_UPD = 2, EDGE_UPD = 3, CLS = 4, TRI = 5 };
 
 struct MlpArgs {
   int64_t n_rows;               // hits (rows of the node modes)
@@ -33,6 +34,8 @@ struct MlpArgs {
   float* logits;                // [E]
   BlockF32 blk;
   ClassifierF32 cls;
+  const int32_t* row_lo_dev;    // TRI: first row (nullptr: 0)
+  int64_t e_rows;               // TRI: rows of e (edge ids are clamped below it)
 };
 
 // ---------------------------------------------------------------------------
@@ -182,6 +185,8 @@ __device__ __forceinline__ float4 gather4(const MlpArgs& a, int64_t row, bool va
   } else if constexpr (MODE == EDGE_UPD) {
     p = k < H ? a.e + row * H + k
               : (k < 2 * H ? a.h + (int64_t)srow * H + (k - H) : a.h + (int64_t)drow * H + (k - 2 * H));
+  } else if constexpr (MODE == TRI) {
+    p = k < H ? a.e + (int64_t)srow * H + k : a.e + (int64_t)drow * H + (k - H);
   } else {  // CLS
     p = a.e + row * H + k;
   }
@@ -197,19 +202,21 @@ __global__ void __launch_bounds__(kTileThreads) k_mlp(MlpArgs a) {
   __shared__ int s_src[kTileM], s_dst[kTileM];
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   const int64_t n_rows = (MODE == NODE_ENC || MODE == NODE_UPD) ? a.n_rows : (int64_t)*a.n_rows_dev;
-  const int64_t n_tiles = (n_rows + kTileM - 1) / kTileM;
-  const LinF32& l1 = MODE == CLS ? a.cls.l1 : a.blk.l1;
+  const int64_t lo_row = (MODE == TRI && a.row_lo_dev) ? (int64_t)*a.row_lo_dev : 0;
+  const int64_t n_tiles = n_rows > lo_row ? (n_rows - lo_row + kTileM - 1) / kTileM : 0;
+  const LinF32& l1 = (MODE == CLS || MODE == TRI) ? a.cls.l1 : a.blk.l1;
 
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const int64_t row0 = tile * kTileM;
+    const int64_t row0 = lo_row + tile * kTileM;
     __syncthreads();
-    if constexpr (MODE == EDGE_ENC || MODE == EDGE_UPD) {
+    if constexpr (MODE == EDGE_ENC || MODE == EDGE_UPD || MODE == TRI) {
       if (tid < kTileM) {
         const int64_t r = row0 + tid;
         // out-of-range ids are flagged by the index pass; clamp so reads stay in bounds
-        const int nn = (int)a.n_rows;
-        s_src[tid] = r < n_rows ? min(max(a.src[r], 0), max(nn - 1, 0)) : 0;
-        s_dst[tid] = r < n_rows ? min(max(a.dst[r], 0), max(nn - 1, 0)) : 0;
+        const int64_t nn = MODE == TRI ? a.e_rows : a.n_rows;
+        const int hi = (int)max(nn - 1, (int64_t)0);
+        s_src[tid] = r < n_rows ? min(max(a.src[r], 0), hi) : 0;
+        s_dst[tid] = r < n_rows ? min(max(a.dst[r], 0), hi) : 0;
       }
     }
     TileAcc<H> acc;
@@ -235,7 +242,7 @@ __global__ void __launch_bounds__(kTileThreads) k_mlp(MlpArgs a) {
       const bool valid = grow < n_rows;
       for (int k0 = 0; k0 < K1; k0 += kKC) {
         __syncthreads();
-        if constexpr (MODE == EDGE_ENC || MODE == EDGE_UPD) {
+        if constexpr (MODE == EDGE_ENC || MODE == EDGE_UPD || MODE == TRI) {
           *reinterpret_cast<float4*>(As + qrow * kLdaChunk + qk) =
               gather4<H, MODE>(a, grow, valid, k0 + qk, s_src[qrow], s_dst[qrow]);
         } else {
@@ -247,7 +254,7 @@ __global__ void __launch_bounds__(kTileThreads) k_mlp(MlpArgs a) {
         acc.template mma<kKC>(As, kLdaChunk, 0, Ws, ty, tx);
       }
     }
-    if constexpr (MODE == CLS) {
+    if constexpr (MODE == CLS || MODE == TRI) {
       bias_ln_relu<H>(acc, a.cls.l1.b, a.cls.g1, a.cls.be1, tx);
       const float b2 = __ldg(a.cls.b2);
 #pragma unroll
@@ -291,7 +298,7 @@ __global__ void __launch_bounds__(kTileThreads) k_mlp(MlpArgs a) {
 
 constexpr const char* kMlpName[] = {"gnn_node_encoder_f32", "gnn_edge_encoder_f32",
                                     "gnn_node_update_f32", "gnn_edge_update_f32",
-                                    "gnn_classifier_f32"};
+                                    "gnn_classifier_f32", "triplet_classifier_f32"};
 
 template <int H, int MODE>
 void launch_mlp(etx_ctx* ctx, const MlpArgs& a, int64_t max_rows, cudaStream_t s) {
@@ -426,6 +433,29 @@ cudaError_t launch_gnn_forward(etx_ctx* ctx, const float* x, const float* y, con
     case 128: return forward<128>(ctx, x, y, z, n_hits, src, dst, n_edges_dev, logits, dtype, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_triplet_classifier(etx_ctx* ctx, const int32_t* first, const int32_t* second,
+                                      const int32_t* row_lo_dev, const int32_t* row_hi_dev,
+                                      int64_t capacity, const ClassifierF32& cls, float* logits,
+                                      cudaStream_t s) {
+  MlpArgs a{};
+  a.n_rows_dev = row_hi_dev;
+  a.row_lo_dev = row_lo_dev;
+  a.src = first;
+  a.dst = second;
+  a.e = ctx->e;
+  a.e_rows = ctx->cfg.max_edges;
+  a.logits = logits;
+  a.cls = cls;
+  switch (ctx->cfg.hidden) {
+    case 16: launch_mlp<16, TRI>(ctx, a, capacity, s); break;
+    case 32: launch_mlp<32, TRI>(ctx, a, capacity, s); break;
+    case 64: launch_mlp<64, TRI>(ctx, a, capacity, s); break;
+    case 128: launch_mlp<128, TRI>(ctx, a, capacity, s); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace etx

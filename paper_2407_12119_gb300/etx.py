@@ -34,7 +34,9 @@ EXPORTED = ["etx_ctx_create", "etx_ctx_destroy", "etx_last_error", "etx_weights_
             "etx_autotune", "etx_tuned", "etx_set_tuned", "etx_edges_to_tracks_sweep",
             "etx_track_metrics_workspace", "etx_track_metrics", "etx_embed_param_count",
             "etx_embed_train_workspace", "etx_embed_forward_train", "etx_embed_backward",
-            "etx_embedding_pairs_workspace", "etx_embedding_pairs", "etx_hinge_loss"]
+            "etx_embedding_pairs_workspace", "etx_embedding_pairs", "etx_hinge_loss",
+            "etx_triplet_weights_size", "etx_load_triplet_weights", "etx_triplets_workspace",
+            "etx_build_triplets", "etx_classify_triplets"]
 # etx_track_metrics outputs
 TRACK_COUNTS = ["particles", "matched_particles", "candidates", "candidate_particles", "tracks",
                 "unmatched_tracks"]
@@ -109,6 +111,12 @@ def lib() -> ctypes.CDLL:
         "etx_embedding_pairs": (i32, [vp, vp, vp, vp, vp, i32, i64, f32, i32, vp, i32, vp,
                                       ctypes.c_size_t, vp, vp, vp, i64, vp, vp]),
         "etx_hinge_loss": (i32, [vp, vp, i64, vp, vp, vp, vp, i64, f32, f32, vp, vp, vp]),
+        "etx_triplet_weights_size": (i64, [cfgp]),
+        "etx_load_triplet_weights": (i32, [vp, vp, i64]),
+        "etx_triplets_workspace": (ctypes.c_size_t, [i64]),
+        "etx_build_triplets": (i32, [vp, vp, vp, vp, f32, vp, i32, i64, vp, ctypes.c_size_t, vp,
+                                     vp, vp, i64, vp, vp]),
+        "etx_classify_triplets": (i32, [vp, vp, vp, vp, i64, vp, vp]),
         "etx_track_metrics": (i32, [vp, vp, vp, vp, i32, i64, i32, i32, i32, vp, ctypes.c_size_t,
                                     vp, vp, vp]),
         "etx_launch_count": (i64, [vp]),
@@ -322,6 +330,51 @@ class Context:
                                                     _ptr(plane), _ptr(hit_offsets), n_events,
                                                     n_hits, _ptr(labels), _stream(stream)))
         return labels
+
+    # ---- triplets (Sec. 5.3) -----------------------------------------------
+    def load_triplet_weights(self, blob: np.ndarray):
+        b = np.ascontiguousarray(blob, dtype=np.float32)
+        self._check(lib().etx_load_triplet_weights(self._h, b.ctypes.data_as(ctypes.c_void_p), b.size))
+
+    def build_triplets(self, src, dst, logits, threshold_logit: float, edge_offsets, n_hits: int,
+                       capacity: int, workspace=None, out=None, stream=None):
+        """Returns (first, second, kind, counts) device tensors; counts =
+        {total, articulations, left elbows, right elbows}."""
+        dev = self.device
+        _need(src, torch.int32, "src", dev)
+        _need(dst, torch.int32, "dst", dev)
+        _need(logits, torch.float32, "logits", dev)
+        _need(edge_offsets, torch.int32, "edge_offsets", dev)
+        n_events = edge_offsets.shape[0] - 1
+        if workspace is None:
+            need = lib().etx_triplets_workspace(int(n_hits))
+            workspace = torch.empty(max(need, 16), dtype=torch.uint8, device=dev)
+        _need(workspace, torch.uint8, "workspace", dev)
+        if out is None:
+            cap = max(int(capacity), 1)
+            out = (torch.empty(cap, dtype=torch.int32, device=dev),
+                   torch.empty(cap, dtype=torch.int32, device=dev),
+                   torch.empty(cap, dtype=torch.int8, device=dev),
+                   torch.empty(4, dtype=torch.int32, device=dev))
+        first, second, kind, counts = out
+        self._check(lib().etx_build_triplets(self._h, _ptr(src), _ptr(dst), _ptr(logits),
+                                             float(threshold_logit), _ptr(edge_offsets), n_events,
+                                             int(n_hits), _ptr(workspace), workspace.numel(),
+                                             _ptr(first), _ptr(second), _ptr(kind), int(capacity),
+                                             _ptr(counts), _stream(stream)))
+        return first, second, kind, counts
+
+    def classify_triplets(self, first, second, counts, logits=None, stream=None):
+        dev = self.device
+        _need(first, torch.int32, "first", dev)
+        _need(second, torch.int32, "second", dev)
+        _need(counts, torch.int32, "counts", dev)
+        if logits is None:
+            logits = torch.empty(first.shape[0], dtype=torch.float32, device=dev)
+        _need(logits, torch.float32, "logits", dev)
+        self._check(lib().etx_classify_triplets(self._h, _ptr(first), _ptr(second), _ptr(counts),
+                                                first.shape[0], _ptr(logits), _stream(stream)))
+        return logits
 
     # ---- embedding training (Sec. 5.1, Eq. 2-3) ----------------------------
     @property

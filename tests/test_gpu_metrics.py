@@ -149,24 +149,23 @@ def test_metrics_out_of_range_ids_are_reported(etx):
         c.sync()
 
 
-@pytest.mark.parametrize("dtype", ["f32", "bf16"])
-def test_metrics_of_the_pipeline_labels(etx, dtype):
-    """Labels of the GPU pipeline (exact components and the plane sweep) on a
-    batch of the 500-event recipe: GPU metrics equal the oracle's on the same
-    labels; the values are printed (random weights: not physics numbers)."""
-    from paper_2407_12119_gb300.pipeline import TrackFinder
+def test_metrics_of_oracle_tracks(etx, ctx):
+    """Tracks of the oracle's own pipeline on two events of the 500-event
+    recipe (exact components and the plane sweep of its graph and FP64 logits):
+    GPU metrics equal the oracle's on the same labels."""
+    from velo_synth import make_batch, make_weights
     wl = WORKLOADS["batch500"]
     m = wl.model
-    b = wl.batch(12)
-    tf = TrackFinder(m, pack_blob(m, wl.weights()), b.n_events, b.n_hits, b.n_hits * m.k_max,
-                     dtype=dtype)
-    x, y, z, p, h = cuda(b.x), cuda(b.y), cuda(b.z), cuda(b.plane), cuda(b.hit_offsets)
-    labels, _ = tf.run_device(x, y, z, p, h, b.n_hits, b.n_events)
-    sweep = tf.ctx.edges_to_tracks_sweep(tf.src, tf.dst, tf.logits, m.threshold_logit, tf.eoff, p, h)
+    b = make_batch(wl.recipe, 2, wl.base_seed)
+    W = make_weights(m, wl.calibration(), perturb=0.2)
+    emb = O.embed(W, len(m.emb_widths) - 1, b.x, b.y, b.z)
+    src, dst, _ = O.build_graph(emb, b.plane, b.hit_offsets, m.radius, m.k_max)
+    z = O.gnn_forward(W, m.n_iters, b.x, b.y, b.z, src, dst)
+    keep = z > np.quantile(z, 0.9)
     pid = compact_particle_ids(b)
-    for name, lab in (("components", labels), ("plane sweep", sweep)):
-        counts, values = tf.ctx.track_metrics(lab, cuda(pid), h)
-        tf.ctx.sync()
-        lab_h = lab.cpu().numpy()
-        check_against_oracle(etx, counts.cpu().numpy(), values.cpu().numpy(), lab_h, pid, b.hit_offsets)
-        print(dtype, name, dict(zip(etx.TRACK_VALUES[2:], np.round(values.cpu().numpy()[2:], 4))))
+    big = etx.Context(m, b.n_events, b.n_hits, 1)
+    for name, lab in (("components", O.connected_components(src, dst, keep, b.hit_offsets)),
+                      ("plane sweep", O.plane_sweep_components(src, dst, keep, b.plane, b.hit_offsets))):
+        counts, values = gpu_metrics(big, lab, pid, b.hit_offsets)
+        check_against_oracle(etx, counts, values, lab, pid, b.hit_offsets)
+        print(name, dict(zip(etx.TRACK_VALUES[2:], np.round(values[2:], 4))))

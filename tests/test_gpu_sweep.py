@@ -71,23 +71,28 @@ def test_sweep_random_plane_graphs_match_oracle(etx):
     np.testing.assert_array_equal(lab, O.plane_sweep_components(s, d, k, plane, offs))
 
 
-def test_sweep_on_the_pipeline_graph(etx):
-    """Batch of the 500-event recipe through the GPU pipeline (FP32): the sweep
-    on the GPU equals the oracle's sweep of the same edges and mask."""
-    from paper_2407_12119_gb300.pipeline import TrackFinder
+def test_sweep_on_a_batch500_graph(etx):
+    """Two events of the 500-event recipe: the oracle's graph and FP64 logits
+    (cut at the model's threshold) go to both sides; the GPU sweep equals the
+    oracle's sweep exactly, and the share of hits it labels differently from
+    the exact components is printed."""
+    from velo_synth import make_batch, make_weights
     wl = WORKLOADS["batch500"]
     m = wl.model
-    b = wl.batch(8)
-    tf = TrackFinder(m, pack_blob(m, wl.weights()), b.n_events, b.n_hits, b.n_hits * m.k_max)
-    x, y, z, p, h = cuda(b.x), cuda(b.y), cuda(b.z), cuda(b.plane), cuda(b.hit_offsets)
-    labels, _ = tf.run_device(x, y, z, p, h, b.n_hits, b.n_events)
-    E = int(tf.eoff[b.n_events].item())
-    sweep = tf.ctx.edges_to_tracks_sweep(tf.src, tf.dst, tf.logits, m.threshold_logit, tf.eoff, p, h)
-    tf.ctx.sync()
-    src, dst = tf.src[:E].cpu().numpy(), tf.dst[:E].cpu().numpy()
-    keep = tf.logits[:E].cpu().numpy() > m.threshold_logit
+    b = make_batch(wl.recipe, 2, wl.base_seed)
+    W = make_weights(m, wl.calibration(), perturb=0.2)
+    emb = O.embed(W, len(m.emb_widths) - 1, b.x, b.y, b.z)
+    src, dst, eoff = O.build_graph(emb, b.plane, b.hit_offsets, m.radius, m.k_max)
+    z = O.gnn_forward(W, m.n_iters, b.x, b.y, b.z, src, dst).astype(np.float32)
+    thr = float(np.quantile(z, 0.9))
+    keep = z > np.float32(thr)
+    ctx = etx.Context(m, b.n_events, b.n_hits, src.size)
+    lab = ctx.edges_to_tracks_sweep(cuda(src.astype(np.int32)), cuda(dst.astype(np.int32)), cuda(z),
+                                    thr, cuda(eoff.astype(np.int32)), cuda(b.plane),
+                                    cuda(b.hit_offsets))
+    ctx.sync()
     ref = O.plane_sweep_components(src, dst, keep, b.plane, b.hit_offsets)
-    np.testing.assert_array_equal(sweep.cpu().numpy(), ref)
-    exact = labels.cpu().numpy()
+    np.testing.assert_array_equal(lab.cpu().numpy(), ref)
+    exact = O.connected_components(src, dst, keep, b.hit_offsets)
     print(f"sweep vs exact components: {float((ref != exact).mean()):.4%} of hits differ")
     assert np.all(ref >= exact)
