@@ -498,6 +498,46 @@ def run_ours(args):
                    "hits_labelled_differently": float((sweep_lab != labels).float().mean().item()),
                    "track_metrics": physics(sweep_lab),
                    "track_metrics_exact": physics(labels)}
+    # triplets of the kept edges and their two classifiers (Sec. 5.3), on the
+    # final edge encodings of the step above
+    from velo_synth import make_triplet_weights, pack_triplet_blob
+    tf.ctx.load_triplet_weights(pack_triplet_blob(m, make_triplet_weights(m)))
+    trip_cap = 2 * E
+    trip_out = (torch.empty(trip_cap, dtype=torch.int32, device=dev),
+                torch.empty(trip_cap, dtype=torch.int32, device=dev),
+                torch.empty(trip_cap, dtype=torch.int8, device=dev),
+                torch.empty(4, dtype=torch.int32, device=dev))
+    trip_ws = torch.empty(max(int(tf.ctx.triplets_workspace(N)), 16), dtype=torch.uint8, device=dev)
+    trip_logits = torch.empty(trip_cap, dtype=torch.float32, device=dev)
+
+    def triplets():
+        f, s_, _, c = tf.ctx.build_triplets(tf.src, tf.dst, tf.logits, m.threshold_logit, tf.eoff,
+                                            N, trip_cap, workspace=trip_ws, out=trip_out)
+        return f, s_, c
+
+    def classify():
+        tf.ctx.classify_triplets(trip_out[0], trip_out[1], trip_out[3], logits=trip_logits)
+
+    triplets()
+    classify()
+    torch.cuda.synchronize()
+    t0, t1, t2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    t0.record(stream)
+    for _ in range(args.steps):
+        triplets()
+    t1.record(stream)
+    for _ in range(args.steps):
+        classify()
+    t2.record(stream)
+    torch.cuda.synchronize()
+    tc = trip_out[3].cpu().tolist()
+    tf.ctx.sync()
+    triplet_report = {"build_ms": t0.elapsed_time(t1) / args.steps,
+                      "classify_ms": t1.elapsed_time(t2) / args.steps,
+                      "triplets": tc[0], "articulations": tc[1], "left_elbows": tc[2],
+                      "right_elbows": tc[3],
+                      "note": "outside the timed step (the paper's port leaves the triplet stage out)"}
+
     # graph-stage ceiling: exact components of the built graph's genuine edges
     src_h, dst_h = tf.src[:E].cpu().numpy(), tf.dst[:E].cpu().numpy()
     genuine = truth_edge_labels(global_particle_ids(batch), batch.plane, src_h, dst_h)
@@ -584,6 +624,7 @@ def run_ours(args):
            "per_dtype": per_dtype,
            "plane_sweep": plane_sweep,
            "track_metrics": track_metrics,
+           "triplets": triplet_report,
            "train64": train,
            "embedding_train": emb_train,
            "kernels": kernels}

@@ -336,6 +336,10 @@ class Context:
         b = np.ascontiguousarray(blob, dtype=np.float32)
         self._check(lib().etx_load_triplet_weights(self._h, b.ctypes.data_as(ctypes.c_void_p), b.size))
 
+    @staticmethod
+    def triplets_workspace(n_hits: int) -> int:
+        return int(lib().etx_triplets_workspace(int(n_hits)))
+
     def build_triplets(self, src, dst, logits, threshold_logit: float, edge_offsets, n_hits: int,
                        capacity: int, workspace=None, out=None, stream=None):
         """Returns (first, second, kind, counts) device tensors; counts =
