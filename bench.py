@@ -53,6 +53,12 @@ def parse():
     p.add_argument("--skip-train", action="store_true", help="no training-step timing")
     p.add_argument("--events", type=int, default=None,
                    help="use only the first N events of the workload (profiling captures)")
+    p.add_argument("--physics", action="store_true",
+                   help="train the embedding and the interaction network on synthetic events, "
+                        "then report the Table 1 metrics per dtype (prints its own JSON line)")
+    p.add_argument("--emb-steps", type=int, default=400)
+    p.add_argument("--gnn-steps", type=int, default=400)
+    p.add_argument("--train-batches", type=int, default=8)
     return p.parse_args()
 
 
@@ -294,6 +300,120 @@ def embedding_train_report(args, local):
             "ms_per_step": 1e3 * el / steps, "events_per_s": b.n_events * steps / el,
             "pairs_per_step": n_pairs, "loss_first": float(first[0]),
             "loss_last": float(last[0]), "steps_timed": steps}
+
+
+def physics_report(args, local):
+    """Train the embedding (Sec. 5.1: f2 kernels) and then the interaction
+    network (weighted BCE, BF16 forward) on synthetic 64-event batches that
+    the evaluation batch does not contain, build the graph with the paper's
+    inference values (d2 < 0.9, k_max 50), cut edges at score 0.5, and measure
+    the Table 1 metrics of each dtype on the 500-event batch."""
+    import dataclasses
+
+    import torch
+
+    from paper_2407_12119_gb300.pipeline import TrackFinder
+    from paper_2407_12119_gb300.train import EmbeddingTrainer, Trainer
+    from velo_synth import (WORKLOADS, compact_particle_ids, drop_noise, global_particle_ids,
+                            make_batch, pack_blob, truth_edge_labels)
+
+    wl = WORKLOADS["batch500"]
+    m = dataclasses.replace(wl.model, radius=float(np.sqrt(0.9)), k_max=50, threshold_logit=0.0)
+    blob = pack_blob(m, wl.weights())
+    dev = torch.device("cuda", local)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    train = [make_batch(wl.recipe, 64, 70000 + 64 * i) for i in range(args.train_batches)]
+    max_hits = max(b.n_hits for b in train)
+    out = {"workload": f"train on {args.train_batches} x 64 events of {wl.name} (seeds from 70000), "
+                       f"evaluate on its {wl.n_events} events; graph d2 < 0.9, k_max 50; "
+                       f"edge cut at score 0.5"}
+    # 1. embedding (noise removed)
+    et = EmbeddingTrainer(m, blob, 64, max_hits, device=local)
+    nf = []
+    for b in train:
+        c = drop_noise(b)
+        nf.append([t(v) for v in (c.x, c.y, c.z, c.plane, compact_particle_ids(c), c.hit_offsets)])
+    t0 = time.perf_counter()
+    first = None
+    for k in range(args.emb_steps):
+        loss = et.step(*nf[k % len(nf)])
+        if first is None:
+            first = loss.cpu().numpy().copy()
+    last = loss.cpu().numpy()
+    out["embedding"] = {"steps": args.emb_steps, "s": time.perf_counter() - t0,
+                        "loss_first": first.tolist(), "loss_last": last.tolist()}
+    blob = et.blob.copy()
+    et.ctx.sync()
+    del et, nf
+    # 2. interaction network on the trained embedding's graphs
+    probe = TrackFinder(m, blob, 64, max_hits, max_hits * m.k_max, device=local)
+    graphs, n_pos, n_all = [], 0, 0
+    for b in train:
+        x, y, z, p, h = t(b.x), t(b.y), t(b.z), t(b.plane), t(b.hit_offsets)
+        emb = probe.ctx.embed(x, y, z)
+        src, dst, eo = probe.ctx.build_graph(emb, p, h, m.radius, m.k_max)
+        probe.ctx.sync()
+        E = int(eo[-1].item())
+        yb = truth_edge_labels(global_particle_ids(b), b.plane, src[:E].cpu().numpy(),
+                               dst[:E].cpu().numpy())
+        n_pos, n_all = n_pos + int(yb.sum()), n_all + E
+        graphs.append((x, y, z, src[:E].contiguous(), dst[:E].contiguous(), eo, t(yb)))
+    del probe
+    frac = n_pos / max(n_all, 1)
+    pos_weight = float(min(10.0, (1.0 - frac) / max(frac, 1e-6)))
+    max_e = max(g[3].shape[0] for g in graphs)
+    gt = Trainer(m, blob, 64, max_hits, max_e, device=local, dtype="bf16", lr=1e-3,
+                 pos_weight=pos_weight)
+    t0 = time.perf_counter()
+    first = None
+    for k in range(args.gnn_steps):
+        loss = gt.step(*graphs[k % len(graphs)])
+        if first is None:
+            first = float(loss.item())
+    out["gnn"] = {"steps": args.gnn_steps, "s": time.perf_counter() - t0, "loss_first": first,
+                  "loss_last": float(loss.item()), "genuine_fraction": frac,
+                  "pos_weight": pos_weight, "edges_per_hit": n_all / sum(b.n_hits for b in train)}
+    blob = gt.blob.copy()
+    gt.ctx.sync()
+    del gt, graphs
+    # 3. evaluation
+    batch = wl.batch()
+    N, B = batch.n_hits, batch.n_events
+    tf = TrackFinder(m, blob, B, N, N * m.k_max, device=local)
+    x, y, z, p, h = t(batch.x), t(batch.y), t(batch.z), t(batch.plane), t(batch.hit_offsets)
+    pid = t(compact_particle_ids(batch))
+    names = ("efficiency", "clone_rate", "fake_rate", "hit_efficiency", "hit_purity")
+    per = {}
+    ref = None
+    for dt in ("f32", "bf16", "fp8"):
+        tf.dtype = dt
+        labels, _ = tf.run_device(x, y, z, p, h, N, B)
+        _, vals = tf.ctx.track_metrics(labels, pid, h)
+        lab = labels.clone()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            tf.run_device(x, y, z, p, h, N, B)
+        e1.record()
+        torch.cuda.synchronize()
+        rec = {k: float(v) for k, v in zip(names, vals.cpu().numpy()[2:])}
+        rec["events_per_s"] = 3 * B / (e0.elapsed_time(e1) / 1e3)
+        if ref is None:
+            ref = lab
+        else:
+            rec["label_agreement_vs_f32"] = float((lab == ref).float().mean().item())
+        per[dt] = rec
+    E = int(tf.eoff[B].item())
+    genuine = truth_edge_labels(global_particle_ids(batch), batch.plane, tf.src[:E].cpu().numpy(),
+                                tf.dst[:E].cpu().numpy())
+    tl = t(np.where(genuine > 0, 1.0, -1.0).astype(np.float32))
+    ceil_lab, _ = tf.ctx.edges_to_tracks(tf.src, tf.dst, tl, 0.0, tf.eoff, h)
+    _, vals = tf.ctx.track_metrics(ceil_lab, pid, h)
+    out["graph"] = {"edges_per_hit": E / N, "genuine_fraction": float(genuine.mean()),
+                    "ceiling": {k: float(v) for k, v in zip(names, vals.cpu().numpy()[2:])}}
+    out["per_dtype"] = per
+    tf.ctx.sync()
+    return out
 
 
 def run_reference(args):
@@ -633,6 +753,14 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.physics:
+        import torch
+        from paper_2407_12119_gb300 import build as build_mod
+        build_mod.build()
+        _, _, local = dist_env()
+        torch.cuda.set_device(local)
+        print(json.dumps({"physics": physics_report(args, local)}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
