@@ -128,7 +128,10 @@ etx_status etx_embed(etx_ctx* ctx, const float* x, const float* y, const float* 
  *                [edge_offsets[b], edge_offsets[b+1]); n_edges = edge_offsets[n_events]
  * If the edges do not fit, ETX_ERR_CAPACITY is recorded on the device, src/dst
  * are left unwritten and edge_offsets still holds the required counts.
- * edge_capacity >= n_hits * k_max can never overflow.
+ * edge_capacity >= n_hits * k_max can never overflow.  When n_hits * k_max
+ * fits the context's max_edges, one distance pass writes each source's kept
+ * edges to fixed slots in context scratch and a compaction forms the list;
+ * otherwise a counting pass precedes the emitting pass.  Same result.
  */
 etx_status etx_build_graph(etx_ctx* ctx, const float* emb, const int8_t* plane,
                            const int32_t* hit_offsets, int32_t n_events, int64_t n_hits,
@@ -160,7 +163,11 @@ etx_status etx_gnn_forward(etx_ctx* ctx, const float* x, const float* y, const f
  * the blob's interaction-network order, starting at the node encoder (the
  * normalisation and embedding entries are not part of it); its length is
  * etx_gnn_param_count(cfg).  Message-passing steps are recomputed from the
- * kept per-step encodings (checkpointing).
+ * kept per-step encodings (checkpointing).  The pass reads the edge index
+ * that the forward built; etx_build_graph (single-pass k-NN),
+ * etx_build_triplets and etx_edges_to_tracks_sweep reuse that scratch, so
+ * after one of them on this context the backward returns ETX_ERR_STATE until
+ * the next training forward.
  */
 int64_t etx_gnn_param_count(const etx_config* cfg);
 etx_status etx_gnn_backward(etx_ctx* ctx, const float* dlogits, float* dparams, void* stream);

@@ -649,6 +649,7 @@ etx_status etx_edges_to_tracks_sweep(etx_ctx* ctx, const int32_t* src, const int
   cudaStream_t s = (cudaStream_t)stream;
   launch(ctx, "clamp_edges", k_clamp_edges, 1, 1, 0, s, edge_offsets, n_events, ctx->cfg.max_edges,
          ctx->n_edges, ctx->d_err);
+  ctx->fwd_saved = false;  // the out-offsets of the last training forward are rebuilt
   cudaError_t e = launch_plane_bins(ctx, plane, hit_offsets, n_events, n_hits, s);
   if (e == cudaSuccess) e = launch_out_offsets(ctx, n_hits, src, dst, ctx->n_edges, s);
   if (e == cudaSuccess)
@@ -700,6 +701,7 @@ etx_status etx_build_triplets(etx_ctx* ctx, const int32_t* src, const int32_t* d
   cudaStream_t s = (cudaStream_t)stream;
   launch(ctx, "clamp_edges", k_clamp_edges, 1, 1, 0, s, edge_offsets, n_events, ctx->cfg.max_edges,
          ctx->n_edges, ctx->d_err);
+  ctx->fwd_saved = false;  // the edge index of the last training forward is rebuilt
   cudaError_t e = launch_build_triplets(ctx, src, dst, logits, threshold_logit, n_hits, workspace,
                                         capacity, first, second, kind, counts, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "etx_build_triplets launch");

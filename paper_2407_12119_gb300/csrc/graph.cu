@@ -14,6 +14,8 @@
 // Two launches of the same kernel: pass 0 writes per-hit counts, an
 // exclusive scan turns them into CSR offsets (which is also the src-CSR of the
 // edge list), pass 1 writes the edges at those offsets in (i, j) order.
+#include <algorithm>
+
 #include "etx_internal.cuh"
 
 namespace etx {
@@ -104,7 +106,10 @@ __global__ void k_plane_bins(const int8_t* __restrict__ plane, const int32_t* __
 // code stays small (instruction-cache misses dominated the unrolled version).
 constexpr int kListCap = 256;  // (key, j) pairs per warp: 2 KB of shared memory
 
-template <bool EMIT, int D>
+// KM: 0 counts min(#inside, k_max) into cnt_or_off[i]; 1 writes (src, dst) at
+// offset cnt_or_off[i]; 2 writes dst at the fixed slot i * k_max and the count
+// into cnt_or_off[i] (a compaction pass forms the edge list).
+template <int KM, int D>
 __device__ __forceinline__ bool knn_source_list(const float* __restrict__ emb, int i,
                                                 const float* cand_s, int n_cand, int c_lo,
                                                 float r2, int k_max, int32_t* cnt_or_off,
@@ -127,19 +132,19 @@ __device__ __forceinline__ bool knn_source_list(const float* __restrict__ emb, i
       key = __float_as_uint(d2);
     }
     const unsigned m = __ballot_sync(full, in);
-    if (EMIT && in) {
+    if (KM != 0 && in) {
       const int pos = n + __popc(m & lt_mask);
       if (pos < kListCap) list[pos] = (static_cast<uint64_t>(key) << 32) | static_cast<uint32_t>(j);
     }
     n += __popc(m);
   }
-  if (!EMIT) {
+  if (KM == 0) {
     if (lane == 0) cnt_or_off[i] = min(n, k_max);
     return true;
   }
   if (n > kListCap) return false;
   __syncwarp();
-  const int base = cnt_or_off[i];
+  const int64_t base = KM == 2 ? (int64_t)i * k_max : (int64_t)cnt_or_off[i];
   constexpr int R = kListCap / 32;  // list entries per lane: q = 32 r + lane
   bool keep[R];
 #pragma unroll
@@ -169,17 +174,18 @@ __device__ __forceinline__ bool knn_source_list(const float* __restrict__ emb, i
     if (32 * r >= n) break;
     const unsigned m = __ballot_sync(full, keep[r]);
     if (keep[r]) {
-      const int pos = base + written + __popc(m & lt_mask);
-      src[pos] = i;
+      const int64_t pos = base + written + __popc(m & lt_mask);
+      if (KM == 1) src[pos] = i;
       dst[pos] = c_lo + static_cast<int>(static_cast<uint32_t>(list[32 * r + lane]));
     }
     written += __popc(m);
   }
+  if (KM == 2 && lane == 0) cnt_or_off[i] = written;
   __syncwarp();
   return true;
 }
 
-template <bool EMIT, int DT>
+template <int KM, int DT>
 __global__ void __launch_bounds__(kKnnThreads)
 k_knn(const float* __restrict__ emb, int D, const int32_t* __restrict__ plane_off, int n_planes,
       float radius, int k_max, int32_t* __restrict__ cnt_or_off, int64_t n_hits,
@@ -196,7 +202,7 @@ k_knn(const float* __restrict__ emb, int D, const int32_t* __restrict__ plane_of
   const int s_lo = po[p], s_hi = po[p + 1];
   const int c_lo = po[p + 1], c_hi = po[min(p + 3, n_planes)];
   const int n_cand = c_hi - c_lo;
-  if (EMIT && cnt_or_off[n_hits] > capacity) {
+  if (KM == 1 && cnt_or_off[n_hits] > capacity) {
     if (threadIdx.x == 0) set_err(err, DERR_CAPACITY);
     return;
   }
@@ -204,7 +210,7 @@ k_knn(const float* __restrict__ emb, int D, const int32_t* __restrict__ plane_of
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt_mask = (1u << lane) - 1u;
   if (n_cand <= 0) {
-    if (!EMIT)
+    if (KM != 1)
       for (int i = s_lo + part * blockDim.x + threadIdx.x; i < s_hi; i += blockDim.x * split)
         cnt_or_off[i] = 0;
     return;
@@ -228,7 +234,7 @@ k_knn(const float* __restrict__ emb, int D, const int32_t* __restrict__ plane_of
   const bool fast = DT > 0 && staged;
   for (int i = s_lo + part * WPB + warp; i < s_hi; i += WPB * split) {
     if constexpr (DT > 0) {
-      if (fast && knn_source_list<EMIT, DT>(emb, i, cand_s, n_cand, c_lo, r2, k_max, cnt_or_off,
+      if (fast && knn_source_list<KM, DT>(emb, i, cand_s, n_cand, c_lo, r2, k_max, cnt_or_off,
                                             src, dst, lane, list_s + kListCap * warp))
         continue;
     }
@@ -242,11 +248,11 @@ k_knn(const float* __restrict__ emb, int D, const int32_t* __restrict__ plane_of
       if (j < n_cand) ok = d2_ordered(ei, cbase + (int64_t)j * cstep, cstride, D) < r2;
       cnt += __popc(__ballot_sync(0xffffffffu, ok));
     }
-    if (!EMIT) {
+    if (KM == 0) {
       if (lane == 0) cnt_or_off[i] = min(cnt, k_max);
       continue;
     }
-    const int base = cnt_or_off[i];
+    const int64_t base = KM == 2 ? (int64_t)i * k_max : (int64_t)cnt_or_off[i];
     uint32_t kth = 0xffffffffu;  // keep keys < kth, plus `take_eq` keys == kth
     int take_eq = 0;
     if (cnt > k_max) {
@@ -297,11 +303,35 @@ k_knn(const float* __restrict__ emb, int D, const int32_t* __restrict__ plane_of
       eq_seen += __popc(eqm);
       const unsigned inm = __ballot_sync(0xffffffffu, in);
       if (in) {
-        const int pos = base + written + __popc(inm & lt_mask);
-        src[pos] = i;
+        const int64_t pos = base + written + __popc(inm & lt_mask);
+        if (KM == 1) src[pos] = i;
         dst[pos] = c_lo + j;
       }
       written += __popc(inm);
+    }
+    if (KM == 2 && lane == 0) cnt_or_off[i] = written;
+  }
+}
+
+// Fixed-stride slots (k_max per source) -> the compact edge list at the
+// scanned offsets, a warp per source.  Nothing is written when the edges do
+// not fit (ETX_ERR_CAPACITY).
+__global__ void k_knn_compact(const int32_t* __restrict__ slots, int k_max,
+                              const int32_t* __restrict__ off, int64_t n_hits,
+                              int32_t* __restrict__ src, int32_t* __restrict__ dst,
+                              int64_t capacity, int* err) {
+  if (off[n_hits] > capacity) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_err(err, DERR_CAPACITY);
+    return;
+  }
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n_hits;
+       i += warps) {
+    const int o = off[i], n = off[i + 1] - o;
+    for (int t = lane; t < n; t += 32) {
+      dst[o + t] = slots[i * k_max + t];
+      src[o + t] = (int32_t)i;
     }
   }
 }
@@ -338,17 +368,40 @@ cudaError_t launch_build_graph(etx_ctx* ctx, const float* emb, const int8_t* pla
     launch(ctx, name, kernel, blocks, kKnnThreads, smem, s, emb, D, (const int32_t*)ctx->plane_off,
            P, radius, k_max, cnt, n_hits, sp, dp, cap, ctx->d_err, split);
   };
-  if (n_hits > 0 && blocks > 0) {
-    if (D == 8) knn(k_knn<false, 8>, "graph_knn_count", nullptr, nullptr, 0);
-    else if (D == 4) knn(k_knn<false, 4>, "graph_knn_count", nullptr, nullptr, 0);
-    else knn(k_knn<false, 0>, "graph_knn_count", nullptr, nullptr, 0);
-  }
-  cudaError_t e = exclusive_scan(ctx, cnt, cnt, n_hits, s);
-  if (e != cudaSuccess) return e;
-  if (n_hits > 0 && blocks > 0) {
-    if (D == 8) knn(k_knn<true, 8>, "graph_knn_emit", src, dst, edge_capacity);
-    else if (D == 4) knn(k_knn<true, 4>, "graph_knn_emit", src, dst, edge_capacity);
-    else knn(k_knn<true, 0>, "graph_knn_emit", src, dst, edge_capacity);
+  // One distance pass into fixed-stride slots when the context's in-edge
+  // permutation (rebuilt by every consumer of the edge index) can hold them;
+  // otherwise count, scan, then emit at the offsets.
+  const int64_t n_slots = n_hits * (int64_t)k_max;
+  const bool single = n_slots <= ctx->cfg.max_edges;
+  if (single) {
+    int32_t* slots = ctx->perm_in;
+    ctx->fwd_saved = false;  // the slots overwrite the edge index a backward pass would read
+    if (n_hits > 0 && blocks > 0) {
+      if (D == 8) knn(k_knn<2, 8>, "graph_knn_slots", nullptr, slots, n_slots);
+      else if (D == 4) knn(k_knn<2, 4>, "graph_knn_slots", nullptr, slots, n_slots);
+      else knn(k_knn<2, 0>, "graph_knn_slots", nullptr, slots, n_slots);
+    }
+    cudaError_t e = exclusive_scan(ctx, cnt, cnt, n_hits, s);
+    if (e != cudaSuccess) return e;
+    if (n_hits > 0) {
+      const int64_t wanted = (n_hits + 7) / 8;  // 8 warps per block
+      const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(wanted, (int64_t)ctx->n_sms * 16));
+      launch(ctx, "graph_knn_compact", k_knn_compact, grid, 256, 0, s, (const int32_t*)slots, k_max,
+             (const int32_t*)cnt, n_hits, src, dst, edge_capacity, ctx->d_err);
+    }
+  } else {
+    if (n_hits > 0 && blocks > 0) {
+      if (D == 8) knn(k_knn<0, 8>, "graph_knn_count", nullptr, nullptr, 0);
+      else if (D == 4) knn(k_knn<0, 4>, "graph_knn_count", nullptr, nullptr, 0);
+      else knn(k_knn<0, 0>, "graph_knn_count", nullptr, nullptr, 0);
+    }
+    cudaError_t e = exclusive_scan(ctx, cnt, cnt, n_hits, s);
+    if (e != cudaSuccess) return e;
+    if (n_hits > 0 && blocks > 0) {
+      if (D == 8) knn(k_knn<1, 8>, "graph_knn_emit", src, dst, edge_capacity);
+      else if (D == 4) knn(k_knn<1, 4>, "graph_knn_emit", src, dst, edge_capacity);
+      else knn(k_knn<1, 0>, "graph_knn_emit", src, dst, edge_capacity);
+    }
   }
   launch(ctx, "graph_edge_offsets", k_edge_offsets, (unsigned)((n_events + 1 + 255) / 256), 256, 0,
          s, cnt, hit_offsets, n_events, (int)n_hits, edge_offsets);
@@ -370,9 +423,9 @@ cudaError_t launch_plane_bins(etx_ctx* ctx, const int8_t* plane, const int32_t* 
 
 cudaError_t knn_set_smem_attr() {
   const int smem = (int)(kStageFloats * sizeof(float) + kKnnThreads / 32 * kListCap * sizeof(uint64_t));
-  const void* ks[] = {(const void*)k_knn<false, 0>, (const void*)k_knn<true, 0>,
-                      (const void*)k_knn<false, 4>, (const void*)k_knn<true, 4>,
-                      (const void*)k_knn<false, 8>, (const void*)k_knn<true, 8>};
+  const void* ks[] = {(const void*)k_knn<0, 0>, (const void*)k_knn<1, 0>, (const void*)k_knn<2, 0>,
+                      (const void*)k_knn<0, 4>, (const void*)k_knn<1, 4>, (const void*)k_knn<2, 4>,
+                      (const void*)k_knn<0, 8>, (const void*)k_knn<1, 8>, (const void*)k_knn<2, 8>};
   for (const void* k : ks) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;

@@ -152,10 +152,10 @@ def test_autograd_function_matches_backward(etx):
     args = (cuda(b.x), cuda(b.y), cuda(b.z), cuda(s.astype(np.int32)), cuda(d.astype(np.int32)),
             cuda(eo.astype(np.int32)))
     logits = InteractionNetworkFn.apply(theta, ctx, *args, "f32")
-    w = torch.linspace(-1, 1, logits.numel(), device="cuda")
-    (logits * w).sum().backward()
+    w_h = np.linspace(-1.0, 1.0, logits.numel())             # upstream gradient, made on the host
+    (logits * cuda(w_h.astype(np.float32))).sum().backward()
     cache = {}
     O.gnn_forward(W, 2, b.x, b.y, b.z, s, d, cache)
-    ref = O.gnn_backward(W, cache, w.cpu().numpy().astype(np.float64))
+    ref = O.gnn_backward(W, cache, w_h.astype(np.float32).astype(np.float64))
     flat = np.concatenate([ref[n].reshape(-1) for n in gnn_names(cfg)])
     assert rel(theta.grad.cpu().numpy().astype(np.float64), flat) <= GRAD_RTOL
