@@ -389,6 +389,7 @@ etx_status etx_load_weights(etx_ctx* ctx, const float* blob, int64_t n_floats) {
     e = cudaMemcpy(ctx->blob_dev, blob, (size_t)n_floats * sizeof(float), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "weight upload");
   ctx->w_dev_floats = dev.size();
+  ctx->w_host = dev;
   // --- BF16 tensor-core operand images (hidden == 128) ------------------------
   if (ctx->w_tc) cudaFree(ctx->w_tc);
   ctx->w_tc = nullptr;

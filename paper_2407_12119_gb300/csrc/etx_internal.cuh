@@ -92,6 +92,7 @@ struct etx_ctx {
   // weights
   float* w_dev = nullptr;   // repacked FP32 weights
   size_t w_dev_floats = 0;
+  std::vector<float> w_host;  // host copy of w_dev (kernel-parameter copies of small vectors)
   float* blob_dev = nullptr;  // raw blob copy (float32) for the backward pass
   uint8_t* w_tc = nullptr;    // BF16 operand images of the interaction network
   etx::Weights w;

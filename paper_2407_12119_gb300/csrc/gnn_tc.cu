@@ -33,6 +33,8 @@
 // raises a shared abort flag and every role stops.
 #include <cuda_bf16.h>
 
+#include <cstring>
+
 #include "sm100.cuh"
 
 namespace etx {
@@ -74,10 +76,16 @@ struct Cfg {
   static constexpr int KS = KIN / SUB;               // producer steps per tile
   static constexpr int C2 = H / Elt<F8>::KCH;        // chunks of the second GEMM
   static constexpr bool G2 = MODE != TC_CLS;
+  // LayerNorm parameters: read from the kernel's parameter space at compile-time
+  // offsets (column loops unrolled), except in the e4m3 node and edge updates,
+  // which ran 5% and 15% slower that way and keep a shared-memory copy read in
+  // rolled loops.
+  static constexpr bool SP = F8 && (MODE == TC_NODE_UPD || MODE == TC_EDGE_UPD);
+  static constexpr int PAR_BYTES = SP ? 7 * H * 4 : 0;
   static constexpr int OFF_W1 = 0;
   static constexpr int OFF_W2 = OFF_W1 + KC1 * CHUNK;
   static constexpr int OFF_A = OFF_W2 + (G2 ? C2 * CHUNK : 0);
-  static constexpr int FIXED = OFF_A + (G2 ? EPI_WARPS * 4096 : 0) + 7 * H * 4 + 8 * 64 + 16 + 1024;
+  static constexpr int FIXED = OFF_A + (G2 ? EPI_WARPS * 4096 : 0) + PAR_BYTES + 8 * 64 + 16 + 1024;
   // NS A-operand ring slots (as far as shared memory holds them).  A deeper ring
   // lets the first GEMM of later tiles queue in the (in-order) tensor pipe
   // ahead of the second GEMM the epilogue waits for; the autotuner picks NS.
@@ -89,8 +97,8 @@ struct Cfg {
                        B_D2EMPTY = B_D2FULL + 2, N_BARS = B_D2EMPTY + 2;
   static_assert(N_BARS <= 64, "barrier area");
   static constexpr int OFF_STG = OFF_A + NST * CHUNK;               // 8 per-warp 4 KB output stages
-  static constexpr int OFF_PAR = OFF_STG + (G2 ? EPI_WARPS * 4096 : 0);  // 7 x 128 floats
-  static constexpr int OFF_BAR = OFF_PAR + 7 * H * 4;
+  static constexpr int OFF_PAR = OFF_STG + (G2 ? EPI_WARPS * 4096 : 0);  // SP: 7 x 128 floats
+  static constexpr int OFF_BAR = OFF_PAR + PAR_BYTES;
   static constexpr int OFF_MISC = OFF_BAR + 8 * 64;                  // tmem addr, abort flag
   static constexpr int BYTES = OFF_MISC + 16;
   static constexpr int SMEM = BYTES + 1024;  // slack for 1024-byte alignment
@@ -109,12 +117,14 @@ struct TcArgs {
   const uint8_t* w1;  // swizzled operand image of W1 (KC1 chunks)
   const uint8_t* w2;  // swizzled operand image of W2 (C2 chunks)
   float ws1, ws2;     // per-tensor weight scales (1 for BF16)
-  const float *b1, *g1, *be1, *b2, *g2, *be2;
-  const float* wcls;  // classifier last Linear [H]
   const float* bcls;  // [1]
   uint8_t* h_lp;      // h rounded to the operand type (node update writes it)
   const uint8_t* m_lp;  // node update: [m_out, m_in] rounded to the operand type, rows of 2H
   int* err;
+  // b1 g1 be1 b2 g2 be2 of the block (or b1 g1 be1, -, -, -, w2 of the classifier), by
+  // value: the epilogue reads them at compile-time offsets from the kernel's
+  // parameter space (constant bank), not through the load/store pipe.
+  alignas(16) float prm[7][H];
 };
 
 // Four values to e4m3 (round to nearest even, saturating to +-448), first value
@@ -189,33 +199,20 @@ __device__ __forceinline__ uint32_t pack_bf16_relu(float lo, float hi) {
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
-// Shared-memory float4 load kept in program order (limits how many parameter
-// loads the compiler hoists ahead of their use, and so the registers they hold).
+// Four LayerNorm parameters: from shared memory (SP, a load kept in program
+// order, which limits how many the compiler hoists ahead of their use and so
+// the registers they hold) or from the kernel's parameter space (compile-time
+// offsets once the loops are unrolled).
+template <bool SP>
 __device__ __forceinline__ float4 lds4(const float* p) {
-  float4 v;
-  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(smem_u32(p)));
-  return v;
-}
-
-// t = sc * acc + b over N columns, in place; returns the sum of t (fixed
-// summation order: four interleaved pair chains).
-template <int N>
-__device__ __forceinline__ float bias_sum(float* __restrict__ t, const float* __restrict__ b, float sc) {
-  float2 acc[4] = {f2(0.f, 0.f), f2(0.f, 0.f), f2(0.f, 0.f), f2(0.f, 0.f)};
-  const float2 sc2 = f2(sc, sc);
-#pragma unroll
-  for (int j = 0; j < N; j += 4) {
-    const float4 bb = lds4(b + j);
-    const float2 x0 = __ffma2_rn(f2(t[j], t[j + 1]), sc2, f2(bb.x, bb.y));
-    const float2 x1 = __ffma2_rn(f2(t[j + 2], t[j + 3]), sc2, f2(bb.z, bb.w));
-    t[j] = x0.x; t[j + 1] = x0.y; t[j + 2] = x1.x; t[j + 3] = x1.y;
-    acc[(j >> 1) & 3] = __fadd2_rn(acc[(j >> 1) & 3], x0);
-    acc[((j >> 1) + 1) & 3] = __fadd2_rn(acc[((j >> 1) + 1) & 3], x1);
+  if constexpr (SP) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(smem_u32(p)));
+    return v;
+  } else {
+    return make_float4(p[0], p[1], p[2], p[3]);
   }
-  const float2 s01 = __fadd2_rn(acc[0], acc[1]), s23 = __fadd2_rn(acc[2], acc[3]);
-  const float2 s = __fadd2_rn(s01, s23);
-  return s.x + s.y;
 }
 
 // t -= mean in place over N values; returns the sum of squares of the centred values.
@@ -236,14 +233,14 @@ __device__ __forceinline__ float centre_sq(float* __restrict__ t, float mean) {
 
 // t = sc * acc + b over N columns, in place; adds the sums of d = t - shift and
 // of d^2 to s and q (four interleaved pair chains, fixed order).
-template <int N>
+template <int N, bool SP>
 __device__ __forceinline__ void shifted_sums(float* __restrict__ t, const float* __restrict__ b,
                                              float sc, float shift, float& s, float& q) {
   float2 as[2] = {f2(0.f, 0.f), f2(0.f, 0.f)}, aq[2] = {f2(0.f, 0.f), f2(0.f, 0.f)};
   const float2 sc2 = f2(sc, sc), ns = f2(-shift, -shift);
 #pragma unroll
   for (int j = 0; j < N; j += 4) {
-    const float4 bb = lds4(b + j);
+    const float4 bb = lds4<SP>(b + j);
     const float2 x0 = __ffma2_rn(f2(t[j], t[j + 1]), sc2, f2(bb.x, bb.y));
     const float2 x1 = __ffma2_rn(f2(t[j + 2], t[j + 3]), sc2, f2(bb.z, bb.w));
     t[j] = x0.x; t[j + 1] = x0.y; t[j + 2] = x1.x; t[j + 3] = x1.y;
@@ -270,14 +267,14 @@ __device__ __forceinline__ void centre(float* __restrict__ t, float mean) {
 }
 
 // y = (d * rstd) * g + be for N centred values d (ReLU left to the caller).
-template <int N>
+template <int N, bool SP>
 __device__ __forceinline__ void affine(float* __restrict__ d, const float* __restrict__ g,
                                        const float* __restrict__ be, float rstd) {
   const float2 rs = f2(rstd, rstd);
 #pragma unroll
   for (int j = 0; j < N; j += 4) {
-    const float4 gg = lds4(g + j);
-    const float4 ee = lds4(be + j);
+    const float4 gg = lds4<SP>(g + j);
+    const float4 ee = lds4<SP>(be + j);
     const float2 y0 = __ffma2_rn(__fmul2_rn(f2(d[j], d[j + 1]), rs), f2(gg.x, gg.y), f2(ee.x, ee.y));
     const float2 y1 =
         __ffma2_rn(__fmul2_rn(f2(d[j + 2], d[j + 3]), rs), f2(gg.z, gg.w), f2(ee.z, ee.w));
@@ -286,7 +283,7 @@ __device__ __forceinline__ void affine(float* __restrict__ d, const float* __res
 }
 
 template <int MODE, bool F8, int NS>
-__global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
+__global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(const __grid_constant__ TcArgs a) {
   using C = Cfg<MODE, F8, NS>;
   using EL = Elt<F8>;
   constexpr int NSTAGE = C::NST;
@@ -299,7 +296,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
   uint8_t* sW1 = smem + C::OFF_W1;
   uint8_t* sW2 = smem + C::OFF_W2;
   uint8_t* sA = smem + C::OFF_A;
-  float* par = reinterpret_cast<float*>(smem + C::OFF_PAR);  // b1 g1 be1 b2 g2 be2 wcls
+  // b1 g1 be1 b2 g2 be2 wcls: parameter space, or (SP) a shared-memory copy
+  const float* par = C::SP ? reinterpret_cast<const float*>(smem + C::OFF_PAR) : &a.prm[0][0];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::OFF_MISC);
   volatile int* abort = reinterpret_cast<volatile int*>(smem + C::OFF_MISC + 4);
@@ -325,17 +323,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
     *abort = 0;
     fence_mbar_init();
   }
-  if (tid < H) {
-    par[tid] = __ldg(a.b1 + tid);
-    par[H + tid] = __ldg(a.g1 + tid);
-    par[2 * H + tid] = __ldg(a.be1 + tid);
-    if (C::G2) {
-      par[3 * H + tid] = __ldg(a.b2 + tid);
-      par[4 * H + tid] = __ldg(a.g2 + tid);
-      par[5 * H + tid] = __ldg(a.be2 + tid);
-    } else {
-      par[6 * H + tid] = __ldg(a.wcls + tid);
-    }
+  if constexpr (C::SP) {
+    float* sp = reinterpret_cast<float*>(smem + C::OFF_PAR);
+    for (int i = tid; i < 7 * H; i += THREADS) sp[i] = a.prm[i / H][i % H];
   }
   if (warp == MMA_WARP) {
     tmem_alloc(tmem_slot, TMEM_COLS);
@@ -613,11 +603,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
     auto layer_stats = [&](uint32_t tb, float (&t)[64], const float* b, float sc, float& mean,
                            float& rstd) {
       float s = 0.f, q = 0.f, shift = 0.f;
-#pragma unroll 1
+#pragma unroll (C::SP ? 1 : NCH)
       for (int ch = 0; ch < NCH; ++ch) {
         tmem_ld64_wait(tb + 64 * ch, t);
         if (ch == 0) shift = fmaf(t[0], sc, b[0]);
-        shifted_sums<64>(t, b + 64 * ch, sc, shift, s, q);
+        shifted_sums<64, C::SP>(t, b + 64 * ch, sc, shift, s, q);
       }
       const float ms = s * (1.0f / H);
       mean = shift + ms;
@@ -628,9 +618,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
                           float mean, float rstd) {
       tmem_ld64_wait(tb + 64 * ch, t);
       float s_unused = 0.f, q_unused = 0.f;
-      shifted_sums<64>(t, p3 + 64 * ch, sc, 0.f, s_unused, q_unused);
+      shifted_sums<64, C::SP>(t, p3 + 64 * ch, sc, 0.f, s_unused, q_unused);
       centre<64>(t, mean);
-      affine<64>(t, p3 + H + 64 * ch, p3 + 2 * H + 64 * ch, rstd);
+      affine<64, C::SP>(t, p3 + H + 64 * ch, p3 + 2 * H + 64 * ch, rstd);
     };
     const float* resid = MODE == TC_NODE_UPD ? a.h : a.e;
     float* outp = MODE == TC_NODE_UPD ? a.h_out : a.e;
@@ -645,13 +635,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
       layer_stats(t1, t, par, a.ws1, mean, rstd);
       if constexpr (MODE == TC_CLS) {
         float2 acc[2] = {f2(0.f, 0.f), f2(0.f, 0.f)};
-#pragma unroll 1
+#pragma unroll (C::SP ? 1 : NCH)
         for (int ch = 0; ch < NCH; ++ch) {
           norm_chunk(t1, t, ch, par, a.ws1, mean, rstd);
           const float* wc = par + 6 * H + 64 * ch;
 #pragma unroll
           for (int j = 0; j < 64; j += 4) {
-            const float4 ww = lds4(wc + j);
+            const float4 ww = lds4<C::SP>(wc + j);
             acc[0] = __ffma2_rn(f2(fmaxf(t[j], 0.f), fmaxf(t[j + 1], 0.f)), f2(ww.x, ww.y), acc[0]);
             acc[1] = __ffma2_rn(f2(fmaxf(t[j + 2], 0.f), fmaxf(t[j + 3], 0.f)), f2(ww.z, ww.w), acc[1]);
           }
@@ -665,7 +655,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
         // Activations of chunk ch (64 columns) go to TMEM columns [32 ch, 32 ch + 32)
         // as BF16 pairs (or [16 ch, 16 ch + 16) as e4m3 quads): accumulator
         // columns this warp has already read, as chunks run in order.
-#pragma unroll 1
+#pragma unroll (C::SP ? 1 : NCH)
         for (int ch = 0; ch < NCH; ++ch) {
           norm_chunk(t1, t, ch, par, a.ws1, mean, rstd);
           if constexpr (F8) {
@@ -703,7 +693,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(TcArgs a) {
         if (!wait_or_abort(&bars[B_D2FULL + grp], ph, a.err, abort)) break;
         tc_fence_after();
         layer_stats(t2, t, par + 3 * H, a.ws2, mean, rstd);
-#pragma unroll 1
+#pragma unroll (C::SP ? 1 : NCH)
         for (int ch = 0; ch < NCH; ++ch) {
           norm_chunk(t2, t, ch, par + 3 * H, a.ws2, mean, rstd);
           if (ch == NCH - 1) {  // D2 fully read: the group's next second GEMM may overwrite it
@@ -821,17 +811,20 @@ TcArgs base_args(etx_ctx* ctx, int64_t N, const int32_t* src, const int32_t* dst
   return a;
 }
 
-void set_block(TcArgs& a, const BlockF32& f, const BlockTC& t, bool f8) {
+// Copy H parameters of a device weight array (inside ctx->w_dev) from the
+// host copy of the repacked weights.
+void host_params(const etx_ctx* ctx, const float* dev_ptr, float* out) {
+  const size_t off = static_cast<size_t>(dev_ptr - ctx->w_dev);
+  std::memcpy(out, ctx->w_host.data() + off, H * sizeof(float));
+}
+
+void set_block(etx_ctx* ctx, TcArgs& a, const BlockF32& f, const BlockTC& t, bool f8) {
   a.w1 = f8 ? t.w1f8 : t.w1;
   a.w2 = f8 ? t.w2f8 : t.w2;
   a.ws1 = f8 ? t.s1 : 1.f;
   a.ws2 = f8 ? t.s2 : 1.f;
-  a.b1 = f.l1.b;
-  a.g1 = f.g1;
-  a.be1 = f.be1;
-  a.b2 = f.l2.b;
-  a.g2 = f.g2;
-  a.be2 = f.be2;
+  const float* src[6] = {f.l1.b, f.g1, f.be1, f.l2.b, f.g2, f.be2};
+  for (int i = 0; i < 6; ++i) host_params(ctx, src[i], a.prm[i]);
 }
 
 template <int MODE>
@@ -846,7 +839,7 @@ cudaError_t launch_any(etx_ctx* ctx, bool f8, const char* n16, const char* n8, c
 cudaError_t launch_edge_encoder_tc(etx_ctx* ctx, int64_t N, const int32_t* src, const int32_t* dst,
                                    const int32_t* n_edges_dev, bool f8, cudaStream_t s) {
   TcArgs a = base_args(ctx, N, src, dst, n_edges_dev, nullptr);
-  set_block(a, ctx->w.edge_enc, ctx->w.edge_enc_tc, f8);
+  set_block(ctx, a, ctx->w.edge_enc, ctx->w.edge_enc_tc, f8);
   return launch_any<TC_EDGE_ENC>(ctx, f8, "gnn_edge_encoder_bf16", "gnn_edge_encoder_fp8", a,
                                  ctx->cfg.max_edges, s);
 }
@@ -854,7 +847,7 @@ cudaError_t launch_edge_encoder_tc(etx_ctx* ctx, int64_t N, const int32_t* src, 
 cudaError_t launch_node_update_tc(etx_ctx* ctx, int k, int64_t N, bool f8, cudaStream_t s) {
   TcArgs a = base_args(ctx, N, nullptr, nullptr, nullptr, nullptr);
   a.m_lp = reinterpret_cast<const uint8_t*>(ctx->m);  // written by the messages kernel
-  set_block(a, ctx->w.node[k], ctx->w.node_tc[k], f8);
+  set_block(ctx, a, ctx->w.node[k], ctx->w.node_tc[k], f8);
   return launch_any<TC_NODE_UPD>(ctx, f8, "gnn_node_update_bf16", "gnn_node_update_fp8", a, N, s);
 }
 
@@ -862,7 +855,7 @@ cudaError_t launch_edge_update_tc(etx_ctx* ctx, int k, int64_t N, const int32_t*
                                   const int32_t* dst, const int32_t* n_edges_dev, bool f8,
                                   cudaStream_t s) {
   TcArgs a = base_args(ctx, N, src, dst, n_edges_dev, nullptr);
-  set_block(a, ctx->w.edge[k], ctx->w.edge_tc[k], f8);
+  set_block(ctx, a, ctx->w.edge[k], ctx->w.edge_tc[k], f8);
   return launch_any<TC_EDGE_UPD>(ctx, f8, "gnn_edge_update_bf16", "gnn_edge_update_fp8", a,
                                  ctx->cfg.max_edges, s);
 }
@@ -886,10 +879,10 @@ cudaError_t launch_classifier_tc(etx_ctx* ctx, int64_t N, const int32_t* n_edges
   a.w1 = f8 ? t.w1f8 : t.w1;
   a.ws1 = f8 ? t.s1 : 1.f;
   a.ws2 = 1.f;
-  a.b1 = ctx->w.cls.l1.b;
-  a.g1 = ctx->w.cls.g1;
-  a.be1 = ctx->w.cls.be1;
-  a.wcls = ctx->w.cls.w2;
+  host_params(ctx, ctx->w.cls.l1.b, a.prm[0]);
+  host_params(ctx, ctx->w.cls.g1, a.prm[1]);
+  host_params(ctx, ctx->w.cls.be1, a.prm[2]);
+  host_params(ctx, ctx->w.cls.w2, a.prm[6]);
   a.bcls = ctx->w.cls.b2;
   return launch_any<TC_CLS>(ctx, f8, "gnn_classifier_bf16", "gnn_classifier_fp8", a,
                             ctx->cfg.max_edges, s);
