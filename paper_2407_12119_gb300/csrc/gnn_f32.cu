@@ -129,7 +129,7 @@ __device__ __forceinline__ uint32_t e4m3x4(float a, float b, float c, float d) {
 // OUTT 0: FP32 messages; 1: rounded to BF16, 2: to e4m3 (the tensor-core node
 // update's operand type; sums are FP32 either way), rows of 2H values at m.
 template <int H, int OUTT = 0>
-__global__ void __launch_bounds__(256, 8)  // 32 registers: eight 256-thread blocks per SM
+__global__ void __launch_bounds__(256, 4)  // 64 registers: eight rows in flight per warp
 k_messages(const float* __restrict__ e, const int32_t* __restrict__ out_off,
                            const int32_t* __restrict__ in_off, const int32_t* __restrict__ perm,
                            const int32_t* __restrict__ n_edges_dev, int n_hits,
@@ -147,14 +147,32 @@ k_messages(const float* __restrict__ e, const int32_t* __restrict__ out_off,
     const int o0 = min(max(out_off[l], 0), E), o1 = min(max(out_off[l + 1], 0), E);
     const int i0 = min(max(in_off[l], 0), E), i1 = min(max(in_off[l + 1], 0), E);
     float4 so = make_float4(0.f, 0.f, 0.f, 0.f), si = so;
-    for (int q = o0; q < o1; ++q) {
-      const float4 v = __ldg(reinterpret_cast<const float4*>(e + (int64_t)q * H + c));
-      so.x += v.x; so.y += v.y; so.z += v.z; so.w += v.w;
+    auto add = [](float4& a, const float4& v) { a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w; };
+    auto row = [&](int64_t r) { return __ldg(reinterpret_cast<const float4*>(e + r * H + c)); };
+    // Eight rows in flight before they are added (in edge order, so the sums
+    // are unchanged): a hit is done in a few memory latencies, and the in-rows
+    // of a hit, read moments earlier as out-rows of its sources, are still in L2.
+    int q = o0;
+    for (; q + 8 <= o1; q += 8) {
+      float4 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = row(q + u);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) add(so, v[u]);
     }
-    for (int q = i0; q < i1; ++q) {
-      const float4 v = __ldg(reinterpret_cast<const float4*>(e + (int64_t)perm[q] * H + c));
-      si.x += v.x; si.y += v.y; si.z += v.z; si.w += v.w;
+    for (; q < o1; ++q) add(so, row(q));
+    q = i0;
+    for (; q + 8 <= i1; q += 8) {
+      int r[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) r[u] = perm[q + u];
+      float4 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = row(r[u]);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) add(si, v[u]);
     }
+    for (; q < i1; ++q) add(si, row(perm[q]));
     if constexpr (OUTT == 0) {
       *reinterpret_cast<float4*>(m + l * 2 * H + c) = so;
       *reinterpret_cast<float4*>(m + l * 2 * H + H + c) = si;
