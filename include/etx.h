@@ -6,13 +6,20 @@
  * hit_offsets[B+1] (event b owns hits [hit_offsets[b], hit_offsets[b+1])).
  * Inside an event, hits must be sorted by plane (non-decreasing).
  *
- * Pipeline (paper Sec. 5 and Sec. 7, triplet stage excluded as in the
- * paper's own C++/CUDA port):
+ * Pipeline (paper Sec. 5 and Sec. 7; the triplet stage is not on it, as in
+ * the paper's own C++/CUDA port):
  *   etx_embed            hit embedding MLP                     (Sec. 5.1)
  *   etx_build_graph      radius-capped k-NN graph p -> p+1, p+2 (Eq. 1, Sec. 5.1, Sec. 7.2)
  *   etx_gnn_forward      interaction network edge logits       (Sec. 5.2, Eq. 4)
  *   etx_gnn_backward     gradient of the network parameters    (Sec. 5.2, Eq. 5)
  *   etx_edges_to_tracks  threshold + connected components      (Sec. 5, Sec. 7.3)
+ *
+ * Around it: training (etx_weighted_bce, etx_adam_step; the embedding's
+ * training set, hinge loss and reverse pass, Sec. 5.1, Eq. 2-3), the paper's
+ * plane-sweep labelling for comparison (etx_edges_to_tracks_sweep, Sec. 7.3),
+ * the Table 1 metrics on truth (etx_track_metrics, Sec. 6), triplets and
+ * their classifiers (etx_build_triplets, etx_classify_triplets, Sec. 5.3),
+ * and the launch-configuration autotuner (etx_autotune).
  *
  * Conventions shared by every entry point
  *  - All array arguments are DEVICE pointers owned by the caller unless a
