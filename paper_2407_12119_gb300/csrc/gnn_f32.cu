@@ -129,7 +129,7 @@ __device__ __forceinline__ uint32_t e4m3x4(float a, float b, float c, float d) {
 // OUTT 0: FP32 messages; 1: rounded to BF16, 2: to e4m3 (the tensor-core node
 // update's operand type; sums are FP32 either way), rows of 2H values at m.
 template <int H, int OUTT = 0>
-__global__ void __launch_bounds__(256, 4)  // 64 registers: eight rows in flight per warp
+__global__ void __launch_bounds__(256, 2)  // 128 registers: sixteen rows in flight per warp
 k_messages(const float* __restrict__ e, const int32_t* __restrict__ out_off,
                            const int32_t* __restrict__ in_off, const int32_t* __restrict__ perm,
                            const int32_t* __restrict__ n_edges_dev, int n_hits,
@@ -149,10 +149,19 @@ k_messages(const float* __restrict__ e, const int32_t* __restrict__ out_off,
     float4 so = make_float4(0.f, 0.f, 0.f, 0.f), si = so;
     auto add = [](float4& a, const float4& v) { a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w; };
     auto row = [&](int64_t r) { return __ldg(reinterpret_cast<const float4*>(e + r * H + c)); };
-    // Eight rows in flight before they are added (in edge order, so the sums
-    // are unchanged): a hit is done in a few memory latencies, and the in-rows
-    // of a hit, read moments earlier as out-rows of its sources, are still in L2.
+    // Sixteen (then eight) rows in flight before they are added (in edge order,
+    // so the sums are those of a plain loop): a hit is done in a few memory
+    // latencies, and the in-rows of a hit, read moments earlier as out-rows of
+    // its sources, are still in L2 (one row in flight: 1.68 ms per step k on
+    // the 500-event batch; eight: 1.49 ms; sixteen: 1.13 ms).
     int q = o0;
+    for (; q + 16 <= o1; q += 16) {
+      float4 v[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) v[u] = row(q + u);
+#pragma unroll
+      for (int u = 0; u < 16; ++u) add(so, v[u]);
+    }
     for (; q + 8 <= o1; q += 8) {
       float4 v[8];
 #pragma unroll
@@ -162,6 +171,16 @@ k_messages(const float* __restrict__ e, const int32_t* __restrict__ out_off,
     }
     for (; q < o1; ++q) add(so, row(q));
     q = i0;
+    for (; q + 16 <= i1; q += 16) {
+      int r[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) r[u] = perm[q + u];
+      float4 v[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) v[u] = row(r[u]);
+#pragma unroll
+      for (int u = 0; u < 16; ++u) add(si, v[u]);
+    }
     for (; q + 8 <= i1; q += 8) {
       int r[8];
 #pragma unroll
