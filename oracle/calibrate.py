@@ -11,6 +11,14 @@ equals the genuine-edge fraction of that graph (the trained classifier keeps
 roughly the genuine edges, Sec. 5.2).
 
     python -m oracle.calibrate batch500 plain
+
+With ``--fp8`` it calibrates the static e4m3 activation scales instead
+(Sec. 7.4 calibrates its INT8 quantisation on simulated events; here the
+largest magnitude of every activation operand of the exact forward over the
+first calibration events, per event so that memory stays small, turned into
+the smallest power-of-two scale that keeps it within e4m3's 448):
+
+    python -m oracle.calibrate --fp8 batch500 pileup4x
 """
 from __future__ import annotations
 
@@ -61,8 +69,33 @@ def calibrate(name: str, n_graph_events: int = 50, n_gnn_events: int = 3,
             "logit_std": float(z.std()) if z.size else 0.0}
 
 
+def calibrate_fp8(name: str, n_events: int) -> dict:
+    """log2 of the e4m3 activation scales (``O.act_scale_names`` order) from
+    the amax over the first ``n_events`` calibration events."""
+    wl = WORKLOADS[name]
+    cfg = wl.model
+    W = wl.weights()
+    depth = len(cfg.emb_widths) - 1
+    b = make_batch(wl.recipe, n_events, CALIB_SEED)
+    amax = np.zeros(O.n_act_scales(cfg.n_iters))
+    for i in range(b.n_events):
+        ev = b.event(i)
+        emb = O.embed(W, depth, ev.x, ev.y, ev.z)
+        s, d, _ = O.build_graph(emb, ev.plane, ev.hit_offsets, cfg.radius, cfg.k_max)
+        if s.size:
+            amax = np.maximum(amax, O.activation_amax(W, cfg.n_iters, ev.x, ev.y, ev.z, s, d))
+    log2 = [int(np.log2(O.fp8_act_scale(a))) for a in amax]
+    return {"fp8_events": n_events, "fp8_act_amax": [float(f"{a:.6g}") for a in amax],
+            "fp8_act_log2": log2}
+
+
 if __name__ == "__main__":
     args = sys.argv[1:]
+    if "--fp8" in args:
+        names = [a for a in args if not a.startswith("--")]
+        n_ev = {"batch500": 40, "pileup4x": 8}
+        print(json.dumps({n: calibrate_fp8(n, n_ev.get(n, 20)) for n in names}, indent=1))
+        sys.exit(0)
     keep = "--keep-radius" in args
     names = [a for a in args if not a.startswith("--")] or ["plain", "batch500"]
     print(json.dumps({n: calibrate(n, n_graph_events=5 if keep else 50, keep_radius=keep)

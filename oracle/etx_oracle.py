@@ -198,6 +198,31 @@ def quant_weight_e4m3(W):
     return round_e4m3(W32 / s) * float(s)
 
 
+def quant_act_e4m3(a, scale):
+    """e4m3 operand of an activation tensor with a per-tensor scale s that is a
+    power of two: e4m3(a / s) * s (a rounded to FP32 first).  Dividing by a
+    power of two is exact, so the scale only moves the e4m3 range: values
+    above 448 s saturate, spacing below 2^-6 s is subnormal."""
+    s = float(scale)
+    if s <= 0 or np.frexp(s)[0] != 0.5:
+        raise ValueError("activation scale must be a positive power of two")
+    return round_e4m3(np.asarray(a, np.float32).astype(np.float64) / s) * s
+
+
+def fp8_act_scale(amax):
+    """Static per-tensor activation scale of the e4m3 reading: the smallest
+    power of two s with amax / s <= 448 (1 for an all-zero tensor)."""
+    amax = float(amax)
+    if not amax > 0:
+        return 1.0
+    s = 2.0 ** int(np.ceil(np.log2(amax / 448.0)))
+    while amax / s > 448.0:     # guard the logarithm's rounding at exact powers
+        s *= 2.0
+    while s > 2.0 ** -126 and amax / (s / 2.0) <= 448.0:
+        s /= 2.0
+    return s
+
+
 def _identity(a):
     return a
 
@@ -209,16 +234,36 @@ GEMM_READINGS = {
 }
 
 
-def mlp_block(X, w, prefix, cache=None, op=_identity, op_w=None):
+def n_act_scales(n_iters):
+    """Number of e4m3 activation scales of a network with n_iters steps: the
+    two matrix products of the edge encoder and of every node and edge
+    network, and the classifier's first one."""
+    return 2 * (1 + 2 * n_iters) + 1
+
+
+def act_scale_names(n_iters):
+    """Order of the activation scales (and of ``activation_amax``):
+    edge_enc in/mid, then per step node{k} in/mid, edge{k} in/mid, then cls in.
+    "in" is the block input (first product), "mid" the ReLU output of its
+    first layer (second product)."""
+    names = ["edge_enc.in", "edge_enc.mid"]
+    for k in range(n_iters):
+        names += [f"node{k}.in", f"node{k}.mid", f"edge{k}.in", f"edge{k}.mid"]
+    return names + ["cls.in"]
+
+
+def mlp_block(X, w, prefix, cache=None, op=_identity, op_w=None, op2=None):
     """Lin -> LN -> ReLU -> Lin -> LN -> ReLU on rows of X.  ``op`` is applied
-    to the activation operand and ``op_w`` (default ``op``) to the weight
-    operand of each matrix product (identity: exact FP64)."""
+    to the activation operand of the first matrix product, ``op2`` (default
+    ``op``) to that of the second, and ``op_w`` (default ``op``) to the weight
+    operand of both (identity: exact FP64)."""
     op_w = op if op_w is None else op_w
+    op2 = op if op2 is None else op2
     f = lambda k: w[f"{prefix}.{k}"].astype(np.float64)
     a1 = op(X) @ op_w(w[f"{prefix}.W1"]).T + f("b1")
     y1, n1, s1 = layer_norm(a1, f("g1"), f("be1"))
     r1 = np.maximum(y1, 0.0)
-    a2 = op(r1) @ op_w(w[f"{prefix}.W2"]).T + f("b2")
+    a2 = op2(r1) @ op_w(w[f"{prefix}.W2"]).T + f("b2")
     y2, n2, s2 = layer_norm(a2, f("g2"), f("be2"))
     out = np.maximum(y2, 0.0)
     if cache is not None:
@@ -236,7 +281,7 @@ def messages(e, src, dst, n_nodes):
     return np.concatenate([m_out, m_in], axis=1)
 
 
-def gnn_forward(weights, n_iters, x, y, z, src, dst, cache=None, gemm="fp64"):
+def gnn_forward(weights, n_iters, x, y, z, src, dst, cache=None, gemm="fp64", act_scales=None):
     """Edge logits [E] (float64) of the interaction network.
 
     gemm="bf16" reads the mixed-precision configuration: the operands of every
@@ -244,9 +289,23 @@ def gnn_forward(weights, n_iters, x, y, z, src, dst, cache=None, gemm="fp64"):
     networks, first classifier layer) are rounded to BF16 and the products
     accumulate exactly; the node encoder (3 inputs), LayerNorm, residual adds,
     message sums and the last classifier dot product stay exact.
-    gemm="fp8" rounds those activation operands to e4m3 (scale 1) and the
-    weights to per-tensor scaled e4m3 (``quant_weight_e4m3``)."""
+    gemm="fp8" rounds the weights to per-tensor scaled e4m3
+    (``quant_weight_e4m3``) and each of those activation operands to e4m3
+    with its static per-tensor scale (``quant_act_e4m3``): ``act_scales``
+    lists them in ``act_scale_names`` order (powers of two; None = all 1).
+    One scale covers a whole concatenated block input ([e, h_i, h_j] or
+    [h, m_out, m_in])."""
     op, op_w = GEMM_READINGS[gemm]
+    n_sc = n_act_scales(n_iters)
+    if act_scales is not None and gemm != "fp8":
+        raise ValueError("activation scales belong to the e4m3 reading")
+    sc = [1.0] * n_sc if act_scales is None else [float(v) for v in act_scales]
+    if len(sc) != n_sc:
+        raise ValueError(f"expected {n_sc} activation scales")
+    if gemm == "fp8":
+        q = lambda i: (lambda a, s=sc[i]: quant_act_e4m3(a, s))
+    else:
+        q = lambda i: op
     src = np.asarray(src, np.int64)
     dst = np.asarray(dst, np.int64)
     N = np.asarray(x).shape[0]
@@ -254,14 +313,15 @@ def gnn_forward(weights, n_iters, x, y, z, src, dst, cache=None, gemm="fp64"):
                               np.asarray(z, np.float64)], axis=1),
                     weights["gnn_mu"], weights["gnn_sigma"])
     h = mlp_block(xin, weights, "node_enc", cache)
-    e = mlp_block(np.concatenate([h[src], h[dst]], axis=1), weights, "edge_enc", cache, op, op_w)
+    e = mlp_block(np.concatenate([h[src], h[dst]], axis=1), weights, "edge_enc", cache, q(0), op_w,
+                  q(1))
     for k in range(n_iters):
         m = messages(e, src, dst, N)
-        h = h + mlp_block(np.concatenate([h, m], axis=1), weights, f"node{k}", cache, op, op_w)
+        h = h + mlp_block(np.concatenate([h, m], axis=1), weights, f"node{k}", cache, q(2 + 4 * k),
+                          op_w, q(3 + 4 * k))
         e = e + mlp_block(np.concatenate([e, h[src], h[dst]], axis=1), weights, f"edge{k}", cache,
-                          op, op_w)
-    W1 = weights["cls.W1"].astype(np.float64)
-    a1 = op(e) @ op_w(weights["cls.W1"]).T + weights["cls.b1"].astype(np.float64)
+                          q(4 + 4 * k), op_w, q(5 + 4 * k))
+    a1 = q(n_sc - 1)(e) @ op_w(weights["cls.W1"]).T + weights["cls.b1"].astype(np.float64)
     y1, n1, s1 = layer_norm(a1, weights["cls.g1"].astype(np.float64),
                             weights["cls.be1"].astype(np.float64))
     r1 = np.maximum(y1, 0.0)
@@ -270,6 +330,20 @@ def gnn_forward(weights, n_iters, x, y, z, src, dst, cache=None, gemm="fp64"):
         cache["cls"] = dict(X=e, y1=y1, n1=n1, s1=s1, r1=r1)
         cache["meta"] = dict(N=N, src=src, dst=dst, n_iters=n_iters)
     return logits
+
+
+def activation_amax(weights, n_iters, x, y, z, src, dst):
+    """Largest magnitude of every e4m3 activation operand of the exact
+    (FP64) forward, in ``act_scale_names`` order: the calibration that
+    ``fp8_act_scale`` turns into static per-tensor scales."""
+    cache = {}
+    gnn_forward(weights, n_iters, x, y, z, src, dst, cache=cache)
+    amax = lambda a: float(np.abs(a).max()) if np.size(a) else 0.0
+    out = [amax(cache["edge_enc"]["X"]), amax(cache["edge_enc"]["r1"])]
+    for k in range(n_iters):
+        for p in (f"node{k}", f"edge{k}"):
+            out += [amax(cache[p]["X"]), amax(cache[p]["r1"])]
+    return out + [amax(cache["cls"]["X"])]
 
 
 # ----------------------------------------------------------------------------

@@ -34,3 +34,20 @@ def test_compact_particle_ids_partition_and_range():
             # same partition of the hits: equal old ids <=> equal new ids
             o, n = old[sig], new[sig]
             assert np.array_equal(o[:, None] == o[None, :], n[:, None] == n[None, :])
+
+
+def test_fp8_scales_of_the_presets_are_the_calibrated_ones():
+    """The e4m3 activation scales in the presets are those that
+    ``python -m oracle.calibrate --fp8`` wrote to oracle/calibration.json,
+    one per tensor-core operand (4 L + 3), and each is a power of two."""
+    import json
+    from pathlib import Path
+
+    from velo_synth import WORKLOADS
+    cal = json.loads((Path(__file__).resolve().parents[1] / "oracle" / "calibration.json").read_text())
+    for name in ("batch500", "pileup4x"):
+        m = WORKLOADS[name].model
+        assert list(m.fp8_act_log2) == cal[name]["fp8_act_log2"]
+        assert len(m.fp8_act_scales) == 4 * m.n_iters + 3
+        for s, amax in zip(m.fp8_act_scales, cal[name]["fp8_act_amax"]):
+            assert amax / s <= 448.0 < amax / (s / 2)

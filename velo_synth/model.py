@@ -29,10 +29,18 @@ class ModelConfig:
     k_max: int = 16                     # max edges per source hit
     n_planes: int = 26
     threshold_logit: float = 0.0        # keep an edge iff logit > this (0 = score 0.5)
+    # log2 of the static e4m3 activation scales (one per matrix-product operand
+    # of the interaction network, 4 n_iters + 3 of them); empty = all 1
+    fp8_act_log2: tuple = ()
 
     @property
     def emb_dim(self) -> int:
         return int(self.emb_widths[-1])
+
+    @property
+    def fp8_act_scales(self):
+        """The e4m3 activation scales (powers of two), or None for all 1."""
+        return tuple(2.0 ** int(k) for k in self.fp8_act_log2) if self.fp8_act_log2 else None
 
 
 def blob_layout(cfg: ModelConfig):
