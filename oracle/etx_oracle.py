@@ -750,3 +750,103 @@ def triplet_logits(tw, e, first, second, kind):
                                   np.asarray(tw[f"{name}.be1"], np.float64))[0], 0.0)
         out[sel] = a @ np.asarray(tw[f"{name}.W2"], np.float64)[0] + float(np.asarray(tw[f"{name}.b2"])[0])
     return out
+
+
+# ----------------------------------------------------------------------------
+# track building on the purified edge graph (Sec. 5.4)
+# ----------------------------------------------------------------------------
+def _find(parent, x):
+    while parent[x] != x:
+        x = parent[x]
+    return x
+
+
+def _union(parent, a, b):
+    ra, rb = _find(parent, a), _find(parent, b)
+    if ra != rb:
+        parent[max(ra, rb)] = min(ra, rb)
+
+
+def tracks_from_triplets(src, dst, edge_mask, first, second, kind, triplet_mask, min_hits=3):
+    """Tracks that may share hits, built from the purified edge graph: the
+    kept edges (``edge_mask``) linked by the kept triplets (``triplet_mask``
+    over ``build_triplets``'s list), in the four steps of Sec. 5.4 as read
+    here (the paper gives them in prose and a figure):
+
+    1. Elbows join continuations.  At each hit C, the kept edges entering C
+       that a chain of kept right elbows joins form one group, and so do the
+       kept edges leaving C joined by kept left elbows.  An articulation
+       (i, o) at C is taken as present when a kept articulation links some
+       edge of i's group to some edge of o's group: two edges of one elbow
+       share their continuations through C.  An articulation that the
+       classifier kept is present once, however many elbows also imply it
+       (the duplicates are dropped).
+    2. An articulation (i, o) at C is shared when i continues into two or
+       more present articulations at C (a fork after i) or o into two or more
+       (a merge before o).  Weakly connected components are taken over the
+       kept edges linked by the present, unshared articulations.
+    3. Every component touched by no shared articulation is a track; every
+       shared articulation (i, o) is a track of its own, the union of i's and
+       o's components (so a shared part is duplicated into each track).
+    4. A track's hits are the end points of its edges.
+
+    Tracks with fewer than ``min_hits`` hits are dropped.  Returns the list of
+    tracks, each a sorted tuple of batch-global hit indices, in lexicographic
+    order (the order is not part of the result)."""
+    src = np.asarray(src, np.int64)
+    dst = np.asarray(dst, np.int64)
+    emask = np.asarray(edge_mask, bool)
+    first = np.asarray(first, np.int64)
+    second = np.asarray(second, np.int64)
+    kind = np.asarray(kind, np.int64)
+    tmask = np.asarray(triplet_mask, bool)
+    E = src.shape[0]
+    # kept edges entering and leaving each hit, ascending edge index
+    ins, outs = {}, {}
+    for k in range(E):
+        if emask[k]:
+            outs.setdefault(int(src[k]), []).append(k)
+            ins.setdefault(int(dst[k]), []).append(k)
+    kept = {(int(f), int(s), int(t)) for f, s, t, m in zip(first, second, kind, tmask) if m}
+    parent = list(range(E))          # union-find over edge indices
+    shared = []
+    for c in sorted(set(ins) & set(outs)):
+        I, O = ins[c], outs[c]
+        # step 1: elbow groups of the in-edges (right elbows) and out-edges (left elbows)
+        gi, go = {i: i for i in I}, {o: o for o in O}
+        for x in range(len(I)):
+            for y in range(x + 1, len(I)):
+                if (I[x], I[y], TRIPLET_RIGHT_ELBOW) in kept:
+                    _union(gi, I[x], I[y])
+        for x in range(len(O)):
+            for y in range(x + 1, len(O)):
+                if (O[x], O[y], TRIPLET_LEFT_ELBOW) in kept:
+                    _union(go, O[x], O[y])
+        linked = {(_find(gi, i), _find(go, o)) for i in I for o in O
+                  if (i, o, TRIPLET_ARTICULATION) in kept}
+        present = [(i, o) for i in I for o in O if (_find(gi, i), _find(go, o)) in linked]
+        # step 2: shared articulations; the others link edges
+        n_out = {i: sum(1 for a, _ in present if a == i) for i in I}
+        n_in = {o: sum(1 for _, b in present if b == o) for o in O}
+        for i, o in present:
+            if n_out[i] >= 2 or n_in[o] >= 2:
+                shared.append((i, o))
+            else:
+                _union(parent, i, o)
+    # step 3: tracks as sets of edges (by component root)
+    comp_edges = {}
+    for k in range(E):
+        if emask[k]:
+            comp_edges.setdefault(_find(parent, k), []).append(k)
+    touched = {_find(parent, i) for i, _ in shared} | {_find(parent, o) for _, o in shared}
+    track_edges = [comp_edges[r] for r in sorted(comp_edges) if r not in touched]
+    for i, o in shared:
+        ri, ro = _find(parent, i), _find(parent, o)
+        track_edges.append(comp_edges[ri] + (comp_edges[ro] if ro != ri else []))
+    # step 4: edges -> hits
+    tracks = []
+    for es in track_edges:
+        hits = sorted({int(src[k]) for k in es} | {int(dst[k]) for k in es})
+        if len(hits) >= min_hits:
+            tracks.append(tuple(hits))
+    return sorted(tracks)
