@@ -77,6 +77,13 @@ typedef struct etx_config {
   int64_t max_edges;                           /* capacity: edges per call (< 2^31)       */
   int32_t train;                               /* nonzero: keep per-step activations for
                                                   etx_gnn_backward                        */
+  int32_t uf_iter_cap;                         /* iteration cap of every union-find loop in
+                                                  etx_edges_to_tracks (each find, and each
+                                                  hook attempt of an edge); 0 = the
+                                                  default (2^22 find steps, 2^20 hook
+                                                  attempts).  Reaching it leaves the
+                                                  labels unspecified and makes
+                                                  etx_ctx_sync return ETX_ERR_TIMEOUT  */
 } etx_config;
 
 typedef struct etx_ctx etx_ctx;
@@ -165,6 +172,27 @@ etx_status etx_gnn_forward(etx_ctx* ctx, const float* x, const float* y, const f
                            float* logits, void* stream);
 
 /*
+ * Static per-tensor activation scales of the e4m3 path (ETX_FP8E4M3; the
+ * paper calibrates its INT8 quantisation on simulated events, Sec. 7.4).
+ * Each matrix-product operand x of the interaction network enters the
+ * tensor cores as e4m3(x / s) and the accumulator is multiplied back by s
+ * (and by the weight's own amax / 448 scale); s is a power of two, so the
+ * scaling itself is exact and only moves e4m3's range (saturation at 448 s,
+ * subnormals below 2^-6 s).  One scale covers a whole concatenated block
+ * input ([e, h_i, h_j] or [h, m_out, m_in]).  Order, n = 4 L + 3 values:
+ *   edge encoder input, edge encoder second-layer input,
+ *   for k = 0 .. L-1: node net k input, its second-layer input,
+ *                     edge net k input, its second-layer input,
+ *   classifier input.
+ * host_scales is a HOST array, copied; (NULL, 0) restores the default (all
+ * 1).  ETX_ERR_ARG for a wrong count or a value that is not a power of two
+ * in [2^-100, 2^100].  BF16 and FP32 ignore the scales.  Takes effect for
+ * the next etx_gnn_forward.
+ */
+int64_t etx_fp8_scale_count(const etx_config* cfg);
+etx_status etx_set_fp8_scales(etx_ctx* ctx, const float* host_scales, int64_t n);
+
+/*
  * Reverse pass of the last etx_gnn_forward of this context (train contexts
  * only): given dlogits = dLoss/dlogit [n_edges], writes dparams, float32 in
  * the blob's interaction-network order, starting at the node encoder (the
@@ -237,15 +265,24 @@ etx_status etx_edges_to_tracks(etx_ctx* ctx, const int32_t* src, const int32_t* 
  * call re-initialises the part of the array it uses, but all calls share
  * it: calls that overlap on the GPU (different streams or devices sharing a
  * context's memory) race and give wrong labels.  Runs on the current device
- * and the given stream; asynchronous.  The union-find loops carry the same
- * iteration caps as etx_edges_to_tracks, but this call has no context to
- * report a cap being hit; valid input does not come near them.
+ * and the given stream; asynchronous.  The union-find loops carry the
+ * default iteration caps of etx_edges_to_tracks, and there is no context to
+ * report to, so device-side problems come back through `status`.
+ *   status   int32 [1] (device) or NULL: once the call's kernels have run it
+ *            holds ETX_OK, ETX_ERR_TIMEOUT (a union-find iteration cap was
+ *            reached: labels unspecified) or ETX_ERR_UNSORTED (an edge index
+ *            outside [0, n_hits) was skipped).  The array's error word is
+ *            cleared at the start of every call, so `status` describes this
+ *            call alone.
+ * The return value covers host-side checks and launch failures of this
+ * call's own kernels.
  */
 etx_status etx_edges_to_tracks_noalloc(const int32_t* src, const int32_t* dst,
                                        const float* logits, float threshold_logit,
                                        const int32_t* edge_offsets, const int32_t* hit_offsets,
                                        int32_t n_events, int64_t n_hits, int32_t min_hits,
-                                       int32_t* labels, int32_t* n_tracks, void* stream);
+                                       int32_t* labels, int32_t* n_tracks, int32_t* status,
+                                       void* stream);
 
 /*
  * The paper's own track-building kernel (Sec. 7.3), for comparison with
@@ -270,8 +307,8 @@ etx_status etx_edges_to_tracks_sweep(etx_ctx* ctx, const int32_t* src, const int
 
 /*
  * Triplets (Sec. 5.3) of the kept edges (logit > threshold_logit) and their
- * two classifiers.  The paper's triplet-aware track building (Sec. 5.4) is
- * not part of this library.
+ * two classifiers; etx_tracks_from_triplets (below) builds the tracks of
+ * Sec. 5.4 from them.
  *
  * etx_build_triplets: every pair of kept edges sharing a hit C, as
  *   articulation  A->C, C->B   (kind 0; first = the edge into C)
@@ -309,6 +346,56 @@ etx_status etx_build_triplets(etx_ctx* ctx, const int32_t* src, const int32_t* d
 etx_status etx_classify_triplets(etx_ctx* ctx, const int32_t* first, const int32_t* second,
                                  const int32_t* counts, int64_t capacity, float* logits,
                                  void* stream);
+
+/*
+ * Track building on the purified edge graph (Sec. 5.4): tracks that may
+ * share hits (e+e- pairs share their first hits).  The graph's nodes are the
+ * kept edges (logits > threshold_logit), its links the kept triplets
+ * (triplet_logits > triplet_threshold) of the list etx_build_triplets wrote
+ * for the same edges and threshold_logit.  Four steps, as read here (the
+ * paper gives them in prose and a figure):
+ *   1. at each hit C, kept edges into C joined by kept right elbows form a
+ *      group, and so do kept edges out of C joined by kept left elbows; an
+ *      articulation (i, o) at C is present when a kept articulation links
+ *      i's group to o's group (an elbow's two edges share their
+ *      continuations through C; an articulation implied twice counts once);
+ *   2. a present articulation (i, o) is shared when i has two or more
+ *      present articulations at C, or o has (a fork or a merge); weakly
+ *      connected components are formed over the kept edges linked by the
+ *      present, unshared articulations;
+ *   3. every component that no shared articulation touches is a track, and
+ *      every shared articulation (i, o) is a track of its own: the union of
+ *      i's and o's components (the shared part is duplicated);
+ *   4. a track's hits are the end points of its edges; tracks with fewer
+ *      than min_hits hits are dropped.
+ * Output: track_offsets int32 [track_capacity + 1] and track_hits int32
+ * [hit_capacity] (batch-global hit indices, ascending within a track) as a
+ * CSR of n_out[0] tracks and n_out[1] hits (n_out: int32 [2], device): first
+ * the components in order of their smallest edge index, then the shared
+ * articulations in list order.  Tracks never span events.
+ *   first, second  int32 [triplet_capacity], counts int32 [4]: the output of
+ *                  etx_build_triplets (its capacity as triplet_capacity)
+ *   triplet_logits float32 [triplet_capacity]: etx_classify_triplets' output
+ *   workspace      >= etx_tracks_workspace(n_hits, max_edges of the context,
+ *                  triplet_capacity) bytes, 4-byte aligned, caller-owned
+ * More than 32 kept edges into or out of one hit: that hit's articulations
+ * are dropped and etx_ctx_sync reports ETX_ERR_CAPACITY; a triplet list that
+ * does not belong to these edges is reported as ETX_ERR_UNSORTED; more
+ * tracks or hits than the capacities: ETX_ERR_CAPACITY and n_out = {0, 0}.
+ * Rebuilds the context's edge index (as etx_build_triplets does).
+ * Asynchronous on `stream`.
+ */
+size_t etx_tracks_workspace(int64_t n_hits, int64_t max_edges, int64_t triplet_capacity);
+etx_status etx_tracks_from_triplets(etx_ctx* ctx, const int32_t* src, const int32_t* dst,
+                                    const float* logits, float threshold_logit,
+                                    const int32_t* edge_offsets, int32_t n_events,
+                                    int64_t n_hits, const int32_t* first, const int32_t* second,
+                                    const float* triplet_logits, float triplet_threshold,
+                                    const int32_t* counts, int64_t triplet_capacity,
+                                    int32_t min_hits, void* workspace, size_t workspace_bytes,
+                                    int32_t* track_offsets, int32_t* track_hits,
+                                    int64_t track_capacity, int64_t hit_capacity,
+                                    int32_t* n_out, void* stream);
 
 /*
  * Training of the hit embedding (Sec. 5.1, Eq. 2-3).  A step is

@@ -21,9 +21,19 @@ namespace {
 constexpr int kFindCap = 1 << 22;
 constexpr int kUnionCap = 1 << 20;
 
-__device__ __forceinline__ int find_root(int* parent, int x, int* err) {
+// Iteration caps of the union-find loops: a find follows at most find_cap
+// parent links, an edge makes at most union_cap hook attempts.
+struct UfCaps {
+  int find_cap, union_cap;
+};
+
+__host__ __device__ inline UfCaps uf_caps(int32_t cfg_cap) {
+  return cfg_cap > 0 ? UfCaps{cfg_cap, cfg_cap} : UfCaps{kFindCap, kUnionCap};
+}
+
+__device__ __forceinline__ int find_root(int* parent, int x, int* err, int cap) {
   volatile int* par = parent;
-  for (int it = 0; it < kFindCap; ++it) {
+  for (int it = 0; it < cap; ++it) {
     const int p = par[x];
     if (p == x) return x;
     const int gp = par[p];
@@ -83,7 +93,7 @@ __global__ void k_init(int32_t* __restrict__ parent, int64_t n) {
 __global__ void k_union(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
                         const float* __restrict__ logits, float thr,
                         const int32_t* __restrict__ n_edges_dev, int n_hits,
-                        int32_t* parent, int* err) {
+                        int32_t* parent, int* err, UfCaps caps) {
   const int E = *n_edges_dev;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -94,24 +104,24 @@ __global__ void k_union(const int32_t* __restrict__ src, const int32_t* __restri
       continue;
     }
     int it = 0;
-    for (; it < kUnionCap; ++it) {
-      a = find_root(parent, a, err);
-      b = find_root(parent, b, err);
+    for (; it < caps.union_cap; ++it) {
+      a = find_root(parent, a, err, caps.find_cap);
+      b = find_root(parent, b, err, caps.find_cap);
       if (a == b) break;
       if (a < b) { const int t = a; a = b; b = t; }  // hook larger root a under b
       const int old = atomicCAS(parent + a, a, b);
       if (old == a) break;
       a = old;  // a was hooked meanwhile: continue from its new parent
     }
-    if (it == kUnionCap) set_err(err, DERR_TIMEOUT);
+    if (it == caps.union_cap) set_err(err, DERR_TIMEOUT);
   }
 }
 
 __global__ void k_labels(int32_t* parent, const int32_t* __restrict__ hoff, int32_t n_events,
-                         int64_t n_hits, int32_t* __restrict__ labels, int* err) {
+                         int64_t n_hits, int32_t* __restrict__ labels, int* err, UfCaps caps) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_hits;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int r = find_root(parent, (int)i, err);
+    const int r = find_root(parent, (int)i, err, caps.find_cap);
     int lo = 0, hi = n_events;  // event b with hoff[b] <= i < hoff[b+1]
     while (hi - lo > 1) {
       const int mid = (lo + hi) >> 1;
@@ -163,11 +173,12 @@ cudaError_t launch_edges_to_tracks(etx_ctx* ctx, const int32_t* src, const int32
   const int gn = grid_for(ctx, (const void*)k_init, 256, 0, (n_hits + 255) / 256);
   launch(ctx, "cc_init", k_init, gn, 256, 0, s, ctx->parent, n_hits);
   const int ge = grid_for(ctx, (const void*)k_union, 256, 0, (ctx->cfg.max_edges + 255) / 256);
+  const UfCaps caps = uf_caps(ctx->cfg.uf_iter_cap);
   launch(ctx, "cc_union", k_union, ge, 256, 0, s, src, dst, logits, thr, n_edges_dev, (int)n_hits,
-         ctx->parent, ctx->d_err);
+         ctx->parent, ctx->d_err, caps);
   const int gl = grid_for(ctx, (const void*)k_labels, 256, 0, (n_hits + 255) / 256);
   launch(ctx, "cc_labels", k_labels, gl, 256, 0, s, ctx->parent, hit_offsets, n_events, n_hits,
-         labels, ctx->d_err);
+         labels, ctx->d_err, caps);
   if (n_tracks) {
     cudaError_t e = cudaMemsetAsync(n_tracks, 0, (size_t)n_events * sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
@@ -202,6 +213,22 @@ constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mu;
 int32_t* g_noalloc_ptr[kNoAllocMaxDevices] = {};
 int g_noalloc_sms[kNoAllocMaxDevices] = {};
+
+// Error bits of the union-find kernels -> etx_status, for the caller's status word.
+__global__ void k_noalloc_status(const int* __restrict__ err, int32_t* __restrict__ status) {
+  const int w = *err;
+  *status = (w & etx::DERR_TIMEOUT) ? ETX_ERR_TIMEOUT : (w & etx::DERR_RANGE) ? ETX_ERR_UNSORTED : ETX_OK;
+}
+
+// Launch one kernel and return that launch's own error (cudaLaunchKernel reports
+// the launch it made; the process-wide last-error state is not consulted, so a
+// failure left there by unrelated earlier work is not charged to this call).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_checked(void (*kernel)(KArgs...), unsigned grid, unsigned block, cudaStream_t s,
+                           Args... args) {
+  void* argv[] = {static_cast<void*>(&args)...};
+  return cudaLaunchKernel(reinterpret_cast<const void*>(kernel), dim3(grid), dim3(block), argv, 0, s);
+}
 }  // namespace
 
 static __device__ __align__(256) int32_t g_cc_scratch[kNoAllocMaxHits + 64];
@@ -212,7 +239,7 @@ extern "C" etx_status etx_edges_to_tracks_noalloc(const int32_t* src, const int3
                                                   const int32_t* hit_offsets, int32_t n_events,
                                                   int64_t n_hits, int32_t min_hits,
                                                   int32_t* labels, int32_t* n_tracks,
-                                                  void* stream) {
+                                                  int32_t* status, void* stream) {
   using namespace etx;
   if (n_events < 0 || n_hits < 0) return ETX_ERR_ARG;
   if (n_hits > kNoAllocMaxHits) return ETX_ERR_CAPACITY;
@@ -237,29 +264,38 @@ extern "C" etx_status etx_edges_to_tracks_noalloc(const int32_t* src, const int3
     sms = g_noalloc_sms[dev];
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int32_t* parent = scratch;
+  int* err = scratch + kNoAllocMaxHits;
+  // this call's error bits start from zero (a memset allocates nothing)
+  if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) return ETX_ERR_CUDA;
   if (n_hits == 0) {
     if (n_tracks && n_events > 0 &&
         cudaMemsetAsync(n_tracks, 0, (size_t)n_events * sizeof(int32_t), s) != cudaSuccess)
       return ETX_ERR_CUDA;
-    return ETX_OK;
-  }
-  int32_t* parent = scratch;
-  int* err = scratch + kNoAllocMaxHits;
-  const int64_t cap = (int64_t)sms * 8;
-  const int64_t hb = (n_hits + 255) / 256;
-  const unsigned gh = (unsigned)(hb < cap ? hb : cap);
-  k_init<<<gh, 256, 0, s>>>(parent, n_hits);
-  // the edge count is read on the device from edge_offsets[n_events]
-  k_union<<<(unsigned)cap, 256, 0, s>>>(src, dst, logits, threshold_logit, edge_offsets + n_events,
-                                        (int)n_hits, parent, err);
-  k_labels<<<gh, 256, 0, s>>>(parent, hit_offsets, n_events, n_hits, labels, err);
-  if (n_tracks) {
-    if (cudaMemsetAsync(n_tracks, 0, (size_t)n_events * sizeof(int32_t), s) != cudaSuccess)
+  } else {
+    const UfCaps caps = uf_caps(0);
+    const int64_t cap = (int64_t)sms * 8;
+    const int64_t hb = (n_hits + 255) / 256;
+    const unsigned gh = (unsigned)(hb < cap ? hb : cap);
+    if (launch_checked(k_init, gh, 256, s, parent, n_hits) != cudaSuccess) return ETX_ERR_CUDA;
+    // the edge count is read on the device from edge_offsets[n_events]
+    if (launch_checked(k_union, (unsigned)cap, 256, s, src, dst, logits, threshold_logit,
+                       edge_offsets + n_events, (int)n_hits, parent, err, caps) != cudaSuccess)
       return ETX_ERR_CUDA;
-    if (cudaMemsetAsync(parent, 0, (size_t)n_hits * sizeof(int32_t), s) != cudaSuccess)
+    if (launch_checked(k_labels, gh, 256, s, parent, hit_offsets, n_events, n_hits, labels, err,
+                       caps) != cudaSuccess)
       return ETX_ERR_CUDA;
-    k_count_tracks<<<gh, 256, 0, s>>>(labels, hit_offsets, n_events, n_hits,
-                                      min_hits < 1 ? 1 : min_hits, parent, n_tracks);
+    if (n_tracks) {
+      if (cudaMemsetAsync(n_tracks, 0, (size_t)n_events * sizeof(int32_t), s) != cudaSuccess)
+        return ETX_ERR_CUDA;
+      if (cudaMemsetAsync(parent, 0, (size_t)n_hits * sizeof(int32_t), s) != cudaSuccess)
+        return ETX_ERR_CUDA;
+      if (launch_checked(k_count_tracks, gh, 256, s, labels, hit_offsets, n_events, n_hits,
+                         min_hits < 1 ? 1 : min_hits, parent, n_tracks) != cudaSuccess)
+        return ETX_ERR_CUDA;
+    }
   }
-  return cudaGetLastError() == cudaSuccess ? ETX_OK : ETX_ERR_CUDA;
+  if (status && launch_checked(k_noalloc_status, 1, 1, s, (const int*)err, status) != cudaSuccess)
+    return ETX_ERR_CUDA;
+  return ETX_OK;
 }

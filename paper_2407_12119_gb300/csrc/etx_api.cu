@@ -86,6 +86,7 @@ const char* config_problem(const etx_config* c) {
   if (c->max_events < 1) return "max_events must be >= 1";
   if (c->max_hits < 1 || c->max_hits >= (int64_t)1 << 31) return "max_hits must be in [1, 2^31)";
   if (c->max_edges < 1 || c->max_edges >= (int64_t)1 << 31) return "max_edges must be in [1, 2^31)";
+  if (c->uf_iter_cap < 0) return "uf_iter_cap must be >= 0 (0 = default caps)";
   return nullptr;
 }
 
@@ -571,6 +572,30 @@ etx_status etx_gnn_forward(etx_ctx* ctx, const float* x, const float* y, const f
   return ETX_OK;
 }
 
+int64_t etx_fp8_scale_count(const etx_config* cfg) {
+  if (config_problem(cfg)) return -1;
+  return 4 * (int64_t)cfg->n_iters + 3;
+}
+
+etx_status etx_set_fp8_scales(etx_ctx* ctx, const float* host_scales, int64_t n) {
+  if (!ctx) return ETX_ERR_ARG;
+  if (n == 0 && !host_scales) {
+    ctx->fp8_act.clear();
+    return ETX_OK;
+  }
+  if (!host_scales) return fail(ctx, ETX_ERR_ARG, "fp8 scales are NULL");
+  if (n != etx_fp8_scale_count(&ctx->cfg))
+    return fail(ctx, ETX_ERR_ARG, "fp8 scale count must be 4 * n_iters + 3");
+  for (int64_t i = 0; i < n; ++i) {
+    const float v = host_scales[i];
+    int ex = 0;
+    if (!(v > 0.f) || !std::isfinite(v) || std::frexp(v, &ex) != 0.5f || ex < -99 || ex > 101)
+      return fail(ctx, ETX_ERR_ARG, "fp8 scales must be powers of two in [2^-100, 2^100]");
+  }
+  ctx->fp8_act.assign(host_scales, host_scales + n);
+  return ETX_OK;
+}
+
 etx_status etx_gnn_backward(etx_ctx* ctx, const float* dlogits, float* dparams, void* stream) {
   if (!ctx) return ETX_ERR_ARG;
   if (!ctx->cfg.train) return fail(ctx, ETX_ERR_STATE, "context was not created for training");
@@ -706,6 +731,53 @@ etx_status etx_build_triplets(etx_ctx* ctx, const int32_t* src, const int32_t* d
   cudaError_t e = launch_build_triplets(ctx, src, dst, logits, threshold_logit, n_hits, workspace,
                                         capacity, first, second, kind, counts, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "etx_build_triplets launch");
+  return ETX_OK;
+}
+
+size_t etx_tracks_workspace(int64_t n_hits, int64_t max_edges, int64_t triplet_capacity) {
+  if (n_hits < 0 || max_edges < 0 || triplet_capacity < 0) return 0;
+  return tracks_workspace(n_hits, max_edges, triplet_capacity);
+}
+
+etx_status etx_tracks_from_triplets(etx_ctx* ctx, const int32_t* src, const int32_t* dst,
+                                    const float* logits, float threshold_logit,
+                                    const int32_t* edge_offsets, int32_t n_events,
+                                    int64_t n_hits, const int32_t* first, const int32_t* second,
+                                    const float* triplet_logits, float triplet_threshold,
+                                    const int32_t* counts, int64_t triplet_capacity,
+                                    int32_t min_hits, void* workspace, size_t workspace_bytes,
+                                    int32_t* track_offsets, int32_t* track_hits,
+                                    int64_t track_capacity, int64_t hit_capacity,
+                                    int32_t* n_out, void* stream) {
+  if (!ctx) return ETX_ERR_ARG;
+  if (n_events < 0 || n_events > ctx->cfg.max_events) return fail(ctx, ETX_ERR_CAPACITY, "n_events exceeds the context capacity");
+  if (n_hits < 0 || n_hits > ctx->cfg.max_hits) return fail(ctx, ETX_ERR_CAPACITY, "n_hits exceeds the context capacity");
+  if (!edge_offsets || !src || !dst || !logits || !counts || !workspace || !n_out || !track_offsets)
+    return fail(ctx, ETX_ERR_ARG, "NULL array");
+  if (triplet_capacity < 0 || triplet_capacity >= ((int64_t)1 << 31)) return fail(ctx, ETX_ERR_ARG, "triplet capacity out of range");
+  if (triplet_capacity > 0 && (!first || !second || !triplet_logits)) return fail(ctx, ETX_ERR_ARG, "NULL triplet arrays");
+  if (track_capacity < 0 || hit_capacity < 0 || track_capacity >= ((int64_t)1 << 31) ||
+      hit_capacity >= ((int64_t)1 << 31))
+    return fail(ctx, ETX_ERR_ARG, "track or hit capacity out of range");
+  if (hit_capacity > 0 && !track_hits) return fail(ctx, ETX_ERR_ARG, "NULL track hits");
+  if (min_hits < 1) return fail(ctx, ETX_ERR_ARG, "min_hits must be >= 1");
+  if (threshold_logit != threshold_logit || triplet_threshold != triplet_threshold)
+    return fail(ctx, ETX_ERR_ARG, "threshold is NaN");
+  if (ctx->cfg.max_edges + triplet_capacity >= ((int64_t)1 << 31))
+    return fail(ctx, ETX_ERR_CAPACITY, "max_edges + triplet capacity must stay below 2^31");
+  if (workspace_bytes < tracks_workspace(n_hits, ctx->cfg.max_edges, triplet_capacity))
+    return fail(ctx, ETX_ERR_CAPACITY, "workspace smaller than etx_tracks_workspace()");
+  if (reinterpret_cast<uintptr_t>(workspace) & 3) return fail(ctx, ETX_ERR_ARG, "workspace not 4-byte aligned");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  launch(ctx, "clamp_edges", k_clamp_edges, 1, 1, 0, s, edge_offsets, n_events, ctx->cfg.max_edges,
+         ctx->n_edges, ctx->d_err);
+  ctx->fwd_saved = false;  // the edge index of the last training forward is rebuilt
+  cudaError_t e = launch_tracks_from_triplets(
+      ctx, src, dst, logits, threshold_logit, n_hits, first, second, triplet_logits,
+      triplet_threshold, counts, triplet_capacity, min_hits, workspace, track_offsets, track_hits,
+      track_capacity, hit_capacity, n_out, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "etx_tracks_from_triplets launch");
   return ETX_OK;
 }
 

@@ -138,6 +138,9 @@ struct etx_ctx {
   int64_t fwd_n_hits = 0;
   int64_t gnn_blob_offset = 0;   // first interaction-network value in the weight blob
 
+  // e4m3 activation scales (etx_set_fp8_scales; powers of two, empty = all 1)
+  std::vector<float> fp8_act;
+
   // launch configurations picked by etx_autotune (defaults: measured on the
   // 500-event workload)
   int knn_split = 1;                         // blocks per (event, plane) in the k-NN
@@ -156,6 +159,9 @@ namespace etx {
 // scan.cu: exclusive scan of n int32 (n host-known); out[n] receives the total.
 cudaError_t exclusive_scan(etx_ctx* ctx, const int32_t* in, int32_t* out, int64_t n,
                            cudaStream_t s);
+// the same with caller-provided block-total scratch of tmp_ints >= scan_tmp_ints(n) ints
+cudaError_t exclusive_scan_with(etx_ctx* ctx, const int32_t* in, int32_t* out, int64_t n,
+                                int32_t* tmp, size_t tmp_ints, cudaStream_t s);
 size_t scan_tmp_ints(int64_t n);
 
 // embed.cu
@@ -216,6 +222,16 @@ cudaError_t launch_build_triplets(etx_ctx* ctx, const int32_t* src, const int32_
                                   int64_t capacity, int32_t* first, int32_t* second, int8_t* kind,
                                   int32_t* counts, cudaStream_t s);
 cudaError_t load_triplet_weights(etx_ctx* ctx, const float* blob);
+// triplets.cu: tracks on the purified edge graph (Sec. 5.4)
+size_t tracks_workspace(int64_t n_hits, int64_t e_cap, int64_t trip_cap);
+cudaError_t launch_tracks_from_triplets(etx_ctx* ctx, const int32_t* src, const int32_t* dst,
+                                        const float* logits, float thr, int64_t n_hits,
+                                        const int32_t* first, const int32_t* second,
+                                        const float* tlogits, float tthr, const int32_t* counts,
+                                        int64_t trip_cap, int32_t min_hits, void* workspace,
+                                        int32_t* track_offsets, int32_t* track_hits,
+                                        int64_t track_capacity, int64_t hit_capacity,
+                                        int32_t* n_out, cudaStream_t s);
 int64_t triplet_weights_size(int H);
 // gnn_f32.cu: a triplet classifier over rows [*row_lo_dev (or 0), *row_hi_dev) of first/second
 cudaError_t launch_triplet_classifier(etx_ctx* ctx, const int32_t* first, const int32_t* second,

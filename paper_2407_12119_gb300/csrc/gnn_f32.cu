@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(256, 2)  // 128 registers: sixteen rows in fli
 k_messages(const float* __restrict__ e, const int32_t* __restrict__ out_off,
                            const int32_t* __restrict__ in_off, const int32_t* __restrict__ perm,
                            const int32_t* __restrict__ n_edges_dev, int n_hits,
-                           float* __restrict__ m) {
+                           float* __restrict__ m, float inv) {
   constexpr int G = H / 4;          // lanes per hit
   constexpr int PER_WARP = 32 / G;  // hits per warp
   const int E = *n_edges_dev;
@@ -200,9 +200,11 @@ k_messages(const float* __restrict__ e, const int32_t* __restrict__ out_off,
       *reinterpret_cast<uint2*>(mb + c) = make_uint2(bf16x2(so.x, so.y), bf16x2(so.z, so.w));
       *reinterpret_cast<uint2*>(mb + H + c) = make_uint2(bf16x2(si.x, si.y), bf16x2(si.z, si.w));
     } else {
+      // e4m3: the sums times the reciprocal power-of-two activation scale of the
+      // node network's input (exact), then rounded
       uint8_t* m8 = reinterpret_cast<uint8_t*>(m) + l * 2 * H;
-      *reinterpret_cast<uint32_t*>(m8 + c) = e4m3x4(so.x, so.y, so.z, so.w);
-      *reinterpret_cast<uint32_t*>(m8 + H + c) = e4m3x4(si.x, si.y, si.z, si.w);
+      *reinterpret_cast<uint32_t*>(m8 + c) = e4m3x4(so.x * inv, so.y * inv, so.z * inv, so.w * inv);
+      *reinterpret_cast<uint32_t*>(m8 + H + c) = e4m3x4(si.x * inv, si.y * inv, si.z * inv, si.w * inv);
     }
   }
 }
@@ -386,8 +388,9 @@ cudaError_t forward(etx_ctx* ctx, const float* x, const float* y, const float* z
     if (N > 0) {
       // the tensor-core node update takes the messages in its operand type
       auto kern = !tc ? k_messages<H, 0> : (f8 ? k_messages<H, 2> : k_messages<H, 1>);
+      const float inv = (tc && f8 && 2 + 4 * k < (int)ctx->fp8_act.size()) ? 1.f / ctx->fp8_act[2 + 4 * k] : 1.f;
       launch(ctx, "gnn_messages", kern, msg_grid, 256, 0, s, ctx->e, ctx->out_off, ctx->in_off,
-             ctx->perm_in, n_edges_dev, (int)N, ctx->m);
+             ctx->perm_in, n_edges_dev, (int)N, ctx->m, inv);
     }
     if (tc) {
       chain(launch_node_update_tc(ctx, k, N, f8, s));
@@ -418,7 +421,7 @@ cudaError_t launch_messages(etx_ctx* ctx, const float* e, float* m, int64_t N, c
     const int grid = grid_for(ctx, (const void*)kernel, 256, 0, (N + per_block - 1) / per_block);
     launch(ctx, "gnn_messages", kernel, grid, 256, 0, s, e, (const int32_t*)ctx->out_off,
            (const int32_t*)ctx->in_off, (const int32_t*)ctx->perm_in,
-           (const int32_t*)ctx->n_edges, (int)N, m);
+           (const int32_t*)ctx->n_edges, (int)N, m, 1.f);
   };
   switch (ctx->cfg.hidden) {
     case 16: go(k_messages<16>, 8 * 8); break;

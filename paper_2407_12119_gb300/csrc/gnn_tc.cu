@@ -116,7 +116,11 @@ struct TcArgs {
   float* logits;
   const uint8_t* w1;  // swizzled operand image of W1 (KC1 chunks)
   const uint8_t* w2;  // swizzled operand image of W2 (C2 chunks)
-  float ws1, ws2;     // per-tensor weight scales (1 for BF16)
+  float ws1, ws2;     // accumulator scales: weight scale x activation scale (1 for BF16)
+  // e4m3 only: reciprocal power-of-two activation scales applied before rounding:
+  // the block input (FP32 stream columns), the second product's operand, and the
+  // low-precision h copy the node update writes for the next edge block
+  float in_inv, mid_inv, hlp_inv;
   const float* bcls;  // [1]
   uint8_t* h_lp;      // h rounded to the operand type (node update writes it)
   const uint8_t* m_lp;  // node update: [m_out, m_in] rounded to the operand type, rows of 2H
@@ -394,7 +398,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(const __grid_constant__ T
           const float4 v = f[k];
           if constexpr (F8)
             *reinterpret_cast<uint32_t*>(dstc + sw128(r, 4 * hpart + (u >> 2)) + 4 * (u & 3)) =
-                pack_e4m3x4(v.x, v.y, v.z, v.w);
+                pack_e4m3x4(v.x * a.in_inv, v.y * a.in_inv, v.z * a.in_inv, v.w * a.in_inv);
           else
             *reinterpret_cast<uint2*>(dstc + sw128(r, u >> 1) + 8 * (u & 1)) =
                 make_uint2(pack_bf16(v.x, v.y), pack_bf16(v.z, v.w));
@@ -660,10 +664,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(const __grid_constant__ T
           norm_chunk(t1, t, ch, par, a.ws1, mean, rstd);
           if constexpr (F8) {
             uint32_t v[16];
+            const float mi = a.mid_inv;  // a power of two: the scaling is exact
 #pragma unroll
             for (int q = 0; q < 16; ++q)
-              v[q] = pack_e4m3x4(fmaxf(t[4 * q], 0.f), fmaxf(t[4 * q + 1], 0.f),
-                                 fmaxf(t[4 * q + 2], 0.f), fmaxf(t[4 * q + 3], 0.f));
+              v[q] = pack_e4m3x4(fmaxf(t[4 * q], 0.f) * mi, fmaxf(t[4 * q + 1], 0.f) * mi,
+                                 fmaxf(t[4 * q + 2], 0.f) * mi, fmaxf(t[4 * q + 3], 0.f) * mi);
             tmem_st16(t1 + 16 * ch, v);
           } else {
 #pragma unroll
@@ -732,7 +737,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(const __grid_constant__ T
                 __stcs(reinterpret_cast<float4*>(outp + el), make_float4(o0.x, o0.y, o1.x, o1.y));
                 if constexpr (MODE == TC_NODE_UPD) {  // the copy the edge blocks gather
                   if constexpr (F8)
-                    *reinterpret_cast<uint32_t*>(a.h_lp + el) = pack_e4m3x4(o0.x, o0.y, o1.x, o1.y);
+                    *reinterpret_cast<uint32_t*>(a.h_lp + el) =
+                        pack_e4m3x4(o0.x * a.hlp_inv, o0.y * a.hlp_inv, o1.x * a.hlp_inv,
+                                    o1.y * a.hlp_inv);
                   else
                     *reinterpret_cast<uint2*>(a.h_lp + 2 * el) =
                         make_uint2(pack_bf16(o0.x, o0.y), pack_bf16(o1.x, o1.y));
@@ -783,14 +790,16 @@ cudaError_t launch_tc(etx_ctx* ctx, const char* name, const TcArgs& a, int64_t m
   }
 }
 
-// h (FP32, [n][128]) rounded to BF16 rows of 256 bytes or e4m3 rows of 128 bytes.
+// h (FP32, [n][128]) rounded to BF16 rows of 256 bytes or e4m3 rows of 128 bytes
+// (e4m3: h * inv, inv the reciprocal power-of-two activation scale).
 template <bool F8>
-__global__ void k_h_lowp(const float* __restrict__ h, uint8_t* __restrict__ out, int64_t n4) {
+__global__ void k_h_lowp(const float* __restrict__ h, uint8_t* __restrict__ out, int64_t n4,
+                         float inv) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4;
        q += (int64_t)gridDim.x * blockDim.x) {
     const float4 v = reinterpret_cast<const float4*>(h)[q];
     if constexpr (F8)
-      reinterpret_cast<uint32_t*>(out)[q] = pack_e4m3x4(v.x, v.y, v.z, v.w);
+      reinterpret_cast<uint32_t*>(out)[q] = pack_e4m3x4(v.x * inv, v.y * inv, v.z * inv, v.w * inv);
     else
       reinterpret_cast<uint2*>(out)[q] = make_uint2(pack_bf16(v.x, v.y), pack_bf16(v.z, v.w));
   }
@@ -810,7 +819,13 @@ TcArgs base_args(etx_ctx* ctx, int64_t N, const int32_t* src, const int32_t* dst
   a.logits = logits;
   a.h_lp = ctx->h_lp;
   a.err = ctx->d_err;
+  a.in_inv = a.mid_inv = a.hlp_inv = 1.f;
   return a;
+}
+
+// e4m3 activation scale i (etx_set_fp8_scales order) of the context: 1 unless set.
+float act_scale(const etx_ctx* ctx, int i) {
+  return i < (int)ctx->fp8_act.size() ? ctx->fp8_act[i] : 1.f;
 }
 
 // Copy H parameters of a device weight array (inside ctx->w_dev) from the
@@ -820,11 +835,15 @@ void host_params(const etx_ctx* ctx, const float* dev_ptr, float* out) {
   std::memcpy(out, ctx->w_host.data() + off, H * sizeof(float));
 }
 
-void set_block(etx_ctx* ctx, TcArgs& a, const BlockF32& f, const BlockTC& t, bool f8) {
+// s_in, s_mid: the block's e4m3 activation scales (powers of two; ignored for BF16)
+void set_block(etx_ctx* ctx, TcArgs& a, const BlockF32& f, const BlockTC& t, bool f8, float s_in,
+               float s_mid) {
   a.w1 = f8 ? t.w1f8 : t.w1;
   a.w2 = f8 ? t.w2f8 : t.w2;
-  a.ws1 = f8 ? t.s1 : 1.f;
-  a.ws2 = f8 ? t.s2 : 1.f;
+  a.ws1 = f8 ? t.s1 * s_in : 1.f;
+  a.ws2 = f8 ? t.s2 * s_mid : 1.f;
+  a.in_inv = f8 ? 1.f / s_in : 1.f;
+  a.mid_inv = f8 ? 1.f / s_mid : 1.f;
   const float* src[6] = {f.l1.b, f.g1, f.be1, f.l2.b, f.g2, f.be2};
   for (int i = 0; i < 6; ++i) host_params(ctx, src[i], a.prm[i]);
 }
@@ -841,7 +860,7 @@ cudaError_t launch_any(etx_ctx* ctx, bool f8, const char* n16, const char* n8, c
 cudaError_t launch_edge_encoder_tc(etx_ctx* ctx, int64_t N, const int32_t* src, const int32_t* dst,
                                    const int32_t* n_edges_dev, bool f8, cudaStream_t s) {
   TcArgs a = base_args(ctx, N, src, dst, n_edges_dev, nullptr);
-  set_block(ctx, a, ctx->w.edge_enc, ctx->w.edge_enc_tc, f8);
+  set_block(ctx, a, ctx->w.edge_enc, ctx->w.edge_enc_tc, f8, act_scale(ctx, 0), act_scale(ctx, 1));
   return launch_any<TC_EDGE_ENC>(ctx, f8, "gnn_edge_encoder_bf16", "gnn_edge_encoder_fp8", a,
                                  ctx->cfg.max_edges, s);
 }
@@ -849,7 +868,10 @@ cudaError_t launch_edge_encoder_tc(etx_ctx* ctx, int64_t N, const int32_t* src, 
 cudaError_t launch_node_update_tc(etx_ctx* ctx, int k, int64_t N, bool f8, cudaStream_t s) {
   TcArgs a = base_args(ctx, N, nullptr, nullptr, nullptr, nullptr);
   a.m_lp = reinterpret_cast<const uint8_t*>(ctx->m);  // written by the messages kernel
-  set_block(ctx, a, ctx->w.node[k], ctx->w.node_tc[k], f8);
+  set_block(ctx, a, ctx->w.node[k], ctx->w.node_tc[k], f8, act_scale(ctx, 2 + 4 * k),
+            act_scale(ctx, 3 + 4 * k));
+  // the h copy it writes feeds edge network k
+  a.hlp_inv = f8 ? 1.f / act_scale(ctx, 4 + 4 * k) : 1.f;
   return launch_any<TC_NODE_UPD>(ctx, f8, "gnn_node_update_bf16", "gnn_node_update_fp8", a, N, s);
 }
 
@@ -857,7 +879,8 @@ cudaError_t launch_edge_update_tc(etx_ctx* ctx, int k, int64_t N, const int32_t*
                                   const int32_t* dst, const int32_t* n_edges_dev, bool f8,
                                   cudaStream_t s) {
   TcArgs a = base_args(ctx, N, src, dst, n_edges_dev, nullptr);
-  set_block(ctx, a, ctx->w.edge[k], ctx->w.edge_tc[k], f8);
+  set_block(ctx, a, ctx->w.edge[k], ctx->w.edge_tc[k], f8, act_scale(ctx, 4 + 4 * k),
+            act_scale(ctx, 5 + 4 * k));
   return launch_any<TC_EDGE_UPD>(ctx, f8, "gnn_edge_update_bf16", "gnn_edge_update_fp8", a,
                                  ctx->cfg.max_edges, s);
 }
@@ -867,10 +890,13 @@ cudaError_t launch_h_lowp(etx_ctx* ctx, int64_t N, bool f8, cudaStream_t s) {
   if (n4 == 0) return cudaSuccess;
   const int grid = grid_for(ctx, f8 ? (const void*)k_h_lowp<true> : (const void*)k_h_lowp<false>,
                             256, 0, (n4 + 255) / 256);
+  // the copy feeds the edge encoder: its e4m3 input scale
   if (f8)
-    launch(ctx, "gnn_h_lowp", k_h_lowp<true>, grid, 256, 0, s, (const float*)ctx->h, ctx->h_lp, n4);
+    launch(ctx, "gnn_h_lowp", k_h_lowp<true>, grid, 256, 0, s, (const float*)ctx->h, ctx->h_lp, n4,
+           1.f / act_scale(ctx, 0));
   else
-    launch(ctx, "gnn_h_lowp", k_h_lowp<false>, grid, 256, 0, s, (const float*)ctx->h, ctx->h_lp, n4);
+    launch(ctx, "gnn_h_lowp", k_h_lowp<false>, grid, 256, 0, s, (const float*)ctx->h, ctx->h_lp, n4,
+           1.f);
   return cudaGetLastError();
 }
 
@@ -878,8 +904,10 @@ cudaError_t launch_classifier_tc(etx_ctx* ctx, int64_t N, const int32_t* n_edges
                                  bool f8, cudaStream_t s) {
   TcArgs a = base_args(ctx, N, nullptr, nullptr, n_edges_dev, logits);
   const BlockTC& t = ctx->w.cls_tc;
+  const float s_in = act_scale(ctx, 4 * ctx->cfg.n_iters + 2);
   a.w1 = f8 ? t.w1f8 : t.w1;
-  a.ws1 = f8 ? t.s1 : 1.f;
+  a.ws1 = f8 ? t.s1 * s_in : 1.f;
+  a.in_inv = f8 ? 1.f / s_in : 1.f;
   a.ws2 = 1.f;
   host_params(ctx, ctx->w.cls.l1.b, a.prm[0]);
   host_params(ctx, ctx->w.cls.g1, a.prm[1]);

@@ -92,8 +92,11 @@ size_t scan_tmp_ints(int64_t n) { return (size_t)((n + kTile - 1) / kTile) + 1; 
 
 cudaError_t exclusive_scan(etx_ctx* ctx, const int32_t* in, int32_t* out, int64_t n,
                            cudaStream_t s) {
-  int32_t* tmp = ctx->scan_tmp;
-  const size_t tmp_ints = ctx->scan_tmp_ints;
+  return exclusive_scan_with(ctx, in, out, n, ctx->scan_tmp, ctx->scan_tmp_ints, s);
+}
+
+cudaError_t exclusive_scan_with(etx_ctx* ctx, const int32_t* in, int32_t* out, int64_t n,
+                                int32_t* tmp, size_t tmp_ints, cudaStream_t s) {
   const int64_t nb = (n + kTile - 1) / kTile;
   if ((size_t)nb + 1 > tmp_ints) return cudaErrorInvalidValue;
   if (nb == 0) {

@@ -36,7 +36,8 @@ EXPORTED = ["etx_ctx_create", "etx_ctx_destroy", "etx_last_error", "etx_weights_
             "etx_embed_train_workspace", "etx_embed_forward_train", "etx_embed_backward",
             "etx_embedding_pairs_workspace", "etx_embedding_pairs", "etx_hinge_loss",
             "etx_triplet_weights_size", "etx_load_triplet_weights", "etx_triplets_workspace",
-            "etx_build_triplets", "etx_classify_triplets"]
+            "etx_build_triplets", "etx_classify_triplets", "etx_fp8_scale_count",
+            "etx_set_fp8_scales", "etx_tracks_workspace", "etx_tracks_from_triplets"]
 # etx_track_metrics outputs
 TRACK_COUNTS = ["particles", "matched_particles", "candidates", "candidate_particles", "tracks",
                 "unmatched_tracks"]
@@ -57,7 +58,8 @@ class EtxConfig(ctypes.Structure):
                 ("max_events", ctypes.c_int32),
                 ("max_hits", ctypes.c_int64),
                 ("max_edges", ctypes.c_int64),
-                ("train", ctypes.c_int32)]
+                ("train", ctypes.c_int32),
+                ("uf_iter_cap", ctypes.c_int32)]
 
 
 class EtxError(RuntimeError):
@@ -94,7 +96,8 @@ def lib() -> ctypes.CDLL:
         "etx_gnn_forward": (i32, [vp, vp, vp, vp, i64, vp, vp, vp, i32, i32, vp, vp]),
         "etx_gnn_backward": (i32, [vp, vp, vp, vp]),
         "etx_edges_to_tracks": (i32, [vp, vp, vp, vp, f32, vp, vp, i32, i64, i32, vp, vp, vp]),
-        "etx_edges_to_tracks_noalloc": (i32, [vp, vp, vp, f32, vp, vp, i32, i64, i32, vp, vp, vp]),
+        "etx_edges_to_tracks_noalloc": (i32, [vp, vp, vp, f32, vp, vp, i32, i64, i32, vp, vp, vp,
+                                              vp]),
         "etx_weighted_bce": (i32, [vp, vp, vp, vp, i32, f32, vp, vp, vp]),
         "etx_adam_step": (i32, [vp, vp, vp, vp, vp, i64, f32, f32, f32, f32, i64, vp]),
         "etx_autotune": (i32, [vp, vp, vp, vp, vp, vp, i32, i64, f32, i32, i32, vp, vp, vp, i64,
@@ -119,6 +122,12 @@ def lib() -> ctypes.CDLL:
         "etx_classify_triplets": (i32, [vp, vp, vp, vp, i64, vp, vp]),
         "etx_track_metrics": (i32, [vp, vp, vp, vp, i32, i64, i32, i32, i32, vp, ctypes.c_size_t,
                                     vp, vp, vp]),
+        "etx_tracks_workspace": (ctypes.c_size_t, [i64, i64, i64]),
+        "etx_tracks_from_triplets": (i32, [vp, vp, vp, vp, f32, vp, i32, i64, vp, vp, vp, f32, vp,
+                                           i64, i32, vp, ctypes.c_size_t, vp, vp, i64, i64, vp,
+                                           vp]),
+        "etx_fp8_scale_count": (i64, [cfgp]),
+        "etx_set_fp8_scales": (i32, [vp, vp, i64]),
         "etx_launch_count": (i64, [vp]),
         "etx_profile_enable": (i32, [vp, i32]),
         "etx_profile_read": (i32, [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
@@ -132,8 +141,10 @@ def lib() -> ctypes.CDLL:
     return L
 
 
-def make_config(model, max_events: int, max_hits: int, max_edges: int, train: bool = False) -> EtxConfig:
-    """``model`` needs emb_widths, hidden, n_iters and n_planes attributes."""
+def make_config(model, max_events: int, max_hits: int, max_edges: int, train: bool = False,
+                uf_iter_cap: int = 0) -> EtxConfig:
+    """``model`` needs emb_widths, hidden, n_iters and n_planes attributes;
+    ``uf_iter_cap`` > 0 replaces the union-find loops' default iteration caps."""
     c = EtxConfig()
     w = list(model.emb_widths)
     if len(w) - 1 > MAX_EMB_LAYERS:
@@ -148,6 +159,7 @@ def make_config(model, max_events: int, max_hits: int, max_edges: int, train: bo
     c.max_hits = int(max_hits)
     c.max_edges = int(max_edges)
     c.train = int(bool(train))
+    c.uf_iter_cap = int(uf_iter_cap)
     return c
 
 
@@ -182,10 +194,12 @@ NOALLOC_MAX_HITS = 1 << 21
 
 
 def edges_to_tracks_noalloc(src, dst, logits, threshold_logit: float, edge_offsets, hit_offsets,
-                            labels, n_tracks=None, min_hits: int = 3, stream=None):
+                            labels, n_tracks=None, min_hits: int = 3, status=None, stream=None):
     """etx_edges_to_tracks_noalloc: the components step without a context and
     without any device allocation (its scratch is a fixed array inside the
-    library, at most NOALLOC_MAX_HITS hits).  Every array is caller-owned."""
+    library, at most NOALLOC_MAX_HITS hits).  Every array is caller-owned;
+    ``status`` (int32 [1] on the device, optional) receives the call's
+    device-side status (ETX_OK, ETX_ERR_TIMEOUT or ETX_ERR_UNSORTED)."""
     dev = labels.device
     _need(src, torch.int32, "src", dev)
     _need(dst, torch.int32, "dst", dev)
@@ -195,10 +209,13 @@ def edges_to_tracks_noalloc(src, dst, logits, threshold_logit: float, edge_offse
     _need(labels, torch.int32, "labels", dev)
     if n_tracks is not None:
         _need(n_tracks, torch.int32, "n_tracks", dev)
+    if status is not None:
+        _need(status, torch.int32, "status", dev)
     st = lib().etx_edges_to_tracks_noalloc(_ptr(src), _ptr(dst), _ptr(logits), float(threshold_logit),
                                            _ptr(edge_offsets), _ptr(hit_offsets),
                                            hit_offsets.shape[0] - 1, labels.shape[0], int(min_hits),
-                                           _ptr(labels), _ptr(n_tracks), _stream(stream))
+                                           _ptr(labels), _ptr(n_tracks), _ptr(status),
+                                           _stream(stream))
     if st != ETX_OK:
         raise EtxError(st, "etx_edges_to_tracks_noalloc failed")
     return labels, n_tracks
@@ -208,10 +225,10 @@ class Context:
     """An etx_ctx: model shapes, capacities, loaded weights and scratch."""
 
     def __init__(self, model, max_events: int, max_hits: int, max_edges: int, device: int = 0,
-                 train: bool = False):
+                 train: bool = False, uf_iter_cap: int = 0):
         L = lib()
         self.model = model
-        self.cfg = make_config(model, max_events, max_hits, max_edges, train)
+        self.cfg = make_config(model, max_events, max_hits, max_edges, train, uf_iter_cap)
         self.device = torch.device("cuda", device)
         h = ctypes.c_void_p()
         st = L.etx_ctx_create(ctypes.byref(self.cfg), int(device), ctypes.byref(h))
@@ -240,6 +257,15 @@ class Context:
     def load_weights(self, blob: np.ndarray):
         b = np.ascontiguousarray(blob, dtype=np.float32)
         self._check(lib().etx_load_weights(self._h, b.ctypes.data_as(ctypes.c_void_p), b.size))
+
+    def set_fp8_scales(self, scales=None):
+        """Static e4m3 activation scales (powers of two, 4 L + 3 of them in the
+        order of include/etx.h); None restores all 1."""
+        if scales is None:
+            self._check(lib().etx_set_fp8_scales(self._h, None, 0))
+            return
+        a = np.ascontiguousarray(scales, dtype=np.float32)
+        self._check(lib().etx_set_fp8_scales(self._h, a.ctypes.data_as(ctypes.c_void_p), a.size))
 
     @property
     def launch_count(self) -> int:
@@ -379,6 +405,46 @@ class Context:
         self._check(lib().etx_classify_triplets(self._h, _ptr(first), _ptr(second), _ptr(counts),
                                                 first.shape[0], _ptr(logits), _stream(stream)))
         return logits
+
+    def tracks_workspace(self, n_hits: int, triplet_capacity: int) -> int:
+        return int(lib().etx_tracks_workspace(int(n_hits), int(self.cfg.max_edges),
+                                              int(triplet_capacity)))
+
+    def tracks_from_triplets(self, src, dst, logits, threshold_logit: float, edge_offsets,
+                             n_hits: int, first, second, triplet_logits, triplet_threshold: float,
+                             counts, min_hits: int = 3, track_capacity: int | None = None,
+                             hit_capacity: int | None = None, workspace=None, out=None,
+                             stream=None):
+        """etx_tracks_from_triplets (Sec. 5.4): tracks that may share hits, as a
+        CSR (track_offsets, track_hits) plus n_out = [tracks, hits] on the
+        device.  ``first``/``second``/``counts`` come from build_triplets,
+        ``triplet_logits`` from classify_triplets."""
+        dev = self.device
+        for t, n in ((src, "src"), (dst, "dst"), (edge_offsets, "edge_offsets"), (first, "first"),
+                     (second, "second"), (counts, "counts")):
+            _need(t, torch.int32, n, dev)
+        _need(logits, torch.float32, "logits", dev)
+        _need(triplet_logits, torch.float32, "triplet_logits", dev)
+        cap = first.shape[0]
+        if track_capacity is None:
+            track_capacity = int(self.cfg.max_edges) + cap
+        if hit_capacity is None:
+            hit_capacity = 2 * (int(self.cfg.max_edges) + cap)
+        if workspace is None:
+            workspace = torch.empty(max(self.tracks_workspace(n_hits, cap), 4), dtype=torch.uint8,
+                                    device=dev)
+        if out is None:
+            out = (torch.empty(track_capacity + 1, dtype=torch.int32, device=dev),
+                   torch.empty(max(hit_capacity, 1), dtype=torch.int32, device=dev),
+                   torch.empty(2, dtype=torch.int32, device=dev))
+        offs, hits, n_out = out
+        self._check(lib().etx_tracks_from_triplets(
+            self._h, _ptr(src), _ptr(dst), _ptr(logits), float(threshold_logit), _ptr(edge_offsets),
+            edge_offsets.shape[0] - 1, int(n_hits), _ptr(first), _ptr(second), _ptr(triplet_logits),
+            float(triplet_threshold), _ptr(counts), cap, int(min_hits), _ptr(workspace),
+            workspace.numel(), _ptr(offs), _ptr(hits), int(track_capacity), int(hit_capacity),
+            _ptr(n_out), _stream(stream)))
+        return offs, hits, n_out
 
     # ---- embedding training (Sec. 5.1, Eq. 2-3) ----------------------------
     @property

@@ -25,6 +25,8 @@ class TrackFinder:
         self.max_edges = int(max_edges or max_hits * model.k_max)
         self.ctx = Context(model, max_events, max_hits, self.max_edges, device=device)
         self.ctx.load_weights(blob)
+        # static e4m3 activation scales of the model (used by dtype "fp8" only)
+        self.ctx.set_fp8_scales(getattr(model, "fp8_act_scales", None))
         dev = self.ctx.device
         self.dev = dev
         self.emb = torch.empty((max_hits, model.emb_widths[-1]), dtype=torch.float32, device=dev)

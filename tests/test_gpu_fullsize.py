@@ -2,10 +2,13 @@
 the whole 500-event batch (and the 1,000-event pile-up batch) goes through the
 autotuned step replayed from its CUDA graph; sampled events, which are
 independent of the rest of the batch, are then recomputed one by one by the
-FP64 oracle from its own inputs and compared: embeddings within the FP32
-bound, edge lists exactly apart from pairs within 1e-5 of the radius or of
-the k-th kept distance (counted), logits within the dtype's tolerance on
-events whose graphs agree, labels exactly where the edge masks agree."""
+FP64 oracle and compared: embeddings within the FP32 bound; edge lists
+exactly, apart from pairs within 1e-5 of the radius or of the k-th kept
+distance (counted); logits, stage-isolated on the GPU's own graph of the
+event (so an event whose graph differs by a near-cut pair is still checked),
+within the dtype's tolerance of the oracle's reading of that dtype; and the
+track labels exactly equal to the oracle's connected components of the same
+graph under the GPU's own edge mask.  Every sampled event must pass."""
 import numpy as np
 import pytest
 import torch
@@ -15,7 +18,11 @@ from velo_synth import WORKLOADS, pack_blob
 
 pytestmark = pytest.mark.gpu
 NEAR_CUT = 1e-5
-LOGIT_TOL = {"f32": 1e-4, "bf16": 2e-2}   # bf16: vs the oracle's BF16 reading, as the stage tests
+# max-abs logit error against the oracle's reading of the dtype, as in the stage tests
+# (e4m3: rounding-boundary flips between FP32 and FP64 operands, each a whole e4m3 step,
+# put the largest difference at the scale of the format's own error)
+LOGIT_TOL = {"f32": 1e-4, "bf16": 2e-2, "fp8": 0.25}
+READING = {"f32": "fp64", "bf16": "bf16", "fp8": "fp8"}
 
 
 @pytest.fixture(scope="module")
@@ -70,45 +77,41 @@ def check_event(wl, b, W, g, ev, dtype):
     emb64 = O.embed(W, len(m.emb_widths) - 1, e.x, e.y, e.z)
     bound = 2e-6 * (1.0 + np.abs(emb64).max())
     assert np.abs(g["emb"][lo:hi] - emb64).max() <= bound
+    # graph: exact apart from near-cut pairs
     s, d, _ = O.build_graph(emb64, e.plane, e.hit_offsets, m.radius, m.k_max)
     e0, e1 = int(g["eoff"][ev]), int(g["eoff"][ev + 1])
     gs, gd = g["src"][e0:e1] - lo, g["dst"][e0:e1] - lo
     diff = set(zip(gs.tolist(), gd.tolist())) ^ set(zip(s.tolist(), d.tolist()))
     assert all(near_cut(emb64, i, j, e.plane, 0, hi - lo, m.radius, m.k_max) for i, j in diff)
-    if diff:
-        return f"event {ev}: {len(diff)} near-cut pairs differ", False
-    ref = O.gnn_forward(W, m.n_iters, e.x, e.y, e.z, s, d,
-                        gemm="bf16" if dtype == "bf16" else "fp64")
-    err = np.abs(g["logits"][e0:e1] - ref).max() if s.size else 0.0
+    # logits, stage-isolated: the oracle on the GPU's own graph of this event
+    kw = {"act_scales": m.fp8_act_scales} if dtype == "fp8" else {}
+    ref = O.gnn_forward(W, m.n_iters, e.x, e.y, e.z, gs, gd, gemm=READING[dtype], **kw)
+    err = np.abs(g["logits"][e0:e1] - ref).max() if gs.size else 0.0
     assert err <= LOGIT_TOL[dtype], (ev, err)
-    mask_gpu = g["logits"][e0:e1] > m.threshold_logit
-    mask_ref = ref > m.threshold_logit
-    flips = int((mask_gpu != mask_ref).sum())
-    if flips == 0:
-        ref_lab = O.connected_components(s, d, mask_ref, e.hit_offsets)
-        np.testing.assert_array_equal(g["labels"][lo:hi], ref_lab)
-    return f"event {ev}: {hi - lo} hits, {s.size} edges, max |logit err| {err:.2e}, mask flips {flips}", True
+    if dtype == "fp8" and gs.size:
+        # the mean error against the reading stays well below the format's own error
+        own = np.abs(ref - O.gnn_forward(W, m.n_iters, e.x, e.y, e.z, gs, gd)).mean()
+        assert np.abs(g["logits"][e0:e1] - ref).mean() <= 0.5 * own + 1e-2, ev
+    # labels: identical to the oracle's components under the GPU's own edge mask
+    mask_gpu = g["logits"][e0:e1] > np.float32(m.threshold_logit)
+    ref_lab = O.connected_components(gs, gd, mask_gpu, e.hit_offsets)
+    np.testing.assert_array_equal(g["labels"][lo:hi], ref_lab)
+    flips = int((mask_gpu != (ref > m.threshold_logit)).sum())
+    return (f"event {ev}: {hi - lo} hits, {gs.size} edges ({len(diff)} near-cut pairs differ), "
+            f"max |logit err| {err:.2e}, mask flips vs the reading {flips}")
 
 
-@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "fp8"])
 def test_full_batch500_sampled_events(pipeline, dtype):
     wl, b, W, g = run_full(pipeline, "batch500", dtype)
     sizes = np.diff(b.hit_offsets)
     sample = sorted({0, b.n_events // 2, b.n_events - 1, int(np.argmax(sizes))})
-    agreed = 0
     for ev in sample:
-        msg, ok = check_event(wl, b, W, g, ev, dtype)
-        agreed += ok
-        print(dtype, msg)
-    assert agreed >= 2
+        print(dtype, check_event(wl, b, W, g, ev, dtype))
 
 
-def test_full_pileup_sampled_events(pipeline):
-    wl, b, W, g = run_full(pipeline, "pileup4x", "bf16")
-    sample = [0, b.n_events - 1]
-    agreed = 0
-    for ev in sample:
-        msg, ok = check_event(wl, b, W, g, ev, "bf16")
-        agreed += ok
-        print("pileup", msg)
-    assert agreed >= 1
+@pytest.mark.parametrize("dtype", ["bf16", "fp8"])
+def test_full_pileup_sampled_events(pipeline, dtype):
+    wl, b, W, g = run_full(pipeline, "pileup4x", dtype)
+    for ev in (0, b.n_events - 1):
+        print("pileup", dtype, check_event(wl, b, W, g, ev, dtype))

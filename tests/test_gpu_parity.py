@@ -384,39 +384,65 @@ def test_gnn_forward_bf16_tensor_cores(etx, n_events):
     assert e16.max() <= BF16_TOL
 
 
-FP8_TOL = 0.15    # vs the oracle's e4m3 reading (max-abs); e4m3 keeps 3 mantissa bits
+# vs the oracle's e4m3 reading (max-abs).  e4m3 keeps 3 mantissa bits: where an FP32
+# operand and its FP64 counterpart fall on either side of a rounding boundary the two
+# roundings differ by a whole e4m3 step, and the network carries such flips on, so the
+# largest difference from the reading is of the order of the format's own error (the
+# reading differs from FP64 by up to 0.2 here); the mean check below is the sharp one
+FP8_TOL = 0.25
 
 
-@pytest.mark.parametrize("n_events", [1, 3])
-def test_gnn_forward_fp8_tensor_cores(etx, n_events):
+@pytest.mark.parametrize("n_events,scales", [(1, "unit"), (3, "unit"), (3, "calibrated")])
+def test_gnn_forward_fp8_tensor_cores(etx, n_events, scales):
     st = setup_for(etx, "batch500", n_events)
+    sc = st.model.fp8_act_scales if scales == "calibrated" else None
+    assert scales == "unit" or sc is not None
+    st.ctx.set_fp8_scales(sc)
     emb64 = st.oracle_emb()
     s, d, eo = O.build_graph(emb64, st.b.plane, st.b.hit_offsets, st.model.radius, st.model.k_max)
     args = (st.W, st.model.n_iters, st.b.x, st.b.y, st.b.z, s, d)
     ref64 = O.gnn_forward(*args)
-    ref8 = O.gnn_forward(*args, gemm="fp8")
+    ref8 = O.gnn_forward(*args, gemm="fp8", act_scales=sc)
     logits = st.ctx.gnn_forward(st.x, st.y, st.z, cuda(s, torch.int32), cuda(d, torch.int32),
                                 cuda(eo, torch.int32), dtype="fp8")
     st.ctx.sync()
     got = logits.cpu().numpy().astype(np.float64)
     e8, e64 = np.abs(got - ref8), np.abs(got - ref64)
-    print(f"fp8 E={s.size}: max|err| vs e4m3 reading {e8.max():.3e} (mean {e8.mean():.2e}), "
-          f"vs fp64 {e64.max():.3e} (mean {e64.mean():.2e}), oracle fp8-vs-fp64 "
-          f"{np.abs(ref8 - ref64).max():.3e}")
+    print(f"fp8 ({scales} scales) E={s.size}: max|err| vs e4m3 reading {e8.max():.3e} "
+          f"(mean {e8.mean():.2e}), vs fp64 {e64.max():.3e} (mean {e64.mean():.2e}), oracle "
+          f"fp8-vs-fp64 {np.abs(ref8 - ref64).max():.3e} (mean {np.abs(ref8 - ref64).mean():.2e})")
     assert e8.max() <= FP8_TOL
     # a layout or scale error would be far larger than the e4m3 rounding itself
     assert e8.mean() <= 0.5 * max(np.abs(ref8 - ref64).mean(), 1e-6) + 1e-2
 
 
+# Per-dtype bounds against the FP64 oracle on the batch500 sample (random weights: logits
+# 2.44 +- 0.23 around the cut 2.848).  An edge mask can only differ where the FP64 logit
+# lies closer to the cut than the dtype's logit error, so the band |z64 - cut| <= NEAR_LOGIT
+# is "near the cut" (counted); outside it the masks must agree exactly.
+NEAR_LOGIT = {"f32": 1e-4, "bf16": 2e-2, "fp8": 0.25}
+MAX_ABS_VS_FP64 = {"f32": 1e-4, "bf16": 2e-2, "fp8": 0.25}
+MASK_DIS_MAX = {"f32": 1e-4, "bf16": 1e-3}
+LABEL_AGREE_MIN = {"f32": 0.999, "bf16": 0.99, "fp8": 0.8}
+
+
 def test_dtype_report_vs_fp64_oracle(etx):
     """Per arithmetic type: max-abs logit error against the FP64 oracle, edge-mask
-    disagreement at the workload's cut and track-label agreement (both sides on
-    the oracle's graph).  Printed; FP32 must reproduce the oracle's tracks."""
-    st = setup_for(etx, "batch500", 3, perturb=0.0)
+    disagreement at the workload's cut (split into near-cut and the rest) and
+    track-label agreement, all on the oracle's graph of 5 events.  FP32 and BF16
+    must keep the mask disagreement within the bound; e4m3's is set by its
+    3-bit mantissa, which the oracle's own e4m3 reading shows independently of
+    the GPU: the GPU may not exceed that reading's disagreement by more than
+    one part in four, plus 1e-3."""
+    st = setup_for(etx, "batch500", 5, perturb=0.0)
+    st.ctx.set_fp8_scales(st.model.fp8_act_scales)
     emb64 = st.oracle_emb()
     s, d, eo = O.build_graph(emb64, st.b.plane, st.b.hit_offsets, st.model.radius, st.model.k_max)
-    z64 = O.gnn_forward(st.W, st.model.n_iters, st.b.x, st.b.y, st.b.z, s, d)
+    args = (st.W, st.model.n_iters, st.b.x, st.b.y, st.b.z, s, d)
+    z64 = O.gnn_forward(*args)
     thr = st.model.threshold_logit
+    z8 = O.gnn_forward(*args, gemm="fp8", act_scales=st.model.fp8_act_scales)
+    reading8_dis = float(((z8 > thr) != (z64 > thr)).mean())
     lab64 = O.connected_components(s, d, z64 > thr, st.b.hit_offsets)
     s_t, d_t, eo_t = cuda(s, torch.int32), cuda(d, torch.int32), cuda(eo, torch.int32)
     report = {}
@@ -425,11 +451,20 @@ def test_dtype_report_vs_fp64_oracle(etx):
         lab, _ = st.ctx.edges_to_tracks(s_t, d_t, z, thr, eo_t, st.hoff)
         st.ctx.sync()
         zg = z.cpu().numpy().astype(np.float64)
-        report[dt] = dict(max_abs=float(np.abs(zg - z64).max()),
-                          mask_dis=float(((zg > thr) != (z64 > thr)).mean()),
+        flip = (zg > thr) != (z64 > thr)
+        near = np.abs(z64 - thr) <= NEAR_LOGIT[dt]
+        report[dt] = dict(max_abs=float(np.abs(zg - z64).max()), mask_dis=float(flip.mean()),
+                          flips_far=int((flip & ~near).sum()), near=int(near.sum()),
                           label_agree=float((lab.cpu().numpy() == lab64).mean()))
     for dt, r in report.items():
         print(f"{dt}: E={s.size} max|logit err| {r['max_abs']:.3e}, mask disagreement "
-              f"{r['mask_dis']:.2e}, label agreement {r['label_agree']:.5f}")
-    assert report["f32"]["max_abs"] <= LOGIT_TOL
-    assert report["f32"]["label_agree"] >= 0.999
+              f"{r['mask_dis']:.2e} ({r['near']} edges near the cut, {r['flips_far']} flips "
+              f"outside), label agreement {r['label_agree']:.5f}")
+    print(f"oracle e4m3 reading vs fp64: mask disagreement {reading8_dis:.2e}")
+    for dt, r in report.items():
+        assert r["max_abs"] <= MAX_ABS_VS_FP64[dt], dt
+        assert r["flips_far"] == 0, dt
+        assert r["label_agree"] >= LABEL_AGREE_MIN[dt], dt
+        if dt in MASK_DIS_MAX:
+            assert r["mask_dis"] <= MASK_DIS_MAX[dt], dt
+    assert report["fp8"]["mask_dis"] <= 1.25 * reading8_dis + 1e-3
