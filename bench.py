@@ -778,16 +778,45 @@ def run_ours(args):
     torch.cuda.synchronize()
     tc = trip_out[3].cpu().tolist()
     tf.ctx.sync()
+    # tracks on the purified edge graph (Sec. 5.4), on the structure a trained
+    # classifier would leave: the graph's genuine edges, every triplet of them
+    # kept (the random-weight classifiers' decisions would be noise)
+    src_h, dst_h = tf.src[:E].cpu().numpy(), tf.dst[:E].cpu().numpy()
+    genuine = truth_edge_labels(global_particle_ids(batch), batch.plane, src_h, dst_h)
+    truth_logits = torch.from_numpy(np.where(genuine > 0, 1.0, -1.0).astype(np.float32)).to(dev)
+    g_out = tf.ctx.build_triplets(tf.src, tf.dst, truth_logits, 0.0, tf.eoff, N, trip_cap,
+                                  workspace=trip_ws)
+    g_logits = torch.ones(trip_cap, dtype=torch.float32, device=dev)
+    trk_ws = torch.empty(max(tf.ctx.tracks_workspace(N, trip_cap), 4), dtype=torch.uint8, device=dev)
+    trk_out = (torch.empty(tf.max_edges + trip_cap + 1, dtype=torch.int32, device=dev),
+               torch.empty(2 * (tf.max_edges + trip_cap), dtype=torch.int32, device=dev),
+               torch.empty(2, dtype=torch.int32, device=dev))
+
+    def tracks():
+        tf.ctx.tracks_from_triplets(tf.src, tf.dst, truth_logits, 0.0, tf.eoff, N, g_out[0],
+                                    g_out[1], g_logits, 0.0, g_out[3], workspace=trk_ws,
+                                    out=trk_out)
+
+    tracks()
+    torch.cuda.synchronize()
+    t3, t4 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+    t3.record(stream)
+    for _ in range(args.steps):
+        tracks()
+    t4.record(stream)
+    torch.cuda.synchronize()
+    n_trk, n_trk_hits = trk_out[2].cpu().tolist()
+    tf.ctx.sync()
     triplet_report = {"build_ms": t0.elapsed_time(t1) / args.steps,
                       "classify_ms": t1.elapsed_time(t2) / args.steps,
                       "triplets": tc[0], "articulations": tc[1], "left_elbows": tc[2],
                       "right_elbows": tc[3],
-                      "note": "outside the timed step (the paper's port leaves the triplet stage out)"}
+                      "tracks_ms": t3.elapsed_time(t4) / args.steps,
+                      "tracks": n_trk, "track_hits": n_trk_hits,
+                      "note": "outside the timed step (the paper's port leaves the triplet stage "
+                              "out); tracks built on the genuine edges with every triplet kept"}
 
     # graph-stage ceiling: exact components of the built graph's genuine edges
-    src_h, dst_h = tf.src[:E].cpu().numpy(), tf.dst[:E].cpu().numpy()
-    genuine = truth_edge_labels(global_particle_ids(batch), batch.plane, src_h, dst_h)
-    truth_logits = torch.from_numpy(np.where(genuine > 0, 1.0, -1.0).astype(np.float32)).to(dev)
     truth_lab, _ = tf.ctx.edges_to_tracks(tf.src, tf.dst, truth_logits, 0.0, tf.eoff, do)
     m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     m0.record(stream)

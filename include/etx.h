@@ -378,8 +378,10 @@ etx_status etx_classify_triplets(etx_ctx* ctx, const int32_t* first, const int32
  *   triplet_logits float32 [triplet_capacity]: etx_classify_triplets' output
  *   workspace      >= etx_tracks_workspace(n_hits, max_edges of the context,
  *                  triplet_capacity) bytes, 4-byte aligned, caller-owned
- * More than 32 kept edges into or out of one hit: that hit's articulations
- * are dropped and etx_ctx_sync reports ETX_ERR_CAPACITY; a triplet list that
+ * More than 64 kept edges into or out of one hit: that hit's articulations
+ * are dropped and etx_ctx_sync reports ETX_ERR_CAPACITY, as it does for a
+ * component of more than 8,192 hits (whose hits are then left unsorted;
+ * a component never spans events); a triplet list that
  * does not belong to these edges is reported as ETX_ERR_UNSORTED; more
  * tracks or hits than the capacities: ETX_ERR_CAPACITY and n_out = {0, 0}.
  * Rebuilds the context's edge index (as etx_build_triplets does).

@@ -129,9 +129,9 @@ __global__ void k_trip_emit(TripCtx c, int64_t n_hits, const int32_t* __restrict
 //  4. a track's hits are the end points of its edges (each component's
 //     distinct hits, merged for two components), at least min_hits of them.
 // At most kTbMaxDeg kept edges may enter or leave one hit (the group masks
-// are 32-bit); a hit above that is skipped and reported as a capacity error.
+// are 64-bit); a hit above that is skipped and reported as a capacity error.
 // ---------------------------------------------------------------------------
-constexpr int kTbMaxDeg = 32;
+constexpr int kTbMaxDeg = 64;
 constexpr int kTbFindCap = 1 << 22;
 constexpr int kTbUnionCap = 1 << 20;
 
@@ -244,13 +244,13 @@ __global__ void k_tb_hits(TbArgs a, int64_t n_hits) {
         if (a.tlogits[t] > a.tthr) tb_join(go, x, y);
       }
     // group pairs linked by a kept articulation (bit g_out of act[g_in])
-    uint32_t act[kTbMaxDeg];
-    for (int k = 0; k < ni; ++k) act[k] = 0u;
+    uint64_t act[kTbMaxDeg];
+    for (int k = 0; k < ni; ++k) act[k] = 0ull;
     for (int x = 0; x < ni; ++x)
       for (int y = 0; y < no; ++y) {
         const int64_t t = a0 + (int64_t)x * no + y;
         bad |= a.first[t] != I[x] || a.second[t] != O[y];
-        if (a.tlogits[t] > a.tthr) act[tb_rep(gi, x)] |= 1u << tb_rep(go, y);
+        if (a.tlogits[t] > a.tthr) act[tb_rep(gi, x)] |= 1ull << tb_rep(go, y);
       }
     if (bad) {
       set_err(a.err, DERR_RANGE);
@@ -264,12 +264,12 @@ __global__ void k_tb_hits(TbArgs a, int64_t n_hits) {
     int n_in_of[kTbMaxDeg];
     for (int y = 0; y < no; ++y) n_in_of[y] = 0;
     for (int x = 0; x < ni; ++x)
-      for (int y = 0; y < no; ++y) n_in_of[y] += (act[rx[x]] >> ry[y]) & 1u;
+      for (int y = 0; y < no; ++y) n_in_of[y] += (int)((act[rx[x]] >> ry[y]) & 1ull);
     for (int x = 0; x < ni; ++x) {
       int n_out = 0;
-      for (int y = 0; y < no; ++y) n_out += (act[rx[x]] >> ry[y]) & 1u;
+      for (int y = 0; y < no; ++y) n_out += (int)((act[rx[x]] >> ry[y]) & 1ull);
       for (int y = 0; y < no; ++y) {
-        const bool present = (act[rx[x]] >> ry[y]) & 1u;
+        const bool present = (act[rx[x]] >> ry[y]) & 1ull;
         a.art_flag[a0 + (int64_t)x * no + y] = !present ? 0 : (n_out >= 2 || n_in_of[y] >= 2 ? 2 : 1);
       }
     }
@@ -354,13 +354,21 @@ __global__ void k_tb_comp_hits(TripCtx c, const int32_t* __restrict__ root, int6
   }
 }
 
-// sort each component's hit list (short lists: insertion sort)
-__global__ void k_tb_sort_comp(const int32_t* __restrict__ standalone_or_any, const int32_t* __restrict__ comp_off,
-                               const int32_t* __restrict__ n_edges_dev, int32_t* __restrict__ comp_hits) {
+// Sort each component's hit list.  A component lies inside one event, so
+// its length is at most the event's hit count.  Lists of up to kTbShort hits:
+// one thread, insertion sort (k_tb_sort_short); longer ones: one block,
+// bitonic sort in shared memory (k_tb_sort_long), up to kTbLong hits; a
+// longer list is left unsorted and reported as a capacity error.
+constexpr int kTbShort = 64;
+constexpr int kTbLong = 8192;
+
+__global__ void k_tb_sort_short(const int32_t* __restrict__ comp_off,
+                                const int32_t* __restrict__ n_edges_dev, int32_t* __restrict__ comp_hits) {
   const int E = *n_edges_dev;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < E;
        r += (int64_t)gridDim.x * blockDim.x) {
     const int lo = comp_off[r], hi = comp_off[r + 1];
+    if (hi - lo > kTbShort) continue;
     for (int i = lo + 1; i < hi; ++i) {
       const int v = comp_hits[i];
       int j = i - 1;
@@ -371,7 +379,42 @@ __global__ void k_tb_sort_comp(const int32_t* __restrict__ standalone_or_any, co
       comp_hits[j + 1] = v;
     }
   }
-  (void)standalone_or_any;
+}
+
+__global__ void __launch_bounds__(1024) k_tb_sort_long(const int32_t* __restrict__ comp_off,
+                                                       const int32_t* __restrict__ n_edges_dev,
+                                                       int32_t* __restrict__ comp_hits, int* err) {
+  __shared__ int32_t v[kTbLong];
+  const int E = *n_edges_dev;
+  for (int64_t r = blockIdx.x; r < E; r += gridDim.x) {
+    const int lo = comp_off[r], n = comp_off[r + 1] - lo;
+    if (n <= kTbShort) continue;  // uniform across the block: every thread reads the same r
+    if (n > kTbLong) {
+      if (threadIdx.x == 0) set_err(err, DERR_CAPACITY);
+      continue;
+    }
+    int m = 1;
+    while (m < n) m <<= 1;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) v[i] = i < n ? comp_hits[lo + i] : INT32_MAX;
+    __syncthreads();
+    for (int k = 2; k <= m; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+          const int p = i ^ j;
+          if (p > i) {
+            const bool up = (i & k) == 0;
+            const int a = v[i], b = v[p];
+            if ((a > b) == up) {
+              v[i] = b;
+              v[p] = a;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) comp_hits[lo + i] = v[i];
+    __syncthreads();
+  }
 }
 
 // number of distinct values in the union of two sorted lists
@@ -597,8 +640,10 @@ cudaError_t launch_tracks_from_triplets(etx_ctx* ctx, const int32_t* src, const 
     launch(ctx, "tracks_comp_emit", k_tb_comp_hits<1>, grid(n_hits), 256, 0, s, c,
            (const int32_t*)root, n_hits, (int32_t*)nullptr, (const int32_t*)comp_off, fill,
            comp_hits);
-  launch(ctx, "tracks_comp_sort", k_tb_sort_comp, grid(E), 256, 0, s, (const int32_t*)nullptr,
-         (const int32_t*)comp_off, (const int32_t*)ctx->n_edges, comp_hits);
+  launch(ctx, "tracks_sort_short", k_tb_sort_short, grid(E), 256, 0, s, (const int32_t*)comp_off,
+         (const int32_t*)ctx->n_edges, comp_hits);
+  launch(ctx, "tracks_sort_long", k_tb_sort_long, (unsigned)ctx->n_sms * 2, 1024, 0, s,
+         (const int32_t*)comp_off, (const int32_t*)ctx->n_edges, comp_hits, ctx->d_err);
   // tracks: sizes, the min_hits filter, offsets, hits
   TbTracks tk{standalone_off, shared_off, art_flag, first, second, root, comp_off, comp_hits, E, A};
   if ((e = cudaMemsetAsync(keep, 0, (size_t)(T + 1) * 4, s)) != cudaSuccess) return e;
