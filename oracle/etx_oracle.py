@@ -281,7 +281,8 @@ def messages(e, src, dst, n_nodes):
     return np.concatenate([m_out, m_in], axis=1)
 
 
-def gnn_forward(weights, n_iters, x, y, z, src, dst, cache=None, gemm="fp64", act_scales=None):
+def gnn_forward(weights, n_iters, x, y, z, src, dst, cache=None, gemm="fp64", act_scales=None,
+                edge_store="fp32"):
     """Edge logits [E] (float64) of the interaction network.
 
     gemm="bf16" reads the mixed-precision configuration: the operands of every
@@ -294,8 +295,17 @@ def gnn_forward(weights, n_iters, x, y, z, src, dst, cache=None, gemm="fp64", ac
     with its static per-tensor scale (``quant_act_e4m3``): ``act_scales``
     lists them in ``act_scale_names`` order (powers of two; None = all 1).
     One scale covers a whole concatenated block input ([e, h_i, h_j] or
-    [h, m_out, m_in])."""
+    [h, m_out, m_in]).
+
+    edge_store="bf16" (with gemm="bf16") reads the variant that stores the
+    edge stream in BF16: e is rounded to BF16 where it is written (after the
+    edge encoder and after every residual edge update, the addition itself
+    exact), so the messages sum and the next blocks read the rounded values;
+    h stays exact."""
     op, op_w = GEMM_READINGS[gemm]
+    if edge_store not in ("fp32", "bf16") or (edge_store == "bf16" and gemm != "bf16"):
+        raise ValueError("edge_store='bf16' is read with gemm='bf16' only")
+    store = round_bf16 if edge_store == "bf16" else _identity
     n_sc = n_act_scales(n_iters)
     if act_scales is not None and gemm != "fp8":
         raise ValueError("activation scales belong to the e4m3 reading")
@@ -313,14 +323,14 @@ def gnn_forward(weights, n_iters, x, y, z, src, dst, cache=None, gemm="fp64", ac
                               np.asarray(z, np.float64)], axis=1),
                     weights["gnn_mu"], weights["gnn_sigma"])
     h = mlp_block(xin, weights, "node_enc", cache)
-    e = mlp_block(np.concatenate([h[src], h[dst]], axis=1), weights, "edge_enc", cache, q(0), op_w,
-                  q(1))
+    e = store(mlp_block(np.concatenate([h[src], h[dst]], axis=1), weights, "edge_enc", cache, q(0),
+                        op_w, q(1)))
     for k in range(n_iters):
         m = messages(e, src, dst, N)
         h = h + mlp_block(np.concatenate([h, m], axis=1), weights, f"node{k}", cache, q(2 + 4 * k),
                           op_w, q(3 + 4 * k))
-        e = e + mlp_block(np.concatenate([e, h[src], h[dst]], axis=1), weights, f"edge{k}", cache,
-                          q(4 + 4 * k), op_w, q(5 + 4 * k))
+        e = store(e + mlp_block(np.concatenate([e, h[src], h[dst]], axis=1), weights, f"edge{k}",
+                                cache, q(4 + 4 * k), op_w, q(5 + 4 * k)))
     a1 = q(n_sc - 1)(e) @ op_w(weights["cls.W1"]).T + weights["cls.b1"].astype(np.float64)
     y1, n1, s1 = layer_norm(a1, weights["cls.g1"].astype(np.float64),
                             weights["cls.be1"].astype(np.float64))

@@ -199,3 +199,27 @@ def test_activation_scale_values_and_saturation():
     assert O.fp8_act_scale(0.0) == 1.0
     with pytest.raises(ValueError):
         O.quant_act_e4m3(np.array([1.0]), 3.0)
+
+
+def test_stored_edge_stream_rounds_where_it_is_written():
+    """edge_store="bf16": the residual edge stream is rounded where it is
+    written.  e0 = [v, 0] from the edge encoder (v = 1 + 2^-9), the edge
+    network adds w = 1 + 2^-7 - 2^-10 (a constant emitter): exact e1 = 2 +
+    2^-7 + 2^-10, which BF16 (spacing 2^-6 in [2, 4)) rounds up to 2 + 2^-6;
+    stored, e0 is already 1 and 1 + w = 2 + 2^-7 - 2^-10 rounds down to 2.
+    The classifier's threshold at 2 + 2^-7 sees the difference, which the
+    plain BF16 reading (only operands rounded) does not have."""
+    v, t = FMT["bf16"]
+    w = 1.0 + 2.0 ** -7 - 2.0 ** -10
+    W, x = build("cls.in", v, t)            # edge encoder emits [v, 0]
+    for k, a in emitter(3 * H, [w, 0.0]).items():
+        W[f"edge0.{k}"] = np.asarray(a, np.float32)
+    for k, a in cls_threshold(0, 2.0 + 2.0 ** -7).items():
+        W[f"cls.{k}"] = np.asarray(a, np.float32)
+    z = np.zeros(2)
+    run = lambda **kw: O.gnn_forward(W, 1, x, z, z, np.array([0]), np.array([1]), **kw)[0]
+    z64, z16 = run(), run(gemm="bf16")
+    z16s = run(gemm="bf16", edge_store="bf16")
+    assert z64 > 0.1 and z16 > 0.1 and z16s < -0.1
+    with pytest.raises(ValueError):
+        run(gemm="fp8", edge_store="bf16")
