@@ -45,7 +45,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="batch500")
-    p.add_argument("--dtype", default="bf16", choices=["f32", "bf16", "fp8"])
+    p.add_argument("--dtype", default="bf16", choices=["f32", "bf16", "bf16s", "fp8"])
     p.add_argument("--cpu-seconds", type=float, default=15.0,
                    help="budget of the oracle CPU baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -180,14 +180,15 @@ def kernel_work(name: str, H: int, E: int, N: int, D: int, emb_widths) -> tuple:
     and written once, index arrays read once (per edge: e 2 x 4H, src/dst 8).
     """
     gnn_block = 2 * (3 * H * H + H * H)
+    es = 2 if name.endswith("_bf16s") else 4   # bytes per stored edge-stream value
     if name.startswith("gnn_edge_update"):
-        return E * gnn_block, E * (2 * 4 * H + 8)
+        return E * gnn_block, E * (2 * es * H + 8)
     if name.startswith("gnn_node_update"):
         return N * gnn_block, N * (2 * 4 * H + 2 * 4 * H)   # h read + write, m read
     if name.startswith("gnn_edge_encoder"):
-        return E * 2 * (2 * H * H + H * H), E * (4 * H + 8)
+        return E * 2 * (2 * H * H + H * H), E * (es * H + 8)
     if name.startswith("gnn_classifier"):
-        return E * 2 * (H * H + H), E * (4 * H + 4)
+        return E * 2 * (H * H + H), E * (es * H + 4)
     if name.startswith("embed"):
         w = list(emb_widths)
         return N * sum(2 * w[i] * w[i + 1] for i in range(len(w) - 1)), N * (12 + 4 * D)
@@ -690,7 +691,7 @@ def run_ours(args):
     per_dtype = {}
     if not args.skip_dtypes:
         ref = None
-        for dt in ("f32", "bf16", "fp8"):
+        for dt in ("f32", "bf16", "bf16s", "fp8"):
             tf.dtype = dt
             labels, _ = step()
             torch.cuda.synchronize()

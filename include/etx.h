@@ -60,8 +60,19 @@ typedef enum etx_status {
 } etx_status;
 
 /* Arithmetic type of the interaction-network GEMMs.  Accumulation, LayerNorm,
- * residual streams, message sums and logits are FP32 in every mode. */
-typedef enum etx_dtype { ETX_F32 = 0, ETX_BF16 = 1, ETX_FP8E4M3 = 2 } etx_dtype;
+ * message sums and logits are FP32 in every mode; so are the residual streams
+ * h and e, except in ETX_BF16_EDGE_STORE, which runs the BF16 GEMMs and stores
+ * the edge stream e in BF16 (each residual edge update is added in FP32 and
+ * the sum rounded to BF16 where it is written): half the bytes of the
+ * dominant edge traffic, at the cost of that extra rounding.  Inference only
+ * (train contexts reject it); after such a forward the final edge encodings
+ * are BF16, so etx_classify_triplets refuses them (ETX_ERR_STATE). */
+typedef enum etx_dtype {
+  ETX_F32 = 0,
+  ETX_BF16 = 1,
+  ETX_FP8E4M3 = 2,
+  ETX_BF16_EDGE_STORE = 3
+} etx_dtype;
 
 #define ETX_MAX_EMB_LAYERS 8
 

@@ -547,8 +547,10 @@ etx_status etx_gnn_forward(etx_ctx* ctx, const float* x, const float* y, const f
   if (n_hits < 0 || n_hits > ctx->cfg.max_hits) return fail(ctx, ETX_ERR_CAPACITY, "n_hits exceeds the context capacity");
   if (!edge_offsets || !src || !dst || !logits) return fail(ctx, ETX_ERR_ARG, "NULL edge array");
   if (n_hits > 0 && (!x || !y || !z)) return fail(ctx, ETX_ERR_ARG, "NULL hit array");
-  if (dtype != ETX_F32 && dtype != ETX_BF16 && dtype != ETX_FP8E4M3)
+  if (dtype != ETX_F32 && dtype != ETX_BF16 && dtype != ETX_FP8E4M3 && dtype != ETX_BF16_EDGE_STORE)
     return fail(ctx, ETX_ERR_ARG, "unknown dtype");
+  if (dtype == ETX_BF16_EDGE_STORE && ctx->cfg.train)
+    return fail(ctx, ETX_ERR_UNSUPPORTED, "BF16 edge storage is for inference (train context)");
   if (dtype != ETX_F32 && !ctx->w.has_tc)
     return fail(ctx, ETX_ERR_UNSUPPORTED, "the tensor-core path needs hidden == 128");
   if (n_hits == 0) return ETX_OK;  // no hits, hence no edges: nothing to compute
@@ -786,6 +788,9 @@ etx_status etx_classify_triplets(etx_ctx* ctx, const int32_t* first, const int32
                                  void* stream) {
   if (!ctx) return ETX_ERR_ARG;
   if (!ctx->trip_loaded) return fail(ctx, ETX_ERR_STATE, "triplet weights not loaded");
+  if (ctx->e_bf16)
+    return fail(ctx, ETX_ERR_STATE, "the last forward stored the edge encodings in BF16; classify "
+                                    "triplets after an FP32-storage forward");
   if (!counts || (capacity > 0 && (!first || !second || !logits))) return fail(ctx, ETX_ERR_ARG, "NULL array");
   if (capacity < 0 || capacity >= ((int64_t)1 << 31)) return fail(ctx, ETX_ERR_ARG, "capacity out of range");
   cudaSetDevice(ctx->device);

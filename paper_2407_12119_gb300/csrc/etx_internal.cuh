@@ -118,6 +118,9 @@ struct etx_ctx {
 
   // components
   int32_t* parent = nullptr;     // [max_hits]
+  // the last forward stored the edge stream in BF16 (dtype ETX_BF16_EDGE_STORE):
+  // ctx->e then holds BF16 rows, which the FP32 readers of e must not use
+  bool e_bf16 = false;
 
   // triplet classifiers (etx_load_triplet_weights): articulations, elbows
   float* w_trip = nullptr;
@@ -199,14 +202,15 @@ cudaError_t launch_adam(etx_ctx* ctx, float* p, const float* g, float* m, float*
 // ctx->h_lp = h rounded to BF16 (or e4m3) for rows [0, N)
 cudaError_t launch_h_lowp(etx_ctx* ctx, int64_t N, bool f8, cudaStream_t s);
 // f8: e4m3 operands (kind::f8f6f4), else BF16 (kind::f16)
+// es: the edge stream is stored in BF16 (dtype ETX_BF16_EDGE_STORE)
 cudaError_t launch_edge_encoder_tc(etx_ctx* ctx, int64_t N, const int32_t* src, const int32_t* dst,
-                                   const int32_t* n_edges_dev, bool f8, cudaStream_t s);
+                                   const int32_t* n_edges_dev, bool f8, bool es, cudaStream_t s);
 cudaError_t launch_node_update_tc(etx_ctx* ctx, int k, int64_t N, bool f8, cudaStream_t s);
 cudaError_t launch_edge_update_tc(etx_ctx* ctx, int k, int64_t N, const int32_t* src,
-                                  const int32_t* dst, const int32_t* n_edges_dev, bool f8,
+                                  const int32_t* dst, const int32_t* n_edges_dev, bool f8, bool es,
                                   cudaStream_t s);
 cudaError_t launch_classifier_tc(etx_ctx* ctx, int64_t N, const int32_t* n_edges_dev, float* logits,
-                                 bool f8, cudaStream_t s);
+                                 bool f8, bool es, cudaStream_t s);
 
 // graph.cu: hit checks and ctx->plane_off (first hit of each plane, per event)
 cudaError_t launch_plane_bins(etx_ctx* ctx, const int8_t* plane, const int32_t* hit_offsets,

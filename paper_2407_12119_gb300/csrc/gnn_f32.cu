@@ -128,7 +128,8 @@ __device__ __forceinline__ uint32_t e4m3x4(float a, float b, float c, float d) {
 
 // OUTT 0: FP32 messages; 1: rounded to BF16, 2: to e4m3 (the tensor-core node
 // update's operand type; sums are FP32 either way), rows of 2H values at m.
-template <int H, int OUTT = 0>
+// EIN: the edge rows are stored in BF16 (rows of H values, 2H bytes).
+template <int H, int OUTT = 0, bool EIN = false>
 __global__ void __launch_bounds__(256, 2)  // 128 registers: sixteen rows in flight per warp
 k_messages(const float* __restrict__ e, const int32_t* __restrict__ out_off,
                            const int32_t* __restrict__ in_off, const int32_t* __restrict__ perm,
@@ -148,7 +149,15 @@ k_messages(const float* __restrict__ e, const int32_t* __restrict__ out_off,
     const int i0 = min(max(in_off[l], 0), E), i1 = min(max(in_off[l + 1], 0), E);
     float4 so = make_float4(0.f, 0.f, 0.f, 0.f), si = so;
     auto add = [](float4& a, const float4& v) { a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w; };
-    auto row = [&](int64_t r) { return __ldg(reinterpret_cast<const float4*>(e + r * H + c)); };
+    auto row = [&](int64_t r) {
+      if constexpr (EIN) {
+        const uint2 u = __ldg(reinterpret_cast<const uint2*>(reinterpret_cast<const uint16_t*>(e) + r * H + c));
+        return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                           __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+      } else {
+        return __ldg(reinterpret_cast<const float4*>(e + r * H + c));
+      }
+    };
     // Sixteen (then eight) rows in flight before they are added (in edge order,
     // so the sums are those of a plain loop): a hit is done in a few memory
     // latencies, and the in-rows of a hit, read moments earlier as out-rows of
@@ -353,6 +362,8 @@ cudaError_t forward(etx_ctx* ctx, const float* x, const float* y, const float* z
                     float* logits, etx_dtype dtype, cudaStream_t s) {
   const bool tc = dtype != ETX_F32;
   const bool f8 = dtype == ETX_FP8E4M3;
+  const bool es = dtype == ETX_BF16_EDGE_STORE;  // the edge stream e stored in BF16
+  ctx->e_bf16 = es;
   const int64_t Ecap = ctx->cfg.max_edges;
   MlpArgs a{};
   a.n_rows = N;
@@ -376,7 +387,7 @@ cudaError_t forward(etx_ctx* ctx, const float* x, const float* y, const float* z
   launch_mlp<H, NODE_ENC>(ctx, a, N, s);
   if (tc) {
     chain(launch_h_lowp(ctx, N, f8, s));
-    chain(launch_edge_encoder_tc(ctx, N, src, dst, n_edges_dev, f8, s));
+    chain(launch_edge_encoder_tc(ctx, N, src, dst, n_edges_dev, f8, es, s));
   } else {
     a.blk = ctx->w.edge_enc;
     launch_mlp<H, EDGE_ENC>(ctx, a, Ecap, s);
@@ -387,14 +398,15 @@ cudaError_t forward(etx_ctx* ctx, const float* x, const float* y, const float* z
   for (int k = 0; k < ctx->cfg.n_iters; ++k) {
     if (N > 0) {
       // the tensor-core node update takes the messages in its operand type
-      auto kern = !tc ? k_messages<H, 0> : (f8 ? k_messages<H, 2> : k_messages<H, 1>);
+      auto kern = !tc ? k_messages<H, 0>
+                      : (f8 ? k_messages<H, 2> : (es ? k_messages<H, 1, true> : k_messages<H, 1>));
       const float inv = (tc && f8 && 2 + 4 * k < (int)ctx->fp8_act.size()) ? 1.f / ctx->fp8_act[2 + 4 * k] : 1.f;
       launch(ctx, "gnn_messages", kern, msg_grid, 256, 0, s, ctx->e, ctx->out_off, ctx->in_off,
              ctx->perm_in, n_edges_dev, (int)N, ctx->m, inv);
     }
     if (tc) {
       chain(launch_node_update_tc(ctx, k, N, f8, s));
-      chain(launch_edge_update_tc(ctx, k, N, src, dst, n_edges_dev, f8, s));
+      chain(launch_edge_update_tc(ctx, k, N, src, dst, n_edges_dev, f8, es, s));
     } else {
       a.blk = ctx->w.node[k];
       launch_mlp<H, NODE_UPD>(ctx, a, N, s);
@@ -404,7 +416,7 @@ cudaError_t forward(etx_ctx* ctx, const float* x, const float* y, const float* z
     save(k + 1);
   }
   if (tc) {
-    chain(launch_classifier_tc(ctx, N, n_edges_dev, logits, f8, s));
+    chain(launch_classifier_tc(ctx, N, n_edges_dev, logits, f8, es, s));
   } else {
     a.cls = ctx->w.cls;
     launch_mlp<H, CLS>(ctx, a, Ecap, s);

@@ -123,6 +123,7 @@ struct TcArgs {
   float in_inv, mid_inv, hlp_inv;
   const float* bcls;  // [1]
   uint8_t* h_lp;      // h rounded to the operand type (node update writes it)
+  uint8_t* e_lp;      // edge stream stored in BF16 (ES kernels): rows of H values, 2H bytes
   const uint8_t* m_lp;  // node update: [m_out, m_in] rounded to the operand type, rows of 2H
   int* err;
   // b1 g1 be1 b2 g2 be2 of the block (or b1 g1 be1, -, -, -, w2 of the classifier), by
@@ -286,8 +287,13 @@ __device__ __forceinline__ void affine(float* __restrict__ d, const float* __res
   }
 }
 
-template <int MODE, bool F8, int NS>
+// ES (BF16 only; edge encoder, edge update, classifier): the edge stream e is
+// stored in BF16 (a.e_lp) instead of FP32: the producers copy its rows into
+// the ring like the gathered node rows, the epilogue adds the BF16 residual
+// and writes the sum rounded to BF16.
+template <int MODE, bool F8, int NS, bool ES = false>
 __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(const __grid_constant__ TcArgs a) {
+  static_assert(!ES || (!F8 && MODE != TC_NODE_UPD), "BF16 edge storage: BF16 edge blocks only");
   using C = Cfg<MODE, F8, NS>;
   using EL = Elt<F8>;
   constexpr int NSTAGE = C::NST;
@@ -360,9 +366,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(const __grid_constant__ T
     constexpr int NG = (TM * 8 + PROD_THREADS - 1) / PROD_THREADS;        // 16-byte copies per thread
     // edge blocks copy [h_i, h_j] from the low-precision h; the node update
     // copies [m_out, m_in] from the low-precision messages (its own row)
-    constexpr bool GATHER = MODE != TC_CLS;
+    constexpr bool GATHER = MODE != TC_CLS || ES;
     // 64-column FP32 steps per tile done by the threads (the copies do the rest)
-    constexpr int SE = GATHER ? (MODE == TC_EDGE_ENC ? 0 : H / SUB) : C::KS;
+    constexpr int SE = GATHER ? ((MODE == TC_EDGE_ENC || ES) ? 0 : H / SUB) : C::KS;
+    // ES: the first H / KCH chunks of the edge blocks are the tile's own e rows
+    constexpr int KOWN = (ES && MODE != TC_EDGE_ENC) ? H / EL::KCH : 0;
     // Loads of step c (64 columns of the FP32 block input) of local tile t.
     auto fetch = [&](int64_t t, int c, float4 (&f)[NF]) {
       if (t >= my_tiles) return;
@@ -423,38 +431,42 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(const __grid_constant__ T
       const int64_t row0 = (blockIdx.x + t * gridDim.x) * TM;
       const int64_t rows = n_rows - row0 < TM ? n_rows - row0 : TM;
       if (rows <= 0) return;
-      const float* base = a.e + row0 * H;
-      prefetch_l2_bulk(base, (uint32_t)(rows * H * sizeof(float)));
+      if constexpr (ES)
+        prefetch_l2_bulk(a.e_lp + row0 * 2 * H, (uint32_t)(rows * H * 2));
+      else
+        prefetch_l2_bulk(a.e + row0 * H, (uint32_t)(rows * H * sizeof(float)));
     };
     float4 b0[NF], b1[NF];
     if constexpr (GATHER) {
       constexpr int KE = (SE * SUB) / EL::KCH;  // chunks of FP32 stream columns
       constexpr int KH = H / EL::KCH;           // chunks per gathered node row
       // node indices of this thread's copy rows, loaded one tile ahead of use
-      int gs[NG], gd[NG], ns[NG], nd[NG];
-      auto load_idx = [&](int64_t t, int (&xs)[NG], int (&xd)[NG]) {
+      int gs[NG], gd[NG], ns[NG], nd[NG], go[NG], no[NG];
+      auto load_idx = [&](int64_t t, int (&xs)[NG], int (&xd)[NG], int (&xo)[NG]) {
         const int64_t r0 = (blockIdx.x + t * gridDim.x) * TM;
 #pragma unroll
         for (int k = 0; k < NG; ++k) {
           const int fi = pt + PROD_THREADS * k;
           const int64_t gr = r0 + (fi >> 3);
           const bool ok = t < my_tiles && fi < TM * 8 && gr < n_rows;
-          if constexpr (MODE == TC_NODE_UPD) {
-            xs[k] = xd[k] = ok ? (int)gr : 0;
+          xo[k] = ok ? (int)gr : 0;  // the tile's own row (rows past the end read row 0)
+          if constexpr (MODE == TC_NODE_UPD || MODE == TC_CLS) {
+            xs[k] = xd[k] = xo[k];
           } else {
             xs[k] = ok ? min(max(a.src[gr], 0), max(nn - 1, 0)) : 0;
             xd[k] = ok ? min(max(a.dst[gr], 0), max(nn - 1, 0)) : 0;
           }
         }
       };
-      load_idx(0, gs, gd);
+      load_idx(0, gs, gd, go);
       if constexpr (SE > 0) {
         fetch(0, 0, b0);
         fetch(0, 1, b1);
       }
       for (int64_t t = 0; t < my_tiles; ++t) {
         if constexpr (MODE == TC_EDGE_UPD && !F8) prefetch_tile(t + 1);
-        load_idx(t + 1, ns, nd);
+        if constexpr (MODE == TC_CLS) prefetch_tile(t + 2);
+        load_idx(t + 1, ns, nd, no);
         if constexpr (SE > 0) {
           if (!store(t, 0, b0)) break;
           if (!store(t, 1, b1)) break;
@@ -474,17 +486,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(const __grid_constant__ T
             ok = false;
             break;
           }
-          const int hc = c - KE;
-          // source rows: node rows of h (H values) or message rows (2H values)
+          // source rows: the tile's own e rows (ES, first KOWN chunks), node rows of h
+          // (H values) or message rows (2H values)
+          const bool own = c < KOWN;
+          const int hc = own ? c : c - KE - KOWN;
           const int rowbytes = (MODE == TC_NODE_UPD ? 2 : 1) * (F8 ? H : 2 * H);
-          const int cbase = (MODE == TC_NODE_UPD ? hc : hc % KH) * 128;  // byte offset in the row
-          const uint8_t* srcb = MODE == TC_NODE_UPD ? a.m_lp : a.h_lp;
+          const int cbase = (MODE == TC_NODE_UPD || own ? hc : hc % KH) * 128;  // byte offset in the row
+          const uint8_t* srcb = own ? a.e_lp : (MODE == TC_NODE_UPD ? a.m_lp : a.h_lp);
 #pragma unroll
           for (int k = 0; k < NG; ++k) {
             const int fi = pt + PROD_THREADS * k;
+            const int row = own ? go[k] : (hc < KH ? gs[k] : gd[k]);
             if (fi < TM * 8)
               cp_async16(sA + slot * CHUNK + sw128(fi >> 3, fi & 7),
-                         srcb + (int64_t)(hc < KH ? gs[k] : gd[k]) * rowbytes + cbase + 16 * (fi & 7));
+                         srcb + (int64_t)row * rowbytes + cbase + 16 * (fi & 7));
           }
           cp_async_arrive(&bars[B_FULL + slot]);
           __syncwarp();
@@ -495,6 +510,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(const __grid_constant__ T
         for (int k = 0; k < NG; ++k) {
           gs[k] = ns[k];
           gd[k] = nd[k];
+          go[k] = no[k];
         }
       }
     } else {
@@ -716,8 +732,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(const __grid_constant__ T
 #pragma unroll
             for (int it = 0; it < 4; ++it) {
               res[it] = make_float4(0.f, 0.f, 0.f, 0.f);
-              if (MODE != TC_EDGE_ENC && 8 * it < nval)
-                res[it] = *reinterpret_cast<const float4*>(resid + coff + 8 * it * H + col);
+              if (MODE != TC_EDGE_ENC && 8 * it < nval) {
+                if constexpr (ES) {
+                  const uint2 u = *reinterpret_cast<const uint2*>(a.e_lp + 2 * (coff + 8 * it * H + col));
+                  res[it] = make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                                        __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+                } else {
+                  res[it] = *reinterpret_cast<const float4*>(resid + coff + 8 * it * H + col);
+                }
+              }
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u)
@@ -734,7 +757,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(const __grid_constant__ T
                 const float2 o1 = __fadd2_rn(f2(v.z, v.w), f2(res[it].z, res[it].w));
                 const int64_t el = coff + 8 * it * H + col;  // element index in the stream
                 // streaming store: the row is not read again in this launch
-                __stcs(reinterpret_cast<float4*>(outp + el), make_float4(o0.x, o0.y, o1.x, o1.y));
+                if constexpr (ES)
+                  __stcs(reinterpret_cast<uint2*>(a.e_lp + 2 * el),
+                         make_uint2(pack_bf16(o0.x, o0.y), pack_bf16(o1.x, o1.y)));
+                else
+                  __stcs(reinterpret_cast<float4*>(outp + el), make_float4(o0.x, o0.y, o1.x, o1.y));
                 if constexpr (MODE == TC_NODE_UPD) {  // the copy the edge blocks gather
                   if constexpr (F8)
                     *reinterpret_cast<uint32_t*>(a.h_lp + el) =
@@ -760,13 +787,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(const __grid_constant__ T
   }
 }
 
-template <int MODE, bool F8, int NS>
+template <int MODE, bool F8, int NS, bool ES>
 cudaError_t launch_tc_ns(etx_ctx* ctx, const char* name, const TcArgs& a, int64_t max_rows,
                          cudaStream_t s) {
   using C = Cfg<MODE, F8, NS>;
   static bool attr_set[8] = {false};
   if (!attr_set[ctx->device & 7]) {
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_tc<MODE, F8, NS>,
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_tc<MODE, F8, NS, ES>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     attr_set[ctx->device & 7] = true;
@@ -774,19 +801,19 @@ cudaError_t launch_tc_ns(etx_ctx* ctx, const char* name, const TcArgs& a, int64_
   const int64_t tiles = (max_rows + TM - 1) / TM;
   if (tiles == 0) return cudaSuccess;
   const int grid = (int)(tiles < ctx->n_sms ? tiles : ctx->n_sms);
-  launch(ctx, name, k_mlp_tc<MODE, F8, NS>, grid, THREADS, C::SMEM, s, a);
+  launch(ctx, name, k_mlp_tc<MODE, F8, NS, ES>, grid, THREADS, C::SMEM, s, a);
   return cudaGetLastError();
 }
 
 // ring depth from the context's tuning (2 to 5 slots; capped by shared memory)
-template <int MODE, bool F8>
+template <int MODE, bool F8, bool ES = false>
 cudaError_t launch_tc(etx_ctx* ctx, const char* name, const TcArgs& a, int64_t max_rows,
                       cudaStream_t s) {
   switch (ctx->tc_stages[MODE][F8 ? 1 : 0]) {
-    case 2: return launch_tc_ns<MODE, F8, 2>(ctx, name, a, max_rows, s);
-    case 4: return launch_tc_ns<MODE, F8, 4>(ctx, name, a, max_rows, s);
-    case 5: return launch_tc_ns<MODE, F8, 5>(ctx, name, a, max_rows, s);
-    default: return launch_tc_ns<MODE, F8, 3>(ctx, name, a, max_rows, s);
+    case 2: return launch_tc_ns<MODE, F8, 2, ES>(ctx, name, a, max_rows, s);
+    case 4: return launch_tc_ns<MODE, F8, 4, ES>(ctx, name, a, max_rows, s);
+    case 5: return launch_tc_ns<MODE, F8, 5, ES>(ctx, name, a, max_rows, s);
+    default: return launch_tc_ns<MODE, F8, 3, ES>(ctx, name, a, max_rows, s);
   }
 }
 
@@ -818,6 +845,7 @@ TcArgs base_args(etx_ctx* ctx, int64_t N, const int32_t* src, const int32_t* dst
   a.h_out = ctx->h;
   a.logits = logits;
   a.h_lp = ctx->h_lp;
+  a.e_lp = reinterpret_cast<uint8_t*>(ctx->e);
   a.err = ctx->d_err;
   a.in_inv = a.mid_inv = a.hlp_inv = 1.f;
   return a;
@@ -848,9 +876,13 @@ void set_block(etx_ctx* ctx, TcArgs& a, const BlockF32& f, const BlockTC& t, boo
   for (int i = 0; i < 6; ++i) host_params(ctx, src[i], a.prm[i]);
 }
 
+// es: the edge stream is stored in BF16 (BF16 edge blocks only)
 template <int MODE>
 cudaError_t launch_any(etx_ctx* ctx, bool f8, const char* n16, const char* n8, const TcArgs& a,
-                       int64_t max_rows, cudaStream_t s) {
+                       int64_t max_rows, cudaStream_t s, bool es = false, const char* n16s = nullptr) {
+  if constexpr (MODE != TC_NODE_UPD) {
+    if (es) return launch_tc<MODE, false, true>(ctx, n16s, a, max_rows, s);
+  }
   return f8 ? launch_tc<MODE, true>(ctx, n8, a, max_rows, s)
             : launch_tc<MODE, false>(ctx, n16, a, max_rows, s);
 }
@@ -858,11 +890,11 @@ cudaError_t launch_any(etx_ctx* ctx, bool f8, const char* n16, const char* n8, c
 }  // namespace
 
 cudaError_t launch_edge_encoder_tc(etx_ctx* ctx, int64_t N, const int32_t* src, const int32_t* dst,
-                                   const int32_t* n_edges_dev, bool f8, cudaStream_t s) {
+                                   const int32_t* n_edges_dev, bool f8, bool es, cudaStream_t s) {
   TcArgs a = base_args(ctx, N, src, dst, n_edges_dev, nullptr);
   set_block(ctx, a, ctx->w.edge_enc, ctx->w.edge_enc_tc, f8, act_scale(ctx, 0), act_scale(ctx, 1));
   return launch_any<TC_EDGE_ENC>(ctx, f8, "gnn_edge_encoder_bf16", "gnn_edge_encoder_fp8", a,
-                                 ctx->cfg.max_edges, s);
+                                 ctx->cfg.max_edges, s, es, "gnn_edge_encoder_bf16s");
 }
 
 cudaError_t launch_node_update_tc(etx_ctx* ctx, int k, int64_t N, bool f8, cudaStream_t s) {
@@ -876,13 +908,13 @@ cudaError_t launch_node_update_tc(etx_ctx* ctx, int k, int64_t N, bool f8, cudaS
 }
 
 cudaError_t launch_edge_update_tc(etx_ctx* ctx, int k, int64_t N, const int32_t* src,
-                                  const int32_t* dst, const int32_t* n_edges_dev, bool f8,
+                                  const int32_t* dst, const int32_t* n_edges_dev, bool f8, bool es,
                                   cudaStream_t s) {
   TcArgs a = base_args(ctx, N, src, dst, n_edges_dev, nullptr);
   set_block(ctx, a, ctx->w.edge[k], ctx->w.edge_tc[k], f8, act_scale(ctx, 4 + 4 * k),
             act_scale(ctx, 5 + 4 * k));
   return launch_any<TC_EDGE_UPD>(ctx, f8, "gnn_edge_update_bf16", "gnn_edge_update_fp8", a,
-                                 ctx->cfg.max_edges, s);
+                                 ctx->cfg.max_edges, s, es, "gnn_edge_update_bf16s");
 }
 
 cudaError_t launch_h_lowp(etx_ctx* ctx, int64_t N, bool f8, cudaStream_t s) {
@@ -901,7 +933,7 @@ cudaError_t launch_h_lowp(etx_ctx* ctx, int64_t N, bool f8, cudaStream_t s) {
 }
 
 cudaError_t launch_classifier_tc(etx_ctx* ctx, int64_t N, const int32_t* n_edges_dev, float* logits,
-                                 bool f8, cudaStream_t s) {
+                                 bool f8, bool es, cudaStream_t s) {
   TcArgs a = base_args(ctx, N, nullptr, nullptr, n_edges_dev, logits);
   const BlockTC& t = ctx->w.cls_tc;
   const float s_in = act_scale(ctx, 4 * ctx->cfg.n_iters + 2);
@@ -915,7 +947,7 @@ cudaError_t launch_classifier_tc(etx_ctx* ctx, int64_t N, const int32_t* n_edges
   host_params(ctx, ctx->w.cls.w2, a.prm[6]);
   a.bcls = ctx->w.cls.b2;
   return launch_any<TC_CLS>(ctx, f8, "gnn_classifier_bf16", "gnn_classifier_fp8", a,
-                            ctx->cfg.max_edges, s);
+                            ctx->cfg.max_edges, s, es, "gnn_classifier_bf16s");
 }
 
 }  // namespace etx

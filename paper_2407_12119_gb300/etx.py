@@ -23,7 +23,7 @@ ETX_ERR_CUDA, ETX_ERR_TIMEOUT, ETX_ERR_UNSUPPORTED, ETX_ERR_STATE = 4, 5, 6, 7
 _STATUS_NAMES = {0: "ETX_OK", 1: "ETX_ERR_ARG", 2: "ETX_ERR_UNSORTED", 3: "ETX_ERR_CAPACITY",
                  4: "ETX_ERR_CUDA", 5: "ETX_ERR_TIMEOUT", 6: "ETX_ERR_UNSUPPORTED",
                  7: "ETX_ERR_STATE"}
-DTYPES = {"f32": 0, "bf16": 1, "fp8": 2}
+DTYPES = {"f32": 0, "bf16": 1, "fp8": 2, "bf16s": 3}  # bf16s: BF16 GEMMs, edge stream stored in BF16
 MAX_EMB_LAYERS = 8
 
 EXPORTED = ["etx_ctx_create", "etx_ctx_destroy", "etx_last_error", "etx_weights_size",

@@ -21,8 +21,8 @@ NEAR_CUT = 1e-5
 # max-abs logit error against the oracle's reading of the dtype, as in the stage tests
 # (e4m3: rounding-boundary flips between FP32 and FP64 operands, each a whole e4m3 step,
 # put the largest difference at the scale of the format's own error)
-LOGIT_TOL = {"f32": 1e-4, "bf16": 2e-2, "fp8": 0.25}
-READING = {"f32": "fp64", "bf16": "bf16", "fp8": "fp8"}
+LOGIT_TOL = {"f32": 1e-4, "bf16": 2e-2, "bf16s": 2e-2, "fp8": 0.25}
+READING = {"f32": "fp64", "bf16": "bf16", "bf16s": "bf16", "fp8": "fp8"}
 
 
 @pytest.fixture(scope="module")
@@ -84,7 +84,8 @@ def check_event(wl, b, W, g, ev, dtype):
     diff = set(zip(gs.tolist(), gd.tolist())) ^ set(zip(s.tolist(), d.tolist()))
     assert all(near_cut(emb64, i, j, e.plane, 0, hi - lo, m.radius, m.k_max) for i, j in diff)
     # logits, stage-isolated: the oracle on the GPU's own graph of this event
-    kw = {"act_scales": m.fp8_act_scales} if dtype == "fp8" else {}
+    kw = ({"act_scales": m.fp8_act_scales} if dtype == "fp8" else
+          {"edge_store": "bf16"} if dtype == "bf16s" else {})
     ref = O.gnn_forward(W, m.n_iters, e.x, e.y, e.z, gs, gd, gemm=READING[dtype], **kw)
     err = np.abs(g["logits"][e0:e1] - ref).max() if gs.size else 0.0
     assert err <= LOGIT_TOL[dtype], (ev, err)
@@ -101,7 +102,7 @@ def check_event(wl, b, W, g, ev, dtype):
             f"max |logit err| {err:.2e}, mask flips vs the reading {flips}")
 
 
-@pytest.mark.parametrize("dtype", ["f32", "bf16", "fp8"])
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "bf16s", "fp8"])
 def test_full_batch500_sampled_events(pipeline, dtype):
     wl, b, W, g = run_full(pipeline, "batch500", dtype)
     sizes = np.diff(b.hit_offsets)
