@@ -746,7 +746,12 @@ def run_ours(args):
                    "track_metrics": physics(sweep_lab),
                    "track_metrics_exact": physics(labels)}
     # triplets of the kept edges and their two classifiers (Sec. 5.3), on the
-    # final edge encodings of the step above
+    # final edge encodings of the step above (FP32-stored: the classifiers read
+    # FP32 encodings, so a BF16-storage step is re-run with FP32 storage)
+    if tf.dtype == "bf16s":
+        tf.dtype = "bf16"
+        step()
+        tf.dtype = args.dtype
     from velo_synth import make_triplet_weights, pack_triplet_blob
     tf.ctx.load_triplet_weights(pack_triplet_blob(m, make_triplet_weights(m)))
     trip_cap = 2 * E
