@@ -221,6 +221,8 @@ etx_status etx_ctx_create(const etx_config* cfg, int32_t device, etx_ctx** out) 
   chk(dmalloc(ctx, &ctx->d_err, 1, "error word"));
   chk(dmalloc(ctx, &ctx->n_edges, 1, "edge count"));
   chk(dmalloc(ctx, &ctx->small, 8, "reduction scratch"));
+  ctx->red_part_n = (int64_t)ctx->n_sms * 16;
+  chk(dmalloc(ctx, &ctx->red_part, (size_t)ctx->red_part_n, "loss partial sums"));
   chk(dmalloc(ctx, &ctx->plane_off, (size_t)B * (cfg->n_planes + 1), "plane offsets"));
   chk(dmalloc(ctx, &ctx->hit_cnt, (size_t)N + 1, "hit counts"));
   ctx->scan_tmp_ints = scan_tmp_ints(N + 1) + 8;
@@ -245,6 +247,8 @@ etx_status etx_ctx_create(const etx_config* cfg, int32_t device, etx_ctx** out) 
     float** rows[] = {&ctx->bw_R1, &ctx->bw_DA1, &ctx->bw_DY1, &ctx->bw_DY1N1,
                       &ctx->bw_DA2, &ctx->bw_DY2, &ctx->bw_DY2N2};
     for (float** q : rows) chk(dmalloc(ctx, q, R * H, "backward row factors"));
+    const size_t part = std::max<size_t>((size_t)ctx->n_sms * H * 3 * H, (size_t)ctx->n_sms * 4 * H);
+    chk(dmalloc(ctx, &ctx->bw_part, part, "partial gradients"));
   }
   if (st == ETX_OK) {
     e = cudaMemset(ctx->d_err, 0, sizeof(int));
@@ -270,7 +274,7 @@ etx_status etx_ctx_destroy(etx_ctx* ctx) {
                   ctx->perm_in, ctx->h, ctx->m, ctx->e, ctx->parent, ctx->h_ck, ctx->e_ck,
                   ctx->de, ctx->dh, ctx->bw_X, ctx->bw_DX, ctx->bw_R1, ctx->bw_DA1, ctx->bw_DY1,
                   ctx->bw_DY1N1, ctx->bw_DA2, ctx->bw_DY2, ctx->bw_DY2N2, ctx->h_lp,
-                  ctx->small, ctx->w_trip};
+                  ctx->small, ctx->w_trip, ctx->bw_part, ctx->red_part};
   for (void* p : bufs)
     if (p) cudaFree(p);
   for (auto& r : ctx->prof) {

@@ -135,6 +135,12 @@ struct etx_ctx {
   float *bw_X = nullptr, *bw_DX = nullptr;          // [rows * 3H]
   float *bw_R1 = nullptr, *bw_DA1 = nullptr, *bw_DY1 = nullptr, *bw_DY1N1 = nullptr;  // [rows * H]
   float *bw_DA2 = nullptr, *bw_DY2 = nullptr, *bw_DY2N2 = nullptr;
+  // per-split partial gradients, added in a fixed order (deterministic reductions):
+  // n_sms x H x 3H floats
+  float* bw_part = nullptr;
+  // per-block partial sums of the loss, red_part_n floats (every context)
+  float* red_part = nullptr;
+  int64_t red_part_n = 0;
   bool fwd_saved = false;        // a training forward ran since the weights were loaded
   const float *fwd_x = nullptr, *fwd_y = nullptr, *fwd_z = nullptr;
   const int32_t *fwd_src = nullptr, *fwd_dst = nullptr;

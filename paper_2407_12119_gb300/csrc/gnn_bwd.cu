@@ -362,7 +362,8 @@ __global__ void __launch_bounds__(kTileThreads) k_block_bwd(BwdArgs a) {
 // Grid: (M / 64) x ceil(N / 128) x splits over r; each CTA adds its partial.
 __global__ void __launch_bounds__(kTileThreads)
 k_gemm_tn(const float* __restrict__ A, int lda, const float* __restrict__ B, int ldb, int M, int N,
-          int64_t R_host, const int32_t* __restrict__ R_dev, float* __restrict__ C) {
+          int64_t R_host, const int32_t* __restrict__ R_dev, float* __restrict__ C,
+          float* __restrict__ P) {
   constexpr int NT = 128;
   __shared__ __align__(16) float As[kTileM * kLdaChunk];
   __shared__ __align__(16) float Ws[kKC * NT];
@@ -390,7 +391,11 @@ k_gemm_tn(const float* __restrict__ A, int lda, const float* __restrict__ B, int
     __syncthreads();
     acc.template mma<kKC>(As, kLdaChunk, 0, Ws, ty, tx);
   }
-  if (c_lo >= c_hi) return;
+  // P != NULL: this split's partial tile (zeros if it had no rows) goes to
+  // P[z][M][N] and k_reduce_parts adds the splits in order (fixed summation
+  // order: the same inputs give the same bits); otherwise atomics into C.
+  if (!P && c_lo >= c_hi) return;
+  float* Pz = P ? P + (int64_t)blockIdx.z * M * N : nullptr;
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     const int m = m0 + ty * 4 + r;
@@ -398,35 +403,77 @@ k_gemm_tn(const float* __restrict__ A, int lda, const float* __restrict__ B, int
 #pragma unroll
     for (int j = 0; j < NT / 16; ++j) {
       const int n = n0 + ColMap<NT>::col(tx, j);
-      if (n < N) atomicAdd(C + (int64_t)m * N + n, acc.v[r][j]);
+      if (n >= N) continue;
+      if (Pz) Pz[(int64_t)m * N + n] = c_lo < c_hi ? acc.v[r][j] : 0.f;
+      else atomicAdd(C + (int64_t)m * N + n, acc.v[r][j]);
     }
   }
 }
 
+// C[i] += sum over z = 0 .. splits-1, in that order, of P[z][i], i < MN.
+__global__ void k_reduce_parts(const float* __restrict__ P, int splits, int64_t MN,
+                               float* __restrict__ C) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < MN;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int z = 0; z < splits; ++z) acc += P[(int64_t)z * MN + i];
+    C[i] += acc;
+  }
+}
+
+// Sum of the threads' values of a block in a fixed order (warp trees, then
+// the warp totals in warp order); the result is valid in thread 0.
+__device__ __forceinline__ float block_sum_fixed(float v, float* sh) {
+  v += __shfl_xor_sync(0xffffffffu, v, 16);
+  v += __shfl_xor_sync(0xffffffffu, v, 8);
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float t = 0.f;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+  __syncthreads();
+  return t;
+}
+
+// *out = scale * sum of part[0 .. n-1] in a fixed order (one block).
+__global__ void k_finish_sum(const float* __restrict__ part, int n, float scale,
+                             float* __restrict__ out) {
+  __shared__ float sh[32];
+  float acc = 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += part[i];
+  const float t = block_sum_fixed(acc, sh);
+  if (threadIdx.x == 0) *out = t * scale;
+}
+
 // out[c] += sum_r A[r][c] * (w ? w[r] : 1), c < H; blocks split the rows.
+// part != NULL: block b writes its column sums to part[b][H] (summed later in
+// block order by k_reduce_parts); otherwise atomics into out.
 __global__ void k_colsum(const float* __restrict__ A, int H, const float* __restrict__ w,
-                         int64_t R_host, const int32_t* __restrict__ R_dev, float* __restrict__ out) {
+                         int64_t R_host, const int32_t* __restrict__ R_dev, float* __restrict__ out,
+                         float* __restrict__ part) {
   const int64_t R = R_dev ? (int64_t)*R_dev : R_host;
   const int c = threadIdx.x;
   if (c >= H) return;
   float s = 0.f;
   for (int64_t r = blockIdx.x; r < R; r += gridDim.x) s += A[r * H + c] * (w ? w[r] : 1.f);
-  atomicAdd(out + c, s);
+  if (part) part[(int64_t)blockIdx.x * H + c] = s;
+  else atomicAdd(out + c, s);
 }
 
+// part[blockIdx.x] = this block's sum (fixed order); k_finish_sum adds the blocks.
 __global__ void k_sum(const float* __restrict__ a, int64_t R_host, const int32_t* __restrict__ R_dev,
-                      float* __restrict__ out) {
+                      float* __restrict__ part) {
+  __shared__ float sh[32];
   const int64_t R = R_dev ? (int64_t)*R_dev : R_host;
   float s = 0.f;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R;
        r += (int64_t)gridDim.x * blockDim.x)
     s += a[r];
-  s += __shfl_xor_sync(0xffffffffu, s, 16);
-  s += __shfl_xor_sync(0xffffffffu, s, 8);
-  s += __shfl_xor_sync(0xffffffffu, s, 4);
-  s += __shfl_xor_sync(0xffffffffu, s, 2);
-  s += __shfl_xor_sync(0xffffffffu, s, 1);
-  if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+  const float t = block_sum_fixed(s, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
 // Y[r][c] = (accumulate ? Y[r][c] : 0) + X[r][c0 + c] for c < H.
@@ -499,6 +546,15 @@ struct BlockGrad {
   float *W1, *b1, *g1, *be1, *W2, *b2, *g2, *be2;
 };
 
+// Splits over rows of a weight-gradient GEMM and blocks of a column sum; the
+// context's partial buffer is sized for the largest of them.
+inline int grad_splits(const etx_ctx* ctx, int64_t rows) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(ctx->n_sms, (rows + 1023) / 1024));
+}
+inline int colsum_blocks(const etx_ctx* ctx, int64_t rows) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(ctx->n_sms * 4, rows));
+}
+
 template <int H>
 struct Bwd {
   etx_ctx* ctx;
@@ -523,25 +579,40 @@ struct Bwd {
     launch(ctx, "gnn_block_backward_f32", k_block_bwd<H, MODE>, grid, kTileThreads, smem_block(), s, a);
   }
 
+  // dW (M x N, split over rows into partial tiles) or column sums, each added
+  // to its gradient in a fixed order (ctx->bw_part holds the partials).
+  void weight_grad(const float* A, int lda, const float* B, int ldb, int M, int Ncols, int64_t Rh,
+                   const int32_t* Rd, int splits, float* out) {
+    launch(ctx, "gnn_weight_grad", k_gemm_tn, dim3((M + kTileM - 1) / kTileM, (Ncols + 127) / 128, splits),
+           kTileThreads, 0, s, A, lda, B, ldb, M, Ncols, Rh, Rd, out, ctx->bw_part);
+    reduce(splits, (int64_t)M * Ncols, out);
+  }
+  void colsum(const float* A, const float* w, int64_t Rh, const int32_t* Rd, int cb, float* out) {
+    launch(ctx, "gnn_colsum", k_colsum, cb, H, 0, s, A, H, w, Rh, Rd, out, ctx->bw_part);
+    reduce(cb, H, out);
+  }
+  void reduce(int parts, int64_t n, float* out) {
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, ctx->n_sms * 4));
+    launch(ctx, "gnn_grad_reduce", k_reduce_parts, g, 256, 0, s, (const float*)ctx->bw_part, parts, n, out);
+  }
+
   // Parameter gradients of one block from the per-row factors.
   void param_grads(const BwdArgs& a, const BlockGrad& g, int K, bool is_edge, bool has_l2) {
     const int32_t* Rd = is_edge ? n_edges : nullptr;
     const int64_t Rh = is_edge ? 0 : N;
     const int64_t Rcap = is_edge ? Ecap : N;
-    const int splits = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->n_sms * 2 / 2, (Rcap + 1023) / 1024));
+    const int splits = grad_splits(ctx, Rcap);
     const int kreal = K == 4 ? 3 : K;  // the node encoder input is padded 3 -> 4
-    launch(ctx, "gnn_weight_grad", k_gemm_tn, dim3(H / kTileM > 0 ? (H + kTileM - 1) / kTileM : 1,
-           (kreal + 127) / 128, splits), kTileThreads, 0, s, a.DA1, H, a.X, K, H, kreal, Rh, Rd, g.W1);
-    const int cb = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->n_sms * 4, Rcap));
-    launch(ctx, "gnn_colsum", k_colsum, cb, H, 0, s, a.DA1, H, (const float*)nullptr, Rh, Rd, g.b1);
-    launch(ctx, "gnn_colsum", k_colsum, cb, H, 0, s, a.DY1N1, H, (const float*)nullptr, Rh, Rd, g.g1);
-    launch(ctx, "gnn_colsum", k_colsum, cb, H, 0, s, a.DY1, H, (const float*)nullptr, Rh, Rd, g.be1);
+    weight_grad(a.DA1, H, a.X, K, H, kreal, Rh, Rd, splits, g.W1);
+    const int cb = colsum_blocks(ctx, Rcap);
+    colsum(a.DA1, nullptr, Rh, Rd, cb, g.b1);
+    colsum(a.DY1N1, nullptr, Rh, Rd, cb, g.g1);
+    colsum(a.DY1, nullptr, Rh, Rd, cb, g.be1);
     if (has_l2) {
-      launch(ctx, "gnn_weight_grad", k_gemm_tn, dim3((H + kTileM - 1) / kTileM, 1, splits),
-             kTileThreads, 0, s, a.DA2, H, a.R1, H, H, H, Rh, Rd, g.W2);
-      launch(ctx, "gnn_colsum", k_colsum, cb, H, 0, s, a.DA2, H, (const float*)nullptr, Rh, Rd, g.b2);
-      launch(ctx, "gnn_colsum", k_colsum, cb, H, 0, s, a.DY2N2, H, (const float*)nullptr, Rh, Rd, g.g2);
-      launch(ctx, "gnn_colsum", k_colsum, cb, H, 0, s, a.DY2, H, (const float*)nullptr, Rh, Rd, g.be2);
+      weight_grad(a.DA2, H, a.R1, H, H, H, Rh, Rd, splits, g.W2);
+      colsum(a.DA2, nullptr, Rh, Rd, cb, g.b2);
+      colsum(a.DY2N2, nullptr, Rh, Rd, cb, g.g2);
+      colsum(a.DY2, nullptr, Rh, Rd, cb, g.be2);
     }
   }
 };
@@ -643,11 +714,11 @@ cudaError_t backward(etx_ctx* ctx, const float* dlogits, float* dparams, cudaStr
     b.template block_pass<B_CLS>(a, Ecap);
     BlockGrad g{gc_W1, gc_b1, gc_g1, gc_be1, nullptr, nullptr, nullptr, nullptr};
     b.param_grads(a, g, H, true, false);
-    const int cb = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->n_sms * 4, Ecap));
-    launch(ctx, "gnn_colsum", k_colsum, cb, H, 0, s, (const float*)a.R1, H, dlogits, (int64_t)0,
-           (const int32_t*)ctx->n_edges, gc_W2);
+    b.colsum(a.R1, dlogits, (int64_t)0, ctx->n_edges, colsum_blocks(ctx, Ecap), gc_W2);
     launch(ctx, "gnn_sum", k_sum, ctx->n_sms, 256, 0, s, dlogits, (int64_t)0,
-           (const int32_t*)ctx->n_edges, gc_b2);
+           (const int32_t*)ctx->n_edges, ctx->bw_part);
+    launch(ctx, "gnn_grad_reduce", k_finish_sum, 1, 256, 0, s, (const float*)ctx->bw_part,
+           (int)ctx->n_sms, 1.0f, gc_b2);
     launch(ctx, "gnn_add_rows", k_add_cols, ge, 256, 0, s, ctx->de, H, (const float*)ctx->bw_DX, H, 0,
            0, (int64_t)0, (const int32_t*)ctx->n_edges);
   }
@@ -746,9 +817,12 @@ cudaError_t launch_gnn_backward(etx_ctx* ctx, const float* dlogits, float* dpara
 // ---------------------------------------------------------------------------
 namespace {
 
+// part[blockIdx.x] = the block's share of the loss sum (fixed order); the
+// mean is formed by k_finish_sum.
 __global__ void k_weighted_bce(const float* __restrict__ z, const float* __restrict__ y,
                                const int32_t* __restrict__ n_edges_dev, float pos_weight,
-                               float* __restrict__ loss, float* __restrict__ dz) {
+                               float* __restrict__ part, float* __restrict__ dz) {
+  __shared__ float sh[32];
   const int64_t E = *n_edges_dev;
   const float inv = E > 0 ? 1.0f / (float)E : 0.f;
   float acc = 0.f;
@@ -762,12 +836,18 @@ __global__ void k_weighted_bce(const float* __restrict__ z, const float* __restr
     acc += pos_weight * yi * sp_neg + (1.0f - yi) * sp_pos;
     dz[i] = inv * (-pos_weight * yi * (1.0f - sig) + (1.0f - yi) * sig);
   }
-  acc += __shfl_xor_sync(0xffffffffu, acc, 16);
-  acc += __shfl_xor_sync(0xffffffffu, acc, 8);
-  acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-  if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc * inv);
+  const float t = block_sum_fixed(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+__global__ void k_bce_mean(const float* __restrict__ part, int n, const int32_t* __restrict__ n_edges_dev,
+                           float* __restrict__ loss) {
+  __shared__ float sh[32];
+  float acc = 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += part[i];
+  const float t = block_sum_fixed(acc, sh);
+  const int64_t E = *n_edges_dev;
+  if (threadIdx.x == 0) *loss = E > 0 ? t * (1.0f / (float)E) : 0.f;
 }
 
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
@@ -789,11 +869,11 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
 cudaError_t launch_weighted_bce(etx_ctx* ctx, const float* logits, const float* targets,
                                 const int32_t* n_edges_dev, float pos_weight, float* loss,
                                 float* dlogits, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(float), s);
-  if (e != cudaSuccess) return e;
-  const int g = grid_for(ctx, (const void*)k_weighted_bce, 256, 0, (ctx->cfg.max_edges + 255) / 256);
+  int g = grid_for(ctx, (const void*)k_weighted_bce, 256, 0, (ctx->cfg.max_edges + 255) / 256);
+  if (g > (int)ctx->red_part_n) g = (int)ctx->red_part_n;
   launch(ctx, "loss_weighted_bce", k_weighted_bce, g, 256, 0, s, logits, targets, n_edges_dev,
-         pos_weight, loss, dlogits);
+         pos_weight, ctx->red_part, dlogits);
+  launch(ctx, "loss_mean", k_bce_mean, 1, 256, 0, s, (const float*)ctx->red_part, g, n_edges_dev, loss);
   return cudaGetLastError();
 }
 
@@ -900,9 +980,9 @@ cudaError_t launch_embed_backward(etx_ctx* ctx, int64_t n, const float* saved, c
     const int ld_in = l > 0 ? EW : 4;
     launch(ctx, "embtrain_weight_grad", k_gemm_tn,
            dim3((M + kTileM - 1) / kTileM, (n_in + 127) / 128, splits), kTileThreads, 0, s, dz, M,
-           in, ld_in, M, n_in, n, (const int32_t*)nullptr, d_params + woff[l]);
+           in, ld_in, M, n_in, n, (const int32_t*)nullptr, d_params + woff[l], (float*)nullptr);
     launch(ctx, "embtrain_colsum", k_colsum, cb, M, 0, s, dz, M, (const float*)nullptr, n,
-           (const int32_t*)nullptr, d_params + boff[l]);
+           (const int32_t*)nullptr, d_params + boff[l], (float*)nullptr);
     if (l > 0) {
       float* out = dz == dz_a ? dz_b : dz_a;
       switch (EW) {

@@ -52,14 +52,17 @@ class Trainer:
         self.blob[self.head:] = self.theta.detach().cpu().numpy()
         self.ctx.load_weights(self.blob)
 
-    def step(self, x, y, z, src, dst, edge_offsets, targets):
-        """One forward / loss / backward / Adam step; returns the loss tensor."""
+    def step(self, x, y, z, src, dst, edge_offsets, targets, reload: bool = True):
+        """One forward / loss / backward / Adam step; returns the loss tensor.
+        ``reload=False`` leaves the context's weights at their old values (for
+        timing the device part alone; call ``sync`` before the next step)."""
         logits = self.ctx.gnn_forward(x, y, z, src, dst, edge_offsets, dtype=self.dtype)
         loss, dlogits = self.ctx.weighted_bce(logits, targets, edge_offsets, self.pos_weight)
         grads = self.ctx.gnn_backward(dlogits)
         self.t += 1
         self.ctx.adam_step(self.theta, grads, self.m, self.v, self.t, lr=self.lr)
-        self.sync()
+        if reload:
+            self.sync()
         return loss
 
 

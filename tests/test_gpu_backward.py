@@ -159,3 +159,14 @@ def test_autograd_function_matches_backward(etx):
     ref = O.gnn_backward(W, cache, w_h.astype(np.float32).astype(np.float64))
     flat = np.concatenate([ref[n].reshape(-1) for n in gnn_names(cfg)])
     assert rel(theta.grad.cpu().numpy().astype(np.float64), flat) <= GRAD_RTOL
+
+
+def test_gradients_and_loss_are_bit_reproducible(etx):
+    """The weight gradients and the loss are sums over edges split across
+    blocks; every split writes its partial and the partials are added in a
+    fixed order, so two runs give the same bits (no atomics)."""
+    cfg, b, W, s, d, eo, y = problem(128, 3, 8, seed=3)
+    runs = [gpu_grads(etx, cfg, b, W, s, d, eo, y, dtype="bf16") for _ in range(2)]
+    assert runs[0][0] == runs[1][0]
+    for n in runs[0][1]:
+        np.testing.assert_array_equal(runs[0][1][n], runs[1][1][n], err_msg=n)
