@@ -123,6 +123,18 @@ int64_t etx_weights_size(const etx_config* cfg);
  * repacking for every arithmetic type).  Synchronous. */
 etx_status etx_load_weights(etx_ctx* ctx, const float* host_blob, int64_t n_floats);
 
+/* Replace the interaction-network parameters with a DEVICE vector theta
+ * (float32, etx_gnn_param_count(cfg) values in the blob's order from the node
+ * encoder on; the layout etx_gnn_backward writes its gradient in), e.g. after
+ * an etx_adam_step on the device: the context's FP32 weights and BF16
+ * tensor-core images are rebuilt by a kernel on `stream` (no host round trip
+ * of the weights; the few values the tensor-core kernels take by value come
+ * back through an asynchronous copy that the next etx_gnn_forward waits for).
+ * The e4m3 images are not rebuilt: ETX_FP8E4M3 returns ETX_ERR_STATE until
+ * the next etx_load_weights.  A pending etx_gnn_backward is invalidated.  No
+ * counterpart in the paper beyond "trained". */
+etx_status etx_set_gnn_params(etx_ctx* ctx, const float* theta, void* stream);
+
 /* Wait for `stream`, then return and clear the context's device error word
  * (ETX_OK if no kernel recorded an error). */
 etx_status etx_ctx_sync(etx_ctx* ctx, void* stream);

@@ -6,6 +6,8 @@
 #include <cstring>
 #include <new>
 
+#include <cuda_bf16.h>
+
 #include "etx_internal.cuh"
 
 namespace etx {
@@ -274,12 +276,17 @@ etx_status etx_ctx_destroy(etx_ctx* ctx) {
                   ctx->perm_in, ctx->h, ctx->m, ctx->e, ctx->parent, ctx->h_ck, ctx->e_ck,
                   ctx->de, ctx->dh, ctx->bw_X, ctx->bw_DX, ctx->bw_R1, ctx->bw_DA1, ctx->bw_DY1,
                   ctx->bw_DY1N1, ctx->bw_DA2, ctx->bw_DY2, ctx->bw_DY2N2, ctx->h_lp,
-                  ctx->small, ctx->w_trip, ctx->bw_part, ctx->red_part};
+                  ctx->small, ctx->w_trip, ctx->bw_part, ctx->red_part, ctx->repack_dev};
   for (void* p : bufs)
     if (p) cudaFree(p);
   for (auto& r : ctx->prof) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
+  }
+  if (ctx->w_host_pinned) {
+    cudaEventSynchronize(ctx->w_host_ev);
+    cudaEventDestroy(ctx->w_host_ev);
+    cudaFreeHost(ctx->w_host_pinned);
   }
   delete ctx;
   return ETX_OK;
@@ -352,9 +359,12 @@ etx_status etx_load_weights(etx_ctx* ctx, const float* blob, int64_t n_floats) {
     p += n_out;
     return q;
   };
+  std::vector<RepackJob> vec_jobs;  // vectors of the interaction network (for etx_set_gnn_params)
+  int64_t gnn_at = -1;               // blob offset of the interaction network once known
   auto push_vec = [&](int n) {
     align4();
     size_t at = dev.size();
+    if (gnn_at >= 0) vec_jobs.push_back(RepackJob{(int64_t)(p - blob) - gnn_at, (int64_t)at, -1, 0, n});
     dev.insert(dev.end(), p, p + n);
     p += n;
     return at;
@@ -363,6 +373,7 @@ etx_status etx_load_weights(etx_ctx* ctx, const float* blob, int64_t n_floats) {
   std::vector<Pending> emb;
   for (int l = 0; l < c.emb_depth; ++l) emb.push_back(push_lin(c.emb_widths[l + 1], c.emb_widths[l]));
   const int64_t gnn_offset = p - blob;
+  gnn_at = gnn_offset;
   struct PB { Pending l1, l2; size_t g1, be1, g2, be2; };
   auto push_block = [&](int k_in) {
     PB b;
@@ -482,9 +493,110 @@ etx_status etx_load_weights(etx_ctx* ctx, const float* blob, int64_t n_floats) {
     next(&ctx->w.cls_tc.w1, &ctx->w.cls_tc.w1f8, &ctx->w.cls_tc.s1);
     ctx->w.has_tc = true;
   }
+  // repack plan of the interaction network for etx_set_gnn_params: every Linear
+  // (W to W^T, its BF16 operand image when there is one) and bias, every vector
+  {
+    std::vector<RepackJob> jobs;
+    auto lin_job = [&](const Pending& q, int64_t img) {
+      const int64_t src = (int64_t)(q.w - blob) - gnn_offset;
+      jobs.push_back(RepackJob{src, (int64_t)q.wt, img, q.k_in, q.n});
+      jobs.push_back(RepackJob{src + (int64_t)q.n * q.k_in, (int64_t)q.b, -1, 0, q.n});
+    };
+    size_t ti = 0;  // next BF16 image (push_img order)
+    auto img = [&]() { return H == 128 ? (int64_t)tc_off[ti++] : (int64_t)-1; };
+    lin_job(node_enc.l1, -1);
+    lin_job(node_enc.l2, -1);
+    lin_job(edge_enc.l1, img());
+    lin_job(edge_enc.l2, img());
+    for (int k = 0; k < c.n_iters; ++k) {
+      lin_job(node[k].l1, img());
+      lin_job(node[k].l2, img());
+      lin_job(edge[k].l1, img());
+      lin_job(edge[k].l2, img());
+    }
+    lin_job(cl1, img());
+    jobs.insert(jobs.end(), vec_jobs.begin(), vec_jobs.end());
+    if (ctx->repack_dev) cudaFree(ctx->repack_dev);
+    ctx->repack_dev = nullptr;
+    if (dmalloc(ctx, &ctx->repack_dev, jobs.size(), "repack plan") != ETX_OK) return ETX_ERR_CUDA;
+    e = cudaMemcpy(ctx->repack_dev, jobs.data(), jobs.size() * sizeof(RepackJob), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "repack plan upload");
+    ctx->n_repack = (int)jobs.size();
+    ctx->n_theta = n_floats - gnn_offset;
+  }
+  ctx->w_host_pending = false;
+  ctx->f8_stale = false;
   ctx->gnn_blob_offset = gnn_offset;
   ctx->fwd_saved = false;
   ctx->weights_loaded = true;
+  return ETX_OK;
+}
+
+}  // extern "C"
+
+namespace etx {
+namespace {
+
+// One repack job per block row of the grid: a Linear's W [n][k_in] (row-major,
+// from the parameter vector) to W^T [k][n] in the FP32 weights, plus, when
+// img >= 0, its BF16 K-major 128-byte-swizzle operand image (64-column chunks,
+// 16-byte unit u of row o at position u ^ (o % 8)); or a plain vector copy.
+__global__ void k_repack(const float* __restrict__ theta, const RepackJob* __restrict__ jobs,
+                         float* __restrict__ w_dev, uint8_t* __restrict__ w_tc) {
+  const RepackJob j = jobs[blockIdx.y];
+  const int64_t total = j.k_in > 0 ? (int64_t)j.k_in * j.n : j.n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = theta[j.src + i];
+    if (j.k_in > 0) {
+      const int o = (int)(i / j.k_in), kk = (int)(i % j.k_in);
+      w_dev[j.dst + (int64_t)kk * j.n + o] = v;
+      if (j.img >= 0) {
+        const int cch = kk >> 6, u = (kk & 63) >> 3, jj = kk & 7;
+        const int64_t off = j.img + (int64_t)cch * j.n * 128 + (int64_t)o * 128 + ((u ^ (o & 7)) << 4) + 2 * jj;
+        const __nv_bfloat16 b = __float2bfloat16_rn(v);
+        *reinterpret_cast<__nv_bfloat16*>(w_tc + off) = b;
+      }
+    } else {
+      w_dev[j.dst + i] = v;
+    }
+  }
+}
+
+}  // namespace
+}  // namespace etx
+
+extern "C" {
+
+etx_status etx_set_gnn_params(etx_ctx* ctx, const float* theta, void* stream) {
+  if (!ctx) return ETX_ERR_ARG;
+  if (!ctx->weights_loaded) return fail(ctx, ETX_ERR_STATE, "weights not loaded");
+  if (!theta) return fail(ctx, ETX_ERR_ARG, "parameter vector is NULL");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!ctx->w_host_pinned) {
+    cudaError_t e = cudaMallocHost((void**)&ctx->w_host_pinned, ctx->w_dev_floats * sizeof(float));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "pinned weight copy");
+    e = cudaEventCreateWithFlags(&ctx->w_host_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "weight copy event");
+  }
+  // a host copy still being filled must land before the buffer is reused
+  if (ctx->w_host_pending) {
+    cudaError_t e = cudaEventSynchronize(ctx->w_host_ev);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "weight copy wait");
+  }
+  launch(ctx, "weights_repack", k_repack, dim3(32, ctx->n_repack), 256, 0, s, theta,
+         (const RepackJob*)ctx->repack_dev, ctx->w_dev, ctx->w_tc);
+  cudaError_t e = cudaMemcpyAsync(ctx->blob_dev + ctx->gnn_blob_offset, theta,
+                                  (size_t)ctx->n_theta * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->w_host_pinned, ctx->w_dev, ctx->w_dev_floats * sizeof(float),
+                        cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->w_host_ev, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "etx_set_gnn_params");
+  ctx->w_host_pending = true;
+  ctx->f8_stale = ctx->w.has_tc;  // the e4m3 images keep the loaded weights
+  ctx->fwd_saved = false;
   return ETX_OK;
 }
 
@@ -557,6 +669,14 @@ etx_status etx_gnn_forward(etx_ctx* ctx, const float* x, const float* y, const f
     return fail(ctx, ETX_ERR_UNSUPPORTED, "BF16 edge storage is for inference (train context)");
   if (dtype != ETX_F32 && !ctx->w.has_tc)
     return fail(ctx, ETX_ERR_UNSUPPORTED, "the tensor-core path needs hidden == 128");
+  if (dtype == ETX_FP8E4M3 && ctx->f8_stale)
+    return fail(ctx, ETX_ERR_STATE, "e4m3 weights predate etx_set_gnn_params: reload the weights");
+  if (ctx->w_host_pending) {  // the kernels take some parameters by value from the host copy
+    cudaError_t e = cudaEventSynchronize(ctx->w_host_ev);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "weight copy wait");
+    std::memcpy(ctx->w_host.data(), ctx->w_host_pinned, ctx->w_dev_floats * sizeof(float));
+    ctx->w_host_pending = false;
+  }
   if (n_hits == 0) return ETX_OK;  // no hits, hence no edges: nothing to compute
   cudaSetDevice(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;

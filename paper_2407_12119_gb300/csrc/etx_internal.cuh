@@ -72,6 +72,15 @@ struct Weights {
 }  // namespace etx
 
 namespace etx {
+// One step of etx_set_gnn_params' device repack (from the interaction-network
+// parameter vector, blob order): k_in > 0: a Linear W [n][k_in] at src to W^T
+// at dst of the FP32 weights (and its BF16 operand image at byte img of w_tc
+// when img >= 0); k_in <= 0: n values copied from src to dst.
+struct RepackJob {
+  int64_t src, dst, img;
+  int32_t k_in, n;
+};
+
 struct ProfRec {
   const char* name;
   cudaEvent_t a, b;
@@ -95,6 +104,14 @@ struct etx_ctx {
   std::vector<float> w_host;  // host copy of w_dev (kernel-parameter copies of small vectors)
   float* blob_dev = nullptr;  // raw blob copy (float32) for the backward pass
   uint8_t* w_tc = nullptr;    // BF16 operand images of the interaction network
+  // device-side weight updates (etx_set_gnn_params)
+  etx::RepackJob* repack_dev = nullptr;
+  int n_repack = 0;
+  int64_t n_theta = 0;             // interaction-network parameters
+  float* w_host_pinned = nullptr;  // asynchronous host copy of w_dev
+  cudaEvent_t w_host_ev = nullptr;
+  bool w_host_pending = false;     // w_host must be refreshed from w_host_pinned
+  bool f8_stale = false;           // e4m3 images predate the last device update
   etx::Weights w;
 
   // graph scratch

@@ -463,6 +463,26 @@ __global__ void k_colsum(const float* __restrict__ A, int H, const float* __rest
   else atomicAdd(out + c, s);
 }
 
+// Column sums of three [R][H] arrays at once (a layer's bias, LayerNorm-gain and
+// LayerNorm-shift gradients): block b writes part[b][3][H].
+__global__ void k_colsum3(const float* __restrict__ A0, const float* __restrict__ A1,
+                          const float* __restrict__ A2, int H, int64_t R_host,
+                          const int32_t* __restrict__ R_dev, float* __restrict__ part) {
+  const int64_t R = R_dev ? (int64_t)*R_dev : R_host;
+  const int c = threadIdx.x;
+  if (c >= H) return;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+  for (int64_t r = blockIdx.x; r < R; r += gridDim.x) {
+    s0 += A0[r * H + c];
+    s1 += A1[r * H + c];
+    s2 += A2[r * H + c];
+  }
+  float* o = part + (int64_t)blockIdx.x * 3 * H;
+  o[c] = s0;
+  o[H + c] = s1;
+  o[2 * H + c] = s2;
+}
+
 // part[blockIdx.x] = this block's sum (fixed order); k_finish_sum adds the blocks.
 __global__ void k_sum(const float* __restrict__ a, int64_t R_host, const int32_t* __restrict__ R_dev,
                       float* __restrict__ part) {
@@ -548,11 +568,13 @@ struct BlockGrad {
 
 // Splits over rows of a weight-gradient GEMM and blocks of a column sum; the
 // context's partial buffer is sized for the largest of them.
+// (about 4,096 rows per split, so the partials stay a small fraction of the
+// rows read).
 inline int grad_splits(const etx_ctx* ctx, int64_t rows) {
-  return (int)std::max<int64_t>(1, std::min<int64_t>(ctx->n_sms, (rows + 1023) / 1024));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(ctx->n_sms, (rows + 4095) / 4096));
 }
 inline int colsum_blocks(const etx_ctx* ctx, int64_t rows) {
-  return (int)std::max<int64_t>(1, std::min<int64_t>(ctx->n_sms * 4, rows));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(ctx->n_sms * 2, (rows + 255) / 256));
 }
 
 template <int H>
@@ -591,6 +613,12 @@ struct Bwd {
     launch(ctx, "gnn_colsum", k_colsum, cb, H, 0, s, A, H, w, Rh, Rd, out, ctx->bw_part);
     reduce(cb, H, out);
   }
+  // out[0..3H) = column sums of A0, A1, A2 (a layer's b, g, be gradients, contiguous)
+  void colsum3(const float* A0, const float* A1, const float* A2, int64_t Rh, const int32_t* Rd,
+               int cb, float* out) {
+    launch(ctx, "gnn_colsum", k_colsum3, cb, H, 0, s, A0, A1, A2, H, Rh, Rd, ctx->bw_part);
+    reduce(cb, 3 * H, out);
+  }
   void reduce(int parts, int64_t n, float* out) {
     const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, ctx->n_sms * 4));
     launch(ctx, "gnn_grad_reduce", k_reduce_parts, g, 256, 0, s, (const float*)ctx->bw_part, parts, n, out);
@@ -605,14 +633,11 @@ struct Bwd {
     const int kreal = K == 4 ? 3 : K;  // the node encoder input is padded 3 -> 4
     weight_grad(a.DA1, H, a.X, K, H, kreal, Rh, Rd, splits, g.W1);
     const int cb = colsum_blocks(ctx, Rcap);
-    colsum(a.DA1, nullptr, Rh, Rd, cb, g.b1);
-    colsum(a.DY1N1, nullptr, Rh, Rd, cb, g.g1);
-    colsum(a.DY1, nullptr, Rh, Rd, cb, g.be1);
+    // b1, g1, be1 (and b2, g2, be2) are contiguous in the blob
+    colsum3(a.DA1, a.DY1N1, a.DY1, Rh, Rd, cb, g.b1);
     if (has_l2) {
       weight_grad(a.DA2, H, a.R1, H, H, H, Rh, Rd, splits, g.W2);
-      colsum(a.DA2, nullptr, Rh, Rd, cb, g.b2);
-      colsum(a.DY2N2, nullptr, Rh, Rd, cb, g.g2);
-      colsum(a.DY2, nullptr, Rh, Rd, cb, g.be2);
+      colsum3(a.DA2, a.DY2N2, a.DY2, Rh, Rd, cb, g.b2);
     }
   }
 };

@@ -37,7 +37,8 @@ EXPORTED = ["etx_ctx_create", "etx_ctx_destroy", "etx_last_error", "etx_weights_
             "etx_embedding_pairs_workspace", "etx_embedding_pairs", "etx_hinge_loss",
             "etx_triplet_weights_size", "etx_load_triplet_weights", "etx_triplets_workspace",
             "etx_build_triplets", "etx_classify_triplets", "etx_fp8_scale_count",
-            "etx_set_fp8_scales", "etx_tracks_workspace", "etx_tracks_from_triplets"]
+            "etx_set_fp8_scales", "etx_tracks_workspace", "etx_tracks_from_triplets",
+            "etx_set_gnn_params"]
 # etx_track_metrics outputs
 TRACK_COUNTS = ["particles", "matched_particles", "candidates", "candidate_particles", "tracks",
                 "unmatched_tracks"]
@@ -127,6 +128,7 @@ def lib() -> ctypes.CDLL:
                                            i64, i32, vp, ctypes.c_size_t, vp, vp, i64, i64, vp,
                                            vp]),
         "etx_fp8_scale_count": (i64, [cfgp]),
+        "etx_set_gnn_params": (i32, [vp, vp, vp]),
         "etx_set_fp8_scales": (i32, [vp, vp, i64]),
         "etx_launch_count": (i64, [vp]),
         "etx_profile_enable": (i32, [vp, i32]),
@@ -257,6 +259,15 @@ class Context:
     def load_weights(self, blob: np.ndarray):
         b = np.ascontiguousarray(blob, dtype=np.float32)
         self._check(lib().etx_load_weights(self._h, b.ctypes.data_as(ctypes.c_void_p), b.size))
+
+    def set_gnn_params(self, theta, stream=None):
+        """etx_set_gnn_params: the interaction-network parameters from a device
+        float32 vector (blob order from the node encoder on), repacked on the
+        device."""
+        _need(theta, torch.float32, "theta", self.device)
+        if theta.numel() != self.gnn_param_count:
+            raise ValueError("theta must hold gnn_param_count values")
+        self._check(lib().etx_set_gnn_params(self._h, _ptr(theta), _stream(stream)))
 
     def set_fp8_scales(self, scales=None):
         """Static e4m3 activation scales (powers of two, 4 L + 3 of them in the

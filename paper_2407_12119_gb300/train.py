@@ -36,33 +36,40 @@ class Trainer:
     def __init__(self, model, blob: np.ndarray, max_events: int, max_hits: int, max_edges: int,
                  device: int = 0, dtype: str = "bf16", lr: float = 1e-3, pos_weight: float = 10.0):
         self.ctx = Context(model, max_events, max_hits, max_edges, device=device, train=True)
-        self.blob = np.array(blob, dtype=np.float32, copy=True)
+        self._blob = np.array(blob, dtype=np.float32, copy=True)
         self.n_theta = self.ctx.gnn_param_count
-        self.head = self.blob.size - self.n_theta        # normalisation + embedding
+        self.head = self._blob.size - self.n_theta       # normalisation + embedding
         dev = self.ctx.device
-        self.theta = torch.from_numpy(self.blob[self.head:].copy()).to(dev)
+        self.theta = torch.from_numpy(self._blob[self.head:].copy()).to(dev)
         self.m = torch.zeros_like(self.theta)
         self.v = torch.zeros_like(self.theta)
         self.dtype, self.lr, self.pos_weight = dtype, lr, pos_weight
         self.t = 0
         self.sync()
 
+    @property
+    def blob(self) -> np.ndarray:
+        """The whole weight blob with the current parameters (a host copy)."""
+        self._blob[self.head:] = self.theta.detach().cpu().numpy()
+        return self._blob
+
     def sync(self):
-        """Load the current parameters into the context."""
-        self.blob[self.head:] = self.theta.detach().cpu().numpy()
+        """Load the current parameters into the context from the host (the
+        full reload, which also rebuilds the e4m3 images)."""
         self.ctx.load_weights(self.blob)
 
     def step(self, x, y, z, src, dst, edge_offsets, targets, reload: bool = True):
         """One forward / loss / backward / Adam step; returns the loss tensor.
-        ``reload=False`` leaves the context's weights at their old values (for
-        timing the device part alone; call ``sync`` before the next step)."""
+        The updated parameters go into the context on the device
+        (``set_gnn_params``); ``reload=False`` leaves the context's weights at
+        their old values (for timing; call ``sync`` before the next step)."""
         logits = self.ctx.gnn_forward(x, y, z, src, dst, edge_offsets, dtype=self.dtype)
         loss, dlogits = self.ctx.weighted_bce(logits, targets, edge_offsets, self.pos_weight)
         grads = self.ctx.gnn_backward(dlogits)
         self.t += 1
         self.ctx.adam_step(self.theta, grads, self.m, self.v, self.t, lr=self.lr)
-        if reload:
-            self.sync()
+        if reload:  # on the device: no host round trip of the weights
+            self.ctx.set_gnn_params(self.theta)
         return loss
 
 

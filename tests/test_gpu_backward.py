@@ -170,3 +170,37 @@ def test_gradients_and_loss_are_bit_reproducible(etx):
     assert runs[0][0] == runs[1][0]
     for n in runs[0][1]:
         np.testing.assert_array_equal(runs[0][1][n], runs[1][1][n], err_msg=n)
+
+
+def test_device_weight_update_equals_a_reload(etx):
+    """etx_set_gnn_params (the device repack of a parameter vector) leaves the
+    context exactly as loading the same values from the host would: the same
+    logits (FP32 and BF16 tensor-core paths) and the same gradients; the e4m3
+    images are not rebuilt, so FP8 is refused until the next load."""
+    cfg, b, W, s, d, eo, y = problem(128, 2, 4, seed=5)
+    blob = pack_blob(cfg, W)
+    ctx_dev = etx.Context(cfg, b.n_events, b.n_hits, max(s.size, 1), train=True)
+    ctx_dev.load_weights(blob)
+    n = ctx_dev.gnn_param_count
+    rng = np.random.default_rng(9)
+    new = blob.copy()
+    new[-n:] += (0.01 * rng.normal(size=n)).astype(np.float32)
+    ctx_dev.set_gnn_params(cuda(new[-n:]))
+    ctx_host = etx.Context(cfg, b.n_events, b.n_hits, max(s.size, 1), train=True)
+    ctx_host.load_weights(new)
+    x, yy, z = cuda(b.x), cuda(b.y), cuda(b.z)
+    st, dt, eot = cuda(s.astype(np.int32)), cuda(d.astype(np.int32)), cuda(eo.astype(np.int32))
+    tgt = cuda(y.astype(np.float32))
+    for dtype in ("f32", "bf16"):
+        outs = []
+        for c in (ctx_dev, ctx_host):
+            logits = c.gnn_forward(x, yy, z, st, dt, eot, dtype=dtype)
+            _, dl = c.weighted_bce(logits, tgt, eot, 10.0)
+            g = c.gnn_backward(dl)
+            c.sync()
+            outs.append((logits.cpu().numpy(), g.cpu().numpy()))
+        np.testing.assert_array_equal(outs[0][0], outs[1][0], err_msg=dtype)
+        np.testing.assert_array_equal(outs[0][1], outs[1][1], err_msg=dtype)
+    with pytest.raises(etx.EtxError) as ei:
+        ctx_dev.gnn_forward(x, yy, z, st, dt, eot, dtype="fp8")
+    assert ei.value.status == etx.ETX_ERR_STATE
