@@ -221,6 +221,13 @@ cudaError_t launch_weighted_bce(etx_ctx* ctx, const float* logits, const float* 
 cudaError_t launch_adam(etx_ctx* ctx, float* p, const float* g, float* m, float* v, int64_t n,
                         float lr, float b1, float b2, float eps, int64_t step, cudaStream_t s);
 
+// gnn_bwd_tc.cu: P[z][128][N] = partial dW = sum over the rows of split z of A[r]^T B[r]
+// (TF32 tensor cores, FP32 accumulation); R_cap bounds the rows, splits CTAs
+bool wgrad_tc_supported(int M, int N);
+cudaError_t launch_wgrad_tc(etx_ctx* ctx, const float* A, int lda, const float* B, int ldb, int N,
+                            int64_t R_host, const int32_t* R_dev, int64_t R_cap, int splits,
+                            float* P, cudaStream_t s);
+
 // gnn_tc.cu (hidden == 128 only)
 // ctx->h_lp = h rounded to BF16 (or e4m3) for rows [0, N)
 cudaError_t launch_h_lowp(etx_ctx* ctx, int64_t N, bool f8, cudaStream_t s);

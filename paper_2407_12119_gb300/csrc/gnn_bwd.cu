@@ -471,16 +471,29 @@ __global__ void k_colsum3(const float* __restrict__ A0, const float* __restrict_
   const int64_t R = R_dev ? (int64_t)*R_dev : R_host;
   const int c = threadIdx.x;
   if (c >= H) return;
-  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-  for (int64_t r = blockIdx.x; r < R; r += gridDim.x) {
-    s0 += A0[r * H + c];
-    s1 += A1[r * H + c];
-    s2 += A2[r * H + c];
+  // four rows in flight per array (independent partial sums, fixed order)
+  float s0[4] = {0.f, 0.f, 0.f, 0.f}, s1[4] = {0.f, 0.f, 0.f, 0.f}, s2[4] = {0.f, 0.f, 0.f, 0.f};
+  const int64_t G = gridDim.x;
+  int64_t r = blockIdx.x;
+  for (; r + 3 * G < R; r += 4 * G) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t i = (r + u * G) * H + c;
+      s0[u] += A0[i];
+      s1[u] += A1[i];
+      s2[u] += A2[i];
+    }
+  }
+  for (int u = 0; r < R; r += G, ++u) {
+    const int64_t i = r * H + c;
+    s0[u] += A0[i];
+    s1[u] += A1[i];
+    s2[u] += A2[i];
   }
   float* o = part + (int64_t)blockIdx.x * 3 * H;
-  o[c] = s0;
-  o[H + c] = s1;
-  o[2 * H + c] = s2;
+  o[c] = (s0[0] + s0[1]) + (s0[2] + s0[3]);
+  o[H + c] = (s1[0] + s1[1]) + (s1[2] + s1[3]);
+  o[2 * H + c] = (s2[0] + s2[1]) + (s2[2] + s2[3]);
 }
 
 // part[blockIdx.x] = this block's sum (fixed order); k_finish_sum adds the blocks.
@@ -574,7 +587,7 @@ inline int grad_splits(const etx_ctx* ctx, int64_t rows) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(ctx->n_sms, (rows + 4095) / 4096));
 }
 inline int colsum_blocks(const etx_ctx* ctx, int64_t rows) {
-  return (int)std::max<int64_t>(1, std::min<int64_t>(ctx->n_sms * 2, (rows + 255) / 256));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(ctx->n_sms * 4, (rows + 127) / 128));
 }
 
 template <int H>
@@ -603,8 +616,17 @@ struct Bwd {
 
   // dW (M x N, split over rows into partial tiles) or column sums, each added
   // to its gradient in a fixed order (ctx->bw_part holds the partials).
+  // H = 128 with 128, 256 or 384 input columns: TF32 tensor cores, one split
+  // per SM; otherwise the FP32 SIMT GEMM.
   void weight_grad(const float* A, int lda, const float* B, int ldb, int M, int Ncols, int64_t Rh,
                    const int32_t* Rd, int splits, float* out) {
+    if (wgrad_tc_supported(M, Ncols)) {
+      const int64_t Rcap = Rd ? Ecap : Rh;
+      const int sp = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->n_sms, (Rcap + 255) / 256));
+      launch_wgrad_tc(ctx, A, lda, B, ldb, Ncols, Rh, Rd, Rcap, sp, ctx->bw_part, s);
+      reduce(sp, (int64_t)M * Ncols, out);
+      return;
+    }
     launch(ctx, "gnn_weight_grad", k_gemm_tn, dim3((M + kTileM - 1) / kTileM, (Ncols + 127) / 128, splits),
            kTileThreads, 0, s, A, lda, B, ldb, M, Ncols, Rh, Rd, out, ctx->bw_part);
     reduce(splits, (int64_t)M * Ncols, out);
