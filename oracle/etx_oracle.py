@@ -399,9 +399,36 @@ def _mlp_block_backward(dout, w, prefix, c, grads):
     return da1 @ f("W1")
 
 
-def gnn_backward(weights, cache, dlogits):
+def _recompute_exact(weights, cache):
+    """A copy of a forward cache whose block internals are recomputed exactly
+    (FP64) from each block's cached input: the checkpointed residual streams
+    of a forward taken in any reading, with exact blocks around them."""
+    out = {"meta": cache["meta"]}
+    for prefix, c in cache.items():
+        if prefix in ("meta", "cls"):
+            continue
+        tmp = {}
+        mlp_block(c["X"], weights, prefix, tmp)
+        out[prefix] = tmp[prefix]
+    X = cache["cls"]["X"]
+    a1 = X @ weights["cls.W1"].astype(np.float64).T + weights["cls.b1"].astype(np.float64)
+    y1, n1, s1 = layer_norm(a1, weights["cls.g1"].astype(np.float64),
+                            weights["cls.be1"].astype(np.float64))
+    out["cls"] = dict(X=X, y1=y1, n1=n1, s1=s1, r1=np.maximum(y1, 0.0))
+    return out
+
+
+def gnn_backward(weights, cache, dlogits, recompute=False):
     """Gradients (float64) of sum_e dlogits[e] * logit[e] w.r.t. every
-    interaction-network parameter, by the chain rule through gnn_forward."""
+    interaction-network parameter, by the chain rule through gnn_forward.
+
+    recompute=True reads the training path of a mixed-precision forward: the
+    forward (gemm="bf16") keeps its residual streams h^k, e^k (the inputs of
+    every block), and the reverse pass recomputes each block's internals from
+    them in exact arithmetic before differentiating it (checkpointing with an
+    exact backward)."""
+    if recompute:
+        cache = _recompute_exact(weights, cache)
     meta = cache["meta"]
     src, dst, N, L = meta["src"], meta["dst"], meta["N"], meta["n_iters"]
     grads = {}

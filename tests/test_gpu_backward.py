@@ -204,3 +204,22 @@ def test_device_weight_update_equals_a_reload(etx):
     with pytest.raises(etx.EtxError) as ei:
         ctx_dev.gnn_forward(x, yy, z, st, dt, eot, dtype="fp8")
     assert ei.value.status == etx.ETX_ERR_STATE
+
+
+def test_bf16_forward_gradient_matches_the_oracle_reading(etx):
+    """The training path with a BF16 tensor-core forward: the GPU's gradient
+    against the oracle's reading of it (BF16-operand forward keeping the
+    residual streams, exact recomputation of every block in the backward,
+    ``gnn_backward(recompute=True)``), on the same logits gradient."""
+    cfg, b, W, s, d, eo, y = problem(128, 2, 2, seed=1)
+    loss, g, logits = gpu_grads(etx, cfg, b, W, s, d, eo, y, dtype="bf16")
+    cache = {}
+    z = O.gnn_forward(W, cfg.n_iters, b.x, b.y, b.z, s, d, cache=cache, gemm="bf16")
+    _, dz = O.weighted_bce(z, y, 10.0)
+    ref = O.gnn_backward(W, cache, dz, recompute=True)
+    devs = {n: rel(g[n], ref[n]) for n in g}
+    worst = max(devs, key=devs.get)
+    print(f"bf16-forward gradient vs the oracle's reading: worst relative L2 {devs[worst]:.2e} "
+          f"({worst}), median {np.median(list(devs.values())):.2e}; logits max diff "
+          f"{np.abs(logits - z).max():.2e}")
+    assert devs[worst] <= 2e-2

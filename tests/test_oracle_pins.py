@@ -973,3 +973,35 @@ def test_triplet_classifiers_against_torch():
             x = torch.cat([torch.tensor(e[f[sel]]), torch.tensor(e[s[sel]])], 1)
             want = l2(torch.relu(ln(l1(x))))[:, 0].numpy()
         np.testing.assert_allclose(z[sel], want, rtol=1e-12, atol=1e-12)
+
+
+def test_backward_recompute_reading():
+    """gnn_backward(recompute=True): on an exact forward it is the plain
+    backward (to rounding); on a BF16-reading forward it differs from the exact
+    gradient by about the BF16 forward error, and recomputing changes the
+    result against differentiating the rounded internals."""
+    from velo_synth import ModelConfig, WORKLOADS, make_batch, make_weights
+    cfg = ModelConfig(emb_widths=(3, 32, 32, 4), hidden=16, n_iters=2, radius=1.5, k_max=16)
+    wl = WORKLOADS["plain"]
+    b = make_batch(wl.recipe, 1, 5001)
+    W = make_weights(cfg, wl.calibration(), perturb=0.3)
+    emb = O.embed(W, 3, b.x, b.y, b.z)
+    s, d, _ = O.build_graph(emb, b.plane, b.hit_offsets, cfg.radius, cfg.k_max)
+    rng = np.random.default_rng(0)
+    dz = rng.normal(size=s.size)
+    c64 = {}
+    O.gnn_forward(W, cfg.n_iters, b.x, b.y, b.z, s, d, cache=c64)
+    g64 = O.gnn_backward(W, c64, dz)
+    g64r = O.gnn_backward(W, c64, dz, recompute=True)
+    for k in g64:
+        np.testing.assert_allclose(g64r[k], g64[k], rtol=1e-12, atol=1e-14)
+    c16 = {}
+    O.gnn_forward(W, cfg.n_iters, b.x, b.y, b.z, s, d, cache=c16, gemm="bf16")
+    g16r = O.gnn_backward(W, c16, dz, recompute=True)
+    g16 = O.gnn_backward(W, c16, dz)
+    rel = lambda a, b_: np.linalg.norm(a - b_) / max(np.linalg.norm(b_), 1e-30)
+    # the BF16 forward moves the gradients by a few per cent (activations one BF16
+    # step off, ReLU masks and LayerNorm of small spreads are sensitive)
+    devs = [rel(g16r[k], g64[k]) for k in g64]
+    assert 1e-3 < np.median(devs) < 0.15 and max(devs) < 0.5
+    assert max(rel(g16r[k], g16[k]) for k in g64) > 1e-6
