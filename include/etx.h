@@ -230,6 +230,15 @@ etx_status etx_set_fp8_scales(etx_ctx* ctx, const float* host_scales, int64_t n)
 int64_t etx_gnn_param_count(const etx_config* cfg);
 etx_status etx_gnn_backward(etx_ctx* ctx, const float* dlogits, float* dparams, void* stream);
 
+/* The residual streams that the last training forward kept (train contexts):
+ * h^k float32 [n_hits][H] and e^k float32 [n_edges][H] of step k (0 = after
+ * the encoders, n_iters = final), copied to caller-owned device buffers (either
+ * may be NULL).  These are the checkpoints etx_gnn_backward recomputes from;
+ * exposed to check the reverse pass against an independent one on the same
+ * inputs.  ETX_ERR_STATE without a training forward, ETX_ERR_ARG for k out of
+ * range.  Asynchronous on `stream`. */
+etx_status etx_gnn_checkpoints(etx_ctx* ctx, int32_t k, float* h_out, float* e_out, void* stream);
+
 /*
  * Training loss: the edge term of Eq. 5 read as class-weighted binary cross
  * entropy on the logits (the paper uses a sigmoid focal loss; this build's

@@ -418,6 +418,30 @@ def _recompute_exact(weights, cache):
     return out
 
 
+def forward_cache_from_streams(weights, n_iters, x, y, z, src, dst, hs, es):
+    """A forward cache (the inputs of every block) built from given residual
+    streams h^0..h^L, e^0..e^L instead of from this module's own forward: to
+    take the reverse pass of ``gnn_backward(recompute=True)`` at another
+    implementation's checkpoints (stage-isolated parity of a backward).
+    Only the block inputs are filled; recompute=True rebuilds the rest."""
+    src = np.asarray(src, np.int64)
+    dst = np.asarray(dst, np.int64)
+    N = np.asarray(x).shape[0]
+    hs = [np.asarray(h, np.float64) for h in hs]
+    es = [np.asarray(e, np.float64) for e in es]
+    xin = normalise(np.stack([np.asarray(x, np.float64), np.asarray(y, np.float64),
+                              np.asarray(z, np.float64)], axis=1),
+                    weights["gnn_mu"], weights["gnn_sigma"])
+    cache = {"node_enc": {"X": xin},
+             "edge_enc": {"X": np.concatenate([hs[0][src], hs[0][dst]], axis=1)}}
+    for k in range(n_iters):
+        cache[f"node{k}"] = {"X": np.concatenate([hs[k], messages(es[k], src, dst, N)], axis=1)}
+        cache[f"edge{k}"] = {"X": np.concatenate([es[k], hs[k + 1][src], hs[k + 1][dst]], axis=1)}
+    cache["cls"] = {"X": es[n_iters]}
+    cache["meta"] = dict(N=N, src=src, dst=dst, n_iters=n_iters)
+    return cache
+
+
 def gnn_backward(weights, cache, dlogits, recompute=False):
     """Gradients (float64) of sum_e dlogits[e] * logit[e] w.r.t. every
     interaction-network parameter, by the chain rule through gnn_forward.

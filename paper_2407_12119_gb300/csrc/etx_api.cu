@@ -698,6 +698,23 @@ etx_status etx_gnn_forward(etx_ctx* ctx, const float* x, const float* y, const f
   return ETX_OK;
 }
 
+etx_status etx_gnn_checkpoints(etx_ctx* ctx, int32_t k, float* h_out, float* e_out, void* stream) {
+  if (!ctx) return ETX_ERR_ARG;
+  if (!ctx->cfg.train || !ctx->fwd_saved) return fail(ctx, ETX_ERR_STATE, "no training forward kept");
+  if (k < 0 || k > ctx->cfg.n_iters) return fail(ctx, ETX_ERR_ARG, "checkpoint index out of range");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t H = ctx->cfg.hidden, N = ctx->fwd_n_hits, Ecap = ctx->cfg.max_edges;
+  cudaError_t e = cudaSuccess;
+  if (h_out)
+    e = cudaMemcpyAsync(h_out, ctx->h_ck + (size_t)k * N * H, (size_t)N * H * sizeof(float),
+                        cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && e_out)
+    e = launch_checkpoint(ctx, e_out, ctx->e_ck + (size_t)k * Ecap * H, 0, ctx->n_edges, Ecap, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "etx_gnn_checkpoints");
+  return ETX_OK;
+}
+
 int64_t etx_fp8_scale_count(const etx_config* cfg) {
   if (config_problem(cfg)) return -1;
   return 4 * (int64_t)cfg->n_iters + 3;

@@ -38,7 +38,7 @@ EXPORTED = ["etx_ctx_create", "etx_ctx_destroy", "etx_last_error", "etx_weights_
             "etx_triplet_weights_size", "etx_load_triplet_weights", "etx_triplets_workspace",
             "etx_build_triplets", "etx_classify_triplets", "etx_fp8_scale_count",
             "etx_set_fp8_scales", "etx_tracks_workspace", "etx_tracks_from_triplets",
-            "etx_set_gnn_params"]
+            "etx_set_gnn_params", "etx_gnn_checkpoints"]
 # etx_track_metrics outputs
 TRACK_COUNTS = ["particles", "matched_particles", "candidates", "candidate_particles", "tracks",
                 "unmatched_tracks"]
@@ -129,6 +129,7 @@ def lib() -> ctypes.CDLL:
                                            vp]),
         "etx_fp8_scale_count": (i64, [cfgp]),
         "etx_set_gnn_params": (i32, [vp, vp, vp]),
+        "etx_gnn_checkpoints": (i32, [vp, i32, vp, vp, vp]),
         "etx_set_fp8_scales": (i32, [vp, vp, i64]),
         "etx_launch_count": (i64, [vp]),
         "etx_profile_enable": (i32, [vp, i32]),
@@ -268,6 +269,15 @@ class Context:
         if theta.numel() != self.gnn_param_count:
             raise ValueError("theta must hold gnn_param_count values")
         self._check(lib().etx_set_gnn_params(self._h, _ptr(theta), _stream(stream)))
+
+    def gnn_checkpoints(self, k: int, n_hits: int, n_edges: int, stream=None):
+        """etx_gnn_checkpoints: (h^k [n_hits][H], e^k [n_edges][H]) that the last
+        training forward kept."""
+        H = int(self.model.hidden)
+        h = torch.empty((n_hits, H), dtype=torch.float32, device=self.device)
+        e = torch.empty((max(n_edges, 1), H), dtype=torch.float32, device=self.device)
+        self._check(lib().etx_gnn_checkpoints(self._h, int(k), _ptr(h), _ptr(e), _stream(stream)))
+        return h, e[:n_edges]
 
     def set_fp8_scales(self, scales=None):
         """Static e4m3 activation scales (powers of two, 4 L + 3 of them in the

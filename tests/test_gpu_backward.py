@@ -222,4 +222,48 @@ def test_bf16_forward_gradient_matches_the_oracle_reading(etx):
     print(f"bf16-forward gradient vs the oracle's reading: worst relative L2 {devs[worst]:.2e} "
           f"({worst}), median {np.median(list(devs.values())):.2e}; logits max diff "
           f"{np.abs(logits - z).max():.2e}")
-    assert devs[worst] <= 2e-2
+    # the BF16 forward itself moves these gradients by ~5% from the exact ones, so
+    # rounding-boundary differences between the two BF16 forwards show at the % level
+    assert devs[worst] <= 5e-2 and np.median(list(devs.values())) <= 2e-2
+
+
+def test_bf16_forward_gradient_stage_isolated(etx):
+    """The same BF16-forward training path, stage-isolated: the oracle's reverse
+    pass (exact recomputation of every block) taken at the GPU's own
+    checkpointed residual streams and the GPU's own logits gradient must give
+    the GPU's gradient within 1e-3 relative per tensor."""
+    cfg, b, W, s, d, eo, y = problem(128, 2, 2, seed=1)
+    ctx = etx.Context(cfg, b.n_events, b.n_hits, max(s.size, 1), train=True)
+    ctx.load_weights(pack_blob(cfg, W))
+    x, yy, z = cuda(b.x), cuda(b.y), cuda(b.z)
+    st, dt, eot = cuda(s.astype(np.int32)), cuda(d.astype(np.int32)), cuda(eo.astype(np.int32))
+    logits = ctx.gnn_forward(x, yy, z, st, dt, eot, dtype="bf16")
+    _, dl = ctx.weighted_bce(logits, cuda(y.astype(np.float32)), eot, 10.0)
+    hs, es = [], []
+    for k in range(cfg.n_iters + 1):
+        h, e = ctx.gnn_checkpoints(k, b.n_hits, s.size)
+        hs.append(h.cpu().numpy())
+        es.append(e.cpu().numpy())
+    g = ctx.gnn_backward(dl)
+    ctx.sync()
+    flat = g.cpu().numpy().astype(np.float64)
+    cache = O.forward_cache_from_streams(W, cfg.n_iters, b.x, b.y, b.z, s, d, hs, es)
+    ref = O.gnn_backward(W, cache, dl.cpu().numpy().astype(np.float64), recompute=True)
+    shapes = dict(blob_layout(cfg))
+    o, worst_m, worst_v = 0, (0.0, ""), (0.0, "")
+    for n in gnn_names(cfg):
+        k = int(np.prod(shapes[n]))
+        r = (rel(flat[o:o + k].reshape(shapes[n]), ref[n]), n)
+        if len(shapes[n]) > 1:
+            worst_m = max(worst_m, r)
+        else:
+            worst_v = max(worst_v, r)
+        o += k
+    print(f"bf16-forward gradient, stage-isolated: worst relative L2 {worst_m[0]:.2e} ({worst_m[1]}) "
+          f"of the matrices, {worst_v[0]:.2e} ({worst_v[1]}) of the vectors")
+    assert worst_m[0] <= GRAD_RTOL
+    # A ReLU mask decided differently by the FP32 and the FP64 recomputation (a
+    # pre-activation within rounding of zero) moves a bias/gain column sum by one
+    # term; the class-weighted BCE gradient cancels ~25x in those sums, so one such
+    # term is ~1e-3 of the vector's norm on this problem.
+    assert worst_v[0] <= 3 * GRAD_RTOL

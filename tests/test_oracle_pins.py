@@ -1005,3 +1005,34 @@ def test_backward_recompute_reading():
     devs = [rel(g16r[k], g64[k]) for k in g64]
     assert 1e-3 < np.median(devs) < 0.15 and max(devs) < 0.5
     assert max(rel(g16r[k], g16[k]) for k in g64) > 1e-6
+
+
+def test_forward_cache_from_streams_matches_the_forward():
+    """forward_cache_from_streams, given the residual streams of the oracle's own
+    forward, rebuilds that forward's block inputs exactly, so the reverse pass
+    taken at given checkpoints is the one taken along the forward (a block fed
+    h^k where it needs h^(k+1), or e^(k+1) where it needs e^k, fails here)."""
+    from velo_synth import ModelConfig, WORKLOADS, make_batch, make_weights
+    cfg = ModelConfig(emb_widths=(3, 32, 32, 4), hidden=16, n_iters=3, radius=1.5, k_max=16)
+    wl = WORKLOADS["plain"]
+    b = make_batch(wl.recipe, 1, 5002)
+    W = make_weights(cfg, wl.calibration(), perturb=0.3)
+    emb = O.embed(W, 3, b.x, b.y, b.z)
+    s, d, _ = O.build_graph(emb, b.plane, b.hit_offsets, cfg.radius, cfg.k_max)
+    H, L = cfg.hidden, cfg.n_iters
+    for gemm in ("fp64", "bf16"):
+        c = {}
+        O.gnn_forward(W, L, b.x, b.y, b.z, s, d, cache=c, gemm=gemm)
+        hs = [c[f"node{k}"]["X"][:, :H] for k in range(L)]
+        hL = np.zeros_like(hs[0])
+        hL[s] = c[f"edge{L - 1}"]["X"][:, H:2 * H]
+        hL[d] = c[f"edge{L - 1}"]["X"][:, 2 * H:]
+        es = [c[f"edge{k}"]["X"][:, :H] for k in range(L)] + [c["cls"]["X"]]
+        r = O.forward_cache_from_streams(W, L, b.x, b.y, b.z, s, d, hs + [hL], es)
+        for name in ["node_enc", "edge_enc", "cls"] + [f"{p}{k}" for k in range(L) for p in ("node", "edge")]:
+            np.testing.assert_array_equal(r[name]["X"], c[name]["X"])
+        dz = np.random.default_rng(1).normal(size=s.size)
+        g0 = O.gnn_backward(W, c, dz, recompute=True)
+        g1 = O.gnn_backward(W, r, dz, recompute=True)
+        for k in g0:
+            np.testing.assert_array_equal(g1[k], g0[k])
