@@ -549,10 +549,10 @@ etx_status etx_track_metrics(etx_ctx* ctx, const int32_t* labels, const int32_t*
  *                               (event, plane) in the k-NN: 1, 2 or 4
  *                               (per-event work partitioning);
  *   "tc_stages/<block>/<dtype>" A-operand ring slots of the tensor-core MLP
- *                               kernel, 2 to 5 (capped by shared memory:
- *                               3 for BF16 edge and node updates), for block
- *                               edge_encoder, node_update, edge_update or
- *                               classifier and dtype bf16 or fp8,
+ *                               kernel, 2 to 5 (capped by shared memory),
+ *                               for block edge_encoder, node_update,
+ *                               edge_update or classifier and dtype bf16 or
+ *                               fp8,
  * and keeps the fastest in the context for all later calls.  Outputs do not
  * depend on these choices.  On return emb, src, dst, edge_offsets (and logits
  * for the tensor-core dtypes) hold the results of the chosen configuration,
