@@ -251,6 +251,22 @@ etx_status etx_ctx_create(const etx_config* cfg, int32_t device, etx_ctx** out) 
     for (float** q : rows) chk(dmalloc(ctx, q, R * H, "backward row factors"));
     const size_t part = std::max<size_t>((size_t)ctx->n_sms * H * 3 * H, (size_t)ctx->n_sms * 4 * H);
     chk(dmalloc(ctx, &ctx->bw_part, part, "partial gradients"));
+    if (H == 128) {
+      // tensor-core block backward: n1 rows, rstd1, TF32 images of every
+      // hidden-width block's W1, W1^T, W2, W2^T, and their job list
+      chk(dmalloc(ctx, &ctx->bw_N1, R * H, "backward n1 rows"));
+      chk(dmalloc(ctx, &ctx->bw_rstd1, R, "backward rstd1"));
+      chk(dmalloc(ctx, &ctx->bw_Xlo, R * 3 * H, "backward input low parts"));
+      chk(dmalloc(ctx, &ctx->bw_R1lo, R * H, "backward R1 low parts"));
+      // per block: W1, W1^T, W1 low [H][K] each, W2, W2^T, W2 low [H][H] each
+      const size_t per_upd = 3 * (size_t)H * 3 * H + 3 * (size_t)H * H;
+      const size_t per_enc = 3 * (size_t)H * 2 * H + 3 * (size_t)H * H;
+      chk(dmalloc(ctx, &ctx->bw_img, per_enc + 2 * (size_t)cfg->n_iters * per_upd, "TF32 weight images"));
+      ctx->bw_img_n_jobs = 6 * (1 + 2 * cfg->n_iters);
+      unsigned char* jobs = nullptr;
+      chk(dmalloc(ctx, &jobs, (size_t)ctx->bw_img_n_jobs * tf32_image_job_bytes(), "image jobs"));
+      ctx->bw_img_jobs = jobs;
+    }
   }
   if (st == ETX_OK) {
     e = cudaMemset(ctx->d_err, 0, sizeof(int));
@@ -276,7 +292,9 @@ etx_status etx_ctx_destroy(etx_ctx* ctx) {
                   ctx->perm_in, ctx->h, ctx->m, ctx->e, ctx->parent, ctx->h_ck, ctx->e_ck,
                   ctx->de, ctx->dh, ctx->bw_X, ctx->bw_DX, ctx->bw_R1, ctx->bw_DA1, ctx->bw_DY1,
                   ctx->bw_DY1N1, ctx->bw_DA2, ctx->bw_DY2, ctx->bw_DY2N2, ctx->h_lp,
-                  ctx->small, ctx->w_trip, ctx->bw_part, ctx->red_part, ctx->repack_dev};
+                  ctx->small, ctx->w_trip, ctx->bw_part, ctx->red_part, ctx->repack_dev,
+                  ctx->bw_N1, ctx->bw_rstd1, ctx->bw_img, ctx->bw_img_jobs, ctx->bw_Xlo,
+                  ctx->bw_R1lo};
   for (void* p : bufs)
     if (p) cudaFree(p);
   for (auto& r : ctx->prof) {

@@ -155,6 +155,17 @@ struct etx_ctx {
   // per-split partial gradients, added in a fixed order (deterministic reductions):
   // n_sms x H x 3H floats
   float* bw_part = nullptr;
+  // tensor-core block backward (H = 128): n1 rows, rstd1, TF32 weight images and
+  // the job list that refreshes them (filled at the first backward)
+  float* bw_N1 = nullptr;
+  float* bw_Xlo = nullptr;   // low parts of the block inputs [R][3H] and of R1 [R][H]
+  float* bw_R1lo = nullptr;
+  float* bw_rstd1 = nullptr;
+  float* bw_img = nullptr;
+  void* bw_img_jobs = nullptr;
+  std::vector<unsigned char> bw_img_jobs_host;
+  int bw_img_n_jobs = 0;
+  bool bw_img_ready = false;
   // per-block partial sums of the loss, red_part_n floats (every context)
   float* red_part = nullptr;
   int64_t red_part_n = 0;
@@ -224,6 +235,30 @@ cudaError_t launch_adam(etx_ctx* ctx, float* p, const float* g, float* m, float*
 // gnn_bwd_tc.cu: P[z][128][N] = partial dW = sum over the rows of split z of A[r]^T B[r]
 // (TF32 tensor cores, FP32 accumulation); R_cap bounds the rows, splits CTAs
 bool wgrad_tc_supported(int M, int N);
+
+// gnn_bwd_gemm.cu: the reverse pass of one hidden-width block (H = 128) on the
+// tensor cores (TF32).  Block kinds as in the FP32 block backward.
+enum BwdBlockMode { BWD_NODE_ENC = 0, BWD_EDGE_ENC = 1, BWD_NODE_UPD = 2, BWD_EDGE_UPD = 3, BWD_CLS = 4 };
+struct BlockBwdTc {
+  int64_t n_nodes;
+  int64_t R_host;              // rows (hits) when R_dev is NULL
+  const int32_t* R_dev;        // rows (edges) on the device; capacity cfg.max_edges
+  const float *hg, *ein, *m;   // gathered node rows, edge rows, messages [N][2H]
+  const int32_t *src, *dst;
+  const float *W1n, *W1t, *W2n, *W2t;  // TF32 images: W1 [H][K], W1^T [K][H], W2, W2^T
+  const float *W1n_lo, *W2n_lo;        // low parts of W1, W2 (split products)
+  const float *b1, *g1, *be1, *b2, *g2, *be2;
+  const float* G;              // incoming gradient rows [R][H]
+  float *X, *R1, *N1, *rstd1, *DA1, *DY1, *DY1N1, *DA2, *DY2, *DY2N2, *DX;
+  float *X_lo, *R1_lo;                 // low parts of X and R1 (split products)
+};
+bool block_bwd_tc_supported(const etx_ctx* ctx);
+cudaError_t launch_block_bwd_tc(etx_ctx* ctx, int mode, const BlockBwdTc& p, cudaStream_t s);
+// TF32 images of the weights: a job list (src, dst, n) held on the device
+size_t tf32_image_job_bytes();
+void tf32_image_job(void* jobs_host, int i, const float* src, float* dst, int64_t n, bool lo);
+cudaError_t launch_tf32_images(etx_ctx* ctx, const void* jobs_dev, int n_jobs, int64_t max_n,
+                               cudaStream_t s);
 cudaError_t launch_wgrad_tc(etx_ctx* ctx, const float* A, int lda, const float* B, int ldb, int N,
                             int64_t R_host, const int32_t* R_dev, int64_t R_cap, int splits,
                             float* P, cudaStream_t s);

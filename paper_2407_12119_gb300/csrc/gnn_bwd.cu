@@ -737,6 +737,83 @@ cudaError_t backward(etx_ctx* ctx, const float* dlogits, float* dparams, cudaStr
     a.W1 = orig(g.W1);
     a.W2 = orig(g.W2);
   };
+  // H = 128: the edge encoder, node and edge updates on the tensor cores (TF32),
+  // from TF32 images of their weights refreshed here
+  const bool tc = H == 128 && ctx->bw_img && block_bwd_tc_supported(ctx);
+  struct Img { float *W1n, *W1t, *W2n, *W2t, *W1n_lo, *W2n_lo; };
+  std::vector<Img> imgs;  // edge encoder, then node k and edge k for k = 0..L-1
+  if (tc) {
+    float* q = ctx->bw_img;
+    const bool fill = ctx->bw_img_jobs_host.empty();
+    if (fill) ctx->bw_img_jobs_host.resize((size_t)ctx->bw_img_n_jobs * tf32_image_job_bytes());
+    int j = 0;
+    auto add = [&](const BlockF32& w, const BlockGrad& g, int K) {
+      const size_t hk = (size_t)H * K, hh = (size_t)H * H;
+      Img im{q, q + hk, q + 3 * hk, q + 3 * hk + hh, q + 2 * hk, q + 3 * hk + 2 * hh};
+      q += 3 * hk + 3 * hh;
+      if (fill) {
+        unsigned char* jh = ctx->bw_img_jobs_host.data();
+        tf32_image_job(jh, j++, orig(g.W1), im.W1n, (int64_t)hk, false);
+        tf32_image_job(jh, j++, w.l1.wt, im.W1t, (int64_t)hk, false);
+        tf32_image_job(jh, j++, orig(g.W1), im.W1n_lo, (int64_t)hk, true);
+        tf32_image_job(jh, j++, orig(g.W2), im.W2n, (int64_t)hh, false);
+        tf32_image_job(jh, j++, w.l2.wt, im.W2t, (int64_t)hh, false);
+        tf32_image_job(jh, j++, orig(g.W2), im.W2n_lo, (int64_t)hh, true);
+      }
+      imgs.push_back(im);
+    };
+    add(ctx->w.edge_enc, g_edge_enc, 2 * H);
+    for (int k = 0; k < L; ++k) {
+      add(ctx->w.node[k], g_node[k], 3 * H);
+      add(ctx->w.edge[k], g_edge[k], 3 * H);
+    }
+    if (fill) {
+      e = cudaMemcpyAsync(ctx->bw_img_jobs, ctx->bw_img_jobs_host.data(), ctx->bw_img_jobs_host.size(),
+                          cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) return e;
+    }
+    e = launch_tf32_images(ctx, ctx->bw_img_jobs, ctx->bw_img_n_jobs, (int64_t)H * 3 * H, s);
+    if (e != cudaSuccess) return e;
+  }
+  // one block's reverse pass on the tensor cores (same stored factors as block_pass)
+  auto tc_block = [&](int mode, const BwdArgs& a, const Img& im, int64_t R_host, const int32_t* R_dev) {
+    BlockBwdTc p{};
+    p.n_nodes = N;
+    p.R_host = R_host;
+    p.R_dev = R_dev;
+    p.hg = a.hg;
+    p.ein = a.ein;
+    p.m = a.m;
+    p.src = a.src;
+    p.dst = a.dst;
+    p.W1n = im.W1n;
+    p.W1t = im.W1t;
+    p.W2n = im.W2n;
+    p.W2t = im.W2t;
+    p.W1n_lo = im.W1n_lo;
+    p.W2n_lo = im.W2n_lo;
+    p.X_lo = ctx->bw_Xlo;
+    p.R1_lo = ctx->bw_R1lo;
+    p.b1 = a.l1.b;
+    p.g1 = a.g1;
+    p.be1 = a.be1;
+    p.b2 = a.l2.b;
+    p.g2 = a.g2;
+    p.be2 = a.be2;
+    p.G = a.gout;
+    p.X = a.X;
+    p.R1 = a.R1;
+    p.N1 = ctx->bw_N1;
+    p.rstd1 = ctx->bw_rstd1;
+    p.DA1 = a.DA1;
+    p.DY1 = a.DY1;
+    p.DY1N1 = a.DY1N1;
+    p.DA2 = a.DA2;
+    p.DY2 = a.DY2;
+    p.DY2N2 = a.DY2N2;
+    p.DX = a.DX;
+    return launch_block_bwd_tc(ctx, mode, p, s);
+  };
   float* hck = ctx->h_ck;
   float* eck = ctx->e_ck;
   auto hk = [&](int k) { return hck + (size_t)k * N * H; };
@@ -778,7 +855,11 @@ cudaError_t backward(etx_ctx* ctx, const float* dlogits, float* dparams, cudaStr
       a.hg = hk(k + 1);
       a.gout = ctx->de;
       a.K = 3 * H;
-      b.template block_pass<B_EDGE_UPD>(a, Ecap);
+      if (tc) {
+        if ((e = tc_block(BWD_EDGE_UPD, a, imgs[2 + 2 * k], 0, ctx->n_edges)) != cudaSuccess) return e;
+      } else {
+        b.template block_pass<B_EDGE_UPD>(a, Ecap);
+      }
       b.param_grads(a, g_edge[k], 3 * H, true, true);
       launch(ctx, "gnn_add_rows", k_add_cols, ge, 256, 0, s, ctx->de, H, (const float*)ctx->bw_DX,
              3 * H, 0, 1, (int64_t)0, (const int32_t*)ctx->n_edges);
@@ -796,7 +877,11 @@ cudaError_t backward(etx_ctx* ctx, const float* dlogits, float* dparams, cudaStr
       a.m = ctx->m;
       a.gout = ctx->dh;
       a.K = 3 * H;
-      b.template block_pass<B_NODE_UPD>(a, N);
+      if (tc) {
+        if ((e = tc_block(BWD_NODE_UPD, a, imgs[1 + 2 * k], N, nullptr)) != cudaSuccess) return e;
+      } else {
+        b.template block_pass<B_NODE_UPD>(a, N);
+      }
       b.param_grads(a, g_node[k], 3 * H, false, true);
       launch(ctx, "gnn_add_rows", k_add_cols, gn, 256, 0, s, ctx->dh, H, (const float*)ctx->bw_DX,
              3 * H, 0, 1, N, (const int32_t*)nullptr);
@@ -812,7 +897,11 @@ cudaError_t backward(etx_ctx* ctx, const float* dlogits, float* dparams, cudaStr
     a.hg = hk(0);
     a.gout = ctx->de;
     a.K = 2 * H;
-    b.template block_pass<B_EDGE_ENC>(a, Ecap);
+    if (tc) {
+      if ((e = tc_block(BWD_EDGE_ENC, a, imgs[0], 0, ctx->n_edges)) != cudaSuccess) return e;
+    } else {
+      b.template block_pass<B_EDGE_ENC>(a, Ecap);
+    }
     b.param_grads(a, g_edge_enc, 2 * H, true, true);
     if (N > 0)
       launch(ctx, "gnn_scatter_backward", k_scatter_bwd<H>, gs, 256, 0, s, (const float*)ctx->bw_DX,

@@ -86,6 +86,19 @@ __device__ __forceinline__ void bulk_g2s(void* smem_dst, const void* gsrc, uint3
       : "memory");
 }
 
+// Tiled tensor copy global -> shared of the box at (x, y) (x the innermost
+// coordinate, in elements; x times the element size a multiple of 16 bytes) of
+// the tensor map at `tmap` (a __grid_constant__ kernel parameter); completion
+// counted in bytes on `bar`.  Out-of-range elements read as zeros.
+__device__ __forceinline__ void tma_load_2d(void* smem_dst, const void* tmap, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(smem_dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // Make this thread's generic-proxy shared-memory writes visible to the async
 // proxy (tensor core operand reads).
 // 16-byte asynchronous copy global -> shared (L2 only, no registers).
