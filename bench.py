@@ -267,6 +267,26 @@ def cpu_baseline_report(wl, W, batch, seconds: float) -> dict:
 
 
 # ---------------------------------------------------------------------------
+# tensor-core block backward (csrc/gnn_bwd_gemm.cu): FP32 bytes per row a launch
+# must move (operands read once, outputs written once; weights, in L2, not
+# counted), K the block's input width
+BWD_TC_KERNELS = ("gnn_block_backward_tc_ln1", "gnn_block_backward_tc_ln2",
+                  "gnn_block_backward_tc_ln1b", "gnn_block_backward_tc_dx")
+
+
+def bwd_tc_bytes(name: str, H: int, E: int, N: int, L: int) -> float:
+    """Algorithmic HBM bytes of all launches of `name` in one training step:
+    the edge encoder (E rows, K = 2H), L edge updates (E rows, K = 3H) and L
+    node updates (N rows, K = 3H)."""
+    def per_row(K):
+        row = 4 * H
+        return {"gnn_block_backward_tc_ln1": 2 * 4 * K + 3 * row + 4,   # X hi, lo -> R1 hi, lo, n1, rstd1
+                "gnn_block_backward_tc_ln2": 2 * row + row + 3 * row,   # R1 hi, lo, G -> DY2, DY2 n2, DA2
+                "gnn_block_backward_tc_ln1b": 2 * row + 4 + 3 * row,    # DA2, n1, rstd1 -> DY1, DY1 n1, DA1
+                "gnn_block_backward_tc_dx": row + 4 * K}[name]          # DA1 -> DX
+    return E * per_row(2 * H) + L * E * per_row(3 * H) + L * N * per_row(3 * H)
+
+
 def train_step_report(args, local):
     """Time the training step (BF16 forward with checkpoints, weighted BCE,
     backward with recomputation, Adam, weight reload) on the 64-event
@@ -315,9 +335,25 @@ def train_step_report(args, local):
     top = sorted(kern.items(), key=lambda kv: -kv[1][0])
     breakdown = {k: round(ms, 3) for k, (ms, _) in top[:10]}
     breakdown["other_kernels"] = round(sum(ms for _, (ms, _) in top[10:]), 3)
-    return {"breakdown_ms": breakdown,
+    # roofline of the dominant tensor-core block-backward kernel: algorithmic
+    # bytes of all its launches in the step over their summed CUDA-event time
+    roof = None
+    bw = {k: v for k, v in kern.items() if k in BWD_TC_KERNELS}
+    if bw:
+        name = max(bw, key=lambda k: bw[k][0])
+        ms = bw[name][0]
+        nbytes = bwd_tc_bytes(name, m.hidden, E, N, m.n_iters)
+        peaks, src = measured_peaks()
+        ach = nbytes / (ms / 1e3) / 1e9
+        roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                "launches": bw[name][1], "ms": ms,
+                "note": "algorithmic bytes of all launches of the step (edge encoder, node and "
+                        "edge updates) over their summed duration; peak " + src}
+    return {"breakdown_ms": breakdown, "roofline": roof,
             "workload": f"{wl.name}: {B} events, {N} hits, {E} edges, hidden {m.hidden}, "
-                        f"{m.n_iters} steps, BF16 forward, FP32 backward with recomputation, "
+                        f"{m.n_iters} steps, BF16 forward, backward with recomputation (tensor cores: "
+                        f"split-TF32 recomputed products, TF32 gradient products; FP32 LayerNorm), "
                         f"weighted BCE (w=10), Adam lr 1e-3, weights updated on the device",
             "ms_per_step": 1e3 * el / steps, "events_per_s": B * steps / el,
             "loss_first": float(losses[0].item()), "loss_last": float(losses[-1].item())}
@@ -949,6 +985,8 @@ def run_ours(args):
                         "pileup4x": pile_line, "roofline_frac": roof["frac"],
                         "roofline_kernel": roof["kernel"],
                         "train64_ms": train["ms_per_step"] if train else None,
+                        "train64_bwd_roofline_frac": (train["roofline"]["frac"]
+                                                      if train and train.get("roofline") else None),
                         "cpu_oracle_events_per_s": {k: v["value"] for k, v in cpu_detail.items()}
                         if cpu_detail else None}}
     print(json.dumps(out), flush=True)

@@ -8,8 +8,11 @@
 // recomputed from the checkpointed block input X, and the two input gradients.
 // Each is one launch of k_bwd_gemm (C = A B^T over 128-row tiles, A and B
 // K-major, both brought in by TMA tensor copies with the 128-byte swizzle the
-// MMA descriptors expect), and the row-wise work between them runs in that
-// launch's epilogue, one row (one TMEM lane) per thread:
+// MMA descriptors expect; persistent, one CTA per SM, two accumulators in
+// tensor memory where they fit so one tile's epilogue overlaps the next tile's
+// products), and the row-wise work between them runs in that launch's
+// epilogue, one row (one TMEM lane) per thread, its global reads and writes
+// made coalesced through a per-warp shared-memory transpose:
 //   1  X W1^T   -> LN1 forward: R1 = ReLU(n1 g1 + be1), n1, rstd1
 //   2  R1 W2^T  -> LN2 forward and backward against the incoming gradient G:
 //                  DY2, DY2 n2, DA2
@@ -44,21 +47,55 @@ constexpr float kBgLnEps = 1e-5f;
 
 enum BgEpi { EPI_LN1F = 0, EPI_LN2 = 1, EPI_LN1B = 2, EPI_STORE = 3 };
 
-// SPLIT: each stage holds A hi, A lo, B hi, B lo
-template <int NB, bool SPLIT = false>
+// SPLIT: each stage holds A hi, A lo, B hi, B lo.  ACC accumulators in tensor
+// memory (two where they fit, so the epilogue of one tile overlaps the products
+// of the next); a 4 KB staging buffer per epilogue warp (32 rows x 32 columns)
+// turns its row-per-thread values into coalesced 128-byte row segments.
+// ROWS: the epilogue reads a [R][H] array row by row (G or n1): each warp's 32
+// rows of a tile come into a 16 KB block by asynchronous copies, all in flight
+// at once, issued before the accumulator wait.
+template <int NB, bool SPLIT = false, bool ROWS = false>
 struct BgCfg {
+  static constexpr int NST = SPLIT && ROWS ? 2 : BG_STAGES;  // ring stages
   static constexpr int NH = NB == 384 ? 192 : NB;  // N per MMA instruction (at most 256)
   static constexpr int NHALF = NB / NH;
+  static constexpr int ACC = 2 * NB <= 512 ? 2 : 1;
   static constexpr int A_BYTES = BG_TM * 128;
   static constexpr int B_BYTES = NB * 128;
   static constexpr int STAGE = (SPLIT ? 2 : 1) * (A_BYTES + B_BYTES);
-  static constexpr int OFF_BAR = BG_STAGES * STAGE;
-  static constexpr int SMEM = OFF_BAR + 8 * 16 + 16 + 1024;
-  static constexpr uint32_t TMEM_COLS = NB <= 128 ? 128 : (NB <= 256 ? 256 : 512);
+  static constexpr int OFF_STG = NST * STAGE;
+  static constexpr int OFF_ROWS = OFF_STG + 4 * 4096;
+  static constexpr int OFF_BAR = OFF_ROWS + (ROWS ? 4 * 16384 : 0);
+  static constexpr int SMEM = OFF_BAR + 16 * 8 + 16 + 1024;
+  static constexpr uint32_t TMEM_COLS = ACC * NB <= 128 ? 128 : (ACC * NB <= 256 ? 256 : 512);
   static constexpr uint32_t IDESC = idesc_tf32_f32<BG_TM, NH>();
   static_assert(SMEM <= 232448, "shared memory");
   static_assert(NB % 128 == 0, "B is copied in boxes of 128 rows");
 };
+
+// Staging of a warp's 32 rows x 32 columns: row r's 16-byte unit q sits at
+// unit q ^ (r % 8) of its 128-byte line, so both the row-per-lane side and the
+// coalesced side (8 lanes per row, 4 rows per instruction) are conflict-free.
+__device__ __forceinline__ void stage_put(float* buf, int lane, const float (&v)[32]) {
+  __syncwarp();  // earlier reads of the buffer are done
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    *reinterpret_cast<float4*>(buf + lane * 32 + 4 * (q ^ (lane & 7))) =
+        make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  __syncwarp();
+}
+
+// Store the staged block to rows g + r * ld (r < nvalid), coalesced.
+__device__ __forceinline__ void stage_flush(const float* buf, int lane, float* g, int64_t ld,
+                                            int nvalid) {
+  const int u = lane & 7;
+#pragma unroll
+  for (int it = 0; it < 8; ++it) {
+    const int r = 4 * it + (lane >> 3);
+    const float4 x = *reinterpret_cast<const float4*>(buf + r * 32 + 4 * (u ^ (r & 7)));
+    if (r < nvalid) *reinterpret_cast<float4*>(g + r * ld + 4 * u) = x;
+  }
+}
 
 struct BgArgs {
   CUtensorMap ta;        // A [rows][K] FP32 (TF32 values), boxes of 32 columns x 128 rows
@@ -94,38 +131,75 @@ __device__ __forceinline__ bool bg_wait(uint64_t* bar, uint32_t parity, int* err
   return false;
 }
 
+__device__ __forceinline__ void bg_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ float tf32r(float f) { return __uint_as_float(to_tf32(f)); }
 
-__device__ __forceinline__ void st4(float* p, float a, float b, float c, float d) {
-  *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+// The warp's 32 rows g + r * H (r < nvalid; zeros after) into its row block:
+// row r's 16-byte unit u at unit u ^ (r % 8), one row per copy instruction.
+__device__ __forceinline__ void rows_fetch(float* blk, int lane, const float* g, int nvalid) {
+#pragma unroll 4
+  for (int r = 0; r < 32; ++r) {
+    float* d = blk + r * BG_H + 4 * (lane ^ (r & 7));
+    if (r < nvalid)
+      cp_async16(d, g + (int64_t)r * BG_H + 4 * lane);
+    else
+      *reinterpret_cast<float4*>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+__device__ __forceinline__ void rows_ready() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncwarp();
+}
+
+// Columns c0 .. c0 + 31 of the lane's own row from the row block.
+__device__ __forceinline__ void rows_get(const float* blk, int lane, int c0, float (&v)[32]) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float4 x = *reinterpret_cast<const float4*>(blk + lane * BG_H + 4 * (((c0 >> 2) + q) ^ (lane & 7)));
+    v[4 * q] = x.x;
+    v[4 * q + 1] = x.y;
+    v[4 * q + 2] = x.z;
+    v[4 * q + 3] = x.w;
+  }
 }
 
 template <int NB, int EPI, bool SPLIT>
 __global__ void __launch_bounds__(BG_THREADS, 1) k_bwd_gemm(const __grid_constant__ BgArgs a) {
-  using C = BgCfg<NB, SPLIT>;
+  using C = BgCfg<NB, SPLIT, EPI == EPI_LN2 || EPI == EPI_LN1B>;
   static_assert(EPI == EPI_STORE || NB == BG_H, "row-wise epilogues take H columns");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);  // FULL[3], EMPTY[3], DONE
+  // FULL[3], EMPTY[3], TFULL[2], TEMPTY[2]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);
   uint64_t* full = bars;
-  uint64_t* empty = bars + BG_STAGES;
-  uint64_t* done = bars + 2 * BG_STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::OFF_BAR + 8 * 16);
-  volatile int* abort = reinterpret_cast<volatile int*>(smem + C::OFF_BAR + 8 * 16 + 4);
+  uint64_t* empty = bars + C::NST;
+  uint64_t* tfull = bars + 2 * C::NST;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::OFF_BAR + 16 * 8);
+  volatile int* abort = reinterpret_cast<volatile int*>(smem + C::OFF_BAR + 16 * 8 + 4);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
+  // persistent: tiles blockIdx.x, blockIdx.x + gridDim.x, ... below R
   const int64_t R = a.R_dev ? (int64_t)*a.R_dev : a.R_host;
-  const int64_t row0 = (int64_t)blockIdx.x * BG_TM;
-  if (row0 >= R) return;  // the whole CTA: no barrier or TMEM use yet
+  const int64_t n_tiles = (R + BG_TM - 1) / BG_TM;
+  if ((int64_t)blockIdx.x >= n_tiles) return;  // the whole CTA: no barrier or TMEM use yet
+  const int64_t my_tiles = (n_tiles - 1 - blockIdx.x) / gridDim.x + 1;
   const int nk = a.K / BG_KC;
 
   if (tid == 0) {
-    for (int s = 0; s < BG_STAGES; ++s) {
+    for (int s = 0; s < C::NST; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);  // every epilogue warp has read the accumulator
+    }
     *abort = 0;
     fence_mbar_init();
   }
@@ -139,13 +213,16 @@ __global__ void __launch_bounds__(BG_THREADS, 1) k_bwd_gemm(const __grid_constan
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 4) {
-    // ---- TMA producer: stage s holds A[row0.., 32 c..] and B[.., 32 c..] -------
+    // ---- TMA producer: chunk q (tile q / nk, K columns 32 (q % nk) ..) into stage q % 3
     if (lane == 0) {
-      int issued = 0;
-      for (int c = 0; c < nk; ++c) {
-        const int st = c % BG_STAGES;
-        const uint32_t round = (uint32_t)(c / BG_STAGES);
+      int64_t issued = 0;
+      const int64_t total = my_tiles * nk;
+      for (int64_t q = 0; q < total; ++q) {
+        const int st = (int)(q % C::NST);
+        const uint32_t round = (uint32_t)(q / C::NST);
         if (round > 0 && !bg_wait(&empty[st], (round - 1) & 1, a.err, abort)) break;
+        const int64_t row0 = (blockIdx.x + (q / nk) * gridDim.x) * BG_TM;
+        const int c = (int)(q % nk);
         uint8_t* sa = smem + st * C::STAGE;
         mbar_arrive_expect_tx(&full[st], C::STAGE);
         tma_load_2d(sa, &a.ta, BG_KC * c, (int)row0, &full[st]);
@@ -163,217 +240,219 @@ __global__ void __launch_bounds__(BG_THREADS, 1) k_bwd_gemm(const __grid_constan
       }
       if (*abort) {
         // let the copies still in flight land before the CTA exits (bounded)
-        for (int c = issued > BG_STAGES ? issued - BG_STAGES : 0; c < issued; ++c)
-          for (int i = 0; i < (1 << 20) && !mbar_try_wait(&full[c % BG_STAGES], (c / BG_STAGES) & 1); ++i) {
+        for (int64_t q = issued > C::NST ? issued - C::NST : 0; q < issued; ++q)
+          for (int i = 0; i < (1 << 20) &&
+                          !mbar_try_wait(&full[q % C::NST], (uint32_t)(q / C::NST) & 1);
+               ++i) {
           }
       }
     }
   } else if (warp == 5) {
-    // ---- MMA issuer ------------------------------------------------------------
+    // ---- MMA issuer: tile i into accumulator i % ACC --------------------------------
     if (lane == 0) {
       bool ok = true;
-      for (int c = 0; c < nk && ok; ++c) {
-        const int st = c % BG_STAGES;
-        ok = bg_wait(&full[st], (uint32_t)(c / BG_STAGES) & 1, a.err, abort);
-        if (!ok) break;
+      int64_t q = 0;
+      for (int64_t i = 0; i < my_tiles && ok; ++i) {
+        const int b = (int)(i % C::ACC);
+        const uint32_t u = (uint32_t)(i / C::ACC);
+        if (u > 0 && !(ok = bg_wait(&tempty[b], (u - 1) & 1, a.err, abort))) break;
         tc_fence_after();
-        const uint32_t sa = smem_u32(smem + st * C::STAGE);
-        const uint32_t sb = sa + C::A_BYTES;
-        const uint32_t sal = sb + C::B_BYTES, sbl = sal + C::A_BYTES;  // SPLIT: low parts
+        const uint32_t d0 = tmem + b * NB;
+        for (int c = 0; c < nk; ++c, ++q) {
+          const int st = (int)(q % C::NST);
+          if (!(ok = bg_wait(&full[st], (uint32_t)(q / C::NST) & 1, a.err, abort))) break;
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + st * C::STAGE);
+          const uint32_t sb = sa + C::A_BYTES;
+          const uint32_t sal = sb + C::B_BYTES, sbl = sal + C::A_BYTES;  // SPLIT: low parts
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
+          for (int k = 0; k < 4; ++k)
 #pragma unroll
-          for (int h = 0; h < C::NHALF; ++h) {
-            const uint32_t d = tmem + h * C::NH, bo = h * C::NH * 128 + 32 * k;
-            if constexpr (SPLIT) {  // the small cross terms first
-              mma_tf32(d, sdesc_k_sw128(sal + 32 * k), sdesc_k_sw128(sb + bo), C::IDESC,
-                       (c > 0 || k > 0) ? 1u : 0u);
-              mma_tf32(d, sdesc_k_sw128(sa + 32 * k), sdesc_k_sw128(sbl + bo), C::IDESC, 1u);
-              mma_tf32(d, sdesc_k_sw128(sa + 32 * k), sdesc_k_sw128(sb + bo), C::IDESC, 1u);
-            } else {
-              mma_tf32(d, sdesc_k_sw128(sa + 32 * k), sdesc_k_sw128(sb + bo), C::IDESC,
-                       (c > 0 || k > 0) ? 1u : 0u);
+            for (int h = 0; h < C::NHALF; ++h) {
+              const uint32_t d = d0 + h * C::NH, bo = h * C::NH * 128 + 32 * k;
+              if constexpr (SPLIT) {  // the small cross terms first
+                mma_tf32(d, sdesc_k_sw128(sal + 32 * k), sdesc_k_sw128(sb + bo), C::IDESC,
+                         (c > 0 || k > 0) ? 1u : 0u);
+                mma_tf32(d, sdesc_k_sw128(sa + 32 * k), sdesc_k_sw128(sbl + bo), C::IDESC, 1u);
+                mma_tf32(d, sdesc_k_sw128(sa + 32 * k), sdesc_k_sw128(sb + bo), C::IDESC, 1u);
+              } else {
+                mma_tf32(d, sdesc_k_sw128(sa + 32 * k), sdesc_k_sw128(sb + bo), C::IDESC,
+                         (c > 0 || k > 0) ? 1u : 0u);
+              }
             }
-          }
-        mma_commit(&empty[st]);
+          mma_commit(&empty[st]);
+        }
+        if (ok) mma_commit(&tfull[b]);
       }
-      mma_commit(done);  // also after an abort: the epilogue's wait then ends
     }
   } else {
     // ---- epilogue: warp w owns TMEM lanes (tile rows) 32 w .. 32 w + 31 ----------
-    const bool ok = bg_wait(done, 0, a.err, abort);
-    tc_fence_after();
-    const int r = 32 * warp + lane;
-    const int64_t gr = row0 + r;
-    const bool valid = ok && gr < R;
-    const uint32_t tl = tmem + (static_cast<uint32_t>(32 * warp) << 16);
-    if constexpr (EPI == EPI_STORE) {
-      for (int c0 = 0; c0 < NB; c0 += 32) {
-        float v[32];
-        tmem_ld32_wait(tl + c0, v);
-        if (valid) {
-          float* o = a.o0 + gr * a.ldo + c0;
-#pragma unroll
-          for (int q = 0; q < 8; ++q) st4(o + 4 * q, v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    float* buf = reinterpret_cast<float*>(smem + C::OFF_STG + 4096 * warp);
+    float* blk = reinterpret_cast<float*>(smem + C::OFF_ROWS + 16384 * warp);  // ROWS only
+    const uint32_t lane_off = static_cast<uint32_t>(32 * warp) << 16;
+    for (int64_t i = 0; i < my_tiles; ++i) {
+      const int b = (int)(i % C::ACC);
+      const int64_t r0w = (blockIdx.x + i * gridDim.x) * BG_TM + 32 * warp;  // the warp's first row
+      const int nvalid = (int)(R - r0w < 32 ? (R - r0w > 0 ? R - r0w : 0) : 32);
+      if constexpr (EPI == EPI_LN2) rows_fetch(blk, lane, a.G + r0w * BG_H, nvalid);
+      if constexpr (EPI == EPI_LN1B) rows_fetch(blk, lane, a.N1 + r0w * BG_H, nvalid);
+      if (!bg_wait(&tfull[b], (uint32_t)(i / C::ACC) & 1, a.err, abort)) break;
+      tc_fence_after();
+      if constexpr (EPI == EPI_LN2 || EPI == EPI_LN1B) rows_ready();
+      const uint32_t tl = tmem + b * NB + lane_off;
+      const int64_t gr = r0w + lane;
+      const bool valid = lane < nvalid;
+      if constexpr (EPI == EPI_STORE) {
+        for (int c0 = 0; c0 < NB; c0 += 32) {
+          float v[32];
+          tmem_ld32_wait(tl + c0, v);
+          stage_put(buf, lane, v);
+          stage_flush(buf, lane, a.o0 + r0w * a.ldo + c0, a.ldo, nvalid);
         }
-      }
-    } else if constexpr (EPI == EPI_LN1F || EPI == EPI_LN2) {
-      // v = acc + b, read from TMEM 32 columns at a time (again for every pass,
-      // which keeps the row out of registers); LayerNorm statistics in two passes
-      auto ldc = [&](int c0, float (&v)[32]) {
-        tmem_ld32_wait(tl + c0, v);
+      } else if constexpr (EPI == EPI_LN1F || EPI == EPI_LN2) {
+        // v = acc + b, read from TMEM 32 columns at a time (again for every pass,
+        // which keeps the row out of registers); LayerNorm statistics in two passes
+        auto ldc = [&](int c0, float (&v)[32]) {
+          tmem_ld32_wait(tl + c0, v);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] += __ldg(a.b + c0 + j);
-      };
-      float s = 0.f;
-#pragma unroll 1
-      for (int c0 = 0; c0 < BG_H; c0 += 32) {
-        float v[32];
-        ldc(c0, v);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) s += v[j];
-      }
-      const float mean = s * (1.0f / BG_H);
-      float q = 0.f;
-#pragma unroll 1
-      for (int c0 = 0; c0 < BG_H; c0 += 32) {
-        float v[32];
-        ldc(c0, v);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const float d = v[j] - mean;
-          q += d * d;
-        }
-      }
-      const float rstd = 1.0f / sqrtf(q * (1.0f / BG_H) + kBgLnEps);
-      if constexpr (EPI == EPI_LN1F) {
-        if (valid) a.rs_out[gr] = rstd;
+          for (int j = 0; j < 32; ++j) v[j] += __ldg(a.b + c0 + j);
+        };
+        float s = 0.f;
 #pragma unroll 1
         for (int c0 = 0; c0 < BG_H; c0 += 32) {
           float v[32];
           ldc(c0, v);
-          if (valid) {
-            float* o_r1 = a.o0 + gr * BG_H + c0;
-            float* o_n1 = a.o1 + gr * BG_H + c0;
 #pragma unroll
-            for (int j = 0; j < 32; j += 4) {
-              float n[4], y[4], lo[4];
+          for (int j = 0; j < 32; ++j) s += v[j];
+        }
+        const float mean = s * (1.0f / BG_H);
+        float q = 0.f;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BG_H; c0 += 32) {
+          float v[32];
+          ldc(c0, v);
 #pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                n[u] = (v[j + u] - mean) * rstd;
-                const float r1 = fmaxf(fmaf(n[u], __ldg(a.g + c0 + j + u), __ldg(a.be + c0 + j + u)), 0.f);
-                y[u] = tf32r(r1);
-                lo[u] = tf32r(r1 - y[u]);
-              }
-              st4(o_r1 + j, y[0], y[1], y[2], y[3]);
-              st4(o_n1 + j, n[0], n[1], n[2], n[3]);
-              if (a.o3) st4(a.o3 + gr * BG_H + c0 + j, lo[0], lo[1], lo[2], lo[3]);
-            }
+          for (int j = 0; j < 32; ++j) {
+            const float d = v[j] - mean;
+            q += d * d;
           }
         }
-      } else {  // EPI_LN2
-        // pass 1: d = G where y2 = n2 g2 + be2 > 0; DY2, DY2 n2; the means of
-        // dn = d g2 and of dn n2
+        const float rstd = 1.0f / sqrtf(q * (1.0f / BG_H) + kBgLnEps);
+        if constexpr (EPI == EPI_LN1F) {
+          if (valid) a.rs_out[gr] = rstd;
+#pragma unroll 1
+          for (int c0 = 0; c0 < BG_H; c0 += 32) {
+            float v[32], y[32];
+            ldc(c0, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              v[j] = (v[j] - mean) * rstd;  // n1
+              y[j] = fmaxf(fmaf(v[j], __ldg(a.g + c0 + j), __ldg(a.be + c0 + j)), 0.f);  // r1
+            }
+            stage_put(buf, lane, v);
+            stage_flush(buf, lane, a.o1 + r0w * BG_H + c0, BG_H, nvalid);
+            if (a.o3) {
+#pragma unroll
+              for (int j = 0; j < 32; ++j) v[j] = tf32r(y[j] - tf32r(y[j]));  // low part
+              stage_put(buf, lane, v);
+              stage_flush(buf, lane, a.o3 + r0w * BG_H + c0, BG_H, nvalid);
+            }
+#pragma unroll
+            for (int j = 0; j < 32; ++j) y[j] = tf32r(y[j]);
+            stage_put(buf, lane, y);
+            stage_flush(buf, lane, a.o0 + r0w * BG_H + c0, BG_H, nvalid);
+          }
+        } else {  // EPI_LN2
+          // pass 1: d = G where y2 = n2 g2 + be2 > 0; DY2, DY2 n2; the means of
+          // dn = d g2 and of dn n2
+          float m1 = 0.f, m2 = 0.f;
+#pragma unroll 1
+          for (int c0 = 0; c0 < BG_H; c0 += 32) {
+            float v[32], gv[32];
+            ldc(c0, v);
+            rows_get(blk, lane, c0, gv);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const float gg = __ldg(a.g + c0 + j);
+              const float n = (v[j] - mean) * rstd;
+              const float d = fmaf(n, gg, __ldg(a.be + c0 + j)) > 0.f ? gv[j] : 0.f;
+              const float dn = d * gg;
+              m1 += dn;
+              m2 += dn * n;
+              gv[j] = d;
+              v[j] = d * n;
+            }
+            stage_put(buf, lane, gv);
+            stage_flush(buf, lane, a.o0 + r0w * BG_H + c0, BG_H, nvalid);
+            stage_put(buf, lane, v);
+            stage_flush(buf, lane, a.o1 + r0w * BG_H + c0, BG_H, nvalid);
+          }
+          m1 *= 1.0f / BG_H;
+          m2 *= 1.0f / BG_H;
+          // pass 2: DA2 = rstd2 (dn - m1 - n2 m2), the incoming rows read again
+#pragma unroll 1
+          for (int c0 = 0; c0 < BG_H; c0 += 32) {
+            float v[32], gv[32];
+            ldc(c0, v);
+            rows_get(blk, lane, c0, gv);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const float gg = __ldg(a.g + c0 + j);
+              const float n = (v[j] - mean) * rstd;
+              const float d = fmaf(n, gg, __ldg(a.be + c0 + j)) > 0.f ? gv[j] : 0.f;
+              v[j] = tf32r(rstd * (d * gg - m1 - n * m2));
+            }
+            stage_put(buf, lane, v);
+            stage_flush(buf, lane, a.o2 + r0w * BG_H + c0, BG_H, nvalid);
+          }
+        }
+      } else {  // EPI_LN1B: acc = dr1
+        const float rstd = valid ? a.rs_in[gr] : 0.f;
         float m1 = 0.f, m2 = 0.f;
-        const float* grow = a.G + (valid ? gr : 0) * BG_H;
+        // pass 1: d = dr1 where n1 g1 + be1 > 0; DY1, DY1 n1; the means
 #pragma unroll 1
         for (int c0 = 0; c0 < BG_H; c0 += 32) {
-          float v[32];
-          ldc(c0, v);
-          if (valid) {
+          float v[32], nv[32];
+          tmem_ld32_wait(tl + c0, v);
+          rows_get(blk, lane, c0, nv);
 #pragma unroll
-            for (int j = 0; j < 32; j += 4) {
-              const float4 go = *reinterpret_cast<const float4*>(grow + c0 + j);
-              const float gv[4] = {go.x, go.y, go.z, go.w};
-              float d[4], n[4];
-#pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                const float gg = __ldg(a.g + c0 + j + u);
-                n[u] = (v[j + u] - mean) * rstd;
-                d[u] = fmaf(n[u], gg, __ldg(a.be + c0 + j + u)) > 0.f ? gv[u] : 0.f;
-                const float dn = d[u] * gg;
-                m1 += dn;
-                m2 += dn * n[u];
-              }
-              st4(a.o0 + gr * BG_H + c0 + j, d[0], d[1], d[2], d[3]);
-              st4(a.o1 + gr * BG_H + c0 + j, d[0] * n[0], d[1] * n[1], d[2] * n[2], d[3] * n[3]);
-            }
+          for (int j = 0; j < 32; ++j) {
+            const float gg = __ldg(a.g + c0 + j);
+            const float d = fmaf(nv[j], gg, __ldg(a.be + c0 + j)) > 0.f ? v[j] : 0.f;
+            const float dn = d * gg;
+            m1 += dn;
+            m2 += dn * nv[j];
+            v[j] = d;
+            nv[j] = d * nv[j];
           }
+          stage_put(buf, lane, v);
+          stage_flush(buf, lane, a.o0 + r0w * BG_H + c0, BG_H, nvalid);
+          stage_put(buf, lane, nv);
+          stage_flush(buf, lane, a.o1 + r0w * BG_H + c0, BG_H, nvalid);
         }
         m1 *= 1.0f / BG_H;
         m2 *= 1.0f / BG_H;
-        // pass 2: DA2 = rstd2 (dn - m1 - n2 m2), the incoming rows read again
+        // pass 2: DA1 = rstd1 (dn - m1 - n1 m2)
 #pragma unroll 1
         for (int c0 = 0; c0 < BG_H; c0 += 32) {
-          float v[32];
-          ldc(c0, v);
-          if (valid) {
+          float v[32], nv[32];
+          tmem_ld32_wait(tl + c0, v);
+          rows_get(blk, lane, c0, nv);
 #pragma unroll
-            for (int j = 0; j < 32; j += 4) {
-              const float4 go = *reinterpret_cast<const float4*>(grow + c0 + j);
-              const float gv[4] = {go.x, go.y, go.z, go.w};
-              float o[4];
-#pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                const float gg = __ldg(a.g + c0 + j + u);
-                const float n = (v[j + u] - mean) * rstd;
-                const float d = fmaf(n, gg, __ldg(a.be + c0 + j + u)) > 0.f ? gv[u] : 0.f;
-                o[u] = tf32r(rstd * (d * gg - m1 - n * m2));
-              }
-              st4(a.o2 + gr * BG_H + c0 + j, o[0], o[1], o[2], o[3]);
-            }
+          for (int j = 0; j < 32; ++j) {
+            const float gg = __ldg(a.g + c0 + j);
+            const float d = fmaf(nv[j], gg, __ldg(a.be + c0 + j)) > 0.f ? v[j] : 0.f;
+            v[j] = tf32r(rstd * (d * gg - m1 - nv[j] * m2));
           }
+          stage_put(buf, lane, v);
+          stage_flush(buf, lane, a.o2 + r0w * BG_H + c0, BG_H, nvalid);
         }
       }
-    } else {  // EPI_LN1B: acc = dr1
-      const float* n1row = a.N1 + (valid ? gr : 0) * BG_H;
-      const float rstd = valid ? a.rs_in[gr] : 0.f;
-      float m1 = 0.f, m2 = 0.f;
-      // pass 1: d = dr1 where n1 g1 + be1 > 0; DY1, DY1 n1; the means
-      for (int c0 = 0; c0 < BG_H; c0 += 32) {
-        float v[32];
-        tmem_ld32_wait(tl + c0, v);
-        if (valid) {
-#pragma unroll
-          for (int j = 0; j < 32; j += 4) {
-            const float4 n4 = *reinterpret_cast<const float4*>(n1row + c0 + j);
-            const float nv[4] = {n4.x, n4.y, n4.z, n4.w};
-            float d[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const float gg = __ldg(a.g + c0 + j + u);
-              d[u] = fmaf(nv[u], gg, __ldg(a.be + c0 + j + u)) > 0.f ? v[j + u] : 0.f;
-              const float dn = d[u] * gg;
-              m1 += dn;
-              m2 += dn * nv[u];
-            }
-            st4(a.o0 + gr * BG_H + c0 + j, d[0], d[1], d[2], d[3]);
-            st4(a.o1 + gr * BG_H + c0 + j, d[0] * nv[0], d[1] * nv[1], d[2] * nv[2], d[3] * nv[3]);
-          }
-        }
-      }
-      m1 *= 1.0f / BG_H;
-      m2 *= 1.0f / BG_H;
-      // pass 2: DA1 = rstd1 (dn - m1 - n1 m2)
-      for (int c0 = 0; c0 < BG_H; c0 += 32) {
-        float v[32];
-        tmem_ld32_wait(tl + c0, v);
-        if (valid) {
-#pragma unroll
-          for (int j = 0; j < 32; j += 4) {
-            const float4 n4 = *reinterpret_cast<const float4*>(n1row + c0 + j);
-            const float nv[4] = {n4.x, n4.y, n4.z, n4.w};
-            float o[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const float gg = __ldg(a.g + c0 + j + u);
-              const float d = fmaf(nv[u], gg, __ldg(a.be + c0 + j + u)) > 0.f ? v[j + u] : 0.f;
-              o[u] = tf32r(rstd * (d * gg - m1 - nv[u] * m2));
-            }
-            st4(a.o2 + gr * BG_H + c0 + j, o[0], o[1], o[2], o[3]);
-          }
-        }
-      }
+      // the accumulator (and the row block) is read: the MMA may reuse it for
+      // tile i + ACC, the next fetch may overwrite the block
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) bg_arrive(&tempty[b]);
     }
   }
   tc_fence_before();
@@ -477,7 +556,7 @@ const char* kBgName[4] = {"gnn_block_backward_tc_ln1", "gnn_block_backward_tc_ln
 template <int NB, int EPI, bool SPLIT = false>
 cudaError_t launch_bg(etx_ctx* ctx, BgArgs& a, const float* A, int64_t Rcap, const float* B,
                       cudaStream_t s, const float* A_lo = nullptr, const float* B_lo = nullptr) {
-  using C = BgCfg<NB, SPLIT>;
+  using C = BgCfg<NB, SPLIT, EPI == EPI_LN2 || EPI == EPI_LN1B>;
   if (!encode_rows(&a.ta, A, Rcap, a.K) || !encode_rows(&a.tb, B, NB, a.K))
     return cudaErrorInvalidValue;
   if (SPLIT && (!encode_rows(&a.ta2, A_lo, Rcap, a.K) || !encode_rows(&a.tb2, B_lo, NB, a.K)))
@@ -491,7 +570,9 @@ cudaError_t launch_bg(etx_ctx* ctx, BgArgs& a, const float* A, int64_t Rcap, con
   }
   const int64_t tiles = (Rcap + BG_TM - 1) / BG_TM;
   if (tiles == 0) return cudaSuccess;
-  launch(ctx, kBgName[EPI], k_bwd_gemm<NB, EPI, SPLIT>, (unsigned)tiles, BG_THREADS, C::SMEM, s, a);
+  // persistent: one CTA per SM (shared memory holds one), tiles strided over them
+  const int grid = (int)(tiles < ctx->n_sms ? tiles : ctx->n_sms);
+  launch(ctx, kBgName[EPI], k_bwd_gemm<NB, EPI, SPLIT>, grid, BG_THREADS, C::SMEM, s, a);
   return cudaGetLastError();
 }
 
