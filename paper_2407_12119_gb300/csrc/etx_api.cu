@@ -258,6 +258,7 @@ etx_status etx_ctx_create(const etx_config* cfg, int32_t device, etx_ctx** out) 
       chk(dmalloc(ctx, &ctx->bw_rstd1, R, "backward rstd1"));
       chk(dmalloc(ctx, &ctx->bw_Xlo, R * 3 * H, "backward input low parts"));
       chk(dmalloc(ctx, &ctx->bw_R1lo, R * H, "backward R1 low parts"));
+      chk(dmalloc(ctx, &ctx->bw_cs_part, 2 * (size_t)ctx->n_sms * 4 * 3 * H, "column-sum partials"));
       // per block: W1, W1^T, W1 low [H][K] each, W2, W2^T, W2 low [H][H] each
       const size_t per_upd = 3 * (size_t)H * 3 * H + 3 * (size_t)H * H;
       const size_t per_enc = 3 * (size_t)H * 2 * H + 3 * (size_t)H * H;
@@ -294,7 +295,7 @@ etx_status etx_ctx_destroy(etx_ctx* ctx) {
                   ctx->bw_DY1N1, ctx->bw_DA2, ctx->bw_DY2, ctx->bw_DY2N2, ctx->h_lp,
                   ctx->small, ctx->w_trip, ctx->bw_part, ctx->red_part, ctx->repack_dev,
                   ctx->bw_N1, ctx->bw_rstd1, ctx->bw_img, ctx->bw_img_jobs, ctx->bw_Xlo,
-                  ctx->bw_R1lo};
+                  ctx->bw_R1lo, ctx->bw_cs_part};
   for (void* p : bufs)
     if (p) cudaFree(p);
   for (auto& r : ctx->prof) {

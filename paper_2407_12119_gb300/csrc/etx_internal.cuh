@@ -160,6 +160,7 @@ struct etx_ctx {
   float* bw_N1 = nullptr;
   float* bw_Xlo = nullptr;   // low parts of the block inputs [R][3H] and of R1 [R][H]
   float* bw_R1lo = nullptr;
+  float* bw_cs_part = nullptr;  // 2 x [4 n_sms][3H]: fused column-sum partials
   float* bw_rstd1 = nullptr;
   float* bw_img = nullptr;
   void* bw_img_jobs = nullptr;
@@ -251,7 +252,11 @@ struct BlockBwdTc {
   const float* G;              // incoming gradient rows [R][H]
   float *X, *R1, *N1, *rstd1, *DA1, *DY1, *DY1N1, *DA2, *DY2, *DY2N2, *DX;
   float *X_lo, *R1_lo;                 // low parts of X and R1 (split products)
+  // column-sum partials of layer 1 and layer 2 ([parts][3H]: b, g, be gradients)
+  float *cs1, *cs2;
 };
+// partials per column-sum array of a block with rows_cap rows
+int block_bwd_tc_colsum_parts(const etx_ctx* ctx, int64_t rows_cap);
 bool block_bwd_tc_supported(const etx_ctx* ctx);
 cudaError_t launch_block_bwd_tc(etx_ctx* ctx, int mode, const BlockBwdTc& p, cudaStream_t s);
 // TF32 images of the weights: a job list (src, dst, n) held on the device

@@ -416,8 +416,30 @@ __global__ void k_reduce_parts(const float* __restrict__ P, int splits, int64_t 
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < MN;
        i += (int64_t)gridDim.x * blockDim.x) {
     float acc = 0.f;
-    for (int z = 0; z < splits; ++z) acc += P[(int64_t)z * MN + i];
+#pragma unroll 8
+    for (int z = 0; z < splits; ++z) acc += P[(int64_t)z * MN + i];  // loads in flight, adds in order
     C[i] += acc;
+  }
+}
+
+// The same sum for a short vector over many partials (column sums): a block
+// takes 32 outputs; warp y adds the partials z = y, y + 8, ... (consecutive
+// lanes read consecutive outputs), and the 8 warp sums are added in warp order.
+__global__ void __launch_bounds__(256) k_reduce_parts_narrow(const float* __restrict__ P, int splits,
+                                                             int64_t MN, float* __restrict__ C) {
+  __shared__ float sh[8][32];
+  const int x = threadIdx.x & 31, y = threadIdx.x >> 5;
+  const int64_t i = (int64_t)blockIdx.x * 32 + x;
+  float acc = 0.f;
+  if (i < MN)
+    for (int z = y; z < splits; z += 8) acc += P[(int64_t)z * MN + i];
+  sh[y][x] = acc;
+  __syncthreads();
+  if (y == 0 && i < MN) {
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += sh[w][x];
+    C[i] += t;
   }
 }
 
@@ -627,6 +649,13 @@ struct Bwd {
       reduce(sp, (int64_t)M * Ncols, out);
       return;
     }
+    // a narrow dW (the node encoder's 3 inputs) is a few hundred values: split its
+    // rows finely (about 128 a CTA) so the row loop is not a serial latency chain
+    if (Ncols <= 32) {
+      const int64_t Rcap = Rd ? Ecap : Rh;
+      const int64_t cap = (int64_t)ctx->n_sms * H * 3 * H / ((int64_t)M * Ncols);  // bw_part size
+      splits = (int)std::max<int64_t>(splits, std::min<int64_t>({(int64_t)ctx->n_sms * 4, (Rcap + 127) / 128, cap}));
+    }
     launch(ctx, "gnn_weight_grad", k_gemm_tn, dim3((M + kTileM - 1) / kTileM, (Ncols + 127) / 128, splits),
            kTileThreads, 0, s, A, lda, B, ldb, M, Ncols, Rh, Rd, out, ctx->bw_part);
     reduce(splits, (int64_t)M * Ncols, out);
@@ -641,9 +670,28 @@ struct Bwd {
     launch(ctx, "gnn_colsum", k_colsum3, cb, H, 0, s, A0, A1, A2, H, Rh, Rd, ctx->bw_part);
     reduce(cb, 3 * H, out);
   }
-  void reduce(int parts, int64_t n, float* out) {
+  void reduce(int parts, int64_t n, float* out, const float* src = nullptr) {
     const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, ctx->n_sms * 4));
-    launch(ctx, "gnn_grad_reduce", k_reduce_parts, g, 256, 0, s, (const float*)ctx->bw_part, parts, n, out);
+    const float* P = src ? src : (const float*)ctx->bw_part;
+    if (n <= 4096 && parts >= 64)
+      launch(ctx, "gnn_grad_reduce", k_reduce_parts_narrow, (int)((n + 31) / 32), 256, 0, s, P, parts, n, out);
+    else
+      launch(ctx, "gnn_grad_reduce", k_reduce_parts, g, 256, 0, s, P, parts, n, out);
+  }
+
+  // Parameter gradients of a block whose reverse pass ran on the tensor cores:
+  // the weight gradients from the per-row factors, the b, g, be gradients of
+  // both layers from the column-sum partials that pass left.
+  void param_grads_tc(const BwdArgs& a, const BlockGrad& g, int K, bool is_edge) {
+    const int32_t* Rd = is_edge ? n_edges : nullptr;
+    const int64_t Rh = is_edge ? 0 : N;
+    const int64_t Rcap = is_edge ? Ecap : N;
+    const int splits = grad_splits(ctx, Rcap);
+    const int parts = block_bwd_tc_colsum_parts(ctx, Rcap);
+    weight_grad(a.DA1, H, a.X, K, H, K, Rh, Rd, splits, g.W1);
+    reduce(parts, 3 * H, g.b1, ctx->bw_cs_part + (size_t)ctx->n_sms * 4 * 3 * H);
+    weight_grad(a.DA2, H, a.R1, H, H, H, Rh, Rd, splits, g.W2);
+    reduce(parts, 3 * H, g.b2, ctx->bw_cs_part);
   }
 
   // Parameter gradients of one block from the per-row factors.
@@ -794,6 +842,8 @@ cudaError_t backward(etx_ctx* ctx, const float* dlogits, float* dparams, cudaStr
     p.W2n_lo = im.W2n_lo;
     p.X_lo = ctx->bw_Xlo;
     p.R1_lo = ctx->bw_R1lo;
+    p.cs2 = ctx->bw_cs_part;
+    p.cs1 = ctx->bw_cs_part + (size_t)ctx->n_sms * 4 * 3 * H;
     p.b1 = a.l1.b;
     p.g1 = a.g1;
     p.be1 = a.be1;
@@ -860,7 +910,8 @@ cudaError_t backward(etx_ctx* ctx, const float* dlogits, float* dparams, cudaStr
       } else {
         b.template block_pass<B_EDGE_UPD>(a, Ecap);
       }
-      b.param_grads(a, g_edge[k], 3 * H, true, true);
+      if (tc) b.param_grads_tc(a, g_edge[k], 3 * H, true);
+      else b.param_grads(a, g_edge[k], 3 * H, true, true);
       launch(ctx, "gnn_add_rows", k_add_cols, ge, 256, 0, s, ctx->de, H, (const float*)ctx->bw_DX,
              3 * H, 0, 1, (int64_t)0, (const int32_t*)ctx->n_edges);
       if (N > 0)
@@ -882,7 +933,8 @@ cudaError_t backward(etx_ctx* ctx, const float* dlogits, float* dparams, cudaStr
       } else {
         b.template block_pass<B_NODE_UPD>(a, N);
       }
-      b.param_grads(a, g_node[k], 3 * H, false, true);
+      if (tc) b.param_grads_tc(a, g_node[k], 3 * H, false);
+      else b.param_grads(a, g_node[k], 3 * H, false, true);
       launch(ctx, "gnn_add_rows", k_add_cols, gn, 256, 0, s, ctx->dh, H, (const float*)ctx->bw_DX,
              3 * H, 0, 1, N, (const int32_t*)nullptr);
       launch(ctx, "gnn_gather_backward", k_gather_bwd<H>, gg, 256, 0, s, (const float*)ctx->bw_DX,
@@ -902,7 +954,8 @@ cudaError_t backward(etx_ctx* ctx, const float* dlogits, float* dparams, cudaStr
     } else {
       b.template block_pass<B_EDGE_ENC>(a, Ecap);
     }
-    b.param_grads(a, g_edge_enc, 2 * H, true, true);
+    if (tc) b.param_grads_tc(a, g_edge_enc, 2 * H, true);
+    else b.param_grads(a, g_edge_enc, 2 * H, true, true);
     if (N > 0)
       launch(ctx, "gnn_scatter_backward", k_scatter_bwd<H>, gs, 256, 0, s, (const float*)ctx->bw_DX,
              2 * H, 0, H, (const int32_t*)ctx->out_off, (const int32_t*)ctx->in_off,

@@ -53,7 +53,9 @@ enum BgEpi { EPI_LN1F = 0, EPI_LN2 = 1, EPI_LN1B = 2, EPI_STORE = 3 };
 // turns its row-per-thread values into coalesced 128-byte row segments.
 // ROWS: the epilogue reads a [R][H] array row by row (G or n1): each warp's 32
 // rows of a tile come into a 16 KB block by asynchronous copies, all in flight
-// at once, issued before the accumulator wait.
+// at once, issued before the accumulator wait.  These epilogues (LN2, LN1B) also
+// sum the columns of the three factors they write (the layer's bias, gain and
+// shift gradients), per warp in shared memory (3 x H floats).
 template <int NB, bool SPLIT = false, bool ROWS = false>
 struct BgCfg {
   static constexpr int NST = SPLIT && ROWS ? 2 : BG_STAGES;  // ring stages
@@ -65,7 +67,8 @@ struct BgCfg {
   static constexpr int STAGE = (SPLIT ? 2 : 1) * (A_BYTES + B_BYTES);
   static constexpr int OFF_STG = NST * STAGE;
   static constexpr int OFF_ROWS = OFF_STG + 4 * 4096;
-  static constexpr int OFF_BAR = OFF_ROWS + (ROWS ? 4 * 16384 : 0);
+  static constexpr int OFF_CS = OFF_ROWS + (ROWS ? 4 * 16384 : 0);
+  static constexpr int OFF_BAR = OFF_CS + (ROWS ? 4 * 3 * BG_H * 4 : 0);
   static constexpr int SMEM = OFF_BAR + 16 * 8 + 16 + 1024;
   static constexpr uint32_t TMEM_COLS = ACC * NB <= 128 ? 128 : (ACC * NB <= 256 ? 256 : 512);
   static constexpr uint32_t IDESC = idesc_tf32_f32<BG_TM, NH>();
@@ -112,6 +115,9 @@ struct BgArgs {
   float *o0, *o1, *o2;   // outputs (see the modes)
   float* o3;             // EPI_LN1F: the low part of R1 (R1 - tf32(R1), rounded), or NULL
   int ldo;               // EPI_STORE: row stride of o0
+  // EPI_LN2 / EPI_LN1B: column sums of o2, o1, o0 (a layer's b, g, be gradients)
+  // per (CTA, epilogue warp): [gridDim.x * 4][3 H], added in a fixed order later
+  float* cs_part;
   int* err;
 };
 
@@ -136,6 +142,16 @@ __device__ __forceinline__ void bg_arrive(uint64_t* bar) {
 }
 
 __device__ __forceinline__ float tf32r(float f) { return __uint_as_float(to_tf32(f)); }
+
+// Lane j adds column j of the staged block's first nvalid rows to *acc (its
+// own shared-memory word: no other lane touches it).
+__device__ __forceinline__ void stage_colsum(const float* buf, int lane, int nvalid, float* acc) {
+  float t = 0.f;
+#pragma unroll 8
+  for (int r = 0; r < 32; ++r)
+    if (r < nvalid) t += buf[r * 32 + 4 * ((lane >> 2) ^ (r & 7)) + (lane & 3)];
+  *acc += t;
+}
 
 // The warp's 32 rows g + r * H (r < nvalid; zeros after) into its row block:
 // row r's 16-byte unit u at unit u ^ (r % 8), one row per copy instruction.
@@ -187,7 +203,11 @@ __global__ void __launch_bounds__(BG_THREADS, 1) k_bwd_gemm(const __grid_constan
   // persistent: tiles blockIdx.x, blockIdx.x + gridDim.x, ... below R
   const int64_t R = a.R_dev ? (int64_t)*a.R_dev : a.R_host;
   const int64_t n_tiles = (R + BG_TM - 1) / BG_TM;
-  if ((int64_t)blockIdx.x >= n_tiles) return;  // the whole CTA: no barrier or TMEM use yet
+  if ((int64_t)blockIdx.x >= n_tiles) {  // the whole CTA: no barrier or TMEM use yet
+    if (a.cs_part)  // an empty partial
+      for (int i = tid; i < 4 * 3 * BG_H; i += BG_THREADS) a.cs_part[(int64_t)blockIdx.x * 4 * 3 * BG_H + i] = 0.f;
+    return;
+  }
   const int64_t my_tiles = (n_tiles - 1 - blockIdx.x) / gridDim.x + 1;
   const int nk = a.K / BG_KC;
 
@@ -289,6 +309,10 @@ __global__ void __launch_bounds__(BG_THREADS, 1) k_bwd_gemm(const __grid_constan
     // ---- epilogue: warp w owns TMEM lanes (tile rows) 32 w .. 32 w + 31 ----------
     float* buf = reinterpret_cast<float*>(smem + C::OFF_STG + 4096 * warp);
     float* blk = reinterpret_cast<float*>(smem + C::OFF_ROWS + 16384 * warp);  // ROWS only
+    float* csm = reinterpret_cast<float*>(smem + C::OFF_CS + 3 * BG_H * 4 * warp);  // ROWS only
+    constexpr bool CS = EPI == EPI_LN2 || EPI == EPI_LN1B;
+    if constexpr (CS)
+      for (int j = lane; j < 3 * BG_H; j += 32) csm[j] = 0.f;
     const uint32_t lane_off = static_cast<uint32_t>(32 * warp) << 16;
     for (int64_t i = 0; i < my_tiles; ++i) {
       const int b = (int)(i % C::ACC);
@@ -383,8 +407,10 @@ __global__ void __launch_bounds__(BG_THREADS, 1) k_bwd_gemm(const __grid_constan
               v[j] = d * n;
             }
             stage_put(buf, lane, gv);
+            stage_colsum(buf, lane, nvalid, csm + 2 * BG_H + c0 + lane);
             stage_flush(buf, lane, a.o0 + r0w * BG_H + c0, BG_H, nvalid);
             stage_put(buf, lane, v);
+            stage_colsum(buf, lane, nvalid, csm + BG_H + c0 + lane);
             stage_flush(buf, lane, a.o1 + r0w * BG_H + c0, BG_H, nvalid);
           }
           m1 *= 1.0f / BG_H;
@@ -403,6 +429,7 @@ __global__ void __launch_bounds__(BG_THREADS, 1) k_bwd_gemm(const __grid_constan
               v[j] = tf32r(rstd * (d * gg - m1 - n * m2));
             }
             stage_put(buf, lane, v);
+            stage_colsum(buf, lane, nvalid, csm + c0 + lane);
             stage_flush(buf, lane, a.o2 + r0w * BG_H + c0, BG_H, nvalid);
           }
         }
@@ -426,8 +453,10 @@ __global__ void __launch_bounds__(BG_THREADS, 1) k_bwd_gemm(const __grid_constan
             nv[j] = d * nv[j];
           }
           stage_put(buf, lane, v);
+          stage_colsum(buf, lane, nvalid, csm + 2 * BG_H + c0 + lane);
           stage_flush(buf, lane, a.o0 + r0w * BG_H + c0, BG_H, nvalid);
           stage_put(buf, lane, nv);
+          stage_colsum(buf, lane, nvalid, csm + BG_H + c0 + lane);
           stage_flush(buf, lane, a.o1 + r0w * BG_H + c0, BG_H, nvalid);
         }
         m1 *= 1.0f / BG_H;
@@ -445,6 +474,7 @@ __global__ void __launch_bounds__(BG_THREADS, 1) k_bwd_gemm(const __grid_constan
             v[j] = tf32r(rstd * (d * gg - m1 - nv[j] * m2));
           }
           stage_put(buf, lane, v);
+          stage_colsum(buf, lane, nvalid, csm + c0 + lane);
           stage_flush(buf, lane, a.o2 + r0w * BG_H + c0, BG_H, nvalid);
         }
       }
@@ -453,6 +483,13 @@ __global__ void __launch_bounds__(BG_THREADS, 1) k_bwd_gemm(const __grid_constan
       tc_fence_before();
       __syncwarp();
       if (lane == 0) bg_arrive(&tempty[b]);
+    }
+    if constexpr (CS) {
+      if (a.cs_part) {
+        __syncwarp();
+        float* P = a.cs_part + ((int64_t)blockIdx.x * 4 + warp) * 3 * BG_H;
+        for (int j = lane; j < 3 * BG_H; j += 32) P[j] = csm[j];
+      }
     }
   }
   tc_fence_before();
@@ -578,6 +615,11 @@ cudaError_t launch_bg(etx_ctx* ctx, BgArgs& a, const float* A, int64_t Rcap, con
 
 }  // namespace
 
+int block_bwd_tc_colsum_parts(const etx_ctx* ctx, int64_t rows_cap) {
+  const int64_t tiles = (rows_cap + BG_TM - 1) / BG_TM;
+  return 4 * (int)(tiles < ctx->n_sms ? tiles : ctx->n_sms);
+}
+
 bool block_bwd_tc_supported(const etx_ctx* ctx) {
   return ctx->cfg.hidden == BG_H && tensor_map_encoder() != nullptr;
 }
@@ -632,15 +674,18 @@ cudaError_t launch_block_bwd_tc(etx_ctx* ctx, int mode, const BlockBwdTc& p, cud
   a.b = p.b2; a.g = p.g2; a.be = p.be2;
   a.G = p.G;
   a.o0 = p.DY2; a.o1 = p.DY2N2; a.o2 = p.DA2; a.o3 = nullptr;
+  a.cs_part = p.cs2;
   if ((e = launch_bg<128, EPI_LN2, true>(ctx, a, p.R1, Rcap, p.W2n, s, p.R1_lo, p.W2n_lo)) != cudaSuccess)
     return e;
   // 4: GEMM 3 + LN1 backward
   a.g = p.g1; a.be = p.be1;
   a.N1 = p.N1; a.rs_in = p.rstd1;
   a.o0 = p.DY1; a.o1 = p.DY1N1; a.o2 = p.DA1;
+  a.cs_part = p.cs1;
   if ((e = launch_bg<128, EPI_LN1B>(ctx, a, p.DA2, Rcap, p.W2t, s)) != cudaSuccess) return e;
   // 5: GEMM 4, the input gradient
   a.o0 = p.DX; a.ldo = K;
+  a.cs_part = nullptr;
   return K == 2 * H ? launch_bg<256, EPI_STORE>(ctx, a, p.DA1, Rcap, p.W1t, s)
                     : launch_bg<384, EPI_STORE>(ctx, a, p.DA1, Rcap, p.W1t, s);
 }
