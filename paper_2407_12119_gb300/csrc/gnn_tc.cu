@@ -453,8 +453,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(const __grid_constant__ T
           if constexpr (MODE == TC_NODE_UPD || MODE == TC_CLS) {
             xs[k] = xd[k] = xo[k];
           } else {
-            xs[k] = ok ? min(max(a.src[gr], 0), max(nn - 1, 0)) : 0;
-            xd[k] = ok ? min(max(a.dst[gr], 0), max(nn - 1, 0)) : 0;
+            // raw indices: clamped where they are used, a tile later, so these
+            // loads stay in flight instead of stalling the producers here
+            xs[k] = ok ? a.src[gr] : 0;
+            xd[k] = ok ? a.dst[gr] : 0;
           }
         }
       };
@@ -496,7 +498,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_tc(const __grid_constant__ T
 #pragma unroll
           for (int k = 0; k < NG; ++k) {
             const int fi = pt + PROD_THREADS * k;
-            const int row = own ? go[k] : (hc < KH ? gs[k] : gd[k]);
+            const int row = own ? go[k] : min(max(hc < KH ? gs[k] : gd[k], 0), max(nn - 1, 0));
             if (fi < TM * 8)
               cp_async16(sA + slot * CHUNK + sw128(fi >> 3, fi & 7),
                          srcb + (int64_t)row * rowbytes + cbase + 16 * (fi & 7));
