@@ -35,7 +35,7 @@ FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA 
 # dram__bytes_read.sum + dram__bytes_write.sum per edge of one launch, from ncu
 # captures on the 50-event case (profiles/edge_update_bf16_batch500.md); to be
 # re-taken whenever the kernel changes (absent: traffic reported as null)
-MEASURED_DRAM_BYTES_PER_EDGE = {"gnn_edge_update_bf16": (603.72e6 + 514.93e6) / 1113945}
+MEASURED_DRAM_BYTES_PER_EDGE = {"gnn_edge_update_bf16": (604.46e6 + 514.99e6) / 1113945}
 
 
 def parse():
