@@ -387,7 +387,18 @@ def embedding_train_report(args, local):
     n_pairs = int(tr.pairs[3].item())
     last = last.cpu().numpy()
     tr.ctx.sync()
-    return {"workload": f"{b.n_events} events of {wl.name} without noise, {b.n_hits} hits, embedding "
+    # where a step's time goes: the library's kernels by name (CUDA events)
+    tr.ctx.profile(True)
+    tr.step(*batch)
+    torch.cuda.synchronize()
+    kern = tr.ctx.profile_read()
+    tr.ctx.profile(False)
+    tr.ctx.sync()
+    top = sorted(kern.items(), key=lambda kv: -kv[1][0])
+    breakdown = {k: round(ms, 3) for k, (ms, _) in top[:8]}
+    breakdown["other_kernels"] = round(sum(ms for _, (ms, _) in top[8:]), 3)
+    return {"breakdown_ms": breakdown,
+            "workload": f"{b.n_events} events of {wl.name} without noise, {b.n_hits} hits, embedding "
                         f"{'-'.join(map(str, m.emb_widths))}, k_max 50, d2 < 1.5, margin 1, "
                         f"w_genuine 2, Adam lr 1e-3",
             "ms_per_step": 1e3 * el / steps, "events_per_s": b.n_events * steps / el,
