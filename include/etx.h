@@ -453,7 +453,9 @@ etx_status etx_tracks_from_triplets(etx_ctx* ctx, const int32_t* src, const int3
  * activations that the last etx_embed_forward_train of the same n_hits and
  * weights left in `workspace` (the rest of the workspace is scratch).  The
  * weights are read from the context's copy of the blob.  FP32 SIMT; the
- * weight gradients accumulate with atomics (order not fixed).
+ * weight gradients and bias sums are formed as per-split partials in the
+ * workspace's tail and added in a fixed order (the same d_emb gives the same
+ * bits).
  *
  * etx_embedding_pairs: the training set T (Sec. 5.1).  For each query q (a
  * hit whose particle has at least min_hits hits in its event) on plane p,

@@ -1139,10 +1139,28 @@ int64_t embed_param_count(const etx_config& c) {
   return p;
 }
 
+// Row splits of the embedding's weight gradients and blocks of its column sums
+// (upper bounds: the partials live in the caller's workspace).
+constexpr int kEmbMaxSplits = 256, kEmbMaxColBlocks = 1024;
+
+// Largest weight-matrix and output widths of the embedding layers.
+static void embed_part_sizes(const etx_config& c, int64_t& max_mn, int64_t& max_m) {
+  max_mn = 0;
+  max_m = 0;
+  for (int l = 0; l < c.emb_depth; ++l) {
+    max_mn = std::max<int64_t>(max_mn, (int64_t)c.emb_widths[l + 1] * c.emb_widths[l]);
+    max_m = std::max<int64_t>(max_m, c.emb_widths[l + 1]);
+  }
+}
+
 size_t embed_backward_workspace(const etx_config& c, int64_t n) {
   const int64_t EW = c.emb_widths[1];
-  // saved inputs [n][4] and hidden activations [depth-1][n][EW], two gradient buffers [n][EW]
-  return (size_t)(n * 4 + (int64_t)(c.emb_depth - 1) * n * EW + 2 * n * EW) * sizeof(float);
+  int64_t max_mn, max_m;
+  embed_part_sizes(c, max_mn, max_m);
+  // saved inputs [n][4] and hidden activations [depth-1][n][EW], two gradient buffers [n][EW],
+  // and the partial sums of the weight gradients and column sums (added in a fixed order)
+  const int64_t part = std::max<int64_t>(kEmbMaxSplits * max_mn, kEmbMaxColBlocks * max_m);
+  return (size_t)(n * 4 + (int64_t)(c.emb_depth - 1) * n * EW + 2 * n * EW + part) * sizeof(float);
 }
 
 cudaError_t launch_embed_backward(etx_ctx* ctx, int64_t n, const float* saved, const float* d_emb,
@@ -1160,8 +1178,19 @@ cudaError_t launch_embed_backward(etx_ctx* ctx, int64_t n, const float* saved, c
   if (e != cudaSuccess || n == 0) return e;
   const float* Wblob = ctx->blob_dev + 12;  // embedding parameters follow the 12 normalisation values
   auto act = [&](int l) { return saved + n * 4 + (int64_t)l * n * EW; };
-  const int splits = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->n_sms, (n + 1023) / 1024));
-  const int cb = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->n_sms * 4, n));
+  const int splits = (int)std::max<int64_t>(
+      1, std::min<int64_t>({(int64_t)ctx->n_sms, (n + 1023) / 1024, (int64_t)kEmbMaxSplits}));
+  const int cb = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)ctx->n_sms * 4, n, (int64_t)kEmbMaxColBlocks}));
+  float* part = dz_b + n * EW;  // partial sums (workspace tail), added in a fixed order
+  auto reduce = [&](int parts, int64_t m, float* out) {
+    if (m <= 4096 && parts >= 64)
+      launch(ctx, "embtrain_grad_reduce", k_reduce_parts_narrow, (int)((m + 31) / 32), 256, 0, s,
+             (const float*)part, parts, m, out);
+    else
+      launch(ctx, "embtrain_grad_reduce", k_reduce_parts,
+             (int)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, ctx->n_sms * 4)), 256, 0, s,
+             (const float*)part, parts, m, out);
+  };
   const float* dz = d_emb;  // gradient at the output of layer l (before its ReLU, if any)
   for (int l = depth - 1; l >= 0; --l) {
     const int M = c.emb_widths[l + 1], n_in = c.emb_widths[l];
@@ -1169,9 +1198,11 @@ cudaError_t launch_embed_backward(etx_ctx* ctx, int64_t n, const float* saved, c
     const int ld_in = l > 0 ? EW : 4;
     launch(ctx, "embtrain_weight_grad", k_gemm_tn,
            dim3((M + kTileM - 1) / kTileM, (n_in + 127) / 128, splits), kTileThreads, 0, s, dz, M,
-           in, ld_in, M, n_in, n, (const int32_t*)nullptr, d_params + woff[l], (float*)nullptr);
+           in, ld_in, M, n_in, n, (const int32_t*)nullptr, d_params + woff[l], part);
+    reduce(splits, (int64_t)M * n_in, d_params + woff[l]);
     launch(ctx, "embtrain_colsum", k_colsum, cb, M, 0, s, dz, M, (const float*)nullptr, n,
-           (const int32_t*)nullptr, d_params + boff[l], (float*)nullptr);
+           (const int32_t*)nullptr, d_params + boff[l], part);
+    reduce(cb, M, d_params + boff[l]);
     if (l > 0) {
       float* out = dz == dz_a ? dz_b : dz_a;
       switch (EW) {
