@@ -490,6 +490,15 @@ etx_status etx_embed_forward_train(etx_ctx* ctx, const float* x, const float* y,
                                    size_t workspace_bytes, void* stream);
 etx_status etx_embed_backward(etx_ctx* ctx, int64_t n_hits, const float* d_emb, float* d_params,
                               void* workspace, size_t workspace_bytes, void* stream);
+
+/* The embedding's parameters (Sec. 5.1) replaced from a device vector theta
+ * float32 [etx_embed_param_count] in blob order (W[out][in], b[out] per layer),
+ * e.g. after an optimiser step: the context's transposed FP32 copies are
+ * rebuilt from it by one kernel and its copy of the blob updated, all on
+ * `stream` (asynchronous; no host round trip).  Later etx_embed,
+ * etx_embed_forward_train and etx_embed_backward see the new weights.
+ * ETX_ERR_STATE before etx_load_weights, ETX_ERR_ARG for a NULL vector. */
+etx_status etx_set_embed_params(etx_ctx* ctx, const float* theta, void* stream);
 size_t etx_embedding_pairs_workspace(int32_t n_events, int64_t n_hits, int32_t k_max);
 etx_status etx_embedding_pairs(etx_ctx* ctx, const float* emb, const int8_t* plane,
                                const int32_t* particle_id, const int32_t* hit_offsets,

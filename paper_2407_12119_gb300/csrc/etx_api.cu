@@ -294,6 +294,7 @@ etx_status etx_ctx_destroy(etx_ctx* ctx) {
                   ctx->de, ctx->dh, ctx->bw_X, ctx->bw_DX, ctx->bw_R1, ctx->bw_DA1, ctx->bw_DY1,
                   ctx->bw_DY1N1, ctx->bw_DA2, ctx->bw_DY2, ctx->bw_DY2N2, ctx->h_lp,
                   ctx->small, ctx->w_trip, ctx->bw_part, ctx->red_part, ctx->repack_dev,
+                  ctx->embed_repack_dev,
                   ctx->bw_N1, ctx->bw_rstd1, ctx->bw_img, ctx->bw_img_jobs, ctx->bw_Xlo,
                   ctx->bw_R1lo, ctx->bw_cs_part};
   for (void* p : bufs)
@@ -542,6 +543,21 @@ etx_status etx_load_weights(etx_ctx* ctx, const float* blob, int64_t n_floats) {
     if (e != cudaSuccess) return cuda_fail(ctx, e, "repack plan upload");
     ctx->n_repack = (int)jobs.size();
     ctx->n_theta = n_floats - gnn_offset;
+    // and of the embedding, for etx_set_embed_params (FP32 layers only)
+    std::vector<RepackJob> ejobs;
+    for (auto& q : emb) {
+      const int64_t src = (int64_t)(q.w - blob) - 12;  // the embedding follows the 12 normalisation values
+      ejobs.push_back(RepackJob{src, (int64_t)q.wt, -1, q.k_in, q.n});
+      ejobs.push_back(RepackJob{src + (int64_t)q.n * q.k_in, (int64_t)q.b, -1, 0, q.n});
+    }
+    if (ctx->embed_repack_dev) cudaFree(ctx->embed_repack_dev);
+    ctx->embed_repack_dev = nullptr;
+    if (dmalloc(ctx, &ctx->embed_repack_dev, ejobs.size(), "embedding repack plan") != ETX_OK)
+      return ETX_ERR_CUDA;
+    e = cudaMemcpy(ctx->embed_repack_dev, ejobs.data(), ejobs.size() * sizeof(RepackJob),
+                   cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "embedding repack plan upload");
+    ctx->n_embed_repack = (int)ejobs.size();
   }
   ctx->w_host_pending = false;
   ctx->f8_stale = false;
@@ -616,6 +632,23 @@ etx_status etx_set_gnn_params(etx_ctx* ctx, const float* theta, void* stream) {
   ctx->w_host_pending = true;
   ctx->f8_stale = ctx->w.has_tc;  // the e4m3 images keep the loaded weights
   ctx->fwd_saved = false;
+  return ETX_OK;
+}
+
+etx_status etx_set_embed_params(etx_ctx* ctx, const float* theta, void* stream) {
+  if (!ctx) return ETX_ERR_ARG;
+  if (!ctx->weights_loaded || !ctx->embed_repack_dev) return fail(ctx, ETX_ERR_STATE, "weights not loaded");
+  if (!theta) return fail(ctx, ETX_ERR_ARG, "parameter vector is NULL");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  launch(ctx, "weights_repack", k_repack, dim3(32, ctx->n_embed_repack), 256, 0, s, theta,
+         (const RepackJob*)ctx->embed_repack_dev, ctx->w_dev, (uint8_t*)nullptr);
+  // the reverse pass reads the weights in blob order
+  cudaError_t e = cudaMemcpyAsync(ctx->blob_dev + 12, theta,
+                                  (size_t)embed_param_count(ctx->cfg) * sizeof(float),
+                                  cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "etx_set_embed_params");
   return ETX_OK;
 }
 

@@ -157,6 +157,8 @@ struct etx_ctx {
   float* bw_part = nullptr;
   // tensor-core block backward (H = 128): n1 rows, rstd1, TF32 weight images and
   // the job list that refreshes them (filled at the first backward)
+  etx::RepackJob* embed_repack_dev = nullptr;  // the embedding's repack plan (etx_set_embed_params)
+  int n_embed_repack = 0;
   float* bw_N1 = nullptr;
   float* bw_Xlo = nullptr;   // low parts of the block inputs [R][3H] and of R1 [R][H]
   float* bw_R1lo = nullptr;

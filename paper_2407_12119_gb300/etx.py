@@ -38,7 +38,7 @@ EXPORTED = ["etx_ctx_create", "etx_ctx_destroy", "etx_last_error", "etx_weights_
             "etx_triplet_weights_size", "etx_load_triplet_weights", "etx_triplets_workspace",
             "etx_build_triplets", "etx_classify_triplets", "etx_fp8_scale_count",
             "etx_set_fp8_scales", "etx_tracks_workspace", "etx_tracks_from_triplets",
-            "etx_set_gnn_params", "etx_gnn_checkpoints"]
+            "etx_set_gnn_params", "etx_gnn_checkpoints", "etx_set_embed_params"]
 # etx_track_metrics outputs
 TRACK_COUNTS = ["particles", "matched_particles", "candidates", "candidate_particles", "tracks",
                 "unmatched_tracks"]
@@ -130,6 +130,7 @@ def lib() -> ctypes.CDLL:
         "etx_fp8_scale_count": (i64, [cfgp]),
         "etx_set_gnn_params": (i32, [vp, vp, vp]),
         "etx_gnn_checkpoints": (i32, [vp, i32, vp, vp, vp]),
+        "etx_set_embed_params": (i32, [vp, vp, vp]),
         "etx_set_fp8_scales": (i32, [vp, vp, i64]),
         "etx_launch_count": (i64, [vp]),
         "etx_profile_enable": (i32, [vp, i32]),
@@ -269,6 +270,14 @@ class Context:
         if theta.numel() != self.gnn_param_count:
             raise ValueError("theta must hold gnn_param_count values")
         self._check(lib().etx_set_gnn_params(self._h, _ptr(theta), _stream(stream)))
+
+    def set_embed_params(self, theta, stream=None):
+        """etx_set_embed_params: the embedding parameters from a device float32
+        vector (blob order), repacked on the device."""
+        _need(theta, torch.float32, "theta", self.device)
+        if theta.numel() != self.embed_param_count:
+            raise ValueError("theta must hold embed_param_count values")
+        self._check(lib().etx_set_embed_params(self._h, _ptr(theta), _stream(stream)))
 
     def gnn_checkpoints(self, k: int, n_hits: int, n_edges: int, stream=None):
         """etx_gnn_checkpoints: (h^k [n_hits][H], e^k [n_edges][H]) that the last

@@ -90,10 +90,10 @@ class EmbeddingTrainer:
                  margin: float = 1.0, w_genuine: float = 2.0, seed: int = 0):
         self.ctx = Context(model, max_events, max_hits, 1, device=device)
         dev = self.ctx.device
-        self.blob = np.array(blob, dtype=np.float32, copy=True)
+        self._blob = np.array(blob, dtype=np.float32, copy=True)
         self.n_theta = self.ctx.embed_param_count
         o = self.EMB_OFFSET
-        self.theta = torch.from_numpy(self.blob[o:o + self.n_theta].copy()).to(dev)
+        self.theta = torch.from_numpy(self._blob[o:o + self.n_theta].copy()).to(dev)
         self.m = torch.zeros_like(self.theta)
         self.v = torch.zeros_like(self.theta)
         self.lr, self.radius, self.k_max = lr, radius, k_max
@@ -111,13 +111,23 @@ class EmbeddingTrainer:
         self.gen = torch.Generator(device=dev)
         self.gen.manual_seed(seed)
         self.loss = torch.empty(3, dtype=torch.float32, device=dev)
-        self.ctx.load_weights(self.blob)
+        self.ctx.load_weights(self._blob)
 
     def sync(self):
-        """Load the current embedding parameters into the context."""
+        """Load the current embedding parameters into the context from the host
+        (the steps update the context on the device: etx_set_embed_params)."""
+        self.ctx.load_weights(self.current_blob())
+
+    def current_blob(self) -> np.ndarray:
+        """The weight blob with the current embedding parameters (host copy)."""
         o = self.EMB_OFFSET
-        self.blob[o:o + self.n_theta] = self.theta.detach().cpu().numpy()
-        self.ctx.load_weights(self.blob)
+        self._blob[o:o + self.n_theta] = self.theta.detach().cpu().numpy()
+        return self._blob
+
+    @property
+    def blob(self) -> np.ndarray:
+        """The weight blob with the current (trained) embedding parameters."""
+        return self.current_blob()
 
     def step(self, x, y, z, plane, particle_id, hit_offsets):
         """One step; returns the loss tensor {L, L_genuine, L_fake} of the
@@ -134,5 +144,5 @@ class EmbeddingTrainer:
         grads = self.ctx.embed_backward(self.d_emb[:n], self.ws)
         self.t += 1
         self.ctx.adam_step(self.theta, grads, self.m, self.v, self.t, lr=self.lr)
-        self.sync()
+        self.ctx.set_embed_params(self.theta)  # on the device: no host round trip
         return self.loss

@@ -196,3 +196,29 @@ def test_embedding_training_reduces_the_loss(etx):
     tr.ctx.sync()
     print("embedding training: loss", first, "->", last)
     assert last[0] < 0.8 * first[0]
+
+
+def test_device_embed_update_equals_a_reload(etx):
+    """etx_set_embed_params with a device vector gives the same embedding and the
+    same reverse pass as loading a blob that holds the same parameters."""
+    rng = np.random.default_rng(9)
+    wl = WORKLOADS["batch500"]
+    m = wl.model
+    b = drop_noise(wl.batch(3))
+    blob = pack_blob(m, wl.weights(perturb=0.2))
+    ctx = etx.Context(m, b.n_events, b.n_hits, 1)
+    ctx.load_weights(blob)
+    n_theta = ctx.embed_param_count
+    theta = blob[12:12 + n_theta] + rng.normal(scale=0.05, size=n_theta).astype(np.float32)
+    ctx.set_embed_params(cuda(theta.astype(np.float32)))
+    blob2 = blob.copy()
+    blob2[12:12 + n_theta] = theta
+    ref = etx.Context(m, b.n_events, b.n_hits, 1)
+    ref.load_weights(blob2)
+    x, y, z = cuda(b.x), cuda(b.y), cuda(b.z)
+    assert torch.equal(ctx.embed(x, y, z), ref.embed(x, y, z))
+    up = cuda(rng.normal(size=(b.n_hits, m.emb_widths[-1])).astype(np.float32))
+    ws1, ws2 = ctx.embed_train_workspace(b.n_hits), ref.embed_train_workspace(b.n_hits)
+    e1, e2 = ctx.embed_forward_train(x, y, z, ws1), ref.embed_forward_train(x, y, z, ws2)
+    assert torch.equal(e1, e2)
+    assert torch.equal(ctx.embed_backward(up, ws1), ref.embed_backward(up, ws2))
