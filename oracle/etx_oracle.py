@@ -377,6 +377,29 @@ def weighted_bce(logits, target, pos_weight=10.0):
     return loss, dz
 
 
+def focal_loss(logits, target, alpha=0.25, gamma=2.0):
+    """Sigmoid focal loss, the edge loss the paper trains with (Sec. 5.2, Eq. 5;
+    the form of its reference, Lin et al. 2017): mean over edges of
+    y alpha (1 - p)^gamma (-log p) + (1 - y) (1 - alpha) p^gamma (-log(1 - p)),
+    p = sigmoid(z); and d loss / d z, differentiated by hand:
+    y alpha (1 - p)^gamma (gamma p log p - (1 - p))
+    + (1 - y) (1 - alpha) p^gamma (p - gamma (1 - p) log(1 - p)), over E.
+    Reading: the paper gives neither alpha nor gamma; the reference's values
+    alpha = 0.25, gamma = 2 are the defaults."""
+    z = np.asarray(logits, np.float64)
+    yv = np.asarray(target, np.float64)
+    E = max(z.shape[0], 1)
+    p, q = sigmoid(z), sigmoid(-z)   # p and 1 - p, each without cancellation
+    lp, lq = -softplus(-z), -softplus(z)   # log p, log(1 - p)
+    l1 = -alpha * q ** gamma * lp
+    l0 = -(1.0 - alpha) * p ** gamma * lq
+    loss = float(np.sum(yv * l1 + (1.0 - yv) * l0) / E)
+    d1 = alpha * q ** gamma * (gamma * p * lp - q)
+    d0 = (1.0 - alpha) * p ** gamma * (p - gamma * q * lq)
+    dz = (yv * d1 + (1.0 - yv) * d0) / E
+    return loss, dz
+
+
 def _ln_backward(dy, n, rstd, g):
     """LayerNorm backward: returns (d input, d gamma, d beta)."""
     dn = dy * g

@@ -1036,3 +1036,33 @@ def test_forward_cache_from_streams_matches_the_forward():
         g1 = O.gnn_backward(W, r, dz, recompute=True)
         for k in g0:
             np.testing.assert_array_equal(g1[k], g0[k])
+
+
+def test_focal_loss_pins():
+    """The sigmoid focal loss (Sec. 5.2, Eq. 5): gamma = 0 with alpha = 1/2 is
+    half the plain binary cross-entropy (pinned separately against torch);
+    hand values at z = 0 (p = 1/2: alpha / 4 ln 2 and (1 - alpha) / 4 ln 2);
+    its gradient against central differences; an edge classified with a large
+    margin costs next to nothing."""
+    rng = np.random.default_rng(3)
+    z = rng.normal(scale=3.0, size=200)
+    y = (rng.random(200) < 0.3).astype(np.float64)
+    lb, db = O.weighted_bce(z, y, 1.0)
+    lf, df = O.focal_loss(z, y, alpha=0.5, gamma=0.0)
+    assert abs(lf - 0.5 * lb) <= 1e-12 * abs(lb)
+    np.testing.assert_allclose(df, 0.5 * db, rtol=1e-12, atol=1e-15)
+    l, d = O.focal_loss(np.zeros(2), np.array([1.0, 0.0]))
+    ln2 = np.log(2.0)
+    assert abs(l - 0.5 * (0.25 * 0.25 * ln2 + 0.75 * 0.25 * ln2)) <= 1e-15
+    # at z = 0 (p = 1/2, gamma = 2): d/dz for y = 1 is 0.25 * 0.25 * (2 * 0.5 * -ln2 - 0.5) / 2
+    assert abs(d[0] - 0.25 * 0.25 * (-ln2 - 0.5) / 2) <= 1e-15
+    h = 1e-6
+    for i in rng.choice(200, size=12, replace=False):
+        zp, zm = z.copy(), z.copy()
+        zp[i] += h
+        zm[i] -= h
+        fd = (O.focal_loss(zp, y)[0] - O.focal_loss(zm, y)[0]) / (2 * h)
+        # central differences carry ~eps * loss / h = 2e-11 of rounding
+        assert abs(O.focal_loss(z, y)[1][i] - fd) <= 1e-5 * abs(fd) + 1e-10
+    big, _ = O.focal_loss(np.array([20.0, -20.0]), np.array([1.0, 0.0]))
+    assert 0.0 < big < 1e-20
