@@ -225,7 +225,9 @@ etx_status etx_set_fp8_scales(etx_ctx* ctx, const float* host_scales, int64_t n)
  * that the forward built; etx_build_graph (single-pass k-NN),
  * etx_build_triplets and etx_edges_to_tracks_sweep reuse that scratch, so
  * after one of them on this context the backward returns ETX_ERR_STATE until
- * the next training forward.
+ * the next training forward.  The forward's input arrays (x, y, z, src, dst)
+ * are read again by the backward: they must stay allocated and unchanged until
+ * it has run (the caller owns them; the context keeps only their addresses).
  */
 int64_t etx_gnn_param_count(const etx_config* cfg);
 etx_status etx_gnn_backward(etx_ctx* ctx, const float* dlogits, float* dparams, void* stream);
@@ -252,6 +254,20 @@ etx_status etx_gnn_checkpoints(etx_ctx* ctx, int32_t k, float* h_out, float* e_o
 etx_status etx_weighted_bce(etx_ctx* ctx, const float* logits, const float* targets,
                             const int32_t* edge_offsets, int32_t n_events, float pos_weight,
                             float* loss, float* dlogits, void* stream);
+
+/*
+ * The paper's own edge loss (Sec. 5.2, Eq. 5): the sigmoid focal loss of its
+ * reference (Lin et al. 2017), p = sigmoid(z),
+ *     loss = mean_e [ y alpha (1 - p)^gamma (-log p)
+ *                     + (1 - y) (1 - alpha) p^gamma (-log(1 - p)) ]
+ * (the paper gives no alpha or gamma; 0.25 and 2 are the reference's
+ * defaults).  Arguments, layouts and errors as etx_weighted_bce; alpha in
+ * [0, 1], gamma >= 0, else ETX_ERR_ARG.  The loss is summed per block and the
+ * block sums added in a fixed order.
+ */
+etx_status etx_focal_loss(etx_ctx* ctx, const float* logits, const float* targets,
+                          const int32_t* edge_offsets, int32_t n_events, float alpha, float gamma,
+                          float* loss, float* dlogits, void* stream);
 
 /*
  * One Adam update (Kingma & Ba) of n float32 parameters in place, with

@@ -818,6 +818,23 @@ etx_status etx_weighted_bce(etx_ctx* ctx, const float* logits, const float* targ
   return ETX_OK;
 }
 
+etx_status etx_focal_loss(etx_ctx* ctx, const float* logits, const float* targets,
+                          const int32_t* edge_offsets, int32_t n_events, float alpha, float gamma,
+                          float* loss, float* dlogits, void* stream) {
+  if (!ctx) return ETX_ERR_ARG;
+  if (!logits || !targets || !edge_offsets || !loss || !dlogits) return fail(ctx, ETX_ERR_ARG, "NULL array");
+  if (n_events < 0 || n_events > ctx->cfg.max_events) return fail(ctx, ETX_ERR_CAPACITY, "n_events exceeds the context capacity");
+  if (!(alpha >= 0.f && alpha <= 1.f) || !(gamma >= 0.f) || gamma > 1e6f)
+    return fail(ctx, ETX_ERR_ARG, "alpha must lie in [0, 1] and gamma be >= 0");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  launch(ctx, "clamp_edges", k_clamp_edges, 1, 1, 0, s, edge_offsets, n_events, ctx->cfg.max_edges,
+         ctx->n_edges, ctx->d_err);
+  cudaError_t e = launch_focal_loss(ctx, logits, targets, ctx->n_edges, alpha, gamma, loss, dlogits, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "etx_focal_loss launch");
+  return ETX_OK;
+}
+
 etx_status etx_adam_step(etx_ctx* ctx, float* params, const float* grads, float* m, float* v,
                          int64_t n, float lr, float beta1, float beta2, float eps, int64_t step,
                          void* stream) {

@@ -232,6 +232,9 @@ cudaError_t launch_gnn_backward(etx_ctx* ctx, const float* dlogits, float* dpara
 cudaError_t launch_weighted_bce(etx_ctx* ctx, const float* logits, const float* targets,
                                 const int32_t* n_edges_dev, float pos_weight, float* loss,
                                 float* dlogits, cudaStream_t s);
+cudaError_t launch_focal_loss(etx_ctx* ctx, const float* logits, const float* targets,
+                              const int32_t* n_edges_dev, float alpha, float gamma, float* loss,
+                              float* dlogits, cudaStream_t s);
 cudaError_t launch_adam(etx_ctx* ctx, float* p, const float* g, float* m, float* v, int64_t n,
                         float lr, float b1, float b2, float eps, int64_t step, cudaStream_t s);
 

@@ -1029,6 +1029,34 @@ __global__ void k_weighted_bce(const float* __restrict__ z, const float* __restr
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
+// The sigmoid focal loss (Sec. 5.2, Eq. 5; the form of Lin et al. 2017): per
+// block sums of the loss terms and dz = d loss / d z over E, written directly.
+// p and 1 - p are formed separately (no cancellation), log p = -softplus(-z),
+// log(1 - p) = -softplus(z).
+__global__ void k_focal(const float* __restrict__ z, const float* __restrict__ y,
+                        const int32_t* __restrict__ n_edges_dev, float alpha, float gamma,
+                        float* __restrict__ part, float* __restrict__ dz) {
+  __shared__ float sh[32];
+  const int64_t E = *n_edges_dev;
+  const float inv = E > 0 ? 1.0f / (float)E : 0.f;
+  float acc = 0.f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < E;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float zi = z[i], yi = y[i];
+    const float sp_pos = fmaxf(zi, 0.f) + log1pf(expf(-fabsf(zi)));  // softplus(z)
+    const float sp_neg = sp_pos - zi;                                 // softplus(-z)
+    const float p = 1.0f / (1.0f + expf(-zi)), q = 1.0f / (1.0f + expf(zi));
+    const float lp = -sp_neg, lq = -sp_pos;                           // log p, log(1 - p)
+    const float qg = powf(q, gamma), pg = powf(p, gamma);
+    acc += yi * (-alpha * qg * lp) + (1.0f - yi) * (-(1.0f - alpha) * pg * lq);
+    const float d1 = alpha * qg * (gamma * p * lp - q);
+    const float d0 = (1.0f - alpha) * pg * (p - gamma * q * lq);
+    dz[i] = inv * (yi * d1 + (1.0f - yi) * d0);
+  }
+  const float t = block_sum_fixed(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
 __global__ void k_bce_mean(const float* __restrict__ part, int n, const int32_t* __restrict__ n_edges_dev,
                            float* __restrict__ loss) {
   __shared__ float sh[32];
@@ -1062,6 +1090,17 @@ cudaError_t launch_weighted_bce(etx_ctx* ctx, const float* logits, const float* 
   if (g > (int)ctx->red_part_n) g = (int)ctx->red_part_n;
   launch(ctx, "loss_weighted_bce", k_weighted_bce, g, 256, 0, s, logits, targets, n_edges_dev,
          pos_weight, ctx->red_part, dlogits);
+  launch(ctx, "loss_mean", k_bce_mean, 1, 256, 0, s, (const float*)ctx->red_part, g, n_edges_dev, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_focal_loss(etx_ctx* ctx, const float* logits, const float* targets,
+                              const int32_t* n_edges_dev, float alpha, float gamma, float* loss,
+                              float* dlogits, cudaStream_t s) {
+  int g = grid_for(ctx, (const void*)k_focal, 256, 0, (ctx->cfg.max_edges + 255) / 256);
+  if (g > (int)ctx->red_part_n) g = (int)ctx->red_part_n;
+  launch(ctx, "loss_focal", k_focal, g, 256, 0, s, logits, targets, n_edges_dev, alpha, gamma,
+         ctx->red_part, dlogits);
   launch(ctx, "loss_mean", k_bce_mean, 1, 256, 0, s, (const float*)ctx->red_part, g, n_edges_dev, loss);
   return cudaGetLastError();
 }

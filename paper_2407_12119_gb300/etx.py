@@ -38,7 +38,7 @@ EXPORTED = ["etx_ctx_create", "etx_ctx_destroy", "etx_last_error", "etx_weights_
             "etx_triplet_weights_size", "etx_load_triplet_weights", "etx_triplets_workspace",
             "etx_build_triplets", "etx_classify_triplets", "etx_fp8_scale_count",
             "etx_set_fp8_scales", "etx_tracks_workspace", "etx_tracks_from_triplets",
-            "etx_set_gnn_params", "etx_gnn_checkpoints", "etx_set_embed_params"]
+            "etx_set_gnn_params", "etx_gnn_checkpoints", "etx_set_embed_params", "etx_focal_loss"]
 # etx_track_metrics outputs
 TRACK_COUNTS = ["particles", "matched_particles", "candidates", "candidate_particles", "tracks",
                 "unmatched_tracks"]
@@ -131,6 +131,7 @@ def lib() -> ctypes.CDLL:
         "etx_set_gnn_params": (i32, [vp, vp, vp]),
         "etx_gnn_checkpoints": (i32, [vp, i32, vp, vp, vp]),
         "etx_set_embed_params": (i32, [vp, vp, vp]),
+        "etx_focal_loss": (i32, [vp, vp, vp, vp, i32, ctypes.c_float, ctypes.c_float, vp, vp, vp]),
         "etx_set_fp8_scales": (i32, [vp, vp, i64]),
         "etx_launch_count": (i64, [vp]),
         "etx_profile_enable": (i32, [vp, i32]),
@@ -649,6 +650,20 @@ class Context:
         self._check(lib().etx_weighted_bce(self._h, _ptr(logits), _ptr(targets), _ptr(edge_offsets),
                                            edge_offsets.shape[0] - 1, float(pos_weight), _ptr(loss),
                                            _ptr(dlogits), _stream(stream)))
+        return loss, dlogits
+
+    def focal_loss(self, logits, targets, edge_offsets, alpha: float = 0.25, gamma: float = 2.0,
+                   stream=None):
+        """(loss [1], dlogits [len(logits)]) of the sigmoid focal loss (Eq. 5)."""
+        dev = self.device
+        _need(logits, torch.float32, "logits", dev)
+        _need(targets, torch.float32, "targets", dev)
+        _need(edge_offsets, torch.int32, "edge_offsets", dev)
+        loss = torch.empty(1, dtype=torch.float32, device=dev)
+        dlogits = torch.zeros_like(logits)
+        self._check(lib().etx_focal_loss(self._h, _ptr(logits), _ptr(targets), _ptr(edge_offsets),
+                                         edge_offsets.shape[0] - 1, float(alpha), float(gamma),
+                                         _ptr(loss), _ptr(dlogits), _stream(stream)))
         return loss, dlogits
 
     def adam_step(self, params, grads, m, v, step: int, lr: float = 1e-3, beta1: float = 0.9,

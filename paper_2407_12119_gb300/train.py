@@ -22,6 +22,8 @@ class InteractionNetworkFn(torch.autograd.Function):
     def forward(fctx, theta, etx_ctx: Context, x, y, z, src, dst, edge_offsets, dtype: str):
         logits = etx_ctx.gnn_forward(x, y, z, src, dst, edge_offsets, dtype=dtype)
         fctx.etx_ctx = etx_ctx
+        # the library's backward reads these again: keep them alive until then
+        fctx.inputs = (x, y, z, src, dst, edge_offsets)
         return logits
 
     @staticmethod
@@ -31,10 +33,16 @@ class InteractionNetworkFn(torch.autograd.Function):
 
 
 class Trainer:
-    """Owns a training context, the parameters and the Adam state."""
+    """Owns a training context, the parameters and the Adam state.  The edge
+    loss is the class-weighted BCE (``loss="bce"``, ``pos_weight``) or the
+    paper's sigmoid focal loss (``loss="focal"``, ``alpha``, ``gamma``)."""
 
     def __init__(self, model, blob: np.ndarray, max_events: int, max_hits: int, max_edges: int,
-                 device: int = 0, dtype: str = "bf16", lr: float = 1e-3, pos_weight: float = 10.0):
+                 device: int = 0, dtype: str = "bf16", lr: float = 1e-3, pos_weight: float = 10.0,
+                 loss: str = "bce", alpha: float = 0.25, gamma: float = 2.0):
+        if loss not in ("bce", "focal"):
+            raise ValueError("loss must be 'bce' or 'focal'")
+        self.loss_kind, self.alpha, self.gamma = loss, alpha, gamma
         self.ctx = Context(model, max_events, max_hits, max_edges, device=device, train=True)
         self._blob = np.array(blob, dtype=np.float32, copy=True)
         self.n_theta = self.ctx.gnn_param_count
@@ -64,7 +72,10 @@ class Trainer:
         (``set_gnn_params``); ``reload=False`` leaves the context's weights at
         their old values (for timing; call ``sync`` before the next step)."""
         logits = self.ctx.gnn_forward(x, y, z, src, dst, edge_offsets, dtype=self.dtype)
-        loss, dlogits = self.ctx.weighted_bce(logits, targets, edge_offsets, self.pos_weight)
+        if self.loss_kind == "focal":
+            loss, dlogits = self.ctx.focal_loss(logits, targets, edge_offsets, self.alpha, self.gamma)
+        else:
+            loss, dlogits = self.ctx.weighted_bce(logits, targets, edge_offsets, self.pos_weight)
         grads = self.ctx.gnn_backward(dlogits)
         self.t += 1
         self.ctx.adam_step(self.theta, grads, self.m, self.v, self.t, lr=self.lr)

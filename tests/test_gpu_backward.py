@@ -299,3 +299,53 @@ def test_backward_with_no_edges(etx):
     _, g, _ = gpu_grads(etx, cfg, b, W, s0, s0, eo0, np.zeros(1))
     for n, v in g.items():
         assert np.all(np.isfinite(v)) and not np.any(v), n
+
+
+@pytest.mark.parametrize("alpha,gamma", [(0.25, 2.0), (0.5, 0.0), (0.9, 1.5)])
+def test_focal_loss_matches_oracle(etx, alpha, gamma):
+    """The sigmoid focal loss (Eq. 5) on the GPU: loss and d loss / d logit
+    against the FP64 oracle on the logits the GPU computed (stage-isolated)."""
+    cfg, b, W, s, d, eo, y = problem(32, 2, 2, seed=6)
+    ctx = etx.Context(cfg, b.n_events, b.n_hits, max(s.size, 1), train=True)
+    ctx.load_weights(pack_blob(cfg, W))
+    eot = cuda(eo.astype(np.int32))
+    logits = ctx.gnn_forward(cuda(b.x), cuda(b.y), cuda(b.z), cuda(s.astype(np.int32)),
+                             cuda(d.astype(np.int32)), eot)
+    loss, dl = ctx.focal_loss(logits, cuda(y.astype(np.float32)), eot, alpha, gamma)
+    ctx.sync()
+    z = logits.cpu().numpy().astype(np.float64)
+    lr, dr = O.focal_loss(z, y, alpha=alpha, gamma=gamma)
+    assert abs(float(loss.item()) - lr) <= 1e-5 * max(abs(lr), 1e-12)
+    got = dl.cpu().numpy().astype(np.float64)
+    assert np.abs(got - dr).max() <= 1e-5 * np.abs(dr).max() + 1e-12
+
+
+def test_training_with_the_focal_loss(etx):
+    """A few training steps with the focal loss lower it, and the gradient of
+    one step matches the oracle's reverse pass of the focal loss."""
+    cfg, b, W, s, d, eo, y = problem(128, 2, 2, seed=7)
+    cache = {}
+    z = O.gnn_forward(W, cfg.n_iters, b.x, b.y, b.z, s, d, cache)
+    _, dz = O.focal_loss(z, y)
+    ref = O.gnn_backward(W, cache, dz)
+    ctx = etx.Context(cfg, b.n_events, b.n_hits, max(s.size, 1), train=True)
+    ctx.load_weights(pack_blob(cfg, W))
+    # the forward's inputs stay alive until the backward (it reads them again)
+    x, yy, zz = cuda(b.x), cuda(b.y), cuda(b.z)
+    st, dt, eot = cuda(s.astype(np.int32)), cuda(d.astype(np.int32)), cuda(eo.astype(np.int32))
+    logits = ctx.gnn_forward(x, yy, zz, st, dt, eot)
+    _, dl = ctx.focal_loss(logits, cuda(y.astype(np.float32)), eot)
+    flat = ctx.gnn_backward(dl).cpu().numpy().astype(np.float64)
+    shapes = dict(blob_layout(cfg))
+    o, worst = 0, (0.0, "")
+    for n in gnn_names(cfg):
+        k = int(np.prod(shapes[n]))
+        worst = max(worst, (rel(flat[o:o + k].reshape(shapes[n]), ref[n]), n))
+        o += k
+    assert worst[0] <= GRAD_RTOL, worst
+    from paper_2407_12119_gb300.train import Trainer
+    tr = Trainer(cfg, pack_blob(cfg, W), b.n_events, b.n_hits, max(s.size, 1), dtype="f32",
+                 lr=1e-3, loss="focal")
+    args = (x, yy, zz, st, dt, eot, cuda(y.astype(np.float32)))
+    losses = [float(tr.step(*args).item()) for _ in range(8)]
+    assert losses[-1] < losses[0], losses
