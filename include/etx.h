@@ -221,7 +221,13 @@ etx_status etx_set_fp8_scales(etx_ctx* ctx, const float* host_scales, int64_t n)
  * the blob's interaction-network order, starting at the node encoder (the
  * normalisation and embedding entries are not part of it); its length is
  * etx_gnn_param_count(cfg).  Message-passing steps are recomputed from the
- * kept per-step encodings (checkpointing).  The pass reads the edge index
+ * kept per-step encodings (checkpointing).  Arithmetic: for hidden width 128
+ * the edge encoder, node and edge updates run on the tensor cores in TF32 (the
+ * recomputed forward products split into high and low TF32 parts, within FP32
+ * rounding of the exact products; the input-gradient products single TF32)
+ * and every weight gradient in TF32 with FP32 accumulation; the node encoder,
+ * the classifier and other widths use FP32 SIMT.  Every sum is formed in a
+ * fixed order: the same inputs give the same bits.  The pass reads the edge index
  * that the forward built; etx_build_graph (single-pass k-NN),
  * etx_build_triplets and etx_edges_to_tracks_sweep reuse that scratch, so
  * after one of them on this context the backward returns ETX_ERR_STATE until
