@@ -10,6 +10,7 @@
 // All edge-row kernels read the edge count from device memory and walk their
 // tiles with a persistent grid-stride loop, so no host synchronisation is
 // needed between the graph build and the network.
+#include <climits>
 #include "simt_tile.cuh"
 
 namespace etx {
@@ -87,20 +88,48 @@ __global__ void k_in_fill(const int32_t* __restrict__ dst, const int32_t* __rest
   }
 }
 
-// Sort each dst segment by edge id (insertion sort; segments are short).
-__global__ void k_in_sort(const int32_t* __restrict__ in_off, int n_hits, int32_t* __restrict__ perm) {
-  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < n_hits;
-       l += (int64_t)gridDim.x * blockDim.x) {
-    const int a = in_off[l], b = in_off[l + 1];
-    for (int i = a + 1; i < b; ++i) {
-      const int v = perm[i];
-      int j = i - 1;
-      while (j >= a && perm[j] > v) {
-        perm[j + 1] = perm[j];
-        --j;
+// Sort each dst segment by edge id: by ranks, a warp per segment: each lane holds
+// up to two of its edge ids, counts the smaller ones over the segment by
+// shuffles and writes its ids to their ranks (ids are distinct, so the ranks
+// are a permutation); one load and one store per id.  Longer segments (above
+// 64) are insertion-sorted by one lane.
+__global__ void k_in_sort_warp(const int32_t* __restrict__ in_off, int n_hits, int32_t* __restrict__ perm) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t l = w0; l < n_hits; l += nw) {
+    const int a = in_off[l], b = in_off[l + 1], d = b - a;
+    if (d <= 1) continue;
+    if (d <= 64) {
+      const int v0 = lane < d ? perm[a + lane] : INT_MAX;
+      const int v1 = lane + 32 < d ? perm[a + 32 + lane] : INT_MAX;
+      int r0 = 0, r1 = 0;
+      const int d0 = d < 32 ? d : 32;
+      for (int j = 0; j < d0; ++j) {
+        const int u = __shfl_sync(0xffffffffu, v0, j);
+        r0 += u < v0;
+        r1 += u < v1;
       }
-      perm[j + 1] = v;
+      for (int j = 32; j < d; ++j) {
+        const int u = __shfl_sync(0xffffffffu, v1, j - 32);
+        r0 += u < v0;
+        r1 += u < v1;
+      }
+      __syncwarp();  // every lane has read its ids before any is written back
+      if (lane < d) perm[a + r0] = v0;
+      if (lane + 32 < d) perm[a + r1] = v1;
+    } else if (lane == 0) {
+      for (int i = a + 1; i < b; ++i) {
+        const int v = perm[i];
+        int j = i - 1;
+        while (j >= a && perm[j] > v) {
+          perm[j + 1] = perm[j];
+          --j;
+        }
+        perm[j + 1] = v;
+      }
     }
+    __syncwarp();
   }
 }
 
@@ -469,8 +498,8 @@ cudaError_t launch_edge_index(etx_ctx* ctx, int64_t N, const int32_t* src, const
   if ((e = cudaMemsetAsync(ctx->in_cnt, 0, (N + 1) * sizeof(int32_t), s)) != cudaSuccess) return e;
   launch(ctx, "index_in_fill", k_in_fill, ge, 256, 0, s, dst, n_edges_dev, (int)N, ctx->in_off,
          ctx->in_cnt, ctx->perm_in);
-  const int gn = grid_for(ctx, (const void*)k_in_sort, 256, 0, (N + 255) / 256);
-  if (N > 0) launch(ctx, "index_in_sort", k_in_sort, gn, 256, 0, s, ctx->in_off, (int)N, ctx->perm_in);
+  const int gn = grid_for(ctx, (const void*)k_in_sort_warp, 256, 0, (N + 7) / 8);  // a warp per hit
+  if (N > 0) launch(ctx, "index_in_sort", k_in_sort_warp, gn, 256, 0, s, ctx->in_off, (int)N, ctx->perm_in);
   return cudaGetLastError();
 }
 
