@@ -410,8 +410,9 @@ def pileup_report(args, local, knobs: dict) -> dict:
     """The 1,000-event 4x pile-up workload (BF16, 8 message-passing steps):
     the whole step captured in one CUDA graph and replayed, with per-batch
     latency percentiles, edges/s, and the HBM rate of the step's algorithmic
-    bytes; the launch configuration is the one tuned on the 500-event batch
-    (same model shapes)."""
+    bytes; the tensor-core launch configuration is the one tuned on the
+    500-event batch (same model shapes), the k-NN's is tuned on this batch
+    (its larger planes want a larger candidate stage)."""
     import torch
 
     from paper_2407_12119_gb300.pipeline import TrackFinder
@@ -426,6 +427,10 @@ def pileup_report(args, local, knobs: dict) -> dict:
     dev = tf.dev
     d = [torch.from_numpy(np.ascontiguousarray(a)).to(dev)
          for a in (batch.x, batch.y, batch.z, batch.plane, batch.hit_offsets)]
+    # the k-NN knobs on this batch (an FP32 tuning run times only embedding and graph)
+    knn = tf.ctx.autotune(*d, m.radius, m.k_max, tf.emb[:N], tf.src, tf.dst, tf.eoff[:B + 1],
+                          tf.logits, dtype="f32")
+    knobs = dict(knobs, **{k: v for k, v in knn.items() if k.startswith("knn_")})
     stream = torch.cuda.current_stream()
     # one eager step with per-kernel timing (for the kernel rates), then the graph
     tf.ctx.profile(True)
@@ -467,6 +472,9 @@ def pileup_report(args, local, knobs: dict) -> dict:
         gbs = kernel_work("gnn_edge_update_bf16", m.hidden, E, N, m.emb_dim, m.emb_widths)[1] / (eu_ms / 1e3) / 1e9
         out["edge_update"] = {"ms_per_launch": eu_ms, "gbs": gbs,
                               "frac_of_measured_hbm": gbs / peaks.get("hbm_gbs", 6800.0)}
+    out["knn"] = {"ms_per_launch": prof["graph_knn_slots"][0] / prof["graph_knn_slots"][1],
+                  "knn_split": knobs.get("knn_split"), "knn_stage": knobs.get("knn_stage")} \
+        if "graph_knn_slots" in prof else None
     del tf
     torch.cuda.empty_cache()
     return out
@@ -672,7 +680,7 @@ def run_ours(args):
     E = int(tf.eoff[B].item())
     # launch configurations timed on this batch by the library's autotuner
     tuned_all = tf.autotune(dx, dy, dz, dp, do, N, B)
-    tuned = {k: v for k, v in tuned_all.items() if k == "knn_split" or k.endswith("/" + args.dtype)}
+    tuned = {k: v for k, v in tuned_all.items() if k.startswith("knn_") or k.endswith("/" + args.dtype)}
 
     # ---- eager launches with per-kernel CUDA events (the kernel profile) ----
     tf.ctx.profile(True)
@@ -933,7 +941,7 @@ def run_ours(args):
     # the 1,000-event pile-up workload, with the launch configuration tuned above
     pileup = None
     if not args.skip_pileup and args.events is None:
-        knobs = {k: v for k, v in tuned_all.items() if k == "knn_split" or k.endswith("/bf16")}
+        knobs = {k: v for k, v in tuned_all.items() if k.endswith("/bf16")}
         del tf
         torch.cuda.empty_cache()
         pileup = pileup_report(args, local, knobs)

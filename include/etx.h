@@ -501,8 +501,15 @@ etx_status etx_tracks_from_triplets(etx_ctx* ctx, const int32_t* src, const int3
  * (device) = {L_fake + w_genuine * L_genuine, L_genuine, L_fake}, L_genuine
  * = mean d2 over genuine pairs, L_fake = mean max(0, margin - d2) over fake
  * pairs (an empty set contributes 0; the hinge is inactive at d2 = margin);
- * d_emb float32 [n_hits][D] = dL/d emb (overwritten; atomics, order not
- * fixed).  pair_capacity bounds n_pairs (sizes the grid).  D <= 16.
+ * d_emb float32 [n_hits][D] = dL/d emb (every row overwritten).  No atomics
+ * on floating point: each hit's gradient is summed over its pairs as query,
+ * then as partner, each in ascending pair index, and the loss from per-block
+ * FP64 sums added in block order, so the same inputs on the same context
+ * give the same bits.  pair_capacity bounds n_pairs and sizes the grid and
+ * the workspace (at least etx_hinge_loss_workspace(n_hits, pair_capacity)
+ * bytes of device scratch, 16-byte aligned, owned by the caller); n_pairs
+ * outside [0, pair_capacity] is reported as ETX_ERR_CAPACITY by etx_ctx_sync
+ * and no pair is used.  n_hits <= the context's max_hits.  D <= 16.
  * Indices outside [0, n_hits) are skipped and reported by etx_ctx_sync.
  */
 int64_t etx_embed_param_count(const etx_config* cfg);
@@ -529,10 +536,12 @@ etx_status etx_embedding_pairs(etx_ctx* ctx, const float* emb, const int8_t* pla
                                size_t workspace_bytes, int32_t* pair_q, int32_t* pair_a,
                                uint8_t* pair_genuine, int64_t capacity, int32_t* n_pairs,
                                void* stream);
+size_t etx_hinge_loss_workspace(int64_t n_hits, int64_t pair_capacity);
 etx_status etx_hinge_loss(etx_ctx* ctx, const float* emb, int64_t n_hits, const int32_t* pair_q,
                           const int32_t* pair_a, const uint8_t* pair_genuine,
                           const int32_t* n_pairs, int64_t pair_capacity, float margin,
-                          float w_genuine, float* loss, float* d_emb, void* stream);
+                          float w_genuine, float* loss, float* d_emb, void* workspace,
+                          size_t workspace_bytes, void* stream);
 
 /*
  * Track-finding performance against truth (Sec. 6, Table 1), for evaluating
@@ -581,6 +590,12 @@ etx_status etx_track_metrics(etx_ctx* ctx, const int32_t* labels, const int32_t*
  *   "knn_split"                 blocks that share the sources of one
  *                               (event, plane) in the k-NN: 1, 2 or 4
  *                               (per-event work partitioning);
+ *   "knn_stage"                 floats of candidate embeddings a k-NN block
+ *                               stages in shared memory: 1024, 2048, 4096
+ *                               (the default), 8192 or 16384 (an (event,
+ *                               plane) whose two candidate planes hold more
+ *                               reads them from global memory; a smaller
+ *                               stage keeps more blocks resident per SM);
  *   "tc_stages/<block>/<dtype>" A-operand ring slots of the tensor-core MLP
  *                               kernel, 2 to 5 (capped by shared memory),
  *                               for block edge_encoder, node_update,

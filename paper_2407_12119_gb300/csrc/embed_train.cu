@@ -15,7 +15,9 @@
 //
 // Loss (Eq. 2-3): L = L_fake + w * L_genuine, L_genuine = mean d2 over the
 // genuine pairs, L_fake = mean max(0, m - d2) over the fake pairs; the
-// gradient with respect to the embedding is scattered with atomics.
+// gradient with respect to the embedding is gathered per hit over its pairs
+// (as query, then as partner, each in ascending pair index): no atomics, a
+// fixed summation order, so a step is bit-reproducible.
 #include <algorithm>
 
 #include "etx_internal.cuh"
@@ -247,16 +249,22 @@ __global__ void k_hinge_count(const uint8_t* __restrict__ pg, const int32_t* __r
   }
 }
 
+// Per pair p: the gradient coefficient c_p of d2 in L (w / n_genuine for a
+// genuine pair, -1 / n_fake for a fake pair inside the margin, else 0; 0 for a
+// pair with an index out of range, which is reported), and this block's sums
+// of d2 over the genuine pairs and of (margin - d2)+ over the fake ones
+// (FP64, a fixed reduction order) in part[2 block], part[2 block + 1].
 template <int D>
-__global__ void __launch_bounds__(kPT) k_hinge(const float* __restrict__ emb, int dim,
-                                               const int32_t* __restrict__ pq,
-                                               const int32_t* __restrict__ pa,
-                                               const uint8_t* __restrict__ pg,
-                                               const int32_t* __restrict__ n_pairs,
-                                               const unsigned long long* __restrict__ counts,
-                                               float margin, float w_gen, double* __restrict__ sums,
-                                               float* __restrict__ d_emb, int64_t n_hits,
-                                               int* err) {
+__global__ void __launch_bounds__(kPT) k_hinge_pairs(const float* __restrict__ emb, int dim,
+                                                     const int32_t* __restrict__ pq,
+                                                     const int32_t* __restrict__ pa,
+                                                     const uint8_t* __restrict__ pg,
+                                                     const int32_t* __restrict__ n_pairs,
+                                                     const unsigned long long* __restrict__ counts,
+                                                     float margin, float w_gen,
+                                                     float* __restrict__ coef,
+                                                     double* __restrict__ part, int64_t n_hits,
+                                                     int* err) {
   __shared__ double red[2][kPT / 32];
   const int Dn = D > 0 ? D : dim;
   const int64_t n = *n_pairs;
@@ -269,32 +277,26 @@ __global__ void __launch_bounds__(kPT) k_hinge(const float* __restrict__ emb, in
     const int64_t q = pq[i], a = pa[i];
     if (q < 0 || q >= n_hits || a < 0 || a >= n_hits) {
       set_err(err, DERR_RANGE);
+      coef[i] = 0.f;
       continue;
     }
     const float* eq = emb + q * Dn;
     const float* ea = emb + a * Dn;
-    float diff[D > 0 ? D : 16];
     float d2 = 0.f;
     for (int k = 0; k < Dn; ++k) {
-      diff[k] = eq[k] - ea[k];
-      d2 += diff[k] * diff[k];
+      const float t = eq[k] - ea[k];
+      d2 += t * t;
     }
-    float coef;
+    float c;
     if (pg[i]) {
       sg += d2;
-      coef = cg;
+      c = cg;
     } else {
       const bool active = d2 < margin;
       sf += active ? (double)(margin - d2) : 0.0;
-      coef = active ? cf : 0.f;
+      c = active ? cf : 0.f;
     }
-    if (coef != 0.f) {
-      for (int k = 0; k < Dn; ++k) {
-        const float v = 2.f * coef * diff[k];
-        atomicAdd(d_emb + q * Dn + k, v);
-        atomicAdd(d_emb + a * Dn + k, -v);
-      }
-    }
+    coef[i] = c;
   }
   for (int o = 16; o > 0; o >>= 1) {
     sg += __shfl_xor_sync(0xffffffffu, sg, o);
@@ -311,18 +313,99 @@ __global__ void __launch_bounds__(kPT) k_hinge(const float* __restrict__ emb, in
       a += red[0][w];
       b += red[1][w];
     }
-    atomicAdd(sums, a);
-    atomicAdd(sums + 1, b);
+    part[2 * blockIdx.x] = a;
+    part[2 * blockIdx.x + 1] = b;
   }
 }
 
-__global__ void k_hinge_final(const double* __restrict__ sums,
-                              const unsigned long long* __restrict__ counts,
-                              const int32_t* __restrict__ n_pairs, float w_gen,
-                              float* __restrict__ loss) {
+// dL/d emb of hit h (a thread per hit): 2 c_p (e_h - e_a) over the pairs p
+// where h is the query, then -2 c_p (e_q - e_h) over those where h is the
+// partner, each list in ascending pair index (the key indices), so the sum
+// has a fixed order.  Every row [0, n_hits) is written.
+template <int D>
+__global__ void __launch_bounds__(kPT) k_hinge_grad(const float* __restrict__ emb, int dim,
+                                                    const int32_t* __restrict__ pq,
+                                                    const int32_t* __restrict__ pa,
+                                                    const float* __restrict__ coef,
+                                                    const int32_t* __restrict__ off_q,
+                                                    const int32_t* __restrict__ perm_q,
+                                                    const int32_t* __restrict__ off_a,
+                                                    const int32_t* __restrict__ perm_a,
+                                                    int64_t n_hits, float* __restrict__ d_emb) {
+  const int Dn = D > 0 ? D : dim;
+  constexpr int DM = D > 0 ? D : 16;
+  for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < n_hits;
+       h += (int64_t)gridDim.x * blockDim.x) {
+    float eh[DM], acc[DM];
+#pragma unroll
+    for (int k = 0; k < DM; ++k) {
+      eh[k] = k < Dn ? emb[h * Dn + k] : 0.f;
+      acc[k] = 0.f;
+    }
+    for (int t = off_q[h]; t < off_q[h + 1]; ++t) {
+      const int p = perm_q[t];
+      const float c = coef[p];
+      if (c == 0.f) continue;
+      const float* ea = emb + (int64_t)pa[p] * Dn;
+#pragma unroll
+      for (int k = 0; k < DM; ++k)
+        if (k < Dn) acc[k] += 2.f * c * (eh[k] - ea[k]);
+    }
+    for (int t = off_a[h]; t < off_a[h + 1]; ++t) {
+      const int p = perm_a[t];
+      const float c = coef[p];
+      if (c == 0.f) continue;
+      const float* eq = emb + (int64_t)pq[p] * Dn;
+#pragma unroll
+      for (int k = 0; k < DM; ++k)
+        if (k < Dn) acc[k] -= 2.f * c * (eq[k] - eh[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < DM; ++k)
+      if (k < Dn) d_emb[h * Dn + k] = acc[k];
+  }
+}
+
+// The pair count the other kernels use: *n_pairs, or 0 (and ETX_ERR_CAPACITY)
+// when it lies outside [0, capacity].
+__global__ void k_hinge_clamp(const int32_t* __restrict__ n_pairs, int64_t capacity,
+                              int32_t* __restrict__ n_eff, int* err) {
+  const int32_t n = *n_pairs;
+  const bool ok = n >= 0 && (int64_t)n <= capacity;
+  if (!ok) set_err(err, DERR_CAPACITY);
+  *n_eff = ok ? n : 0;
+}
+
+// The blocks' sums added in a fixed order (thread t: blocks t, t + kPT, ...;
+// then a fixed tree over the threads), then the loss.  One block of kPT.
+__global__ void __launch_bounds__(kPT) k_hinge_final(const double* __restrict__ part, int n_part,
+                                                     const unsigned long long* __restrict__ counts,
+                                                     const int32_t* __restrict__ n_pairs,
+                                                     float w_gen, float* __restrict__ loss) {
+  __shared__ double red[2][kPT / 32];
+  double sg = 0.0, sf = 0.0;
+  for (int b = threadIdx.x; b < n_part; b += kPT) {
+    sg += part[2 * b];
+    sf += part[2 * b + 1];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sg += __shfl_xor_sync(0xffffffffu, sg, o);
+    sf += __shfl_xor_sync(0xffffffffu, sf, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = sg;
+    red[1][threadIdx.x >> 5] = sf;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  sg = sf = 0.0;
+  for (int w = 0; w < kPT / 32; ++w) {
+    sg += red[0][w];
+    sf += red[1][w];
+  }
   const unsigned long long ng = counts[0], nf = (unsigned long long)*n_pairs - counts[0];
-  const double lg = ng ? sums[0] / (double)ng : 0.0;
-  const double lf = nf ? sums[1] / (double)nf : 0.0;
+  const double lg = ng ? sg / (double)ng : 0.0;
+  const double lf = nf ? sf / (double)nf : 0.0;
   loss[0] = (float)(lf + (double)w_gen * lg);
   loss[1] = (float)lg;
   loss[2] = (float)lf;
@@ -373,33 +456,99 @@ cudaError_t launch_embedding_pairs(etx_ctx* ctx, const float* emb, const int8_t*
   return cudaGetLastError();
 }
 
+namespace {
+constexpr int kHingeMaxBlocks = 2048;  // per-block loss sums in the workspace
+
+struct HingeWs {
+  double* part;                 // [2 kHingeMaxBlocks]
+  unsigned long long* counts;   // [2]
+  int32_t* n_eff;               // the pair count in use
+  float* coef;                  // [cap]
+  int32_t *cnt, *off_q, *off_a; // [n_hits + 1] each
+  int32_t *perm_q, *perm_a;     // [cap] each
+  size_t bytes;
+};
+
+HingeWs hinge_ws(void* base, int64_t n_hits, int64_t cap) {
+  HingeWs w{};
+  uint8_t* b = static_cast<uint8_t*>(base);
+  size_t o = 0;
+  auto take = [&](size_t n) {
+    uint8_t* r = b ? b + o : nullptr;
+    o += (n + 15) & ~static_cast<size_t>(15);
+    return r;
+  };
+  w.part = reinterpret_cast<double*>(take(2 * kHingeMaxBlocks * sizeof(double)));
+  w.counts = reinterpret_cast<unsigned long long*>(take(2 * sizeof(unsigned long long)));
+  w.n_eff = reinterpret_cast<int32_t*>(take(sizeof(int32_t)));
+  w.coef = reinterpret_cast<float*>(take((size_t)cap * sizeof(float)));
+  w.cnt = reinterpret_cast<int32_t*>(take((size_t)(n_hits + 1) * sizeof(int32_t)));
+  w.off_q = reinterpret_cast<int32_t*>(take((size_t)(n_hits + 1) * sizeof(int32_t)));
+  w.off_a = reinterpret_cast<int32_t*>(take((size_t)(n_hits + 1) * sizeof(int32_t)));
+  w.perm_q = reinterpret_cast<int32_t*>(take((size_t)cap * sizeof(int32_t)));
+  w.perm_a = reinterpret_cast<int32_t*>(take((size_t)cap * sizeof(int32_t)));
+  w.bytes = o;
+  return w;
+}
+}  // namespace
+
+size_t hinge_loss_workspace(int64_t n_hits, int64_t pair_capacity) {
+  return hinge_ws(nullptr, n_hits, pair_capacity).bytes;
+}
+
 cudaError_t launch_hinge_loss(etx_ctx* ctx, const float* emb, int64_t n_hits, const int32_t* pq,
                               const int32_t* pa, const uint8_t* pg, const int32_t* n_pairs,
                               int64_t pair_capacity, float margin, float w_genuine, float* loss,
-                              float* d_emb, void* scratch, cudaStream_t s) {
+                              float* d_emb, void* workspace, cudaStream_t s) {
   const int D = ctx->cfg.emb_widths[ctx->cfg.emb_depth];
-  unsigned long long* counts = static_cast<unsigned long long*>(scratch);
-  double* sums = reinterpret_cast<double*>(counts + 1);
-  cudaError_t e = cudaMemsetAsync(scratch, 0, 3 * sizeof(double), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d_emb, 0, (size_t)n_hits * D * sizeof(float), s);
+  const HingeWs w = hinge_ws(workspace, n_hits, pair_capacity);
+  cudaError_t e = cudaMemsetAsync(w.counts, 0, 2 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
+  launch(ctx, "embtrain_hinge_clamp", k_hinge_clamp, 1, 1, 0, s, n_pairs, pair_capacity, w.n_eff,
+         ctx->d_err);
+  n_pairs = w.n_eff;
+  // a grid fixed by the context and the capacity: the loss sums' order with it
   const unsigned grid = (unsigned)std::max<int64_t>(
-      1, std::min<int64_t>((pair_capacity + kPT - 1) / kPT, (int64_t)ctx->n_sms * 8));
-  launch(ctx, "embtrain_hinge_count", k_hinge_count, grid, kPT, 0, s, pg, n_pairs, counts);
+      1, std::min<int64_t>(std::min<int64_t>((pair_capacity + kPT - 1) / kPT, (int64_t)ctx->n_sms * 8),
+                           kHingeMaxBlocks));
+  launch(ctx, "embtrain_hinge_count", k_hinge_count, grid, kPT, 0, s, pg, n_pairs, w.counts);
+  const auto* cnts = (const unsigned long long*)w.counts;
   if (D == 8)
-    launch(ctx, "embtrain_hinge", k_hinge<8>, grid, kPT, 0, s, emb, D, pq, pa, pg, n_pairs,
-           (const unsigned long long*)counts, margin, w_genuine, sums, d_emb, n_hits,
-           ctx->d_err);
+    launch(ctx, "embtrain_hinge_pairs", k_hinge_pairs<8>, grid, kPT, 0, s, emb, D, pq, pa, pg,
+           n_pairs, cnts, margin, w_genuine, w.coef, w.part, n_hits, ctx->d_err);
   else if (D == 4)
-    launch(ctx, "embtrain_hinge", k_hinge<4>, grid, kPT, 0, s, emb, D, pq, pa, pg, n_pairs,
-           (const unsigned long long*)counts, margin, w_genuine, sums, d_emb, n_hits,
-           ctx->d_err);
+    launch(ctx, "embtrain_hinge_pairs", k_hinge_pairs<4>, grid, kPT, 0, s, emb, D, pq, pa, pg,
+           n_pairs, cnts, margin, w_genuine, w.coef, w.part, n_hits, ctx->d_err);
   else
-    launch(ctx, "embtrain_hinge", k_hinge<0>, grid, kPT, 0, s, emb, D, pq, pa, pg, n_pairs,
-           (const unsigned long long*)counts, margin, w_genuine, sums, d_emb, n_hits,
-           ctx->d_err);
-  launch(ctx, "embtrain_hinge_final", k_hinge_final, 1, 1, 0, s, (const double*)sums,
-         (const unsigned long long*)counts, n_pairs, w_genuine, loss);
+    launch(ctx, "embtrain_hinge_pairs", k_hinge_pairs<0>, grid, kPT, 0, s, emb, D, pq, pa, pg,
+           n_pairs, cnts, margin, w_genuine, w.coef, w.part, n_hits, ctx->d_err);
+  // each hit's pairs as query and as partner, in ascending pair index
+  static const char* const kQNames[3] = {"embtrain_hinge_index_count", "embtrain_hinge_index_fill",
+                                         "embtrain_hinge_index_sort"};
+  e = launch_key_index(ctx, pq, n_pairs, pair_capacity, n_hits, w.cnt, w.off_q, w.perm_q, kQNames, s);
+  if (e == cudaSuccess)
+    e = launch_key_index(ctx, pa, n_pairs, pair_capacity, n_hits, w.cnt, w.off_a, w.perm_a, kQNames, s);
+  if (e != cudaSuccess) return e;
+  if (n_hits > 0) {
+    const int64_t want = (n_hits + kPT - 1) / kPT;
+    const void* kg = D == 8 ? (const void*)k_hinge_grad<8>
+                   : D == 4 ? (const void*)k_hinge_grad<4> : (const void*)k_hinge_grad<0>;
+    const int gg = grid_for(ctx, kg, kPT, 0, want);
+    if (D == 8)
+      launch(ctx, "embtrain_hinge_grad", k_hinge_grad<8>, gg, kPT, 0, s, emb, D, pq, pa,
+             (const float*)w.coef, (const int32_t*)w.off_q, (const int32_t*)w.perm_q,
+             (const int32_t*)w.off_a, (const int32_t*)w.perm_a, n_hits, d_emb);
+    else if (D == 4)
+      launch(ctx, "embtrain_hinge_grad", k_hinge_grad<4>, gg, kPT, 0, s, emb, D, pq, pa,
+             (const float*)w.coef, (const int32_t*)w.off_q, (const int32_t*)w.perm_q,
+             (const int32_t*)w.off_a, (const int32_t*)w.perm_a, n_hits, d_emb);
+    else
+      launch(ctx, "embtrain_hinge_grad", k_hinge_grad<0>, gg, kPT, 0, s, emb, D, pq, pa,
+             (const float*)w.coef, (const int32_t*)w.off_q, (const int32_t*)w.perm_q,
+             (const int32_t*)w.off_a, (const int32_t*)w.perm_a, n_hits, d_emb);
+  }
+  launch(ctx, "embtrain_hinge_final", k_hinge_final, 1, kPT, 0, s, (const double*)w.part, (int)grid,
+         cnts, n_pairs, w_genuine, loss);
   return cudaGetLastError();
 }
 

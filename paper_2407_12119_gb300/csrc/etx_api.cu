@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <iterator>
 #include <new>
 
 #include <cuda_bf16.h>
@@ -1096,20 +1097,31 @@ etx_status etx_embedding_pairs(etx_ctx* ctx, const float* emb, const int8_t* pla
   return ETX_OK;
 }
 
+size_t etx_hinge_loss_workspace(int64_t n_hits, int64_t pair_capacity) {
+  if (n_hits < 0 || pair_capacity < 0) return 0;
+  return hinge_loss_workspace(n_hits, pair_capacity);
+}
+
 etx_status etx_hinge_loss(etx_ctx* ctx, const float* emb, int64_t n_hits, const int32_t* pair_q,
                           const int32_t* pair_a, const uint8_t* pair_genuine,
                           const int32_t* n_pairs, int64_t pair_capacity, float margin,
-                          float w_genuine, float* loss, float* d_emb, void* stream) {
+                          float w_genuine, float* loss, float* d_emb, void* workspace,
+                          size_t workspace_bytes, void* stream) {
   if (!ctx) return ETX_ERR_ARG;
   if (n_hits < 0 || n_hits >= ((int64_t)1 << 31)) return fail(ctx, ETX_ERR_ARG, "n_hits out of range");
+  if (n_hits > ctx->cfg.max_hits) return fail(ctx, ETX_ERR_CAPACITY, "n_hits exceeds the context capacity");
   if (pair_capacity < 0 || pair_capacity >= ((int64_t)1 << 31)) return fail(ctx, ETX_ERR_ARG, "pair_capacity out of range");
+  if (!workspace) return fail(ctx, ETX_ERR_ARG, "NULL workspace");
+  if (reinterpret_cast<uintptr_t>(workspace) & 15) return fail(ctx, ETX_ERR_ARG, "workspace not 16-byte aligned");
+  if (workspace_bytes < hinge_loss_workspace(n_hits, pair_capacity))
+    return fail(ctx, ETX_ERR_CAPACITY, "workspace smaller than etx_hinge_loss_workspace()");
   if (!n_pairs || !loss || (n_hits > 0 && (!emb || !d_emb))) return fail(ctx, ETX_ERR_ARG, "NULL array");
   if (pair_capacity > 0 && (!pair_q || !pair_a || !pair_genuine)) return fail(ctx, ETX_ERR_ARG, "NULL pair arrays");
   if (!(margin == margin) || !(w_genuine >= 0.f) || w_genuine > 1e30f) return fail(ctx, ETX_ERR_ARG, "bad margin or w_genuine");
   if (ctx->cfg.emb_widths[ctx->cfg.emb_depth] > 16) return fail(ctx, ETX_ERR_UNSUPPORTED, "embedding dimension above 16");
   cudaSetDevice(ctx->device);
   cudaError_t e = launch_hinge_loss(ctx, emb, n_hits, pair_q, pair_a, pair_genuine, n_pairs,
-                                    pair_capacity, margin, w_genuine, loss, d_emb, ctx->small,
+                                    pair_capacity, margin, w_genuine, loss, d_emb, workspace,
                                     (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "etx_hinge_loss launch");
   return ETX_OK;
@@ -1152,6 +1164,9 @@ etx_status etx_track_metrics(etx_ctx* ctx, const int32_t* labels, const int32_t*
 namespace {
 
 const char* const kTcBlock[4] = {"edge_encoder", "node_update", "edge_update", "classifier"};
+// k-NN launch candidates: blocks per (event, plane), candidate floats staged per block
+constexpr int kKnnSplits[3] = {1, 2, 4};
+constexpr int kKnnStages[5] = {1024, 2048, 4096, 8192, 16384};
 
 // Milliseconds of the recorded launches whose name starts with `prefix`
 // (waits for them); clears the record.
@@ -1185,27 +1200,32 @@ etx_status etx_autotune(etx_ctx* ctx, const float* x, const float* y, const floa
   ctx->prof_on = true;
   ctx->prof_used = 0;
   constexpr int kReps = 2;
-  // k-NN: blocks per (event, plane)
-  const int splits[3] = {1, 2, 4};
+  // k-NN: blocks per (event, plane) x candidate stage per block
   double best = 1e300;
-  int best_split = ctx->knn_split;
-  for (int split : splits) {
-    ctx->knn_split = split;
-    double ms = 0.0;
-    for (int r = 0; r <= kReps && st == ETX_OK; ++r) {
-      st = etx_build_graph(ctx, emb, plane, hit_offsets, n_events, n_hits, radius, k_max, src, dst,
-                           edge_capacity, edge_offsets, stream);
-      const double t = prof_take(ctx, "graph_knn");
-      if (t < 0) st = fail(ctx, ETX_ERR_CUDA, "autotune timing");
-      if (r > 0) ms += t;  // the first run warms up
+  int best_split = ctx->knn_split, best_stage = ctx->knn_stage;
+  for (int stage : kKnnStages) {
+    for (int split : kKnnSplits) {
+      ctx->knn_split = split;
+      ctx->knn_stage = stage;
+      double ms = 0.0;
+      for (int r = 0; r <= kReps && st == ETX_OK; ++r) {
+        st = etx_build_graph(ctx, emb, plane, hit_offsets, n_events, n_hits, radius, k_max, src,
+                             dst, edge_capacity, edge_offsets, stream);
+        const double t = prof_take(ctx, "graph_knn");
+        if (t < 0) st = fail(ctx, ETX_ERR_CUDA, "autotune timing");
+        if (r > 0) ms += t;  // the first run warms up
+      }
+      if (st != ETX_OK) break;
+      if (ms < best) {
+        best = ms;
+        best_split = split;
+        best_stage = stage;
+      }
     }
     if (st != ETX_OK) break;
-    if (ms < best) {
-      best = ms;
-      best_split = split;
-    }
   }
   ctx->knn_split = best_split;
+  ctx->knn_stage = best_stage;
   if (st == ETX_OK)
     st = etx_build_graph(ctx, emb, plane, hit_offsets, n_events, n_hits, radius, k_max, src, dst,
                          edge_capacity, edge_offsets, stream);
@@ -1261,6 +1281,7 @@ int32_t etx_tuned(const etx_ctx* ctx, const char* knob) {
   if (!ctx || !knob) return -1;
   const std::string k(knob);
   if (k == "knn_split") return ctx->knn_split;
+  if (k == "knn_stage") return ctx->knn_stage;
   for (int m = 0; m < 4; ++m)
     for (int f8 = 0; f8 < 2; ++f8)
       if (k == std::string("tc_stages/") + kTcBlock[m] + (f8 ? "/fp8" : "/bf16"))
@@ -1275,6 +1296,12 @@ etx_status etx_set_tuned(etx_ctx* ctx, const char* knob, int32_t value) {
   if (k == "knn_split") {
     if (value != 1 && value != 2 && value != 4) return fail(ctx, ETX_ERR_ARG, "knn_split must be 1, 2 or 4");
     ctx->knn_split = value;
+    return ETX_OK;
+  }
+  if (k == "knn_stage") {
+    if (std::find(std::begin(kKnnStages), std::end(kKnnStages), value) == std::end(kKnnStages))
+      return fail(ctx, ETX_ERR_ARG, "knn_stage must be 1024, 2048, 4096, 8192 or 16384");
+    ctx->knn_stage = value;
     return ETX_OK;
   }
   for (int m = 0; m < 4; ++m)

@@ -184,6 +184,7 @@ struct etx_ctx {
   // launch configurations picked by etx_autotune (defaults: measured on the
   // 500-event workload)
   int knn_split = 1;                         // blocks per (event, plane) in the k-NN
+  int knn_stage = 4096;                      // floats of staged k-NN candidates per block
   int tc_stages[4][2] = {{3, 2}, {3, 2}, {3, 2}, {3, 2}};  // ring slots [mode][e4m3]
 
   // launch accounting and optional per-launch CUDA-event timing
@@ -222,6 +223,13 @@ cudaError_t launch_gnn_forward(etx_ctx* ctx, const float* x, const float* y, con
                                cudaStream_t s);
 cudaError_t launch_edge_index(etx_ctx* ctx, int64_t n_hits, const int32_t* src,
                               const int32_t* dst, const int32_t* n_edges_dev, cudaStream_t s);
+// CSR of the element ids 0 .. *n_dev - 1 grouped by keys[id] (ids whose key is
+// outside [0, n_keys) are left out), each segment in ascending id (so the
+// order is fixed): off [n_keys + 1], perm [n_cap]; cnt [n_keys + 1] scratch.
+// names: the three launches' profile names (count, fill, sort).
+cudaError_t launch_key_index(etx_ctx* ctx, const int32_t* keys, const int32_t* n_dev, int64_t n_cap,
+                             int64_t n_keys, int32_t* cnt, int32_t* off, int32_t* perm,
+                             const char* const names[3], cudaStream_t s);
 // messages of edge features e (uses the context's edge index structures)
 cudaError_t launch_messages(etx_ctx* ctx, const float* e, float* m, int64_t n_hits, cudaStream_t s);
 
@@ -327,10 +335,11 @@ cudaError_t launch_embedding_pairs(etx_ctx* ctx, const float* emb, const int8_t*
                                    int32_t* pq, int32_t* pa, uint8_t* pg, int64_t capacity,
                                    int32_t* n_pairs, cudaStream_t s);
 // scratch: 3 doubles of device memory
+size_t hinge_loss_workspace(int64_t n_hits, int64_t pair_capacity);
 cudaError_t launch_hinge_loss(etx_ctx* ctx, const float* emb, int64_t n_hits, const int32_t* pq,
                               const int32_t* pa, const uint8_t* pg, const int32_t* n_pairs,
                               int64_t pair_capacity, float margin, float w_genuine, float* loss,
-                              float* d_emb, void* scratch, cudaStream_t s);
+                              float* d_emb, void* workspace, cudaStream_t s);
 // embed.cu / gnn_bwd.cu: embedding forward with saved activations, and its reverse pass
 size_t embed_backward_workspace(const etx_config& cfg, int64_t n_hits);
 int64_t embed_param_count(const etx_config& cfg);

@@ -489,17 +489,28 @@ cudaError_t launch_edge_index(etx_ctx* ctx, int64_t N, const int32_t* src, const
   const int64_t Ecap = ctx->cfg.max_edges;
   cudaError_t e;
   if ((e = cudaMemsetAsync(ctx->out_off, 0, (N + 1) * sizeof(int32_t), s)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(ctx->in_cnt, 0, (N + 1) * sizeof(int32_t), s)) != cudaSuccess) return e;
   const int ge = grid_for(ctx, (const void*)k_out_offsets, 256, 0, (Ecap + 256) / 256);
   launch(ctx, "index_out_offsets", k_out_offsets, ge, 256, 0, s, src, dst, n_edges_dev, (int)N,
          ctx->out_off, ctx->d_err);
-  launch(ctx, "index_in_count", k_in_count, ge, 256, 0, s, dst, n_edges_dev, (int)N, ctx->in_cnt);
-  if ((e = exclusive_scan(ctx, ctx->in_cnt, ctx->in_off, N, s)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(ctx->in_cnt, 0, (N + 1) * sizeof(int32_t), s)) != cudaSuccess) return e;
-  launch(ctx, "index_in_fill", k_in_fill, ge, 256, 0, s, dst, n_edges_dev, (int)N, ctx->in_off,
-         ctx->in_cnt, ctx->perm_in);
-  const int gn = grid_for(ctx, (const void*)k_in_sort_warp, 256, 0, (N + 7) / 8);  // a warp per hit
-  if (N > 0) launch(ctx, "index_in_sort", k_in_sort_warp, gn, 256, 0, s, ctx->in_off, (int)N, ctx->perm_in);
+  static const char* const kInNames[3] = {"index_in_count", "index_in_fill", "index_in_sort"};
+  return launch_key_index(ctx, dst, n_edges_dev, Ecap, N, ctx->in_cnt, ctx->in_off, ctx->perm_in,
+                          kInNames, s);
+}
+
+cudaError_t launch_key_index(etx_ctx* ctx, const int32_t* keys, const int32_t* n_dev, int64_t n_cap,
+                             int64_t n_keys, int32_t* cnt, int32_t* off, int32_t* perm,
+                             const char* const names[3], cudaStream_t s) {
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(cnt, 0, (n_keys + 1) * sizeof(int32_t), s)) != cudaSuccess) return e;
+  const int ge = grid_for(ctx, (const void*)k_in_count, 256, 0, (n_cap + 256) / 256);
+  launch(ctx, names[0], k_in_count, ge, 256, 0, s, keys, n_dev, (int)n_keys, cnt);
+  if ((e = exclusive_scan(ctx, cnt, off, n_keys, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(cnt, 0, (n_keys + 1) * sizeof(int32_t), s)) != cudaSuccess) return e;
+  launch(ctx, names[1], k_in_fill, ge, 256, 0, s, keys, n_dev, (int)n_keys, (const int32_t*)off,
+         cnt, perm);
+  const int gn = grid_for(ctx, (const void*)k_in_sort_warp, 256, 0, (n_keys + 7) / 8);  // a warp per key
+  if (n_keys > 0)
+    launch(ctx, names[2], k_in_sort_warp, gn, 256, 0, s, (const int32_t*)off, (int)n_keys, perm);
   return cudaGetLastError();
 }
 

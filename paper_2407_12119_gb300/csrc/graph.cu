@@ -3,9 +3,12 @@
 // Hits arrive plane-sorted per event, so the candidates of every source hit
 // on plane p (the hits of planes p+1 and p+2) form one contiguous index range.
 // One block per (event, plane): the candidate embeddings are staged in shared
-// memory (structure of arrays, so lane j reads candidate j bank-conflict free),
-// one warp per source hit, lanes over candidates, ballot + popc to count and
-// compact the hits inside the radius.  When more than k_max hits qualify, the
+// memory (structure of arrays, so lane j reads candidate j bank-conflict free)
+// when they fit the block's stage, else read from global memory; one warp per
+// source hit, lanes over candidates, ballot + popc to count and compact the
+// hits inside the radius.  The stage size is a launch parameter (autotuned):
+// a stage sized for the typical event keeps more blocks resident per SM than
+// one sized for the largest.  When more than k_max hits qualify, the
 // k_max-th smallest squared distance is found by a 32-step radix select on
 // the FP32 bit patterns (non-negative floats order like their bits); ties at
 // that value are taken in ascending candidate index, which realises the
@@ -22,7 +25,7 @@ namespace etx {
 namespace {
 
 constexpr int kKnnThreads = 128;
-constexpr int kStageFloats = 16384;  // 64 KB of staged candidate coordinates per block
+constexpr int kStageMaxFloats = 16384;  // largest candidate stage: 64 KB per block
 constexpr int kMaxDim = 32;
 
 // register-resident candidate keys per lane: 16 (512 candidates per block) or
@@ -94,7 +97,8 @@ __global__ void k_plane_bins(const int8_t* __restrict__ plane, const int32_t* __
   plane_off[t] = lo;
 }
 
-// Fast path for one source hit (compile-time D, candidates staged): one pass
+// Fast path for one source hit (compile-time D; candidate j's dimension d at
+// cand[j * cstep + d * cstride], staged or in global memory): one pass
 // over the candidates lists the qualifying ones (d2 < r2) in the warp's
 // scratch as (key, j) pairs, key = the FP32 bit pattern of d2 (order-preserving
 // for d2 >= 0), in ascending j (ballot compaction).  If more than k_max
@@ -111,7 +115,8 @@ constexpr int kListCap = 256;  // (key, j) pairs per warp: 2 KB of shared memory
 // into cnt_or_off[i] (a compaction pass forms the edge list).
 template <int KM, int D>
 __device__ __forceinline__ bool knn_source_list(const float* __restrict__ emb, int i,
-                                                const float* cand_s, int n_cand, int c_lo,
+                                                const float* cand, int cstride, int cstep,
+                                                int n_cand, int c_lo,
                                                 float r2, int k_max, int32_t* cnt_or_off,
                                                 int32_t* __restrict__ src,
                                                 int32_t* __restrict__ dst, int lane,
@@ -127,7 +132,7 @@ __device__ __forceinline__ bool knn_source_list(const float* __restrict__ emb, i
     bool in = false;
     uint32_t key = 0;
     if (j < n_cand) {
-      const float d2 = d2_fixed<D>(ei, cand_s + j, n_cand);
+      const float d2 = d2_fixed<D>(ei, cand + (int64_t)j * cstep, cstride);
       in = d2 < r2;
       key = __float_as_uint(d2);
     }
@@ -190,9 +195,10 @@ __global__ void __launch_bounds__(kKnnThreads)
 k_knn(const float* __restrict__ emb, int D, const int32_t* __restrict__ plane_off, int n_planes,
       float radius, int k_max, int32_t* __restrict__ cnt_or_off, int64_t n_hits,
       int32_t* __restrict__ src, int32_t* __restrict__ dst, int64_t capacity, int* err,
-      int split) {
-  extern __shared__ float cand_s[];  // [D][n_stage], then kListCap (key, j) pairs per warp
-  uint64_t* list_s = reinterpret_cast<uint64_t*>(cand_s + kStageFloats);  // per-warp pair lists
+      int split, int stage_floats) {
+  // [D][n_cand] within the first stage_floats, then kListCap (key, j) pairs per warp
+  extern __shared__ float cand_s[];
+  uint64_t* list_s = reinterpret_cast<uint64_t*>(cand_s + stage_floats);  // per-warp pair lists
   // `split` blocks share the sources of one (event, plane): block `part` takes
   // every split-th group of warps' sources (each stages the candidates itself)
   const int bp = blockIdx.x / split, part = blockIdx.x % split;
@@ -218,7 +224,7 @@ k_knn(const float* __restrict__ emb, int D, const int32_t* __restrict__ plane_of
   constexpr int WPB = kKnnThreads / 32;  // warps per block
   if (s_lo + part * WPB >= s_hi) return;  // no source for this part
   // candidate storage: shared (SoA, stride n_cand) or global (AoS, stride 1)
-  const bool staged = n_cand * D <= kStageFloats;
+  const bool staged = n_cand * D <= stage_floats;
   if (staged) {
     for (int t = threadIdx.x; t < n_cand * D; t += blockDim.x) {
       const int j = t / D, d = t - j * D;
@@ -231,11 +237,10 @@ k_knn(const float* __restrict__ emb, int D, const int32_t* __restrict__ plane_of
   const int cstep = staged ? 1 : D;              // stride between candidates
   const float r2 = __fmul_rn(radius, radius);
 
-  const bool fast = DT > 0 && staged;
   for (int i = s_lo + part * WPB + warp; i < s_hi; i += WPB * split) {
     if constexpr (DT > 0) {
-      if (fast && knn_source_list<KM, DT>(emb, i, cand_s, n_cand, c_lo, r2, k_max, cnt_or_off,
-                                            src, dst, lane, list_s + kListCap * warp))
+      if (knn_source_list<KM, DT>(emb, i, cbase, cstride, cstep, n_cand, c_lo, r2, k_max,
+                                  cnt_or_off, src, dst, lane, list_s + kListCap * warp))
         continue;
     }
     float ei[kMaxDim];
@@ -359,14 +364,15 @@ cudaError_t launch_build_graph(etx_ctx* ctx, const float* emb, const int8_t* pla
            hit_offsets, n_events, (int)n_hits, P, ctx->plane_off);
   int32_t* cnt = ctx->hit_cnt;  // counts, then (in place) offsets; [n_hits + 1]
   const int split = ctx->knn_split;
+  const int stage = ctx->knn_stage;  // a multiple of 4 in [1024, kStageMaxFloats]
   const unsigned blocks = (unsigned)n_events * (unsigned)(P - 1) * (unsigned)split;
-  const size_t smem = (size_t)kStageFloats * sizeof(float) + kKnnThreads / 32 * kListCap * sizeof(uint64_t);
+  const size_t smem = (size_t)stage * sizeof(float) + kKnnThreads / 32 * kListCap * sizeof(uint64_t);
   // hits of the last plane get no block: start from zero counts
   cudaError_t e0 = cudaMemsetAsync(cnt, 0, (size_t)(n_hits + 1) * sizeof(int32_t), s);
   if (e0 != cudaSuccess) return e0;
   auto knn = [&](auto kernel, const char* name, int32_t* sp, int32_t* dp, int64_t cap) {
     launch(ctx, name, kernel, blocks, kKnnThreads, smem, s, emb, D, (const int32_t*)ctx->plane_off,
-           P, radius, k_max, cnt, n_hits, sp, dp, cap, ctx->d_err, split);
+           P, radius, k_max, cnt, n_hits, sp, dp, cap, ctx->d_err, split, stage);
   };
   // One distance pass into fixed-stride slots when the context's in-edge
   // permutation (rebuilt by every consumer of the edge index) can hold them;
@@ -422,7 +428,7 @@ cudaError_t launch_plane_bins(etx_ctx* ctx, const int8_t* plane, const int32_t* 
 }
 
 cudaError_t knn_set_smem_attr() {
-  const int smem = (int)(kStageFloats * sizeof(float) + kKnnThreads / 32 * kListCap * sizeof(uint64_t));
+  const int smem = (int)(kStageMaxFloats * sizeof(float) + kKnnThreads / 32 * kListCap * sizeof(uint64_t));
   const void* ks[] = {(const void*)k_knn<0, 0>, (const void*)k_knn<1, 0>, (const void*)k_knn<2, 0>,
                       (const void*)k_knn<0, 4>, (const void*)k_knn<1, 4>, (const void*)k_knn<2, 4>,
                       (const void*)k_knn<0, 8>, (const void*)k_knn<1, 8>, (const void*)k_knn<2, 8>};

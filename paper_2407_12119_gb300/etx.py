@@ -34,7 +34,8 @@ EXPORTED = ["etx_ctx_create", "etx_ctx_destroy", "etx_last_error", "etx_weights_
             "etx_autotune", "etx_tuned", "etx_set_tuned", "etx_edges_to_tracks_sweep",
             "etx_track_metrics_workspace", "etx_track_metrics", "etx_embed_param_count",
             "etx_embed_train_workspace", "etx_embed_forward_train", "etx_embed_backward",
-            "etx_embedding_pairs_workspace", "etx_embedding_pairs", "etx_hinge_loss",
+            "etx_embedding_pairs_workspace", "etx_embedding_pairs", "etx_hinge_loss_workspace",
+            "etx_hinge_loss",
             "etx_triplet_weights_size", "etx_load_triplet_weights", "etx_triplets_workspace",
             "etx_build_triplets", "etx_classify_triplets", "etx_fp8_scale_count",
             "etx_set_fp8_scales", "etx_tracks_workspace", "etx_tracks_from_triplets",
@@ -45,7 +46,7 @@ TRACK_COUNTS = ["particles", "matched_particles", "candidates", "candidate_parti
 TRACK_VALUES = ["hit_eff_sum", "hit_purity_sum", "efficiency", "clone_rate", "fake_rate",
                 "hit_efficiency", "hit_purity"]
 # knob names of the autotuner (etx_tuned)
-TUNE_KNOBS = ["knn_split"] + [f"tc_stages/{b}/{d}" for b in
+TUNE_KNOBS = ["knn_split", "knn_stage"] + [f"tc_stages/{b}/{d}" for b in
                               ("edge_encoder", "node_update", "edge_update", "classifier")
                               for d in ("bf16", "fp8")]
 
@@ -114,7 +115,9 @@ def lib() -> ctypes.CDLL:
         "etx_embedding_pairs_workspace": (ctypes.c_size_t, [i32, i64, i32]),
         "etx_embedding_pairs": (i32, [vp, vp, vp, vp, vp, i32, i64, f32, i32, vp, i32, vp,
                                       ctypes.c_size_t, vp, vp, vp, i64, vp, vp]),
-        "etx_hinge_loss": (i32, [vp, vp, i64, vp, vp, vp, vp, i64, f32, f32, vp, vp, vp]),
+        "etx_hinge_loss_workspace": (ctypes.c_size_t, [i64, i64]),
+        "etx_hinge_loss": (i32, [vp, vp, i64, vp, vp, vp, vp, i64, f32, f32, vp, vp, vp,
+                                 ctypes.c_size_t, vp]),
         "etx_triplet_weights_size": (i64, [cfgp]),
         "etx_load_triplet_weights": (i32, [vp, vp, i64]),
         "etx_triplets_workspace": (ctypes.c_size_t, [i64]),
@@ -544,8 +547,13 @@ class Context:
                                               _stream(stream)))
         return pq, pa, pg, npairs
 
+    @staticmethod
+    def hinge_loss_workspace(n_hits: int, pair_capacity: int) -> int:
+        """Bytes of device scratch that hinge_loss needs."""
+        return int(lib().etx_hinge_loss_workspace(int(n_hits), int(pair_capacity)))
+
     def hinge_loss(self, emb, pair_q, pair_a, pair_genuine, n_pairs, margin: float = 1.0,
-                   w_genuine: float = 2.0, loss=None, d_emb=None, stream=None):
+                   w_genuine: float = 2.0, loss=None, d_emb=None, workspace=None, stream=None):
         """Eq. 2-3; returns (loss float32[3] = {L, L_genuine, L_fake}, d_emb) on the device."""
         dev = self.device
         _need(emb, torch.float32, "emb", dev)
@@ -558,10 +566,15 @@ class Context:
         if d_emb is None:
             d_emb = torch.empty_like(emb)
         _need(d_emb, torch.float32, "d_emb", dev)
+        if workspace is None:
+            need = self.hinge_loss_workspace(emb.shape[0], pair_q.shape[0])
+            workspace = torch.empty(max(need, 16), dtype=torch.uint8, device=dev)
+        _need(workspace, torch.uint8, "workspace", dev)
         self._check(lib().etx_hinge_loss(self._h, _ptr(emb), emb.shape[0], _ptr(pair_q),
                                          _ptr(pair_a), _ptr(pair_genuine), _ptr(n_pairs),
                                          pair_q.shape[0], float(margin), float(w_genuine),
-                                         _ptr(loss), _ptr(d_emb), _stream(stream)))
+                                         _ptr(loss), _ptr(d_emb), _ptr(workspace),
+                                         workspace.numel(), _stream(stream)))
         return loss, d_emb
 
     @staticmethod

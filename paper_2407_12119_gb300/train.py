@@ -119,6 +119,8 @@ class EmbeddingTrainer:
                       torch.empty(self.capacity, dtype=torch.int32, device=dev),
                       torch.empty(self.capacity, dtype=torch.uint8, device=dev),
                       torch.empty(1, dtype=torch.int32, device=dev))
+        self.hinge_ws = torch.empty(max(self.ctx.hinge_loss_workspace(max_hits, self.capacity), 16),
+                                    dtype=torch.uint8, device=dev)
         self.gen = torch.Generator(device=dev)
         self.gen.manual_seed(seed)
         self.loss = torch.empty(3, dtype=torch.float32, device=dev)
@@ -151,7 +153,7 @@ class EmbeddingTrainer:
                                                       self.radius, self.k_max, rand,
                                                       self.capacity, out=self.pairs)
         self.ctx.hinge_loss(emb, pq, pa, pg, npairs, self.margin, self.w_genuine, loss=self.loss,
-                            d_emb=self.d_emb[:n])
+                            d_emb=self.d_emb[:n], workspace=self.hinge_ws)
         grads = self.ctx.embed_backward(self.d_emb[:n], self.ws)
         self.t += 1
         self.ctx.adam_step(self.theta, grads, self.m, self.v, self.t, lr=self.lr)

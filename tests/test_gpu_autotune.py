@@ -1,5 +1,6 @@
-"""Launch configurations (k-NN work partitioning, tensor-core ring depth) do
-not change any output, and the autotuner picks one of its candidates."""
+"""Launch configurations (k-NN work partitioning and candidate stage,
+tensor-core ring depth) do not change any output, and the autotuner picks one
+of its candidates."""
 import numpy as np
 import pytest
 import torch
@@ -38,12 +39,15 @@ def outputs(tf, args):
 def test_every_configuration_gives_the_same_results(finder, dtype):
     tf, args = finder
     tf.dtype = dtype
-    tf.ctx.set_tuned(knn_split=1)
+    tf.ctx.set_tuned(knn_split=1, knn_stage=16384)
     for blk in ("edge_encoder", "node_update", "edge_update", "classifier"):
         tf.ctx.set_tuned(**{f"tc_stages__{blk}__{dtype}": 3})
     ref = outputs(tf, args)
-    for split, stages in ((2, 2), (4, 3), (4, 2), (1, 4), (2, 5)):
-        tf.ctx.set_tuned(knn_split=split)
+    # stage 1024 (128 candidates of dimension 8) leaves most (event, plane)
+    # blocks reading their candidates from global memory
+    for split, stage, stages in ((2, 1024, 2), (4, 2048, 3), (4, 4096, 2), (1, 8192, 4),
+                                 (2, 1024, 5)):
+        tf.ctx.set_tuned(knn_split=split, knn_stage=stage)
         for blk in ("edge_encoder", "node_update", "edge_update", "classifier"):
             tf.ctx.set_tuned(**{f"tc_stages__{blk}__{dtype}": stages})
         got = outputs(tf, args)
@@ -57,6 +61,7 @@ def test_autotune_picks_candidates_and_keeps_results(finder):
     ref = outputs(tf, args)
     choice = tf.autotune(*args)
     assert choice["knn_split"] in (1, 2, 4)
+    assert choice["knn_stage"] in (1024, 2048, 4096, 8192, 16384)
     for blk in ("edge_encoder", "node_update", "edge_update", "classifier"):
         assert choice[f"tc_stages/{blk}/bf16"] in (2, 3, 4, 5)
     E = int(tf.eoff[args[-1]].item())
@@ -71,6 +76,8 @@ def test_set_tuned_rejects_bad_values(finder):
     from paper_2407_12119_gb300.etx import EtxError
     with pytest.raises(EtxError):
         tf.ctx.set_tuned(knn_split=3)
+    with pytest.raises(EtxError):
+        tf.ctx.set_tuned(knn_stage=3000)
     with pytest.raises(EtxError):
         tf.ctx.set_tuned(tc_stages__edge_update__bf16=6)
     with pytest.raises(EtxError):

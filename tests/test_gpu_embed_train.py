@@ -112,10 +112,54 @@ def test_hinge_loss_matches_oracle(etx):
     ctx.sync()
     L, Lg, Lf, dref = O.hinge_embedding_loss(emb, q, a, g, 1.0, 2.5)
     np.testing.assert_allclose(loss.cpu().numpy(), [L, Lg, Lf], rtol=2e-6)
-    # FP32 terms scattered with atomics: error far below 1e-5 of the largest entry
+    # FP32 terms summed per hit: error far below 1e-5 of the largest entry
     dg = d.cpu().numpy()
     assert np.abs(dg - dref).max() <= 1e-5 * np.abs(dref).max()
     assert cap > q.size
+
+
+def test_hinge_loss_fixed_order_and_any_pair_order(etx):
+    """The hinge loss and its gradient come out bit for bit the same on a
+    repeat; pairs in any order (here shuffled) give the oracle's values; a
+    pair with an index out of range is skipped and reported; a pair count
+    above the capacity is reported and uses no pair."""
+    rng = np.random.default_rng(11)
+    wl = WORKLOADS["batch500"]
+    b = drop_noise(wl.batch(6))
+    pid = compact_particle_ids(b)
+    D = wl.model.emb_widths[-1]
+    emb = (rng.normal(size=(b.n_hits, D)) * 0.3).astype(np.float32)
+    r, _ = rand_bits(rng, b.n_hits)
+    q, a, g = O.embedding_pairs(emb, b.plane, pid, b.hit_offsets, 1.2, 30, r, precision="fp32")
+    ctx = etx.Context(wl.model, b.n_events, b.n_hits, 1)
+    args = (cuda(emb), cuda(q.astype(np.int32)), cuda(a.astype(np.int32)), cuda(g.astype(np.uint8)),
+            cuda(np.array([q.size], np.int32)), 1.0, 2.0)
+    l1, d1 = (t.clone() for t in ctx.hinge_loss(*args))
+    l2, d2 = ctx.hinge_loss(*args)
+    ctx.sync()
+    assert torch.equal(l1, l2) and torch.equal(d1, d2)
+    L, Lg, Lf, dref = O.hinge_embedding_loss(emb, q, a, g, 1.0, 2.0)
+    np.testing.assert_allclose(l1.cpu().numpy(), [L, Lg, Lf], rtol=2e-6)
+    assert np.abs(d1.cpu().numpy() - dref).max() <= 1e-5 * np.abs(dref).max()
+    perm = rng.permutation(q.size)
+    ls, ds = ctx.hinge_loss(cuda(emb), cuda(q[perm].astype(np.int32)), cuda(a[perm].astype(np.int32)),
+                            cuda(g[perm].astype(np.uint8)), cuda(np.array([q.size], np.int32)), 1.0, 2.0)
+    ctx.sync()
+    np.testing.assert_allclose(ls.cpu().numpy(), [L, Lg, Lf], rtol=2e-6)
+    assert np.abs(ds.cpu().numpy() - dref).max() <= 1e-5 * np.abs(dref).max()
+    # an index out of range: that pair is left out of the loss and the gradient
+    qb = q.astype(np.int32).copy()
+    qb[0] = b.n_hits
+    ctx.hinge_loss(cuda(emb), cuda(qb), cuda(a.astype(np.int32)), cuda(g.astype(np.uint8)),
+                   cuda(np.array([q.size], np.int32)), 1.0, 2.0)
+    with pytest.raises(etx.EtxError):
+        ctx.sync()
+    # more pairs than the capacity: reported, nothing used (loss 0, gradient 0)
+    lc, dc = ctx.hinge_loss(*args[:4], cuda(np.array([q.size + 1], np.int32)), 1.0, 2.0)
+    with pytest.raises(etx.EtxError) as e:
+        ctx.sync()
+    assert e.value.status == etx.ETX_ERR_CAPACITY
+    assert not lc.any() and not dc.any()
 
 
 def test_embed_backward_matches_oracle(etx):
@@ -196,6 +240,28 @@ def test_embedding_training_reduces_the_loss(etx):
     tr.ctx.sync()
     print("embedding training: loss", first, "->", last)
     assert last[0] < 0.8 * first[0]
+
+
+def test_embedding_training_steps_are_reproducible(etx):
+    """Two trainers with the same seed give the same parameters bit for bit
+    after several steps (pairs, hinge gradient, reverse pass and Adam all in a
+    fixed order)."""
+    from paper_2407_12119_gb300.train import EmbeddingTrainer
+    wl = WORKLOADS["batch500"]
+    m = wl.model
+    b = drop_noise(wl.batch(4))
+    pid = compact_particle_ids(b)
+    args = [cuda(v) for v in (b.x, b.y, b.z, b.plane, pid, b.hit_offsets)]
+    thetas, losses = [], []
+    for _ in range(2):
+        tr = EmbeddingTrainer(m, pack_blob(m, wl.weights()), b.n_events, b.n_hits, lr=1e-3, seed=3)
+        for _ in range(4):
+            loss = tr.step(*args)
+        tr.ctx.sync()
+        thetas.append(tr.theta.clone())
+        losses.append(loss.clone())
+    assert torch.equal(thetas[0], thetas[1])
+    assert torch.equal(losses[0], losses[1])
 
 
 def test_device_embed_update_equals_a_reload(etx):
