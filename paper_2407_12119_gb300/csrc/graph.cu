@@ -97,58 +97,87 @@ __global__ void k_plane_bins(const int8_t* __restrict__ plane, const int32_t* __
   plane_off[t] = lo;
 }
 
-// Fast path for one source hit (compile-time D; candidate j's dimension d at
-// cand[j * cstep + d * cstride], staged or in global memory): one pass
-// over the candidates lists the qualifying ones (d2 < r2) in the warp's
-// scratch as (key, j) pairs, key = the FP32 bit pattern of d2 (order-preserving
-// for d2 >= 0), in ascending j (ballot compaction).  If more than k_max
-// qualify, a pair is kept iff fewer than k_max listed pairs are smaller than it
-// ((key, j) pairs are distinct, so this keeps exactly the k_max smallest by
-// (d2, j)); kept pairs are written in list order, i.e. ascending j.  Returns
-// false (nothing written) when more than kListCap qualify: the caller then
-// takes the general path.  The loops run over runtime trip counts so that the
-// code stays small (instruction-cache misses dominated the unrolled version).
-constexpr int kListCap = 256;  // (key, j) pairs per warp: 2 KB of shared memory
+// Fast path (compile-time D; candidate j's dimension d at
+// cand[j * cstep + d * cstride], staged or in global memory), two source hits
+// per warp: one pass over the candidates computes both sources' distances
+// from the same candidate loads (two independent chains) and lists each
+// source's qualifying candidates (d2 < r2) in its own per-warp scratch as
+// (key, j) pairs, key = the FP32 bit pattern of d2 (order-preserving for
+// d2 >= 0), in ascending j (ballot compaction).  Then per source: if more than
+// k_max qualify, a pair is kept iff fewer than k_max listed pairs are smaller
+// than it ((key, j) pairs are distinct, so this keeps exactly the k_max
+// smallest by (d2, j)); kept pairs are written in list order, i.e. ascending j.
+// A source with more than kListCap qualifying candidates is left to the
+// general path.  The loops run over runtime trip counts so that the code stays
+// small (instruction-cache misses dominated the unrolled version).
+constexpr int kListCap = 256;  // (key, j) pairs per list: 2 KB of shared memory
 
 // KM: 0 counts min(#inside, k_max) into cnt_or_off[i]; 1 writes (src, dst) at
 // offset cnt_or_off[i]; 2 writes dst at the fixed slot i * k_max and the count
 // into cnt_or_off[i] (a compaction pass forms the edge list).
+// The listing pass for sources i0 and (if two) i1: n0, n1 = qualifying counts.
 template <int KM, int D>
-__device__ __forceinline__ bool knn_source_list(const float* __restrict__ emb, int i,
-                                                const float* cand, int cstride, int cstep,
-                                                int n_cand, int c_lo,
-                                                float r2, int k_max, int32_t* cnt_or_off,
-                                                int32_t* __restrict__ src,
-                                                int32_t* __restrict__ dst, int lane,
-                                                uint64_t* list) {
+__device__ __forceinline__ void knn_scan2(const float* __restrict__ emb, int i0, int i1, bool two,
+                                          const float* cand, int cstride, int cstep, int n_cand,
+                                          float r2, int lane, uint64_t* list0, uint64_t* list1,
+                                          int& n0, int& n1) {
   const unsigned full = 0xffffffffu, lt_mask = (1u << lane) - 1u;
-  float ei[D];
+  float e0[D], e1[D];
 #pragma unroll
-  for (int d = 0; d < D; ++d) ei[d] = emb[(int64_t)i * D + d];
-  int n = 0;
+  for (int d = 0; d < D; ++d) {
+    e0[d] = emb[(int64_t)i0 * D + d];
+    e1[d] = two ? emb[(int64_t)i1 * D + d] : 0.f;
+  }
+  n0 = n1 = 0;
 #pragma unroll 1
   for (int j0 = 0; j0 < n_cand; j0 += 32) {
     const int j = j0 + lane;
-    bool in = false;
-    uint32_t key = 0;
+    bool in0 = false, in1 = false;
+    uint32_t k0 = 0, k1 = 0;
     if (j < n_cand) {
-      const float d2 = d2_fixed<D>(ei, cand + (int64_t)j * cstep, cstride);
-      in = d2 < r2;
-      key = __float_as_uint(d2);
+      const float* cj = cand + (int64_t)j * cstep;
+      float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const float c = cj[d * cstride];
+        const float t0 = __fsub_rn(e0[d], c), t1 = __fsub_rn(e1[d], c);
+        s0 = __fadd_rn(s0, __fmul_rn(t0, t0));
+        s1 = __fadd_rn(s1, __fmul_rn(t1, t1));
+      }
+      in0 = s0 < r2;
+      in1 = two && s1 < r2;
+      k0 = __float_as_uint(s0);
+      k1 = __float_as_uint(s1);
     }
-    const unsigned m = __ballot_sync(full, in);
-    if (KM != 0 && in) {
-      const int pos = n + __popc(m & lt_mask);
-      if (pos < kListCap) list[pos] = (static_cast<uint64_t>(key) << 32) | static_cast<uint32_t>(j);
+    const unsigned m0 = __ballot_sync(full, in0), m1 = __ballot_sync(full, in1);
+    if (KM != 0) {
+      if (in0) {
+        const int pos = n0 + __popc(m0 & lt_mask);
+        if (pos < kListCap) list0[pos] = (static_cast<uint64_t>(k0) << 32) | static_cast<uint32_t>(j);
+      }
+      if (in1) {
+        const int pos = n1 + __popc(m1 & lt_mask);
+        if (pos < kListCap) list1[pos] = (static_cast<uint64_t>(k1) << 32) | static_cast<uint32_t>(j);
+      }
     }
-    n += __popc(m);
+    n0 += __popc(m0);
+    n1 += __popc(m1);
   }
+  __syncwarp();
+}
+
+// The selection and output of one listed source; false (nothing written) when
+// its list overflowed.
+template <int KM>
+__device__ __forceinline__ bool knn_emit(int i, int n, const uint64_t* list, int c_lo, int k_max,
+                                         int32_t* cnt_or_off, int32_t* __restrict__ src,
+                                         int32_t* __restrict__ dst, int lane) {
+  const unsigned full = 0xffffffffu, lt_mask = (1u << lane) - 1u;
   if (KM == 0) {
     if (lane == 0) cnt_or_off[i] = min(n, k_max);
     return true;
   }
   if (n > kListCap) return false;
-  __syncwarp();
   const int64_t base = KM == 2 ? (int64_t)i * k_max : (int64_t)cnt_or_off[i];
   constexpr int R = kListCap / 32;  // list entries per lane: q = 32 r + lane
   bool keep[R];
@@ -196,7 +225,7 @@ k_knn(const float* __restrict__ emb, int D, const int32_t* __restrict__ plane_of
       float radius, int k_max, int32_t* __restrict__ cnt_or_off, int64_t n_hits,
       int32_t* __restrict__ src, int32_t* __restrict__ dst, int64_t capacity, int* err,
       int split, int stage_floats) {
-  // [D][n_cand] within the first stage_floats, then kListCap (key, j) pairs per warp
+  // [D][n_cand] within the first stage_floats, then two lists of kListCap (key, j) pairs per warp
   extern __shared__ float cand_s[];
   uint64_t* list_s = reinterpret_cast<uint64_t*>(cand_s + stage_floats);  // per-warp pair lists
   // `split` blocks share the sources of one (event, plane): block `part` takes
@@ -237,12 +266,8 @@ k_knn(const float* __restrict__ emb, int D, const int32_t* __restrict__ plane_of
   const int cstep = staged ? 1 : D;              // stride between candidates
   const float r2 = __fmul_rn(radius, radius);
 
-  for (int i = s_lo + part * WPB + warp; i < s_hi; i += WPB * split) {
-    if constexpr (DT > 0) {
-      if (knn_source_list<KM, DT>(emb, i, cbase, cstride, cstep, n_cand, c_lo, r2, k_max,
-                                  cnt_or_off, src, dst, lane, list_s + kListCap * warp))
-        continue;
-    }
+  // The general path for one source (any D, candidates anywhere, any count).
+  auto general = [&](int i) {
     float ei[kMaxDim];
     for (int d = 0; d < D; ++d) ei[d] = emb[(int64_t)i * D + d];
     // pass A: count the hits inside the radius
@@ -255,7 +280,7 @@ k_knn(const float* __restrict__ emb, int D, const int32_t* __restrict__ plane_of
     }
     if (KM == 0) {
       if (lane == 0) cnt_or_off[i] = min(cnt, k_max);
-      continue;
+      return;
     }
     const int64_t base = KM == 2 ? (int64_t)i * k_max : (int64_t)cnt_or_off[i];
     uint32_t kth = 0xffffffffu;  // keep keys < kth, plus `take_eq` keys == kth
@@ -315,6 +340,23 @@ k_knn(const float* __restrict__ emb, int D, const int32_t* __restrict__ plane_of
       written += __popc(inm);
     }
     if (KM == 2 && lane == 0) cnt_or_off[i] = written;
+  };
+  // Sources in pairs per warp: i and i + WPB * split
+  const int stride = WPB * split;
+  for (int i = s_lo + part * WPB + warp; i < s_hi; i += 2 * stride) {
+    const int i2 = i + stride;
+    const bool two = i2 < s_hi;
+    bool done0 = false, done1 = !two;
+    if constexpr (DT > 0) {
+      uint64_t* l0 = list_s + 2 * kListCap * warp;
+      int n0, n1;
+      knn_scan2<KM, DT>(emb, i, i2, two, cbase, cstride, cstep, n_cand, r2, lane, l0,
+                        l0 + kListCap, n0, n1);
+      done0 = knn_emit<KM>(i, n0, l0, c_lo, k_max, cnt_or_off, src, dst, lane);
+      if (two) done1 = knn_emit<KM>(i2, n1, l0 + kListCap, c_lo, k_max, cnt_or_off, src, dst, lane);
+    }
+    if (!done0) general(i);
+    if (!done1) general(i2);
   }
 }
 
@@ -366,7 +408,7 @@ cudaError_t launch_build_graph(etx_ctx* ctx, const float* emb, const int8_t* pla
   const int split = ctx->knn_split;
   const int stage = ctx->knn_stage;  // a multiple of 4 in [1024, kStageMaxFloats]
   const unsigned blocks = (unsigned)n_events * (unsigned)(P - 1) * (unsigned)split;
-  const size_t smem = (size_t)stage * sizeof(float) + kKnnThreads / 32 * kListCap * sizeof(uint64_t);
+  const size_t smem = (size_t)stage * sizeof(float) + kKnnThreads / 32 * 2 * kListCap * sizeof(uint64_t);
   // hits of the last plane get no block: start from zero counts
   cudaError_t e0 = cudaMemsetAsync(cnt, 0, (size_t)(n_hits + 1) * sizeof(int32_t), s);
   if (e0 != cudaSuccess) return e0;
@@ -428,7 +470,7 @@ cudaError_t launch_plane_bins(etx_ctx* ctx, const int8_t* plane, const int32_t* 
 }
 
 cudaError_t knn_set_smem_attr() {
-  const int smem = (int)(kStageMaxFloats * sizeof(float) + kKnnThreads / 32 * kListCap * sizeof(uint64_t));
+  const int smem = (int)(kStageMaxFloats * sizeof(float) + kKnnThreads / 32 * 2 * kListCap * sizeof(uint64_t));
   const void* ks[] = {(const void*)k_knn<0, 0>, (const void*)k_knn<1, 0>, (const void*)k_knn<2, 0>,
                       (const void*)k_knn<0, 4>, (const void*)k_knn<1, 4>, (const void*)k_knn<2, 4>,
                       (const void*)k_knn<0, 8>, (const void*)k_knn<1, 8>, (const void*)k_knn<2, 8>};
