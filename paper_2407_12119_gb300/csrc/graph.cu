@@ -2,21 +2,27 @@
 //
 // Hits arrive plane-sorted per event, so the candidates of every source hit
 // on plane p (the hits of planes p+1 and p+2) form one contiguous index range.
-// One block per (event, plane): the candidate embeddings are staged in shared
-// memory (structure of arrays, so lane j reads candidate j bank-conflict free)
-// when they fit the block's stage, else read from global memory; one warp per
-// source hit, lanes over candidates, ballot + popc to count and compact the
-// hits inside the radius.  The stage size is a launch parameter (autotuned):
-// a stage sized for the typical event keeps more blocks resident per SM than
-// one sized for the largest.  When more than k_max hits qualify, the
-// k_max-th smallest squared distance is found by a 32-step radix select on
-// the FP32 bit patterns (non-negative floats order like their bits); ties at
-// that value are taken in ascending candidate index, which realises the
-// (d2, j) order.
+// One block (or 2 or 4) per (event, plane): the candidate embeddings are
+// staged in shared memory (structure of arrays, so lane j reads candidate j
+// bank-conflict free) when they fit the block's stage, else read from global
+// memory.  The stage size and the blocks per (event, plane) are launch
+// parameters (autotuned): a stage sized for the typical event keeps more
+// blocks resident per SM than one sized for the largest.  A warp takes two
+// source hits at a time, lanes over candidates: one pass computes both
+// sources' FP32 distances from the same candidate loads and ballot-compacts
+// the hits inside the radius into a (d2, j) list per source; when more than
+// k_max qualify, a listed pair is kept iff fewer than k_max listed pairs are
+// smaller, which realises the (d2, j) order.  A source with more than 256
+// qualifying hits takes the general path: the k_max-th smallest squared
+// distance by a 32-step radix select on the FP32 bit patterns (non-negative
+// floats order like their bits), ties at that value in ascending candidate
+// index.
 //
-// Two launches of the same kernel: pass 0 writes per-hit counts, an
-// exclusive scan turns them into CSR offsets (which is also the src-CSR of the
-// edge list), pass 1 writes the edges at those offsets in (i, j) order.
+// Either one pass writes each source's kept edges into k_max fixed slots with
+// its count, and a compaction after the scan of the counts forms the edge
+// list; or (when the slots do not fit the context) a counting pass, the scan,
+// and an emitting pass at the scanned offsets.  The counts' scan is also the
+// src-CSR of the edge list; edges come out in (i, j) order.
 #include <algorithm>
 
 #include "etx_internal.cuh"
