@@ -69,3 +69,19 @@ def test_null_handles(etx):
     assert L.etx_embed(None, None, None, None, 0, None, None) == etx.ETX_ERR_ARG
     assert L.etx_launch_count(None) == -1
     assert L.etx_last_error(None) == b"no context"
+
+
+def test_workspace_sizes_are_host_functions(etx):
+    """The workspace-size calls run on the host: they grow with their sizes,
+    cover at least the arrays the call keeps there, and refuse negative sizes."""
+    L = etx.lib()
+    w = lambda n, cap: int(L.etx_hinge_loss_workspace(n, cap))
+    # per pair: a coefficient and the pair's id in two key indices (3 x 4 bytes);
+    # per hit: a count and two offset arrays of n + 1 entries (3 x 4 bytes)
+    for n, cap in [(0, 0), (1, 1), (1000, 52000), (100000, 5200000)]:
+        assert w(n, cap) >= 12 * cap + 12 * (n + 1)
+        assert w(n, cap) % 16 == 0
+    assert w(1000, 52000) <= w(1001, 52000) <= w(1001, 52001) < w(1101, 53000)
+    assert w(-1, 10) == 0 and w(10, -1) == 0
+    t = lambda b, n: int(L.etx_track_metrics_workspace(b, n))
+    assert t(10, 1000) <= t(10, 2000) and t(-1, 5) == 0
