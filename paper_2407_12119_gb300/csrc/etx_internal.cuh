@@ -281,9 +281,8 @@ cudaError_t launch_wgrad_tc(etx_ctx* ctx, const float* A, int lda, const float* 
                             int64_t R_host, const int32_t* R_dev, int64_t R_cap, int splits,
                             float* P, cudaStream_t s);
 
-// gnn_tc.cu (hidden == 128 only)
-// ctx->h_lp = h rounded to BF16 (or e4m3) for rows [0, N)
-cudaError_t launch_h_lowp(etx_ctx* ctx, int64_t N, bool f8, cudaStream_t s);
+// gnn_tc.cu (hidden == 128 only; the edge encoder gathers ctx->h_lp, the copy
+// of h that the node encoder writes in the operand type)
 // f8: e4m3 operands (kind::f8f6f4), else BF16 (kind::f16)
 // es: the edge stream is stored in BF16 (dtype ETX_BF16_EDGE_STORE)
 cudaError_t launch_edge_encoder_tc(etx_ctx* ctx, int64_t N, const int32_t* src, const int32_t* dst,

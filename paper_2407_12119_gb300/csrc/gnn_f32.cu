@@ -37,6 +37,12 @@ struct MlpArgs {
   ClassifierF32 cls;
   const int32_t* row_lo_dev;    // TRI: first row (nullptr: 0)
   int64_t e_rows;               // TRI: rows of e (edge ids are clamped below it)
+  // NODE_ENC: also write h rounded to the tensor-core operand type for the edge
+  // encoder's gathers (0: none, 1: BF16 rows of 2H bytes, 2: e4m3 rows of H
+  // bytes, each value times lp_inv, the reciprocal activation scale)
+  uint8_t* lp_out;
+  int lp_kind;
+  float lp_inv;
 };
 
 // ---------------------------------------------------------------------------
@@ -368,6 +374,20 @@ __global__ void __launch_bounds__(kTileThreads) k_mlp(MlpArgs a) {
           if (res) v += res[c];
           out[c] = v;
         }
+        if constexpr (MODE == NODE_ENC && H >= 64) {
+          // the low-precision copy: four consecutive columns per group of j
+#pragma unroll
+          for (int g = 0; g < H / 64; ++g) {
+            const int c = ColMap<H>::col(tx, 4 * g);
+            const float* v = &acc.v[r][4 * g];
+            if (a.lp_kind == 1)
+              *reinterpret_cast<uint2*>(a.lp_out + 2 * (row * H + c)) =
+                  make_uint2(bf16x2(v[0], v[1]), bf16x2(v[2], v[3]));
+            else if (a.lp_kind == 2)
+              *reinterpret_cast<uint32_t*>(a.lp_out + row * H + c) =
+                  e4m3x4(v[0] * a.lp_inv, v[1] * a.lp_inv, v[2] * a.lp_inv, v[3] * a.lp_inv);
+          }
+        }
       }
     }
   }
@@ -412,10 +432,18 @@ cudaError_t forward(etx_ctx* ctx, const float* x, const float* y, const float* z
   };
 
   // the node encoder (K = 3) always runs on the FP32 SIMT path
+  // and writes the copy of h that the tensor-core edge encoder gathers (e4m3:
+  // times the reciprocal of that encoder's input scale)
   a.blk = ctx->w.node_enc;
-  launch_mlp<H, NODE_ENC>(ctx, a, N, s);
   if (tc) {
-    chain(launch_h_lowp(ctx, N, f8, s));
+    a.lp_out = ctx->h_lp;
+    a.lp_kind = f8 ? 2 : 1;
+    a.lp_inv = f8 && !ctx->fp8_act.empty() ? 1.f / ctx->fp8_act[0] : 1.f;
+  }
+  launch_mlp<H, NODE_ENC>(ctx, a, N, s);
+  a.lp_out = nullptr;
+  a.lp_kind = 0;
+  if (tc) {
     chain(launch_edge_encoder_tc(ctx, N, src, dst, n_edges_dev, f8, es, s));
   } else {
     a.blk = ctx->w.edge_enc;

@@ -819,21 +819,6 @@ cudaError_t launch_tc(etx_ctx* ctx, const char* name, const TcArgs& a, int64_t m
   }
 }
 
-// h (FP32, [n][128]) rounded to BF16 rows of 256 bytes or e4m3 rows of 128 bytes
-// (e4m3: h * inv, inv the reciprocal power-of-two activation scale).
-template <bool F8>
-__global__ void k_h_lowp(const float* __restrict__ h, uint8_t* __restrict__ out, int64_t n4,
-                         float inv) {
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    const float4 v = reinterpret_cast<const float4*>(h)[q];
-    if constexpr (F8)
-      reinterpret_cast<uint32_t*>(out)[q] = pack_e4m3x4(v.x * inv, v.y * inv, v.z * inv, v.w * inv);
-    else
-      reinterpret_cast<uint2*>(out)[q] = make_uint2(pack_bf16(v.x, v.y), pack_bf16(v.z, v.w));
-  }
-}
-
 TcArgs base_args(etx_ctx* ctx, int64_t N, const int32_t* src, const int32_t* dst,
                  const int32_t* n_edges_dev, float* logits) {
   TcArgs a{};
@@ -917,21 +902,6 @@ cudaError_t launch_edge_update_tc(etx_ctx* ctx, int k, int64_t N, const int32_t*
             act_scale(ctx, 5 + 4 * k));
   return launch_any<TC_EDGE_UPD>(ctx, f8, "gnn_edge_update_bf16", "gnn_edge_update_fp8", a,
                                  ctx->cfg.max_edges, s, es, "gnn_edge_update_bf16s");
-}
-
-cudaError_t launch_h_lowp(etx_ctx* ctx, int64_t N, bool f8, cudaStream_t s) {
-  const int64_t n4 = N * H / 4;
-  if (n4 == 0) return cudaSuccess;
-  const int grid = grid_for(ctx, f8 ? (const void*)k_h_lowp<true> : (const void*)k_h_lowp<false>,
-                            256, 0, (n4 + 255) / 256);
-  // the copy feeds the edge encoder: its e4m3 input scale
-  if (f8)
-    launch(ctx, "gnn_h_lowp", k_h_lowp<true>, grid, 256, 0, s, (const float*)ctx->h, ctx->h_lp, n4,
-           1.f / act_scale(ctx, 0));
-  else
-    launch(ctx, "gnn_h_lowp", k_h_lowp<false>, grid, 256, 0, s, (const float*)ctx->h, ctx->h_lp, n4,
-           1.f);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_classifier_tc(etx_ctx* ctx, int64_t N, const int32_t* n_edges_dev, float* logits,
