@@ -457,7 +457,8 @@ etx_status etx_tracks_from_triplets(etx_ctx* ctx, const int32_t* src, const int3
  * Training of the hit embedding (Sec. 5.1, Eq. 2-3).  A step is
  *   etx_embed_forward_train -> etx_embedding_pairs -> etx_hinge_loss ->
  *   etx_embed_backward -> etx_adam_step on the embedding parameters ->
- *   etx_load_weights.
+ *   etx_set_embed_params (on the device; etx_load_weights with a host blob
+ *   does the same through the host).
  * The batch has its noise hits removed (Sec. 5.1), hits plane-sorted per
  * event as everywhere.
  *
